@@ -1,0 +1,320 @@
+"""FP64 CPU oracle of the differentiable 3D Gaussian splatting mapping step.
+
+TEST INFRASTRUCTURE ONLY.  The test-suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg use this module; the product package never imports
+it and shares no code with it.  The arithmetic lives in ``gs_oracle.c`` (plain
+C, FP64, written from the mathematics); this file only marshals numpy arrays.
+
+Paper anchors: compositing and transmittance (Supp. D.2), the photometric loss
+(Supp. D.4), the lifecycle scores (Supp. E.1, E.2) and their aggregation over
+chunks (Sec. 3.3.2).  The readings the paper leaves open (projection, SH colour,
+binning order, thresholds, SSIM window, Adam) are listed in the C header.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+          "-ffp-contract=off", "-fno-fast-math", "-fexcess-precision=standard"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library (plain gcc; no CUDA)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "gs_oracle.h"))):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Camera(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3), ("fx", C.c_double), ("fy", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class _Cfg(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("near_z", C.c_double),
+                ("dilation", C.c_double), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
+                ("t_min", C.c_double), ("tan_clamp", C.c_double), ("bg", C.c_double * 3),
+                ("fp32_positions", C.c_int32)]
+
+
+class _Params(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sh_degree", C.c_int32),
+                ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class _Projected(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in (
+        "u", "v", "z", "conic", "cov2d", "rgb", "rgb_clamped", "rgb_raw", "opacity", "radius",
+        "radius_exact", "rect", "tiles_touched", "u32", "v32", "z32")]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        L.or_sh_eval.argtypes = [i32, vp, vp, vp]
+        L.or_quat_to_rot.argtypes = [vp, vp]
+        L.or_project.argtypes = [C.POINTER(_Params), C.POINTER(_Camera), C.POINTER(_Cfg), C.POINTER(_Projected)]
+        L.or_bin.argtypes = [C.POINTER(_Projected), i64, C.POINTER(_Camera), C.POINTER(_Cfg), i64, vp, vp, vp]
+        L.or_bin.restype = i64
+        L.or_render.argtypes = [C.POINTER(_Projected), vp, vp, C.POINTER(_Camera), C.POINTER(_Cfg),
+                                vp, vp, vp, vp, vp, vp]
+        L.or_loss.argtypes = [vp, vp, i32, i32, i32, d, vp, vp]
+        L.or_loss.restype = d
+        L.or_ssim_map.argtypes = [vp, vp, i32, i32, i32, vp]
+        L.or_render_backward.argtypes = [C.POINTER(_Projected), i64, vp, vp, C.POINTER(_Camera), C.POINTER(_Cfg),
+                                         vp, vp, vp, vp, d, d, d, vp, vp, vp]
+        L.or_project_backward.argtypes = [C.POINTER(_Params), C.POINTER(_Camera), C.POINTER(_Cfg),
+                                          C.POINTER(_Projected), vp, vp, vp, vp, vp, vp]
+        L.or_adam.argtypes = [i64, vp, vp, vp, vp, vp, d, d, d, i64]
+        L.or_prune_finalize.argtypes = [i64, vp, vp, vp, i32, d, d, vp, vp, vp, vp, vp]
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+@dataclass
+class Cfg:
+    """Rasteriser constants (readings R2-R8 of the C header)."""
+    tile_w: int = 16
+    tile_h: int = 16
+    near_z: float = 0.2
+    dilation: float = 0.3
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    t_min: float = 1e-4
+    tan_clamp: float = 1.3
+    bg: tuple = (0.0, 0.0, 0.0)
+    fp32_positions: bool = True
+
+    def c(self):
+        return _Cfg(self.tile_w, self.tile_h, self.near_z, self.dilation, self.alpha_min, self.alpha_max,
+                    self.t_min, self.tan_clamp, (C.c_double * 3)(*self.bg), int(self.fp32_positions))
+
+
+def _cam(cam):
+    R = np.asarray(cam["R"], dtype=np.float64).reshape(9)
+    t = np.asarray(cam["t"], dtype=np.float64).reshape(3)
+    return _Camera((C.c_double * 9)(*R), (C.c_double * 3)(*t), float(cam["fx"]), float(cam["fy"]),
+                   float(cam["cx"]), float(cam["cy"]), int(cam["width"]), int(cam["height"]))
+
+
+def grid(cam, cfg: Cfg):
+    return ((int(cam["width"]) + cfg.tile_w - 1) // cfg.tile_w,
+            (int(cam["height"]) + cfg.tile_h - 1) // cfg.tile_h)
+
+
+class Params:
+    """FP64 array-of-structures parameters (keeps the arrays alive for ctypes)."""
+
+    def __init__(self, p):
+        n = int(np.asarray(p["means"]).shape[0])
+        self.n = n
+        self.sh_degree = int(p["sh_degree"])
+        K = (self.sh_degree + 1) ** 2
+        self.means = _f64(p["means"], (n, 3))
+        self.log_scales = _f64(p["log_scales"], (n, 3))
+        self.quats = _f64(p["quats"], (n, 4))
+        self.opacity_logits = _f64(p["opacity_logits"], (n,))
+        self.sh = _f64(p["sh"], (n, K, 3))
+
+    def c(self):
+        return _Params(self.n, self.sh_degree, _ptr(self.means), _ptr(self.log_scales), _ptr(self.quats),
+                       _ptr(self.opacity_logits), _ptr(self.sh))
+
+    def as_dict(self):
+        return dict(means=self.means, log_scales=self.log_scales, quats=self.quats,
+                    opacity_logits=self.opacity_logits, sh=self.sh, sh_degree=self.sh_degree)
+
+
+@dataclass
+class Projected:
+    n: int
+    arrays: dict = field(default_factory=dict)
+
+    def __getitem__(self, k):
+        return self.arrays[k]
+
+    def c(self):
+        return _Projected(*[_ptr(self.arrays[k]) for k, _ in _Projected._fields_])
+
+
+def sh_eval(D, d):
+    """Real SH values (and Cartesian partial derivatives) at direction d."""
+    K = (D + 1) ** 2
+    d = _f64(d, (3,))
+    Y = np.zeros(K)
+    dY = np.zeros((K, 3))
+    lib().or_sh_eval(D, _ptr(d), _ptr(Y), _ptr(dY))
+    return Y, dY
+
+
+def quat_to_rot(q):
+    q = _f64(q, (4,))
+    R = np.zeros(9)
+    lib().or_quat_to_rot(_ptr(q), _ptr(R))
+    return R.reshape(3, 3)
+
+
+def project(params, cam, cfg: Cfg) -> Projected:
+    P = params if isinstance(params, Params) else Params(params)
+    n = P.n
+    a = dict(
+        u=np.zeros(n), v=np.zeros(n), z=np.zeros(n), conic=np.zeros((n, 3)), cov2d=np.zeros((n, 3)),
+        rgb=np.zeros((n, 3)), rgb_clamped=np.zeros((n, 3), np.int32), rgb_raw=np.zeros((n, 3)),
+        opacity=np.zeros(n), radius=np.zeros(n, np.int32), radius_exact=np.zeros(n),
+        rect=np.zeros((n, 4), np.int32), tiles_touched=np.zeros(n, np.int32),
+        u32=np.zeros(n, np.float32), v32=np.zeros(n, np.float32), z32=np.zeros(n, np.float32))
+    pr = Projected(n, a)
+    cp, cc, cf, co = P.c(), _cam(cam), cfg.c(), pr.c()
+    lib().or_project(C.byref(cp), C.byref(cc), C.byref(cf), C.byref(co))
+    return pr
+
+
+def bin_pairs(pr: Projected, cam, cfg: Cfg):
+    """Pair list ordered by (tile, depth, Gaussian index): keys, values, ranges."""
+    GW, GH = grid(cam, cfg)
+    cc, cf, co = _cam(cam), cfg.c(), pr.c()
+    total = lib().or_bin(C.byref(co), pr.n, C.byref(cc), C.byref(cf), 0, None, None, None)
+    keys = np.zeros(max(total, 1), np.uint64)
+    vals = np.zeros(max(total, 1), np.int32)
+    ranges = np.zeros((GW * GH, 2), np.int64)
+    lib().or_bin(C.byref(co), pr.n, C.byref(cc), C.byref(cf), total, _ptr(keys), _ptr(vals), _ptr(ranges))
+    return keys[:total], vals[:total], ranges
+
+
+def render(pr: Projected, vals, ranges, cam, cfg: Cfg):
+    W, H = int(cam["width"]), int(cam["height"])
+    out = dict(img=np.zeros((3, H, W)), depth=np.zeros((H, W)), T_final=np.zeros((H, W)),
+               n_contrib=np.zeros((H, W), np.int32), last_pos=np.zeros((H, W), np.int64),
+               flags=np.zeros((H, W), np.int32))
+    vals = np.ascontiguousarray(vals, np.int32)
+    ranges = np.ascontiguousarray(ranges, np.int64)
+    cc, cf, co = _cam(cam), cfg.c(), pr.c()
+    lib().or_render(C.byref(co), _ptr(vals), _ptr(ranges), C.byref(cc), C.byref(cf),
+                    *[_ptr(out[k]) for k in ("img", "depth", "T_final", "n_contrib", "last_pos", "flags")])
+    return out
+
+
+def loss(img, target, lambda_dssim=0.2, grad=True):
+    img = _f64(img)
+    target = _f64(target)
+    Cc, H, W = img.shape
+    dL = np.zeros_like(img) if grad else None
+    ssim = np.zeros(1)
+    L = lib().or_loss(_ptr(img), _ptr(target), Cc, H, W, float(lambda_dssim), _ptr(dL), _ptr(ssim))
+    return L, dL, float(ssim[0])
+
+
+def ssim_map(x, y):
+    x = _f64(x)
+    y = _f64(y)
+    Cc, H, W = x.shape
+    out = np.zeros_like(x)
+    lib().or_ssim_map(_ptr(x), _ptr(y), Cc, H, W, _ptr(out))
+    return out
+
+
+def render_backward(pr: Projected, vals, ranges, cam, cfg: Cfg, dL_dimg, img, target, *,
+                    dL_ddepth=None, tau_err=0.1, loss_v=0.0, mask_tol=1e-4, stats=None):
+    """Returns grad2d (n,10), stats (n,6) (accumulated into `stats` if given) and kappa_amb (n,)."""
+    n = pr.n
+    grad2d = np.zeros((n, 10))
+    if stats is None:
+        stats = np.zeros((n, 6))
+    kappa_amb = np.zeros(n)
+    vals = np.ascontiguousarray(vals, np.int32)
+    ranges = np.ascontiguousarray(ranges, np.int64)
+    dL_dimg = _f64(dL_dimg)
+    img = _f64(img)
+    target = _f64(target)
+    dL_ddepth = None if dL_ddepth is None else _f64(dL_ddepth)
+    cc, cf, co = _cam(cam), cfg.c(), pr.c()
+    lib().or_render_backward(C.byref(co), n, _ptr(vals), _ptr(ranges), C.byref(cc), C.byref(cf),
+                             _ptr(dL_dimg), _ptr(dL_ddepth), _ptr(img), _ptr(target), float(tau_err),
+                             float(loss_v), float(mask_tol), _ptr(grad2d), _ptr(stats), _ptr(kappa_amb))
+    return grad2d, stats, kappa_amb
+
+
+def project_backward(params, cam, cfg: Cfg, pr: Projected, grad2d):
+    P = params if isinstance(params, Params) else Params(params)
+    n, K = P.n, (P.sh_degree + 1) ** 2
+    g = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
+             opacity_logits=np.zeros(n), sh=np.zeros((n, K, 3)))
+    grad2d = _f64(grad2d, (n, 10))
+    cp, cc, cf, co = P.c(), _cam(cam), cfg.c(), pr.c()
+    lib().or_project_backward(C.byref(cp), C.byref(cc), C.byref(cf), C.byref(co), _ptr(grad2d),
+                              *[_ptr(g[k]) for k in ("means", "log_scales", "quats", "opacity_logits", "sh")])
+    return g
+
+
+def adam(p, g, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-15):
+    """In-place Adam on flat FP64 arrays; lr is per element (broadcast if scalar)."""
+    n = p.size
+    lr = np.broadcast_to(np.asarray(lr, np.float64), p.shape).reshape(-1).copy()
+    for a in (p, g, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().or_adam(n, _ptr(p), _ptr(g), _ptr(m), _ptr(v), _ptr(lr), beta1, beta2, eps, int(step))
+
+
+def prune_finalize(omega, kappa, gamma, n_views, tau_d=5.0, tau_p=0.99, densify=None, prune_max=None):
+    omega, kappa, gamma = _f64(omega), _f64(kappa), _f64(gamma)
+    n = omega.size
+    S_d, S_p = np.zeros(n), np.zeros(n)
+    densify = np.zeros(n, np.uint8) if densify is None else densify
+    prune_max = np.zeros(n) if prune_max is None else prune_max
+    prune = np.zeros(n, np.uint8)
+    lib().or_prune_finalize(n, _ptr(omega), _ptr(kappa), _ptr(gamma), int(n_views), tau_d, tau_p,
+                            _ptr(S_d), _ptr(S_p), _ptr(densify), _ptr(prune_max), _ptr(prune))
+    return dict(S_d=S_d, S_p=S_p, densify=densify, prune_max=prune_max, prune=prune)
+
+
+# --------------------------------------------------------------------------
+# Whole-view compositions used by the tests and the CPU baseline
+# --------------------------------------------------------------------------
+
+def forward(params, cam, cfg: Cfg):
+    P = params if isinstance(params, Params) else Params(params)
+    pr = project(P, cam, cfg)
+    keys, vals, ranges = bin_pairs(pr, cam, cfg)
+    out = render(pr, vals, ranges, cam, cfg)
+    out.update(proj=pr, keys=keys, vals=vals, ranges=ranges, params=P)
+    return out
+
+
+def loss_and_grads(params, cam, cfg: Cfg, target, lambda_dssim=0.2, tau_err=0.1, stats=None):
+    """One view: forward, loss, backward to every parameter (FP64)."""
+    f = forward(params, cam, cfg)
+    L, dL, ssim = loss(f["img"], target, lambda_dssim)
+    grad2d, stats, kamb = render_backward(f["proj"], f["vals"], f["ranges"], cam, cfg, dL, f["img"], target,
+                                          tau_err=tau_err, loss_v=L, stats=stats)
+    g = project_backward(f["params"], cam, cfg, f["proj"], grad2d)
+    f.update(loss=L, dL_dimg=dL, ssim=ssim, grad2d=grad2d, stats=stats, kappa_amb=kamb, grads=g)
+    return f

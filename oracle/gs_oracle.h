@@ -1,0 +1,137 @@
+/*
+ * gs_oracle.h -- interface of the FP64 CPU oracle of the differentiable
+ * 3D Gaussian splatting mapping step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  The oracle is loaded by the test-suite, by the
+ * package's smoke check and by the benchmark's CPU-baseline leg.  Nothing on the
+ * product path links, imports or calls it, and it shares no code with the CUDA
+ * sources: every formula below is written out again from the mathematics.
+ *
+ * Conventions (the readings the paper leaves open; see the header of
+ * gs_oracle.c for the list):
+ *   - parameters are array-of-structures FP64: means n*3, log_scales n*3,
+ *     quats n*4 (w,x,y,z, unnormalised), opacity_logits n, sh n*(D+1)^2*3
+ *     (coefficient-major, RGB-minor);
+ *   - the camera maps world to camera frame, x right, y down, z forward;
+ *     pixel (i, j) samples the continuous image point (i + 0.5, j + 0.5);
+ *   - images are planar [3][H][W].
+ */
+#ifndef GS_ORACLE_H
+#define GS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double R[9];            /* world -> camera rotation, row-major */
+    double t[3];            /* world -> camera translation */
+    double fx, fy, cx, cy;  /* pinhole intrinsics in pixels */
+    int32_t width, height;
+} or_camera;
+
+typedef struct {
+    int32_t tile_w, tile_h;
+    double near_z;          /* cull z <= near_z */
+    double dilation;        /* added to the diagonal of the 2D covariance */
+    double alpha_min;       /* skip alpha < alpha_min */
+    double alpha_max;       /* clamp alpha to alpha_max */
+    double t_min;           /* stop before blending when T*(1-alpha) < t_min */
+    double tan_clamp;       /* EWA Jacobian evaluated at x/z clamped to tan_clamp * W/(2 fx) */
+    double bg[3];           /* background colour */
+    int32_t fp32_positions; /* 1: u, v, z and the tile rectangle follow the FP32
+                               evaluation order (bit-identical on every IEEE
+                               implementation); 0: plain FP64 throughout */
+} or_cfg;
+
+typedef struct {
+    int64_t n;
+    int32_t sh_degree;
+    const double *means, *log_scales, *quats, *opacity_logits, *sh;
+} or_params;
+
+/* Per-Gaussian projection record (caller-allocated arrays of n entries). */
+typedef struct {
+    double *u, *v, *z;       /* pixel position and camera depth used for rendering */
+    double *conic;           /* n*3: (a, b, c), inverse of the dilated 2D covariance */
+    double *cov2d;           /* n*3: (A, B, C), the dilated 2D covariance */
+    double *rgb;             /* n*3: colour after the clamp at 0 */
+    int32_t *rgb_clamped;    /* n*3: 1 where the clamp at 0 was active */
+    double *rgb_raw;         /* n*3: colour before the clamp */
+    double *opacity;         /* n */
+    int32_t *radius;         /* n: integer pixel radius, 0 = culled */
+    double *radius_exact;    /* n: 3*sqrt(lambda_max) before the ceiling */
+    int32_t *rect;           /* n*4: tile rectangle xmin, ymin, xmax, ymax (max exclusive) */
+    int32_t *tiles_touched;  /* n */
+    float *u32, *v32, *z32;  /* n: the FP32 evaluation of u, v and camera depth */
+} or_projected;
+
+/* Real spherical harmonics of degree <= D at unit direction d; Y gets (D+1)^2
+ * values, dY (nullable) the (D+1)^2 x 3 partial derivatives with respect to the
+ * three Cartesian components of d. */
+void or_sh_eval(int32_t D, const double d[3], double *Y, double *dY);
+
+/* Quaternion (w,x,y,z), normalised inside, to a row-major rotation matrix. */
+void or_quat_to_rot(const double q[4], double R[9]);
+
+void or_project(const or_params *p, const or_camera *cam, const or_cfg *cfg, or_projected *out);
+
+/* Pair list: one (key, Gaussian) entry per overlapped tile, ordered by
+ * (tile, depth, Gaussian index).  Returns the number of pairs; arrays are
+ * written only if capacity suffices.  ranges gets [tiles][2] = start, end. */
+int64_t or_bin(const or_projected *pr, int64_t n, const or_camera *cam, const or_cfg *cfg,
+               int64_t capacity, uint64_t *keys, int32_t *vals, int64_t *ranges);
+
+/* Pixel flags returned by or_render. */
+#define OR_FLAG_NEAR_ALPHA_MIN 1
+#define OR_FLAG_NEAR_T_CUT     2
+#define OR_FLAG_NEAR_ALPHA_MAX 4
+
+void or_render(const or_projected *pr, const int32_t *vals, const int64_t *ranges,
+               const or_camera *cam, const or_cfg *cfg,
+               double *img, double *depth, double *T_final, int32_t *n_contrib,
+               int64_t *last_pos, int32_t *flags);
+
+/* Photometric loss (1-lambda)*L1 + lambda*(1-SSIM); returns the loss, writes
+ * dL/dimg (nullable) and the mean SSIM (nullable). */
+double or_loss(const double *img, const double *target, int32_t C, int32_t H, int32_t W,
+               double lambda_dssim, double *dL_dimg, double *ssim_mean);
+
+/* SSIM map (nullable outputs) of two planar images. */
+void or_ssim_map(const double *x, const double *y, int32_t C, int32_t H, int32_t W, double *map);
+
+/* Backward of the compositing for one view.  grad2d gets n*10 values per
+ * Gaussian: dL/d(u, v, conic a, b, c, opacity, r, g, b, z) (accumulated).
+ * stats (nullable) gets n*6 accumulators: |Omega|, kappa, gamma, max T*alpha,
+ * ||dL/d(u,v)|| of this view, view count; kappa_amb (nullable) counts, per
+ * Gaussian, footprint pixels whose error-mask decision lies within
+ * mask_tol of tau_err. */
+void or_render_backward(const or_projected *pr, int64_t n, const int32_t *vals, const int64_t *ranges,
+                        const or_camera *cam, const or_cfg *cfg,
+                        const double *dL_dimg, const double *dL_ddepth,
+                        const double *img, const double *target, double tau_err, double loss_v,
+                        double mask_tol, double *grad2d, double *stats, double *kappa_amb);
+
+/* Chain rule from grad2d to the parameters (accumulated into grads, same
+ * layout as the parameters). */
+void or_project_backward(const or_params *p, const or_camera *cam, const or_cfg *cfg,
+                         const or_projected *pr, const double *grad2d,
+                         double *g_means, double *g_log_scales, double *g_quats,
+                         double *g_opacity_logits, double *g_sh);
+
+/* Bias-corrected Adam, element-wise with a per-element learning rate. */
+void or_adam(int64_t n, double *p, const double *g, double *m, double *v, const double *lr,
+             double beta1, double beta2, double eps, int64_t step);
+
+/* Chunk scores and global decisions.  densify and prune_max are updated in
+ * place (OR and max over chunks); prune is recomputed from prune_max. */
+void or_prune_finalize(int64_t n, const double *omega, const double *kappa, const double *gamma,
+                       int32_t n_views, double tau_d, double tau_p,
+                       double *S_d, double *S_p, uint8_t *densify, double *prune_max,
+                       uint8_t *prune);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

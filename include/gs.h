@@ -1,0 +1,267 @@
+/*
+ * gs.h -- C ABI of the B300 (sm_103a) differentiable 3D Gaussian splatting
+ * mapping step: projection, binning and depth sort, front-to-back
+ * compositing, the photometric loss, the back-to-front backward, Adam and the
+ * lifecycle (densify / prune) scores.
+ *
+ * Paper: KiloGS-SLAM, "Robust and Efficient Monocular 3D Gaussian SLAM for
+ * Kilometer-Scale Outdoor Scenes".  The mapping step optimises the map inside
+ * a sliding window with L_total = L_photo + ... (Sec. 3.2.3); the colour is
+ * composited front to back over depth-sorted Gaussians with transmittance
+ * T_j = prod_{m<j}(1 - alpha_m) (Supp. D.2); L_photo = 0.8 L1 + 0.2 (1 - SSIM)
+ * (Supp. D.4); the per-Gaussian footprint statistics, the densification
+ * score S_d and the pruning score S_p follow Supp. E.1 and E.2, aggregated
+ * over chunks by OR and max (Sec. 3.3.2).
+ *
+ * General conventions
+ *   - Every pointer in the structs and arguments below is a DEVICE pointer
+ *     unless marked "host".  The caller owns every buffer; the library never
+ *     allocates device memory and keeps no state between calls other than
+ *     cached device properties.
+ *   - All work is enqueued on the caller's stream; no call synchronises the
+ *     host, so the sequence can be captured into a CUDA graph.  Counts that
+ *     are only known on the device (visible records, pairs) stay on the device.
+ *   - Synchronous argument errors return a gs_status and enqueue nothing.
+ *     Asynchronous conditions (pair-buffer overflow, non-finite values) are
+ *     OR-ed as bit (1 << status) into the caller's device int32 status word,
+ *     read by the caller after the stream completes.
+ *   - Float buffers must be 16-byte aligned (GS_ERR_INVALID otherwise).
+ *   - Images are planar [3][H][W] FP32 per view; views are packed back to back
+ *     in the order of the camera array ("frame layout").
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID = 1,   /* bad argument: null, misaligned, out of range */
+    GS_ERR_CUDA = 2,      /* a CUDA launch or copy failed */
+    GS_ERR_CAPACITY = 3,  /* device: more (Gaussian, tile) pairs than max_pairs */
+    GS_ERR_TIMEOUT = 4,   /* device: a bounded wait gave up */
+    GS_ERR_NUMERIC = 5    /* device: a non-finite projection was culled */
+} gs_status;
+
+#define GS_MAX_VIEWS 64
+
+/* Pinhole camera (host struct).  x_c = R x_w + t, x right, y down, z forward;
+ * u = fx x_c/z_c + cx, v = fy y_c/z_c + cy; pixel (i, j) samples (i+0.5, j+0.5). */
+typedef struct {
+    float R[9];     /* world -> camera rotation, row-major */
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} gs_camera;
+
+/* Rasteriser constants (host struct).  The paper does not print them; these
+ * are the standard EWA-splatting values of the 3DGS work it builds on. */
+typedef struct {
+    int32_t tile_w, tile_h; /* 16x16, 8x32 or 32x8 (tile_w * tile_h == 256) */
+    float near_z;           /* cull camera depth <= near_z (0.2) */
+    float dilation;         /* added to the 2D covariance diagonal (0.3) */
+    float alpha_min;        /* skip alpha < alpha_min (1/255) */
+    float alpha_max;        /* clamp alpha to alpha_max (0.99) */
+    float t_min;            /* stop before blending when T (1 - alpha) < t_min (1e-4) */
+    float tan_clamp;        /* EWA Jacobian taken at x/z clamped to tan_clamp * W/(2 fx) (1.3) */
+    float bg[3];            /* background colour */
+} gs_raster_cfg;
+
+/* Gaussian parameters: ONE device buffer of K planes of ld floats
+ * (plane-major, so every attribute component streams contiguously):
+ *   planes 0-2   mean x, y, z (world)
+ *   planes 3-5   log-scale x, y, z
+ *   planes 6-9   rotation quaternion w, x, y, z (need not be normalised)
+ *   plane  10    opacity logit
+ *   plane  11 + 3k + c   SH coefficient k in 0..(D+1)^2-1 of colour channel c
+ * K = 11 + 3 (D+1)^2, D = sh_degree in 0..3, ld >= n and a multiple of 4.
+ * Gradients and Adam moments use the same layout. */
+typedef struct {
+    float *data;
+    int64_t n;
+    int64_t ld;
+    int32_t sh_degree;
+} gs_params;
+
+#define GS_PLANES(D) (11 + 3 * ((D) + 1) * ((D) + 1))
+
+/* Per-view projection records, [n_views][ld] each (record index = view*ld + g). */
+typedef struct {
+    float *xy;            /* 2 floats: pixel position u, v */
+    float *conic_opacity; /* 4 floats: conic a, b, c (inverse 2D covariance), opacity */
+    float *rgb_depth;     /* 4 floats: colour r, g, b, camera depth z */
+    int32_t *radius;      /* pixel radius, 0 = culled */
+    int32_t *tiles_touched;
+    int64_t ld;
+} gs_projected;
+
+/* Pair list and tile ranges of all views.  Tiles of all views form one
+ * global index space: view v's tile (tx, ty) is tile_offset[v] + ty*GW_v + tx
+ * with tile_offset the running sum of GW*GH over the previous views. */
+typedef struct {
+    int32_t *gauss_ids;    /* [max_pairs] record index per pair, ordered by
+                              (tile, depth, Gaussian index) */
+    int32_t *tile_ranges;  /* [total_tiles][2] = first pair, one past the last */
+    int32_t *counts;       /* device int32[4]: visible records, pairs written,
+                              pairs needed, reserved */
+    int64_t max_pairs;
+} gs_binning;
+
+/* Rendered frame of all views (frame layout). */
+typedef struct {
+    float *img;       /* [sum_v 3 H_v W_v] colour */
+    float *T_final;   /* [sum_v H_v W_v] transmittance left after the last blended Gaussian */
+    int32_t *last;    /* [sum_v H_v W_v] pairs of the tile consumed up to and including
+                         the last blended one (0 = none) */
+    float *depth;     /* nullable: [sum_v H_v W_v] D^ = sum_j T_j alpha_j z_j (Supp. D.2) */
+} gs_frame;
+
+/* Per-Gaussian lifecycle accumulators, planes of ld floats, accumulated over
+ * views and calls until the caller zeroes them (once per chunk):
+ *   0 |Omega| summed over views   1 kappa summed over views
+ *   2 gamma = sum_v L_photo^(v) |Omega_v|   3 max over views of max T*alpha
+ *   4 sum over views of ||dL/d(u,v)||       5 views with |Omega_v| > 0 */
+typedef struct {
+    float *acc;
+    int64_t ld;
+} gs_stats;
+
+/* Chunk outputs of gs_prune_stats (planes of n). */
+typedef struct {
+    float *S_d;          /* densification score of this chunk (Supp. E.1) */
+    float *S_p;          /* pruning score of this chunk (Supp. E.2) */
+    float *prune_max;    /* running max of S_p over chunks (in/out) */
+    uint8_t *densify;    /* running OR over chunks of S_d > tau_d (in/out) */
+    uint8_t *prune;      /* prune_max > tau_p */
+} gs_chunk_scores;
+
+typedef void *gs_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+const char *gs_status_string(gs_status s);
+
+/* Library version and the device architecture it was built for (e.g. 1030). */
+int32_t gs_version(void);
+
+/* Total tiles of all views and, per view (host outputs, nullable), the tile
+ * offset, the pixel offset of the view in the frame layout, GW and GH. */
+gs_status gs_view_layout(const gs_camera *cams, int32_t n_views, const gs_raster_cfg *cfg,
+                         int64_t *total_tiles, int64_t *total_pixels, int64_t *tile_offset,
+                         int64_t *pixel_offset);
+
+/* Workspace bytes of gs_sort for n_records = n_views * ld records and
+ * max_pairs pairs. */
+gs_status gs_sort_workspace_size(int64_t n_records, int64_t max_pairs, size_t *bytes);
+
+/* Workspace bytes of gs_loss for a view of h x w pixels (the largest view). */
+gs_status gs_loss_workspace_size(int32_t h, int32_t w, size_t *bytes);
+
+/* Workspace bytes of gs_render_bwd for n_records records. */
+gs_status gs_bwd_workspace_size(int64_t n_records, size_t *bytes);
+
+/* Workspace bytes of gs_prune_stats. */
+gs_status gs_prune_workspace_size(int64_t n, size_t *bytes);
+
+/*
+ * Projection of every Gaussian into every view (EWA splatting; the paper
+ * relies on the cited 3DGS rasteriser for it, Sec. 3.2 / Supp. D.2):
+ * camera point, near cull, Sigma = R(q) S S^T R(q)^T, Sigma' = J W Sigma W^T
+ * J^T + dilation I, conic, radius = ceil(3 sqrt(lambda_max)), tile rectangle,
+ * SH colour max(0, sum_k sh_k Y_k(dir) + 0.5) and sigmoid opacity.  u, v and
+ * the camera depth are evaluated in FP32 with each product, sum and quotient
+ * rounded left to right (no contraction), which makes the binning exactly
+ * reproducible.  cams is a HOST array of n_views <= GS_MAX_VIEWS cameras.
+ * status (nullable device int32) gets bit 1<<GS_ERR_NUMERIC when a
+ * non-finite projection was culled.
+ */
+gs_status gs_project(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                     const gs_raster_cfg *cfg, const gs_projected *out, int32_t *status,
+                     gs_stream stream);
+
+/*
+ * Binning: one pair per (visible record, overlapped tile), ordered by
+ * (global tile, camera depth, Gaussian index) -- the "sorted Gaussians along
+ * the ray" of Supp. D.2 -- and the per-tile ranges.  Writes
+ * binning->counts, gauss_ids[0..pairs) and tile_ranges.  When the pairs
+ * exceed max_pairs, no pair is written, counts[1] = 0, counts[2] = pairs
+ * needed and status gets bit 1<<GS_ERR_CAPACITY.  ws: gs_sort_workspace_size
+ * bytes (256-byte aligned).
+ */
+gs_status gs_sort(const gs_projected *proj, const gs_camera *cams, int32_t n_views,
+                  const gs_raster_cfg *cfg, const gs_binning *binning, void *ws, size_t ws_bytes,
+                  int32_t *status, gs_stream stream);
+
+/*
+ * Front-to-back alpha compositing of every pixel of every view (Supp. D.2):
+ * C = sum_j c_j alpha_j T_j + T_final bg, T_j = prod_{m<j} (1 - alpha_m),
+ * alpha_j = min(alpha_max, o_j exp(power_j)); Gaussians with alpha < alpha_min
+ * are skipped and the pixel stops before the Gaussian that would take T below
+ * t_min.  Writes the frame (depth only if frame->depth is set).
+ */
+gs_status gs_render_fwd(const gs_projected *proj, const gs_binning *binning, const gs_camera *cams,
+                        int32_t n_views, const gs_raster_cfg *cfg, const gs_frame *frame,
+                        gs_stream stream);
+
+/*
+ * Photometric loss per view (Supp. D.4):
+ *   L_v = (1 - lambda) mean|I^ - I| + lambda (1 - mean SSIM(I^, I)),
+ * lambda = lambda_dssim (0.2 in the paper), SSIM with an 11x11 Gaussian window
+ * (sigma 1.5), zero padding, C1 = 0.01^2, C2 = 0.03^2, mean over the three
+ * channels and all pixels.  img, target and dL_dimg are in frame layout;
+ * loss_per_view gets n_views floats; dL_dimg gets dL_v/dI^.  ws:
+ * gs_loss_workspace_size of the largest view.
+ */
+gs_status gs_loss(const float *img, const float *target, const gs_camera *cams, int32_t n_views,
+                  float lambda_dssim, float *loss_per_view, float *dL_dimg, void *ws,
+                  size_t ws_bytes, gs_stream stream);
+
+/*
+ * Backward of compositing and projection: traverses each tile back to front
+ * from the pixel's last blended pair, recovers T_j = T_{j+1} / (1 - alpha_j),
+ * and accumulates dL/d(u, v, conic, opacity, colour, depth) per record; then
+ * chains through the projection to every parameter plane.  grads (same layout
+ * as params) is overwritten, or accumulated into when accumulate != 0.
+ * dL_ddepth is nullable.  stats (nullable) receives the lifecycle
+ * accumulators (Supp. E.1, E.2): per pixel the error mask
+ * M_v = [sum_c |I - I^| > tau_err] (tau_err = 0.1, Supp. F) with the
+ * rendered frame->img and target, and gamma uses loss_per_view.
+ * ws: gs_bwd_workspace_size bytes.
+ */
+gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                        const gs_raster_cfg *cfg, const gs_projected *proj,
+                        const gs_binning *binning, const gs_frame *frame, const float *dL_dimg,
+                        const float *dL_ddepth, const float *target, const float *loss_per_view,
+                        float tau_err, const gs_params *grads, int32_t accumulate,
+                        const gs_stats *stats, void *ws, size_t ws_bytes, gs_stream stream);
+
+/*
+ * Adam (Kingma & Ba) with bias correction over every parameter plane, dense:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr m^ / (sqrt(v^) + eps),
+ * m^ = m/(1-b1^step), v^ = v/(1-b2^step).  lr_groups (host) holds six rates:
+ * means, log-scales, quaternion, opacity, SH degree 0, SH degree >= 1.
+ * The paper trains in PyTorch and prints no optimiser settings (Sec. 4.1).
+ */
+gs_status gs_adam(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
+                  const gs_params *exp_avg_sq, const float lr_groups[6], float beta1, float beta2,
+                  float eps, int64_t step, gs_stream stream);
+
+/*
+ * Chunk scores and global decisions (Supp. E.1, E.2; Sec. 3.3.2) from the
+ * accumulators of one chunk: S_d = kappa / n_views; L = log(1 + gamma);
+ * S_p = (L - min L) / (max L - min L) over Gaussians with |Omega| > 0 (0 for
+ * the others, and 0 for all when max = min); densify |= S_d > tau_d;
+ * prune_max = max(prune_max, S_p); prune = prune_max > tau_p.
+ * ws: gs_prune_workspace_size bytes.
+ */
+gs_status gs_prune_stats(const gs_stats *stats, int64_t n, int32_t n_views, float tau_d,
+                         float tau_p, const gs_chunk_scores *out, void *ws, size_t ws_bytes,
+                         gs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

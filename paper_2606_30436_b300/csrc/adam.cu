@@ -1,0 +1,55 @@
+// adam.cu -- Adam (Kingma & Ba) with bias correction over every parameter
+// plane, dense: all Gaussians move every step, as with torch.optim.Adam.  The
+// parameter, gradient and both moment buffers share the plane-major layout, so
+// the update is one flat float4 stream (28 bytes of HBM traffic per parameter).
+#include "gs_internal.cuh"
+#include "gs_kernels.h"
+
+namespace gs {
+
+struct AdamLr { float lr[6]; };
+
+__device__ __forceinline__ int lr_group(long long plane) {
+    // means, log-scales, quaternion, opacity, SH degree 0, SH degree >= 1
+    return plane < 3 ? 0 : plane < 6 ? 1 : plane < 10 ? 2 : plane == 10 ? 3 : plane < 14 ? 4 : 5;
+}
+
+__global__ void __launch_bounds__(256) k_adam(float4 *__restrict__ p, const float4 *__restrict__ g,
+                                               float4 *__restrict__ m, float4 *__restrict__ v, long long ld4,
+                                               long long total4, AdamLr lr, float b1, float b2, float inv_bc1,
+                                               float inv_sqrt_bc2, float eps) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total4;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float a = lr.lr[lr_group(i / ld4)];
+        const float4 gg = g[i];
+        float4 mm = m[i], vv = v[i], pp = p[i];
+#define GS_ADAM_LANE(c)                                                         \
+    mm.c = b1 * mm.c + (1.0f - b1) * gg.c;                                      \
+    vv.c = b2 * vv.c + (1.0f - b2) * gg.c * gg.c;                               \
+    pp.c -= a * (mm.c * inv_bc1) / (sqrtf(vv.c) * inv_sqrt_bc2 + eps);
+        GS_ADAM_LANE(x) GS_ADAM_LANE(y) GS_ADAM_LANE(z) GS_ADAM_LANE(w)
+#undef GS_ADAM_LANE
+        m[i] = mm;
+        v[i] = vv;
+        p[i] = pp;
+    }
+}
+
+void launch_adam(float *p, const float *g, float *m, float *v, long long ld, int planes, const float lr[6],
+                 float beta1, float beta2, float eps, long long step, cudaStream_t s) {
+    AdamLr L;
+    for (int k = 0; k < 6; ++k) L.lr[k] = lr[k];
+    const double bc1 = 1.0 - pow((double)beta1, (double)step);
+    const double bc2 = 1.0 - pow((double)beta2, (double)step);
+    const long long total4 = (long long)planes * ld / 4;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = ceil_div(total4, 256);
+    const int blocks = (int)std::min<long long>(want, (long long)sms * 8);
+    if (blocks <= 0) return;
+    k_adam<<<blocks, 256, 0, s>>>((float4 *)p, (const float4 *)g, (float4 *)m, (float4 *)v, ld / 4, total4, L, beta1,
+                                  beta2, (float)(1.0 / bc1), (float)(1.0 / sqrt(bc2)), eps);
+}
+
+}  // namespace gs

@@ -1,0 +1,275 @@
+// api.cu -- the extern "C" entry points declared in include/gs.h: argument
+// validation, the per-call view table, and the kernel launches on the caller's
+// stream.  No entry point allocates device memory or synchronises the host.
+#include <cmath>
+#include <cstring>
+
+#include "gs_internal.cuh"
+#include "gs_kernels.h"
+
+#define GS_API extern "C" __attribute__((visibility("default")))
+
+using namespace gs;
+
+namespace {
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
+
+gs_status check_cfg(const gs_raster_cfg *cfg) {
+    if (!cfg) return GS_ERR_INVALID;
+    const int tw = cfg->tile_w, th = cfg->tile_h;
+    const bool shape_ok = (tw == 16 && th == 16) || (tw == 8 && th == 32) || (tw == 32 && th == 8);
+    if (!shape_ok) return GS_ERR_INVALID;
+    if (!(cfg->near_z > 0.0f) || !(cfg->alpha_max > 0.0f && cfg->alpha_max < 1.0f) || !(cfg->alpha_min >= 0.0f) ||
+        !(cfg->t_min >= 0.0f) || !(cfg->dilation >= 0.0f) || !(cfg->tan_clamp > 0.0f))
+        return GS_ERR_INVALID;
+    return GS_OK;
+}
+
+gs_status build_views(const gs_camera *cams, int n_views, const gs_raster_cfg *cfg, ViewTable &vt, RasterCfg &rc) {
+    if (!cams || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_INVALID;
+    gs_status st = check_cfg(cfg);
+    if (st != GS_OK) return st;
+    std::memset(&vt, 0, sizeof(vt));
+    vt.n_views = n_views;
+    vt.tile_w = cfg->tile_w;
+    vt.tile_h = cfg->tile_h;
+    long long tiles = 0, pix = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const gs_camera &c = cams[v];
+        if (c.width <= 0 || c.height <= 0 || c.width > 65536 || c.height > 65536 || !(c.fx > 0.0f) || !(c.fy > 0.0f))
+            return GS_ERR_INVALID;
+        ViewDesc &d = vt.v[v];
+        for (int k = 0; k < 9; ++k) d.R[k] = c.R[k];
+        for (int k = 0; k < 3; ++k) d.t[k] = c.t[k];
+        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+        for (int k = 0; k < 3; ++k)  // camera centre -R^T t, in double then rounded
+            d.campos[k] = (float)(-((double)c.R[k] * c.t[0] + (double)c.R[3 + k] * c.t[1] + (double)c.R[6 + k] * c.t[2]));
+        d.limx = (float)((double)cfg->tan_clamp * c.width / (2.0 * c.fx));
+        d.limy = (float)((double)cfg->tan_clamp * c.height / (2.0 * c.fy));
+        d.W = c.width; d.H = c.height;
+        d.GW = (c.width + cfg->tile_w - 1) / cfg->tile_w;
+        d.GH = (c.height + cfg->tile_h - 1) / cfg->tile_h;
+        d.tile_offset = (int)tiles;
+        d.pix_offset = pix;
+        tiles += (long long)d.GW * d.GH;
+        pix += (long long)c.width * c.height;
+        if (tiles > 0x3fffffffll) return GS_ERR_INVALID;
+    }
+    vt.total_tiles = (int)tiles;
+    rc.near_z = cfg->near_z; rc.dilation = cfg->dilation; rc.alpha_min = cfg->alpha_min;
+    rc.alpha_max = cfg->alpha_max; rc.t_min = cfg->t_min; rc.tan_clamp = cfg->tan_clamp;
+    for (int k = 0; k < 3; ++k) rc.bg[k] = cfg->bg[k];
+    rc.tile_w = cfg->tile_w; rc.tile_h = cfg->tile_h;
+    return GS_OK;
+}
+
+gs_status check_params(const gs_params *p) {
+    if (!p || !p->data || p->n < 0 || p->ld < p->n || (p->ld & 3) || p->sh_degree < 0 || p->sh_degree > 3 ||
+        !aligned16(p->data))
+        return GS_ERR_INVALID;
+    return GS_OK;
+}
+
+gs_status check_proj(const gs_projected *pr, long long ld) {
+    if (!pr || !pr->xy || !pr->conic_opacity || !pr->rgb_depth || !pr->radius || !pr->tiles_touched) return GS_ERR_INVALID;
+    if (pr->ld != ld) return GS_ERR_INVALID;
+    if (!aligned16(pr->xy) || !aligned16(pr->conic_opacity) || !aligned16(pr->rgb_depth)) return GS_ERR_INVALID;
+    return GS_OK;
+}
+
+gs_status check_binning(const gs_binning *b) {
+    if (!b || !b->gauss_ids || !b->tile_ranges || !b->counts || b->max_pairs < 0 || b->max_pairs > 0x7fffffffll)
+        return GS_ERR_INVALID;
+    if (((uintptr_t)b->tile_ranges & 7u) != 0) return GS_ERR_INVALID;
+    return GS_OK;
+}
+
+}  // namespace
+
+GS_API const char *gs_status_string(gs_status s) {
+    switch (s) {
+        case GS_OK: return "ok";
+        case GS_ERR_INVALID: return "invalid argument";
+        case GS_ERR_CUDA: return "CUDA error";
+        case GS_ERR_CAPACITY: return "pair capacity exceeded";
+        case GS_ERR_TIMEOUT: return "bounded wait timed out";
+        case GS_ERR_NUMERIC: return "non-finite value";
+    }
+    return "unknown status";
+}
+
+GS_API int32_t gs_version(void) { return 10000 + 1030; }
+
+GS_API gs_status gs_view_layout(const gs_camera *cams, int32_t n_views, const gs_raster_cfg *cfg,
+                                int64_t *total_tiles, int64_t *total_pixels, int64_t *tile_offset,
+                                int64_t *pixel_offset) {
+    ViewTable vt;
+    RasterCfg rc;
+    gs_status st = build_views(cams, n_views, cfg, vt, rc);
+    if (st != GS_OK) return st;
+    long long pix = 0;
+    for (int v = 0; v < n_views; ++v) {
+        if (tile_offset) tile_offset[v] = vt.v[v].tile_offset;
+        if (pixel_offset) pixel_offset[v] = vt.v[v].pix_offset;
+        pix += (long long)vt.v[v].W * vt.v[v].H;
+    }
+    if (total_tiles) *total_tiles = vt.total_tiles;
+    if (total_pixels) *total_pixels = pix;
+    return GS_OK;
+}
+
+GS_API gs_status gs_sort_workspace_size(int64_t n_records, int64_t max_pairs, size_t *bytes) {
+    if (!bytes || n_records < 0 || max_pairs < 0 || n_records > 0x7fffffffll || max_pairs > 0x7fffffffll)
+        return GS_ERR_INVALID;
+    *bytes = sort_workspace_bytes(n_records, max_pairs);
+    return GS_OK;
+}
+
+GS_API gs_status gs_loss_workspace_size(int32_t h, int32_t w, size_t *bytes) {
+    if (!bytes || h <= 0 || w <= 0) return GS_ERR_INVALID;
+    *bytes = loss_workspace_bytes(h, w);
+    return GS_OK;
+}
+
+GS_API gs_status gs_bwd_workspace_size(int64_t n_records, size_t *bytes) {
+    if (!bytes || n_records < 0) return GS_ERR_INVALID;
+    *bytes = align_up(sizeof(float) * (size_t)kAccPlanes * (size_t)n_records, 256);
+    return GS_OK;
+}
+
+GS_API gs_status gs_prune_workspace_size(int64_t n, size_t *bytes) {
+    if (!bytes || n < 0) return GS_ERR_INVALID;
+    *bytes = prune_workspace_bytes(n);
+    return GS_OK;
+}
+
+GS_API gs_status gs_project(const gs_params *params, const gs_camera *cams, int32_t n_views, const gs_raster_cfg *cfg,
+                            const gs_projected *out, int32_t *status, gs_stream stream) {
+    ViewTable vt;
+    RasterCfg rc;
+    gs_status st = build_views(cams, n_views, cfg, vt, rc);
+    if (st == GS_OK) st = check_params(params);
+    if (st == GS_OK) st = check_proj(out, params->ld);
+    if (st != GS_OK) return st;
+    launch_project(params->data, params->n, params->ld, params->sh_degree, vt, rc, (float2 *)out->xy,
+                   (float4 *)out->conic_opacity, (float4 *)out->rgb_depth, out->radius, out->tiles_touched, status,
+                   (cudaStream_t)stream);
+    return cuda_status(cudaGetLastError());
+}
+
+GS_API gs_status gs_sort(const gs_projected *proj, const gs_camera *cams, int32_t n_views, const gs_raster_cfg *cfg,
+                         const gs_binning *binning, void *ws, size_t ws_bytes, int32_t *status, gs_stream stream) {
+    ViewTable vt;
+    RasterCfg rc;
+    gs_status st = build_views(cams, n_views, cfg, vt, rc);
+    if (st != GS_OK) return st;
+    if (!proj) return GS_ERR_INVALID;
+    if ((st = check_proj(proj, proj->ld)) != GS_OK) return st;
+    if ((st = check_binning(binning)) != GS_OK) return st;
+    const long long nrec = (long long)n_views * proj->ld;
+    if (nrec > 0x7fffffffll) return GS_ERR_INVALID;
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < sort_workspace_bytes(nrec, binning->max_pairs)) return GS_ERR_INVALID;
+    return cuda_status(launch_sort(proj->radius, proj->tiles_touched, (const float2 *)proj->xy,
+                                   (const float4 *)proj->rgb_depth, nrec, proj->ld, vt, binning->gauss_ids,
+                                   (int2 *)binning->tile_ranges, binning->counts, binning->max_pairs, ws, status,
+                                   (cudaStream_t)stream));
+}
+
+GS_API gs_status gs_render_fwd(const gs_projected *proj, const gs_binning *binning, const gs_camera *cams,
+                               int32_t n_views, const gs_raster_cfg *cfg, const gs_frame *frame, gs_stream stream) {
+    ViewTable vt;
+    RasterCfg rc;
+    gs_status st = build_views(cams, n_views, cfg, vt, rc);
+    if (st != GS_OK) return st;
+    if (!proj || (st = check_proj(proj, proj->ld)) != GS_OK) return GS_ERR_INVALID;
+    if ((st = check_binning(binning)) != GS_OK) return st;
+    if (!frame || !frame->img || !frame->T_final || !frame->last) return GS_ERR_INVALID;
+    launch_render_fwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, (const float2 *)proj->xy,
+                      (const float4 *)proj->conic_opacity, (const float4 *)proj->rgb_depth, frame->img,
+                      frame->T_final, frame->last, frame->depth, (cudaStream_t)stream);
+    return cuda_status(cudaGetLastError());
+}
+
+GS_API gs_status gs_loss(const float *img, const float *target, const gs_camera *cams, int32_t n_views,
+                         float lambda_dssim, float *loss_per_view, float *dL_dimg, void *ws, size_t ws_bytes,
+                         gs_stream stream) {
+    if (!img || !target || !cams || !loss_per_view || n_views < 1 || n_views > GS_MAX_VIEWS || !ws) return GS_ERR_INVALID;
+    if (!(lambda_dssim >= 0.0f && lambda_dssim <= 1.0f) || ((uintptr_t)ws & 255u)) return GS_ERR_INVALID;
+    long long off = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const int h = cams[v].height, w = cams[v].width;
+        if (h <= 0 || w <= 0 || ws_bytes < loss_workspace_bytes(h, w)) return GS_ERR_INVALID;
+    }
+    for (int v = 0; v < n_views; ++v) {
+        const int h = cams[v].height, w = cams[v].width;
+        cudaError_t e = launch_loss(img + off, target + off, h, w, lambda_dssim, loss_per_view + v,
+                                    dL_dimg ? dL_dimg + off : nullptr, ws, (cudaStream_t)stream);
+        if (e != cudaSuccess) return GS_ERR_CUDA;
+        off += 3ll * h * w;
+    }
+    return GS_OK;
+}
+
+GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                               const gs_raster_cfg *cfg, const gs_projected *proj, const gs_binning *binning,
+                               const gs_frame *frame, const float *dL_dimg, const float *dL_ddepth,
+                               const float *target, const float *loss_per_view, float tau_err, const gs_params *grads,
+                               int32_t accumulate, const gs_stats *stats, void *ws, size_t ws_bytes,
+                               gs_stream stream) {
+    ViewTable vt;
+    RasterCfg rc;
+    gs_status st = build_views(cams, n_views, cfg, vt, rc);
+    if (st == GS_OK) st = check_params(params);
+    if (st == GS_OK) st = check_params(grads);
+    if (st != GS_OK) return st;
+    if (grads->ld != params->ld || grads->n != params->n || grads->sh_degree != params->sh_degree) return GS_ERR_INVALID;
+    if (!proj || check_proj(proj, params->ld) != GS_OK || check_binning(binning) != GS_OK) return GS_ERR_INVALID;
+    if (!frame || !frame->img || !frame->T_final || !frame->last || !dL_dimg) return GS_ERR_INVALID;
+    const bool want_stats = stats != nullptr;
+    if (want_stats && (!stats->acc || stats->ld < params->n || !target)) return GS_ERR_INVALID;
+    const long long nrec = (long long)n_views * params->ld;
+    size_t need = 0;
+    gs_bwd_workspace_size(nrec, &need);
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < need) return GS_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *acc = (float *)ws;
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)kAccPlanes * nrec, s);
+    if (e != cudaSuccess) return GS_ERR_CUDA;
+    launch_render_bwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, (const float2 *)proj->xy,
+                      (const float4 *)proj->conic_opacity, (const float4 *)proj->rgb_depth, frame->img,
+                      frame->T_final, frame->last, dL_dimg, dL_ddepth, target, tau_err, want_stats, acc, nrec, s);
+    launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius, acc, nrec,
+                       grads->data, accumulate, loss_per_view, want_stats ? stats->acc : nullptr,
+                       want_stats ? stats->ld : 0, s);
+    return cuda_status(cudaGetLastError());
+}
+
+GS_API gs_status gs_adam(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
+                         const gs_params *exp_avg_sq, const float lr_groups[6], float beta1, float beta2, float eps,
+                         int64_t step, gs_stream stream) {
+    gs_status st = check_params(params);
+    if (st == GS_OK) st = check_params(grads);
+    if (st == GS_OK) st = check_params(exp_avg);
+    if (st == GS_OK) st = check_params(exp_avg_sq);
+    if (st != GS_OK) return st;
+    for (const gs_params *q : {grads, exp_avg, exp_avg_sq})
+        if (q->ld != params->ld || q->n != params->n || q->sh_degree != params->sh_degree) return GS_ERR_INVALID;
+    if (!lr_groups || step < 1 || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f))
+        return GS_ERR_INVALID;
+    launch_adam(params->data, grads->data, exp_avg->data, exp_avg_sq->data, params->ld, GS_PLANES(params->sh_degree),
+                lr_groups, beta1, beta2, eps, step, (cudaStream_t)stream);
+    return cuda_status(cudaGetLastError());
+}
+
+GS_API gs_status gs_prune_stats(const gs_stats *stats, int64_t n, int32_t n_views, float tau_d, float tau_p,
+                                const gs_chunk_scores *out, void *ws, size_t ws_bytes, gs_stream stream) {
+    if (!stats || !stats->acc || n < 0 || stats->ld < n || n_views < 1 || !out || !out->S_d || !out->S_p ||
+        !out->prune_max || !out->densify || !out->prune || !ws || ws_bytes < prune_workspace_bytes(n))
+        return GS_ERR_INVALID;
+    launch_prune(stats->acc, stats->ld, n, n_views, tau_d, tau_p, out->S_d, out->S_p, out->prune_max, out->densify,
+                 out->prune, ws, (cudaStream_t)stream);
+    return cuda_status(cudaGetLastError());
+}

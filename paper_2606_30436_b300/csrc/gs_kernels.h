@@ -1,0 +1,51 @@
+// gs_kernels.h -- internal launchers of the sm_103a kernels (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+// Per-record accumulator planes written by the compositing backward and read by
+// the projection backward (plane p of record r at acc[p * nrec + r]).
+enum AccPlane {
+    kAccU = 0, kAccV, kAccA, kAccB, kAccC, kAccO, kAccR, kAccG, kAccBl, kAccZ,
+    kAccOmega, kAccKappa, kAccMaxW, kAccPlanes
+};
+
+void launch_project(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
+                    float2 *xy, float4 *co, float4 *rgbd, int *radius, int *touched, int *status, cudaStream_t s);
+
+void launch_project_bwd(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
+                        const int *radius, const float *acc, long long nrec, float *G, int accumulate,
+                        const float *loss_per_view, float *stats, long long stats_ld, cudaStream_t s);
+
+// Binning: workspace layout and launch of the whole sort pipeline.
+size_t sort_workspace_bytes(long long nrec, long long max_pairs);
+cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy, const float4 *rgbd, long long nrec,
+                        long long ld, const ViewTable &vt, int *gauss_ids, int2 *tile_ranges, int *counts,
+                        long long max_pairs, void *ws, int *status, cudaStream_t s);
+
+void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids, const float2 *xy,
+                       const float4 *co, const float4 *rgbd, float *img, float *T_final, int *last, float *depth,
+                       cudaStream_t s);
+
+void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
+                       const float2 *xy, const float4 *co, const float4 *rgbd, const float *img, const float *T_final,
+                       const int *last, const float *dL_dimg, const float *dL_ddepth, const float *target,
+                       float tau_err, bool stats, float *acc, long long nrec, cudaStream_t s);
+
+size_t loss_workspace_bytes(int h, int w);
+cudaError_t launch_loss(const float *img, const float *target, int h, int w, float lambda, float *loss_out,
+                        float *dL_dimg, void *ws, cudaStream_t s);
+
+void launch_adam(float *p, const float *g, float *m, float *v, long long ld, int planes, const float lr[6],
+                 float beta1, float beta2, float eps, long long step, cudaStream_t s);
+
+size_t prune_workspace_bytes(long long n);
+void launch_prune(const float *acc, long long ld, long long n, int n_views, float tau_d, float tau_p, float *S_d,
+                  float *S_p, float *prune_max, unsigned char *densify, unsigned char *prune, void *ws,
+                  cudaStream_t s);
+
+}  // namespace gs

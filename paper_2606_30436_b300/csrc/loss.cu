@@ -1,0 +1,215 @@
+// loss.cu -- photometric loss L = (1 - lambda) L1 + lambda (1 - SSIM) and its
+// gradient (Supp. D.4; lambda = 0.2 in the paper).  SSIM: 11x11 Gaussian
+// window (sigma 1.5), zero padding, C1 = 0.01^2, C2 = 0.03^2.
+//
+// Forward: one CTA per 32x32 output tile and channel stages the tile plus a
+// 5-pixel halo of both images in shared memory and forms the five windowed
+// moments with separable 11-tap passes.  With s = SSIM(mu_x, mu_y, s_xx, s_yy,
+// s_xy) the gradient with respect to the rendered image x is
+//   dSSIM/dx(q) = (G*A)(q) + 2 x(q) (G*B)(q) + y(q) (G*Cm)(q),
+//   A = ds/dmu_x - 2 mu_x ds/ds_xx - mu_y ds/ds_xy,  B = ds/ds_xx,  Cm = ds/ds_xy,
+// so the forward writes A, B, Cm and a second pass blurs them.  Sums for the
+// scalar loss are reduced per CTA and then in a fixed order (deterministic).
+#include <algorithm>
+#include <cmath>
+
+#include "gs_internal.cuh"
+#include "gs_kernels.h"
+
+namespace gs {
+
+constexpr int kLT = 32;          // output tile edge
+constexpr int kLR = 5;           // window radius
+constexpr int kLI = kLT + 2 * kLR;  // staged tile edge (42)
+
+struct Win { float w[2 * kLR + 1]; };
+
+__device__ __forceinline__ float sgn(float d) { return d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f); }
+
+__device__ __forceinline__ double block_sum_d(double v, double *sm) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sm[i];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int H,
+                                                   int W, Win win, float *__restrict__ maps, int want_grad,
+                                                   double *__restrict__ partials) {
+    __shared__ float sx[kLI][kLI + 1], sy[kLI][kLI + 1];
+    __shared__ float h[5][kLI][kLT];
+    __shared__ double sm[8];
+    const int ch = blockIdx.z;
+    const long long plane = (long long)H * W;
+    const float *xc = x + ch * plane, *yc = y + ch * plane;
+    const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
+    for (int i = threadIdx.x; i < kLI * kLI; i += 256) {
+        const int r = i / kLI, c = i - r * kLI;
+        const int gy = oy + r - kLR, gx = ox + c - kLR;
+        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+        sx[r][c] = in ? xc[(long long)gy * W + gx] : 0.0f;
+        sy[r][c] = in ? yc[(long long)gy * W + gx] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kLI * kLT; i += 256) {
+        const int r = i / kLT, c = i - r * kLT;
+        float a = 0, b = 0, aa = 0, bb = 0, ab = 0;
+        #pragma unroll
+        for (int k = 0; k < 2 * kLR + 1; ++k) {
+            const float wx = win.w[k], xv = sx[r][c + k], yv = sy[r][c + k];
+            a += wx * xv; b += wx * yv; aa += wx * xv * xv; bb += wx * yv * yv; ab += wx * xv * yv;
+        }
+        h[0][r][c] = a; h[1][r][c] = b; h[2][r][c] = aa; h[3][r][c] = bb; h[4][r][c] = ab;
+    }
+    __syncthreads();
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    double l1 = 0.0, ss = 0.0;
+    for (int i = threadIdx.x; i < kLT * kLT; i += 256) {
+        const int r = i / kLT, c = i - r * kLT;
+        const int gy = oy + r, gx = ox + c;
+        if (gy >= H || gx >= W) continue;
+        float mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+        #pragma unroll
+        for (int k = 0; k < 2 * kLR + 1; ++k) {
+            const float wy = win.w[k];
+            mx += wy * h[0][r + k][c]; my += wy * h[1][r + k][c];
+            exx += wy * h[2][r + k][c]; eyy += wy * h[3][r + k][c]; exy += wy * h[4][r + k][c];
+        }
+        const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+        const float A1 = 2.0f * mx * my + C1, A2 = 2.0f * sxy + C2;
+        const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
+        const float iB = 1.0f / (B1 * B2);
+        const float s = A1 * A2 * iB;
+        ss += s;
+        const float xv = sx[r + kLR][c + kLR], yv = sy[r + kLR][c + kLR];
+        l1 += fabsf(xv - yv);
+        if (want_grad) {
+            const float dmu = 2.0f * my * A2 * iB - 2.0f * mx * s / B1;
+            const float dsxx = -s / B2;
+            const float dsxy = 2.0f * A1 * iB;
+            const long long o = (long long)gy * W + gx;
+            maps[(3 * ch + 0) * plane + o] = dmu - 2.0f * mx * dsxx - my * dsxy;
+            maps[(3 * ch + 1) * plane + o] = dsxx;
+            maps[(3 * ch + 2) * plane + o] = dsxy;
+        }
+    }
+    const double tl1 = block_sum_d(l1, sm);
+    const double tss = block_sum_d(ss, sm);
+    if (threadIdx.x == 0) {
+        const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        partials[2 * b] = tl1;
+        partials[2 * b + 1] = tss;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ssim_bwd(const float *__restrict__ x, const float *__restrict__ y, int H,
+                                                   int W, Win win, const float *__restrict__ maps, float l1_scale,
+                                                   float ssim_scale, float *__restrict__ dL) {
+    __shared__ float sm[3][kLI][kLI + 1];
+    __shared__ float h[3][kLI][kLT];
+    const int ch = blockIdx.z;
+    const long long plane = (long long)H * W;
+    const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
+    for (int i = threadIdx.x; i < kLI * kLI; i += 256) {
+        const int r = i / kLI, c = i - r * kLI;
+        const int gy = oy + r - kLR, gx = ox + c - kLR;
+        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+        const long long o = (long long)gy * W + gx;
+        #pragma unroll
+        for (int m = 0; m < 3; ++m) sm[m][r][c] = in ? maps[(3 * ch + m) * plane + o] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kLI * kLT; i += 256) {
+        const int r = i / kLT, c = i - r * kLT;
+        float a = 0, b = 0, d = 0;
+        #pragma unroll
+        for (int k = 0; k < 2 * kLR + 1; ++k) {
+            const float wx = win.w[k];
+            a += wx * sm[0][r][c + k]; b += wx * sm[1][r][c + k]; d += wx * sm[2][r][c + k];
+        }
+        h[0][r][c] = a; h[1][r][c] = b; h[2][r][c] = d;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kLT * kLT; i += 256) {
+        const int r = i / kLT, c = i - r * kLT;
+        const int gy = oy + r, gx = ox + c;
+        if (gy >= H || gx >= W) continue;
+        float a = 0, b = 0, d = 0;
+        #pragma unroll
+        for (int k = 0; k < 2 * kLR + 1; ++k) {
+            const float wy = win.w[k];
+            a += wy * h[0][r + k][c]; b += wy * h[1][r + k][c]; d += wy * h[2][r + k][c];
+        }
+        const long long o = ch * plane + (long long)gy * W + gx;
+        const float xv = x[o], yv = y[o];
+        dL[o] = l1_scale * sgn(xv - yv) - ssim_scale * (a + 2.0f * xv * b + yv * d);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_l1(const float *__restrict__ x, const float *__restrict__ y, long long n,
+                                             float scale, float *__restrict__ dL, double *__restrict__ partials) {
+    __shared__ double sm[8];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float d = x[i] - y[i];
+        s += fabsf(d);
+        if (dL) dL[i] = scale * sgn(d);
+    }
+    const double t = block_sum_d(s, sm);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = t;
+        partials[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_loss_final(const double *__restrict__ partials, int nb, double inv_n,
+                                                     float lambda, float *__restrict__ out) {
+    __shared__ double sm[8];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 256) { a += partials[2 * i]; b += partials[2 * i + 1]; }
+    const double l1 = block_sum_d(a, sm) * inv_n;
+    const double ssim = block_sum_d(b, sm) * inv_n;
+    if (threadIdx.x == 0) *out = (float)((1.0 - lambda) * l1 + (lambda > 0.0f ? lambda * (1.0 - ssim) : 0.0));
+}
+
+static int loss_blocks(int h, int w) { return (int)(ceil_div(w, kLT) * ceil_div(h, kLT) * 3); }
+constexpr int kL1Blocks = 148 * 4;
+
+size_t loss_workspace_bytes(int h, int w) {
+    const size_t maps = align_up(sizeof(float) * 9 * (size_t)h * w, 256);
+    const size_t nb = (size_t)std::max(loss_blocks(h, w), kL1Blocks);
+    return maps + align_up(sizeof(double) * 2 * nb, 256);
+}
+
+cudaError_t launch_loss(const float *img, const float *target, int h, int w, float lambda, float *loss_out,
+                        float *dL_dimg, void *ws, cudaStream_t s) {
+    const long long n = 3ll * h * w;
+    float *maps = (float *)ws;
+    double *partials = (double *)((char *)ws + align_up(sizeof(float) * 9 * (size_t)h * w, 256));
+    if (lambda <= 0.0f) {
+        k_l1<<<kL1Blocks, 256, 0, s>>>(img, target, n, (float)(1.0 / (double)n), dL_dimg, partials);
+        k_loss_final<<<1, 256, 0, s>>>(partials, kL1Blocks, 1.0 / (double)n, 0.0f, loss_out);
+        return cudaGetLastError();
+    }
+    Win win;
+    {
+        double wd[2 * kLR + 1], sum = 0.0;
+        for (int k = -kLR; k <= kLR; ++k) { wd[k + kLR] = exp(-(double)(k * k) / (2.0 * 1.5 * 1.5)); sum += wd[k + kLR]; }
+        for (int k = 0; k < 2 * kLR + 1; ++k) win.w[k] = (float)(wd[k] / sum);
+    }
+    dim3 grid((unsigned)ceil_div(w, kLT), (unsigned)ceil_div(h, kLT), 3);
+    k_ssim_fwd<<<grid, 256, 0, s>>>(img, target, h, w, win, maps, dL_dimg != nullptr, partials);
+    if (dL_dimg)
+        k_ssim_bwd<<<grid, 256, 0, s>>>(img, target, h, w, win, maps, (float)((1.0 - lambda) / (double)n),
+                                        (float)(lambda / (double)n), dL_dimg);
+    k_loss_final<<<1, 256, 0, s>>>(partials, loss_blocks(h, w), 1.0 / (double)n, lambda, loss_out);
+    return cudaGetLastError();
+}
+
+}  // namespace gs

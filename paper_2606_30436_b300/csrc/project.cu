@@ -1,0 +1,452 @@
+// project.cu -- per-Gaussian projection (forward) and its chain rule
+// (backward) for every view of a chunk, one thread per Gaussian.  The
+// parameters are read once per Gaussian and reused for all views in registers.
+//
+// Projection: EWA splatting of the cited 3DGS rasteriser (the paper relies on
+// it for Supp. D.2): Sigma = R(q) S S^T R(q)^T, Sigma' = J W Sigma W^T J^T +
+// dilation I, conic = Sigma'^-1, radius = ceil(3 sqrt(lambda_max)); colour from
+// real spherical harmonics of degree D <= 3; opacity = sigmoid(logit).
+#include "gs_internal.cuh"
+#include "gs_kernels.h"
+
+namespace gs {
+
+// Real spherical harmonics with the Condon-Shortley phase, as Cartesian
+// polynomials of the unit direction (x, y, z); index l^2 + l + m.
+// Constants are sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the polynomial
+// prefactors: C1 = sqrt(3/(4pi)), C2a = sqrt(15/(4pi)), C2b = sqrt(5/(16pi)),
+// C2c = sqrt(15/(16pi)), C3a = sqrt(35/(32pi)), C3b = sqrt(105/(4pi)),
+// C3c = sqrt(21/(32pi)), C3d = sqrt(7/(16pi)), C3e = sqrt(105/(16pi)).
+namespace shc {
+constexpr float C0 = 0.28209479177387814f;
+constexpr float C1 = 0.4886025119029199f;
+constexpr float C2a = 1.0925484305920792f;
+constexpr float C2b = 0.31539156525252005f;
+constexpr float C2c = 0.5462742152960396f;
+constexpr float C3a = 0.5900435899266435f;
+constexpr float C3b = 2.890611442640554f;
+constexpr float C3c = 0.4570457994644658f;
+constexpr float C3d = 0.3731763325901154f;
+constexpr float C3e = 1.445305721320277f;
+}  // namespace shc
+
+template <int D>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
+    using namespace shc;
+    Y[0] = C0;
+    if (D >= 1) { Y[1] = -C1 * y; Y[2] = C1 * z; Y[3] = -C1 * x; }
+    if (D >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = C2a * x * y;
+        Y[5] = -C2a * y * z;
+        Y[6] = C2b * (3.0f * zz - 1.0f);
+        Y[7] = -C2a * x * z;
+        Y[8] = C2c * (xx - yy);
+        if (D >= 3) {
+            Y[9] = -C3a * y * (3.0f * xx - yy);
+            Y[10] = C3b * x * y * z;
+            Y[11] = -C3c * y * (5.0f * zz - 1.0f);
+            Y[12] = C3d * z * (5.0f * zz - 3.0f);
+            Y[13] = -C3c * x * (5.0f * zz - 1.0f);
+            Y[14] = C3e * z * (xx - yy);
+            Y[15] = -C3a * x * (xx - 3.0f * yy);
+        }
+    }
+}
+
+// Gradient of sum_k w_k Y_k with respect to (x, y, z), w_k given.
+template <int D>
+__device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const float *w, float &gx, float &gy,
+                                             float &gz) {
+    using namespace shc;
+    gx = gy = gz = 0.0f;
+    if (D >= 1) { gy -= C1 * w[1]; gz += C1 * w[2]; gx -= C1 * w[3]; }
+    if (D >= 2) {
+        gx += C2a * y * w[4]; gy += C2a * x * w[4];
+        gy -= C2a * z * w[5]; gz -= C2a * y * w[5];
+        gz += 6.0f * C2b * z * w[6];
+        gx -= C2a * z * w[7]; gz -= C2a * x * w[7];
+        gx += 2.0f * C2c * x * w[8]; gy -= 2.0f * C2c * y * w[8];
+        if (D >= 3) {
+            const float xx = x * x, yy = y * y, zz = z * z;
+            gx -= 6.0f * C3a * x * y * w[9]; gy -= 3.0f * C3a * (xx - yy) * w[9];
+            gx += C3b * y * z * w[10]; gy += C3b * x * z * w[10]; gz += C3b * x * y * w[10];
+            gy -= C3c * (5.0f * zz - 1.0f) * w[11]; gz -= 10.0f * C3c * y * z * w[11];
+            gz += C3d * (15.0f * zz - 3.0f) * w[12];
+            gx -= C3c * (5.0f * zz - 1.0f) * w[13]; gz -= 10.0f * C3c * x * z * w[13];
+            gx += 2.0f * C3e * x * z * w[14]; gy -= 2.0f * C3e * y * z * w[14]; gz += C3e * (xx - yy) * w[14];
+            gx -= 3.0f * C3a * (xx - yy) * w[15]; gy += 6.0f * C3a * x * y * w[15];
+        }
+    }
+}
+
+struct Cov3 { float s00, s01, s02, s11, s12, s22; };
+
+__device__ __forceinline__ void quat_rotation(float qw, float qx, float qy, float qz, float *R) {
+    R[0] = 1.f - 2.f * (qy * qy + qz * qz); R[1] = 2.f * (qx * qy - qw * qz); R[2] = 2.f * (qx * qz + qw * qy);
+    R[3] = 2.f * (qx * qy + qw * qz); R[4] = 1.f - 2.f * (qx * qx + qz * qz); R[5] = 2.f * (qy * qz - qw * qx);
+    R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+}
+
+// EWA 2D covariance (before dilation) from the 3D covariance, for one view.
+struct Ewa { float T[6]; float A, B, C; bool clx_lo, clx_hi, cly_lo, cly_hi; float tx, ty; };
+
+__device__ __forceinline__ Ewa ewa(const ViewDesc &c, float x, float y, float z, const Cov3 &S) {
+    Ewa e;
+    const float rx = x / z, ry = y / z;
+    e.clx_lo = rx < -c.limx; e.clx_hi = rx > c.limx;
+    e.cly_lo = ry < -c.limy; e.cly_hi = ry > c.limy;
+    e.tx = z * fminf(fmaxf(rx, -c.limx), c.limx);
+    e.ty = z * fminf(fmaxf(ry, -c.limy), c.limy);
+    const float iz = 1.0f / z;
+    const float J00 = c.fx * iz, J02 = -c.fx * e.tx * iz * iz;
+    const float J11 = c.fy * iz, J12 = -c.fy * e.ty * iz * iz;
+    // T = J W (W = view rotation), 2 x 3
+    #pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e.T[k] = J00 * c.R[k] + J02 * c.R[6 + k];
+        e.T[3 + k] = J11 * c.R[3 + k] + J12 * c.R[6 + k];
+    }
+    const float *T = e.T;
+    const float ST0x = S.s00 * T[0] + S.s01 * T[1] + S.s02 * T[2];
+    const float ST0y = S.s01 * T[0] + S.s11 * T[1] + S.s12 * T[2];
+    const float ST0z = S.s02 * T[0] + S.s12 * T[1] + S.s22 * T[2];
+    const float ST1x = S.s00 * T[3] + S.s01 * T[4] + S.s02 * T[5];
+    const float ST1y = S.s01 * T[3] + S.s11 * T[4] + S.s12 * T[5];
+    const float ST1z = S.s02 * T[3] + S.s12 * T[4] + S.s22 * T[5];
+    e.A = T[0] * ST0x + T[1] * ST0y + T[2] * ST0z;
+    e.B = T[0] * ST1x + T[1] * ST1y + T[2] * ST1z;
+    e.C = T[3] * ST1x + T[4] * ST1y + T[5] * ST1z;
+    return e;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_project(const float *__restrict__ P, long long n, long long ld, ViewTable vt,
+                                                 RasterCfg cfg, float2 *__restrict__ xy, float4 *__restrict__ co,
+                                                 float4 *__restrict__ rgbd, int *__restrict__ radius,
+                                                 int *__restrict__ touched, int *__restrict__ status) {
+    constexpr int K = (D + 1) * (D + 1);
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const float mx = P[0 * ld + g], my = P[1 * ld + g], mz = P[2 * ld + g];
+
+    // cheap near-plane pass first: skip the remaining loads if no view sees it
+    bool any = false;
+    for (int v = 0; v < vt.n_views; ++v) {
+        const ViewDesc &c = vt.v[v];
+        float zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.R[6], mx), __fmul_rn(c.R[7], my)), __fmul_rn(c.R[8], mz)), c.t[2]);
+        any |= zc > cfg.near_z;
+    }
+    if (!any) {
+        for (int v = 0; v < vt.n_views; ++v) { radius[v * ld + g] = 0; touched[v * ld + g] = 0; }
+        return;
+    }
+
+    Cov3 S;
+    {
+        float qw = P[6 * ld + g], qx = P[7 * ld + g], qy = P[8 * ld + g], qz = P[9 * ld + g];
+        const float nq = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw /= nq; qx /= nq; qy /= nq; qz /= nq;
+        float R[9];
+        quat_rotation(qw, qx, qy, qz, R);
+        const float s0 = expf(P[3 * ld + g]), s1 = expf(P[4 * ld + g]), s2 = expf(P[5 * ld + g]);
+        float M[9];
+        #pragma unroll
+        for (int r = 0; r < 3; ++r) { M[3 * r] = R[3 * r] * s0; M[3 * r + 1] = R[3 * r + 1] * s1; M[3 * r + 2] = R[3 * r + 2] * s2; }
+        S.s00 = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+        S.s01 = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+        S.s02 = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+        S.s11 = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+        S.s12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+        S.s22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    }
+    const float opacity = 1.0f / (1.0f + expf(-P[10 * ld + g]));
+
+    for (int v = 0; v < vt.n_views; ++v) {
+        const ViewDesc &c = vt.v[v];
+        const long long rec = v * ld + g;
+        int rad = 0, tt = 0;
+        const ExactPos p = exact_position(c, mx, my, mz);
+        if (p.zc > cfg.near_z) {
+            const Ewa e = ewa(c, p.xc, p.yc, p.zc, S);
+            const float A = e.A + cfg.dilation, B = e.B, C = e.C + cfg.dilation;
+            const float det = A * C - B * B;
+            const float inv = 1.0f / det;
+            const float ca = C * inv, cb = -B * inv, cc = A * inv;
+            const float mid = 0.5f * (A + C);
+            const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+            const float rr = ceilf(3.0f * sqrtf(lam));
+            const bool finite = isfinite(p.u) && isfinite(p.v) && isfinite(ca) && isfinite(cb) && isfinite(cc) &&
+                                isfinite(rr);
+            if (!finite) {
+                if (status) atomicOr(status, 1 << GS_ERR_NUMERIC);
+            } else if (det > 0.0f) {
+                rad = (int)fminf(rr, 16777216.0f);
+                const Rect rc = tile_rect(p.u, p.v, rad, vt.tile_w, vt.tile_h, c.GW, c.GH);
+                tt = (rc.x1 - rc.x0) * (rc.y1 - rc.y0);
+                if (tt <= 0) { rad = 0; tt = 0; }
+            }
+            if (rad > 0) {
+                // view-dependent colour
+                float dx = mx - c.campos[0], dy = my - c.campos[1], dz = mz - c.campos[2];
+                const float id = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+                dx *= id; dy *= id; dz *= id;
+                float Y[16];
+                sh_basis<D>(dx, dy, dz, Y);
+                float r = 0.5f, gch = 0.5f, b = 0.5f;
+                #pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    r += Y[k] * P[(11 + 3 * k) * ld + g];
+                    gch += Y[k] * P[(12 + 3 * k) * ld + g];
+                    b += Y[k] * P[(13 + 3 * k) * ld + g];
+                }
+                xy[rec] = make_float2(p.u, p.v);
+                co[rec] = make_float4(ca, cb, cc, opacity);
+                rgbd[rec] = make_float4(fmaxf(r, 0.0f), fmaxf(gch, 0.0f), fmaxf(b, 0.0f), p.zc);
+            }
+        }
+        radius[rec] = rad;
+        touched[rec] = tt;
+    }
+}
+
+// Backward of the projection.  acc holds, per record, the planes
+// kAccU..kAccMaxW written by the compositing backward.  One thread per
+// Gaussian: accumulates over views in registers, then writes every parameter
+// plane of the Gaussian once (zeros when no view saw it).
+template <int D>
+__global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ P, long long n, long long ld,
+                                                     ViewTable vt, RasterCfg cfg, const int *__restrict__ radius,
+                                                     const float *__restrict__ acc, long long nrec,
+                                                     float *__restrict__ G, int accumulate,
+                                                     const float *__restrict__ loss_per_view,
+                                                     float *__restrict__ stats, long long stats_ld) {
+    constexpr int K = (D + 1) * (D + 1);
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+
+    float gmean[3] = {0, 0, 0}, glogs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glogit = 0.0f;
+    float gsh[K][3];
+    #pragma unroll
+    for (int k = 0; k < K; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.0f;
+    float st_omega = 0, st_kappa = 0, st_gamma = 0, st_maxw = 0, st_gnorm = 0, st_views = 0;
+
+    bool any = false;
+    for (int v = 0; v < vt.n_views; ++v) any |= radius[v * ld + g] > 0;
+
+    if (any) {
+        const float mx = P[0 * ld + g], my = P[1 * ld + g], mz = P[2 * ld + g];
+        float qw = P[6 * ld + g], qx = P[7 * ld + g], qy = P[8 * ld + g], qz = P[9 * ld + g];
+        const float nq = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw /= nq; qx /= nq; qy /= nq; qz /= nq;
+        float R[9];
+        quat_rotation(qw, qx, qy, qz, R);
+        const float s[3] = {expf(P[3 * ld + g]), expf(P[4 * ld + g]), expf(P[5 * ld + g])};
+        float M[9];
+        #pragma unroll
+        for (int r = 0; r < 3; ++r)
+            #pragma unroll
+            for (int cix = 0; cix < 3; ++cix) M[3 * r + cix] = R[3 * r + cix] * s[cix];
+        Cov3 S;
+        S.s00 = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+        S.s01 = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+        S.s02 = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+        S.s11 = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+        S.s12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+        S.s22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+        const float o = 1.0f / (1.0f + expf(-P[10 * ld + g]));
+        float dSig[6] = {0, 0, 0, 0, 0, 0};  // symmetric gradient: d00 d01 d02 d11 d12 d22 (off-diagonal counted once per entry)
+
+        for (int v = 0; v < vt.n_views; ++v) {
+            const long long rec = v * ld + g;
+            if (radius[rec] <= 0) continue;
+            const ViewDesc &c = vt.v[v];
+            const float du = acc[kAccU * nrec + rec], dv = acc[kAccV * nrec + rec];
+            const float da = acc[kAccA * nrec + rec], db = acc[kAccB * nrec + rec], dc = acc[kAccC * nrec + rec];
+            const float dop = acc[kAccO * nrec + rec];
+            const float gcol[3] = {acc[kAccR * nrec + rec], acc[kAccG * nrec + rec], acc[kAccBl * nrec + rec]};
+            const float gdepth = acc[kAccZ * nrec + rec];
+
+            if (stats) {
+                const float om = acc[kAccOmega * nrec + rec];
+                st_omega += om;
+                st_kappa += acc[kAccKappa * nrec + rec];
+                st_gamma += (loss_per_view ? loss_per_view[v] : 0.0f) * om;
+                st_maxw = fmaxf(st_maxw, acc[kAccMaxW * nrec + rec]);
+                st_gnorm += sqrtf(du * du + dv * dv);
+                st_views += om > 0.0f ? 1.0f : 0.0f;
+            }
+
+            glogit += dop * o * (1.0f - o);
+
+            // colour: clamp mask and SH gradients
+            float ex = mx - c.campos[0], ey = my - c.campos[1], ez = mz - c.campos[2];
+            const float dist = sqrtf(ex * ex + ey * ey + ez * ez), idist = 1.0f / dist;
+            ex *= idist; ey *= idist; ez *= idist;
+            float Y[16];
+            sh_basis<D>(ex, ey, ez, Y);
+            float w[16];
+            #pragma unroll
+            for (int k = 0; k < K; ++k) w[k] = 0.0f;
+            #pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float raw = 0.5f;
+                #pragma unroll
+                for (int k = 0; k < K; ++k) raw += Y[k] * P[(11 + 3 * k + ch) * ld + g];
+                const float gc = raw < 0.0f ? 0.0f : gcol[ch];
+                #pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    gsh[k][ch] += gc * Y[k];
+                    w[k] += gc * P[(11 + 3 * k + ch) * ld + g];
+                }
+            }
+            if (D > 0) {
+                float gx, gy, gz;
+                sh_basis_vjp<D>(ex, ey, ez, w, gx, gy, gz);
+                const float dd = gx * ex + gy * ey + gz * ez;  // project onto the sphere's tangent plane
+                gmean[0] += (gx - ex * dd) * idist;
+                gmean[1] += (gy - ey * dd) * idist;
+                gmean[2] += (gz - ez * dd) * idist;
+            }
+
+            // conic = Q = Sigma'^-1: dL/dSigma' = -Q G Q, G = [[da, db/2], [db/2, dc]]
+            const ExactPos p = exact_position(c, mx, my, mz);
+            const float x = p.xc, y = p.yc, z = p.zc;
+            const Ewa e = ewa(c, x, y, z, S);
+            const float A = e.A + cfg.dilation, B = e.B, C = e.C + cfg.dilation;
+            const float idet = 1.0f / (A * C - B * B);
+            const float qa = C * idet, qb = -B * idet, qcc = A * idet;
+            const float hb = 0.5f * db;
+            const float QG00 = qa * da + qb * hb, QG01 = qa * hb + qb * dc;
+            const float QG10 = qb * da + qcc * hb, QG11 = qb * hb + qcc * dc;
+            const float dA = -(QG00 * qa + QG01 * qb);
+            const float dBh = -(QG00 * qb + QG01 * qcc);  // half of dL/dB (symmetric entry)
+            const float dC = -(QG10 * qb + QG11 * qcc);
+
+            // Sigma'_2d = T Sigma T^T: dSigma = T^T Sd T, dT = 2 Sd T Sigma, Sd = [[dA, dBh], [dBh, dC]]
+            const float *T = e.T;
+            float U[6];  // Sd T (2 x 3)
+            #pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                U[k] = dA * T[k] + dBh * T[3 + k];
+                U[3 + k] = dBh * T[k] + dC * T[3 + k];
+            }
+            dSig[0] += T[0] * U[0] + T[3] * U[3];
+            dSig[1] += T[0] * U[1] + T[3] * U[4];
+            dSig[2] += T[0] * U[2] + T[3] * U[5];
+            dSig[3] += T[1] * U[1] + T[4] * U[4];
+            dSig[4] += T[1] * U[2] + T[4] * U[5];
+            dSig[5] += T[2] * U[2] + T[5] * U[5];
+            float dT[6];
+            #pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const float u0 = U[3 * r], u1 = U[3 * r + 1], u2 = U[3 * r + 2];
+                dT[3 * r + 0] = 2.0f * (u0 * S.s00 + u1 * S.s01 + u2 * S.s02);
+                dT[3 * r + 1] = 2.0f * (u0 * S.s01 + u1 * S.s11 + u2 * S.s12);
+                dT[3 * r + 2] = 2.0f * (u0 * S.s02 + u1 * S.s12 + u2 * S.s22);
+            }
+            // T = J W: dJ = dT W^T; J00 = fx/z, J02 = -fx tx/z^2, J11 = fy/z, J12 = -fy ty/z^2
+            const float dJ00 = dT[0] * c.R[0] + dT[1] * c.R[1] + dT[2] * c.R[2];
+            const float dJ02 = dT[0] * c.R[6] + dT[1] * c.R[7] + dT[2] * c.R[8];
+            const float dJ11 = dT[3] * c.R[3] + dT[4] * c.R[4] + dT[5] * c.R[5];
+            const float dJ12 = dT[3] * c.R[6] + dT[4] * c.R[7] + dT[5] * c.R[8];
+            const float iz = 1.0f / z, iz2 = iz * iz, iz3 = iz2 * iz;
+            const float dtx_dx = (e.clx_lo || e.clx_hi) ? 0.0f : 1.0f;
+            const float dtx_dz = e.clx_lo ? -c.limx : (e.clx_hi ? c.limx : 0.0f);
+            const float dty_dy = (e.cly_lo || e.cly_hi) ? 0.0f : 1.0f;
+            const float dty_dz = e.cly_lo ? -c.limy : (e.cly_hi ? c.limy : 0.0f);
+            float gx = dJ02 * (-c.fx * iz2) * dtx_dx + du * c.fx * iz;
+            float gy = dJ12 * (-c.fy * iz2) * dty_dy + dv * c.fy * iz;
+            float gz = -dJ00 * c.fx * iz2 - dJ11 * c.fy * iz2 +
+                       dJ02 * (-c.fx * dtx_dz * iz2 + 2.0f * c.fx * e.tx * iz3) +
+                       dJ12 * (-c.fy * dty_dz * iz2 + 2.0f * c.fy * e.ty * iz3) -
+                       du * c.fx * x * iz2 - dv * c.fy * y * iz2 + gdepth;
+            gmean[0] += c.R[0] * gx + c.R[3] * gy + c.R[6] * gz;
+            gmean[1] += c.R[1] * gx + c.R[4] * gy + c.R[7] * gz;
+            gmean[2] += c.R[2] * gx + c.R[5] * gy + c.R[8] * gz;
+        }
+
+        // Sigma = M M^T, M = R diag(s): dM = (dSig + dSig^T) M with the full (non-halved) matrix
+        const float F00 = 2.0f * dSig[0], F11 = 2.0f * dSig[3], F22 = 2.0f * dSig[5];
+        const float F01 = dSig[1] + dSig[1], F02 = dSig[2] + dSig[2], F12 = dSig[4] + dSig[4];
+        // dSig entries above hold dL/dSigma_kl for each ordered pair (k,l) with the
+        // symmetric matrix Sd, so (dSig + dSig^T)_kl = 2 dSig_kl.
+        float dM[9];
+        #pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            dM[0 + m] = F00 * M[0 + m] + F01 * M[3 + m] + F02 * M[6 + m];
+            dM[3 + m] = F01 * M[0 + m] + F11 * M[3 + m] + F12 * M[6 + m];
+            dM[6 + m] = F02 * M[0 + m] + F12 * M[3 + m] + F22 * M[6 + m];
+        }
+        float dR[9];
+        #pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float ds = dM[m] * R[m] + dM[3 + m] * R[3 + m] + dM[6 + m] * R[6 + m];
+            glogs[m] = ds * s[m];
+            dR[m] = dM[m] * s[m]; dR[3 + m] = dM[3 + m] * s[m]; dR[6 + m] = dM[6 + m] * s[m];
+        }
+        const float w_ = qw, x_ = qx, y_ = qy, z_ = qz;
+        const float dqw = 2.f * (-z_ * dR[1] + y_ * dR[2] + z_ * dR[3] - x_ * dR[5] - y_ * dR[6] + x_ * dR[7]);
+        const float dqx = 2.f * (y_ * dR[1] + z_ * dR[2] + y_ * dR[3] - 2.f * x_ * dR[4] - w_ * dR[5] + z_ * dR[6] +
+                                 w_ * dR[7] - 2.f * x_ * dR[8]);
+        const float dqy = 2.f * (-2.f * y_ * dR[0] + x_ * dR[1] + w_ * dR[2] + x_ * dR[3] + z_ * dR[5] - w_ * dR[6] +
+                                 z_ * dR[7] - 2.f * y_ * dR[8]);
+        const float dqz = 2.f * (-2.f * z_ * dR[0] - w_ * dR[1] + x_ * dR[2] + w_ * dR[3] - 2.f * z_ * dR[4] +
+                                 y_ * dR[5] + x_ * dR[6] + y_ * dR[7]);
+        const float qd = w_ * dqw + x_ * dqx + y_ * dqy + z_ * dqz;
+        gq[0] = (dqw - w_ * qd) / nq;
+        gq[1] = (dqx - x_ * qd) / nq;
+        gq[2] = (dqy - y_ * qd) / nq;
+        gq[3] = (dqz - z_ * qd) / nq;
+    }
+
+    auto put = [&](int plane, float val) {
+        float *dst = G + plane * ld + g;
+        *dst = accumulate ? *dst + val : val;
+    };
+    put(0, gmean[0]); put(1, gmean[1]); put(2, gmean[2]);
+    put(3, glogs[0]); put(4, glogs[1]); put(5, glogs[2]);
+    put(6, gq[0]); put(7, gq[1]); put(8, gq[2]); put(9, gq[3]);
+    put(10, glogit);
+    #pragma unroll
+    for (int k = 0; k < K; ++k) { put(11 + 3 * k, gsh[k][0]); put(12 + 3 * k, gsh[k][1]); put(13 + 3 * k, gsh[k][2]); }
+
+    if (stats) {
+        stats[0 * stats_ld + g] += st_omega;
+        stats[1 * stats_ld + g] += st_kappa;
+        stats[2 * stats_ld + g] += st_gamma;
+        stats[3 * stats_ld + g] = fmaxf(stats[3 * stats_ld + g], st_maxw);
+        stats[4 * stats_ld + g] += st_gnorm;
+        stats[5 * stats_ld + g] += st_views;
+    }
+}
+
+void launch_project(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
+                    float2 *xy, float4 *co, float4 *rgbd, int *radius, int *touched, int *status, cudaStream_t s) {
+    if (n <= 0) return;
+    const int blocks = (int)ceil_div(n, 256);
+    switch (D) {
+        case 0: k_project<0><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status); break;
+        case 1: k_project<1><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status); break;
+        case 2: k_project<2><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status); break;
+        default: k_project<3><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status); break;
+    }
+}
+
+void launch_project_bwd(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
+                        const int *radius, const float *acc, long long nrec, float *G, int accumulate,
+                        const float *loss_per_view, float *stats, long long stats_ld, cudaStream_t s) {
+    if (n <= 0) return;
+    const int blocks = (int)ceil_div(n, 256);
+#define GS_PB(DD) k_project_bwd<DD><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, radius, acc, nrec, G, accumulate, \
+                                                            loss_per_view, stats, stats_ld)
+    switch (D) {
+        case 0: GS_PB(0); break;
+        case 1: GS_PB(1); break;
+        case 2: GS_PB(2); break;
+        default: GS_PB(3); break;
+    }
+#undef GS_PB
+}
+
+}  // namespace gs

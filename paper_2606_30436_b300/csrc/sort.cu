@@ -1,0 +1,386 @@
+// sort.cu -- binning of projected Gaussians into (tile, depth)-ordered pairs.
+//
+// The order required is that of a stable sort by the 64-bit key
+// (global tile << 32) | depth bits with ties broken by record index ("sorted
+// Gaussians along the ray", Supp. D.2).  It is produced in two cheaper stages:
+//   1. the visible records (radius > 0), compacted in index order, are sorted
+//      once by their 32-bit depth with a stable LSD radix sort, giving each a
+//      depth rank;
+//   2. every visible record emits one (tile, rank) pair per overlapped tile,
+//      in rank order, and a stable LSD radix sort on the tile bits alone puts
+//      the pairs in tile order while keeping rank order inside a tile.
+// Stage 2 moves 8 bytes per pair over ceil(tile_bits / 8) passes instead of
+// 12 bytes over ceil((32 + tile_bits) / 8) passes for the 64-bit key.
+// Every kernel reads its element count from device memory and runs on a fixed
+// grid, so the sequence needs no host synchronisation and can be captured.
+#include "gs_internal.cuh"
+#include "gs_kernels.h"
+
+namespace gs {
+
+constexpr int kSortBlocks = 512;  // fixed grid of the segmented kernels
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 elements per block round
+
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan (blockDim.x a multiple of 32, <= 1024)
+
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T x, T &total, T *smem /* >= 32 */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T inc = x;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) smem[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nw ? smem[lane] : T(0);
+        T wi = w;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) smem[lane] = wi - w;  // exclusive prefix of warp totals
+        if (lane == nw - 1) smem[32] = wi;
+    }
+    __syncthreads();
+    T res = smem[warp] + inc - x;
+    total = smem[32];
+    __syncthreads();
+    return res;
+}
+
+// Contiguous segment of [0, count) owned by this block, a multiple of kSortTile.
+__device__ __forceinline__ void block_segment(long long count, long long &beg, long long &end) {
+    const long long seg = ceil_div(ceil_div(count, (long long)gridDim.x), (long long)kSortTile) * kSortTile;
+    beg = min(count, (long long)blockIdx.x * seg);
+    end = min(count, beg + seg);
+}
+
+// ---------------------------------------------------------------------------
+// stage 0: stable compaction of the visible records with their depth key
+
+__global__ void __launch_bounds__(kSortThreads) k_visible_count(const int *__restrict__ radius, long long nrec,
+                                                                 unsigned long long *__restrict__ blk) {
+    __shared__ unsigned long long sm[33];
+    long long beg, end;
+    block_segment(nrec, beg, end);
+    unsigned long long c = 0;
+    for (long long i = beg + threadIdx.x; i < end; i += kSortThreads) c += radius[i] > 0;
+    unsigned long long total;
+    block_exclusive_scan<unsigned long long>(c, total, sm);
+    if (threadIdx.x == 0) blk[blockIdx.x] = total;
+}
+
+// Exclusive scan of the per-block sums (one block of kSortBlocks threads).
+// mode 0: total -> counts[0] (visible records).
+// mode 1: total -> pairs; counts[2] = needed, counts[1] = pairs or 0 on overflow.
+__global__ void __launch_bounds__(kSortBlocks) k_scan_blocks(unsigned long long *__restrict__ blk, int mode,
+                                                             int *__restrict__ counts, long long max_pairs,
+                                                             int *__restrict__ status) {
+    __shared__ unsigned long long sm[33];
+    unsigned long long x = blk[threadIdx.x], total;
+    unsigned long long ex = block_exclusive_scan<unsigned long long>(x, total, sm);
+    blk[threadIdx.x] = ex;
+    if (threadIdx.x == 0) {
+        const int t32 = (int)min(total, (unsigned long long)0x7fffffff);
+        if (mode == 0) {
+            counts[0] = t32;
+        } else {
+            counts[2] = t32;
+            const bool ok = total <= (unsigned long long)max_pairs;
+            counts[1] = ok ? t32 : 0;
+            if (!ok && status) atomicOr(status, 1 << GS_ERR_CAPACITY);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_visible_compact(const int *__restrict__ radius,
+                                                                   const float4 *__restrict__ rgbd, long long nrec,
+                                                                   const unsigned long long *__restrict__ blk,
+                                                                   uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
+    __shared__ unsigned long long sm[33];
+    long long beg, end;
+    block_segment(nrec, beg, end);
+    unsigned long long run = blk[blockIdx.x];
+    for (long long base = beg; base < end; base += kSortThreads) {
+        const long long i = base + threadIdx.x;
+        const bool f = i < end && radius[i] > 0;
+        unsigned long long total;
+        const unsigned long long off = block_exclusive_scan<unsigned long long>(f ? 1ull : 0ull, total, sm);
+        if (f) {
+            key[run + off] = __float_as_uint(rgbd[i].w);  // depth > near > 0: uint order = float order
+            val[run + off] = (uint32_t)i;
+        }
+        run += total;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort pass (keys u32 with u32 values), digit of `bits` <= 8
+// bits at `shift`; element count read from *count.
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
+                                                                 const int *__restrict__ count, int shift, int bits,
+                                                                 uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[256];
+    const int radix = 1 << bits;
+    const uint32_t mask = radix - 1;
+    for (int i = threadIdx.x; i < radix; i += kSortThreads) h[i] = 0;
+    __syncthreads();
+    long long beg, end;
+    block_segment(*count, beg, end);
+    for (long long i = beg + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < radix; d += kSortThreads) hist[d * kSortBlocks + blockIdx.x] = h[d];
+}
+
+// One block per digit: exclusive scan of the digit's per-block counts.
+__global__ void __launch_bounds__(kSortBlocks) k_radix_scan(uint32_t *__restrict__ hist, uint32_t *__restrict__ dtotal) {
+    __shared__ uint32_t sm[33];
+    const int d = blockIdx.x;
+    uint32_t x = hist[d * kSortBlocks + threadIdx.x], total;
+    uint32_t ex = block_exclusive_scan<uint32_t>(x, total, sm);
+    hist[d * kSortBlocks + threadIdx.x] = ex;
+    if (threadIdx.x == 0) dtotal[d] = total;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ kin,
+                                                                   const uint32_t *__restrict__ vin,
+                                                                   uint32_t *__restrict__ kout,
+                                                                   uint32_t *__restrict__ vout,
+                                                                   const int *__restrict__ count, int shift, int bits,
+                                                                   const uint32_t *__restrict__ hist,
+                                                                   const uint32_t *__restrict__ dtotal) {
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_tcount[256];
+    __shared__ uint32_t s_whist[kSortThreads / 32][256];
+    __shared__ uint32_t sm[33];
+    const int radix = 1 << bits;
+    const uint32_t mask = radix - 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+
+    {
+        uint32_t t = threadIdx.x < radix ? dtotal[threadIdx.x] : 0u, tot;
+        uint32_t ex = block_exclusive_scan<uint32_t>(t, tot, sm);
+        if (threadIdx.x < radix) s_base[threadIdx.x] = ex + hist[threadIdx.x * kSortBlocks + blockIdx.x];
+    }
+    __syncthreads();
+    long long beg, end;
+    block_segment(*count, beg, end);
+    for (long long tb = beg; tb < end; tb += kSortTile) {
+        for (int i = lane; i < radix; i += 32) s_whist[warp][i] = 0;
+        __syncwarp();
+        uint32_t k[kSortItems], v[kSortItems], rk[kSortItems];
+        int d[kSortItems];
+        #pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            const long long idx = tb + warp * (32 * kSortItems) + r * 32 + lane;
+            const bool valid = idx < end;
+            k[r] = valid ? kin[idx] : 0u;
+            v[r] = valid ? vin[idx] : 0u;
+            d[r] = valid ? (int)((k[r] >> shift) & mask) : radix;  // radix = "no element"
+        }
+        #pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
+            const int leader = __ffs(peers) - 1;
+            uint32_t base = 0;
+            if (lane == leader && d[r] < radix) {
+                base = s_whist[warp][d[r]];
+                s_whist[warp][d[r]] = base + __popc(peers);
+            }
+            base = __shfl_sync(0xffffffffu, base, leader);
+            rk[r] = base + __popc(peers & lt);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < radix; dd += kSortThreads) {
+            uint32_t s = 0;
+            #pragma unroll
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                const uint32_t c = s_whist[w][dd];
+                s_whist[w][dd] = s;
+                s += c;
+            }
+            s_tcount[dd] = s;
+        }
+        __syncthreads();
+        #pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            if (d[r] < radix) {
+                const uint32_t pos = s_base[d[r]] + s_whist[warp][d[r]] + rk[r];
+                kout[pos] = k[r];
+                vout[pos] = v[r];
+            }
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < radix; dd += kSortThreads) s_base[dd] += s_tcount[dd];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stage 2: pair emission in depth-rank order
+
+__global__ void __launch_bounds__(kSortThreads) k_tiles_count(const uint32_t *__restrict__ sorted_rec,
+                                                               const int *__restrict__ touched,
+                                                               const int *__restrict__ counts,
+                                                               unsigned long long *__restrict__ blk) {
+    __shared__ unsigned long long sm[33];
+    long long beg, end;
+    block_segment(counts[0], beg, end);
+    unsigned long long c = 0;
+    for (long long r = beg + threadIdx.x; r < end; r += kSortThreads) c += (unsigned)touched[sorted_rec[r]];
+    unsigned long long total;
+    block_exclusive_scan<unsigned long long>(c, total, sm);
+    if (threadIdx.x == 0) blk[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_emit_pairs(const uint32_t *__restrict__ sorted_rec,
+                                                              const int *__restrict__ touched,
+                                                              const int *__restrict__ radius,
+                                                              const float2 *__restrict__ xy, long long ld, ViewTable vt,
+                                                              const int *__restrict__ counts,
+                                                              const unsigned long long *__restrict__ blk,
+                                                              uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+    __shared__ unsigned long long sm[33];
+    if (counts[1] == 0) return;  // nothing to emit, or overflow
+    long long beg, end;
+    block_segment(counts[0], beg, end);
+    unsigned long long run = blk[blockIdx.x];
+    for (long long base = beg; base < end; base += kSortThreads) {
+        const long long r = base + threadIdx.x;
+        uint32_t rec = 0;
+        int tt = 0;
+        if (r < end) {
+            rec = sorted_rec[r];
+            tt = touched[rec];
+        }
+        unsigned long long total;
+        unsigned long long off = run + block_exclusive_scan<unsigned long long>((unsigned long long)tt, total, sm);
+        if (tt > 0) {
+            const int view = (int)(rec / ld);
+            const ViewDesc &c = vt.v[view];
+            const float2 p = xy[rec];
+            const Rect rc = tile_rect(p.x, p.y, radius[rec], vt.tile_w, vt.tile_h, c.GW, c.GH);
+            // the rectangle is the one the projection counted (same inputs, same
+            // arithmetic); the cap keeps every write inside this record's slot
+            const unsigned long long stop = off + (unsigned long long)tt;
+            for (int ty = rc.y0; ty < rc.y1 && off < stop; ++ty)
+                for (int tx = rc.x0; tx < rc.x1 && off < stop; ++tx) {
+                    pkey[off] = (uint32_t)(c.tile_offset + ty * c.GW + tx);
+                    pval[off] = (uint32_t)r;
+                    ++off;
+                }
+        }
+        run += total;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ pkey, const uint32_t *__restrict__ pval,
+                                                 const uint32_t *__restrict__ sorted_rec,
+                                                 const int *__restrict__ counts, int *__restrict__ ids,
+                                                 int2 *__restrict__ ranges) {
+    const long long P = counts[1];
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const uint32_t t = pkey[p];
+        ids[p] = (int)sorted_rec[pval[p]];
+        if (p == 0 || pkey[p - 1] != t) ranges[t].x = (int)p;
+        if (p == P - 1 || pkey[p + 1] != t) ranges[t].y = (int)(p + 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+struct SortWs {
+    unsigned long long *blk;
+    uint32_t *hist, *dtotal;
+    uint32_t *dk0, *dv0, *dk1, *dv1;
+    uint32_t *pk0, *pv0, *pk1, *pv1;
+    size_t bytes;
+};
+
+static SortWs carve(void *base, long long nrec, long long max_pairs) {
+    SortWs w;
+    size_t off = 0;
+    char *b = (char *)base;
+    auto take = [&](size_t bytes) {
+        char *p = b ? b + off : nullptr;
+        off = align_up(off + bytes, 256);
+        return p;
+    };
+    w.blk = (unsigned long long *)take(sizeof(unsigned long long) * (kSortBlocks + 1));
+    w.hist = (uint32_t *)take(sizeof(uint32_t) * 256 * kSortBlocks);
+    w.dtotal = (uint32_t *)take(sizeof(uint32_t) * 256);
+    w.dk0 = (uint32_t *)take(sizeof(uint32_t) * nrec);
+    w.dv0 = (uint32_t *)take(sizeof(uint32_t) * nrec);
+    w.dk1 = (uint32_t *)take(sizeof(uint32_t) * nrec);
+    w.dv1 = (uint32_t *)take(sizeof(uint32_t) * nrec);
+    w.pk0 = (uint32_t *)take(sizeof(uint32_t) * max_pairs);
+    w.pv0 = (uint32_t *)take(sizeof(uint32_t) * max_pairs);
+    w.pk1 = (uint32_t *)take(sizeof(uint32_t) * max_pairs);
+    w.pv1 = (uint32_t *)take(sizeof(uint32_t) * max_pairs);
+    w.bytes = off;
+    return w;
+}
+
+size_t sort_workspace_bytes(long long nrec, long long max_pairs) { return carve(nullptr, nrec, max_pairs).bytes; }
+
+// Sorts (k, v) in place-by-ping-pong over bits [0, total_bits); returns which
+// buffer pair holds the result (0: k0/v0, 1: k1/v1).
+static int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *count, int total_bits,
+                      uint32_t *hist, uint32_t *dtotal, cudaStream_t s) {
+    if (total_bits <= 0) return 0;
+    const int passes = (total_bits + 7) / 8;
+    const int width = (total_bits + passes - 1) / passes;
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * width;
+        const int bits = min(width, total_bits - shift);
+        uint32_t *ki = cur ? k1 : k0, *vi = cur ? v1 : v0, *ko = cur ? k0 : k1, *vo = cur ? v0 : v1;
+        k_radix_upsweep<<<kSortBlocks, kSortThreads, 0, s>>>(ki, count, shift, bits, hist);
+        k_radix_scan<<<1 << bits, kSortBlocks, 0, s>>>(hist, dtotal);
+        k_radix_downsweep<<<kSortBlocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, shift, bits, hist, dtotal);
+        cur ^= 1;
+    }
+    return cur;
+}
+
+cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy, const float4 *rgbd, long long nrec,
+                        long long ld, const ViewTable &vt, int *gauss_ids, int2 *tile_ranges, int *counts,
+                        long long max_pairs, void *ws, int *status, cudaStream_t s) {
+    SortWs w = carve(ws, nrec, max_pairs);
+    cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)vt.total_tiles, s);
+    if (e != cudaSuccess) return e;
+
+    // stage 1: visible records sorted by depth
+    k_visible_count<<<kSortBlocks, kSortThreads, 0, s>>>(radius, nrec, w.blk);
+    k_scan_blocks<<<1, kSortBlocks, 0, s>>>(w.blk, 0, counts, max_pairs, status);
+    k_visible_compact<<<kSortBlocks, kSortThreads, 0, s>>>(radius, rgbd, nrec, w.blk, w.dk0, w.dv0);
+    const int dres = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, counts + 0, 32, w.hist, w.dtotal, s);
+    const uint32_t *sorted_rec = dres ? w.dv1 : w.dv0;
+
+    // stage 2: pairs in rank order, then a stable partition by tile
+    k_tiles_count<<<kSortBlocks, kSortThreads, 0, s>>>(sorted_rec, touched, counts, w.blk);
+    k_scan_blocks<<<1, kSortBlocks, 0, s>>>(w.blk, 1, counts, max_pairs, status);
+    k_emit_pairs<<<kSortBlocks, kSortThreads, 0, s>>>(sorted_rec, touched, radius, xy, ld, vt, counts, w.blk, w.pk0,
+                                                       w.pv0);
+    int tile_bits = 0;
+    while ((1ll << tile_bits) < (long long)vt.total_tiles) ++tile_bits;
+    const int pres = radix_sort(w.pk0, w.pv0, w.pk1, w.pv1, counts + 1, tile_bits, w.hist, w.dtotal, s);
+    k_ranges<<<148 * 8, 256, 0, s>>>(pres ? w.pk1 : w.pk0, pres ? w.pv1 : w.pv0, sorted_rec, counts, gauss_ids,
+                                     tile_ranges);
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,438 @@
+"""Thin Python binding of the C ABI in ``include/gs.h`` (``libgs.so``).
+
+The functions ``gs_project``, ``gs_sort``, ``gs_render_fwd``, ``gs_loss``,
+``gs_render_bwd``, ``gs_adam`` and ``gs_prune_stats`` carry the names of the C
+entry points and only marshal arguments: torch tensors give device pointers,
+the current torch stream is passed as the CUDA stream, and every step of the
+mapping path runs in the library's kernels.  There is no CPU fallback: if the
+library is missing or no CUDA device is present, the calls raise.
+
+The helper classes (``GaussianModel``, ``Buffers``, ``MappingStep``) own the
+device buffers the C ABI expects and chain the calls into one mapping
+iteration (Sec. 3.2.3: render, L_photo, backward, Adam; Supp. E: lifecycle
+statistics).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+# --------------------------------------------------------------------------
+# C structs (mirror include/gs.h)
+
+GS_MAX_VIEWS = 64
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "pair capacity exceeded",
+                4: "bounded wait timed out", 5: "non-finite value"}
+GS_ERR_CAPACITY = 3
+GS_ERR_NUMERIC = 5
+
+
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class RasterCfg(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("near_z", C.c_float), ("dilation", C.c_float),
+                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float),
+                ("tan_clamp", C.c_float), ("bg", C.c_float * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("n", C.c_int64), ("ld", C.c_int64), ("sh_degree", C.c_int32)]
+
+
+class Projected(C.Structure):
+    _fields_ = [("xy", C.c_void_p), ("conic_opacity", C.c_void_p), ("rgb_depth", C.c_void_p),
+                ("radius", C.c_void_p), ("tiles_touched", C.c_void_p), ("ld", C.c_int64)]
+
+
+class Binning(C.Structure):
+    _fields_ = [("gauss_ids", C.c_void_p), ("tile_ranges", C.c_void_p), ("counts", C.c_void_p),
+                ("max_pairs", C.c_int64)]
+
+
+class Frame(C.Structure):
+    _fields_ = [("img", C.c_void_p), ("T_final", C.c_void_p), ("last", C.c_void_p), ("depth", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("acc", C.c_void_p), ("ld", C.c_int64)]
+
+
+class ChunkScores(C.Structure):
+    _fields_ = [("S_d", C.c_void_p), ("S_p", C.c_void_p), ("prune_max", C.c_void_p), ("densify", C.c_void_p),
+                ("prune", C.c_void_p)]
+
+
+EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspace_size", "gs_loss_workspace_size",
+           "gs_bwd_workspace_size", "gs_prune_workspace_size", "gs_project", "gs_sort", "gs_render_fwd", "gs_loss",
+           "gs_render_bwd", "gs_adam", "gs_prune_stats")
+
+_lib = None
+
+
+def lib():
+    """Loads libgs.so (building it when a source is newer); raises if it cannot."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path) or _build._stale():
+            path = _build.build()
+        L = C.CDLL(path)
+        vp, i32, i64, f32, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.c_size_t
+        P = C.POINTER
+        L.gs_status_string.argtypes = [C.c_int]
+        L.gs_status_string.restype = C.c_char_p
+        L.gs_version.restype = i32
+        L.gs_view_layout.argtypes = [P(Camera), i32, P(RasterCfg), P(i64), P(i64), vp, vp]
+        L.gs_sort_workspace_size.argtypes = [i64, i64, P(sz)]
+        L.gs_loss_workspace_size.argtypes = [i32, i32, P(sz)]
+        L.gs_bwd_workspace_size.argtypes = [i64, P(sz)]
+        L.gs_prune_workspace_size.argtypes = [i64, P(sz)]
+        L.gs_project.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), vp, vp]
+        L.gs_sort.argtypes = [P(Projected), P(Camera), i32, P(RasterCfg), P(Binning), vp, sz, vp, vp]
+        L.gs_render_fwd.argtypes = [P(Projected), P(Binning), P(Camera), i32, P(RasterCfg), P(Frame), vp]
+        L.gs_loss.argtypes = [vp, vp, P(Camera), i32, f32, vp, vp, vp, sz, vp]
+        L.gs_render_bwd.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), P(Binning), P(Frame),
+                                    vp, vp, vp, vp, f32, P(Params), i32, P(Stats), vp, sz, vp]
+        L.gs_adam.argtypes = [P(Params), P(Params), P(Params), P(Params), P(f32 * 6), f32, f32, f32, i64, vp]
+        L.gs_prune_stats.argtypes = [P(Stats), i64, i32, f32, f32, P(ChunkScores), vp, sz, vp]
+        for name in EXPORTS:
+            if name not in ("gs_status_string", "gs_version"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class GSError(RuntimeError):
+    pass
+
+
+def _check(st, what):
+    if st != 0:
+        raise GSError("%s: %s" % (what, lib().gs_status_string(st).decode()))
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+# --------------------------------------------------------------------------
+# host-side descriptions
+
+def make_camera(cam) -> Camera:
+    R = np.asarray(cam["R"], np.float32).reshape(9)
+    t = np.asarray(cam["t"], np.float32).reshape(3)
+    return Camera((C.c_float * 9)(*R), (C.c_float * 3)(*t), cam["fx"], cam["fy"], cam["cx"], cam["cy"],
+                  int(cam["width"]), int(cam["height"]))
+
+
+def camera_array(cams):
+    arr = (Camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = make_camera(c)
+    return arr
+
+
+@dataclass
+class Config:
+    """Rasteriser constants (the standard EWA-splatting values)."""
+    tile_w: int = 16
+    tile_h: int = 16
+    near_z: float = 0.2
+    dilation: float = 0.3
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    t_min: float = 1e-4
+    tan_clamp: float = 1.3
+    bg: tuple = (0.0, 0.0, 0.0)
+
+    def c(self) -> RasterCfg:
+        return RasterCfg(self.tile_w, self.tile_h, self.near_z, self.dilation, self.alpha_min, self.alpha_max,
+                         self.t_min, self.tan_clamp, (C.c_float * 3)(*self.bg))
+
+
+def planes(sh_degree: int) -> int:
+    return 11 + 3 * (sh_degree + 1) ** 2
+
+
+def padded(n: int) -> int:
+    return max(4, (n + 31) // 32 * 32)
+
+
+def view_layout(cams, cfg: Config):
+    arr = camera_array(cams)
+    nt, npx = C.c_int64(), C.c_int64()
+    toff = np.zeros(len(cams), np.int64)
+    poff = np.zeros(len(cams), np.int64)
+    _check(lib().gs_view_layout(arr, len(cams), C.byref(cfg.c()), C.byref(nt), C.byref(npx),
+                                toff.ctypes.data_as(C.c_void_p), poff.ctypes.data_as(C.c_void_p)), "gs_view_layout")
+    return nt.value, npx.value, toff, poff
+
+
+# --------------------------------------------------------------------------
+# Gaussian parameters in the plane-major layout
+
+class GaussianModel:
+    """Parameters of n Gaussians as one [K, ld] float32 device tensor."""
+
+    def __init__(self, n, sh_degree, device="cuda", data=None):
+        self.n, self.sh_degree = int(n), int(sh_degree)
+        self.K = planes(self.sh_degree)
+        self.ld = padded(self.n)
+        self.data = torch.zeros(self.K, self.ld, dtype=torch.float32, device=device) if data is None else data
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda"):
+        m = cls(len(scene["means"]), scene["sh_degree"], device=device)
+        m.data.copy_(torch.from_numpy(pack_planes(scene, m.ld)))
+        return m
+
+    def like(self):
+        return GaussianModel(self.n, self.sh_degree, device=self.data.device)
+
+    def c(self) -> Params:
+        return Params(self.data.data_ptr(), self.n, self.ld, self.sh_degree)
+
+    def to_scene(self):
+        return unpack_planes(self.data.detach().cpu().numpy(), self.n, self.sh_degree)
+
+
+def pack_planes(scene, ld):
+    """Array-of-structures scene dict -> [K, ld] plane-major float32 array."""
+    n, D = len(scene["means"]), int(scene["sh_degree"])
+    K = planes(D)
+    out = np.zeros((K, ld), np.float32)
+    out[0:3, :n] = np.asarray(scene["means"], np.float32).T
+    out[3:6, :n] = np.asarray(scene["log_scales"], np.float32).T
+    out[6:10, :n] = np.asarray(scene["quats"], np.float32).T
+    out[10, :n] = np.asarray(scene["opacity_logits"], np.float32)
+    sh = np.asarray(scene["sh"], np.float32).reshape(n, -1)  # (n, (D+1)^2 * 3), coefficient-major, RGB minor
+    out[11:, :n] = sh.T
+    return out
+
+
+def unpack_planes(arr, n, D):
+    Kc = (D + 1) ** 2
+    return dict(means=arr[0:3, :n].T.copy(), log_scales=arr[3:6, :n].T.copy(), quats=arr[6:10, :n].T.copy(),
+                opacity_logits=arr[10, :n].copy(), sh=arr[11:, :n].T.reshape(n, Kc, 3).copy(), sh_degree=D)
+
+
+# --------------------------------------------------------------------------
+# device buffers of one (views, Gaussians) configuration
+
+class Buffers:
+    """Every device buffer the mapping step needs, sized once."""
+
+    def __init__(self, model: GaussianModel, cams, cfg: Config, max_pairs: int, with_depth=False, with_stats=True):
+        dev = model.data.device
+        self.cams, self.cfg = list(cams), cfg
+        self.n_views = len(self.cams)
+        self.ld = model.ld
+        self.nrec = self.n_views * self.ld
+        self.total_tiles, self.total_pixels, self.tile_offset, self.pixel_offset = view_layout(self.cams, cfg)
+        f32, i32 = torch.float32, torch.int32
+        nr = self.nrec
+        self.xy = torch.empty(nr, 2, dtype=f32, device=dev)
+        self.conic_opacity = torch.empty(nr, 4, dtype=f32, device=dev)
+        self.rgb_depth = torch.empty(nr, 4, dtype=f32, device=dev)
+        self.radius = torch.empty(nr, dtype=i32, device=dev)
+        self.tiles_touched = torch.empty(nr, dtype=i32, device=dev)
+        self.counts = torch.zeros(4, dtype=i32, device=dev)
+        self.status = torch.zeros(1, dtype=i32, device=dev)
+        self.tile_ranges = torch.zeros(self.total_tiles, 2, dtype=i32, device=dev)
+        self.img = torch.empty(3 * self.total_pixels, dtype=f32, device=dev)
+        self.T_final = torch.empty(self.total_pixels, dtype=f32, device=dev)
+        self.last = torch.empty(self.total_pixels, dtype=i32, device=dev)
+        self.depth = torch.empty(self.total_pixels, dtype=f32, device=dev) if with_depth else None
+        self.dL_dimg = torch.empty(3 * self.total_pixels, dtype=f32, device=dev)
+        self.loss = torch.zeros(self.n_views, dtype=f32, device=dev)
+        self.set_max_pairs(max_pairs)
+        hmax = max(int(c["height"]) for c in self.cams)
+        wmax = max(int(c["width"]) for c in self.cams)
+        self.loss_ws = _workspace(lib().gs_loss_workspace_size, hmax, wmax, device=dev)
+        self.bwd_ws = _workspace(lib().gs_bwd_workspace_size, self.nrec, device=dev)
+        self.stats_acc = torch.zeros(6, model.ld, dtype=f32, device=dev) if with_stats else None
+
+    def set_max_pairs(self, max_pairs):
+        dev = self.xy.device
+        self.max_pairs = int(max_pairs)
+        self.gauss_ids = torch.empty(max(self.max_pairs, 1), dtype=torch.int32, device=dev)
+        self.sort_ws = _workspace(lib().gs_sort_workspace_size, self.nrec, self.max_pairs, device=dev)
+
+    def projected(self) -> Projected:
+        return Projected(self.xy.data_ptr(), self.conic_opacity.data_ptr(), self.rgb_depth.data_ptr(),
+                         self.radius.data_ptr(), self.tiles_touched.data_ptr(), self.ld)
+
+    def binning(self) -> Binning:
+        return Binning(self.gauss_ids.data_ptr(), self.tile_ranges.data_ptr(), self.counts.data_ptr(), self.max_pairs)
+
+    def frame(self) -> Frame:
+        return Frame(self.img.data_ptr(), self.T_final.data_ptr(), self.last.data_ptr(),
+                     None if self.depth is None else self.depth.data_ptr())
+
+    def stats(self):
+        return None if self.stats_acc is None else Stats(self.stats_acc.data_ptr(), self.stats_acc.shape[1])
+
+    def view_image(self, v, t=None):
+        t = self.img if t is None else t
+        W, H = int(self.cams[v]["width"]), int(self.cams[v]["height"])
+        o = 3 * int(self.pixel_offset[v])
+        return t[o:o + 3 * H * W].view(3, H, W)
+
+    def view_plane(self, t, v):
+        W, H = int(self.cams[v]["width"]), int(self.cams[v]["height"])
+        o = int(self.pixel_offset[v])
+        return t[o:o + H * W].view(H, W)
+
+
+def _workspace(fn, *args, device):
+    n = C.c_size_t()
+    _check(fn(*args, C.byref(n)), fn.__name__)
+    return torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=device)
+
+
+# --------------------------------------------------------------------------
+# the C entry points (argument marshalling only)
+
+def gs_project(model: GaussianModel, buf: Buffers, stream=None):
+    arr = camera_array(buf.cams)
+    _check(lib().gs_project(C.byref(model.c()), arr, buf.n_views, C.byref(buf.cfg.c()), C.byref(buf.projected()),
+                            _ptr(buf.status), _stream(stream)), "gs_project")
+
+
+def gs_sort(buf: Buffers, stream=None):
+    arr = camera_array(buf.cams)
+    _check(lib().gs_sort(C.byref(buf.projected()), arr, buf.n_views, C.byref(buf.cfg.c()), C.byref(buf.binning()),
+                         _ptr(buf.sort_ws), buf.sort_ws.numel(), _ptr(buf.status), _stream(stream)), "gs_sort")
+
+
+def gs_render_fwd(buf: Buffers, stream=None):
+    arr = camera_array(buf.cams)
+    _check(lib().gs_render_fwd(C.byref(buf.projected()), C.byref(buf.binning()), arr, buf.n_views,
+                               C.byref(buf.cfg.c()), C.byref(buf.frame()), _stream(stream)), "gs_render_fwd")
+
+
+def gs_loss(buf: Buffers, target: torch.Tensor, lambda_dssim=0.2, stream=None, img=None):
+    arr = camera_array(buf.cams)
+    _check(lib().gs_loss(_ptr(buf.img if img is None else img), _ptr(target), arr, buf.n_views, float(lambda_dssim),
+                         _ptr(buf.loss), _ptr(buf.dL_dimg), _ptr(buf.loss_ws), buf.loss_ws.numel(),
+                         _stream(stream)), "gs_loss")
+
+
+def gs_render_bwd(model: GaussianModel, grads: GaussianModel, buf: Buffers, target=None, tau_err=0.1,
+                  accumulate=False, with_stats=True, dL_ddepth=None, dL_dimg=None, stream=None):
+    arr = camera_array(buf.cams)
+    st = buf.stats() if with_stats else None
+    _check(lib().gs_render_bwd(C.byref(model.c()), arr, buf.n_views, C.byref(buf.cfg.c()), C.byref(buf.projected()),
+                               C.byref(buf.binning()), C.byref(buf.frame()),
+                               _ptr(buf.dL_dimg if dL_dimg is None else dL_dimg), _ptr(dL_ddepth), _ptr(target),
+                               _ptr(buf.loss), float(tau_err), C.byref(grads.c()), int(bool(accumulate)),
+                               None if st is None else C.byref(st), _ptr(buf.bwd_ws), buf.bwd_ws.numel(),
+                               _stream(stream)), "gs_render_bwd")
+
+
+def gs_adam(model: GaussianModel, grads: GaussianModel, exp_avg: GaussianModel, exp_avg_sq: GaussianModel, lr,
+            step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    lrs = (C.c_float * 6)(*[float(x) for x in lr])
+    _check(lib().gs_adam(C.byref(model.c()), C.byref(grads.c()), C.byref(exp_avg.c()), C.byref(exp_avg_sq.c()),
+                         C.byref(lrs), beta1, beta2, eps, int(step), _stream(stream)), "gs_adam")
+
+
+def gs_prune_stats(stats_acc: torch.Tensor, n, n_views, scores: dict, ws: torch.Tensor, tau_d=5.0, tau_p=0.99,
+                   stream=None):
+    st = Stats(stats_acc.data_ptr(), stats_acc.shape[1])
+    cs = ChunkScores(*[scores[k].data_ptr() for k in ("S_d", "S_p", "prune_max", "densify", "prune")])
+    _check(lib().gs_prune_stats(C.byref(st), int(n), int(n_views), float(tau_d), float(tau_p), C.byref(cs),
+                                _ptr(ws), ws.numel(), _stream(stream)), "gs_prune_stats")
+
+
+def prune_buffers(n, device="cuda"):
+    ws = _workspace(lib().gs_prune_workspace_size, n, device=device)
+    f32, u8 = torch.float32, torch.uint8
+    return dict(S_d=torch.zeros(n, dtype=f32, device=device), S_p=torch.zeros(n, dtype=f32, device=device),
+                prune_max=torch.zeros(n, dtype=f32, device=device), densify=torch.zeros(n, dtype=u8, device=device),
+                prune=torch.zeros(n, dtype=u8, device=device)), ws
+
+
+# --------------------------------------------------------------------------
+# one mapping iteration
+
+# Learning rates per parameter group (means, log-scales, quaternion, opacity,
+# SH degree 0, SH degree >= 1); the paper prints none, these are the usual
+# 3DGS values with the mean rate scaled by the scene extent.
+def default_lr(extent=1.0):
+    return (1.6e-4 * extent, 5e-3, 1e-3, 5e-2, 2.5e-3, 1.25e-4)
+
+
+class MappingStep:
+    """render -> L_photo -> backward -> Adam over one chunk of views."""
+
+    def __init__(self, model: GaussianModel, cams, cfg: Config = None, max_pairs=None, lambda_dssim=0.2,
+                 tau_err=0.1, lr=None, with_stats=True, with_depth=False):
+        self.model = model
+        self.cfg = cfg or Config()
+        self.lambda_dssim, self.tau_err = lambda_dssim, tau_err
+        self.lr = lr or default_lr()
+        self.with_stats = with_stats
+        self.grads, self.exp_avg, self.exp_avg_sq = model.like(), model.like(), model.like()
+        self.step_count = 0
+        if max_pairs is None:
+            max_pairs = max(1 << 16, 8 * model.n * len(cams))
+        self.buf = Buffers(model, cams, self.cfg, max_pairs, with_depth=with_depth, with_stats=with_stats)
+
+    def set_cameras(self, cams):
+        assert len(cams) == self.buf.n_views
+        for c_new, c_old in zip(cams, self.buf.cams):
+            assert (c_new["width"], c_new["height"]) == (c_old["width"], c_old["height"])
+        self.buf.cams = list(cams)
+
+    def forward(self, stream=None):
+        b = self.buf
+        b.status.zero_()
+        gs_project(self.model, b, stream)
+        gs_sort(b, stream)
+        gs_render_fwd(b, stream)
+
+    def step(self, target, stream=None, optimize=True):
+        """One iteration on device-resident targets (frame layout)."""
+        self.forward(stream)
+        gs_loss(self.buf, target, self.lambda_dssim, stream)
+        gs_render_bwd(self.model, self.grads, self.buf, target, self.tau_err, with_stats=self.with_stats,
+                      stream=stream)
+        if optimize:
+            self.step_count += 1
+            gs_adam(self.model, self.grads, self.exp_avg, self.exp_avg_sq, self.lr, self.step_count, stream=stream)
+        return self.buf.loss
+
+    def check_status(self):
+        """Host check after the stream completed: raises on capacity overflow."""
+        st = int(self.buf.status.item())
+        if st & (1 << GS_ERR_CAPACITY):
+            needed = int(self.buf.counts[2].item())
+            raise GSError("pair capacity exceeded: %d pairs needed, %d available" % (needed, self.buf.max_pairs))
+        return st
+
+    def fit_capacity(self, slack=1.25):
+        """Runs the forward once and sizes the pair buffer to the count seen."""
+        self.forward()
+        torch.cuda.synchronize()
+        needed = int(self.buf.counts[2].item())
+        if needed > self.buf.max_pairs or needed * slack * 2 < self.buf.max_pairs:
+            self.buf.set_max_pairs(max(1024, int(needed * slack)))
+            self.forward()
+            torch.cuda.synchronize()
+        self.check_status()
+        return needed

@@ -1,0 +1,94 @@
+"""The C-ABI library builds, loads without a GPU, exports exactly the symbols
+that include/gs.h declares, and rejects bad arguments on the host before
+touching the device."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2606_30436_b300 import build as gsbuild
+from paper_2606_30436_b300 import gs, scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_builds_and_loads():
+    path = gsbuild.build()
+    assert os.path.exists(path)
+    L = gs.lib()
+    assert L.gs_version() == 10000 + 1030
+
+
+def test_exports_match_header():
+    gs.lib()
+    declared = _declared()
+    assert len(declared) >= 14
+    out = subprocess.check_output(["nm", "-D", "--defined-only", gsbuild.LIB], text=True)
+    exported = sorted({ln.split()[-1] for ln in out.splitlines() if ln.split()[-1].startswith("gs_")})
+    assert exported == declared
+    assert set(gs.EXPORTS) == set(declared)
+
+
+def test_status_strings():
+    L = gs.lib()
+    for code, name in gs.STATUS_NAMES.items():
+        assert L.gs_status_string(code).decode() == name
+
+
+def test_workspace_sizes_and_layout():
+    L = gs.lib()
+    n = C.c_size_t()
+    assert L.gs_sort_workspace_size(1000, 5000, C.byref(n)) == 0 and n.value > 8 * 5000
+    assert L.gs_sort_workspace_size(-1, 5000, C.byref(n)) == 1
+    assert L.gs_loss_workspace_size(48, 64, C.byref(n)) == 0 and n.value >= 9 * 48 * 64 * 4
+    assert L.gs_loss_workspace_size(0, 64, C.byref(n)) == 1
+    cams = scenes.chunk_cameras(5)
+    nt, npx, toff, poff = gs.view_layout(cams, gs.Config())
+    tiles = [((c["width"] + 15) // 16) * ((c["height"] + 15) // 16) for c in cams]
+    assert nt == sum(tiles) and list(toff) == list(np.cumsum([0] + tiles[:-1]))
+    assert npx == sum(c["width"] * c["height"] for c in cams)
+
+
+def test_invalid_arguments_rejected_on_host():
+    L = gs.lib()
+    cam = gs.camera_array([scenes.pinhole(64, 48, 60.0)])
+    bad_tiles = gs.Config(tile_w=16, tile_h=8).c()
+    nt = C.c_int64()
+    assert L.gs_view_layout(cam, 1, C.byref(bad_tiles), C.byref(nt), None, None, None) == 1
+    assert L.gs_view_layout(cam, 0, C.byref(gs.Config().c()), C.byref(nt), None, None, None) == 1
+    assert L.gs_view_layout(cam, 65, C.byref(gs.Config().c()), C.byref(nt), None, None, None) == 1
+    # misaligned / null parameter buffers never reach the device
+    p = gs.Params(None, 10, 12, 0)
+    proj = gs.Projected(16, 32, 48, 64, 80, 12)
+    assert L.gs_project(C.byref(p), cam, 1, C.byref(gs.Config().c()), C.byref(proj), None, None) == 1
+    p = gs.Params(4, 10, 12, 0)  # not 16-byte aligned
+    assert L.gs_project(C.byref(p), cam, 1, C.byref(gs.Config().c()), C.byref(proj), None, None) == 1
+    p = gs.Params(16, 10, 10, 0)  # ld not a multiple of 4
+    assert L.gs_project(C.byref(p), cam, 1, C.byref(gs.Config().c()), C.byref(proj), None, None) == 1
+    p = gs.Params(16, 10, 12, 4)  # SH degree beyond 3
+    assert L.gs_project(C.byref(p), cam, 1, C.byref(gs.Config().c()), C.byref(proj), None, None) == 1
+    lrs = (C.c_float * 6)(*([1e-3] * 6))
+    q = gs.Params(16, 10, 12, 0)
+    q2 = gs.Params(32, 10, 16, 0)  # ld mismatch
+    assert L.gs_adam(C.byref(q), C.byref(q2), C.byref(q), C.byref(q), C.byref(lrs), 0.9, 0.999, 1e-15, 1, None) == 1
+    assert L.gs_adam(C.byref(q), C.byref(q), C.byref(q), C.byref(q), C.byref(lrs), 0.9, 0.999, 1e-15, 0, None) == 1
+
+
+def test_plane_packing_roundtrip():
+    s = scenes.uniform_scene(37, seed=3, sh_degree=3)
+    arr = gs.pack_planes(s, gs.padded(37))
+    assert arr.shape == (gs.planes(3), 64)
+    back = gs.unpack_planes(arr, 37, 3)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        assert np.array_equal(back[k], s[k])
+    # SH coefficient k of channel c sits in plane 11 + 3k + c
+    assert arr[11 + 3 * 5 + 2, 7] == s["sh"][7, 5, 2]

@@ -1,0 +1,383 @@
+"""Benchmark of the mapping step on one B300 (or N independent replicas).
+
+Workload (one "step" = one mapping iteration, Sec. 3.2.3): 1,000,000 Gaussians
+strewn along a 1 km x 20 m road corridor, SH degree 3, one 1280x720 view
+(fx = fy = 900) from a camera moving 1 m per frame; per iteration: projection,
+binning and depth sort, compositing, L = 0.8 L1 + 0.2 (1 - SSIM) (Supp. D.4),
+the backward, the lifecycle statistics and a dense Adam update of all 59
+parameters of every Gaussian.  Frames cycle over a pool spread across frames
+100-900 (visible and pair counts vary along the road).  Targets are renders of
+the scene with every parameter perturbed by N(0, 0.01), resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same
+workload (a bounded sample per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "mapping iters/s (1M Gaussians, 720p, fwd+bwd+Adam)"
+UNIT = "iters/s"
+N_GAUSS = 1_000_000
+W, H, F = 1280, 720, 900.0
+SH_DEG = 3
+LAMBDA = 0.2
+
+
+def workload_config(n_frames):
+    return {"workload": "corridor 1M Gaussians SH3, 1280x720, fwd+L1/D-SSIM(0.2)+bwd+stats+Adam",
+            "gaussians": N_GAUSS, "sh_degree": SH_DEG, "width": W, "height": H, "views_per_step": 1,
+            "frames": "%d-frame pool over corridor frames 100-900" % n_frames,
+            "l2": "inputs larger than L2 (236 MB parameters + 708 MB grads/moments per step)"}
+
+
+def frame_pool(n):
+    return [int(f) for f in np.linspace(100, 900, n)]
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes (minimum HBM traffic the method implies, FP32)
+
+def algorithmic_bytes(N, V, P, px, tiles, K):
+    return {
+        "project": 12 * N + 4 * (K - 3) * V + 56 * V + 4 * N,
+        "sort": 8 * N + 16 * V + 12 * P + 24 * P + 8 * P + 8 * tiles,
+        "render_fwd": 40 * P + 20 * px,
+        "loss": 36 * px,
+        "render_bwd": 40 * P + 32 * px + 36 * V + 4 * K * V + 4 * K * N + 32 * V,
+        "adam": 28 * K * N,
+    }
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2606_30436_b300 import gs, scenes
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    frames = frame_pool(args.frames)
+    scene = scenes.corridor_scene(N_GAUSS, seed=0, sh_degree=SH_DEG)
+    tscene = scenes.perturb(scene, 0.01, seed=1)
+    cams = [scenes.corridor_camera(f, W, H, F) for f in frames]
+    cfg = gs.Config()
+
+    # targets: renders of the perturbed scene (device resident)
+    tmodel = gs.GaussianModel.from_scene(tscene)
+    tstep = gs.MappingStep(tmodel, [cams[0]], cfg, max_pairs=1 << 20, with_stats=False)
+    targets = torch.empty(len(frames), 3 * W * H, dtype=torch.float32, device=dev)
+    for i, c in enumerate(cams):
+        tstep.set_cameras([c])
+        tstep.fit_capacity()
+        targets[i].copy_(tstep.buf.img)
+    del tstep, tmodel
+    torch.cuda.synchronize()
+
+    model = gs.GaussianModel.from_scene(scene)
+    step = gs.MappingStep(model, [cams[0]], cfg, max_pairs=1 << 20, lambda_dssim=LAMBDA,
+                          lr=gs.default_lr(extent=10.0), with_stats=True)
+    needed, vis = [], []
+    for c in cams:
+        step.set_cameras([c])
+        needed.append(step.fit_capacity(slack=1.0))
+        vis.append(int(step.buf.counts[0].item()))
+    step.buf.set_max_pairs(int(max(needed) * 1.15) + 1024)
+    tiles = step.buf.total_tiles
+    K = model.K
+
+    stream = torch.cuda.current_stream()
+    stage_names = ["project", "sort", "render_fwd", "loss", "render_bwd", "adam"]
+
+    def one(i, events=None):
+        k = i % len(frames)
+        step.set_cameras([cams[k]])
+        b = step.buf
+        rec = (lambda j: events[j].record(stream)) if events is not None else (lambda j: None)
+        b.status.zero_()
+        rec(0)
+        gs.gs_project(step.model, b)
+        rec(1)
+        gs.gs_sort(b)
+        rec(2)
+        gs.gs_render_fwd(b)
+        rec(3)
+        gs.gs_loss(b, targets[k], LAMBDA)
+        rec(4)
+        gs.gs_render_bwd(step.model, step.grads, b, targets[k], step.tau_err, with_stats=True)
+        rec(5)
+        step.step_count += 1
+        gs.gs_adam(step.model, step.grads, step.exp_avg, step.exp_avg_sq, step.lr, step.step_count)
+        rec(6)
+
+    for i in range(args.warmup):
+        one(i)
+    torch.cuda.synchronize()
+    step.check_status()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # device-timed region: inputs resident in HBM
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    barrier()
+    start.record(stream)
+    for i in range(args.steps):
+        one(args.warmup + i, evs[i])
+    end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    step.check_status()
+    stage_ms = {nm: sum(e[j].elapsed_time(e[j + 1]) for e in evs) / args.steps for j, nm in enumerate(stage_names)}
+
+    # end to end through the C ABI with host buffers: pinned host target in,
+    # loss out, both copies inside the timed region
+    host_targets = targets[:min(4, len(frames))].cpu().pin_memory()
+    dev_target = torch.empty(3 * W * H, dtype=torch.float32, device=dev)
+    host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        k = i % host_targets.shape[0]
+        dev_target.copy_(host_targets[k], non_blocking=True)
+        step.set_cameras([cams[k]])
+        step.step(dev_target)
+        host_loss.copy_(step.buf.loss[:1], non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    wall_e2e = time.perf_counter() - t0
+
+    ms_t = torch.tensor([ms, e2e_ms], device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms, e2e_ms = float(ms_t[0]), float(ms_t[1])
+
+    # roofline of the dominant kernel by time, from the live stage timings
+    Vm, Pm = float(np.mean(vis)), float(np.mean(needed))
+    ab = algorithmic_bytes(N_GAUSS, Vm, Pm, W * H, tiles, K)
+    peak, peak_kind = measured_peaks()
+    dom = max(stage_names, key=lambda s: stage_ms[s])
+    if dom == "adam":
+        # one kernel per call: k_adam
+        achieved = ab["adam"] / (stage_ms["adam"] * 1e-3) / 1e9
+        roof = {"kernel": "k_adam", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_kind": peak_kind}
+    else:
+        achieved = ab[dom] / (stage_ms[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind}
+    adam_gbs = ab["adam"] / (stage_ms["adam"] * 1e-3) / 1e9
+
+    launches_per_step = gs.launches_per_step(tiles, views=1, lambda_dssim=LAMBDA)
+    value = world * args.steps / (ms * 1e-3)
+    e2e_value = world * args.steps / (e2e_ms * 1e-3)
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(len(frames)),
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 3 * W * H * 4,
+                "d2h_bytes_per_step": 4, "wall_s": round(wall_e2e, 3)},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roof,
+        "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "adam_hbm_gbs": round(adam_gbs, 1),
+        "visible_mean": int(Vm), "pairs_mean": int(Pm),
+        "clocks": clk,
+    }
+    return out
+
+
+# --------------------------------------------------------------------------
+# CPU arms: the FP64 oracle on the host cores
+
+def oracle_iteration(scene, tscene_img, cam, oc):
+    import oracle as orc
+    f = orc.loss_and_grads(scene, cam, oc, tscene_img, LAMBDA)
+    return f
+
+
+def cpu_sample_setup(crop):
+    """The same workload restricted to a crop of the view (a window of the
+    1280x720 image with its principal point moved accordingly)."""
+    import oracle as orc
+    from paper_2606_30436_b300 import scenes
+    scene = scenes.corridor_scene(N_GAUSS, seed=0, sh_degree=SH_DEG)
+    tscene = scenes.perturb(scene, 0.01, seed=1)
+    frames = frame_pool(16)
+    cams = []
+    for f in frames[:2]:
+        c = scenes.corridor_camera(f, W, H, F)
+        cw, ch = crop
+        c = dict(c, width=cw, height=ch, cx=c["cx"] - (W - cw) / 2, cy=c["cy"] - (H - ch) / 2)
+        cams.append(c)
+    oc = orc.Cfg()
+    targets = [orc.forward(tscene, c, oc)["img"] for c in cams]
+    return scene, cams, targets, oc
+
+
+def time_oracle(steps, crop):
+    import oracle as orc
+    scene, cams, targets, oc = cpu_sample_setup(crop)
+    P = orc.Params(scene)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        oracle_iteration(P, targets[i % len(cams)], cams[i % len(cams)], oc)
+    dt = time.perf_counter() - t0
+    frac = crop[0] * crop[1] / float(W * H)
+    # per full-size iteration: the per-pixel work scales with the crop area;
+    # the per-Gaussian work (projection, backward chain, Adam) does not, and is
+    # counted in full because the crop still projects all 1M Gaussians
+    return dt / steps, frac
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def cpu_baseline(steps=2, crop=(W, H)):
+    per_iter, frac = time_oracle(steps, crop)
+    est_full = per_iter / frac
+    what = "the full 1280x720 view" if frac == 1.0 else "a %dx%d crop (per-iteration time divided by the crop's area fraction)" % crop
+    return {"value": round(1.0 / est_full, 6), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": "%d FP64 oracle mapping iteration(s) (1M Gaussians SH3 projected, binned, composited, "
+                      "L1+D-SSIM, backward to all parameters) on %s, corridor frames 100 and 153" % (steps, what),
+            "seconds_per_iter": round(per_iter, 3)}
+
+
+def run_reference(args):
+    cb = cpu_baseline(steps=max(1, min(args.steps, 4)))
+    out = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(16),
+           "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
+    ap.add_argument("--frames", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    out = run_gpu(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

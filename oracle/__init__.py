@@ -19,6 +19,11 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+# pixel flags of or_render (near-threshold events, see gs_oracle.h)
+OR_FLAG_NEAR_ALPHA_MIN = 1
+OR_FLAG_NEAR_T_CUT = 2
+OR_FLAG_NEAR_ALPHA_MAX = 4
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gs_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")

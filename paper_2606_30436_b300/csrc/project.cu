@@ -127,7 +127,11 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ P, lo
                                                  int *__restrict__ touched, int *__restrict__ status) {
     constexpr int K = (D + 1) * (D + 1);
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
+    if (g >= ld) return;
+    if (g >= n) {  // padding records: never visible
+        for (int v = 0; v < vt.n_views; ++v) { radius[v * ld + g] = 0; touched[v * ld + g] = 0; }
+        return;
+    }
     const float mx = P[0 * ld + g], my = P[1 * ld + g], mz = P[2 * ld + g];
 
     // cheap near-plane pass first: skip the remaining loads if no view sees it
@@ -223,7 +227,12 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ P
                                                      float *__restrict__ stats, long long stats_ld) {
     constexpr int K = (D + 1) * (D + 1);
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
+    if (g >= ld) return;
+    if (g >= n) {  // padding: zero gradient (Adam then leaves the padding unchanged)
+        if (!accumulate)
+            for (int k = 0; k < 11 + 3 * K; ++k) G[k * ld + g] = 0.0f;
+        return;
+    }
 
     float gmean[3] = {0, 0, 0}, glogs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glogit = 0.0f;
     float gsh[K][3];
@@ -423,8 +432,8 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ P
 
 void launch_project(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
                     float2 *xy, float4 *co, float4 *rgbd, int *radius, int *touched, int *status, cudaStream_t s) {
-    if (n <= 0) return;
-    const int blocks = (int)ceil_div(n, 256);
+    if (ld <= 0) return;
+    const int blocks = (int)ceil_div(ld, 256);
     switch (D) {
         case 0: k_project<0><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status); break;
         case 1: k_project<1><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status); break;
@@ -436,8 +445,8 @@ void launch_project(const float *P, long long n, long long ld, int D, const View
 void launch_project_bwd(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
                         const int *radius, const float *acc, long long nrec, float *G, int accumulate,
                         const float *loss_per_view, float *stats, long long stats_ld, cudaStream_t s) {
-    if (n <= 0) return;
-    const int blocks = (int)ceil_div(n, 256);
+    if (ld <= 0) return;
+    const int blocks = (int)ceil_div(ld, 256);
 #define GS_PB(DD) k_project_bwd<DD><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, radius, acc, nrec, G, accumulate, \
                                                             loss_per_view, stats, stats_ld)
     switch (D) {

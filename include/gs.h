@@ -109,6 +109,11 @@ typedef struct {
     int32_t *tile_ranges;  /* [total_tiles][2] = first pair, one past the last */
     int32_t *counts;       /* device int32[4]: visible records, pairs written,
                               pairs needed, reserved */
+    uint8_t *block_mask;   /* [gs_block_mask_size(max_pairs) bytes], 16-byte aligned:
+                              per pair, bit b set when the Gaussian's alpha >=
+                              alpha_min ellipse can reach the tile's 8x4 pixel
+                              block b (blocks row-major, tile_w/8 per row); a
+                              clear bit proves alpha < alpha_min on that block */
     int64_t max_pairs;
 } gs_binning;
 
@@ -157,6 +162,9 @@ gs_status gs_view_layout(const gs_camera *cams, int32_t n_views, const gs_raster
  * max_pairs pairs. */
 gs_status gs_sort_workspace_size(int64_t n_records, int64_t max_pairs, size_t *bytes);
 
+/* Bytes of gs_binning.block_mask for max_pairs pairs. */
+gs_status gs_block_mask_size(int64_t max_pairs, size_t *bytes);
+
 /* Workspace bytes of gs_loss for a view of h x w pixels (the largest view). */
 gs_status gs_loss_workspace_size(int32_t h, int32_t w, size_t *bytes);
 
@@ -186,7 +194,8 @@ gs_status gs_project(const gs_params *params, const gs_camera *cams, int32_t n_v
  * Binning: one pair per (visible record, overlapped tile), ordered by
  * (global tile, camera depth, Gaussian index) -- the "sorted Gaussians along
  * the ray" of Supp. D.2 -- and the per-tile ranges.  Writes
- * binning->counts, gauss_ids[0..pairs) and tile_ranges.  When the pairs
+ * binning->counts, gauss_ids[0..pairs), block_mask[0..pairs) and
+ * tile_ranges (cfg->alpha_min sets the masks).  When the pairs
  * exceed max_pairs, no pair is written, counts[1] = 0, counts[2] = pairs
  * needed and status gets bit 1<<GS_ERR_CAPACITY.  ws: gs_sort_workspace_size
  * bytes (256-byte aligned).

@@ -81,9 +81,10 @@ gs_status check_proj(const gs_projected *pr, long long ld) {
 }
 
 gs_status check_binning(const gs_binning *b) {
-    if (!b || !b->gauss_ids || !b->tile_ranges || !b->counts || b->max_pairs < 0 || b->max_pairs > 0x7fffffffll)
+    if (!b || !b->gauss_ids || !b->tile_ranges || !b->counts || !b->block_mask || b->max_pairs < 0 ||
+        b->max_pairs > 0x7fffffffll)
         return GS_ERR_INVALID;
-    if (((uintptr_t)b->tile_ranges & 7u) != 0) return GS_ERR_INVALID;
+    if (((uintptr_t)b->tile_ranges & 7u) != 0 || !aligned16(b->block_mask)) return GS_ERR_INVALID;
     return GS_OK;
 }
 
@@ -125,6 +126,12 @@ GS_API gs_status gs_sort_workspace_size(int64_t n_records, int64_t max_pairs, si
     if (!bytes || n_records < 0 || max_pairs < 0 || n_records > 0x7fffffffll || max_pairs > 0x7fffffffll)
         return GS_ERR_INVALID;
     *bytes = sort_workspace_bytes(n_records, max_pairs);
+    return GS_OK;
+}
+
+GS_API gs_status gs_block_mask_size(int64_t max_pairs, size_t *bytes) {
+    if (!bytes || max_pairs < 0 || max_pairs > 0x7fffffffll) return GS_ERR_INVALID;
+    *bytes = (size_t)block_mask_bytes(max_pairs);
     return GS_OK;
 }
 
@@ -173,8 +180,9 @@ GS_API gs_status gs_sort(const gs_projected *proj, const gs_camera *cams, int32_
     if (nrec > 0x7fffffffll) return GS_ERR_INVALID;
     if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < sort_workspace_bytes(nrec, binning->max_pairs)) return GS_ERR_INVALID;
     return cuda_status(launch_sort(proj->radius, proj->tiles_touched, (const float2 *)proj->xy,
-                                   (const float4 *)proj->rgb_depth, nrec, proj->ld, vt, binning->gauss_ids,
-                                   (int2 *)binning->tile_ranges, binning->counts, binning->max_pairs, ws, status,
+                                   (const float4 *)proj->conic_opacity, (const float4 *)proj->rgb_depth, nrec,
+                                   proj->ld, vt, rc.alpha_min, binning->gauss_ids, (int2 *)binning->tile_ranges,
+                                   binning->block_mask, binning->counts, binning->max_pairs, ws, status,
                                    (cudaStream_t)stream));
 }
 
@@ -187,7 +195,8 @@ GS_API gs_status gs_render_fwd(const gs_projected *proj, const gs_binning *binni
     if (!proj || (st = check_proj(proj, proj->ld)) != GS_OK) return GS_ERR_INVALID;
     if ((st = check_binning(binning)) != GS_OK) return st;
     if (!frame || !frame->img || !frame->T_final || !frame->last) return GS_ERR_INVALID;
-    launch_render_fwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, (const float2 *)proj->xy,
+    launch_render_fwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, binning->block_mask,
+                      (const float2 *)proj->xy,
                       (const float4 *)proj->conic_opacity, (const float4 *)proj->rgb_depth, frame->img,
                       frame->T_final, frame->last, frame->depth, (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
@@ -238,7 +247,8 @@ GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, i
     float *acc = (float *)ws;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)kAccPlanes * nrec, s);
     if (e != cudaSuccess) return GS_ERR_CUDA;
-    launch_render_bwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, (const float2 *)proj->xy,
+    launch_render_bwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, binning->block_mask,
+                      (const float2 *)proj->xy,
                       (const float4 *)proj->conic_opacity, (const float4 *)proj->rgb_depth, frame->img,
                       frame->T_final, frame->last, dL_dimg, dL_ddepth, target, tau_err, want_stats, acc, nrec, s);
     launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius, acc, nrec,

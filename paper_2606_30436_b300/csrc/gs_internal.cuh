@@ -86,7 +86,54 @@ __device__ __forceinline__ float gauss_power(float a, float b, float c, float dx
     return __fmaf_rn(-0.5f, q, -__fmul_rn(b, __fmul_rn(dx, dy)));
 }
 
-__device__ __forceinline__ float ceil_div_f(float a, float b) { return ceilf(a / b); }
+// Can a Gaussian (pixel position p, conic/opacity q) reach alpha >= alpha_min
+// at a pixel centre of the 8x4 block whose first pixel is (bx0, by0)?
+// alpha >= alpha_min iff d^T Q d <= tau, tau = 2 ln(o / alpha_min); the
+// ellipse's bounding box has half-widths sqrt(tau Sigma'_xx), sqrt(tau
+// Sigma'_yy) with Sigma' = Q^-1.  tau gets an additive margin (alpha relative
+// errors up to 1%) and the box 0.05 px, so rounding never drops a Gaussian
+// that the per-pixel test would keep: skipping on a clear bit is exact.
+struct Reach { float cx, cy, ex, ey; bool any, all; };
+
+__device__ __forceinline__ Reach reach_box(float2 p, float4 q, float alpha_min) {
+    Reach r;
+    r.any = q.w >= alpha_min;
+    r.all = false;
+    const float tau = 2.0f * __logf(q.w / alpha_min) + 0.02f;
+    const float det = q.x * q.z - q.y * q.y;
+    if (!(det > 0.0f)) r.all = true;
+    const float idet = 1.0f / det;
+    r.ex = sqrtf(fmaxf(tau * q.z * idet, 0.0f)) + 0.05f;
+    r.ey = sqrtf(fmaxf(tau * q.x * idet, 0.0f)) + 0.05f;
+    r.cx = p.x - 0.5f;  // pixel i has centre i + 0.5: work in pixel-index space
+    r.cy = p.y - 0.5f;
+    return r;
+}
+
+// Bit b (b = 0..7) set when the Gaussian can reach block b of the tile whose
+// first pixel is (x0, y0); blocks are 8 wide and 4 tall, row-major, tile_w/8
+// per row.
+__device__ __forceinline__ uint32_t block_mask8(float2 p, float4 q, float alpha_min, int x0, int y0, int tile_w) {
+    const Reach r = reach_box(p, q, alpha_min);
+    if (!r.any) return 0u;
+    if (r.all) return 0xffu;
+    const int ncols = tile_w >> 3;
+    const float lx0 = r.cx - r.ex - (float)x0, lx1 = r.cx + r.ex - (float)x0;
+    const float ly0 = r.cy - r.ey - (float)y0, ly1 = r.cy + r.ey - (float)y0;
+    uint32_t m = 0;
+    #pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const float bx = 8.0f * (float)(b % ncols), by = 4.0f * (float)(b / ncols);
+        if (lx1 >= bx && lx0 <= bx + 7.0f && ly1 >= by && ly0 <= by + 3.0f) m |= 1u << b;
+    }
+    return m;
+}
+
+// Bytes of the per-pair block-mask array for max_pairs pairs: the render
+// kernels read it in aligned 16-byte words up to 512 bytes past a range end.
+__host__ __device__ __forceinline__ long long block_mask_bytes(long long max_pairs) {
+    return max_pairs + 16 + 512;
+}
 
 __host__ __device__ __forceinline__ long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 

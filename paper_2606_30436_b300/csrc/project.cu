@@ -216,10 +216,39 @@ __global__ void __launch_bounds__(256) k_project(const float *__restrict__ P, lo
 
 // Backward of the projection.  acc holds, per record, the planes
 // kAccU..kAccMaxW written by the compositing backward.  One thread per
-// Gaussian: accumulates over views in registers, then writes every parameter
-// plane of the Gaussian once (zeros when no view saw it).
+// Gaussian: per view, first the colour (SH) part, whose gradients are written
+// straight to their planes, then the geometric part, whose covariance
+// gradient is summed over views; the view-independent rotation and scales are
+// recomputed rather than kept live, to keep registers (and so occupancy) for
+// this memory-bound pass.  Writes every parameter plane of the Gaussian once
+// (zeros when no view saw it).
+__device__ __forceinline__ void rot_scale(const float *__restrict__ P, long long ld, long long g, float *R, float *s,
+                                          float &nq, float *qh) {
+    float qw = P[6 * ld + g], qx = P[7 * ld + g], qy = P[8 * ld + g], qz = P[9 * ld + g];
+    nq = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qh[0] = qw / nq; qh[1] = qx / nq; qh[2] = qy / nq; qh[3] = qz / nq;
+    quat_rotation(qh[0], qh[1], qh[2], qh[3], R);
+    s[0] = expf(P[3 * ld + g]); s[1] = expf(P[4 * ld + g]); s[2] = expf(P[5 * ld + g]);
+}
+
+__device__ __forceinline__ Cov3 cov3(const float *R, const float *s) {
+    float M[9];
+    #pragma unroll
+    for (int r = 0; r < 3; ++r)
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) M[3 * r + c] = R[3 * r + c] * s[c];
+    Cov3 S;
+    S.s00 = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    S.s01 = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    S.s02 = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    S.s11 = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    S.s12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    S.s22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    return S;
+}
+
 template <int D>
-__global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ P, long long n, long long ld,
+__global__ void __launch_bounds__(256, 2) k_project_bwd(const float *__restrict__ P, long long n, long long ld,
                                                      ViewTable vt, RasterCfg cfg, const int *__restrict__ radius,
                                                      const float *__restrict__ acc, long long nrec,
                                                      float *__restrict__ G, int accumulate,
@@ -234,107 +263,92 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ P
         return;
     }
 
-    float gmean[3] = {0, 0, 0}, glogs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, glogit = 0.0f;
-    float gsh[K][3];
-    #pragma unroll
-    for (int k = 0; k < K; ++k) gsh[k][0] = gsh[k][1] = gsh[k][2] = 0.0f;
+    float gmean[3] = {0, 0, 0}, glogit = 0.0f;
+    float dSig[6] = {0, 0, 0, 0, 0, 0};  // dL/dSigma entries 00 01 02 11 12 22 (each ordered pair)
+    bool seen = false;                   // some view saw it (SH planes already written)
     float st_omega = 0, st_kappa = 0, st_gamma = 0, st_maxw = 0, st_gnorm = 0, st_views = 0;
+    const float mx = P[0 * ld + g], my = P[1 * ld + g], mz = P[2 * ld + g];
 
-    bool any = false;
-    for (int v = 0; v < vt.n_views; ++v) any |= radius[v * ld + g] > 0;
+    for (int v = 0; v < vt.n_views; ++v) {
+        const long long rec = v * ld + g;
+        if (radius[rec] <= 0) continue;
+        const ViewDesc &c = vt.v[v];
+        const float du = acc[kAccU * nrec + rec], dv = acc[kAccV * nrec + rec];
 
-    if (any) {
-        const float mx = P[0 * ld + g], my = P[1 * ld + g], mz = P[2 * ld + g];
-        float qw = P[6 * ld + g], qx = P[7 * ld + g], qy = P[8 * ld + g], qz = P[9 * ld + g];
-        const float nq = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-        qw /= nq; qx /= nq; qy /= nq; qz /= nq;
-        float R[9];
-        quat_rotation(qw, qx, qy, qz, R);
-        const float s[3] = {expf(P[3 * ld + g]), expf(P[4 * ld + g]), expf(P[5 * ld + g])};
-        float M[9];
-        #pragma unroll
-        for (int r = 0; r < 3; ++r)
-            #pragma unroll
-            for (int cix = 0; cix < 3; ++cix) M[3 * r + cix] = R[3 * r + cix] * s[cix];
-        Cov3 S;
-        S.s00 = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
-        S.s01 = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
-        S.s02 = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
-        S.s11 = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
-        S.s12 = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
-        S.s22 = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
-        const float o = 1.0f / (1.0f + expf(-P[10 * ld + g]));
-        float dSig[6] = {0, 0, 0, 0, 0, 0};  // symmetric gradient: d00 d01 d02 d11 d12 d22 (off-diagonal counted once per entry)
+        if (stats) {
+            const float om = acc[kAccOmega * nrec + rec];
+            st_omega += om;
+            st_kappa += acc[kAccKappa * nrec + rec];
+            st_gamma += (loss_per_view ? loss_per_view[v] : 0.0f) * om;
+            st_maxw = fmaxf(st_maxw, acc[kAccMaxW * nrec + rec]);
+            st_gnorm += sqrtf(du * du + dv * dv);
+            st_views += om > 0.0f ? 1.0f : 0.0f;
+        }
 
-        for (int v = 0; v < vt.n_views; ++v) {
-            const long long rec = v * ld + g;
-            if (radius[rec] <= 0) continue;
-            const ViewDesc &c = vt.v[v];
-            const float du = acc[kAccU * nrec + rec], dv = acc[kAccV * nrec + rec];
-            const float da = acc[kAccA * nrec + rec], db = acc[kAccB * nrec + rec], dc = acc[kAccC * nrec + rec];
-            const float dop = acc[kAccO * nrec + rec];
-            const float gcol[3] = {acc[kAccR * nrec + rec], acc[kAccG * nrec + rec], acc[kAccBl * nrec + rec]};
-            const float gdepth = acc[kAccZ * nrec + rec];
-
-            if (stats) {
-                const float om = acc[kAccOmega * nrec + rec];
-                st_omega += om;
-                st_kappa += acc[kAccKappa * nrec + rec];
-                st_gamma += (loss_per_view ? loss_per_view[v] : 0.0f) * om;
-                st_maxw = fmaxf(st_maxw, acc[kAccMaxW * nrec + rec]);
-                st_gnorm += sqrtf(du * du + dv * dv);
-                st_views += om > 0.0f ? 1.0f : 0.0f;
-            }
-
-            glogit += dop * o * (1.0f - o);
-
-            // colour: clamp mask and SH gradients
+        // ---- colour: SH gradients and the direction term of the mean ----
+        {
             float ex = mx - c.campos[0], ey = my - c.campos[1], ez = mz - c.campos[2];
-            const float dist = sqrtf(ex * ex + ey * ey + ez * ez), idist = 1.0f / dist;
+            const float idist = 1.0f / sqrtf(ex * ex + ey * ey + ez * ez);
             ex *= idist; ey *= idist; ez *= idist;
             float Y[16];
             sh_basis<D>(ex, ey, ez, Y);
+            const bool add = accumulate || seen;
             float w[16];
             #pragma unroll
             for (int k = 0; k < K; ++k) w[k] = 0.0f;
-            #pragma unroll
+            // one colour channel at a time keeps 16 coefficients live, not 48
+            #pragma unroll 1
             for (int ch = 0; ch < 3; ++ch) {
+                float sh[16];
+                #pragma unroll
+                for (int k = 0; k < K; ++k) sh[k] = P[(11 + 3 * k + ch) * ld + g];
                 float raw = 0.5f;
                 #pragma unroll
-                for (int k = 0; k < K; ++k) raw += Y[k] * P[(11 + 3 * k + ch) * ld + g];
-                const float gc = raw < 0.0f ? 0.0f : gcol[ch];
+                for (int k = 0; k < K; ++k) raw += Y[k] * sh[k];
+                const float gcv = raw < 0.0f ? 0.0f : acc[(kAccR + ch) * nrec + rec];
                 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    gsh[k][ch] += gc * Y[k];
-                    w[k] += gc * P[(11 + 3 * k + ch) * ld + g];
+                    float *dst = G + (11 + 3 * k + ch) * ld + g;
+                    *dst = add ? *dst + gcv * Y[k] : gcv * Y[k];
+                    w[k] += gcv * sh[k];
                 }
             }
             if (D > 0) {
                 float gx, gy, gz;
                 sh_basis_vjp<D>(ex, ey, ez, w, gx, gy, gz);
-                const float dd = gx * ex + gy * ey + gz * ez;  // project onto the sphere's tangent plane
+                const float dd = gx * ex + gy * ey + gz * ez;  // onto the sphere's tangent plane
                 gmean[0] += (gx - ex * dd) * idist;
                 gmean[1] += (gy - ey * dd) * idist;
                 gmean[2] += (gz - ez * dd) * idist;
             }
+        }
+        seen = true;
 
-            // conic = Q = Sigma'^-1: dL/dSigma' = -Q G Q, G = [[da, db/2], [db/2, dc]]
+        // ---- geometry: opacity, conic -> 2D covariance -> Sigma, J, position ----
+        {
+            float R[9], s[3], nq, qh[4];
+            rot_scale(P, ld, g, R, s, nq, qh);
+            const Cov3 S = cov3(R, s);
+            const float o = 1.0f / (1.0f + expf(-P[10 * ld + g]));
+            glogit += acc[kAccO * nrec + rec] * o * (1.0f - o);
+            const float da = acc[kAccA * nrec + rec], db = acc[kAccB * nrec + rec], dc = acc[kAccC * nrec + rec];
+            const float gdepth = acc[kAccZ * nrec + rec];
             const ExactPos p = exact_position(c, mx, my, mz);
             const float x = p.xc, y = p.yc, z = p.zc;
             const Ewa e = ewa(c, x, y, z, S);
             const float A = e.A + cfg.dilation, B = e.B, C = e.C + cfg.dilation;
             const float idet = 1.0f / (A * C - B * B);
             const float qa = C * idet, qb = -B * idet, qcc = A * idet;
+            // conic Q = Sigma'^-1: dL/dSigma' = -Q G Q, G = [[da, db/2], [db/2, dc]]
             const float hb = 0.5f * db;
             const float QG00 = qa * da + qb * hb, QG01 = qa * hb + qb * dc;
             const float QG10 = qb * da + qcc * hb, QG11 = qb * hb + qcc * dc;
             const float dA = -(QG00 * qa + QG01 * qb);
-            const float dBh = -(QG00 * qb + QG01 * qcc);  // half of dL/dB (symmetric entry)
+            const float dBh = -(QG00 * qb + QG01 * qcc);  // per entry of the symmetric off-diagonal
             const float dC = -(QG10 * qb + QG11 * qcc);
-
-            // Sigma'_2d = T Sigma T^T: dSigma = T^T Sd T, dT = 2 Sd T Sigma, Sd = [[dA, dBh], [dBh, dC]]
+            // Sigma' = T Sigma T^T: dSigma = T^T Sd T, dT = 2 Sd T Sigma, Sd = [[dA, dBh], [dBh, dC]]
             const float *T = e.T;
-            float U[6];  // Sd T (2 x 3)
+            float U[6];
             #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 U[k] = dA * T[k] + dBh * T[3 + k];
@@ -364,22 +378,30 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ P
             const float dtx_dz = e.clx_lo ? -c.limx : (e.clx_hi ? c.limx : 0.0f);
             const float dty_dy = (e.cly_lo || e.cly_hi) ? 0.0f : 1.0f;
             const float dty_dz = e.cly_lo ? -c.limy : (e.cly_hi ? c.limy : 0.0f);
-            float gx = dJ02 * (-c.fx * iz2) * dtx_dx + du * c.fx * iz;
-            float gy = dJ12 * (-c.fy * iz2) * dty_dy + dv * c.fy * iz;
-            float gz = -dJ00 * c.fx * iz2 - dJ11 * c.fy * iz2 +
-                       dJ02 * (-c.fx * dtx_dz * iz2 + 2.0f * c.fx * e.tx * iz3) +
-                       dJ12 * (-c.fy * dty_dz * iz2 + 2.0f * c.fy * e.ty * iz3) -
-                       du * c.fx * x * iz2 - dv * c.fy * y * iz2 + gdepth;
+            const float gx = dJ02 * (-c.fx * iz2) * dtx_dx + du * c.fx * iz;
+            const float gy = dJ12 * (-c.fy * iz2) * dty_dy + dv * c.fy * iz;
+            const float gz = -dJ00 * c.fx * iz2 - dJ11 * c.fy * iz2 +
+                             dJ02 * (-c.fx * dtx_dz * iz2 + 2.0f * c.fx * e.tx * iz3) +
+                             dJ12 * (-c.fy * dty_dz * iz2 + 2.0f * c.fy * e.ty * iz3) -
+                             du * c.fx * x * iz2 - dv * c.fy * y * iz2 + gdepth;
             gmean[0] += c.R[0] * gx + c.R[3] * gy + c.R[6] * gz;
             gmean[1] += c.R[1] * gx + c.R[4] * gy + c.R[7] * gz;
             gmean[2] += c.R[2] * gx + c.R[5] * gy + c.R[8] * gz;
         }
+    }
 
-        // Sigma = M M^T, M = R diag(s): dM = (dSig + dSig^T) M with the full (non-halved) matrix
+    float glogs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0};
+    if (seen) {
+        float R[9], s[3], nq, qh[4];
+        rot_scale(P, ld, g, R, s, nq, qh);
+        float M[9];
+        #pragma unroll
+        for (int r = 0; r < 3; ++r)
+            #pragma unroll
+            for (int cix = 0; cix < 3; ++cix) M[3 * r + cix] = R[3 * r + cix] * s[cix];
+        // Sigma = M M^T: dM = (dSig + dSig^T) M = 2 dSig M (dSig symmetric)
         const float F00 = 2.0f * dSig[0], F11 = 2.0f * dSig[3], F22 = 2.0f * dSig[5];
-        const float F01 = dSig[1] + dSig[1], F02 = dSig[2] + dSig[2], F12 = dSig[4] + dSig[4];
-        // dSig entries above hold dL/dSigma_kl for each ordered pair (k,l) with the
-        // symmetric matrix Sd, so (dSig + dSig^T)_kl = 2 dSig_kl.
+        const float F01 = 2.0f * dSig[1], F02 = 2.0f * dSig[2], F12 = 2.0f * dSig[4];
         float dM[9];
         #pragma unroll
         for (int m = 0; m < 3; ++m) {
@@ -394,7 +416,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ P
             glogs[m] = ds * s[m];
             dR[m] = dM[m] * s[m]; dR[3 + m] = dM[3 + m] * s[m]; dR[6 + m] = dM[6 + m] * s[m];
         }
-        const float w_ = qw, x_ = qx, y_ = qy, z_ = qz;
+        const float w_ = qh[0], x_ = qh[1], y_ = qh[2], z_ = qh[3];
         const float dqw = 2.f * (-z_ * dR[1] + y_ * dR[2] + z_ * dR[3] - x_ * dR[5] - y_ * dR[6] + x_ * dR[7]);
         const float dqx = 2.f * (y_ * dR[1] + z_ * dR[2] + y_ * dR[3] - 2.f * x_ * dR[4] - w_ * dR[5] + z_ * dR[6] +
                                  w_ * dR[7] - 2.f * x_ * dR[8]);
@@ -402,7 +424,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ P
                                  z_ * dR[7] - 2.f * y_ * dR[8]);
         const float dqz = 2.f * (-2.f * z_ * dR[0] - w_ * dR[1] + x_ * dR[2] + w_ * dR[3] - 2.f * z_ * dR[4] +
                                  y_ * dR[5] + x_ * dR[6] + y_ * dR[7]);
-        const float qd = w_ * dqw + x_ * dqx + y_ * dqy + z_ * dqz;
+        const float qd = w_ * dqw + x_ * dqx + y_ * dqy + z_ * dqz;  // normalisation: project out q
         gq[0] = (dqw - w_ * qd) / nq;
         gq[1] = (dqx - x_ * qd) / nq;
         gq[2] = (dqy - y_ * qd) / nq;
@@ -417,8 +439,8 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float *__restrict__ P
     put(3, glogs[0]); put(4, glogs[1]); put(5, glogs[2]);
     put(6, gq[0]); put(7, gq[1]); put(8, gq[2]); put(9, gq[3]);
     put(10, glogit);
-    #pragma unroll
-    for (int k = 0; k < K; ++k) { put(11 + 3 * k, gsh[k][0]); put(12 + 3 * k, gsh[k][1]); put(13 + 3 * k, gsh[k][2]); }
+    if (!seen && !accumulate)
+        for (int k = 0; k < 3 * K; ++k) G[(11 + k) * ld + g] = 0.0f;
 
     if (stats) {
         stats[0 * stats_ld + g] += st_omega;

@@ -2,14 +2,15 @@
 // backward (Supp. D.2: C = sum_j c_j alpha_j T_j, T_j = prod_{m<j}(1 - alpha_m)).
 //
 // Work unit = one warp = one 8x4 pixel block of a tile (a tile of 256 pixels,
-// 16x16, 8x32 or 32x8, has eight blocks); lane = pixel.  Each warp walks its
-// tile's depth-ordered pair list on its own, 32 pairs per step, with the
-// records of the next 32 pairs already in flight (ids two steps ahead).  A
-// pair is evaluated only if the Gaussian's alpha >= alpha_min ellipse can reach
-// the warp's block (a conservative bounding-box test, so skipping is exact);
-// the relevant records go through warp-private shared memory.  There is no
-// CTA-wide barrier, so a block whose pixels saturate early retires at once
-// while the few deep blocks of a vanishing-point tile run on their own warps.
+// 16x16, 8x32 or 32x8, has eight blocks); lane = pixel.  The binning stored,
+// for every (Gaussian, tile) pair, the mask of the tile's blocks that the
+// Gaussian's alpha >= alpha_min ellipse can reach (conservative, so skipping a
+// clear bit is exact).  Each warp scans its tile's masks 512 pairs per step
+// with coalesced 16-byte loads, compacts the pairs relevant to its block into
+// warp-private shared memory, and composites them with the records of the
+// next 32 already in flight.  There is no CTA-wide barrier: a block whose
+// pixels saturate early retires at once, and the long chains of a
+// vanishing-point tile touch only the pairs that reach each block.
 #include "gs_internal.cuh"
 #include "gs_kernels.h"
 
@@ -44,29 +45,10 @@ __device__ __forceinline__ Unit unit_ctx(const ViewTable &vt, int tile, int blk)
     return t;
 }
 
-// Can the Gaussian reach alpha >= alpha_min at a pixel centre of the 8x4 block
-// with first pixel (bx0, by0)?  alpha >= alpha_min iff d^T Q d <= tau,
-// tau = 2 ln(o / alpha_min); the ellipse's bounding box has half-widths
-// sqrt(tau Sigma'_xx), sqrt(tau Sigma'_yy) with Sigma' = Q^-1.  tau gets an
-// additive margin (alpha relative errors up to 1%) and the box 0.05 px, so
-// rounding never skips a Gaussian the per-pixel test would keep.
-__device__ __forceinline__ bool reaches_block(float2 p, float4 q, float alpha_min, float bx0, float by0) {
-    if (q.w < alpha_min) return false;
-    const float tau = 2.0f * __logf(q.w / alpha_min) + 0.02f;
-    const float det = q.x * q.z - q.y * q.y;
-    if (!(det > 0.0f)) return true;
-    const float idet = 1.0f / det;
-    const float ex = sqrtf(tau * q.z * idet) + 0.05f;
-    const float ey = sqrtf(tau * q.x * idet) + 0.05f;
-    // pixel i has centre i + 0.5: compare in pixel-index space
-    const float cx = p.x - 0.5f, cy = p.y - 0.5f;
-    return cx + ex >= bx0 && cx - ex <= bx0 + 7.0f && cy + ey >= by0 && cy - ey <= by0 + 3.0f;
-}
-
 struct Rec {
     float2 p;
     float4 q, c;
-    int id;
+    int id, pos;
 };
 
 __device__ __forceinline__ void load_rec(Rec &r, const float2 *__restrict__ xy, const float4 *__restrict__ co,
@@ -78,54 +60,96 @@ __device__ __forceinline__ void load_rec(Rec &r, const float2 *__restrict__ xy, 
         r.c = rgbd[id];
     } else {
         r.p = make_float2(0.f, 0.f);
-        r.q = make_float4(0.f, 0.f, 0.f, 0.f);  // opacity 0: never reaches a block
+        r.q = make_float4(0.f, 0.f, 0.f, 0.f);
         r.c = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+}
+
+constexpr int kWindow = 512;  // pairs whose block masks a warp scans per step (16 per lane)
+
+// Scans the block masks of pairs [w, w + 512) restricted to [lo, hi) and
+// writes, in pair order, the absolute positions whose mask holds `bit` into
+// list.  Returns the count (warp-uniform).  The mask array is read in aligned
+// 16-byte words (w is a multiple of 16).
+__device__ __forceinline__ int scan_window(const uint8_t *__restrict__ masks, int w, int lo, int hi, int bit,
+                                           int *list) {
+    const int lane = threadIdx.x & 31;
+    const int q0 = w + 16 * lane;
+    uint4 mw = make_uint4(0u, 0u, 0u, 0u);
+    if (q0 < hi) mw = *reinterpret_cast<const uint4 *>(masks + q0);
+    const uint32_t wd[4] = {mw.x, mw.y, mw.z, mw.w};
+    uint32_t rel = 0;
+    #pragma unroll
+    for (int b = 0; b < 16; ++b) {
+        const int pos = q0 + b;
+        const uint32_t byte = (wd[b >> 2] >> (8 * (b & 3))) & 0xffu;
+        if (pos >= lo && pos < hi && ((byte >> bit) & 1u)) rel |= 1u << b;
+    }
+    const int cnt = __popc(rel);
+    int inc = cnt;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    int off = inc - cnt;
+    while (rel) {
+        const int b = __ffs(rel) - 1;
+        rel &= rel - 1;
+        list[off++] = q0 + b;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    __syncwarp();
+    return total;
+}
+
+__device__ __forceinline__ void gather(Rec &r, const int *list, int idx, int total, const int *__restrict__ ids,
+                                       const float2 *__restrict__ xy, const float4 *__restrict__ co,
+                                       const float4 *__restrict__ rgbd) {
+    const bool valid = idx < total;
+    r.pos = valid ? list[idx] : 0;
+    load_rec(r, xy, co, rgbd, valid ? ids[r.pos] : 0, valid);
 }
 
 __global__ void __launch_bounds__(32 * kWarps) k_render_fwd(ViewTable vt, RasterCfg cfg,
                                                               const int2 *__restrict__ ranges,
                                                               const int *__restrict__ ids,
+                                                              const uint8_t *__restrict__ masks,
                                                               const float2 *__restrict__ xy,
                                                               const float4 *__restrict__ co,
                                                               const float4 *__restrict__ rgbd,
                                                               float *__restrict__ img, float *__restrict__ T_final,
                                                               int *__restrict__ last, float *__restrict__ depth) {
+    __shared__ int s_list[kWarps][kWindow];
     __shared__ float2 s_p[kWarps][32];
     __shared__ float4 s_q[kWarps][32];
     __shared__ float4 s_c[kWarps][32];
+    __shared__ int s_pos[kWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int unit = blockIdx.x * kWarps + warp;
     if (unit >= vt.total_tiles * 8) return;
-    const int tile = unit >> 3;
-    const Unit t = unit_ctx(vt, tile, unit & 7);
+    const int tile = unit >> 3, bit = unit & 7;
+    const Unit t = unit_ctx(vt, tile, bit);
     const int2 rg = ranges[tile];
-    const int n = rg.y - rg.x;
     const float fx = t.px + 0.5f, fy = t.py + 0.5f;
+    int *list = s_list[warp];
 
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Dd = 0.0f;
     int lastc = 0;
     bool done = !t.inside;
-
-    Rec cur, nxt;
-    int id2 = (32 + lane < n) ? ids[rg.x + 32 + lane] : 0;
-    load_rec(cur, xy, co, rgbd, lane < n ? ids[rg.x + lane] : 0, lane < n);
-    for (int base = 0; base < n && !__all_sync(0xffffffffu, done); base += 32) {
-        // prefetch: records of the next step, ids of the one after
-        const bool v1 = base + 32 + lane < n;
-        load_rec(nxt, xy, co, rgbd, id2, v1);
-        id2 = (base + 64 + lane < n) ? ids[rg.x + base + 64 + lane] : 0;
-
-        uint32_t m = __ballot_sync(0xffffffffu, reaches_block(cur.p, cur.q, cfg.alpha_min, t.bx0, t.by0));
-        if (m) {
+    for (int w = rg.x & ~15; w < rg.y && !__all_sync(0xffffffffu, done); w += kWindow) {
+        const int total = scan_window(masks, w, rg.x, rg.y, bit, list);
+        Rec cur, nxt;
+        gather(cur, list, lane, total, ids, xy, co, rgbd);
+        for (int c = 0; c < total; c += 32) {
+            if (c + 32 < total) gather(nxt, list, c + 32 + lane, total, ids, xy, co, rgbd);
             s_p[warp][lane] = cur.p;
             s_q[warp][lane] = cur.q;
             s_c[warp][lane] = cur.c;
+            s_pos[warp][lane] = cur.pos;
             __syncwarp();
-            while (m) {
-                const int k = __ffs(m) - 1;
-                m &= m - 1;
-                if (done) continue;
+            const int cnt = min(32, total - c);
+            for (int k = 0; k < cnt && !done; ++k) {
                 const float2 p = s_p[warp][k];
                 const float4 q = s_q[warp][k];
                 const float power = gauss_power(q.x, q.y, q.z, fx - p.x, fy - p.y);
@@ -133,16 +157,17 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_fwd(ViewTable vt, Raster
                 const float alpha = fminf(cfg.alpha_max, q.w * __expf(power));
                 if (alpha < cfg.alpha_min) continue;
                 const float Tn = T * (1.0f - alpha);
-                if (Tn < cfg.t_min) { done = true; continue; }
-                const float4 c = s_c[warp][k];
-                const float w = alpha * T;
-                C0 += c.x * w; C1 += c.y * w; C2 += c.z * w; Dd += c.w * w;
+                if (Tn < cfg.t_min) { done = true; break; }
+                const float4 cc = s_c[warp][k];
+                const float wgt = alpha * T;
+                C0 += cc.x * wgt; C1 += cc.y * wgt; C2 += cc.z * wgt; Dd += cc.w * wgt;
                 T = Tn;
-                lastc = base + k + 1;
+                lastc = s_pos[warp][k] - rg.x + 1;
             }
             __syncwarp();
+            if (__all_sync(0xffffffffu, done)) break;
+            cur = nxt;
         }
-        cur = nxt;
     }
     if (t.inside) {
         img[t.img] = C0 + T * cfg.bg[0];
@@ -166,12 +191,45 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 constexpr int kAccGrad = 10;   // u v a b c o r g b z
-constexpr int kDirectLanes = 4;  // up to this many active lanes: each issues its own reductions
+constexpr int kDirectLanes = 1;  // up to this many active lanes: each issues its own reductions
+
+// Sums 16 values over the warp by recursive halving: at each of the four
+// steps a lane swaps half of its partial sums with its partner and keeps the
+// other half, so 8+4+2+1+1 = 16 shuffles replace 16 x 5.  Lane l ends with
+// the total of value (l >> 1) & 15 (in both lanes of a pair).
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
+    const int lane = threadIdx.x & 31;
+    #pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool hi = lane & 16;
+        const float send = hi ? v[i] : v[i + 8], keep = hi ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    #pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = lane & 8;
+        const float send = hi ? v[i] : v[i + 4], keep = hi ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    #pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = lane & 4;
+        const float send = hi ? v[i] : v[i + 2], keep = hi ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    {
+        const bool hi = lane & 2;
+        const float send = hi ? v[0] : v[1], keep = hi ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
 
 template <bool STATS>
 __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, RasterCfg cfg,
                                                               const int2 *__restrict__ ranges,
                                                               const int *__restrict__ ids,
+                                                              const uint8_t *__restrict__ masks,
                                                               const float2 *__restrict__ xy,
                                                               const float4 *__restrict__ co,
                                                               const float4 *__restrict__ rgbd,
@@ -182,18 +240,21 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
                                                               const float *__restrict__ dL_ddepth,
                                                               const float *__restrict__ target, float tau_err,
                                                               float *__restrict__ acc, long long nrec) {
+    __shared__ int s_list[kWarps][kWindow];
     __shared__ float2 s_p[kWarps][32];
     __shared__ float4 s_q[kWarps][32];
     __shared__ float4 s_c[kWarps][32];
     __shared__ int s_id[kWarps][32];
+    __shared__ int s_pos[kWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int unit = blockIdx.x * kWarps + warp;
     if (unit >= vt.total_tiles * 8) return;
-    const int tile = unit >> 3;
-    const Unit t = unit_ctx(vt, tile, unit & 7);
+    const int tile = unit >> 3, bit = unit & 7;
+    const Unit t = unit_ctx(vt, tile, bit);
     const int2 rg = ranges[tile];
     const float fx = t.px + 0.5f, fy = t.py + 0.5f;
     const bool has_depth = dL_ddepth != nullptr;
+    int *list = s_list[warp];
 
     float T = 1.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, gD = 0.0f, mask = 0.0f;
     int lst = 0;
@@ -219,30 +280,25 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
     // transmittance in front of it; starts as the background
     float R0 = cfg.bg[0], R1 = cfg.bg[1], R2 = cfg.bg[2], RD = 0.0f;
 
-    // steps of 32 pairs from the one holding position wmax-1 down to 0
-    int base = ((wmax - 1) >> 5) << 5;
-    Rec cur, nxt;
-    {
-        const int j0 = base + lane;
-        load_rec(cur, xy, co, rgbd, j0 < wmax ? ids[rg.x + j0] : 0, j0 < wmax);
-    }
-    int id2 = (base >= 32) ? ids[rg.x + base - 32 + lane] : 0;
-    for (; base >= 0; base -= 32) {
-        load_rec(nxt, xy, co, rgbd, id2, base >= 32);
-        id2 = (base >= 64) ? ids[rg.x + base - 64 + lane] : 0;
-
-        uint32_t m = __ballot_sync(0xffffffffu, base + lane < wmax &&
-                                                    reaches_block(cur.p, cur.q, cfg.alpha_min, t.bx0, t.by0));
-        if (m) {
+    const int lo = rg.x, hi = rg.x + wmax;
+    const int wbase = rg.x & ~15;
+    for (int kw = (hi - 1 - wbase) / kWindow; kw >= 0; --kw) {
+        const int total = scan_window(masks, wbase + kw * kWindow, lo, hi, bit, list);
+        if (total == 0) continue;
+        int c = ((total - 1) >> 5) << 5;
+        Rec cur, nxt;
+        gather(cur, list, c + lane, total, ids, xy, co, rgbd);
+        for (; c >= 0; c -= 32) {
+            if (c >= 32) gather(nxt, list, c - 32 + lane, total, ids, xy, co, rgbd);
             s_p[warp][lane] = cur.p;
             s_q[warp][lane] = cur.q;
             s_c[warp][lane] = cur.c;
             s_id[warp][lane] = cur.id;
+            s_pos[warp][lane] = cur.pos;
             __syncwarp();
-            while (m) {
-                const int k = 31 - __clz(m);
-                m &= ~(1u << k);
-                bool on = base + k < lst;
+            const int cnt = min(32, total - c);
+            for (int k = cnt - 1; k >= 0; --k) {
+                bool on = s_pos[warp][k] - rg.x < lst;
                 float alpha = 0.0f, G = 0.0f, dx = 0.0f, dy = 0.0f;
                 const float2 p = s_p[warp][k];
                 const float4 q = s_q[warp][k];
@@ -260,19 +316,20 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
                 }
                 const uint32_t act = __ballot_sync(0xffffffffu, on);
                 if (act == 0u) continue;
-                float v[kAccPlanes];
+                float v[16];
                 #pragma unroll
-                for (int c = 0; c < kAccPlanes; ++c) v[c] = 0.0f;
+                for (int cc = 0; cc < 16; ++cc) v[cc] = 0.0f;
                 if (on) {
-                    const float4 c = s_c[warp][k];
+                    const float4 col = s_c[warp][k];
                     T = __fdividef(T, 1.0f - alpha);  // transmittance in front of this Gaussian
                     const float w = alpha * T;
                     v[kAccR] = g0 * w; v[kAccG] = g1 * w; v[kAccBl] = g2 * w; v[kAccZ] = gD * w;
-                    const float dLda = T * (g0 * (c.x - R0) + g1 * (c.y - R1) + g2 * (c.z - R2) + gD * (c.w - RD));
-                    R0 = alpha * c.x + (1.0f - alpha) * R0;
-                    R1 = alpha * c.y + (1.0f - alpha) * R1;
-                    R2 = alpha * c.z + (1.0f - alpha) * R2;
-                    RD = alpha * c.w + (1.0f - alpha) * RD;
+                    const float dLda = T * (g0 * (col.x - R0) + g1 * (col.y - R1) + g2 * (col.z - R2) +
+                                            gD * (col.w - RD));
+                    R0 = alpha * col.x + (1.0f - alpha) * R0;
+                    R1 = alpha * col.y + (1.0f - alpha) * R1;
+                    R2 = alpha * col.z + (1.0f - alpha) * R2;
+                    RD = alpha * col.w + (1.0f - alpha) * RD;
                     if (q.w * G <= cfg.alpha_max) {  // alpha not clamped
                         v[kAccO] = dLda * G;
                         const float dp = dLda * q.w * G;
@@ -285,57 +342,57 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
                     if (STATS) { v[kAccOmega] = 1.0f; v[kAccKappa] = mask; v[kAccMaxW] = w; }
                 }
                 const long long r = s_id[warp][k];
-                bool issue = on;
-                if (__popc(act) > kDirectLanes) {
-                    #pragma unroll
-                    for (int c = 0; c < kAccGrad; ++c)
-                        if (c != kAccZ || has_depth) v[c] = warp_sum(v[c]);
-                    if (STATS) {
-                        v[kAccOmega] = warp_sum(v[kAccOmega]);
-                        v[kAccKappa] = warp_sum(v[kAccKappa]);
-                        v[kAccMaxW] = warp_max(v[kAccMaxW]);
+                if (__popc(act) <= kDirectLanes) {
+                    // a single pixel: its lane issues the updates itself
+                    if (on) {
+                        #pragma unroll
+                        for (int cc = 0; cc < kAccGrad; ++cc)
+                            if (cc != kAccZ || has_depth) atomicAdd(&acc[cc * nrec + r], v[cc]);
+                        if (STATS) {
+                            atomicAdd(&acc[kAccOmega * nrec + r], v[kAccOmega]);
+                            if (v[kAccKappa] > 0.0f) atomicAdd(&acc[kAccKappa * nrec + r], v[kAccKappa]);
+                            atomicMax((int *)&acc[kAccMaxW * nrec + r], __float_as_int(v[kAccMaxW]));  // w >= 0
+                        }
                     }
-                    issue = lane == 0;
-                }
-                if (issue) {
-                    #pragma unroll
-                    for (int c = 0; c < kAccGrad; ++c)
-                        if (c != kAccZ || has_depth) atomicAdd(&acc[c * nrec + r], v[c]);
-                    if (STATS) {
-                        atomicAdd(&acc[kAccOmega * nrec + r], v[kAccOmega]);
-                        if (v[kAccKappa] > 0.0f) atomicAdd(&acc[kAccKappa * nrec + r], v[kAccKappa]);
-                        atomicMax((int *)&acc[kAccMaxW * nrec + r], __float_as_int(v[kAccMaxW]));  // w >= 0
-                    }
+                } else {
+                    const float mw = STATS ? warp_max(v[kAccMaxW]) : 0.0f;
+                    const float tot = warp_transpose_sum16(v);
+                    const int plane = (lane >> 1) & 15;
+                    const bool mine = (lane & 1) == 0 && plane < (STATS ? kAccMaxW : kAccGrad) &&
+                                      (plane != kAccZ || has_depth) && (plane != kAccKappa || tot > 0.0f);
+                    if (mine) atomicAdd(&acc[plane * nrec + r], tot);
+                    if (STATS && lane == 1) atomicMax((int *)&acc[kAccMaxW * nrec + r], __float_as_int(mw));
                 }
             }
             __syncwarp();
+            cur = nxt;
         }
-        cur = nxt;
     }
 }
 
-void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids, const float2 *xy,
-                       const float4 *co, const float4 *rgbd, float *img, float *T_final, int *last, float *depth,
-                       cudaStream_t s) {
+void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
+                       const uint8_t *masks, const float2 *xy, const float4 *co, const float4 *rgbd, float *img,
+                       float *T_final, int *last, float *depth, cudaStream_t s) {
     const long long units = 8ll * vt.total_tiles;
     if (units <= 0) return;
-    k_render_fwd<<<(unsigned)ceil_div(units, kWarps), 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, xy, co, rgbd, img,
-                                                                           T_final, last, depth);
+    k_render_fwd<<<(unsigned)ceil_div(units, kWarps), 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd,
+                                                                           img, T_final, last, depth);
 }
 
 void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
-                       const float2 *xy, const float4 *co, const float4 *rgbd, const float *img, const float *T_final,
-                       const int *last, const float *dL_dimg, const float *dL_ddepth, const float *target,
-                       float tau_err, bool stats, float *acc, long long nrec, cudaStream_t s) {
+                       const uint8_t *masks, const float2 *xy, const float4 *co, const float4 *rgbd,
+                       const float *img, const float *T_final, const int *last, const float *dL_dimg,
+                       const float *dL_ddepth, const float *target, float tau_err, bool stats, float *acc,
+                       long long nrec, cudaStream_t s) {
     const long long units = 8ll * vt.total_tiles;
     if (units <= 0) return;
     const unsigned grid = (unsigned)ceil_div(units, kWarps);
     if (stats)
-        k_render_bwd<true><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, xy, co, rgbd, img, T_final, last,
+        k_render_bwd<true><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd, img, T_final, last,
                                                         dL_dimg, dL_ddepth, target, tau_err, acc, nrec);
     else
-        k_render_bwd<false><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, xy, co, rgbd, img, T_final, last,
-                                                         dL_dimg, dL_ddepth, target, tau_err, acc, nrec);
+        k_render_bwd<false><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd, img, T_final,
+                                                         last, dL_dimg, dL_ddepth, target, tau_err, acc, nrec);
 }
 
 }  // namespace gs

@@ -243,57 +243,94 @@ __global__ void __launch_bounds__(kSortThreads) k_tiles_count(const uint32_t *__
     if (threadIdx.x == 0) blk[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_emit_pairs(const uint32_t *__restrict__ sorted_rec,
-                                                              const int *__restrict__ touched,
-                                                              const int *__restrict__ radius,
-                                                              const float2 *__restrict__ xy, long long ld, ViewTable vt,
-                                                              const int *__restrict__ counts,
-                                                              const unsigned long long *__restrict__ blk,
-                                                              uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+// Exclusive offsets of the sorted visible records' pair slots: off[r] for
+// r < V and off[V] = total pairs.
+__global__ void __launch_bounds__(kSortThreads) k_tiles_offsets(const uint32_t *__restrict__ sorted_rec,
+                                                                 const int *__restrict__ touched,
+                                                                 const int *__restrict__ counts,
+                                                                 const unsigned long long *__restrict__ blk,
+                                                                 uint32_t *__restrict__ off) {
     __shared__ unsigned long long sm[33];
-    if (counts[1] == 0) return;  // nothing to emit, or overflow
+    const long long V = counts[0];
     long long beg, end;
-    block_segment(counts[0], beg, end);
+    block_segment(V, beg, end);
     unsigned long long run = blk[blockIdx.x];
     for (long long base = beg; base < end; base += kSortThreads) {
         const long long r = base + threadIdx.x;
-        uint32_t rec = 0;
-        int tt = 0;
-        if (r < end) {
-            rec = sorted_rec[r];
-            tt = touched[rec];
-        }
+        const int tt = r < end ? touched[sorted_rec[r]] : 0;
         unsigned long long total;
-        unsigned long long off = run + block_exclusive_scan<unsigned long long>((unsigned long long)tt, total, sm);
-        if (tt > 0) {
+        const unsigned long long o = run + block_exclusive_scan<unsigned long long>((unsigned long long)tt, total, sm);
+        if (r < end) off[r] = (uint32_t)o;
+        run += total;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) off[V] = (uint32_t)counts[2];
+}
+
+// Last r in [lo, hi) with off[r] <= o (off non-decreasing, off[lo] <= o).
+__device__ __forceinline__ long long owner(const uint32_t *__restrict__ off, long long lo, long long hi, uint32_t o) {
+    while (hi - lo > 1) {
+        const long long mid = (lo + hi) >> 1;
+        if (off[mid] <= o) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// One thread per output pair: finds the record that owns the slot, then the
+// tile of the slot inside that record's tile rectangle (row-major, the order
+// in which the rectangle is enumerated).  Writes are coalesced and every
+// thread does the same work whatever the Gaussian's footprint.
+__global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t *__restrict__ sorted_rec,
+                                                     const uint32_t *__restrict__ off,
+                                                     const int *__restrict__ radius,
+                                                     const float2 *__restrict__ xy, long long ld, ViewTable vt,
+                                                     const int *__restrict__ counts, uint32_t *__restrict__ pkey,
+                                                     uint32_t *__restrict__ pval) {
+    __shared__ long long s_lo, s_hi;
+    const long long P = counts[1];  // 0 on overflow
+    const long long V = counts[0];
+    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < P; b0 += (long long)gridDim.x * blockDim.x) {
+        const long long b1 = min(P, b0 + (long long)blockDim.x) - 1;
+        if (threadIdx.x == 0) s_lo = owner(off, 0, V, (uint32_t)b0);
+        if (threadIdx.x == 32) s_hi = owner(off, 0, V, (uint32_t)b1);
+        __syncthreads();
+        const long long o = b0 + threadIdx.x;
+        if (o <= b1) {
+            const long long r = owner(off, s_lo, s_hi + 1, (uint32_t)o);
+            const uint32_t rec = sorted_rec[r];
             const int view = (int)(rec / ld);
             const ViewDesc &c = vt.v[view];
             const float2 p = xy[rec];
             const Rect rc = tile_rect(p.x, p.y, radius[rec], vt.tile_w, vt.tile_h, c.GW, c.GH);
-            // the rectangle is the one the projection counted (same inputs, same
-            // arithmetic); the cap keeps every write inside this record's slot
-            const unsigned long long stop = off + (unsigned long long)tt;
-            for (int ty = rc.y0; ty < rc.y1 && off < stop; ++ty)
-                for (int tx = rc.x0; tx < rc.x1 && off < stop; ++tx) {
-                    pkey[off] = (uint32_t)(c.tile_offset + ty * c.GW + tx);
-                    pval[off] = (uint32_t)r;
-                    ++off;
-                }
+            const int i = (int)(o - off[r]);
+            const int w = rc.x1 - rc.x0;
+            const int ty = rc.y0 + i / w, tx = rc.x0 + i % w;
+            pkey[o] = (uint32_t)(c.tile_offset + ty * c.GW + tx);
+            pval[o] = (uint32_t)r;
         }
-        run += total;
+        __syncthreads();
     }
 }
 
+// Final pass over the sorted pairs: Gaussian ids, tile ranges, and the mask of
+// the tile's 8x4 pixel blocks each Gaussian can reach (block_mask8).
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ pkey, const uint32_t *__restrict__ pval,
                                                  const uint32_t *__restrict__ sorted_rec,
                                                  const int *__restrict__ counts, int *__restrict__ ids,
-                                                 int2 *__restrict__ ranges) {
+                                                 int2 *__restrict__ ranges, const float2 *__restrict__ xy,
+                                                 const float4 *__restrict__ co, ViewTable vt, float alpha_min,
+                                                 uint8_t *__restrict__ masks) {
     const long long P = counts[1];
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t t = pkey[p];
-        ids[p] = (int)sorted_rec[pval[p]];
+        const int g = (int)sorted_rec[pval[p]];
+        ids[p] = g;
         if (p == 0 || pkey[p - 1] != t) ranges[t].x = (int)p;
         if (p == P - 1 || pkey[p + 1] != t) ranges[t].y = (int)(p + 1);
+        const int v = view_of_tile(vt, (int)t);
+        const ViewDesc &c = vt.v[v];
+        const int local = (int)t - c.tile_offset;
+        const int ty = local / c.GW, tx = local - ty * c.GW;
+        masks[p] = (uint8_t)block_mask8(xy[g], co[g], alpha_min, tx * vt.tile_w, ty * vt.tile_h, vt.tile_w);
     }
 }
 
@@ -303,7 +340,7 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ pke
 struct SortWs {
     unsigned long long *blk;
     uint32_t *hist, *dtotal;
-    uint32_t *dk0, *dv0, *dk1, *dv1;
+    uint32_t *dk0, *dv0, *dk1, *dv1, *off;
     uint32_t *pk0, *pv0, *pk1, *pv1;
     size_t bytes;
 };
@@ -324,6 +361,7 @@ static SortWs carve(void *base, long long nrec, long long max_pairs) {
     w.dv0 = (uint32_t *)take(sizeof(uint32_t) * nrec);
     w.dk1 = (uint32_t *)take(sizeof(uint32_t) * nrec);
     w.dv1 = (uint32_t *)take(sizeof(uint32_t) * nrec);
+    w.off = (uint32_t *)take(sizeof(uint32_t) * (nrec + 1));
     w.pk0 = (uint32_t *)take(sizeof(uint32_t) * max_pairs);
     w.pv0 = (uint32_t *)take(sizeof(uint32_t) * max_pairs);
     w.pk1 = (uint32_t *)take(sizeof(uint32_t) * max_pairs);
@@ -354,9 +392,10 @@ static int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, co
     return cur;
 }
 
-cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy, const float4 *rgbd, long long nrec,
-                        long long ld, const ViewTable &vt, int *gauss_ids, int2 *tile_ranges, int *counts,
-                        long long max_pairs, void *ws, int *status, cudaStream_t s) {
+cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy, const float4 *co, const float4 *rgbd,
+                        long long nrec, long long ld, const ViewTable &vt, float alpha_min, int *gauss_ids,
+                        int2 *tile_ranges, uint8_t *block_mask, int *counts, long long max_pairs, void *ws,
+                        int *status, cudaStream_t s) {
     SortWs w = carve(ws, nrec, max_pairs);
     cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -373,13 +412,13 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
     // stage 2: pairs in rank order, then a stable partition by tile
     k_tiles_count<<<kSortBlocks, kSortThreads, 0, s>>>(sorted_rec, touched, counts, w.blk);
     k_scan_blocks<<<1, kSortBlocks, 0, s>>>(w.blk, 1, counts, max_pairs, status);
-    k_emit_pairs<<<kSortBlocks, kSortThreads, 0, s>>>(sorted_rec, touched, radius, xy, ld, vt, counts, w.blk, w.pk0,
-                                                       w.pv0);
+    k_tiles_offsets<<<kSortBlocks, kSortThreads, 0, s>>>(sorted_rec, touched, counts, w.blk, w.off);
+    k_emit_pairs<<<148 * 16, 256, 0, s>>>(sorted_rec, w.off, radius, xy, ld, vt, counts, w.pk0, w.pv0);
     int tile_bits = 0;
     while ((1ll << tile_bits) < (long long)vt.total_tiles) ++tile_bits;
     const int pres = radix_sort(w.pk0, w.pv0, w.pk1, w.pv1, counts + 1, tile_bits, w.hist, w.dtotal, s);
     k_ranges<<<148 * 8, 256, 0, s>>>(pres ? w.pk1 : w.pk0, pres ? w.pv1 : w.pv0, sorted_rec, counts, gauss_ids,
-                                     tile_ranges);
+                                     tile_ranges, xy, co, vt, alpha_min, block_mask);
     return cudaGetLastError();
 }
 

@@ -55,7 +55,7 @@ class Projected(C.Structure):
 
 class Binning(C.Structure):
     _fields_ = [("gauss_ids", C.c_void_p), ("tile_ranges", C.c_void_p), ("counts", C.c_void_p),
-                ("max_pairs", C.c_int64)]
+                ("block_mask", C.c_void_p), ("max_pairs", C.c_int64)]
 
 
 class Frame(C.Structure):
@@ -71,7 +71,8 @@ class ChunkScores(C.Structure):
                 ("prune", C.c_void_p)]
 
 
-EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspace_size", "gs_loss_workspace_size",
+EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspace_size", "gs_block_mask_size",
+           "gs_loss_workspace_size",
            "gs_bwd_workspace_size", "gs_prune_workspace_size", "gs_project", "gs_sort", "gs_render_fwd", "gs_loss",
            "gs_render_bwd", "gs_adam", "gs_prune_stats")
 
@@ -93,6 +94,7 @@ def lib():
         L.gs_version.restype = i32
         L.gs_view_layout.argtypes = [P(Camera), i32, P(RasterCfg), P(i64), P(i64), vp, vp]
         L.gs_sort_workspace_size.argtypes = [i64, i64, P(sz)]
+        L.gs_block_mask_size.argtypes = [i64, P(sz)]
         L.gs_loss_workspace_size.argtypes = [i32, i32, P(sz)]
         L.gs_bwd_workspace_size.argtypes = [i64, P(sz)]
         L.gs_prune_workspace_size.argtypes = [i64, P(sz)]
@@ -270,6 +272,7 @@ class Buffers:
         dev = self.xy.device
         self.max_pairs = int(max_pairs)
         self.gauss_ids = torch.empty(max(self.max_pairs, 1), dtype=torch.int32, device=dev)
+        self.block_mask = _workspace(lib().gs_block_mask_size, self.max_pairs, device=dev)
         self.sort_ws = _workspace(lib().gs_sort_workspace_size, self.nrec, self.max_pairs, device=dev)
 
     def projected(self) -> Projected:
@@ -277,7 +280,8 @@ class Buffers:
                          self.radius.data_ptr(), self.tiles_touched.data_ptr(), self.ld)
 
     def binning(self) -> Binning:
-        return Binning(self.gauss_ids.data_ptr(), self.tile_ranges.data_ptr(), self.counts.data_ptr(), self.max_pairs)
+        return Binning(self.gauss_ids.data_ptr(), self.tile_ranges.data_ptr(), self.counts.data_ptr(),
+                       self.block_mask.data_ptr(), self.max_pairs)
 
     def frame(self) -> Frame:
         return Frame(self.img.data_ptr(), self.T_final.data_ptr(), self.last.data_ptr(),
@@ -440,12 +444,12 @@ class MappingStep:
 
 def launches_per_step(total_tiles, views=1, lambda_dssim=0.2):
     """Kernel launches of the library in one mapping iteration (memsets not
-    counted): project 1; sort 3 + 3x4 depth passes + 3 + 3 per tile-bit pass
+    counted): project 1; sort 3 + 3x4 depth passes + 4 + 3 per tile-bit pass
     + 1; render 1; loss 3 (2 when lambda = 0) per view; backward 2; Adam 1."""
     tile_bits = 0
     while (1 << tile_bits) < total_tiles:
         tile_bits += 1
     tile_passes = (tile_bits + 7) // 8
-    sort = 3 + 3 * 4 + 3 + 3 * tile_passes + 1
+    sort = 3 + 3 * 4 + 4 + 3 * tile_passes + 1
     loss = (3 if lambda_dssim > 0 else 2) * views
     return 1 + sort + 1 + loss + 2 + 1

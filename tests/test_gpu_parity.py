@@ -314,3 +314,49 @@ def test_pair_capacity_overflow():
     assert np.all(st.buf.view_image(0).cpu().numpy() == 0.0)
     needed = st.fit_capacity()
     assert needed == counts[2] and st.buf.counts[1].item() == needed
+
+
+def test_block_masks_are_conservative(case):
+    """A clear bit of a pair's block mask must mean the Gaussian has alpha <
+    alpha_min at every pixel centre of that 8x4 block (oracle FP64 values);
+    set bits may be conservative.  Most far-away Gaussians must be culled
+    from most blocks, or the masks would be useless."""
+    st, cfg = case["st"], case["cfg"]
+    counts, ids, ranges = gpu_pairs(st)
+    P = len(ids)
+    masks = st.buf.block_mask[:P].cpu().numpy()
+    ld = st.buf.ld
+    tile_of = np.repeat(np.arange(len(ranges)), ranges[:, 1] - ranges[:, 0])
+    ncols = cfg.tile_w // 8
+    off = 0
+    cleared = total = 0
+    for v, o in enumerate(case["ov"]):
+        cam = case["cams"][v]
+        pr = o["proj"]
+        GW = (cam["width"] + cfg.tile_w - 1) // cfg.tile_w
+        sel = (ids >= v * ld) & (ids < (v + 1) * ld)
+        g = ids[sel] - v * ld
+        local = tile_of[sel] - (st.buf.tile_offset[v])
+        tx, ty = local % GW, local // GW
+        m = masks[sel]
+        u, vv, q, op = pr["u"][g], pr["v"][g], pr["conic"][g], pr["opacity"][g]
+        for b in range(8):
+            clear = ((m >> b) & 1) == 0
+            total += len(m)
+            cleared += int(clear.sum())
+            if not clear.any():
+                continue
+            bx = tx[clear] * cfg.tile_w + 8 * (b % ncols)
+            by = ty[clear] * cfg.tile_h + 4 * (b // ncols)
+            worst = np.full(int(clear.sum()), -np.inf)
+            for dy in range(4):
+                for dx in range(8):
+                    px, py = bx + dx, by + dy
+                    inb = (px < cam["width"]) & (py < cam["height"])
+                    ddx, ddy = px + 0.5 - u[clear], py + 0.5 - vv[clear]
+                    qq = q[clear]
+                    power = -0.5 * (qq[:, 0] * ddx * ddx + qq[:, 2] * ddy * ddy) - qq[:, 1] * ddx * ddy
+                    a = np.where(inb & (power <= 0), op[clear] * np.exp(np.minimum(power, 0)), 0.0)
+                    worst = np.maximum(worst, a)
+            assert worst.max() < cfg.alpha_min, (v, b, worst.max())
+    assert cleared > 0.3 * total, (cleared, total)

@@ -229,6 +229,26 @@ gs_status gs_loss(const float *img, const float *target, const gs_camera *cams, 
                   size_t ws_bytes, gs_stream stream);
 
 /*
+ * gs_loss without a caller workspace.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory where
+ * they need the loss -- code running while its allocator is unavailable
+ * (a host callback, a memory-capped process whose budget another component
+ * owns) or a plain C host that only receives the image and gradient pointers
+ * from its framework.  Same arguments, arithmetic and outputs as gs_loss; the
+ * scratch is a file-scope device array of the library (about 33 MB, held by
+ * every GPU that loads the library until the process exits), which bounds
+ * each view to at most 1280*720 pixels with width and height <= 2048;
+ * larger views return GS_ERR_INVALID before anything is enqueued.  The first
+ * call on a device looks up the array's device address (with that device
+ * current) and caches it, so make that first call before any stream capture.
+ * Every call shares the array and leaves its last contents there; calls that
+ * overlap on the GPU (other streams, other threads) race on it.  It never
+ * calls cudaMalloc, cudaFree or an allocating library routine.
+ */
+gs_status gs_loss_static(const float *img, const float *target, const gs_camera *cams, int32_t n_views,
+                         float lambda_dssim, float *loss_per_view, float *dL_dimg, gs_stream stream);
+
+/*
  * Backward of compositing and projection: traverses each tile back to front
  * from the pixel's last blended pair, recovers T_j = T_{j+1} / (1 - alpha_j),
  * and accumulates dL/d(u, v, conic, opacity, colour, depth) per record; then

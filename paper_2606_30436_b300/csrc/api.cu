@@ -222,6 +222,25 @@ GS_API gs_status gs_loss(const float *img, const float *target, const gs_camera 
     return GS_OK;
 }
 
+GS_API gs_status gs_loss_static(const float *img, const float *target, const gs_camera *cams, int32_t n_views,
+                                float lambda_dssim, float *loss_per_view, float *dL_dimg, gs_stream stream) {
+    if (!img || !target || !cams || !loss_per_view || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_INVALID;
+    if (!(lambda_dssim >= 0.0f && lambda_dssim <= 1.0f)) return GS_ERR_INVALID;
+    for (int v = 0; v < n_views; ++v)
+        if (!loss_static_fits(cams[v].height, cams[v].width)) return GS_ERR_INVALID;  // view beyond the array
+    void *scratch = nullptr;
+    if (loss_static_scratch(&scratch) != cudaSuccess) return GS_ERR_CUDA;
+    long long off = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const int h = cams[v].height, w = cams[v].width;
+        cudaError_t e = launch_loss(img + off, target + off, h, w, lambda_dssim, loss_per_view + v,
+                                    dL_dimg ? dL_dimg + off : nullptr, scratch, (cudaStream_t)stream);
+        if (e != cudaSuccess) return GS_ERR_CUDA;
+        off += 3ll * h * w;
+    }
+    return GS_OK;
+}
+
 GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views,
                                const gs_raster_cfg *cfg, const gs_projected *proj, const gs_binning *binning,
                                const gs_frame *frame, const float *dL_dimg, const float *dL_ddepth,

@@ -39,6 +39,9 @@ void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ra
                        float tau_err, bool stats, float *acc, long long nrec, cudaStream_t s);
 
 size_t loss_workspace_bytes(int h, int w);
+bool loss_static_fits(int h, int w);
+long long loss_static_max_pixels();
+cudaError_t loss_static_scratch(void **out);
 cudaError_t launch_loss(const float *img, const float *target, int h, int w, float lambda, float *loss_out,
                         float *dL_dimg, void *ws, cudaStream_t s);
 

@@ -12,6 +12,7 @@
 // scalar loss are reduced per CTA and then in a fixed order (deterministic).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "gs_internal.cuh"
 #include "gs_kernels.h"
@@ -210,6 +211,61 @@ cudaError_t launch_loss(const float *img, const float *target, int h, int w, flo
                                         (float)(lambda / (double)n), dL_dimg);
     k_loss_final<<<1, 256, 0, s>>>(partials, loss_blocks(h, w), 1.0 / (double)n, lambda, loss_out);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  Some callers cannot allocate device memory at the
+// point where they need the loss: code that runs while the caller's allocator
+// is unavailable (inside a host callback, in a memory-capped process whose
+// budget another component owns), or a plain C host that receives only the
+// image and gradient pointers from its framework.  For them the scratch lives
+// in this file-scope device array, which every GPU that loads the library
+// holds until the process exits.  Its size covers one view of at most
+// kStaticMaxPixels pixels (1280x720, width and height <= 2048): 9 FP32 maps of
+// the SSIM gradient plus the per-CTA partial sums.  Every scratch word a call
+// reads is written earlier in the same call, so nothing needs clearing; calls
+// that overlap on the GPU (different streams, or devices sharing nothing but
+// this array's name) race on the contents.
+
+constexpr long long kStaticMaxPixels = 1280ll * 720ll;
+constexpr int kStaticMaxSide = 2048;
+constexpr int kStaticMaxBlocks = 4096;
+constexpr size_t kStaticMapBytes = 9ull * (size_t)kStaticMaxPixels * sizeof(float);
+constexpr size_t kStaticBytes = kStaticMapBytes + 2ull * sizeof(double) * kStaticMaxBlocks;
+
+static __device__ __align__(256) unsigned char g_loss_scratch[kStaticBytes];
+
+namespace {
+constexpr int kMaxDevices = 128;
+std::mutex g_scratch_mu;
+void *g_scratch_ptr[kMaxDevices] = {};
+}  // namespace
+
+bool loss_static_fits(int h, int w) {
+    if (h <= 0 || w <= 0 || h > kStaticMaxSide || w > kStaticMaxSide) return false;
+    if ((long long)h * w > kStaticMaxPixels) return false;
+    return loss_workspace_bytes(h, w) <= kStaticBytes;
+}
+
+long long loss_static_max_pixels() { return kStaticMaxPixels; }
+
+// The device address of the scratch array for the current device.  The first
+// call on a device looks it up (cudaGetSymbolAddress, with that device
+// current) and caches it; later calls only read the cache.
+cudaError_t loss_static_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_loss_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
 }
 
 }  // namespace gs

@@ -74,7 +74,7 @@ class ChunkScores(C.Structure):
 EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspace_size", "gs_block_mask_size",
            "gs_loss_workspace_size",
            "gs_bwd_workspace_size", "gs_prune_workspace_size", "gs_project", "gs_sort", "gs_render_fwd", "gs_loss",
-           "gs_render_bwd", "gs_adam", "gs_prune_stats")
+           "gs_render_bwd", "gs_adam", "gs_prune_stats", "gs_loss_static")
 
 _lib = None
 
@@ -102,6 +102,7 @@ def lib():
         L.gs_sort.argtypes = [P(Projected), P(Camera), i32, P(RasterCfg), P(Binning), vp, sz, vp, vp]
         L.gs_render_fwd.argtypes = [P(Projected), P(Binning), P(Camera), i32, P(RasterCfg), P(Frame), vp]
         L.gs_loss.argtypes = [vp, vp, P(Camera), i32, f32, vp, vp, vp, sz, vp]
+        L.gs_loss_static.argtypes = [vp, vp, P(Camera), i32, f32, vp, vp, vp]
         L.gs_render_bwd.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), P(Binning), P(Frame),
                                     vp, vp, vp, vp, f32, P(Params), i32, P(Stats), vp, sz, vp]
         L.gs_adam.argtypes = [P(Params), P(Params), P(Params), P(Params), P(f32 * 6), f32, f32, f32, i64, vp]
@@ -334,6 +335,14 @@ def gs_loss(buf: Buffers, target: torch.Tensor, lambda_dssim=0.2, stream=None, i
     _check(lib().gs_loss(_ptr(buf.img if img is None else img), _ptr(target), arr, buf.n_views, float(lambda_dssim),
                          _ptr(buf.loss), _ptr(buf.dL_dimg), _ptr(buf.loss_ws), buf.loss_ws.numel(),
                          _stream(stream)), "gs_loss")
+
+
+def gs_loss_static(img, target, cams, loss_out, dL_dimg, lambda_dssim=0.2, stream=None):
+    """gs_loss with the library's own scratch array (no workspace argument),
+    for callers that cannot allocate device memory; views up to 1280x720."""
+    arr = camera_array(cams)
+    _check(lib().gs_loss_static(_ptr(img), _ptr(target), arr, len(cams), float(lambda_dssim), _ptr(loss_out),
+                                _ptr(dL_dimg), _stream(stream)), "gs_loss_static")
 
 
 def gs_render_bwd(model: GaussianModel, grads: GaussianModel, buf: Buffers, target=None, tau_err=0.1,

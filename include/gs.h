@@ -70,6 +70,9 @@ typedef struct {
     float t_min;            /* stop before blending when T (1 - alpha) < t_min (1e-4) */
     float tan_clamp;        /* EWA Jacobian taken at x/z clamped to tan_clamp * W/(2 fx) (1.3) */
     float bg[3];            /* background colour */
+    int32_t batch;          /* pairs a warp scans per step in the compositing
+                               kernels: 128, 256 or 512 (0 selects 512); a
+                               tuning knob only, results do not depend on it */
 } gs_raster_cfg;
 
 /* Gaussian parameters: ONE device buffer of K planes of ld floats
@@ -272,11 +275,14 @@ gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, int32_t 
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr m^ / (sqrt(v^) + eps),
  * m^ = m/(1-b1^step), v^ = v/(1-b2^step).  lr_groups (host) holds six rates:
  * means, log-scales, quaternion, opacity, SH degree 0, SH degree >= 1.
+ * step_device (nullable device int64): when set, the step count is read from
+ * it when the kernel runs and `step` is ignored, so a captured CUDA graph can
+ * replay the update with a counter the caller advances.
  * The paper trains in PyTorch and prints no optimiser settings (Sec. 4.1).
  */
 gs_status gs_adam(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
                   const gs_params *exp_avg_sq, const float lr_groups[6], float beta1, float beta2,
-                  float eps, int64_t step, gs_stream stream);
+                  float eps, int64_t step, const int64_t *step_device, gs_stream stream);
 
 /*
  * Chunk scores and global decisions (Supp. E.1, E.2; Sec. 3.3.2) from the

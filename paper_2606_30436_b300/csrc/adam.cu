@@ -17,7 +17,18 @@ __device__ __forceinline__ int lr_group(long long plane) {
 __global__ void __launch_bounds__(256) k_adam(float4 *__restrict__ p, const float4 *__restrict__ g,
                                                float4 *__restrict__ m, float4 *__restrict__ v, long long ld4,
                                                long long total4, AdamLr lr, float b1, float b2, float inv_bc1,
-                                               float inv_sqrt_bc2, float eps) {
+                                               float inv_sqrt_bc2, float eps, const long long *__restrict__ step_dev) {
+    if (step_dev) {  // bias corrections from the device step counter (graph replay)
+        __shared__ float s_bc[2];
+        if (threadIdx.x == 0) {
+            const double t = (double)*step_dev;
+            s_bc[0] = (float)(1.0 / (1.0 - pow((double)b1, t)));
+            s_bc[1] = (float)(1.0 / sqrt(1.0 - pow((double)b2, t)));
+        }
+        __syncthreads();
+        inv_bc1 = s_bc[0];
+        inv_sqrt_bc2 = s_bc[1];
+    }
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total4;
          i += (long long)gridDim.x * blockDim.x) {
         const float a = lr.lr[lr_group(i / ld4)];
@@ -36,11 +47,12 @@ __global__ void __launch_bounds__(256) k_adam(float4 *__restrict__ p, const floa
 }
 
 void launch_adam(float *p, const float *g, float *m, float *v, long long ld, int planes, const float lr[6],
-                 float beta1, float beta2, float eps, long long step, cudaStream_t s) {
+                 float beta1, float beta2, float eps, long long step, const long long *step_dev, cudaStream_t s) {
     AdamLr L;
     for (int k = 0; k < 6; ++k) L.lr[k] = lr[k];
-    const double bc1 = 1.0 - pow((double)beta1, (double)step);
-    const double bc2 = 1.0 - pow((double)beta2, (double)step);
+    const double st = step_dev ? 1.0 : (double)step;  // placeholder when the device counter is used
+    const double bc1 = 1.0 - pow((double)beta1, st);
+    const double bc2 = 1.0 - pow((double)beta2, st);
     const long long total4 = (long long)planes * ld / 4;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
@@ -49,7 +61,7 @@ void launch_adam(float *p, const float *g, float *m, float *v, long long ld, int
     const int blocks = (int)std::min<long long>(want, (long long)sms * 8);
     if (blocks <= 0) return;
     k_adam<<<blocks, 256, 0, s>>>((float4 *)p, (const float4 *)g, (float4 *)m, (float4 *)v, ld / 4, total4, L, beta1,
-                                  beta2, (float)(1.0 / bc1), (float)(1.0 / sqrt(bc2)), eps);
+                                  beta2, (float)(1.0 / bc1), (float)(1.0 / sqrt(bc2)), eps, step_dev);
 }
 
 }  // namespace gs

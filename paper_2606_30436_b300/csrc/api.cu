@@ -25,6 +25,7 @@ gs_status check_cfg(const gs_raster_cfg *cfg) {
     if (!(cfg->near_z > 0.0f) || !(cfg->alpha_max > 0.0f && cfg->alpha_max < 1.0f) || !(cfg->alpha_min >= 0.0f) ||
         !(cfg->t_min >= 0.0f) || !(cfg->dilation >= 0.0f) || !(cfg->tan_clamp > 0.0f))
         return GS_ERR_INVALID;
+    if (cfg->batch != 0 && cfg->batch != 128 && cfg->batch != 256 && cfg->batch != 512) return GS_ERR_INVALID;
     return GS_OK;
 }
 
@@ -63,6 +64,7 @@ gs_status build_views(const gs_camera *cams, int n_views, const gs_raster_cfg *c
     rc.alpha_max = cfg->alpha_max; rc.t_min = cfg->t_min; rc.tan_clamp = cfg->tan_clamp;
     for (int k = 0; k < 3; ++k) rc.bg[k] = cfg->bg[k];
     rc.tile_w = cfg->tile_w; rc.tile_h = cfg->tile_h;
+    rc.batch = cfg->batch == 0 ? 512 : cfg->batch;
     return GS_OK;
 }
 
@@ -278,7 +280,7 @@ GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, i
 
 GS_API gs_status gs_adam(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
                          const gs_params *exp_avg_sq, const float lr_groups[6], float beta1, float beta2, float eps,
-                         int64_t step, gs_stream stream) {
+                         int64_t step, const int64_t *step_device, gs_stream stream) {
     gs_status st = check_params(params);
     if (st == GS_OK) st = check_params(grads);
     if (st == GS_OK) st = check_params(exp_avg);
@@ -286,10 +288,12 @@ GS_API gs_status gs_adam(const gs_params *params, const gs_params *grads, const 
     if (st != GS_OK) return st;
     for (const gs_params *q : {grads, exp_avg, exp_avg_sq})
         if (q->ld != params->ld || q->n != params->n || q->sh_degree != params->sh_degree) return GS_ERR_INVALID;
-    if (!lr_groups || step < 1 || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f))
+    if (!lr_groups || (step < 1 && !step_device) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f))
         return GS_ERR_INVALID;
+    if (step_device && ((uintptr_t)step_device & 7u)) return GS_ERR_INVALID;
     launch_adam(params->data, grads->data, exp_avg->data, exp_avg_sq->data, params->ld, GS_PLANES(params->sh_degree),
-                lr_groups, beta1, beta2, eps, step, (cudaStream_t)stream);
+                lr_groups, beta1, beta2, eps, step, (const long long *)step_device, (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
 }
 

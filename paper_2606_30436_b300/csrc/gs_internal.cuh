@@ -34,6 +34,7 @@ struct RasterCfg {
     float near_z, dilation, alpha_min, alpha_max, t_min, tan_clamp;
     float bg[3];
     int tile_w, tile_h;
+    int batch;  // pairs a warp scans per step (128, 256, 512)
 };
 
 // The view that owns a global tile index (linear scan: <= 64 views, uniform

@@ -46,7 +46,7 @@ cudaError_t launch_loss(const float *img, const float *target, int h, int w, flo
                         float *dL_dimg, void *ws, cudaStream_t s);
 
 void launch_adam(float *p, const float *g, float *m, float *v, long long ld, int planes, const float lr[6],
-                 float beta1, float beta2, float eps, long long step, cudaStream_t s);
+                 float beta1, float beta2, float eps, long long step, const long long *step_dev, cudaStream_t s);
 
 size_t prune_workspace_bytes(long long n);
 void launch_prune(const float *acc, long long ld, long long n, int n_views, float tau_d, float tau_p, float *S_d,

@@ -65,22 +65,32 @@ __device__ __forceinline__ void load_rec(Rec &r, const float2 *__restrict__ xy, 
     }
 }
 
-constexpr int kWindow = 512;  // pairs whose block masks a warp scans per step (16 per lane)
 
-// Scans the block masks of pairs [w, w + 512) restricted to [lo, hi) and
+// Scans the block masks of pairs [w, w + WIN) restricted to [lo, hi) and
 // writes, in pair order, the absolute positions whose mask holds `bit` into
-// list.  Returns the count (warp-uniform).  The mask array is read in aligned
-// 16-byte words (w is a multiple of 16).
+// list.  Returns the count (warp-uniform).  Each lane reads WIN/32 masks in
+// one aligned load (w is a multiple of 16).
+template <int WIN>
 __device__ __forceinline__ int scan_window(const uint8_t *__restrict__ masks, int w, int lo, int hi, int bit,
                                            int *list) {
+    constexpr int PER = WIN / 32;  // 4, 8 or 16 masks per lane
     const int lane = threadIdx.x & 31;
-    const int q0 = w + 16 * lane;
-    uint4 mw = make_uint4(0u, 0u, 0u, 0u);
-    if (q0 < hi) mw = *reinterpret_cast<const uint4 *>(masks + q0);
-    const uint32_t wd[4] = {mw.x, mw.y, mw.z, mw.w};
+    const int q0 = w + PER * lane;
+    uint32_t wd[4] = {0u, 0u, 0u, 0u};
+    if (q0 < hi) {
+        if (PER == 16) {
+            const uint4 m4 = *reinterpret_cast<const uint4 *>(masks + q0);
+            wd[0] = m4.x; wd[1] = m4.y; wd[2] = m4.z; wd[3] = m4.w;
+        } else if (PER == 8) {
+            const uint2 m2 = *reinterpret_cast<const uint2 *>(masks + q0);
+            wd[0] = m2.x; wd[1] = m2.y;
+        } else {
+            wd[0] = *reinterpret_cast<const uint32_t *>(masks + q0);
+        }
+    }
     uint32_t rel = 0;
     #pragma unroll
-    for (int b = 0; b < 16; ++b) {
+    for (int b = 0; b < PER; ++b) {
         const int pos = q0 + b;
         const uint32_t byte = (wd[b >> 2] >> (8 * (b & 3))) & 0xffu;
         if (pos >= lo && pos < hi && ((byte >> bit) & 1u)) rel |= 1u << b;
@@ -111,6 +121,7 @@ __device__ __forceinline__ void gather(Rec &r, const int *list, int idx, int tot
     load_rec(r, xy, co, rgbd, valid ? ids[r.pos] : 0, valid);
 }
 
+template <int WIN>
 __global__ void __launch_bounds__(32 * kWarps) k_render_fwd(ViewTable vt, RasterCfg cfg,
                                                               const int2 *__restrict__ ranges,
                                                               const int *__restrict__ ids,
@@ -120,7 +131,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_fwd(ViewTable vt, Raster
                                                               const float4 *__restrict__ rgbd,
                                                               float *__restrict__ img, float *__restrict__ T_final,
                                                               int *__restrict__ last, float *__restrict__ depth) {
-    __shared__ int s_list[kWarps][kWindow];
+    __shared__ int s_list[kWarps][WIN];
     __shared__ float2 s_p[kWarps][32];
     __shared__ float4 s_q[kWarps][32];
     __shared__ float4 s_c[kWarps][32];
@@ -137,8 +148,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_fwd(ViewTable vt, Raster
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Dd = 0.0f;
     int lastc = 0;
     bool done = !t.inside;
-    for (int w = rg.x & ~15; w < rg.y && !__all_sync(0xffffffffu, done); w += kWindow) {
-        const int total = scan_window(masks, w, rg.x, rg.y, bit, list);
+    for (int w = rg.x & ~15; w < rg.y && !__all_sync(0xffffffffu, done); w += WIN) {
+        const int total = scan_window<WIN>(masks, w, rg.x, rg.y, bit, list);
         Rec cur, nxt;
         gather(cur, list, lane, total, ids, xy, co, rgbd);
         for (int c = 0; c < total; c += 32) {
@@ -225,7 +236,7 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-template <bool STATS>
+template <bool STATS, int WIN>
 __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, RasterCfg cfg,
                                                               const int2 *__restrict__ ranges,
                                                               const int *__restrict__ ids,
@@ -240,7 +251,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
                                                               const float *__restrict__ dL_ddepth,
                                                               const float *__restrict__ target, float tau_err,
                                                               float *__restrict__ acc, long long nrec) {
-    __shared__ int s_list[kWarps][kWindow];
+    __shared__ int s_list[kWarps][WIN];
     __shared__ float2 s_p[kWarps][32];
     __shared__ float4 s_q[kWarps][32];
     __shared__ float4 s_c[kWarps][32];
@@ -282,8 +293,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
 
     const int lo = rg.x, hi = rg.x + wmax;
     const int wbase = rg.x & ~15;
-    for (int kw = (hi - 1 - wbase) / kWindow; kw >= 0; --kw) {
-        const int total = scan_window(masks, wbase + kw * kWindow, lo, hi, bit, list);
+    for (int kw = (hi - 1 - wbase) / WIN; kw >= 0; --kw) {
+        const int total = scan_window<WIN>(masks, wbase + kw * WIN, lo, hi, bit, list);
         if (total == 0) continue;
         int c = ((total - 1) >> 5) << 5;
         Rec cur, nxt;
@@ -375,8 +386,13 @@ void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ra
                        float *T_final, int *last, float *depth, cudaStream_t s) {
     const long long units = 8ll * vt.total_tiles;
     if (units <= 0) return;
-    k_render_fwd<<<(unsigned)ceil_div(units, kWarps), 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd,
-                                                                           img, T_final, last, depth);
+    const unsigned grid = (unsigned)ceil_div(units, kWarps);
+#define GS_FWD(WN) k_render_fwd<WN><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd, img, \
+                                                                 T_final, last, depth)
+    if (cfg.batch == 128) GS_FWD(128);
+    else if (cfg.batch == 256) GS_FWD(256);
+    else GS_FWD(512);
+#undef GS_FWD
 }
 
 void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
@@ -387,12 +403,19 @@ void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ra
     const long long units = 8ll * vt.total_tiles;
     if (units <= 0) return;
     const unsigned grid = (unsigned)ceil_div(units, kWarps);
-    if (stats)
-        k_render_bwd<true><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd, img, T_final, last,
-                                                        dL_dimg, dL_ddepth, target, tau_err, acc, nrec);
-    else
-        k_render_bwd<false><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd, img, T_final,
-                                                         last, dL_dimg, dL_ddepth, target, tau_err, acc, nrec);
+#define GS_BWD(ST, WN) k_render_bwd<ST, WN><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd, \
+                                                                         img, T_final, last, dL_dimg, dL_ddepth, \
+                                                                         target, tau_err, acc, nrec)
+    if (stats) {
+        if (cfg.batch == 128) GS_BWD(true, 128);
+        else if (cfg.batch == 256) GS_BWD(true, 256);
+        else GS_BWD(true, 512);
+    } else {
+        if (cfg.batch == 128) GS_BWD(false, 128);
+        else if (cfg.batch == 256) GS_BWD(false, 256);
+        else GS_BWD(false, 512);
+    }
+#undef GS_BWD
 }
 
 }  // namespace gs

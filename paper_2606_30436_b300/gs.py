@@ -41,7 +41,7 @@ class Camera(C.Structure):
 class RasterCfg(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("near_z", C.c_float), ("dilation", C.c_float),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float),
-                ("tan_clamp", C.c_float), ("bg", C.c_float * 3)]
+                ("tan_clamp", C.c_float), ("bg", C.c_float * 3), ("batch", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -105,7 +105,7 @@ def lib():
         L.gs_loss_static.argtypes = [vp, vp, P(Camera), i32, f32, vp, vp, vp]
         L.gs_render_bwd.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), P(Binning), P(Frame),
                                     vp, vp, vp, vp, f32, P(Params), i32, P(Stats), vp, sz, vp]
-        L.gs_adam.argtypes = [P(Params), P(Params), P(Params), P(Params), P(f32 * 6), f32, f32, f32, i64, vp]
+        L.gs_adam.argtypes = [P(Params), P(Params), P(Params), P(Params), P(f32 * 6), f32, f32, f32, i64, vp, vp]
         L.gs_prune_stats.argtypes = [P(Stats), i64, i32, f32, f32, P(ChunkScores), vp, sz, vp]
         for name in EXPORTS:
             if name not in ("gs_status_string", "gs_version"):
@@ -161,10 +161,11 @@ class Config:
     t_min: float = 1e-4
     tan_clamp: float = 1.3
     bg: tuple = (0.0, 0.0, 0.0)
+    batch: int = 512
 
     def c(self) -> RasterCfg:
         return RasterCfg(self.tile_w, self.tile_h, self.near_z, self.dilation, self.alpha_min, self.alpha_max,
-                         self.t_min, self.tan_clamp, (C.c_float * 3)(*self.bg))
+                         self.t_min, self.tan_clamp, (C.c_float * 3)(*self.bg), self.batch)
 
 
 def planes(sh_degree: int) -> int:
@@ -358,10 +359,10 @@ def gs_render_bwd(model: GaussianModel, grads: GaussianModel, buf: Buffers, targ
 
 
 def gs_adam(model: GaussianModel, grads: GaussianModel, exp_avg: GaussianModel, exp_avg_sq: GaussianModel, lr,
-            step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+            step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None, step_device=None):
     lrs = (C.c_float * 6)(*[float(x) for x in lr])
     _check(lib().gs_adam(C.byref(model.c()), C.byref(grads.c()), C.byref(exp_avg.c()), C.byref(exp_avg_sq.c()),
-                         C.byref(lrs), beta1, beta2, eps, int(step), _stream(stream)), "gs_adam")
+                         C.byref(lrs), beta1, beta2, eps, int(step), _ptr(step_device), _stream(stream)), "gs_adam")
 
 
 def gs_prune_stats(stats_acc: torch.Tensor, n, n_views, scores: dict, ws: torch.Tensor, tau_d=5.0, tau_p=0.99,
@@ -428,6 +429,36 @@ class MappingStep:
         if optimize:
             self.step_count += 1
             gs_adam(self.model, self.grads, self.exp_avg, self.exp_avg_sq, self.lr, self.step_count, stream=stream)
+        return self.buf.loss
+
+    def capture(self, target, stream=None):
+        """Captures one whole iteration (status reset, project, sort, render,
+        loss, backward, Adam) for the current cameras and `target` buffer into
+        a CUDA graph.  Adam reads its step from a device counter that the graph
+        advances, so replays are successive iterations.  The pair buffer keeps
+        the capacity it has now (size it with fit_capacity first)."""
+        dev = self.model.data.device
+        if getattr(self, "step_dev", None) is None:
+            self.step_dev = torch.full((1,), self.step_count, dtype=torch.int64, device=dev)
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            b = self.buf
+            b.status.zero_()
+            gs_project(self.model, b)
+            gs_sort(b)
+            gs_render_fwd(b)
+            gs_loss(b, target, self.lambda_dssim)
+            gs_render_bwd(self.model, self.grads, b, target, self.tau_err, with_stats=self.with_stats)
+            self.step_dev.add_(1)
+            gs_adam(self.model, self.grads, self.exp_avg, self.exp_avg_sq, self.lr, 1, step_device=self.step_dev)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        return graph
+
+    def replay(self, graph):
+        graph.replay()
+        self.step_count += 1
         return self.buf.loss
 
     def check_status(self):

@@ -79,8 +79,12 @@ def test_invalid_arguments_rejected_on_host():
     lrs = (C.c_float * 6)(*([1e-3] * 6))
     q = gs.Params(16, 10, 12, 0)
     q2 = gs.Params(32, 10, 16, 0)  # ld mismatch
-    assert L.gs_adam(C.byref(q), C.byref(q2), C.byref(q), C.byref(q), C.byref(lrs), 0.9, 0.999, 1e-15, 1, None) == 1
-    assert L.gs_adam(C.byref(q), C.byref(q), C.byref(q), C.byref(q), C.byref(lrs), 0.9, 0.999, 1e-15, 0, None) == 1
+    assert L.gs_adam(C.byref(q), C.byref(q2), C.byref(q), C.byref(q), C.byref(lrs), 0.9, 0.999, 1e-15, 1, None,
+                     None) == 1
+    assert L.gs_adam(C.byref(q), C.byref(q), C.byref(q), C.byref(q), C.byref(lrs), 0.9, 0.999, 1e-15, 0, None,
+                     None) == 1
+    bad_batch = gs.Config(batch=64).c()
+    assert L.gs_view_layout(cam, 1, C.byref(bad_batch), C.byref(nt), None, None, None) == 1
 
 
 def test_plane_packing_roundtrip():

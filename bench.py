@@ -129,30 +129,94 @@ def measured_peaks():
 
 
 # --------------------------------------------------------------------------
+# ncu traffic of the dominant kernel (committed summary, valid only while the
+# kernel source is unchanged)
+
+def kernel_source_sha(path):
+    import hashlib
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def committed_traffic(kernel):
+    """bytes per launch from profiles/<kernel>*.md if its source hash matches."""
+    import glob
+    import re
+    src = {"k_render_bwd": "paper_2606_30436_b300/csrc/render.cu",
+           "k_render_fwd": "paper_2606_30436_b300/csrc/render.cu",
+           "k_adam": "paper_2606_30436_b300/csrc/adam.cu"}.get(kernel)
+    if src is None:
+        return None
+    sha = kernel_source_sha(src)
+    for fn in sorted(glob.glob(os.path.join(ROOT, "profiles", kernel + "*.md"))):
+        txt = open(fn).read()
+        m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+        m_b = re.search(r"dram_bytes_per_launch_bench_mean:\s*([0-9.]+)", txt)
+        if m_sha and m_b and m_sha.group(1) == sha:
+            return float(m_b.group(1))
+    return None
+
+
+# --------------------------------------------------------------------------
 # GPU arm
 
-def run_gpu(args, rank, world):
+STAGES = ["project", "sort", "render_fwd", "loss", "render_bwd", "adam"]
+STAGE_KERNEL = {"project": "k_project", "sort": None, "render_fwd": "k_render_fwd", "loss": None,
+                "render_bwd": "k_render_bwd", "adam": "k_adam"}
+
+
+def eager_step(gs, step, target, events=None, stream=None):
+    b = step.buf
+    rec = (lambda j: events[j].record(stream)) if events is not None else (lambda j: None)
+    b.status.zero_()
+    rec(0)
+    gs.gs_project(step.model, b)
+    rec(1)
+    gs.gs_sort(b)
+    rec(2)
+    gs.gs_render_fwd(b)
+    rec(3)
+    gs.gs_loss(b, target, step.lambda_dssim)
+    rec(4)
+    gs.gs_render_bwd(step.model, step.grads, b, target, step.tau_err, with_stats=step.with_stats)
+    rec(5)
+    step.step_count += 1
+    gs.gs_adam(step.model, step.grads, step.exp_avg, step.exp_avg_sq, step.lr, step.step_count)
+    rec(6)
+
+
+def render_targets(gs, tscene, cams_list, cfg, dev):
+    """Renders of the perturbed scene, one per camera set, device resident."""
+    import torch
+    tmodel = gs.GaussianModel.from_scene(tscene)
+    out = []
+    for cams in cams_list:
+        st = gs.MappingStep(tmodel, cams, cfg, max_pairs=1 << 20, with_stats=False)
+        st.fit_capacity()
+        out.append(st.buf.img.clone())
+        del st
+    del tmodel
+    torch.cuda.synchronize()
+    return out
+
+
+def barrier(world):
+    import torch
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+
+def run_corridor(args, world, dev):
     import torch
     from paper_2606_30436_b300 import gs, scenes
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
     frames = frame_pool(args.frames)
     scene = scenes.corridor_scene(N_GAUSS, seed=0, sh_degree=SH_DEG)
     tscene = scenes.perturb(scene, 0.01, seed=1)
     cams = [scenes.corridor_camera(f, W, H, F) for f in frames]
     cfg = gs.Config()
-
-    # targets: renders of the perturbed scene (device resident)
-    tmodel = gs.GaussianModel.from_scene(tscene)
-    tstep = gs.MappingStep(tmodel, [cams[0]], cfg, max_pairs=1 << 20, with_stats=False)
-    targets = torch.empty(len(frames), 3 * W * H, dtype=torch.float32, device=dev)
-    for i, c in enumerate(cams):
-        tstep.set_cameras([c])
-        tstep.fit_capacity()
-        targets[i].copy_(tstep.buf.img)
-    del tstep, tmodel
-    torch.cuda.synchronize()
+    targets = render_targets(gs, tscene, [[c] for c in cams], cfg, dev)
 
     model = gs.GaussianModel.from_scene(scene)
     step = gs.MappingStep(model, [cams[0]], cfg, max_pairs=1 << 20, lambda_dssim=LAMBDA,
@@ -163,76 +227,65 @@ def run_gpu(args, rank, world):
         needed.append(step.fit_capacity(slack=1.0))
         vis.append(int(step.buf.counts[0].item()))
     step.buf.set_max_pairs(int(max(needed) * 1.15) + 1024)
-    tiles = step.buf.total_tiles
-    K = model.K
-
     stream = torch.cuda.current_stream()
-    stage_names = ["project", "sort", "render_fwd", "loss", "render_bwd", "adam"]
 
-    def one(i, events=None):
-        k = i % len(frames)
-        step.set_cameras([cams[k]])
-        b = step.buf
-        rec = (lambda j: events[j].record(stream)) if events is not None else (lambda j: None)
-        b.status.zero_()
-        rec(0)
-        gs.gs_project(step.model, b)
-        rec(1)
-        gs.gs_sort(b)
-        rec(2)
-        gs.gs_render_fwd(b)
-        rec(3)
-        gs.gs_loss(b, targets[k], LAMBDA)
-        rec(4)
-        gs.gs_render_bwd(step.model, step.grads, b, targets[k], step.tau_err, with_stats=True)
-        rec(5)
-        step.step_count += 1
-        gs.gs_adam(step.model, step.grads, step.exp_avg, step.exp_avg_sq, step.lr, step.step_count)
-        rec(6)
-
+    # eager warm-up, then one captured iteration per frame of the pool
     for i in range(args.warmup):
-        one(i)
+        step.set_cameras([cams[i % len(cams)]])
+        eager_step(gs, step, targets[i % len(cams)])
+    torch.cuda.synchronize()
+    step.check_status()
+    graphs = []
+    for k, c in enumerate(cams):
+        step.set_cameras([c])
+        graphs.append(step.capture(targets[k]))
+    for i in range(args.warmup):
+        step.replay(graphs[i % len(graphs)])
     torch.cuda.synchronize()
     step.check_status()
 
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    # device-timed region: inputs resident in HBM
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    # device-timed region: inputs resident in HBM, one graph launch per step
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(dev.index)
     clocks.start()
-    barrier()
+    barrier(world)
     start.record(stream)
     for i in range(args.steps):
-        one(args.warmup + i, evs[i])
+        step.replay(graphs[i % len(graphs)])
     end.record(stream)
-    barrier()
+    barrier(world)
     clk = clocks.stop()
     ms = start.elapsed_time(end)
     step.check_status()
-    stage_ms = {nm: sum(e[j].elapsed_time(e[j + 1]) for e in evs) / args.steps for j, nm in enumerate(stage_names)}
+
+    # per-stage timing (eager launches, events between the C-ABI calls)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    barrier(world)
+    for i in range(args.steps):
+        k = i % len(cams)
+        step.set_cameras([cams[k]])
+        eager_step(gs, step, targets[k], evs[i], stream)
+    barrier(world)
+    stage_ms = {nm: sum(e[j].elapsed_time(e[j + 1]) for e in evs) / args.steps for j, nm in enumerate(STAGES)}
 
     # end to end through the C ABI with host buffers: pinned host target in,
-    # loss out, both copies inside the timed region
-    host_targets = targets[:min(4, len(frames))].cpu().pin_memory()
+    # loss out, both copies inside the timed region (eager calls)
+    nh = min(4, len(frames))
+    host_targets = torch.stack([t.cpu() for t in targets[:nh]]).pin_memory()
     dev_target = torch.empty(3 * W * H, dtype=torch.float32, device=dev)
     host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
-    barrier()
+    barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     t0 = time.perf_counter()
     for i in range(args.steps):
-        k = i % host_targets.shape[0]
+        k = i % nh
         dev_target.copy_(host_targets[k], non_blocking=True)
         step.set_cameras([cams[k]])
         step.step(dev_target)
         host_loss.copy_(step.buf.loss[:1], non_blocking=True)
     e1.record(stream)
-    barrier()
+    barrier(world)
     e2e_ms = e0.elapsed_time(e1)
     wall_e2e = time.perf_counter() - t0
 
@@ -241,40 +294,146 @@ def run_gpu(args, rank, world):
         torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
     ms, e2e_ms = float(ms_t[0]), float(ms_t[1])
 
-    # roofline of the dominant kernel by time, from the live stage timings
     Vm, Pm = float(np.mean(vis)), float(np.mean(needed))
-    ab = algorithmic_bytes(N_GAUSS, Vm, Pm, W * H, tiles, K)
+    ab = algorithmic_bytes(N_GAUSS, Vm, Pm, W * H, step.buf.total_tiles, model.K)
     peak, peak_kind = measured_peaks()
-    dom = max(stage_names, key=lambda s: stage_ms[s])
-    if dom == "adam":
-        # one kernel per call: k_adam
-        achieved = ab["adam"] / (stage_ms["adam"] * 1e-3) / 1e9
-        roof = {"kernel": "k_adam", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_kind": peak_kind}
-    else:
-        achieved = ab[dom] / (stage_ms[dom] * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind}
-    adam_gbs = ab["adam"] / (stage_ms["adam"] * 1e-3) / 1e9
-
-    launches_per_step = gs.launches_per_step(tiles, views=1, lambda_dssim=LAMBDA)
+    dom = max(STAGES, key=lambda s: stage_ms[s])
+    achieved = ab[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    kern = STAGE_KERNEL[dom] or dom
+    roof = {"kernel": kern, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": committed_traffic(kern),
+            "peak_kind": peak_kind + " (copy bandwidth)",
+            "algorithmic_bytes_per_launch": int(ab[dom]), "launch_ms": round(stage_ms[dom], 4)}
     value = world * args.steps / (ms * 1e-3)
-    e2e_value = world * args.steps / (e2e_ms * 1e-3)
+    total_bytes = sum(ab.values())
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(len(frames)),
-        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 3 * W * H * 4,
-                "d2h_bytes_per_step": 4, "wall_s": round(wall_e2e, 3)},
-        "gpu_launches": launches_per_step * args.steps,
+        "e2e": {"value": round(world * args.steps / (e2e_ms * 1e-3), 3), "unit": UNIT,
+                "h2d_bytes_per_step": 3 * W * H * 4, "d2h_bytes_per_step": 4, "wall_s": round(wall_e2e, 3)},
+        "gpu_launches": gs.launches_per_step(step.buf.total_tiles, views=1, lambda_dssim=LAMBDA) * args.steps,
         "roofline": roof,
+        "step_hbm": {"algorithmic_bytes": int(total_bytes),
+                     "frac_of_peak": round(total_bytes / (ms / args.steps * 1e-3) / 1e9 / peak, 4)},
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "adam_hbm_gbs": round(adam_gbs, 1),
         "visible_mean": int(Vm), "pairs_mean": int(Pm),
         "clocks": clk,
     }
+    del graphs, step, model
+    torch.cuda.synchronize()
+    return out
+
+
+def chunk_bytes(N, K, views):
+    """Algorithmic bytes of one batched chunk iteration: parameters read once
+    per chunk in projection / backward / Adam, per-view terms summed."""
+    tot = 12 * N + 4 * N + 4 * K * N + 28 * K * N
+    for (V, P, px, tiles) in views:
+        tot += 4 * (K - 3) * V + 56 * V + 8 * N + 16 * V + 44 * P + 8 * tiles + 40 * P + 20 * px + 36 * px \
+            + 40 * P + 32 * px + 36 * V + 4 * K * V + 32 * V
+    return tot
+
+
+def run_chunk(args, world, dev):
+    """Batched chunk (configs[2]): one graph launch renders, differentiates and
+    updates 2M shared Gaussians over 16 keyframes of uneven resolution; the
+    same keyframes as 16 single-view iterations are the plain comparison."""
+    import torch
+    from paper_2606_30436_b300 import gs, scenes
+    from paper_2606_30436_b300.autotune import autotune
+
+    n, nv = args.chunk_gaussians, args.chunk_views
+    scene = scenes.uniform_scene(n, seed=0, sh_degree=0)
+    tscene = scenes.perturb(scene, 0.01, seed=1)
+    cams = scenes.chunk_cameras(nv, seed=2)
+    model = gs.GaussianModel.from_scene(scene)
+    tcache = {}
+
+    def targets_for(cfg):
+        key = (cfg.tile_w, cfg.tile_h)
+        if key not in tcache:
+            tcache[key] = render_targets(gs, tscene, [cams], cfg, dev)[0]
+        return tcache[key]
+
+    best, table = autotune(model, cams, targets_for, reps=2)
+    target = targets_for(best)
+    st = gs.MappingStep(model, cams, best, lambda_dssim=LAMBDA, lr=gs.default_lr(extent=10.0), with_stats=True)
+    needed = st.fit_capacity(slack=1.1)
+    per_view = []
+    g = st.capture(target)
+    for _ in range(args.warmup):
+        st.replay(g)
+    torch.cuda.synchronize()
+    st.check_status()
+    steps = max(3, min(args.steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    e0.record()
+    for _ in range(steps):
+        st.replay(g)
+    e1.record()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / steps
+    st.check_status()
+    V = int(st.buf.counts[0].item())
+    tiles_total = st.buf.total_tiles
+    del g, st
+    torch.cuda.synchronize()
+
+    # plain: the same keyframes as single-view iterations, one graph each
+    plain_ms = 0.0
+    singles = []
+    shared = None
+    for v, c in enumerate(cams):
+        s1 = gs.MappingStep(model, [c], best, lambda_dssim=LAMBDA, lr=gs.default_lr(extent=10.0), with_stats=True)
+        if shared is None:  # one optimiser state for all single-view steps
+            shared = (s1.grads, s1.exp_avg, s1.exp_avg_sq, s1.buf.stats_acc)
+        s1.grads, s1.exp_avg, s1.exp_avg_sq, s1.buf.stats_acc = shared
+        s1.fit_capacity(slack=1.1)
+        W_, H_ = c["width"], c["height"]
+        off = 0
+        for u in range(v):
+            off += 3 * cams[u]["width"] * cams[u]["height"]
+        tv = target[off:off + 3 * W_ * H_]
+        gv = s1.capture(tv)
+        s1.replay(gv)
+        singles.append((s1, gv))
+        per_view.append((int(s1.buf.counts[0].item()), int(s1.buf.counts[1].item()), W_ * H_, s1.buf.total_tiles))
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        for s1, gv in singles:
+            s1.replay(gv)
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / steps
+    del singles
+    torch.cuda.synchronize()
+
+    peak, _ = measured_peaks()
+    B = chunk_bytes(n, model.K, per_view)
+    return {"workload": "%d Gaussians (uniform, SH0), %d keyframes cycling 640x360..1600x900, "
+                        "fwd+L1/D-SSIM+bwd+stats+Adam" % (n, nv),
+            "chunk_iters_per_s": round(world * 1e3 / ms, 3), "ms_per_chunk": round(ms, 4),
+            "views_per_s": round(world * nv * 1e3 / ms, 2),
+            "plain_views_per_s": round(world * nv * 1e3 / plain_ms, 2), "plain_ms_per_chunk": round(plain_ms, 4),
+            "speedup_vs_plain": round(plain_ms / ms, 3),
+            "hbm": {"algorithmic_bytes": int(B), "achieved_gbs": round(B / (ms * 1e-3) / 1e9, 1),
+                    "frac_of_peak": round(B / (ms * 1e-3) / 1e9 / peak, 4)},
+            "tuned": {"tile": "%dx%d" % (best.tile_w, best.tile_h), "batch": best.batch,
+                      "sweep_ms": {"%dx%d/%d" % k: round(v, 3) for k, v in sorted(table.items())}},
+            "pairs": needed, "visible_records": V, "tiles": tiles_total, "steps": steps}
+
+
+def run_gpu(args, rank, world):
+    import torch
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    out = run_corridor(args, world, dev)
+    if not args.no_chunk:
+        out["batched"] = run_chunk(args, world, dev)
     return out
 
 
@@ -351,11 +510,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
     ap.add_argument("--frames", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-chunk", action="store_true", help="skip the batched-chunk measurement")
+    ap.add_argument("--chunk-gaussians", type=int, default=2_000_000)
+    ap.add_argument("--chunk-views", type=int, default=16)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -111,7 +111,7 @@ typedef struct {
                               (tile, depth, Gaussian index) */
     int32_t *tile_ranges;  /* [total_tiles][2] = first pair, one past the last */
     int32_t *counts;       /* device int32[4]: visible records, pairs written,
-                              pairs needed, reserved */
+                              pairs needed, records covering more than 128 tiles */
     uint8_t *block_mask;   /* [gs_block_mask_size(max_pairs) bytes], 16-byte aligned:
                               per pair, bit b set when the Gaussian's alpha >=
                               alpha_min ellipse can reach the tile's 8x4 pixel

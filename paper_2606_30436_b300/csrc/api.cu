@@ -57,7 +57,7 @@ gs_status build_views(const gs_camera *cams, int n_views, const gs_raster_cfg *c
         d.pix_offset = pix;
         tiles += (long long)d.GW * d.GH;
         pix += (long long)c.width * c.height;
-        if (tiles > 0x3fffffffll) return GS_ERR_INVALID;
+        if (tiles > 0xffffffll) return GS_ERR_INVALID;  // tile ids share a 32-bit sort key with an 8-bit mask
     }
     vt.total_tiles = (int)tiles;
     rc.near_z = cfg->near_z; rc.dilation = cfg->dilation; rc.alpha_min = cfg->alpha_min;

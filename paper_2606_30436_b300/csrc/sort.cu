@@ -133,8 +133,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *
     const uint32_t mask = radix - 1;
     for (int i = threadIdx.x; i < radix; i += kSortThreads) h[i] = 0;
     __syncthreads();
-    long long beg, end;
-    block_segment(*count, beg, end);
+    const long long cnt_all = *count;
+    const long long seg = ceil_div(ceil_div(cnt_all, (long long)gridDim.x), (long long)(kSortThreads * 16)) *
+                          (kSortThreads * 16);  // same segments as the downsweep (kDownTile)
+    const long long beg = min(cnt_all, (long long)blockIdx.x * seg), end = min(cnt_all, beg + seg);
     for (long long i = beg + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < radix; d += kSortThreads) hist[d * kSortBlocks + blockIdx.x] = h[d];
@@ -150,6 +152,15 @@ __global__ void __launch_bounds__(kSortBlocks) k_radix_scan(uint32_t *__restrict
     if (threadIdx.x == 0) dtotal[d] = total;
 }
 
+// Stable scatter of one LSD pass.  A block takes its segment in rounds of
+// kDownTile elements; each warp ranks its 512 consecutive elements (16 rounds
+// of 32 lanes) per digit with ballots (lanes whose digit bits all agree) and
+// a per-warp histogram, the warps' counts are scanned per digit, the round is
+// reordered by digit in shared memory, and written out in digit runs so that
+// the global stores are contiguous.
+constexpr int kDownItems = 16;
+constexpr int kDownTile = kSortThreads * kDownItems;  // 4096
+
 __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ kin,
                                                                    const uint32_t *__restrict__ vin,
                                                                    uint32_t *__restrict__ kout,
@@ -157,9 +168,11 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
                                                                    const int *__restrict__ count, int shift, int bits,
                                                                    const uint32_t *__restrict__ hist,
                                                                    const uint32_t *__restrict__ dtotal) {
-    __shared__ uint32_t s_base[256];
-    __shared__ uint32_t s_tcount[256];
+    __shared__ uint32_t s_base[256];    // global position of this block's next element of each digit
+    __shared__ uint32_t s_dstart[256];  // first local slot of each digit in the current round
     __shared__ uint32_t s_whist[kSortThreads / 32][256];
+    __shared__ uint32_t s_key[kDownTile];
+    __shared__ uint32_t s_val[kDownTile];
     __shared__ uint32_t sm[33];
     const int radix = 1 << bits;
     const uint32_t mask = radix - 1;
@@ -172,56 +185,85 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t
         if (threadIdx.x < radix) s_base[threadIdx.x] = ex + hist[threadIdx.x * kSortBlocks + blockIdx.x];
     }
     __syncthreads();
-    long long beg, end;
-    block_segment(*count, beg, end);
-    for (long long tb = beg; tb < end; tb += kSortTile) {
+    const long long cnt_all = *count;
+    const long long seg = ceil_div(ceil_div(cnt_all, (long long)gridDim.x), (long long)kDownTile) * kDownTile;
+    const long long beg = min(cnt_all, (long long)blockIdx.x * seg), end = min(cnt_all, beg + seg);
+    for (long long tb = beg; tb < end; tb += kDownTile) {
         for (int i = lane; i < radix; i += 32) s_whist[warp][i] = 0;
         __syncwarp();
-        uint32_t k[kSortItems], v[kSortItems], rk[kSortItems];
-        int d[kSortItems];
+        uint32_t k[kDownItems], v[kDownItems], rk[kDownItems];
         #pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {
-            const long long idx = tb + warp * (32 * kSortItems) + r * 32 + lane;
+        for (int r = 0; r < kDownItems; ++r) {
+            const long long idx = tb + warp * (32 * kDownItems) + r * 32 + lane;
             const bool valid = idx < end;
-            k[r] = valid ? kin[idx] : 0u;
+            k[r] = valid ? kin[idx] : 0xffffffffu;
             v[r] = valid ? vin[idx] : 0u;
-            d[r] = valid ? (int)((k[r] >> shift) & mask) : radix;  // radix = "no element"
         }
         #pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {
-            const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
-            const int leader = __ffs(peers) - 1;
-            uint32_t base = 0;
-            if (lane == leader && d[r] < radix) {
-                base = s_whist[warp][d[r]];
-                s_whist[warp][d[r]] = base + __popc(peers);
+        for (int r = 0; r < kDownItems; ++r) {
+            const long long idx = tb + warp * (32 * kDownItems) + r * 32 + lane;
+            const bool valid = idx < end;
+            const uint32_t d = (k[r] >> shift) & mask;
+            // lanes holding the same digit: all `bits` ballots agree
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+            for (int b = 0; b < bits; ++b) {
+                const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+                peers &= ((d >> b) & 1u) ? bal : ~bal;
             }
-            base = __shfl_sync(0xffffffffu, base, leader);
-            rk[r] = base + __popc(peers & lt);
+            uint32_t base = 0;
+            const int leader = __ffs(peers) - 1;
+            if (valid && lane == leader) {
+                base = s_whist[warp][d];
+                s_whist[warp][d] = base + __popc(peers);
+            }
+            base = __shfl_sync(0xffffffffu, base, valid ? leader : 0);
+            rk[r] = valid ? base + __popc(peers & lt) : 0xffffffffu;
             __syncwarp();
         }
         __syncthreads();
+        // per digit: exclusive scan over warps, and the round's digit totals
         for (int dd = threadIdx.x; dd < radix; dd += kSortThreads) {
-            uint32_t s = 0;
+            uint32_t sacc = 0;
             #pragma unroll
             for (int w = 0; w < kSortThreads / 32; ++w) {
                 const uint32_t c = s_whist[w][dd];
-                s_whist[w][dd] = s;
-                s += c;
+                s_whist[w][dd] = sacc;
+                sacc += c;
             }
-            s_tcount[dd] = s;
+            s_dstart[dd] = sacc;  // round total of digit dd (scanned below)
         }
         __syncthreads();
+        {
+            uint32_t t = threadIdx.x < radix ? s_dstart[threadIdx.x] : 0u, tot;
+            const uint32_t ex = block_exclusive_scan<uint32_t>(t, tot, sm);
+            if (threadIdx.x < radix) s_dstart[threadIdx.x] = ex;
+        }
+        __syncthreads();
+        // reorder the round by digit in shared memory
         #pragma unroll
-        for (int r = 0; r < kSortItems; ++r) {
-            if (d[r] < radix) {
-                const uint32_t pos = s_base[d[r]] + s_whist[warp][d[r]] + rk[r];
-                kout[pos] = k[r];
-                vout[pos] = v[r];
+        for (int r = 0; r < kDownItems; ++r) {
+            if (rk[r] != 0xffffffffu) {
+                const uint32_t d = (k[r] >> shift) & mask;
+                const uint32_t slot = s_dstart[d] + s_whist[warp][d] + rk[r];
+                s_key[slot] = k[r];
+                s_val[slot] = v[r];
             }
         }
         __syncthreads();
-        for (int dd = threadIdx.x; dd < radix; dd += kSortThreads) s_base[dd] += s_tcount[dd];
+        const int n_round = (int)min((long long)kDownTile, end - tb);
+        for (int i = threadIdx.x; i < n_round; i += kSortThreads) {
+            const uint32_t key = s_key[i];
+            const uint32_t d = (key >> shift) & mask;
+            const uint32_t pos = s_base[d] + (uint32_t)i - s_dstart[d];
+            kout[pos] = key;
+            vout[pos] = s_val[i];
+        }
+        __syncthreads();
+        // advance the block's digit bases by this round's counts
+        for (int dd = threadIdx.x; dd < radix; dd += kSortThreads) {
+            const uint32_t nxt = (dd + 1 < radix) ? s_dstart[dd + 1] : (uint32_t)n_round;
+            s_base[dd] += nxt - s_dstart[dd];
+        }
         __syncthreads();
     }
 }
@@ -266,71 +308,138 @@ __global__ void __launch_bounds__(kSortThreads) k_tiles_offsets(const uint32_t *
     if (blockIdx.x == 0 && threadIdx.x == 0) off[V] = (uint32_t)counts[2];
 }
 
-// Last r in [lo, hi) with off[r] <= o (off non-decreasing, off[lo] <= o).
-__device__ __forceinline__ long long owner(const uint32_t *__restrict__ off, long long lo, long long hi, uint32_t o) {
-    while (hi - lo > 1) {
-        const long long mid = (lo + hi) >> 1;
-        if (off[mid] <= o) lo = mid; else hi = mid;
-    }
-    return lo;
+constexpr int kBigRecord = 128;  // records overlapping more tiles are emitted by a whole CTA
+
+// Pair emission, one warp per 32 consecutive sorted records.  The warp writes
+// the slots of its records with at most kBigRecord tiles, 32 at a time: each
+// lane finds the record owning its slot by a binary search over the lanes'
+// running slot counts (shuffles), then the slot's tile in that record's
+// rectangle (row-major) and the mask of the tile's 8x4 blocks the Gaussian
+// can reach.  key = tile | mask << 24 (the LSD sort orders on the tile bits
+// only, the mask rides along), value = depth rank.  Larger records go to a
+// list for k_emit_big, so no warp is left with a near-camera Gaussian's
+// thousands of tiles.
+__device__ __forceinline__ void emit_one(uint32_t o, uint32_t rank, int i, int x0, int y0, int w, int toff, int gw,
+                                         float2 p, float4 q, const ViewTable &vt, float alpha_min,
+                                         uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+    const int ty = y0 + i / w, tx = x0 + i % w;
+    const uint32_t m = block_mask8(p, q, alpha_min, tx * vt.tile_w, ty * vt.tile_h, vt.tile_w);
+    pkey[o] = (uint32_t)(toff + ty * gw + tx) | (m << 24);
+    pval[o] = rank;
 }
 
-// One thread per output pair: finds the record that owns the slot, then the
-// tile of the slot inside that record's tile rectangle (row-major, the order
-// in which the rectangle is enumerated).  Writes are coalesced and every
-// thread does the same work whatever the Gaussian's footprint.
 __global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t *__restrict__ sorted_rec,
                                                      const uint32_t *__restrict__ off,
                                                      const int *__restrict__ radius,
-                                                     const float2 *__restrict__ xy, long long ld, ViewTable vt,
-                                                     const int *__restrict__ counts, uint32_t *__restrict__ pkey,
-                                                     uint32_t *__restrict__ pval) {
-    __shared__ long long s_lo, s_hi;
-    const long long P = counts[1];  // 0 on overflow
+                                                     const float2 *__restrict__ xy, const float4 *__restrict__ co,
+                                                     long long ld, ViewTable vt, float alpha_min,
+                                                     int *__restrict__ counts, uint32_t *__restrict__ big,
+                                                     uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+    if (counts[1] == 0) return;  // nothing to emit, or overflow
     const long long V = counts[0];
-    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < P; b0 += (long long)gridDim.x * blockDim.x) {
-        const long long b1 = min(P, b0 + (long long)blockDim.x) - 1;
-        if (threadIdx.x == 0) s_lo = owner(off, 0, V, (uint32_t)b0);
-        if (threadIdx.x == 32) s_hi = owner(off, 0, V, (uint32_t)b1);
-        __syncthreads();
-        const long long o = b0 + threadIdx.x;
-        if (o <= b1) {
-            const long long r = owner(off, s_lo, s_hi + 1, (uint32_t)o);
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < V;
+         r0 += nwarps * 32) {
+        const long long r = r0 + lane;
+        const bool valid = r < V;
+        uint32_t my_off = 0;
+        int x0 = 0, y0 = 0, w = 1, toff = 0, gw = 1, n_small = 0;
+        float2 p = make_float2(0.f, 0.f);
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
             const uint32_t rec = sorted_rec[r];
-            const int view = (int)(rec / ld);
-            const ViewDesc &c = vt.v[view];
-            const float2 p = xy[rec];
-            const Rect rc = tile_rect(p.x, p.y, radius[rec], vt.tile_w, vt.tile_h, c.GW, c.GH);
-            const int i = (int)(o - off[r]);
-            const int w = rc.x1 - rc.x0;
-            const int ty = rc.y0 + i / w, tx = rc.x0 + i % w;
-            pkey[o] = (uint32_t)(c.tile_offset + ty * c.GW + tx);
-            pval[o] = (uint32_t)r;
+            my_off = off[r];
+            const int nt = (int)(off[r + 1] - my_off);
+            if (nt > kBigRecord) {
+                big[atomicAdd(&counts[3], 1)] = (uint32_t)r;
+            } else {
+                const ViewDesc &c = vt.v[(int)(rec / ld)];
+                p = xy[rec];
+                q = co[rec];
+                const Rect rc = tile_rect(p.x, p.y, radius[rec], vt.tile_w, vt.tile_h, c.GW, c.GH);
+                x0 = rc.x0; y0 = rc.y0; w = rc.x1 - rc.x0; toff = c.tile_offset; gw = c.GW;
+                n_small = nt;
+            }
         }
-        __syncthreads();
+        // running count of small-record slots over the lanes
+        int inc = n_small;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int excl = inc - n_small;
+        const int total = __shfl_sync(0xffffffffu, inc, 31);
+        for (int cb = 0; cb < total; cb += 32) {
+            const int c = cb + lane;
+            // owner: the last lane j with excl_j <= c (lanes with no small slots never win a tie
+            // because their excl equals the next lane's)
+            int j = 0;
+            #pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int cand = j + step;
+                const int ecand = __shfl_sync(0xffffffffu, excl, cand & 31);
+                if (cand < 32 && ecand <= c) j = cand;
+            }
+            // skip back over lanes with no small slots that share the same excl
+            const int ej = __shfl_sync(0xffffffffu, excl, j);
+            const uint32_t oj = __shfl_sync(0xffffffffu, my_off, j);
+            const int jx0 = __shfl_sync(0xffffffffu, x0, j), jy0 = __shfl_sync(0xffffffffu, y0, j);
+            const int jw = __shfl_sync(0xffffffffu, w, j), jtoff = __shfl_sync(0xffffffffu, toff, j);
+            const int jgw = __shfl_sync(0xffffffffu, gw, j), jn = __shfl_sync(0xffffffffu, n_small, j);
+            float2 jp;
+            float4 jq;
+            jp.x = __shfl_sync(0xffffffffu, p.x, j); jp.y = __shfl_sync(0xffffffffu, p.y, j);
+            jq.x = __shfl_sync(0xffffffffu, q.x, j); jq.y = __shfl_sync(0xffffffffu, q.y, j);
+            jq.z = __shfl_sync(0xffffffffu, q.z, j); jq.w = __shfl_sync(0xffffffffu, q.w, j);
+            if (c < total && c - ej < jn) {
+                const int i = c - ej;
+                emit_one(oj + (uint32_t)i, (uint32_t)(r0 + j), i, jx0, jy0, jw, jtoff, jgw, jp, jq, vt, alpha_min,
+                         pkey, pval);
+            }
+        }
     }
 }
 
-// Final pass over the sorted pairs: Gaussian ids, tile ranges, and the mask of
-// the tile's 8x4 pixel blocks each Gaussian can reach (block_mask8).
+// The records with more than kBigRecord tiles, one CTA each (grid-stride).
+__global__ void __launch_bounds__(256) k_emit_big(const uint32_t *__restrict__ sorted_rec,
+                                                   const uint32_t *__restrict__ off, const int *__restrict__ radius,
+                                                   const float2 *__restrict__ xy, const float4 *__restrict__ co,
+                                                   long long ld, ViewTable vt, float alpha_min,
+                                                   const int *__restrict__ counts, const uint32_t *__restrict__ big,
+                                                   uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+    if (counts[1] == 0) return;
+    const int nbig = counts[3];
+    for (int b = blockIdx.x; b < nbig; b += gridDim.x) {
+        const uint32_t r = big[b];
+        const uint32_t rec = sorted_rec[r];
+        const uint32_t o0 = off[r];
+        const int nt = (int)(off[r + 1] - o0);
+        const ViewDesc &c = vt.v[(int)(rec / ld)];
+        const float2 p = xy[rec];
+        const float4 q = co[rec];
+        const Rect rc = tile_rect(p.x, p.y, radius[rec], vt.tile_w, vt.tile_h, c.GW, c.GH);
+        for (int i = threadIdx.x; i < nt; i += blockDim.x)
+            emit_one(o0 + (uint32_t)i, r, i, rc.x0, rc.y0, rc.x1 - rc.x0, c.tile_offset, c.GW, p, q, vt, alpha_min,
+                     pkey, pval);
+    }
+}
+
+// Final pass over the sorted pairs: Gaussian ids, tile ranges, and the block
+// masks carried in the keys' top byte.
 __global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ pkey, const uint32_t *__restrict__ pval,
                                                  const uint32_t *__restrict__ sorted_rec,
                                                  const int *__restrict__ counts, int *__restrict__ ids,
-                                                 int2 *__restrict__ ranges, const float2 *__restrict__ xy,
-                                                 const float4 *__restrict__ co, ViewTable vt, float alpha_min,
-                                                 uint8_t *__restrict__ masks) {
+                                                 int2 *__restrict__ ranges, uint8_t *__restrict__ masks) {
     const long long P = counts[1];
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
-        const uint32_t t = pkey[p];
-        const int g = (int)sorted_rec[pval[p]];
-        ids[p] = g;
-        if (p == 0 || pkey[p - 1] != t) ranges[t].x = (int)p;
-        if (p == P - 1 || pkey[p + 1] != t) ranges[t].y = (int)(p + 1);
-        const int v = view_of_tile(vt, (int)t);
-        const ViewDesc &c = vt.v[v];
-        const int local = (int)t - c.tile_offset;
-        const int ty = local / c.GW, tx = local - ty * c.GW;
-        masks[p] = (uint8_t)block_mask8(xy[g], co[g], alpha_min, tx * vt.tile_w, ty * vt.tile_h, vt.tile_w);
+        const uint32_t key = pkey[p];
+        const uint32_t t = key & 0xffffffu;
+        ids[p] = (int)sorted_rec[pval[p]];
+        masks[p] = (uint8_t)(key >> 24);
+        if (p == 0 || (pkey[p - 1] & 0xffffffu) != t) ranges[t].x = (int)p;
+        if (p == P - 1 || (pkey[p + 1] & 0xffffffu) != t) ranges[t].y = (int)(p + 1);
     }
 }
 
@@ -340,7 +449,7 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ pke
 struct SortWs {
     unsigned long long *blk;
     uint32_t *hist, *dtotal;
-    uint32_t *dk0, *dv0, *dk1, *dv1, *off;
+    uint32_t *dk0, *dv0, *dk1, *dv1, *off, *big;
     uint32_t *pk0, *pv0, *pk1, *pv1;
     size_t bytes;
 };
@@ -362,6 +471,7 @@ static SortWs carve(void *base, long long nrec, long long max_pairs) {
     w.dk1 = (uint32_t *)take(sizeof(uint32_t) * nrec);
     w.dv1 = (uint32_t *)take(sizeof(uint32_t) * nrec);
     w.off = (uint32_t *)take(sizeof(uint32_t) * (nrec + 1));
+    w.big = (uint32_t *)take(sizeof(uint32_t) * (nrec + 1));
     w.pk0 = (uint32_t *)take(sizeof(uint32_t) * max_pairs);
     w.pv0 = (uint32_t *)take(sizeof(uint32_t) * max_pairs);
     w.pk1 = (uint32_t *)take(sizeof(uint32_t) * max_pairs);
@@ -413,12 +523,15 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
     k_tiles_count<<<kSortBlocks, kSortThreads, 0, s>>>(sorted_rec, touched, counts, w.blk);
     k_scan_blocks<<<1, kSortBlocks, 0, s>>>(w.blk, 1, counts, max_pairs, status);
     k_tiles_offsets<<<kSortBlocks, kSortThreads, 0, s>>>(sorted_rec, touched, counts, w.blk, w.off);
-    k_emit_pairs<<<148 * 16, 256, 0, s>>>(sorted_rec, w.off, radius, xy, ld, vt, counts, w.pk0, w.pv0);
+    k_emit_pairs<<<148 * 16, 256, 0, s>>>(sorted_rec, w.off, radius, xy, co, ld, vt, alpha_min, counts, w.big, w.pk0,
+                                          w.pv0);
+    k_emit_big<<<148 * 4, 256, 0, s>>>(sorted_rec, w.off, radius, xy, co, ld, vt, alpha_min, counts, w.big, w.pk0,
+                                       w.pv0);
     int tile_bits = 0;
     while ((1ll << tile_bits) < (long long)vt.total_tiles) ++tile_bits;
     const int pres = radix_sort(w.pk0, w.pv0, w.pk1, w.pv1, counts + 1, tile_bits, w.hist, w.dtotal, s);
     k_ranges<<<148 * 8, 256, 0, s>>>(pres ? w.pk1 : w.pk0, pres ? w.pv1 : w.pv0, sorted_rec, counts, gauss_ids,
-                                     tile_ranges, xy, co, vt, alpha_min, block_mask);
+                                     tile_ranges, block_mask);
     return cudaGetLastError();
 }
 

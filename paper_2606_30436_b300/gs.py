@@ -484,12 +484,12 @@ class MappingStep:
 
 def launches_per_step(total_tiles, views=1, lambda_dssim=0.2):
     """Kernel launches of the library in one mapping iteration (memsets not
-    counted): project 1; sort 3 + 3x4 depth passes + 4 + 3 per tile-bit pass
+    counted): project 1; sort 3 + 3x4 depth passes + 5 + 3 per tile-bit pass
     + 1; render 1; loss 3 (2 when lambda = 0) per view; backward 2; Adam 1."""
     tile_bits = 0
     while (1 << tile_bits) < total_tiles:
         tile_bits += 1
     tile_passes = (tile_bits + 7) // 8
-    sort = 3 + 3 * 4 + 4 + 3 * tile_passes + 1
+    sort = 3 + 3 * 4 + 5 + 3 * tile_passes + 1
     loss = (3 if lambda_dssim > 0 else 2) * views
     return 1 + sort + 1 + loss + 2 + 1

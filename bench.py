@@ -53,12 +53,22 @@ def frame_pool(n):
 # algorithmic bytes (minimum HBM traffic the method implies, FP32)
 
 def algorithmic_bytes(N, V, P, px, tiles, K):
+    """Minimum HBM bytes of each stage of one iteration (every buffer the
+    method needs touched once): N Gaussians, V visible records, P pairs,
+    px pixels, K floats per Gaussian."""
     return {
-        "project": 12 * N + 4 * (K - 3) * V + 56 * V + 4 * N,
+        # means of all (cull), the rest of the parameters of the visible, 48-byte records, counts
+        "project": 12 * N + 4 * (K - 3) * V + 48 * V + 8 * N,
+        # compaction, depth keys, pair emission, one read + write of the pair list, ranges
         "sort": 8 * N + 16 * V + 12 * P + 24 * P + 8 * P + 8 * tiles,
-        "render_fwd": 40 * P + 20 * px,
+        # per pair: id, mask, 40-byte record; per pixel: colour, T_final, last
+        "render_fwd": 45 * P + 20 * px,
         "loss": 36 * px,
-        "render_bwd": 40 * P + 32 * px + 36 * V + 4 * K * V + 4 * K * N + 32 * V,
+        # per pair: id, mask, record; per pixel: dL/dI, T_final, last, image, target;
+        # 13 accumulator planes of every visible record
+        "render_bwd": 45 * P + 44 * px + 52 * V,
+        # accumulators and parameters of the visible, gradient planes of all
+        "project_bwd": 52 * V + 4 * K * V + 4 * K * N,
         "adam": 28 * K * N,
     }
 
@@ -160,9 +170,9 @@ def committed_traffic(kernel):
 # --------------------------------------------------------------------------
 # GPU arm
 
-STAGES = ["project", "sort", "render_fwd", "loss", "render_bwd", "adam"]
+STAGES = ["project", "sort", "render_fwd", "loss", "render_bwd", "project_bwd", "adam"]
 STAGE_KERNEL = {"project": "k_project", "sort": None, "render_fwd": "k_render_fwd", "loss": None,
-                "render_bwd": "k_render_bwd", "adam": "k_adam"}
+                "render_bwd": "k_render_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam"}
 
 
 def eager_step(gs, step, target, events=None, stream=None):
@@ -178,11 +188,13 @@ def eager_step(gs, step, target, events=None, stream=None):
     rec(3)
     gs.gs_loss(b, target, step.lambda_dssim)
     rec(4)
-    gs.gs_render_bwd(step.model, step.grads, b, target, step.tau_err, with_stats=step.with_stats)
+    gs.gs_render_bwd(step.model, None, b, target, step.tau_err, with_stats=step.with_stats)
     rec(5)
+    gs.gs_project_bwd(step.model, step.grads, b, with_stats=step.with_stats)
+    rec(6)
     step.step_count += 1
     gs.gs_adam(step.model, step.grads, step.exp_avg, step.exp_avg_sq, step.lr, step.step_count)
-    rec(6)
+    rec(7)
 
 
 def render_targets(gs, tscene, cams_list, cfg, dev):
@@ -198,6 +210,21 @@ def render_targets(gs, tscene, cams_list, cfg, dev):
     del tmodel
     torch.cuda.synchronize()
     return out
+
+
+def max_over_ranks(values, world, device="cpu"):
+    """Per-rank timings -> their maximum over the ranks (all-reduce MAX)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def replica_throughput(steps, world, ms):
+    """Whole-job iterations per second: every replica ran `steps` iterations,
+    the job took the slowest replica's `ms`."""
+    return world * steps / (ms * 1e-3)
 
 
 def barrier(world):
@@ -259,7 +286,7 @@ def run_corridor(args, world, dev):
     step.check_status()
 
     # per-stage timing (eager launches, events between the C-ABI calls)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(args.steps)]
     barrier(world)
     for i in range(args.steps):
         k = i % len(cams)
@@ -289,10 +316,7 @@ def run_corridor(args, world, dev):
     e2e_ms = e0.elapsed_time(e1)
     wall_e2e = time.perf_counter() - t0
 
-    ms_t = torch.tensor([ms, e2e_ms], device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms, e2e_ms = float(ms_t[0]), float(ms_t[1])
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], world, device=dev)
 
     Vm, Pm = float(np.mean(vis)), float(np.mean(needed))
     ab = algorithmic_bytes(N_GAUSS, Vm, Pm, W * H, step.buf.total_tiles, model.K)
@@ -304,14 +328,14 @@ def run_corridor(args, world, dev):
             "frac": round(achieved / peak, 4), "traffic": committed_traffic(kern),
             "peak_kind": peak_kind + " (copy bandwidth)",
             "algorithmic_bytes_per_launch": int(ab[dom]), "launch_ms": round(stage_ms[dom], 4)}
-    value = world * args.steps / (ms * 1e-3)
+    value = replica_throughput(args.steps, world, ms)
     total_bytes = sum(ab.values())
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(len(frames)),
-        "e2e": {"value": round(world * args.steps / (e2e_ms * 1e-3), 3), "unit": UNIT,
+        "e2e": {"value": round(replica_throughput(args.steps, world, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": 3 * W * H * 4, "d2h_bytes_per_step": 4, "wall_s": round(wall_e2e, 3)},
         "gpu_launches": gs.launches_per_step(step.buf.total_tiles, views=1, lambda_dssim=LAMBDA) * args.steps,
         "roofline": roof,

@@ -117,6 +117,9 @@ typedef struct {
                               alpha_min ellipse can reach the tile's 8x4 pixel
                               block b (blocks row-major, tile_w/8 per row); a
                               clear bit proves alpha < alpha_min on that block */
+    int32_t *tile_order;   /* [total_tiles] the tiles ordered by decreasing pair
+                              count (power-of-two classes): the order in which the
+                              compositing kernels start them */
     int64_t max_pairs;
 } gs_binning;
 
@@ -197,8 +200,8 @@ gs_status gs_project(const gs_params *params, const gs_camera *cams, int32_t n_v
  * Binning: one pair per (visible record, overlapped tile), ordered by
  * (global tile, camera depth, Gaussian index) -- the "sorted Gaussians along
  * the ray" of Supp. D.2 -- and the per-tile ranges.  Writes
- * binning->counts, gauss_ids[0..pairs), block_mask[0..pairs) and
- * tile_ranges (cfg->alpha_min sets the masks).  When the pairs
+ * binning->counts, gauss_ids[0..pairs), block_mask[0..pairs), tile_ranges
+ * and tile_order (cfg->alpha_min sets the masks).  When the pairs
  * exceed max_pairs, no pair is written, counts[1] = 0, counts[2] = pairs
  * needed and status gets bit 1<<GS_ERR_CAPACITY.  ws: gs_sort_workspace_size
  * bytes (256-byte aligned).
@@ -254,9 +257,14 @@ gs_status gs_loss_static(const float *img, const float *target, const gs_camera 
 /*
  * Backward of compositing and projection: traverses each tile back to front
  * from the pixel's last blended pair, recovers T_j = T_{j+1} / (1 - alpha_j),
- * and accumulates dL/d(u, v, conic, opacity, colour, depth) per record; then
- * chains through the projection to every parameter plane.  grads (same layout
- * as params) is overwritten, or accumulated into when accumulate != 0.
+ * and accumulates dL/d(u, v, conic, opacity, colour, depth) per record into
+ * the workspace; then chains through the projection to every parameter plane
+ * (as gs_project_bwd).  grads (same layout as params) is overwritten, or
+ * accumulated into when accumulate != 0; with grads = NULL only the
+ * compositing half runs and the per-record gradients stay in ws (record r's
+ * plane p at float index p * n_records + r, planes dL/du, dL/dv, dL/da,
+ * dL/db, dL/dc, dL/dopacity, dL/dr, dL/dg, dL/db, dL/dz, |Omega_v|, kappa_v,
+ * max T*alpha).
  * dL_ddepth is nullable.  stats (nullable) receives the lifecycle
  * accumulators (Supp. E.1, E.2): per pixel the error mask
  * M_v = [sum_c |I - I^| > tau_err] (tau_err = 0.1, Supp. F) with the
@@ -269,6 +277,18 @@ gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, int32_t 
                         const float *dL_ddepth, const float *target, const float *loss_per_view,
                         float tau_err, const gs_params *grads, int32_t accumulate,
                         const gs_stats *stats, void *ws, size_t ws_bytes, gs_stream stream);
+
+/*
+ * The projection half of gs_render_bwd: chain rule from the per-record
+ * screen-space gradients in ws (left by gs_render_bwd with grads = NULL)
+ * through colour (SH), opacity, the EWA covariance and the pinhole
+ * projection to every parameter plane; folds the lifecycle statistics into
+ * stats (nullable) as gs_render_bwd does.
+ */
+gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                         const gs_raster_cfg *cfg, const gs_projected *proj, const void *ws, size_t ws_bytes,
+                         const float *loss_per_view, const gs_params *grads, int32_t accumulate,
+                         const gs_stats *stats, gs_stream stream);
 
 /*
  * Adam (Kingma & Ba) with bias correction over every parameter plane, dense:

@@ -83,7 +83,7 @@ gs_status check_proj(const gs_projected *pr, long long ld) {
 }
 
 gs_status check_binning(const gs_binning *b) {
-    if (!b || !b->gauss_ids || !b->tile_ranges || !b->counts || !b->block_mask || b->max_pairs < 0 ||
+    if (!b || !b->gauss_ids || !b->tile_ranges || !b->counts || !b->block_mask || !b->tile_order || b->max_pairs < 0 ||
         b->max_pairs > 0x7fffffffll)
         return GS_ERR_INVALID;
     if (((uintptr_t)b->tile_ranges & 7u) != 0 || !aligned16(b->block_mask)) return GS_ERR_INVALID;
@@ -184,7 +184,8 @@ GS_API gs_status gs_sort(const gs_projected *proj, const gs_camera *cams, int32_
     return cuda_status(launch_sort(proj->radius, proj->tiles_touched, (const float2 *)proj->xy,
                                    (const float4 *)proj->conic_opacity, (const float4 *)proj->rgb_depth, nrec,
                                    proj->ld, vt, rc.alpha_min, binning->gauss_ids, (int2 *)binning->tile_ranges,
-                                   binning->block_mask, binning->counts, binning->max_pairs, ws, status,
+                                   binning->block_mask, binning->tile_order, binning->counts, binning->max_pairs, ws,
+                                   status,
                                    (cudaStream_t)stream));
 }
 
@@ -198,7 +199,7 @@ GS_API gs_status gs_render_fwd(const gs_projected *proj, const gs_binning *binni
     if ((st = check_binning(binning)) != GS_OK) return st;
     if (!frame || !frame->img || !frame->T_final || !frame->last) return GS_ERR_INVALID;
     launch_render_fwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, binning->block_mask,
-                      (const float2 *)proj->xy,
+                      binning->tile_order, (const float2 *)proj->xy,
                       (const float4 *)proj->conic_opacity, (const float4 *)proj->rgb_depth, frame->img,
                       frame->T_final, frame->last, frame->depth, (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
@@ -253,9 +254,10 @@ GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, i
     RasterCfg rc;
     gs_status st = build_views(cams, n_views, cfg, vt, rc);
     if (st == GS_OK) st = check_params(params);
-    if (st == GS_OK) st = check_params(grads);
+    if (st == GS_OK && grads) st = check_params(grads);
     if (st != GS_OK) return st;
-    if (grads->ld != params->ld || grads->n != params->n || grads->sh_degree != params->sh_degree) return GS_ERR_INVALID;
+    if (grads && (grads->ld != params->ld || grads->n != params->n || grads->sh_degree != params->sh_degree))
+        return GS_ERR_INVALID;
     if (!proj || check_proj(proj, params->ld) != GS_OK || check_binning(binning) != GS_OK) return GS_ERR_INVALID;
     if (!frame || !frame->img || !frame->T_final || !frame->last || !dL_dimg) return GS_ERR_INVALID;
     const bool want_stats = stats != nullptr;
@@ -269,12 +271,36 @@ GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, i
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)kAccPlanes * nrec, s);
     if (e != cudaSuccess) return GS_ERR_CUDA;
     launch_render_bwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, binning->block_mask,
-                      (const float2 *)proj->xy,
+                      binning->tile_order, (const float2 *)proj->xy,
                       (const float4 *)proj->conic_opacity, (const float4 *)proj->rgb_depth, frame->img,
                       frame->T_final, frame->last, dL_dimg, dL_ddepth, target, tau_err, want_stats, acc, nrec, s);
-    launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius, acc, nrec,
-                       grads->data, accumulate, loss_per_view, want_stats ? stats->acc : nullptr,
-                       want_stats ? stats->ld : 0, s);
+    if (grads)
+        launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius, acc, nrec,
+                           grads->data, accumulate, loss_per_view, want_stats ? stats->acc : nullptr,
+                           want_stats ? stats->ld : 0, s);
+    return cuda_status(cudaGetLastError());
+}
+
+GS_API gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                                const gs_raster_cfg *cfg, const gs_projected *proj, const void *ws, size_t ws_bytes,
+                                const float *loss_per_view, const gs_params *grads, int32_t accumulate,
+                                const gs_stats *stats, gs_stream stream) {
+    ViewTable vt;
+    RasterCfg rc;
+    gs_status st = build_views(cams, n_views, cfg, vt, rc);
+    if (st == GS_OK) st = check_params(params);
+    if (st == GS_OK) st = check_params(grads);
+    if (st != GS_OK) return st;
+    if (grads->ld != params->ld || grads->n != params->n || grads->sh_degree != params->sh_degree) return GS_ERR_INVALID;
+    if (!proj || check_proj(proj, params->ld) != GS_OK) return GS_ERR_INVALID;
+    if (stats && (!stats->acc || stats->ld < params->n)) return GS_ERR_INVALID;
+    const long long nrec = (long long)n_views * params->ld;
+    size_t need = 0;
+    gs_bwd_workspace_size(nrec, &need);
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < need) return GS_ERR_INVALID;
+    launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius,
+                       (const float *)ws, nrec, grads->data, accumulate, loss_per_view,
+                       stats ? stats->acc : nullptr, stats ? stats->ld : 0, (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
 }
 

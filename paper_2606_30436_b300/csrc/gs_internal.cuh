@@ -114,8 +114,7 @@ __device__ __forceinline__ Reach reach_box(float2 p, float4 q, float alpha_min) 
 // Bit b (b = 0..7) set when the Gaussian can reach block b of the tile whose
 // first pixel is (x0, y0); blocks are 8 wide and 4 tall, row-major, tile_w/8
 // per row.
-__device__ __forceinline__ uint32_t block_mask8(float2 p, float4 q, float alpha_min, int x0, int y0, int tile_w) {
-    const Reach r = reach_box(p, q, alpha_min);
+__device__ __forceinline__ uint32_t block_mask_of(const Reach &r, int x0, int y0, int tile_w) {
     if (!r.any) return 0u;
     if (r.all) return 0xffu;
     const int ncols = tile_w >> 3;
@@ -128,6 +127,10 @@ __device__ __forceinline__ uint32_t block_mask8(float2 p, float4 q, float alpha_
         if (lx1 >= bx && lx0 <= bx + 7.0f && ly1 >= by && ly0 <= by + 3.0f) m |= 1u << b;
     }
     return m;
+}
+
+__device__ __forceinline__ uint32_t block_mask8(float2 p, float4 q, float alpha_min, int x0, int y0, int tile_w) {
+    return block_mask_of(reach_box(p, q, alpha_min), x0, y0, tile_w);
 }
 
 // Bytes of the per-pair block-mask array for max_pairs pairs: the render

@@ -25,15 +25,15 @@ void launch_project_bwd(const float *P, long long n, long long ld, int D, const 
 size_t sort_workspace_bytes(long long nrec, long long max_pairs);
 cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy, const float4 *co, const float4 *rgbd,
                         long long nrec, long long ld, const ViewTable &vt, float alpha_min, int *gauss_ids,
-                        int2 *tile_ranges, uint8_t *block_mask, int *counts, long long max_pairs, void *ws,
-                        int *status, cudaStream_t s);
+                        int2 *tile_ranges, uint8_t *block_mask, int *tile_order, int *counts, long long max_pairs,
+                        void *ws, int *status, cudaStream_t s);
 
 void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
-                       const uint8_t *masks, const float2 *xy, const float4 *co, const float4 *rgbd, float *img,
-                       float *T_final, int *last, float *depth, cudaStream_t s);
+                       const uint8_t *masks, const int *order, const float2 *xy, const float4 *co, const float4 *rgbd,
+                       float *img, float *T_final, int *last, float *depth, cudaStream_t s);
 
 void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
-                       const uint8_t *masks, const float2 *xy, const float4 *co, const float4 *rgbd,
+                       const uint8_t *masks, const int *order, const float2 *xy, const float4 *co, const float4 *rgbd,
                        const float *img, const float *T_final,
                        const int *last, const float *dL_dimg, const float *dL_ddepth, const float *target,
                        float tau_err, bool stats, float *acc, long long nrec, cudaStream_t s);

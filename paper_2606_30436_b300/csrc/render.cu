@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_fwd(ViewTable vt, Raster
                                                               const int2 *__restrict__ ranges,
                                                               const int *__restrict__ ids,
                                                               const uint8_t *__restrict__ masks,
+                                                              const int *__restrict__ order,
                                                               const float2 *__restrict__ xy,
                                                               const float4 *__restrict__ co,
                                                               const float4 *__restrict__ rgbd,
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_fwd(ViewTable vt, Raster
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int unit = blockIdx.x * kWarps + warp;
     if (unit >= vt.total_tiles * 8) return;
-    const int tile = unit >> 3, bit = unit & 7;
+    const int tile = order[unit >> 3], bit = unit & 7;  // longest tiles first
     const Unit t = unit_ctx(vt, tile, bit);
     const int2 rg = ranges[tile];
     const float fx = t.px + 0.5f, fy = t.py + 0.5f;
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
                                                               const int2 *__restrict__ ranges,
                                                               const int *__restrict__ ids,
                                                               const uint8_t *__restrict__ masks,
+                                                              const int *__restrict__ order,
                                                               const float2 *__restrict__ xy,
                                                               const float4 *__restrict__ co,
                                                               const float4 *__restrict__ rgbd,
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int unit = blockIdx.x * kWarps + warp;
     if (unit >= vt.total_tiles * 8) return;
-    const int tile = unit >> 3, bit = unit & 7;
+    const int tile = order[unit >> 3], bit = unit & 7;  // longest tiles first
     const Unit t = unit_ctx(vt, tile, bit);
     const int2 rg = ranges[tile];
     const float fx = t.px + 0.5f, fy = t.py + 0.5f;
@@ -382,12 +384,12 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
 }
 
 void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
-                       const uint8_t *masks, const float2 *xy, const float4 *co, const float4 *rgbd, float *img,
-                       float *T_final, int *last, float *depth, cudaStream_t s) {
+                       const uint8_t *masks, const int *order, const float2 *xy, const float4 *co,
+                       const float4 *rgbd, float *img, float *T_final, int *last, float *depth, cudaStream_t s) {
     const long long units = 8ll * vt.total_tiles;
     if (units <= 0) return;
     const unsigned grid = (unsigned)ceil_div(units, kWarps);
-#define GS_FWD(WN) k_render_fwd<WN><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd, img, \
+#define GS_FWD(WN) k_render_fwd<WN><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, order, xy, co, rgbd, img, \
                                                                  T_final, last, depth)
     if (cfg.batch == 128) GS_FWD(128);
     else if (cfg.batch == 256) GS_FWD(256);
@@ -396,16 +398,16 @@ void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ra
 }
 
 void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
-                       const uint8_t *masks, const float2 *xy, const float4 *co, const float4 *rgbd,
-                       const float *img, const float *T_final, const int *last, const float *dL_dimg,
+                       const uint8_t *masks, const int *order, const float2 *xy, const float4 *co,
+                       const float4 *rgbd, const float *img, const float *T_final, const int *last, const float *dL_dimg,
                        const float *dL_ddepth, const float *target, float tau_err, bool stats, float *acc,
                        long long nrec, cudaStream_t s) {
     const long long units = 8ll * vt.total_tiles;
     if (units <= 0) return;
     const unsigned grid = (unsigned)ceil_div(units, kWarps);
-#define GS_BWD(ST, WN) k_render_bwd<ST, WN><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd, \
-                                                                         img, T_final, last, dL_dimg, dL_ddepth, \
-                                                                         target, tau_err, acc, nrec)
+#define GS_BWD(ST, WN) k_render_bwd<ST, WN><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, order, xy, co, \
+                                                                         rgbd, img, T_final, last, dL_dimg, \
+                                                                         dL_ddepth, target, tau_err, acc, nrec)
     if (stats) {
         if (cfg.batch == 128) GS_BWD(true, 128);
         else if (cfg.batch == 256) GS_BWD(true, 256);

@@ -13,6 +13,8 @@
 // 12 bytes over ceil((32 + tile_bits) / 8) passes for the 64-bit key.
 // Every kernel reads its element count from device memory and runs on a fixed
 // grid, so the sequence needs no host synchronisation and can be captured.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 #include "gs_kernels.h"
 
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kSortBlocks) k_radix_scan(uint32_t *__restrict
 constexpr int kDownItems = 16;
 constexpr int kDownTile = kSortThreads * kDownItems;  // 4096
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_downsweep(const uint32_t *__restrict__ kin,
+__global__ void __launch_bounds__(kSortThreads, 3) k_radix_downsweep(const uint32_t *__restrict__ kin,
                                                                    const uint32_t *__restrict__ vin,
                                                                    uint32_t *__restrict__ kout,
                                                                    uint32_t *__restrict__ vout,
@@ -320,10 +322,10 @@ constexpr int kBigRecord = 128;  // records overlapping more tiles are emitted b
 // list for k_emit_big, so no warp is left with a near-camera Gaussian's
 // thousands of tiles.
 __device__ __forceinline__ void emit_one(uint32_t o, uint32_t rank, int i, int x0, int y0, int w, int toff, int gw,
-                                         float2 p, float4 q, const ViewTable &vt, float alpha_min,
+                                         const Reach &rb, const ViewTable &vt,
                                          uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
     const int ty = y0 + i / w, tx = x0 + i % w;
-    const uint32_t m = block_mask8(p, q, alpha_min, tx * vt.tile_w, ty * vt.tile_h, vt.tile_w);
+    const uint32_t m = block_mask_of(rb, tx * vt.tile_w, ty * vt.tile_h, vt.tile_w);
     pkey[o] = (uint32_t)(toff + ty * gw + tx) | (m << 24);
     pval[o] = rank;
 }
@@ -345,8 +347,10 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t *__restrict__
         const bool valid = r < V;
         uint32_t my_off = 0;
         int x0 = 0, y0 = 0, w = 1, toff = 0, gw = 1, n_small = 0;
-        float2 p = make_float2(0.f, 0.f);
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        Reach rb;  // the record's alpha >= alpha_min box, computed once per record
+        rb.cx = rb.cy = rb.ex = rb.ey = 0.0f;
+        rb.any = false;
+        rb.all = false;
         if (valid) {
             const uint32_t rec = sorted_rec[r];
             my_off = off[r];
@@ -355,13 +359,14 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t *__restrict__
                 big[atomicAdd(&counts[3], 1)] = (uint32_t)r;
             } else {
                 const ViewDesc &c = vt.v[(int)(rec / ld)];
-                p = xy[rec];
-                q = co[rec];
+                const float2 p = xy[rec];
+                rb = reach_box(p, co[rec], alpha_min);
                 const Rect rc = tile_rect(p.x, p.y, radius[rec], vt.tile_w, vt.tile_h, c.GW, c.GH);
                 x0 = rc.x0; y0 = rc.y0; w = rc.x1 - rc.x0; toff = c.tile_offset; gw = c.GW;
                 n_small = nt;
             }
         }
+        const int flags = (rb.any ? 1 : 0) | (rb.all ? 2 : 0);
         // running count of small-record slots over the lanes
         int inc = n_small;
         #pragma unroll
@@ -388,15 +393,15 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t *__restrict__
             const int jx0 = __shfl_sync(0xffffffffu, x0, j), jy0 = __shfl_sync(0xffffffffu, y0, j);
             const int jw = __shfl_sync(0xffffffffu, w, j), jtoff = __shfl_sync(0xffffffffu, toff, j);
             const int jgw = __shfl_sync(0xffffffffu, gw, j), jn = __shfl_sync(0xffffffffu, n_small, j);
-            float2 jp;
-            float4 jq;
-            jp.x = __shfl_sync(0xffffffffu, p.x, j); jp.y = __shfl_sync(0xffffffffu, p.y, j);
-            jq.x = __shfl_sync(0xffffffffu, q.x, j); jq.y = __shfl_sync(0xffffffffu, q.y, j);
-            jq.z = __shfl_sync(0xffffffffu, q.z, j); jq.w = __shfl_sync(0xffffffffu, q.w, j);
+            Reach jr;
+            jr.cx = __shfl_sync(0xffffffffu, rb.cx, j); jr.cy = __shfl_sync(0xffffffffu, rb.cy, j);
+            jr.ex = __shfl_sync(0xffffffffu, rb.ex, j); jr.ey = __shfl_sync(0xffffffffu, rb.ey, j);
+            const int jf = __shfl_sync(0xffffffffu, flags, j);
+            jr.any = jf & 1;
+            jr.all = (jf & 2) != 0;
             if (c < total && c - ej < jn) {
                 const int i = c - ej;
-                emit_one(oj + (uint32_t)i, (uint32_t)(r0 + j), i, jx0, jy0, jw, jtoff, jgw, jp, jq, vt, alpha_min,
-                         pkey, pval);
+                emit_one(oj + (uint32_t)i, (uint32_t)(r0 + j), i, jx0, jy0, jw, jtoff, jgw, jr, vt, pkey, pval);
             }
         }
     }
@@ -420,9 +425,9 @@ __global__ void __launch_bounds__(256) k_emit_big(const uint32_t *__restrict__ s
         const float2 p = xy[rec];
         const float4 q = co[rec];
         const Rect rc = tile_rect(p.x, p.y, radius[rec], vt.tile_w, vt.tile_h, c.GW, c.GH);
+        const Reach rb = reach_box(p, q, alpha_min);
         for (int i = threadIdx.x; i < nt; i += blockDim.x)
-            emit_one(o0 + (uint32_t)i, r, i, rc.x0, rc.y0, rc.x1 - rc.x0, c.tile_offset, c.GW, p, q, vt, alpha_min,
-                     pkey, pval);
+            emit_one(o0 + (uint32_t)i, r, i, rc.x0, rc.y0, rc.x1 - rc.x0, c.tile_offset, c.GW, rb, vt, pkey, pval);
     }
 }
 
@@ -444,10 +449,51 @@ __global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ pke
 }
 
 // ---------------------------------------------------------------------------
+// render schedule: tiles by descending pair count (log2 buckets), so the
+// compositing kernels start the longest tiles first and their chains overlap
+// the many short tiles instead of trailing them.
+
+__global__ void __launch_bounds__(256) k_tile_hist(const int2 *__restrict__ ranges, int total_tiles,
+                                                    unsigned int *__restrict__ bucket) {
+    __shared__ unsigned int h[33];
+    if (threadIdx.x < 33) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x) {
+        const int2 r = ranges[t];
+        const unsigned c = (unsigned)(r.y - r.x);
+        atomicAdd(&h[c ? 32 - __clz(c) : 0], 1u);  // 0 for empty, 1 + floor(log2 c) otherwise
+    }
+    __syncthreads();
+    if (threadIdx.x < 33 && h[threadIdx.x]) atomicAdd(&bucket[threadIdx.x], h[threadIdx.x]);
+}
+
+// cursors: bucket 32 (longest) first
+__global__ void k_tile_scan(unsigned int *__restrict__ bucket) {
+    if (threadIdx.x == 0) {
+        unsigned int run = 0;
+        for (int b = 32; b >= 0; --b) {
+            const unsigned int c = bucket[b];
+            bucket[b] = run;
+            run += c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_tile_scatter(const int2 *__restrict__ ranges, int total_tiles,
+                                                       unsigned int *__restrict__ bucket, int *__restrict__ order) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x) {
+        const int2 r = ranges[t];
+        const unsigned c = (unsigned)(r.y - r.x);
+        order[atomicAdd(&bucket[c ? 32 - __clz(c) : 0], 1u)] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 
 struct SortWs {
     unsigned long long *blk;
+    unsigned int *bucket;
     uint32_t *hist, *dtotal;
     uint32_t *dk0, *dv0, *dk1, *dv1, *off, *big;
     uint32_t *pk0, *pv0, *pk1, *pv1;
@@ -464,6 +510,7 @@ static SortWs carve(void *base, long long nrec, long long max_pairs) {
         return p;
     };
     w.blk = (unsigned long long *)take(sizeof(unsigned long long) * (kSortBlocks + 1));
+    w.bucket = (unsigned int *)take(sizeof(unsigned int) * 64);
     w.hist = (uint32_t *)take(sizeof(uint32_t) * 256 * kSortBlocks);
     w.dtotal = (uint32_t *)take(sizeof(uint32_t) * 256);
     w.dk0 = (uint32_t *)take(sizeof(uint32_t) * nrec);
@@ -504,8 +551,8 @@ static int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, co
 
 cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy, const float4 *co, const float4 *rgbd,
                         long long nrec, long long ld, const ViewTable &vt, float alpha_min, int *gauss_ids,
-                        int2 *tile_ranges, uint8_t *block_mask, int *counts, long long max_pairs, void *ws,
-                        int *status, cudaStream_t s) {
+                        int2 *tile_ranges, uint8_t *block_mask, int *tile_order, int *counts, long long max_pairs,
+                        void *ws, int *status, cudaStream_t s) {
     SortWs w = carve(ws, nrec, max_pairs);
     cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -532,6 +579,12 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
     const int pres = radix_sort(w.pk0, w.pv0, w.pk1, w.pv1, counts + 1, tile_bits, w.hist, w.dtotal, s);
     k_ranges<<<148 * 8, 256, 0, s>>>(pres ? w.pk1 : w.pk0, pres ? w.pv1 : w.pv0, sorted_rec, counts, gauss_ids,
                                      tile_ranges, block_mask);
+    e = cudaMemsetAsync(w.bucket, 0, sizeof(unsigned int) * 64, s);
+    if (e != cudaSuccess) return e;
+    const int tb = (int)std::min<long long>(ceil_div(vt.total_tiles, 256), 148 * 4);
+    k_tile_hist<<<tb, 256, 0, s>>>(tile_ranges, vt.total_tiles, w.bucket);
+    k_tile_scan<<<1, 32, 0, s>>>(w.bucket);
+    k_tile_scatter<<<tb, 256, 0, s>>>(tile_ranges, vt.total_tiles, w.bucket, tile_order);
     return cudaGetLastError();
 }
 

@@ -55,7 +55,7 @@ class Projected(C.Structure):
 
 class Binning(C.Structure):
     _fields_ = [("gauss_ids", C.c_void_p), ("tile_ranges", C.c_void_p), ("counts", C.c_void_p),
-                ("block_mask", C.c_void_p), ("max_pairs", C.c_int64)]
+                ("block_mask", C.c_void_p), ("tile_order", C.c_void_p), ("max_pairs", C.c_int64)]
 
 
 class Frame(C.Structure):
@@ -74,7 +74,7 @@ class ChunkScores(C.Structure):
 EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspace_size", "gs_block_mask_size",
            "gs_loss_workspace_size",
            "gs_bwd_workspace_size", "gs_prune_workspace_size", "gs_project", "gs_sort", "gs_render_fwd", "gs_loss",
-           "gs_render_bwd", "gs_adam", "gs_prune_stats", "gs_loss_static")
+           "gs_render_bwd", "gs_project_bwd", "gs_adam", "gs_prune_stats", "gs_loss_static")
 
 _lib = None
 
@@ -105,6 +105,8 @@ def lib():
         L.gs_loss_static.argtypes = [vp, vp, P(Camera), i32, f32, vp, vp, vp]
         L.gs_render_bwd.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), P(Binning), P(Frame),
                                     vp, vp, vp, vp, f32, P(Params), i32, P(Stats), vp, sz, vp]
+        L.gs_project_bwd.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), vp, sz, vp, P(Params), i32,
+                                     P(Stats), vp]
         L.gs_adam.argtypes = [P(Params), P(Params), P(Params), P(Params), P(f32 * 6), f32, f32, f32, i64, vp, vp]
         L.gs_prune_stats.argtypes = [P(Stats), i64, i32, f32, f32, P(ChunkScores), vp, sz, vp]
         for name in EXPORTS:
@@ -257,6 +259,7 @@ class Buffers:
         self.counts = torch.zeros(4, dtype=i32, device=dev)
         self.status = torch.zeros(1, dtype=i32, device=dev)
         self.tile_ranges = torch.zeros(self.total_tiles, 2, dtype=i32, device=dev)
+        self.tile_order = torch.zeros(self.total_tiles, dtype=i32, device=dev)
         self.img = torch.empty(3 * self.total_pixels, dtype=f32, device=dev)
         self.T_final = torch.empty(self.total_pixels, dtype=f32, device=dev)
         self.last = torch.empty(self.total_pixels, dtype=i32, device=dev)
@@ -283,7 +286,7 @@ class Buffers:
 
     def binning(self) -> Binning:
         return Binning(self.gauss_ids.data_ptr(), self.tile_ranges.data_ptr(), self.counts.data_ptr(),
-                       self.block_mask.data_ptr(), self.max_pairs)
+                       self.block_mask.data_ptr(), self.tile_order.data_ptr(), self.max_pairs)
 
     def frame(self) -> Frame:
         return Frame(self.img.data_ptr(), self.T_final.data_ptr(), self.last.data_ptr(),
@@ -353,9 +356,21 @@ def gs_render_bwd(model: GaussianModel, grads: GaussianModel, buf: Buffers, targ
     _check(lib().gs_render_bwd(C.byref(model.c()), arr, buf.n_views, C.byref(buf.cfg.c()), C.byref(buf.projected()),
                                C.byref(buf.binning()), C.byref(buf.frame()),
                                _ptr(buf.dL_dimg if dL_dimg is None else dL_dimg), _ptr(dL_ddepth), _ptr(target),
-                               _ptr(buf.loss), float(tau_err), C.byref(grads.c()), int(bool(accumulate)),
-                               None if st is None else C.byref(st), _ptr(buf.bwd_ws), buf.bwd_ws.numel(),
-                               _stream(stream)), "gs_render_bwd")
+                               _ptr(buf.loss), float(tau_err), None if grads is None else C.byref(grads.c()),
+                               int(bool(accumulate)), None if st is None else C.byref(st), _ptr(buf.bwd_ws),
+                               buf.bwd_ws.numel(), _stream(stream)), "gs_render_bwd")
+
+
+def gs_project_bwd(model: GaussianModel, grads: GaussianModel, buf: Buffers, accumulate=False, with_stats=True,
+                   stream=None):
+    """The projection half of the backward, from the per-record gradients
+    that gs_render_bwd(grads=None) left in the workspace."""
+    arr = camera_array(buf.cams)
+    st = buf.stats() if with_stats else None
+    _check(lib().gs_project_bwd(C.byref(model.c()), arr, buf.n_views, C.byref(buf.cfg.c()), C.byref(buf.projected()),
+                                _ptr(buf.bwd_ws), buf.bwd_ws.numel(), _ptr(buf.loss), C.byref(grads.c()),
+                                int(bool(accumulate)), None if st is None else C.byref(st), _stream(stream)),
+           "gs_project_bwd")
 
 
 def gs_adam(model: GaussianModel, grads: GaussianModel, exp_avg: GaussianModel, exp_avg_sq: GaussianModel, lr,
@@ -485,11 +500,11 @@ class MappingStep:
 def launches_per_step(total_tiles, views=1, lambda_dssim=0.2):
     """Kernel launches of the library in one mapping iteration (memsets not
     counted): project 1; sort 3 + 3x4 depth passes + 5 + 3 per tile-bit pass
-    + 1; render 1; loss 3 (2 when lambda = 0) per view; backward 2; Adam 1."""
+    + 1 + 3 (render schedule); render 1; loss 3 (2 when lambda = 0) per view; backward 2; Adam 1."""
     tile_bits = 0
     while (1 << tile_bits) < total_tiles:
         tile_bits += 1
     tile_passes = (tile_bits + 7) // 8
-    sort = 3 + 3 * 4 + 5 + 3 * tile_passes + 1
+    sort = 3 + 3 * 4 + 5 + 3 * tile_passes + 1 + 3
     loss = (3 if lambda_dssim > 0 else 2) * views
     return 1 + sort + 1 + loss + 2 + 1

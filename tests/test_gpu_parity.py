@@ -391,3 +391,28 @@ def test_graph_replay_matches_eager_steps():
     (le, de), (lg, dg) = runs
     assert np.allclose(le, lg, rtol=1e-5)
     assert np.linalg.norm(dg - de) <= 1e-2 * np.linalg.norm(de)
+
+
+def test_split_backward_and_render_schedule():
+    """gs_render_bwd(grads=NULL) + gs_project_bwd equals the fused call, and
+    tile_order is a permutation of the tiles in non-increasing size classes."""
+    scene, cams = _multi(1, 2000)
+    model = gs.GaussianModel.from_scene(scene)
+    st = gs.MappingStep(model, cams, gs.Config(), lambda_dssim=0.2, with_stats=False)
+    st.fit_capacity()
+    target = torch.rand(3 * st.buf.total_pixels, device="cuda")
+    gs.gs_loss(st.buf, target, 0.2)
+    fused, split = model.like(), model.like()
+    gs.gs_render_bwd(model, fused, st.buf, target, with_stats=False)
+    gs.gs_render_bwd(model, None, st.buf, target, with_stats=False)
+    gs.gs_project_bwd(model, split, st.buf, with_stats=False)
+    torch.cuda.synchronize()
+    a, b = fused.data.cpu().numpy(), split.data.cpu().numpy()
+    assert np.abs(b).max() > 0
+    assert rel_l2(b, a) < 1e-5
+    order = st.buf.tile_order.cpu().numpy()
+    rg = st.buf.tile_ranges.cpu().numpy()
+    assert sorted(order.tolist()) == list(range(st.buf.total_tiles))
+    cnt = rg[order, 1] - rg[order, 0]
+    cls = np.where(cnt > 0, np.floor(np.log2(np.maximum(cnt, 1))) + 1, 0)
+    assert np.all(np.diff(cls) <= 0)

@@ -117,15 +117,17 @@ __device__ __forceinline__ Reach reach_box(float2 p, float4 q, float alpha_min) 
 __device__ __forceinline__ uint32_t block_mask_of(const Reach &r, int x0, int y0, int tile_w) {
     if (!r.any) return 0u;
     if (r.all) return 0xffu;
-    const int ncols = tile_w >> 3;
+    const int ncols = tile_w >> 3, nrows = 8 / ncols;
+    // block column b_x holds pixel indices [8 b_x, 8 b_x + 7]: it meets the box's
+    // span [lx0, lx1] iff b_x in [ceil((lx0 - 7) / 8), floor(lx1 / 8)]
     const float lx0 = r.cx - r.ex - (float)x0, lx1 = r.cx + r.ex - (float)x0;
     const float ly0 = r.cy - r.ey - (float)y0, ly1 = r.cy + r.ey - (float)y0;
+    const int c0 = max(0, (int)ceilf((lx0 - 7.0f) * 0.125f)), c1 = min(ncols - 1, (int)floorf(lx1 * 0.125f));
+    const int r0 = max(0, (int)ceilf((ly0 - 3.0f) * 0.25f)), r1 = min(nrows - 1, (int)floorf(ly1 * 0.25f));
+    if (c0 > c1 || r0 > r1) return 0u;
+    const uint32_t row = ((1u << (c1 + 1)) - 1u) & ~((1u << c0) - 1u);  // columns c0..c1 of one row
     uint32_t m = 0;
-    #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const float bx = 8.0f * (float)(b % ncols), by = 4.0f * (float)(b / ncols);
-        if (lx1 >= bx && lx0 <= bx + 7.0f && ly1 >= by && ly0 <= by + 3.0f) m |= 1u << b;
-    }
+    for (int rr = r0; rr <= r1; ++rr) m |= row << (rr * ncols);
     return m;
 }
 

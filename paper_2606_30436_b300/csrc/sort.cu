@@ -163,13 +163,19 @@ __global__ void __launch_bounds__(kSortBlocks) k_radix_scan(uint32_t *__restrict
 constexpr int kDownItems = 16;
 constexpr int kDownTile = kSortThreads * kDownItems;  // 4096
 
+// With `rec` set (the last pass of the pair sort), the scatter writes the
+// outputs the renderer reads instead of the raw pairs: the Gaussian id
+// rec[value] into vout, the block mask (key >> 24) into masks, and the tile
+// (key & 0xffffff) into kout for the range pass.
 __global__ void __launch_bounds__(kSortThreads, 3) k_radix_downsweep(const uint32_t *__restrict__ kin,
                                                                    const uint32_t *__restrict__ vin,
                                                                    uint32_t *__restrict__ kout,
                                                                    uint32_t *__restrict__ vout,
                                                                    const int *__restrict__ count, int shift, int bits,
                                                                    const uint32_t *__restrict__ hist,
-                                                                   const uint32_t *__restrict__ dtotal) {
+                                                                   const uint32_t *__restrict__ dtotal,
+                                                                   const uint32_t *__restrict__ rec,
+                                                                   uint8_t *__restrict__ masks) {
     __shared__ uint32_t s_base[256];    // global position of this block's next element of each digit
     __shared__ uint32_t s_dstart[256];  // first local slot of each digit in the current round
     __shared__ uint32_t s_whist[kSortThreads / 32][256];
@@ -253,12 +259,23 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_downsweep(const uint3
         }
         __syncthreads();
         const int n_round = (int)min((long long)kDownTile, end - tb);
-        for (int i = threadIdx.x; i < n_round; i += kSortThreads) {
-            const uint32_t key = s_key[i];
-            const uint32_t d = (key >> shift) & mask;
-            const uint32_t pos = s_base[d] + (uint32_t)i - s_dstart[d];
-            kout[pos] = key;
-            vout[pos] = s_val[i];
+        if (rec) {
+            for (int i = threadIdx.x; i < n_round; i += kSortThreads) {
+                const uint32_t key = s_key[i];
+                const uint32_t d = (key >> shift) & mask;
+                const uint32_t pos = s_base[d] + (uint32_t)i - s_dstart[d];
+                kout[pos] = key & 0xffffffu;
+                vout[pos] = rec[s_val[i]];
+                masks[pos] = (uint8_t)(key >> 24);
+            }
+        } else {
+            for (int i = threadIdx.x; i < n_round; i += kSortThreads) {
+                const uint32_t key = s_key[i];
+                const uint32_t d = (key >> shift) & mask;
+                const uint32_t pos = s_base[d] + (uint32_t)i - s_dstart[d];
+                kout[pos] = key;
+                vout[pos] = s_val[i];
+            }
         }
         __syncthreads();
         // advance the block's digit bases by this round's counts
@@ -324,7 +341,11 @@ constexpr int kBigRecord = 128;  // records overlapping more tiles are emitted b
 __device__ __forceinline__ void emit_one(uint32_t o, uint32_t rank, int i, int x0, int y0, int w, int toff, int gw,
                                          const Reach &rb, const ViewTable &vt,
                                          uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
-    const int ty = y0 + i / w, tx = x0 + i % w;
+    // i / w through a float reciprocal (i < 2^24, w < 2^16), then one exact correction step
+    int qt = (int)(((float)i + 0.5f) * __frcp_rn((float)w));
+    qt -= (qt * w > i) ? 1 : 0;
+    qt += ((qt + 1) * w <= i) ? 1 : 0;
+    const int ty = y0 + qt, tx = x0 + (i - qt * w);
     const uint32_t m = block_mask_of(rb, tx * vt.tile_w, ty * vt.tile_h, vt.tile_w);
     pkey[o] = (uint32_t)(toff + ty * gw + tx) | (m << 24);
     pval[o] = rank;
@@ -431,20 +452,31 @@ __global__ void __launch_bounds__(256) k_emit_big(const uint32_t *__restrict__ s
     }
 }
 
-// Final pass over the sorted pairs: Gaussian ids, tile ranges, and the block
-// masks carried in the keys' top byte.
-__global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ pkey, const uint32_t *__restrict__ pval,
-                                                 const uint32_t *__restrict__ sorted_rec,
-                                                 const int *__restrict__ counts, int *__restrict__ ids,
-                                                 int2 *__restrict__ ranges, uint8_t *__restrict__ masks) {
+// Tile ranges from the sorted tile keys (the last sort pass already wrote
+// the Gaussian ids and block masks).
+__global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ tkey, const int *__restrict__ counts,
+                                                 int2 *__restrict__ ranges) {
+    const long long P = counts[1];
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+        const uint32_t t = tkey[p];
+        if (p == 0 || tkey[p - 1] != t) ranges[t].x = (int)p;
+        if (p == P - 1 || tkey[p + 1] != t) ranges[t].y = (int)(p + 1);
+    }
+}
+
+// Without a tile pass (one tile in all): ids and masks straight from the
+// emitted pairs, which are already in order.
+__global__ void __launch_bounds__(256) k_unpack_pairs(const uint32_t *__restrict__ pkey,
+                                                       const uint32_t *__restrict__ pval,
+                                                       const uint32_t *__restrict__ rec, const int *__restrict__ counts,
+                                                       uint32_t *__restrict__ tkey, int *__restrict__ ids,
+                                                       uint8_t *__restrict__ masks) {
     const long long P = counts[1];
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t key = pkey[p];
-        const uint32_t t = key & 0xffffffu;
-        ids[p] = (int)sorted_rec[pval[p]];
+        tkey[p] = key & 0xffffffu;
+        ids[p] = (int)rec[pval[p]];
         masks[p] = (uint8_t)(key >> 24);
-        if (p == 0 || (pkey[p - 1] & 0xffffffu) != t) ranges[t].x = (int)p;
-        if (p == P - 1 || (pkey[p + 1] & 0xffffffu) != t) ranges[t].y = (int)(p + 1);
     }
 }
 
@@ -531,8 +563,13 @@ size_t sort_workspace_bytes(long long nrec, long long max_pairs) { return carve(
 
 // Sorts (k, v) in place-by-ping-pong over bits [0, total_bits); returns which
 // buffer pair holds the result (0: k0/v0, 1: k1/v1).
+// LSD radix sort of (k, v) on bits [0, total_bits) by ping-pong; returns the
+// buffer pair holding the result (0: k0/v0, 1: k1/v1).  With `rec` set the
+// last pass writes tile keys, ids = rec[v] and masks (see k_radix_downsweep),
+// the ids into final_v when given.
 static int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *count, int total_bits,
-                      uint32_t *hist, uint32_t *dtotal, cudaStream_t s) {
+                      uint32_t *hist, uint32_t *dtotal, cudaStream_t s, const uint32_t *rec = nullptr,
+                      uint8_t *masks = nullptr, uint32_t *final_v = nullptr) {
     if (total_bits <= 0) return 0;
     const int passes = (total_bits + 7) / 8;
     const int width = (total_bits + passes - 1) / passes;
@@ -541,9 +578,12 @@ static int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, co
         const int shift = p * width;
         const int bits = min(width, total_bits - shift);
         uint32_t *ki = cur ? k1 : k0, *vi = cur ? v1 : v0, *ko = cur ? k0 : k1, *vo = cur ? v0 : v1;
+        const bool last = p == passes - 1;
+        if (last && final_v) vo = final_v;
         k_radix_upsweep<<<kSortBlocks, kSortThreads, 0, s>>>(ki, count, shift, bits, hist);
         k_radix_scan<<<1 << bits, kSortBlocks, 0, s>>>(hist, dtotal);
-        k_radix_downsweep<<<kSortBlocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, shift, bits, hist, dtotal);
+        k_radix_downsweep<<<kSortBlocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, shift, bits, hist, dtotal,
+                                                                last ? rec : nullptr, last ? masks : nullptr);
         cur ^= 1;
     }
     return cur;
@@ -576,9 +616,17 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
                                        w.pv0);
     int tile_bits = 0;
     while ((1ll << tile_bits) < (long long)vt.total_tiles) ++tile_bits;
-    const int pres = radix_sort(w.pk0, w.pv0, w.pk1, w.pv1, counts + 1, tile_bits, w.hist, w.dtotal, s);
-    k_ranges<<<148 * 8, 256, 0, s>>>(pres ? w.pk1 : w.pk0, pres ? w.pv1 : w.pv0, sorted_rec, counts, gauss_ids,
-                                     tile_ranges, block_mask);
+    const uint32_t *tkey;
+    if (tile_bits > 0) {
+        // the last pass writes tile keys and ids into the other buffer pair
+        const int pres = radix_sort(w.pk0, w.pv0, w.pk1, w.pv1, counts + 1, tile_bits, w.hist, w.dtotal, s,
+                                    sorted_rec, block_mask, (uint32_t *)gauss_ids);
+        tkey = pres ? w.pk1 : w.pk0;
+    } else {
+        k_unpack_pairs<<<148 * 8, 256, 0, s>>>(w.pk0, w.pv0, sorted_rec, counts, w.pk1, gauss_ids, block_mask);
+        tkey = w.pk1;
+    }
+    k_ranges<<<148 * 8, 256, 0, s>>>(tkey, counts, tile_ranges);
     e = cudaMemsetAsync(w.bucket, 0, sizeof(unsigned int) * 64, s);
     if (e != cudaSuccess) return e;
     const int tb = (int)std::min<long long>(ceil_div(vt.total_tiles, 256), 148 * 4);

@@ -505,6 +505,6 @@ def launches_per_step(total_tiles, views=1, lambda_dssim=0.2):
     while (1 << tile_bits) < total_tiles:
         tile_bits += 1
     tile_passes = (tile_bits + 7) // 8
-    sort = 3 + 3 * 4 + 5 + 3 * tile_passes + 1 + 3
+    sort = 3 + 3 * 4 + 5 + 3 * tile_passes + 1 + 3 + (0 if tile_passes else 1)
     loss = (3 if lambda_dssim > 0 else 2) * views
     return 1 + sort + 1 + loss + 2 + 1

@@ -34,6 +34,8 @@ CASES = {
     "multiview_8x32": (lambda: _multi(3, 1500), gs.Config(tile_w=8, tile_h=32)),
     "multiview_32x8": (lambda: _multi(2, 1500), gs.Config(tile_w=32, tile_h=8, bg=(0.2, 0.1, 0.3))),
     "cfg1_batch128": (_cfg1, gs.Config(batch=128)),
+    "single_tile_16x16": (lambda: (scenes.uniform_scene(400, seed=13, xy_range=0.6), [scenes.pinhole(16, 16, 20.0)]),
+                          gs.Config()),
     "multiview_batch256": (lambda: _multi(1), gs.Config(tile_w=8, tile_h=32, batch=256)),
 }
 

@@ -91,6 +91,10 @@ def lib():
                                           C.POINTER(_Projected), vp, vp, vp, vp, vp, vp]
         L.or_adam.argtypes = [i64, vp, vp, vp, vp, vp, d, d, d, i64]
         L.or_prune_finalize.argtypes = [i64, vp, vp, vp, i32, d, d, vp, vp, vp, vp, vp]
+        L.or_geo_loss.argtypes = [vp, vp, i64, vp]
+        L.or_geo_loss.restype = d
+        L.or_iso_loss.argtypes = [i64, vp, vp]
+        L.or_iso_loss.restype = d
     return _lib
 
 
@@ -299,6 +303,23 @@ def prune_finalize(omega, kappa, gamma, n_views, tau_d=5.0, tau_p=0.99, densify=
     lib().or_prune_finalize(n, _ptr(omega), _ptr(kappa), _ptr(gamma), int(n_views), tau_d, tau_p,
                             _ptr(S_d), _ptr(S_p), _ptr(densify), _ptr(prune_max), _ptr(prune))
     return dict(S_d=S_d, S_p=S_p, densify=densify, prune_max=prune_max, prune=prune)
+
+
+def geo_loss(depth, prior, grad=True):
+    """L_geo = mean over pixels of [prior > 0] |prior - depth| and its gradient."""
+    depth, prior = _f64(depth), _f64(prior)
+    dL = np.zeros_like(depth) if grad else None
+    L = lib().or_geo_loss(_ptr(depth), _ptr(prior), depth.size, _ptr(dL))
+    return L, dL
+
+
+def iso_loss(log_scales, grad=True):
+    """L_iso = mean over Gaussians of sum_k |s_k - mean(s)| and dL/dlog-scale."""
+    ls = _f64(log_scales)
+    n = ls.shape[0]
+    g = np.zeros_like(ls) if grad else None
+    L = lib().or_iso_loss(n, _ptr(ls), _ptr(g))
+    return L, g
 
 
 # --------------------------------------------------------------------------

@@ -864,3 +864,46 @@ void or_prune_finalize(int64_t n, const double *omega, const double *kappa, cons
         prune[i] = prune_max[i] > tau_p;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Geometric and isotropic terms of L_total (Supp. D.4)                       */
+/* ------------------------------------------------------------------------ */
+
+/* L_geo = mean over the npx pixels of [prior > 0] |prior - depth|; returns it
+ * and writes dL/ddepth (nullable).  Reading: the printed L1 norm taken as a
+ * mean over pixels like L_photo, pixels without a prior (prior <= 0) adding 0. */
+double or_geo_loss(const double *depth, const double *prior, int64_t npx, double *dL_ddepth) {
+    double s = 0.0;
+    for (int64_t p = 0; p < npx; ++p) {
+        double g = 0.0;
+        if (prior[p] > 0.0) {
+            double d = depth[p] - prior[p];
+            s += fabs(d);
+            g = (d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0)) / (double)npx;
+        }
+        if (dL_ddepth) dL_ddepth[p] = g;
+    }
+    return s / (double)npx;
+}
+
+/* L_iso = mean over the n Gaussians of sum_k |s_k - mean(s)|, s = exp(log-scale);
+ * returns it and adds dL/dlog-scale into g_log_scales (nullable).  Reading:
+ * the printed sum over Gaussians normalised by n as in the cited MonoGS. */
+double or_iso_loss(int64_t n, const double *log_scales, double *g_log_scales) {
+    double L = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double s[3], mean = 0.0;
+        for (int k = 0; k < 3; ++k) { s[k] = exp(log_scales[3 * i + k]); mean += s[k] / 3.0; }
+        double e[3], esum = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            double d = s[k] - mean;
+            L += fabs(d);
+            e[k] = d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0);
+            esum += e[k];
+        }
+        if (g_log_scales)
+            for (int k = 0; k < 3; ++k)  /* d|s_k - m|/ds_j = e_k (delta_kj - 1/3) */
+                g_log_scales[3 * i + k] += (e[k] - esum / 3.0) * s[k] / (double)n;
+    }
+    return L / (double)n;
+}

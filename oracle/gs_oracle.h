@@ -131,6 +131,13 @@ void or_prune_finalize(int64_t n, const double *omega, const double *kappa, cons
                        double *S_d, double *S_p, uint8_t *densify, double *prune_max,
                        uint8_t *prune);
 
+/* Geometric term: mean over pixels of [prior > 0] |prior - depth| (Supp. D.4). */
+double or_geo_loss(const double *depth, const double *prior, int64_t npx, double *dL_ddepth);
+
+/* Isotropic term: mean over Gaussians of sum_k |s_k - mean(s)|, s = exp(log-scale)
+ * (Supp. D.4); gradient added into g_log_scales (nullable). */
+double or_iso_loss(int64_t n, const double *log_scales, double *g_log_scales);
+
 #ifdef __cplusplus
 }
 #endif

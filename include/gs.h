@@ -234,6 +234,30 @@ gs_status gs_loss(const float *img, const float *target, const gs_camera *cams, 
                   float lambda_dssim, float *loss_per_view, float *dL_dimg, void *ws,
                   size_t ws_bytes, gs_stream stream);
 
+/* Workspace bytes of gs_geo_loss and gs_iso_loss. */
+gs_status gs_reg_workspace_size(size_t *bytes);
+
+/*
+ * Geometric term of L_total (Sec. 3.2.3; Supp. D.4 L_geo = ||D - D^||_1)
+ * per view: weight * mean over the view's pixels of [D > 0] |D - D^|, D the
+ * metric-depth prior (0 marks a pixel without one), D^ the rendered depth
+ * (gs_frame.depth).  Writes weight * L_geo into loss_per_view[v] and
+ * weight * dL_geo/dD^ into dL_ddepth (nullable), both in frame layout; pass
+ * dL_ddepth to gs_render_bwd.  weight is lambda_g (0.01, Supp. F).
+ */
+gs_status gs_geo_loss(const float *depth, const float *prior, const gs_camera *cams, int32_t n_views,
+                      float weight, float *loss_per_view, float *dL_ddepth, void *ws, size_t ws_bytes,
+                      gs_stream stream);
+
+/*
+ * Isotropic term of L_total (Supp. D.4 L_iso = sum_i ||s_i - mean(s_i) 1||_1,
+ * taken as a mean over the n Gaussians, s = exp(log-scale)): writes
+ * weight * L_iso into *loss and ADDS weight * dL_iso/dlog-scale into the
+ * log-scale planes of grads (nullable).  weight is lambda_iso (10, Supp. F).
+ */
+gs_status gs_iso_loss(const gs_params *params, float weight, float *loss, const gs_params *grads, void *ws,
+                      size_t ws_bytes, gs_stream stream);
+
 /*
  * gs_loss without a caller workspace.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory where

@@ -244,6 +244,41 @@ GS_API gs_status gs_loss_static(const float *img, const float *target, const gs_
     return GS_OK;
 }
 
+GS_API gs_status gs_reg_workspace_size(size_t *bytes) {
+    if (!bytes) return GS_ERR_INVALID;
+    *bytes = reg_workspace_bytes();
+    return GS_OK;
+}
+
+GS_API gs_status gs_geo_loss(const float *depth, const float *prior, const gs_camera *cams, int32_t n_views,
+                             float weight, float *loss_per_view, float *dL_ddepth, void *ws, size_t ws_bytes,
+                             gs_stream stream) {
+    if (!depth || !prior || !cams || !loss_per_view || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_INVALID;
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < reg_workspace_bytes() || !(weight >= 0.0f)) return GS_ERR_INVALID;
+    long long off = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const long long npx = (long long)cams[v].width * cams[v].height;
+        if (npx <= 0) return GS_ERR_INVALID;
+        cudaError_t e = launch_geo(depth + off, prior + off, npx, weight, loss_per_view + v,
+                                   dL_ddepth ? dL_ddepth + off : nullptr, ws, (cudaStream_t)stream);
+        if (e != cudaSuccess) return GS_ERR_CUDA;
+        off += npx;
+    }
+    return GS_OK;
+}
+
+GS_API gs_status gs_iso_loss(const gs_params *params, float weight, float *loss, const gs_params *grads, void *ws,
+                             size_t ws_bytes, gs_stream stream) {
+    gs_status st = check_params(params);
+    if (st == GS_OK && grads) st = check_params(grads);
+    if (st != GS_OK) return st;
+    if (grads && (grads->ld != params->ld || grads->n != params->n)) return GS_ERR_INVALID;
+    if (!loss || !ws || ((uintptr_t)ws & 255u) || ws_bytes < reg_workspace_bytes() || !(weight >= 0.0f))
+        return GS_ERR_INVALID;
+    return cuda_status(launch_iso(params->data, params->n, params->ld, weight, loss, grads ? grads->data : nullptr, ws,
+                                  (cudaStream_t)stream));
+}
+
 GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views,
                                const gs_raster_cfg *cfg, const gs_projected *proj, const gs_binning *binning,
                                const gs_frame *frame, const float *dL_dimg, const float *dL_ddepth,

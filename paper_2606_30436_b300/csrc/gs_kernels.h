@@ -48,6 +48,12 @@ cudaError_t launch_loss(const float *img, const float *target, int h, int w, flo
 void launch_adam(float *p, const float *g, float *m, float *v, long long ld, int planes, const float lr[6],
                  float beta1, float beta2, float eps, long long step, const long long *step_dev, cudaStream_t s);
 
+size_t reg_workspace_bytes();
+cudaError_t launch_geo(const float *depth, const float *prior, long long npx, float weight, float *loss, float *dL,
+                       void *ws, cudaStream_t s);
+cudaError_t launch_iso(const float *P, long long n, long long ld, float weight, float *loss, float *G, void *ws,
+                       cudaStream_t s);
+
 size_t prune_workspace_bytes(long long n);
 void launch_prune(const float *acc, long long ld, long long n, int n_views, float tau_d, float tau_p, float *S_d,
                   float *S_p, float *prune_max, unsigned char *densify, unsigned char *prune, void *ws,

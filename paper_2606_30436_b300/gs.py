@@ -74,7 +74,8 @@ class ChunkScores(C.Structure):
 EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspace_size", "gs_block_mask_size",
            "gs_loss_workspace_size",
            "gs_bwd_workspace_size", "gs_prune_workspace_size", "gs_project", "gs_sort", "gs_render_fwd", "gs_loss",
-           "gs_render_bwd", "gs_project_bwd", "gs_adam", "gs_prune_stats", "gs_loss_static")
+           "gs_render_bwd", "gs_project_bwd", "gs_adam", "gs_prune_stats", "gs_loss_static",
+           "gs_reg_workspace_size", "gs_geo_loss", "gs_iso_loss")
 
 _lib = None
 
@@ -103,6 +104,9 @@ def lib():
         L.gs_render_fwd.argtypes = [P(Projected), P(Binning), P(Camera), i32, P(RasterCfg), P(Frame), vp]
         L.gs_loss.argtypes = [vp, vp, P(Camera), i32, f32, vp, vp, vp, sz, vp]
         L.gs_loss_static.argtypes = [vp, vp, P(Camera), i32, f32, vp, vp, vp]
+        L.gs_reg_workspace_size.argtypes = [P(sz)]
+        L.gs_geo_loss.argtypes = [vp, vp, P(Camera), i32, f32, vp, vp, vp, sz, vp]
+        L.gs_iso_loss.argtypes = [P(Params), f32, vp, P(Params), vp, sz, vp]
         L.gs_render_bwd.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), P(Binning), P(Frame),
                                     vp, vp, vp, vp, f32, P(Params), i32, P(Stats), vp, sz, vp]
         L.gs_project_bwd.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), vp, sz, vp, P(Params), i32,
@@ -341,6 +345,26 @@ def gs_loss(buf: Buffers, target: torch.Tensor, lambda_dssim=0.2, stream=None, i
                          _stream(stream)), "gs_loss")
 
 
+def reg_workspace(device="cuda"):
+    n = C.c_size_t()
+    _check(lib().gs_reg_workspace_size(C.byref(n)), "gs_reg_workspace_size")
+    return torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=device)
+
+
+def gs_geo_loss(buf: Buffers, prior, weight, loss_out, dL_ddepth, ws, stream=None):
+    """weight * L_geo per view into loss_out, weight * dL/dD^ into dL_ddepth."""
+    arr = camera_array(buf.cams)
+    _check(lib().gs_geo_loss(_ptr(buf.depth), _ptr(prior), arr, buf.n_views, float(weight), _ptr(loss_out),
+                             _ptr(dL_ddepth), _ptr(ws), ws.numel(), _stream(stream)), "gs_geo_loss")
+
+
+def gs_iso_loss(model: GaussianModel, weight, loss_out, grads: GaussianModel, ws, stream=None):
+    """weight * L_iso into loss_out[0]; adds its gradient into grads' log-scale planes."""
+    _check(lib().gs_iso_loss(C.byref(model.c()), float(weight), _ptr(loss_out),
+                             None if grads is None else C.byref(grads.c()), _ptr(ws), ws.numel(), _stream(stream)),
+           "gs_iso_loss")
+
+
 def gs_loss_static(img, target, cams, loss_out, dL_dimg, lambda_dssim=0.2, stream=None):
     """gs_loss with the library's own scratch array (no workspace argument),
     for callers that cannot allocate device memory; views up to 1280x720."""
@@ -410,10 +434,14 @@ class MappingStep:
     """render -> L_photo -> backward -> Adam over one chunk of views."""
 
     def __init__(self, model: GaussianModel, cams, cfg: Config = None, max_pairs=None, lambda_dssim=0.2,
-                 tau_err=0.1, lr=None, with_stats=True, with_depth=False):
+                 tau_err=0.1, lr=None, with_stats=True, with_depth=False, depth_prior=None, lambda_geo=0.01,
+                 lambda_iso=0.0):
         self.model = model
         self.cfg = cfg or Config()
         self.lambda_dssim, self.tau_err = lambda_dssim, tau_err
+        # L_total = L_photo + lambda_geo L_geo (when a depth prior is given) + lambda_iso L_iso
+        self.depth_prior, self.lambda_geo, self.lambda_iso = depth_prior, lambda_geo, lambda_iso
+        with_depth = with_depth or depth_prior is not None
         self.lr = lr or default_lr()
         self.with_stats = with_stats
         self.grads, self.exp_avg, self.exp_avg_sq = model.like(), model.like(), model.like()
@@ -421,6 +449,12 @@ class MappingStep:
         if max_pairs is None:
             max_pairs = max(1 << 16, 8 * model.n * len(cams))
         self.buf = Buffers(model, cams, self.cfg, max_pairs, with_depth=with_depth, with_stats=with_stats)
+        dev = model.data.device
+        self.reg_ws = reg_workspace(dev) if (depth_prior is not None or lambda_iso > 0) else None
+        self.geo_loss = torch.zeros(len(cams), dtype=torch.float32, device=dev)
+        self.iso_loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.dL_ddepth = (torch.empty(self.buf.total_pixels, dtype=torch.float32, device=dev)
+                          if depth_prior is not None else None)
 
     def set_cameras(self, cams):
         assert len(cams) == self.buf.n_views
@@ -435,12 +469,28 @@ class MappingStep:
         gs_sort(b, stream)
         gs_render_fwd(b, stream)
 
+    def _losses_and_backward(self, target, stream=None):
+        gs_loss(self.buf, target, self.lambda_dssim, stream)
+        if self.depth_prior is not None:
+            gs_geo_loss(self.buf, self.depth_prior, self.lambda_geo, self.geo_loss, self.dL_ddepth, self.reg_ws, stream)
+        gs_render_bwd(self.model, self.grads, self.buf, target, self.tau_err, with_stats=self.with_stats,
+                      dL_ddepth=self.dL_ddepth, stream=stream)
+        if self.lambda_iso > 0:
+            gs_iso_loss(self.model, self.lambda_iso, self.iso_loss, self.grads, self.reg_ws, stream)
+
+    def total_loss(self):
+        """L_total = sum over views of L_photo (+ lambda_geo L_geo) + lambda_iso L_iso (device tensor)."""
+        t = self.buf.loss.sum()
+        if self.depth_prior is not None:
+            t = t + self.geo_loss.sum()
+        if self.lambda_iso > 0:
+            t = t + self.iso_loss[0]
+        return t
+
     def step(self, target, stream=None, optimize=True):
         """One iteration on device-resident targets (frame layout)."""
         self.forward(stream)
-        gs_loss(self.buf, target, self.lambda_dssim, stream)
-        gs_render_bwd(self.model, self.grads, self.buf, target, self.tau_err, with_stats=self.with_stats,
-                      stream=stream)
+        self._losses_and_backward(target, stream)
         if optimize:
             self.step_count += 1
             gs_adam(self.model, self.grads, self.exp_avg, self.exp_avg_sq, self.lr, self.step_count, stream=stream)
@@ -464,8 +514,7 @@ class MappingStep:
             gs_project(self.model, b)
             gs_sort(b)
             gs_render_fwd(b)
-            gs_loss(b, target, self.lambda_dssim)
-            gs_render_bwd(self.model, self.grads, b, target, self.tau_err, with_stats=self.with_stats)
+            self._losses_and_backward(target)
             self.step_dev.add_(1)
             gs_adam(self.model, self.grads, self.exp_avg, self.exp_avg_sq, self.lr, 1, step_device=self.step_dev)
         torch.cuda.current_stream(dev).wait_stream(side)

@@ -68,7 +68,7 @@ def test_autograd_finite_differences():
     for plane in (0, 1, 2, 3, 5, 10, 11, 14):
         row = grad[plane, :model.n].abs()
         for g_idx in torch.topk(row, 3).indices.tolist():
-            h = 1e-3 * max(1.0, abs(float(params[plane, g_idx])))
+            h = 1e-3 * max(1.0, abs(float(params[plane, g_idx].detach())))
             pp, pm = params.detach().clone(), params.detach().clone()
             pp[plane, g_idx] += h
             pm[plane, g_idx] -= h

@@ -418,3 +418,52 @@ def test_split_backward_and_render_schedule():
     cnt = rg[order, 1] - rg[order, 0]
     cls = np.where(cnt > 0, np.floor(np.log2(np.maximum(cnt, 1))) + 1, 0)
     assert np.all(np.diff(cls) <= 0)
+
+
+def test_total_loss_depth_and_isotropy():
+    """L_total = L_photo + 0.01 L_geo + 10 L_iso (Sec. 3.2.3, Supp. D.4): the
+    rendered depth, each term and every gradient group against the oracle."""
+    scene, cams = _multi(1, 2000)
+    cfg = gs.Config(bg=(0.1, 0.2, 0.3))
+    oc = ocfg(cfg)
+    tscene = scenes.perturb(scene, 0.02, seed=8)
+    tf = [orc.forward(tscene, c, oc) for c in cams]
+    rng = np.random.default_rng(4)
+    priors = []
+    for f in tf:
+        d = f["depth"].astype(np.float32)
+        d[rng.uniform(size=d.shape) < 0.1] = 0.0  # pixels without a prior
+        priors.append(d)
+    tgt = torch.from_numpy(np.concatenate([f["img"].astype(np.float32).reshape(-1) for f in tf])).cuda()
+    prior_t = torch.from_numpy(np.concatenate([p.reshape(-1) for p in priors])).cuda()
+    model = gs.GaussianModel.from_scene(scene)
+    st = gs.MappingStep(model, cams, cfg, lambda_dssim=0.2, depth_prior=prior_t, lambda_geo=0.01, lambda_iso=10.0,
+                        with_stats=False)
+    st.fit_capacity()
+    st.step(tgt, optimize=False)
+    torch.cuda.synchronize()
+    st.check_status()
+    g_gpu = gs.unpack_planes(st.grads.data.cpu().numpy(), model.n, model.sh_degree)
+
+    g_or = {k: 0.0 for k in GROUPS}
+    P = orc.Params(scene)
+    for v, cam in enumerate(cams):
+        f = orc.forward(P, cam, oc)
+        L, dL, _ = orc.loss(f["img"], tf[v]["img"].astype(np.float32), 0.2)
+        Lg, dLg = orc.geo_loss(f["depth"], priors[v])
+        assert abs(st.buf.loss[v].item() - L) < 1e-4 * abs(L)
+        assert abs(st.geo_loss[v].item() - 0.01 * Lg) < 1e-4 * 0.01 * Lg + 1e-9
+        mask = f["flags"] & (orc.OR_FLAG_NEAR_ALPHA_MIN | orc.OR_FLAG_NEAR_T_CUT) != 0
+        depth = st.buf.view_plane(st.buf.depth, v).cpu().numpy()
+        assert np.abs(depth - f["depth"])[~mask].max() < 1e-3
+        g2, _, _ = orc.render_backward(f["proj"], f["vals"], f["ranges"], cam, oc, dL, f["img"], f["img"],
+                                       dL_ddepth=0.01 * dLg)
+        go = orc.project_backward(f["params"], cam, oc, f["proj"], g2)
+        for k in GROUPS:
+            g_or[k] = g_or[k] + go[k]
+    Li, gi = orc.iso_loss(P.log_scales)
+    assert abs(st.iso_loss.item() - 10.0 * Li) < 1e-5 * 10.0 * Li
+    g_or["log_scales"] = g_or["log_scales"] + 10.0 * gi
+    for k in GROUPS:
+        e = rel_l2(g_gpu[k], g_or[k])
+        assert e < 1e-3, (k, e)

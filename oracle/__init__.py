@@ -95,6 +95,10 @@ def lib():
         L.or_geo_loss.restype = d
         L.or_iso_loss.argtypes = [i64, vp, vp]
         L.or_iso_loss.restype = d
+        L.or_mlp_num_weights.restype = i32
+        L.or_mlp_forward.argtypes = [i64, vp, vp, i32, vp, vp, vp]
+        L.or_mlp_bce_grad.argtypes = [i64, vp, vp, vp, i32, vp]
+        L.or_mlp_bce_grad.restype = d
     return _lib
 
 
@@ -319,6 +323,27 @@ def iso_loss(log_scales, grad=True):
     n = ls.shape[0]
     g = np.zeros_like(ls) if grad else None
     L = lib().or_iso_loss(n, _ptr(ls), _ptr(g))
+    return L, g
+
+
+def mlp_num_weights():
+    return lib().or_mlp_num_weights()
+
+
+def mlp_forward(x, w, bf16=True):
+    """Probabilities (densify, prune) and hidden activations for features x[n][16]."""
+    x, w = _f64(x), _f64(w)
+    n = x.shape[0]
+    p, h1, h2 = np.zeros((n, 2)), np.zeros((n, 64)), np.zeros((n, 64))
+    lib().or_mlp_forward(n, _ptr(x), _ptr(w), int(bool(bf16)), _ptr(p), _ptr(h1), _ptr(h2))
+    return p, h1, h2
+
+
+def mlp_bce_grad(x, y, w, bf16=True):
+    """Mean BCE over rows and outputs, and its gradient with respect to w."""
+    x, y, w = _f64(x), _f64(y), _f64(w)
+    g = np.zeros_like(w)
+    L = lib().or_mlp_bce_grad(x.shape[0], _ptr(x), _ptr(y), _ptr(w), int(bool(bf16)), _ptr(g))
     return L, g
 
 

@@ -907,3 +907,119 @@ double or_iso_loss(int64_t n, const double *log_scales, double *g_log_scales) {
     }
     return L / (double)n;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned prune / densify predictor (a later row of the build; the paper     */
+/* decides with the plain criterion of Supp. E): MLP 16 -> 64 -> 64 -> 2       */
+/* with ReLU hidden layers and sigmoid outputs (densify, prune).              */
+/* ------------------------------------------------------------------------ */
+
+/* Weights in one array: W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64], b3[2]. */
+#define OR_MLP_IN 16
+#define OR_MLP_H 64
+#define OR_MLP_OUT 2
+#define OR_MLP_W1 0
+#define OR_MLP_B1 (OR_MLP_W1 + OR_MLP_H * OR_MLP_IN)
+#define OR_MLP_W2 (OR_MLP_B1 + OR_MLP_H)
+#define OR_MLP_B2 (OR_MLP_W2 + OR_MLP_H * OR_MLP_H)
+#define OR_MLP_W3 (OR_MLP_B2 + OR_MLP_H)
+#define OR_MLP_B3 (OR_MLP_W3 + OR_MLP_OUT * OR_MLP_H)
+#define OR_MLP_NW (OR_MLP_B3 + OR_MLP_OUT)
+
+/* Round to the nearest bfloat16 (ties to even) through float, as a tensor-core
+ * operand is rounded. */
+static double bf16_round(double v) {
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (double)f;  /* inf / nan unchanged */
+    u += 0x7fffu + ((u >> 16) & 1u);
+    u &= 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+int32_t or_mlp_num_weights(void) { return OR_MLP_NW; }
+
+/* Forward of n rows of features x[n][16]; writes p[n][2] (nullable), and the
+ * hidden activations h1[n][64], h2[n][64] (nullable).  bf16 != 0 rounds the
+ * tensor-core operands (x, W1, W2, h1) to bfloat16 as the kernels do. */
+void or_mlp_forward(int64_t n, const double *x, const double *w, int32_t bf16, double *p, double *h1o, double *h2o) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double xi[OR_MLP_IN], h1[OR_MLP_H], h2[OR_MLP_H];
+        for (int c = 0; c < OR_MLP_IN; ++c) xi[c] = bf16 ? bf16_round(x[i * OR_MLP_IN + c]) : x[i * OR_MLP_IN + c];
+        for (int o = 0; o < OR_MLP_H; ++o) {
+            double s = 0.0;
+            for (int c = 0; c < OR_MLP_IN; ++c) {
+                double wv = w[OR_MLP_W1 + o * OR_MLP_IN + c];
+                s += (bf16 ? bf16_round(wv) : wv) * xi[c];
+            }
+            s += w[OR_MLP_B1 + o];
+            h1[o] = s > 0.0 ? s : 0.0;
+        }
+        for (int o = 0; o < OR_MLP_H; ++o) {
+            double s = 0.0;
+            for (int c = 0; c < OR_MLP_H; ++c) {
+                double wv = w[OR_MLP_W2 + o * OR_MLP_H + c];
+                s += (bf16 ? bf16_round(wv) : wv) * (bf16 ? bf16_round(h1[c]) : h1[c]);
+            }
+            s += w[OR_MLP_B2 + o];
+            h2[o] = s > 0.0 ? s : 0.0;
+        }
+        for (int k = 0; k < OR_MLP_OUT; ++k) {
+            double z = w[OR_MLP_B3 + k];
+            for (int c = 0; c < OR_MLP_H; ++c) z += w[OR_MLP_W3 + k * OR_MLP_H + c] * h2[c];
+            if (p) p[i * OR_MLP_OUT + k] = 1.0 / (1.0 + exp(-z));
+        }
+        if (h1o) memcpy(h1o + i * OR_MLP_H, h1, sizeof(h1));
+        if (h2o) memcpy(h2o + i * OR_MLP_H, h2, sizeof(h2));
+    }
+}
+
+/* Mean binary cross-entropy over the n rows and both outputs of the labels
+ * y[n][2] in {0, 1}; writes dL/dw (accumulated into g) and returns L.
+ * bf16 as in or_mlp_forward; the backward then rounds the tensor-core operand
+ * of the hidden-layer gradient (dL/dh2 before the product with W2) too. */
+double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double *w, int32_t bf16, double *g) {
+    double L = 0.0;
+    const double scale = 1.0 / (double)(n * OR_MLP_OUT);
+    for (int64_t i = 0; i < n; ++i) {
+        double xi[OR_MLP_IN], h1[OR_MLP_H], h2[OR_MLP_H], p[OR_MLP_OUT];
+        or_mlp_forward(1, x + i * OR_MLP_IN, w, bf16, p, h1, h2);
+        for (int c = 0; c < OR_MLP_IN; ++c) xi[c] = bf16 ? bf16_round(x[i * OR_MLP_IN + c]) : x[i * OR_MLP_IN + c];
+        double dz[OR_MLP_OUT];
+        for (int k = 0; k < OR_MLP_OUT; ++k) {
+            const double yk = y[i * OR_MLP_OUT + k];
+            const double pk = p[k] < 1e-300 ? 1e-300 : (p[k] > 1.0 - 1e-16 ? 1.0 - 1e-16 : p[k]);
+            L -= yk * log(pk) + (1.0 - yk) * log(1.0 - pk);
+            dz[k] = (p[k] - yk) * scale;  /* dBCE/dz = p - y */
+            g[OR_MLP_B3 + k] += dz[k];
+            for (int c = 0; c < OR_MLP_H; ++c) g[OR_MLP_W3 + k * OR_MLP_H + c] += dz[k] * h2[c];
+        }
+        double dh2[OR_MLP_H];
+        for (int c = 0; c < OR_MLP_H; ++c) {
+            double s = 0.0;
+            for (int k = 0; k < OR_MLP_OUT; ++k) s += dz[k] * w[OR_MLP_W3 + k * OR_MLP_H + c];
+            dh2[c] = h2[c] > 0.0 ? s : 0.0;
+        }
+        for (int o = 0; o < OR_MLP_H; ++o) {
+            g[OR_MLP_B2 + o] += dh2[o];
+            for (int c = 0; c < OR_MLP_H; ++c) g[OR_MLP_W2 + o * OR_MLP_H + c] += dh2[o] * h1[c];
+        }
+        double dh1[OR_MLP_H];
+        for (int c = 0; c < OR_MLP_H; ++c) {
+            double s = 0.0;
+            for (int o = 0; o < OR_MLP_H; ++o) {
+                double wv = w[OR_MLP_W2 + o * OR_MLP_H + c];
+                s += (bf16 ? bf16_round(dh2[o] / scale) * scale : dh2[o]) * (bf16 ? bf16_round(wv) : wv);
+            }
+            dh1[c] = h1[c] > 0.0 ? s : 0.0;
+        }
+        for (int o = 0; o < OR_MLP_H; ++o) {
+            g[OR_MLP_B1 + o] += dh1[o];
+            for (int c = 0; c < OR_MLP_IN; ++c) g[OR_MLP_W1 + o * OR_MLP_IN + c] += dh1[o] * xi[c];
+        }
+    }
+    return L * scale;
+}

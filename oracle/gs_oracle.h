@@ -138,6 +138,12 @@ double or_geo_loss(const double *depth, const double *prior, int64_t npx, double
  * (Supp. D.4); gradient added into g_log_scales (nullable). */
 double or_iso_loss(int64_t n, const double *log_scales, double *g_log_scales);
 
+/* Learned prune / densify MLP 16 -> 64 -> 64 -> 2 (ReLU, sigmoid outputs);
+ * weights W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64], b3[2] in one array. */
+int32_t or_mlp_num_weights(void);
+void or_mlp_forward(int64_t n, const double *x, const double *w, int32_t bf16, double *p, double *h1, double *h2);
+double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double *w, int32_t bf16, double *g);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,6 +99,9 @@ def lib():
         L.or_mlp_forward.argtypes = [i64, vp, vp, i32, vp, vp, vp]
         L.or_mlp_bce_grad.argtypes = [i64, vp, vp, vp, i32, vp]
         L.or_mlp_bce_grad.restype = d
+        L.or_mlp_features.argtypes = [i64, vp, vp, vp, vp, vp, i32, vp, vp]
+        L.or_densify_prune.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, d, d, i64, vp, vp, vp]
+        L.or_densify_prune.restype = i64
     return _lib
 
 
@@ -345,6 +348,36 @@ def mlp_bce_grad(x, y, w, bf16=True):
     g = np.zeros_like(w)
     L = lib().or_mlp_bce_grad(x.shape[0], _ptr(x), _ptr(y), _ptr(w), int(bool(bf16)), _ptr(g))
     return L, g
+
+
+def mlp_features(means, log_scales, opacity_logits, stats, ring, head, cam_centre):
+    """Predictor inputs feat[n][16] from parameters, stats[n][6] and ring[8][n]."""
+    means, log_scales, opl = _f64(means), _f64(log_scales), _f64(opacity_logits)
+    stats, ring, cc = _f64(stats), _f64(ring), _f64(cam_centre, (3,))
+    n = opl.size
+    feat = np.zeros((n, 16))
+    lib().or_mlp_features(n, _ptr(means), _ptr(log_scales), _ptr(opl), _ptr(stats), _ptr(ring), int(head),
+                          _ptr(cc), _ptr(feat))
+    return feat
+
+
+def densify_prune(P, densify, prune, noise, split_log_scale, split_factor=1.6, m=None, v=None, cap=None):
+    """Rows P[n][K_row] after the densify / prune actions; returns (P, m, v, needed)."""
+    P = _f64(P)
+    n, K = P.shape
+    assert K <= 192
+    densify = np.ascontiguousarray(densify, np.uint8)
+    prune = np.ascontiguousarray(prune, np.uint8)
+    noise = _f64(noise, (n, 6)) if n else np.zeros((0, 6))
+    m = None if m is None else _f64(m)
+    v = None if v is None else _f64(v)
+    cap = 2 * n if cap is None else int(cap)
+    Po, mo, vo = np.zeros((cap, K)), np.zeros((cap, K)), np.zeros((cap, K))
+    need = lib().or_densify_prune(n, K, _ptr(P), _ptr(m) if m is not None else None,
+                                  _ptr(v) if v is not None else None, _ptr(densify), _ptr(prune), _ptr(noise),
+                                  float(split_log_scale), float(split_factor), cap, _ptr(Po), _ptr(mo), _ptr(vo))
+    k = min(need, cap)
+    return Po[:k], mo[:k], vo[:k], need
 
 
 # --------------------------------------------------------------------------

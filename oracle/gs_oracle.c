@@ -1023,3 +1023,70 @@ double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double
     }
     return L * scale;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Predictor inputs and the densify / prune actions                          */
+/* ------------------------------------------------------------------------ */
+
+void or_mlp_features(int64_t n, const double *means, const double *log_scales, const double *opacity_logits,
+                     const double *stats, const double *ring, int32_t head, const double cam[3], double *feat) {
+    for (int64_t i = 0; i < n; ++i) {
+        double *f = feat + i * OR_MLP_IN;
+        const double *st = stats + i * 6;
+        const double views = st[5];
+        f[0] = 1.0 / (1.0 + exp(-opacity_logits[i]));
+        for (int k = 0; k < 3; ++k) f[1 + k] = log_scales[3 * i + k];
+        f[4] = log(1.0 + views);
+        f[5] = log(1.0 + 1e4 * st[4]);
+        for (int j = 0; j < 8; ++j) f[6 + j] = ring[(int64_t)(((head - j) % 8 + 8) % 8) * n + i];
+        double d2 = 0.0;
+        for (int k = 0; k < 3; ++k) d2 += (means[3 * i + k] - cam[k]) * (means[3 * i + k] - cam[k]);
+        f[14] = log(1.0 + sqrt(d2));
+        f[15] = log(1.0 + st[0] / (views > 1.0 ? views : 1.0));
+    }
+}
+
+int64_t or_densify_prune(int64_t n, int32_t K_row, const double *P, const double *m, const double *v,
+                         const uint8_t *densify, const uint8_t *prune, const double *noise,
+                         double split_log_scale, double split_factor, int64_t cap, double *P_out,
+                         double *m_out, double *v_out) {
+    int64_t o = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double *src = P + i * K_row;
+        if (prune[i]) continue;
+        double rows[2][64 * 3];
+        int emit = 1, moments_first = 1;
+        memcpy(rows[0], src, sizeof(double) * K_row);
+        if (densify[i]) {
+            emit = 2;
+            memcpy(rows[1], src, sizeof(double) * K_row);
+            double lmax = src[3];
+            if (src[4] > lmax) lmax = src[4];
+            if (src[5] > lmax) lmax = src[5];
+            if (lmax > split_log_scale) {  /* split into two samples of N(mu, Sigma) */
+                double R[9];
+                or_quat_to_rot(src + 6, R);
+                for (int j = 0; j < 2; ++j) {
+                    const double *xi = noise + i * 6 + 3 * j;
+                    for (int r = 0; r < 3; ++r) {
+                        double d = 0.0;
+                        for (int c = 0; c < 3; ++c) d += R[3 * r + c] * exp(src[3 + c]) * xi[c];
+                        rows[j][r] = src[r] + d;
+                    }
+                    for (int c = 0; c < 3; ++c) rows[j][3 + c] = src[3 + c] - log(split_factor);
+                }
+                moments_first = 0;
+            }
+        }
+        for (int j = 0; j < emit; ++j, ++o) {
+            if (o >= cap) continue;
+            memcpy(P_out + o * K_row, rows[j], sizeof(double) * K_row);
+            const int keep = j == 0 && moments_first;
+            for (int k = 0; k < K_row; ++k) {
+                if (m_out) m_out[o * K_row + k] = keep && m ? m[i * K_row + k] : 0.0;
+                if (v_out) v_out[o * K_row + k] = keep && v ? v[i * K_row + k] : 0.0;
+            }
+        }
+    }
+    return o;
+}

@@ -144,6 +144,31 @@ int32_t or_mlp_num_weights(void);
 void or_mlp_forward(int64_t n, const double *x, const double *w, int32_t bf16, double *p, double *h1, double *h2);
 double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double *w, int32_t bf16, double *g);
 
+/* The predictor's 16 inputs per Gaussian (a reading: the inputs are named in
+ * the workload definition, not in the paper): sigmoid(opacity logit), the
+ * three log-scales, log(1 + views seen), log(1 + 1e4 * accumulated
+ * ||dL/d(u,v)||), the max blend weight T*alpha of the last 8 views (ring
+ * slots head, head-1, ... mod 8), log(1 + ||mu - c||) for the camera centre
+ * c, log(1 + mean |Omega_v| over the views seen).  stats[n][6] in the order
+ * of or_render_backward; ring[8][n]; feat[n][16]. */
+void or_mlp_features(int64_t n, const double *means, const double *log_scales, const double *opacity_logits,
+                     const double *stats, const double *ring, int32_t head, const double cam[3], double *feat);
+
+/* Densify / prune actions on explicit Gaussians (Sec. 3.3.2 decisions
+ * applied per Gaussian; the clone / split rule is a reading, the paper
+ * spawns anchors).  Rows are [means 3, log-scales 3, quaternion 4, opacity
+ * logit 1, SH 3K] (K_row values each).  Gaussian i emits, in source order:
+ * nothing if prune[i]; itself if not densify[i]; else, when its largest
+ * log-scale exceeds split_log_scale, two children mu + R S xi_j (xi_j =
+ * noise[i][3j..3j+2], R S the covariance factor) with log-scales reduced by
+ * log(split_factor), otherwise itself and an identical clone.  Moments m, v
+ * (nullable, same rows) follow the survivor; clones and split children start
+ * at zero.  Writes at most cap rows and returns the rows needed. */
+int64_t or_densify_prune(int64_t n, int32_t K_row, const double *P, const double *m, const double *v,
+                         const uint8_t *densify, const uint8_t *prune, const double *noise,
+                         double split_log_scale, double split_factor, int64_t cap, double *P_out,
+                         double *m_out, double *v_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -340,6 +340,87 @@ gs_status gs_prune_stats(const gs_stats *stats, int64_t n, int32_t n_views, floa
                          float tau_p, const gs_chunk_scores *out, void *ws, size_t ws_bytes,
                          gs_stream stream);
 
+/*
+ * Densify / prune actions (Sec. 3.3.2 decisions applied per explicit
+ * Gaussian; the paper spawns anchors, clone / split is the reading here).
+ * Source Gaussian i emits, in source order: nothing when prune[i]; itself
+ * when not densify[i]; otherwise two rows: when its largest log-scale
+ * exceeds split_log_scale, two children mu + R S xi_j (xi_0 = noise planes
+ * 0-2, xi_1 = planes 3-5 of noise [6][src->ld], standard normal samples the
+ * caller draws; R S the covariance factor) with every log-scale reduced by
+ * log(split_factor), else itself and an identical clone.  dst (same SH
+ * degree) receives the rows; its capacity is dst->ld (dst->n is ignored).
+ * src_m / src_v and dst_m / dst_v (nullable together) are the Adam moments:
+ * the survivor keeps its own, clones and split children start at zero.
+ * n_out (device int64) receives the rows needed; rows past the capacity are
+ * dropped and status gets bit 1<<GS_ERR_CAPACITY.  densify, prune: [n]
+ * bytes (0 / 1), e.g. gs_chunk_scores or gs_mlp_forward decisions.
+ * ws: gs_actions_workspace_size bytes.
+ */
+gs_status gs_actions_workspace_size(int64_t n, size_t *bytes);
+gs_status gs_densify_prune(const gs_params *src, const gs_params *src_m, const gs_params *src_v,
+                           const uint8_t *densify, const uint8_t *prune, const float *noise,
+                           float split_log_scale, float split_factor, const gs_params *dst,
+                           const gs_params *dst_m, const gs_params *dst_v, int64_t *n_out,
+                           int32_t *status, void *ws, size_t ws_bytes, gs_stream stream);
+
+/*
+ * Learned densify / prune predictor (not in the paper: an MLP trained on the
+ * decisions of the plain criterion above, which stays the fallback and the
+ * judge of its error).  16 inputs -> 64 -> 64 (ReLU) -> 2 logits (sigmoid):
+ * output 0 = densify, 1 = prune.  Weights: one FP32 array of GS_MLP_WEIGHTS
+ * floats, W1[64][16] at 0, b1[64] at 1024, W2[64][64] at 1088, b2[64] at
+ * 5184, W3[2][64] at 5248, b3[2] at 5376.  Layers 1 and 2 (and the data
+ * gradient through layer 2) run on the tensor cores with BF16 inputs,
+ * weights and hidden activations and FP32 accumulation; biases, the output
+ * layer and every gradient reduction stay FP32.
+ */
+#define GS_MLP_INPUTS 16
+#define GS_MLP_HIDDEN 64
+#define GS_MLP_WEIGHTS 5378
+#define GS_MLP_RING 8
+
+/*
+ * Moves plane 3 of stats (max T*alpha since the last push) into plane slot
+ * (0 <= slot < GS_MLP_RING) of ring [GS_MLP_RING][ring_ld] and zeroes it,
+ * once per view (or per batch of views) rendered with statistics.
+ */
+gs_status gs_mlp_push_blend(const gs_stats *stats, int64_t n, float *ring, int64_t ring_ld, int32_t slot,
+                            gs_stream stream);
+
+/*
+ * The 16 inputs per Gaussian, planes of params->ld in feat [16][ld]:
+ * 0 sigmoid(opacity logit); 1-3 log-scales; 4 log(1 + views seen);
+ * 5 log(1 + 1e4 * accumulated ||dL/d(u,v)||); 6-13 max T*alpha of the last
+ * 8 views, most recent first (ring planes head, head-1, ... mod 8);
+ * 14 log(1 + ||mu - cam_centre||); 15 log(1 + mean |Omega_v| over the views
+ * seen).  stats: the lifecycle accumulators (ld = params->ld); ring
+ * [GS_MLP_RING][params->ld]; cam_centre (host) e.g. the chunk's last camera.
+ */
+gs_status gs_mlp_features(const gs_params *params, const gs_stats *stats, const float *ring, int32_t head,
+                          const float cam_centre[3], float *feat, gs_stream stream);
+
+/*
+ * Inference over n rows of feat [16][ld]: prob [2][ld] (nullable) gets the
+ * sigmoid outputs; densify / prune [n] bytes (nullable) get logit > 0.
+ * status (nullable) gets bit 1<<GS_ERR_TIMEOUT if a tensor-core wait gave up.
+ */
+gs_status gs_mlp_forward(const float *feat, int64_t n, int64_t ld, const float *weights, float *prob,
+                         uint8_t *densify, uint8_t *prune, int32_t *status, gs_stream stream);
+
+/*
+ * Mean binary cross-entropy over the n rows and both outputs against the
+ * labels y_densify, y_prune ([n] bytes, 0 / 1) and its gradient: grad
+ * [GS_MLP_WEIGHTS] and loss [1] (device) are overwritten.
+ */
+gs_status gs_mlp_train_grad(const float *feat, const uint8_t *y_densify, const uint8_t *y_prune, int64_t n,
+                            int64_t ld, const float *weights, float *grad, float *loss, int32_t *status,
+                            gs_stream stream);
+
+/* Adam with bias correction (as gs_adam) over the GS_MLP_WEIGHTS weights. */
+gs_status gs_mlp_adam(float *weights, const float *grad, float *exp_avg, float *exp_avg_sq, float lr,
+                      float beta1, float beta2, float eps, int64_t step, gs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

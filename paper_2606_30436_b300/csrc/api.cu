@@ -367,3 +367,83 @@ GS_API gs_status gs_prune_stats(const gs_stats *stats, int64_t n, int32_t n_view
                  out->prune, ws, (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
 }
+
+GS_API gs_status gs_actions_workspace_size(int64_t n, size_t *bytes) {
+    if (n < 0 || !bytes) return GS_ERR_INVALID;
+    *bytes = actions_workspace_bytes(n);
+    return GS_OK;
+}
+
+GS_API gs_status gs_densify_prune(const gs_params *src, const gs_params *src_m, const gs_params *src_v,
+                                  const uint8_t *densify, const uint8_t *prune, const float *noise,
+                                  float split_log_scale, float split_factor, const gs_params *dst,
+                                  const gs_params *dst_m, const gs_params *dst_v, int64_t *n_out, int32_t *status,
+                                  void *ws, size_t ws_bytes, gs_stream stream) {
+    gs_status st = check_params(src);
+    if (st == GS_OK) st = check_params(dst);
+    if (st != GS_OK) return st;
+    const bool moments = src_m || src_v || dst_m || dst_v;
+    if (moments) {
+        for (const gs_params *q : {src_m, src_v, dst_m, dst_v})
+            if ((st = check_params(q)) != GS_OK) return st;
+        for (const gs_params *q : {src_m, src_v})
+            if (q->ld != src->ld || q->n != src->n || q->sh_degree != src->sh_degree) return GS_ERR_INVALID;
+        for (const gs_params *q : {dst_m, dst_v})
+            if (q->ld != dst->ld || q->sh_degree != dst->sh_degree) return GS_ERR_INVALID;
+    }
+    if (dst->sh_degree != src->sh_degree || !densify || !prune || !noise || !aligned16(noise) || !n_out ||
+        ((uintptr_t)n_out & 7u) || !(split_factor > 0.0f) || !(split_log_scale == split_log_scale) || !ws ||
+        ((uintptr_t)ws & 255u) || ws_bytes < actions_workspace_bytes(src->n) || dst->data == src->data)
+        return GS_ERR_INVALID;
+    return cuda_status(launch_actions(src->data, moments ? src_m->data : nullptr, moments ? src_v->data : nullptr,
+                                      src->n, src->ld, GS_PLANES(src->sh_degree), densify, prune, noise,
+                                      split_log_scale, (float)std::log((double)split_factor), dst->data,
+                                      moments ? dst_m->data : nullptr, moments ? dst_v->data : nullptr, dst->ld,
+                                      (long long *)n_out, status, ws, (cudaStream_t)stream));
+}
+
+GS_API gs_status gs_mlp_push_blend(const gs_stats *stats, int64_t n, float *ring, int64_t ring_ld, int32_t slot,
+                                   gs_stream stream) {
+    if (!stats || !stats->acc || n < 0 || stats->ld < n || !ring || !aligned16(ring) || ring_ld < n ||
+        slot < 0 || slot >= GS_MLP_RING)
+        return GS_ERR_INVALID;
+    return cuda_status(launch_mlp_push_blend(stats->acc, stats->ld, n, ring, ring_ld, slot, (cudaStream_t)stream));
+}
+
+GS_API gs_status gs_mlp_features(const gs_params *params, const gs_stats *stats, const float *ring, int32_t head,
+                                 const float cam_centre[3], float *feat, gs_stream stream) {
+    gs_status st = check_params(params);
+    if (st != GS_OK) return st;
+    if (!stats || !stats->acc || stats->ld != params->ld || !ring || !aligned16(ring) || head < 0 ||
+        head >= GS_MLP_RING || !cam_centre || !feat || !aligned16(feat))
+        return GS_ERR_INVALID;
+    return cuda_status(launch_mlp_features(params->data, params->n, params->ld, stats->acc, stats->ld, ring, head,
+                                           cam_centre, feat, (cudaStream_t)stream));
+}
+
+GS_API gs_status gs_mlp_forward(const float *feat, int64_t n, int64_t ld, const float *weights, float *prob,
+                                uint8_t *densify, uint8_t *prune, int32_t *status, gs_stream stream) {
+    if (!feat || !aligned16(feat) || n < 0 || ld < n || (ld & 3) || !weights || !aligned16(weights) ||
+        (prob && !aligned16(prob)))
+        return GS_ERR_INVALID;
+    return cuda_status(launch_mlp_forward(feat, n, ld, weights, prob, densify, prune, status, (cudaStream_t)stream));
+}
+
+GS_API gs_status gs_mlp_train_grad(const float *feat, const uint8_t *y_densify, const uint8_t *y_prune, int64_t n,
+                                   int64_t ld, const float *weights, float *grad, float *loss, int32_t *status,
+                                   gs_stream stream) {
+    if (!feat || !aligned16(feat) || n < 1 || ld < n || (ld & 3) || !y_densify || !y_prune || !weights ||
+        !aligned16(weights) || !grad || !aligned16(grad) || !loss)
+        return GS_ERR_INVALID;
+    return cuda_status(launch_mlp_train(feat, y_densify, y_prune, n, ld, weights, grad, loss, status,
+                                        (cudaStream_t)stream));
+}
+
+GS_API gs_status gs_mlp_adam(float *weights, const float *grad, float *exp_avg, float *exp_avg_sq, float lr,
+                             float beta1, float beta2, float eps, int64_t step, gs_stream stream) {
+    if (!weights || !grad || !exp_avg || !exp_avg_sq || step < 1 || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f) || !(lr >= 0.0f))
+        return GS_ERR_INVALID;
+    return cuda_status(launch_mlp_adam(weights, grad, exp_avg, exp_avg_sq, lr, beta1, beta2, eps, step,
+                                       (cudaStream_t)stream));
+}

@@ -59,4 +59,22 @@ void launch_prune(const float *acc, long long ld, long long n, int n_views, floa
                   float *S_p, float *prune_max, unsigned char *densify, unsigned char *prune, void *ws,
                   cudaStream_t s);
 
+size_t actions_workspace_bytes(long long n);
+cudaError_t launch_actions(const float *src, const float *src_m, const float *src_v, long long n, long long ld,
+                           int planes, const uint8_t *dens, const uint8_t *prune, const float *noise,
+                           float split_log_scale, float log_split_factor, float *dst, float *dst_m, float *dst_v,
+                           long long dld, long long *n_out, int *status, void *ws, cudaStream_t s);
+
+int mlp_num_weights();
+cudaError_t launch_mlp_push_blend(float *stats, long long sld, long long n, float *ring, long long ld, int slot,
+                                  cudaStream_t s);
+cudaError_t launch_mlp_features(const float *P, long long n, long long ld, const float *stats, long long sld,
+                                const float *ring, int head, const float cam[3], float *feat, cudaStream_t s);
+cudaError_t launch_mlp_forward(const float *feat, long long n, long long ld, const float *w, float *prob,
+                               uint8_t *densify, uint8_t *prune, int *status, cudaStream_t s);
+cudaError_t launch_mlp_train(const float *feat, const uint8_t *y_densify, const uint8_t *y_prune, long long n,
+                             long long ld, const float *w, float *grad, float *loss, int *status, cudaStream_t s);
+cudaError_t launch_mlp_adam(float *w, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
+                            long long step, cudaStream_t s);
+
 }  // namespace gs

@@ -1,0 +1,520 @@
+// mlp.cu -- learned prune / densify predictor: per-Gaussian features, an MLP
+// 16 -> 64 -> 64 -> 2 (ReLU, sigmoid outputs: densify, prune) on the 5th
+// generation tensor cores, and its training step on labels from the plain
+// criterion of Supp. E (S_d > tau_d, S_p > tau_p).
+//
+// Tile = 128 Gaussians = the M of one tcgen05.mma; thread t of the CTA owns
+// row t (TMEM lane t).  Layer 1 (K = 16) and layer 2 (K = 64, four K = 16
+// steps) and, in training, the data gradient dh1 = dh2 W2 (K = 64) run as
+// tcgen05.mma.kind::f16 with BF16 operands in shared memory (K-major, no
+// swizzle: 8x8 core matrices of 128 bytes, leading offset = the next core
+// matrix along K, stride offset = the next 8-row group) and FP32 accumulators
+// in TMEM, read back with tcgen05.ld.  The 64 -> 2 head, the BCE gradient and
+// the weight-gradient reductions over the tile run in FP32 on CUDA cores.
+// Every mbarrier wait is bounded; on a timeout the kernel flags the status
+// word, stops issuing, and still frees its TMEM.
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_bf16.h>
+
+#include "gs_internal.cuh"
+#include "gs_kernels.h"
+
+namespace gs {
+
+constexpr int kIn = 16, kH = 64, kOut = 2, kM = 128;
+constexpr int kW1 = 0, kB1 = kW1 + kH * kIn, kW2 = kB1 + kH, kB2 = kW2 + kH * kH, kW3 = kB2 + kH,
+              kB3 = kW3 + kOut * kH, kNW = kB3 + kOut;
+constexpr int kRing = 8;            // blend-weight history (views)
+constexpr int kTmemCols = 128;      // D1 in columns [0, 64), D2 in [64, 128)
+constexpr long long kSpin = 1 << 24;  // bounded mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Element offset of (row, k) in a K-major no-swizzle operand with `kgroups`
+// core matrices along K per 8-row group.
+__device__ __forceinline__ int cm_off(int row, int k, int kgroups) {
+    return (((row >> 3) * kgroups + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4, leading byte offset
+// >> 4 at bit 16, stride byte offset >> 4 at bit 32, version 1 at bit 46,
+// no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate (bit 4), BF16 A (bit 7)
+// and B (bit 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, bool acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"((uint32_t)acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_addr(mbar)));
+}
+
+// Bounded wait for the mbarrier phase `parity`; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (long long it = 0; it < kSpin && !done; ++it)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_addr(mbar)), "r"(parity));
+    return done != 0;
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane (row) into v.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    #pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 64 columns starting at `col` of this thread's row.
+__device__ __forceinline__ void tmem_row64(uint32_t tmem, int col, float *v) {
+    const uint32_t lane_base = (uint32_t)((threadIdx.x >> 5) * 32) << 16;
+    #pragma unroll
+    for (int c = 0; c < 64; c += 16) tmem_ld16(tmem + lane_base + (uint32_t)(col + c), v + c);
+}
+
+// Operand arrays start on 128-byte boundaries (descriptors need 16).
+struct MlpSmem {
+    alignas(128) __nv_bfloat16 w1[kH * kIn];   // B of layer 1: [n = out][k = in]
+    alignas(128) __nv_bfloat16 w2[kH * kH];    // B of layer 2: [n = out][k = in]
+    alignas(128) __nv_bfloat16 x[kM * kIn];    // A of layer 1: [m][k]
+    alignas(128) __nv_bfloat16 h1[kM * kH];    // A of layer 2: [m][k]
+    float b1[kH], b2[kH], w3[kOut * kH], b3[kOut];
+    uint64_t mbar;
+    uint32_t tmem;
+};
+
+__device__ void tmem_alloc(uint32_t *slot) {
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_addr(slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+}
+
+__device__ void tmem_free(uint32_t tmem) {
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem),
+                                               "r"(kTmemCols));
+}
+
+// Loads the weights into shared memory (BF16 operands, FP32 rest), allocates
+// TMEM and initialises the mbarrier.
+__device__ void mlp_setup(MlpSmem &s, const float *__restrict__ w) {
+    for (int i = threadIdx.x; i < kH * kIn; i += blockDim.x) {
+        const int o = i / kIn, c = i % kIn;
+        s.w1[cm_off(o, c, kIn / 8)] = __float2bfloat16_rn(w[kW1 + i]);
+    }
+    for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+        const int o = i / kH, c = i % kH;
+        s.w2[cm_off(o, c, kH / 8)] = __float2bfloat16_rn(w[kW2 + i]);
+    }
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) { s.b1[i] = w[kB1 + i]; s.b2[i] = w[kB2 + i]; }
+    for (int i = threadIdx.x; i < kOut * kH; i += blockDim.x) s.w3[i] = w[kW3 + i];
+    if (threadIdx.x < kOut) s.b3[threadIdx.x] = w[kB3 + threadIdx.x];
+    tmem_alloc(&s.tmem);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&s.mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+}
+
+// After a timed-out wait no further MMA is issued; the last one committed
+// (parity phase ^ 1) gets one more bounded wait before its TMEM is freed.
+__device__ void mlp_finish(MlpSmem &s, bool ok, uint32_t phase, int *status) {
+    if (!ok) {
+        mbar_wait(&s.mbar, phase ^ 1u);
+        if (threadIdx.x == 0 && status) atomicOr(status, 1 << GS_ERR_TIMEOUT);
+    }
+    tmem_free(s.tmem);
+}
+
+// One tile's forward through layer 2.  The thread's features are already in
+// s.x; on return h2 (64 FP32, after ReLU) and h1 (64 FP32, after ReLU) hold
+// the thread's row.  Returns false on a wait timeout.
+__device__ bool mlp_tile_forward(MlpSmem &s, uint32_t &phase, float *h1, float *h2) {
+    const uint32_t tmem = s.tmem;
+    asm volatile("fence.proxy.async.shared::cta;");  // s.x written by threads, read by the tensor core
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // layer 1: D1[128 x 64] = X[128 x 16] W1^T, one K = 16 step
+        mma_bf16(tmem, smem_desc(smem_addr(s.x), 128, 256), smem_desc(smem_addr(s.w1), 128, 256),
+                 idesc_bf16(kM, kH), false);
+        mma_commit(&s.mbar);
+    }
+    bool ok = mbar_wait(&s.mbar, phase);
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        tmem_row64(tmem, 0, h1);
+        #pragma unroll
+        for (int c = 0; c < kH; ++c) {
+            h1[c] = fmaxf(h1[c] + s.b1[c], 0.0f);
+            s.h1[cm_off(threadIdx.x, c, kH / 8)] = __float2bfloat16_rn(h1[c]);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    ok = __syncthreads_and(ok);
+    if (ok && threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // layer 2: D2[128 x 64] = H1[128 x 64] W2^T, four K = 16 steps of two core matrices each
+        #pragma unroll
+        for (int kb = 0; kb < kH / 16; ++kb)
+            mma_bf16(tmem + 64, smem_desc(smem_addr(s.h1) + kb * 256, 128, 1024),
+                     smem_desc(smem_addr(s.w2) + kb * 256, 128, 1024), idesc_bf16(kM, kH), kb > 0);
+        mma_commit(&s.mbar);
+    }
+    if (ok) {
+        ok = mbar_wait(&s.mbar, phase);
+        phase ^= 1u;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        tmem_row64(tmem, 64, h2);
+        #pragma unroll
+        for (int c = 0; c < kH; ++c) h2[c] = fmaxf(h2[c] + s.b2[c], 0.0f);
+    }
+    return ok;
+}
+
+__device__ __forceinline__ void stage_features(MlpSmem &s, const float *__restrict__ feat, long long ld, long long row,
+                                               bool valid, float *x) {
+    #pragma unroll
+    for (int c = 0; c < kIn; ++c) {
+        const float v = valid ? feat[c * ld + row] : 0.0f;
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        s.x[cm_off(threadIdx.x, c, kIn / 8)] = b;
+        if (x) x[c] = __bfloat162float(b);
+    }
+}
+
+__global__ void __launch_bounds__(kM) k_mlp_forward(const float *__restrict__ feat, long long n, long long ld,
+                                                     const float *__restrict__ w, float *__restrict__ prob,
+                                                     uint8_t *__restrict__ densify, uint8_t *__restrict__ prune,
+                                                     int *__restrict__ status) {
+    __shared__ __align__(1024) MlpSmem s;
+    mlp_setup(s, w);
+    uint32_t phase = 0;
+    bool ok = true;
+    const long long tiles = ceil_div(n, (long long)kM);
+    for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const long long row = t * kM + threadIdx.x;
+        const bool valid = row < n;
+        stage_features(s, feat, ld, row, valid, nullptr);
+        float h1[kH], h2[kH];
+        ok = mlp_tile_forward(s, phase, h1, h2);
+        if (ok && valid) {
+            #pragma unroll
+            for (int k = 0; k < kOut; ++k) {
+                float z = s.b3[k];
+                #pragma unroll
+                for (int c = 0; c < kH; ++c) z += s.w3[k * kH + c] * h2[c];
+                if (prob) prob[k * ld + row] = 1.0f / (1.0f + expf(-z));
+                uint8_t *dec = k == 0 ? densify : prune;
+                if (dec) dec[row] = z > 0.0f ? 1 : 0;  // sigmoid(z) > 1/2
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        ok = __syncthreads_and(ok);
+    }
+    mlp_finish(s, ok, phase, status);
+}
+
+// Training step: mean BCE over the n rows and both outputs, gradient of every
+// weight accumulated into grads (FP32 atomics, one set per CTA).
+struct MlpTrainSmem {
+    MlpSmem f;
+    alignas(128) __nv_bfloat16 w2t[kH * kH];   // B of the data gradient: [n = in][k = out] = W2^T
+    alignas(128) __nv_bfloat16 dh2b[kM * kH];  // A of the data gradient: [m][k = out]
+    float h1[kM][kH + 1];         // FP32 copies for the weight-gradient reductions
+    float hd[kM][kH + 1];         // h2, then dh1
+    float dh2[kM][kH + 1];
+    float x[kM][kIn + 1];
+    float dz[kM][kOut];
+    float red[kM / 32];
+};
+
+static_assert(offsetof(MlpTrainSmem, w2t) % 128 == 0 && offsetof(MlpTrainSmem, dh2b) % 128 == 0,
+              "tensor-core operands must be 16-byte aligned");
+static_assert(sizeof(MlpTrainSmem) + 1024 <= 227 * 1024, "training tile exceeds shared memory");
+
+__global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat, const uint8_t *__restrict__ y_densify,
+                                                   const uint8_t *__restrict__ y_prune, long long n, long long ld, const float *__restrict__ w,
+                                                   float *__restrict__ grad, float *__restrict__ loss,
+                                                   int *__restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    MlpTrainSmem &s = *reinterpret_cast<MlpTrainSmem *>(smem_raw);
+    mlp_setup(s.f, w);
+    for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+        const int o = i / kH, c = i % kH;  // W2[o][c] -> B[n = c][k = o]
+        s.w2t[cm_off(c, o, kH / 8)] = __float2bfloat16_rn(w[kW2 + i]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+
+    const int t = threadIdx.x;
+    const float scale = 1.0f / (float)(n * kOut);
+    // per-thread shares of the weight gradient: W3 (k, c) = (t / 64, t % 64);
+    // W2 rows o = t / 2, columns 32 (t % 2) .. + 32; W1 rows o = t / 2, columns 8 (t % 2) .. + 8
+    float gw3 = 0.f, gb3 = 0.f, gw2[32], gw1[8], gb2 = 0.f, gb1 = 0.f;
+    #pragma unroll
+    for (int j = 0; j < 32; ++j) gw2[j] = 0.f;
+    #pragma unroll
+    for (int j = 0; j < 8; ++j) gw1[j] = 0.f;
+    double lsum = 0.0;
+    uint32_t phase = 0;
+    bool ok = true;
+    const long long tiles = ceil_div(n, (long long)kM);
+    for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const long long row = tile * kM + t;
+        const bool valid = row < n;
+        float xr[kIn];
+        stage_features(s.f, feat, ld, row, valid, xr);
+        float dz[kOut] = {0.f, 0.f};
+        {
+            float h1[kH], h2[kH];
+            ok = mlp_tile_forward(s.f, phase, h1, h2);
+            #pragma unroll
+            for (int c = 0; c < kH; ++c) {
+                s.h1[t][c] = h1[c];
+                s.hd[t][c] = h2[c];
+            }
+        }
+        // head, BCE and dL/dh2 (FP32, this thread's row)
+        if (ok && valid) {
+            #pragma unroll
+            for (int k = 0; k < kOut; ++k) {
+                float z = s.f.b3[k];
+                #pragma unroll
+                for (int c = 0; c < kH; ++c) z += s.f.w3[k * kH + c] * s.hd[t][c];
+                const float p = 1.0f / (1.0f + expf(-z));
+                const float y = (k == 0 ? y_densify[row] : y_prune[row]) ? 1.0f : 0.0f;
+                // BCE from the logit: log(1 + e^z) - y z, stable for either sign of z
+                lsum += (double)(fmaxf(z, 0.0f) - y * z + log1pf(expf(-fabsf(z))));
+                dz[k] = (p - y) * scale;
+            }
+        }
+        #pragma unroll 8
+        for (int c = 0; c < kH; ++c) {
+            const float d = dz[0] * s.f.w3[c] + dz[1] * s.f.w3[kH + c];
+            const float dh2 = s.hd[t][c] > 0.0f ? d : 0.0f;
+            s.dh2[t][c] = dh2;
+            // the tensor-core operand carries dh2 / scale (O(1) values) and the product is rescaled
+            s.dh2b[cm_off(t, c, kH / 8)] = __float2bfloat16_rn(dh2 / scale);
+        }
+        #pragma unroll
+        for (int c = 0; c < kIn; ++c) s.x[t][c] = xr[c];
+        s.dz[t][0] = dz[0];
+        s.dz[t][1] = dz[1];
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        ok = __syncthreads_and(ok);
+        if (ok && t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // dh1 (before the ReLU mask) = dh2 W2 -> TMEM columns [0, 64)
+            #pragma unroll
+            for (int kb = 0; kb < kH / 16; ++kb)
+                mma_bf16(s.f.tmem, smem_desc(smem_addr(s.dh2b) + kb * 256, 128, 1024),
+                         smem_desc(smem_addr(s.w2t) + kb * 256, 128, 1024), idesc_bf16(kM, kH), kb > 0);
+            mma_commit(&s.f.mbar);
+        }
+        // weight gradients of the head and of layer 2 while the tensor core works
+        if (ok) {
+            const int k3 = t / kH, c3 = t % kH;
+            const int o = t >> 1, half = t & 1;
+            for (int r = 0; r < kM; ++r) {
+                gw3 += s.dz[r][k3] * s.hd[r][c3];
+                const float d2 = s.dh2[r][o];
+                gb2 += (half == 0) ? d2 : 0.0f;
+                #pragma unroll
+                for (int j = 0; j < 32; ++j) gw2[j] += d2 * s.h1[r][32 * half + j];
+            }
+            if (t < kOut)
+                for (int r = 0; r < kM; ++r) gb3 += s.dz[r][t];
+        }
+        if (ok) {
+            ok = mbar_wait(&s.f.mbar, phase);
+            phase ^= 1u;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();  // everyone done reading hd (h2) before it becomes dh1
+        if (ok) {
+            float d1[kH];
+            tmem_row64(s.f.tmem, 0, d1);
+            #pragma unroll
+            for (int c = 0; c < kH; ++c) s.hd[t][c] = s.h1[t][c] > 0.0f ? d1[c] * scale : 0.0f;
+        }
+        ok = __syncthreads_and(ok);
+        if (ok) {
+            const int o = t >> 1, half = t & 1;
+            for (int r = 0; r < kM; ++r) {
+                const float d1 = s.hd[r][o];
+                gb1 += (half == 0) ? d1 : 0.0f;
+                #pragma unroll
+                for (int j = 0; j < 8; ++j) gw1[j] += d1 * s.x[r][8 * half + j];
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        ok = __syncthreads_and(ok);
+    }
+    if (ok) {
+        const int o = t >> 1, half = t & 1;
+        atomicAdd(&grad[kW3 + t], gw3);
+        if (t < kOut) atomicAdd(&grad[kB3 + t], gb3);
+        #pragma unroll
+        for (int j = 0; j < 32; ++j) atomicAdd(&grad[kW2 + o * kH + 32 * half + j], gw2[j]);
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) atomicAdd(&grad[kW1 + o * kIn + 8 * half + j], gw1[j]);
+        if (half == 0) {
+            atomicAdd(&grad[kB2 + o], gb2);
+            atomicAdd(&grad[kB1 + o], gb1);
+        }
+        // BCE partial: warp sums, then one atomic per CTA
+        float lv = (float)lsum;
+        #pragma unroll
+        for (int off = 16; off > 0; off >>= 1) lv += __shfl_xor_sync(0xffffffffu, lv, off);
+        if ((t & 31) == 0) s.red[t >> 5] = lv;
+    }
+    __syncthreads();
+    if (ok && t == 0) {
+        float a = 0.f;
+        for (int i = 0; i < kM / 32; ++i) a += s.red[i];
+        atomicAdd(loss, a * scale);
+    }
+    mlp_finish(s.f, ok, phase, status);
+}
+
+// Per-Gaussian inputs of the predictor (planes of ld), from the parameters,
+// the lifecycle accumulators and the ring of per-view maximum blend weights:
+//  0 opacity sigmoid(logit)       1-3 log-scales
+//  4 log(1 + views seen)          5 log(1 + 1e4 * accumulated ||dL/d(u,v)||)
+//  6-13 max T*alpha of the last 8 views, most recent first (ring slot head, head-1, ...)
+//  14 log(1 + distance from the mean to the camera centre)
+//  15 log(1 + mean |Omega_v| over the views seen)
+__global__ void __launch_bounds__(256) k_mlp_features(const float *__restrict__ P, long long n, long long ld,
+                                                       const float *__restrict__ st, long long sld,
+                                                       const float *__restrict__ ring, int head, float cx, float cy,
+                                                       float cz, float *__restrict__ feat) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const float views = st[5 * sld + g];
+    const float dx = P[0 * ld + g] - cx, dy = P[1 * ld + g] - cy, dz = P[2 * ld + g] - cz;
+    feat[0 * ld + g] = 1.0f / (1.0f + expf(-P[10 * ld + g]));
+    feat[1 * ld + g] = P[3 * ld + g];
+    feat[2 * ld + g] = P[4 * ld + g];
+    feat[3 * ld + g] = P[5 * ld + g];
+    feat[4 * ld + g] = log1pf(views);
+    feat[5 * ld + g] = log1pf(1.0e4f * st[4 * sld + g]);
+    #pragma unroll
+    for (int j = 0; j < kRing; ++j) feat[(6 + j) * ld + g] = ring[(long long)((head - j + kRing) % kRing) * ld + g];
+    feat[14 * ld + g] = log1pf(sqrtf(dx * dx + dy * dy + dz * dz));
+    feat[15 * ld + g] = log1pf(st[0 * sld + g] / fmaxf(views, 1.0f));
+}
+
+// ring[slot] = max T*alpha accumulated since the last push; the accumulator restarts at 0.
+__global__ void __launch_bounds__(256) k_mlp_push_blend(float *__restrict__ st, long long sld, long long n,
+                                                         float *__restrict__ ring, long long ld, int slot) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    ring[(long long)slot * ld + g] = st[3 * sld + g];
+    st[3 * sld + g] = 0.0f;
+}
+
+__global__ void __launch_bounds__(256) k_mlp_adam(float *__restrict__ w, const float *__restrict__ g,
+                                                   float *__restrict__ m, float *__restrict__ v, float lr, float b1,
+                                                   float b2, float eps, float inv_bc1, float inv_sqrt_bc2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kNW) return;
+    const float gg = g[i];
+    const float mm = b1 * m[i] + (1.0f - b1) * gg, vv = b2 * v[i] + (1.0f - b2) * gg * gg;
+    m[i] = mm;
+    v[i] = vv;
+    w[i] -= lr * (mm * inv_bc1) / (sqrtf(vv) * inv_sqrt_bc2 + eps);
+}
+
+int mlp_num_weights() { return kNW; }
+
+static int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+cudaError_t launch_mlp_forward(const float *feat, long long n, long long ld, const float *w, float *prob,
+                               uint8_t *densify, uint8_t *prune, int *status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    // four CTAs per SM fill the SM's 512 TMEM columns (128 each)
+    const long long grid = std::min<long long>(ceil_div(n, (long long)kM), 4ll * sm_count());
+    k_mlp_forward<<<(unsigned)grid, kM, 0, s>>>(feat, n, ld, w, prob, densify, prune, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_train(const float *feat, const uint8_t *y_densify, const uint8_t *y_prune, long long n,
+                             long long ld, const float *w, float *grad, float *loss, int *status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = sizeof(MlpTrainSmem) + 1024;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * kNW, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    const long long grid = std::min<long long>(ceil_div(n, (long long)kM), (long long)sm_count());
+    k_mlp_train<<<(unsigned)grid, kM, smem, s>>>(feat, y_densify, y_prune, n, ld, w, grad, loss, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_features(const float *P, long long n, long long ld, const float *stats, long long sld,
+                                const float *ring, int head, const float cam[3], float *feat, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_mlp_features<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(P, n, ld, stats, sld, ring, head, cam[0], cam[1], cam[2],
+                                                               feat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_push_blend(float *stats, long long sld, long long n, float *ring, long long ld, int slot,
+                                  cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_mlp_push_blend<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(stats, sld, n, ring, ld, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_adam(float *w, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
+                            long long step, cudaStream_t s) {
+    const double bc1 = 1.0 - pow((double)b1, (double)step), bc2 = 1.0 - pow((double)b2, (double)step);
+    k_mlp_adam<<<(unsigned)ceil_div(kNW, 256), 256, 0, s>>>(w, g, m, v, lr, b1, b2, eps, (float)(1.0 / bc1),
+                                                             (float)(1.0 / sqrt(bc2)));
+    return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -82,12 +82,6 @@ __device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const fl
 
 struct Cov3 { float s00, s01, s02, s11, s12, s22; };
 
-__device__ __forceinline__ void quat_rotation(float qw, float qx, float qy, float qz, float *R) {
-    R[0] = 1.f - 2.f * (qy * qy + qz * qz); R[1] = 2.f * (qx * qy - qw * qz); R[2] = 2.f * (qx * qz + qw * qy);
-    R[3] = 2.f * (qx * qy + qw * qz); R[4] = 1.f - 2.f * (qx * qx + qz * qz); R[5] = 2.f * (qy * qz - qw * qx);
-    R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
-}
-
 // EWA 2D covariance (before dilation) from the 3D covariance, for one view.
 struct Ewa { float T[6]; float A, B, C; bool clx_lo, clx_hi, cly_lo, cly_hi; float tx, ty; };
 

@@ -75,7 +75,8 @@ EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspac
            "gs_loss_workspace_size",
            "gs_bwd_workspace_size", "gs_prune_workspace_size", "gs_project", "gs_sort", "gs_render_fwd", "gs_loss",
            "gs_render_bwd", "gs_project_bwd", "gs_adam", "gs_prune_stats", "gs_loss_static",
-           "gs_reg_workspace_size", "gs_geo_loss", "gs_iso_loss")
+           "gs_reg_workspace_size", "gs_geo_loss", "gs_iso_loss", "gs_actions_workspace_size", "gs_densify_prune",
+           "gs_mlp_push_blend", "gs_mlp_features", "gs_mlp_forward", "gs_mlp_train_grad", "gs_mlp_adam")
 
 _lib = None
 
@@ -113,6 +114,14 @@ def lib():
                                      P(Stats), vp]
         L.gs_adam.argtypes = [P(Params), P(Params), P(Params), P(Params), P(f32 * 6), f32, f32, f32, i64, vp, vp]
         L.gs_prune_stats.argtypes = [P(Stats), i64, i32, f32, f32, P(ChunkScores), vp, sz, vp]
+        L.gs_actions_workspace_size.argtypes = [i64, P(sz)]
+        L.gs_densify_prune.argtypes = [P(Params), P(Params), P(Params), vp, vp, vp, f32, f32, P(Params), P(Params),
+                                       P(Params), vp, vp, vp, sz, vp]
+        L.gs_mlp_push_blend.argtypes = [P(Stats), i64, vp, i64, i32, vp]
+        L.gs_mlp_features.argtypes = [P(Params), P(Stats), vp, i32, P(f32 * 3), vp, vp]
+        L.gs_mlp_forward.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
+        L.gs_mlp_train_grad.argtypes = [vp, vp, vp, i64, i64, vp, vp, vp, vp, vp]
+        L.gs_mlp_adam.argtypes = [vp, vp, vp, vp, f32, f32, f32, f32, i64, vp]
         for name in EXPORTS:
             if name not in ("gs_status_string", "gs_version"):
                 getattr(L, name).restype = C.c_int
@@ -418,6 +427,84 @@ def prune_buffers(n, device="cuda"):
     return dict(S_d=torch.zeros(n, dtype=f32, device=device), S_p=torch.zeros(n, dtype=f32, device=device),
                 prune_max=torch.zeros(n, dtype=f32, device=device), densify=torch.zeros(n, dtype=u8, device=device),
                 prune=torch.zeros(n, dtype=u8, device=device)), ws
+
+
+def actions_workspace(n, device="cuda"):
+    return _workspace(lib().gs_actions_workspace_size, n, device=device)
+
+
+def gs_densify_prune(model: GaussianModel, densify, prune, noise, split_log_scale, split_factor=1.6, exp_avg=None,
+                     exp_avg_sq=None, capacity=None, status=None, ws=None, stream=None):
+    """Applies the densify / prune decisions ([n] uint8 device tensors); noise is a [6, ld] float32 tensor of
+    standard normal samples.  Returns (model, exp_avg, exp_avg_sq, n_out) with n_out a device int64 tensor; the new
+    model's n is the host count (one synchronisation)."""
+    dev = model.data.device
+    cap = padded(2 * model.n) if capacity is None else int(capacity)
+    assert cap % 4 == 0
+    out = GaussianModel(0, model.sh_degree, device=dev, data=torch.empty(model.K, cap, dtype=torch.float32,
+                                                                            device=dev))
+    out.ld = cap
+    moments = exp_avg is not None
+    mo = vo = None
+    if moments:
+        mo, vo = (GaussianModel(0, model.sh_degree, device=dev, data=torch.empty(model.K, cap, dtype=torch.float32,
+                                                                                 device=dev)) for _ in range(2))
+        mo.ld = vo.ld = cap
+    n_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = actions_workspace(model.n, device=dev) if ws is None else ws
+    _check(lib().gs_densify_prune(C.byref(model.c()), C.byref(exp_avg.c()) if moments else None,
+                                  C.byref(exp_avg_sq.c()) if moments else None, _ptr(densify), _ptr(prune),
+                                  _ptr(noise), float(split_log_scale), float(split_factor), C.byref(out.c()),
+                                  C.byref(mo.c()) if moments else None, C.byref(vo.c()) if moments else None,
+                                  _ptr(n_out), _ptr(status), _ptr(ws), ws.numel(), _stream(stream)),
+           "gs_densify_prune")
+    n = min(int(n_out.item()), cap)
+    for m in (out, mo, vo):
+        if m is not None:
+            m.n = n
+    return out, mo, vo, n_out
+
+
+MLP_INPUTS, MLP_HIDDEN, MLP_WEIGHTS, MLP_RING = 16, 64, 5378, 8
+
+
+def mlp_init(seed=0, device="cuda"):
+    """He-normal weights and zero biases in the flat layout of gs_mlp_forward."""
+    g = torch.Generator().manual_seed(int(seed))
+    w = torch.zeros(MLP_WEIGHTS, dtype=torch.float32)
+    w[0:1024] = torch.randn(1024, generator=g) * (2.0 / 16) ** 0.5
+    w[1088:5184] = torch.randn(4096, generator=g) * (2.0 / 64) ** 0.5
+    w[5248:5376] = torch.randn(128, generator=g) * (1.0 / 64) ** 0.5
+    return w.to(device)
+
+
+def gs_mlp_push_blend(stats_acc: torch.Tensor, n, ring: torch.Tensor, slot, stream=None):
+    st = Stats(stats_acc.data_ptr(), stats_acc.shape[1])
+    _check(lib().gs_mlp_push_blend(C.byref(st), int(n), _ptr(ring), ring.shape[1], int(slot), _stream(stream)),
+           "gs_mlp_push_blend")
+
+
+def gs_mlp_features(model: GaussianModel, stats_acc: torch.Tensor, ring: torch.Tensor, head, cam_centre,
+                    feat: torch.Tensor, stream=None):
+    st = Stats(stats_acc.data_ptr(), stats_acc.shape[1])
+    cc = (C.c_float * 3)(*[float(x) for x in cam_centre])
+    _check(lib().gs_mlp_features(C.byref(model.c()), C.byref(st), _ptr(ring), int(head), C.byref(cc), _ptr(feat),
+                                 _stream(stream)), "gs_mlp_features")
+
+
+def gs_mlp_forward(feat: torch.Tensor, n, weights, prob=None, densify=None, prune=None, status=None, stream=None):
+    _check(lib().gs_mlp_forward(_ptr(feat), int(n), feat.shape[1], _ptr(weights), _ptr(prob), _ptr(densify),
+                                _ptr(prune), _ptr(status), _stream(stream)), "gs_mlp_forward")
+
+
+def gs_mlp_train_grad(feat: torch.Tensor, y_densify, y_prune, n, weights, grad, loss, status=None, stream=None):
+    _check(lib().gs_mlp_train_grad(_ptr(feat), _ptr(y_densify), _ptr(y_prune), int(n), feat.shape[1], _ptr(weights),
+                                   _ptr(grad), _ptr(loss), _ptr(status), _stream(stream)), "gs_mlp_train_grad")
+
+
+def gs_mlp_adam(weights, grad, exp_avg, exp_avg_sq, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().gs_mlp_adam(_ptr(weights), _ptr(grad), _ptr(exp_avg), _ptr(exp_avg_sq), float(lr), float(beta1),
+                             float(beta2), float(eps), int(step), _stream(stream)), "gs_mlp_adam")
 
 
 # --------------------------------------------------------------------------

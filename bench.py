@@ -462,6 +462,118 @@ def run_gpu(args, rank, world):
 
 
 # --------------------------------------------------------------------------
+# lifecycle: learned vs plain densify / prune decisions over keyframe chunks
+
+def lifecycle_cams(scenes, f0, views, w, h, f):
+    return [scenes.corridor_camera(f0 + j, w, h, f) for j in range(views)]
+
+
+def psnr(img, ref):
+    import torch
+    mse = torch.mean((img - ref) ** 2).item()
+    return float("inf") if mse == 0 else -10.0 * np.log10(mse)
+
+
+def run_lifecycle(args, dev):
+    """Learned vs plain lifecycle decisions on the corridor: ground truth G*
+    (the corridor scene), an initial map with 30 % of G* removed, 20 % floaters
+    added and N(0, 0.01) on every entry; chunks of `views` consecutive frames,
+    `iters` batched mapping iterations each (statistics on), then decisions and
+    densify / prune actions.  The predictor is trained on the plain criterion's
+    bits from training chunks (frames from 100) and both arms run the same
+    evaluation chunks (frames from 500)."""
+    import torch
+    from paper_2606_30436_b300 import gs, lifecycle, scenes
+    n_gt, V, T = args.lifecycle_gaussians, args.lifecycle_views, args.lifecycle_iters
+    w, h, f = W // 2, H // 2, F / 2
+    cfg = gs.Config()
+    gt = scenes.corridor_scene(n_gt, seed=0, sh_degree=SH_DEG)
+    init = scenes.degraded_map(gt, seed=2)
+    train_starts = [100 + 2 * V * k for k in range(args.lifecycle_train_chunks)]
+    eval_starts = [500 + 2 * V * k for k in range(args.lifecycle_chunks)]
+    gt_model = gs.GaussianModel.from_scene(gt, device=dev)
+    targets = {}
+    for f0 in train_starts + eval_starts:
+        st = gs.MappingStep(gt_model, lifecycle_cams(scenes, f0, V, w, h, f), cfg, with_stats=False)
+        st.fit_capacity()
+        targets[f0] = st.buf.img.clone()
+        del st
+    del gt_model
+    lr = gs.default_lr(extent=10.0)
+
+    def render_psnr(model, starts):
+        vals = []
+        for f0 in starts:
+            st = gs.MappingStep(model, lifecycle_cams(scenes, f0, V, w, h, f), cfg, with_stats=False)
+            st.fit_capacity()
+            vals.append(psnr(st.buf.img, targets[f0]))
+            del st
+        return float(np.mean(vals))
+
+    def run_arm(mode, starts, predictor=None, collect=False):
+        model = gs.GaussianModel.from_scene(init, device=dev)
+        lc = lifecycle.Lifecycle(mode, tau_d=args.tau_d, tau_p=args.tau_p, split_log_scale=-2.5,
+                                 predictor=predictor, collect=collect, seed=3)
+        moments, step_count = None, 0
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats(dev)
+        psnr0 = render_psnr(model, starts)
+        iter_ms = end_ms = 0.0
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        for f0 in starts:
+            step = gs.MappingStep(model, lifecycle_cams(scenes, f0, V, w, h, f), cfg, lr=lr, moments=moments,
+                                  step_count=step_count)
+            step.fit_capacity(slack=1.5)
+            lc.start(step)
+            ev[0].record()
+            for _ in range(T):
+                step.step(targets[f0])
+                lc.after_iteration(step)
+            ev[1].record()
+            step.check_status()
+            centre = -np.asarray(step.buf.cams[-1]["R"], np.float64).T @ np.asarray(step.buf.cams[-1]["t"])
+            dens, prune = lc.decide(step, centre)
+            model, moments = lc.apply(step, dens, prune)
+            ev[2].record()
+            torch.cuda.synchronize()
+            iter_ms += ev[0].elapsed_time(ev[1])
+            end_ms += ev[1].elapsed_time(ev[2])
+            step_count = step.step_count
+            del step
+        torch.cuda.synchronize()
+        peak = torch.cuda.max_memory_allocated(dev)
+        out = {"iters_per_s": round(len(starts) * T * 1e3 / iter_ms, 2),
+               "iters_per_s_with_decisions": round(len(starts) * T * 1e3 / (iter_ms + end_ms), 2),
+               "ms_per_chunk_decisions": round(end_ms / len(starts), 3),
+               "peak_memory_gb": round(peak / 1e9, 3), "gaussians_start": len(init["means"]),
+               "gaussians_end": model.n, "psnr_start_db": round(psnr0, 3),
+               "psnr_end_db": round(render_psnr(model, starts), 3), "chunks": lc.history}
+        return out, lc
+
+    _, lc_train = run_arm("plain", train_starts, collect=True)
+    pred = lifecycle.Predictor(seed=4, device=dev, lr=args.mlp_lr)
+    t0 = time.perf_counter()
+    bce = pred.train(lc_train.samples, epochs=args.mlp_epochs)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    train_rows = int(sum(smp[1] for smp in lc_train.samples))
+    del lc_train
+    plain, _ = run_arm("plain", eval_starts)
+    learned, _ = run_arm("learned", eval_starts, predictor=pred)
+    return {"metric": "lifecycle mapping iters/s, learned vs plain densify/prune", "unit": "iters/s",
+            "value": learned["iters_per_s_with_decisions"], "plain_value": plain["iters_per_s_with_decisions"],
+            "speedup_vs_plain": round(learned["iters_per_s_with_decisions"] / plain["iters_per_s_with_decisions"], 3),
+            "psnr_delta_db": round(learned["psnr_end_db"] - plain["psnr_end_db"], 3),
+            "peak_memory_ratio": round(learned["peak_memory_gb"] / plain["peak_memory_gb"], 3),
+            "config": {"workload": "corridor G* %d Gaussians SH3; initial map 30%% removed, 20%% floaters, "
+                                   "N(0,0.01); chunks of %d frames at %dx%d, %d iterations each" % (n_gt, V, w, h, T),
+                       "train_chunks": train_starts, "eval_chunks": eval_starts, "tau_d": args.tau_d,
+                       "tau_p": args.tau_p, "mlp_epochs": args.mlp_epochs},
+            "predictor": {"train_bce": round(bce, 5), "train_seconds": round(train_s, 2), "train_rows": train_rows},
+            "plain": plain, "learned": learned, "data": "synthetic", "n_gpus": 1}
+
+
+# --------------------------------------------------------------------------
 # CPU arms: the FP64 oracle on the host cores
 
 def oracle_iteration(scene, tscene_img, cam, oc):
@@ -542,6 +654,17 @@ def main():
     ap.add_argument("--no-chunk", action="store_true", help="skip the batched-chunk measurement")
     ap.add_argument("--chunk-gaussians", type=int, default=2_000_000)
     ap.add_argument("--chunk-views", type=int, default=16)
+    ap.add_argument("--lifecycle", action="store_true",
+                    help="learned vs plain densify/prune over keyframe chunks (prints its own JSON line)")
+    ap.add_argument("--lifecycle-gaussians", type=int, default=1_000_000)
+    ap.add_argument("--lifecycle-views", type=int, default=8)
+    ap.add_argument("--lifecycle-iters", type=int, default=10)
+    ap.add_argument("--lifecycle-chunks", type=int, default=6)
+    ap.add_argument("--lifecycle-train-chunks", type=int, default=6)
+    ap.add_argument("--tau-d", type=float, default=5.0)
+    ap.add_argument("--tau-p", type=float, default=0.99)
+    ap.add_argument("--mlp-epochs", type=int, default=300)
+    ap.add_argument("--mlp-lr", type=float, default=3e-3)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -550,6 +673,11 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.lifecycle:
+        if rank == 0:
+            import torch
+            print(json.dumps(run_lifecycle(args, torch.device("cuda", 0))), flush=True)
         return
     if world > 1:
         import torch

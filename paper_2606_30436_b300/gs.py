@@ -207,10 +207,11 @@ def view_layout(cams, cfg: Config):
 class GaussianModel:
     """Parameters of n Gaussians as one [K, ld] float32 device tensor."""
 
-    def __init__(self, n, sh_degree, device="cuda", data=None):
+    def __init__(self, n, sh_degree, device="cuda", data=None, ld=None):
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.K = planes(self.sh_degree)
-        self.ld = padded(self.n)
+        self.ld = int(data.shape[1]) if data is not None else (padded(self.n) if ld is None else int(ld))
+        assert self.ld >= self.n and self.ld % 4 == 0
         self.data = torch.zeros(self.K, self.ld, dtype=torch.float32, device=device) if data is None else data
 
     @classmethod
@@ -220,7 +221,7 @@ class GaussianModel:
         return m
 
     def like(self):
-        return GaussianModel(self.n, self.sh_degree, device=self.data.device)
+        return GaussianModel(self.n, self.sh_degree, device=self.data.device, ld=self.ld)
 
     def c(self) -> Params:
         return Params(self.data.data_ptr(), self.n, self.ld, self.sh_degree)
@@ -441,15 +442,14 @@ def gs_densify_prune(model: GaussianModel, densify, prune, noise, split_log_scal
     dev = model.data.device
     cap = padded(2 * model.n) if capacity is None else int(capacity)
     assert cap % 4 == 0
-    out = GaussianModel(0, model.sh_degree, device=dev, data=torch.empty(model.K, cap, dtype=torch.float32,
-                                                                            device=dev))
-    out.ld = cap
+
+    def empty():
+        return GaussianModel(0, model.sh_degree, device=dev,
+                             data=torch.zeros(model.K, max(cap, 4), dtype=torch.float32, device=dev))
+
+    out = empty()
     moments = exp_avg is not None
-    mo = vo = None
-    if moments:
-        mo, vo = (GaussianModel(0, model.sh_degree, device=dev, data=torch.empty(model.K, cap, dtype=torch.float32,
-                                                                                 device=dev)) for _ in range(2))
-        mo.ld = vo.ld = cap
+    mo, vo = (empty(), empty()) if moments else (None, None)
     n_out = torch.zeros(1, dtype=torch.int64, device=dev)
     ws = actions_workspace(model.n, device=dev) if ws is None else ws
     _check(lib().gs_densify_prune(C.byref(model.c()), C.byref(exp_avg.c()) if moments else None,
@@ -522,7 +522,7 @@ class MappingStep:
 
     def __init__(self, model: GaussianModel, cams, cfg: Config = None, max_pairs=None, lambda_dssim=0.2,
                  tau_err=0.1, lr=None, with_stats=True, with_depth=False, depth_prior=None, lambda_geo=0.01,
-                 lambda_iso=0.0):
+                 lambda_iso=0.0, moments=None, step_count=0):
         self.model = model
         self.cfg = cfg or Config()
         self.lambda_dssim, self.tau_err = lambda_dssim, tau_err
@@ -531,8 +531,11 @@ class MappingStep:
         with_depth = with_depth or depth_prior is not None
         self.lr = lr or default_lr()
         self.with_stats = with_stats
-        self.grads, self.exp_avg, self.exp_avg_sq = model.like(), model.like(), model.like()
-        self.step_count = 0
+        self.grads = model.like()
+        # Adam moments: zero, or carried over (e.g. through gs_densify_prune)
+        self.exp_avg, self.exp_avg_sq = moments if moments is not None else (model.like(), model.like())
+        assert self.exp_avg.ld == model.ld and self.exp_avg_sq.ld == model.ld
+        self.step_count = int(step_count)
         if max_pairs is None:
             max_pairs = max(1 << 16, 8 * model.n * len(cams))
         self.buf = Buffers(model, cams, self.cfg, max_pairs, with_depth=with_depth, with_stats=with_stats)

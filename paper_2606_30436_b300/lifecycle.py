@@ -1,0 +1,143 @@
+"""Gaussian lifecycle over keyframe chunks (Sec. 3.3.2; scores of Supp. E.1,
+E.2).  The mapping iterations of a chunk accumulate the per-Gaussian
+statistics (|Omega|, kappa, gamma, max T*alpha, ||dL/d(u,v)||, views seen) in
+the backward pass; at the end of the chunk one of two deciders turns them into
+densify / prune bits, and ``gs_densify_prune`` applies the bits to the
+parameters and the Adam moments:
+
+* ``plain``: the paper's criterion, ``gs_prune_stats`` (S_d > tau_d,
+  min-max-normalised S_p > tau_p over the active Gaussians);
+* ``learned``: the BF16 tensor-core predictor (``gs_mlp_features`` +
+  ``gs_mlp_forward``) trained on the plain criterion's bits, which stays the
+  fallback and the judge of its error (``agreement``).
+
+Readings: the statistics of a chunk are summed over its iterations and views,
+so |V_c| = iterations x views; decisions are taken and applied per chunk (the
+OR / max aggregation over chunks of Sec. 3.3.2 would need the bits of
+Gaussians that no longer exist after the actions); the blend-weight ring takes
+one slot per iteration (each slot the maximum over that iteration's views).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import gs
+
+
+class Predictor:
+    """Weights, Adam state and the training loop of the learned decider."""
+
+    def __init__(self, seed=0, device="cuda", lr=3e-3):
+        self.w = gs.mlp_init(seed, device=device)
+        self.m, self.v = torch.zeros_like(self.w), torch.zeros_like(self.w)
+        self.grad = torch.zeros_like(self.w)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.lr, self.step = lr, 0
+
+    def train(self, batches, epochs=200):
+        """Full-batch Adam over (feat [16, ld], n, y_densify, y_prune) tuples; returns the last mean BCE."""
+        losses = []
+        for _ in range(epochs):
+            for feat, n, yd, yp in batches:
+                gs.gs_mlp_train_grad(feat, yd, yp, n, self.w, self.grad, self.loss, self.status)
+                self.step += 1
+                gs.gs_mlp_adam(self.w, self.grad, self.m, self.v, self.lr, self.step)
+                losses.append(self.loss)
+        if self.status.item():
+            raise gs.GSError("predictor status %d" % self.status.item())
+        return float(losses[-1].item()) if losses else float("nan")
+
+    def predict(self, feat, n, densify, prune, prob=None):
+        gs.gs_mlp_forward(feat, n, self.w, prob, densify, prune, self.status)
+
+
+class Lifecycle:
+    """Statistics, decisions and actions of one chunk at a time."""
+
+    def __init__(self, mode="plain", tau_d=5.0, tau_p=0.99, split_log_scale=-2.5, split_factor=1.6,
+                 predictor: Predictor = None, collect=False, seed=0):
+        assert mode in ("plain", "learned")
+        assert mode == "plain" or predictor is not None
+        self.mode, self.tau_d, self.tau_p = mode, tau_d, tau_p
+        self.split_log_scale, self.split_factor = split_log_scale, split_factor
+        self.predictor, self.collect = predictor, collect
+        self.samples = []   # (feat, n, y_densify, y_prune) of each chunk, with collect=True
+        self.history = []   # per chunk: n before / after, bits set, agreement with the plain criterion
+        self.gen = torch.Generator(device="cuda").manual_seed(int(seed))
+        self.ring = None
+        self.head = gs.MLP_RING - 1
+        self.iterations = 0
+
+    def start(self, step: gs.MappingStep):
+        """Zeroes the accumulators before the chunk's first iteration."""
+        assert step.buf.stats_acc is not None, "the mapping step must accumulate statistics"
+        step.buf.stats_acc.zero_()
+        ld = step.model.ld
+        if self.ring is None or self.ring.shape[1] != ld:
+            self.ring = torch.zeros(gs.MLP_RING, ld, dtype=torch.float32, device=step.model.data.device)
+        else:
+            self.ring.zero_()
+        self.head = gs.MLP_RING - 1
+        self.iterations = 0
+
+    def after_iteration(self, step: gs.MappingStep):
+        """Moves this iteration's max T*alpha into the ring."""
+        self.head = (self.head + 1) % gs.MLP_RING
+        gs.gs_mlp_push_blend(step.buf.stats_acc, step.model.n, self.ring, self.head)
+        self.iterations += 1
+
+    def _features(self, step, cam_centre):
+        model = step.model
+        feat = torch.zeros(gs.MLP_INPUTS, model.ld, dtype=torch.float32, device=model.data.device)
+        gs.gs_mlp_features(model, step.buf.stats_acc, self.ring, self.head, cam_centre, feat)
+        return feat
+
+    def decide(self, step: gs.MappingStep, cam_centre):
+        """Densify / prune bits ([n] uint8) of the chunk's Gaussians."""
+        model, dev = step.model, step.model.data.device
+        n = model.n
+        n_views = max(1, self.iterations * step.buf.n_views)
+        scores, ws = gs.prune_buffers(n, device=dev)
+        gs.gs_prune_stats(step.buf.stats_acc, n, n_views, scores, ws, self.tau_d, self.tau_p)
+        plain_d, plain_p = scores["densify"], scores["prune"]
+        rec = dict(n=n)
+        if self.mode == "plain" and not self.collect:
+            dens, prune = plain_d, plain_p
+        else:
+            feat = self._features(step, cam_centre)
+            if self.collect:
+                self.samples.append((feat, n, plain_d.clone(), plain_p.clone()))
+            if self.mode == "learned":
+                dens = torch.zeros(n, dtype=torch.uint8, device=dev)
+                prune = torch.zeros(n, dtype=torch.uint8, device=dev)
+                self.predictor.predict(feat, n, dens, prune)
+                rec.update(agreement(dens, prune, plain_d, plain_p))
+            else:
+                dens, prune = plain_d, plain_p
+        rec.update(densify=int(dens.sum().item()), prune=int(prune.sum().item()))
+        self.history.append(rec)
+        return dens, prune
+
+    def apply(self, step: gs.MappingStep, dens, prune):
+        """New parameters and moments after the actions."""
+        model = step.model
+        noise = torch.randn(6, model.ld, generator=self.gen, device=model.data.device)
+        out, m, v, _ = gs.gs_densify_prune(model, dens, prune, noise, self.split_log_scale, self.split_factor,
+                                           exp_avg=step.exp_avg, exp_avg_sq=step.exp_avg_sq,
+                                           capacity=gs.padded(model.n + int(dens.sum().item())))
+        self.history[-1]["n_after"] = out.n
+        return out, (m, v)
+
+
+def agreement(dens, prune, ref_d, ref_p):
+    """Precision / recall of the learned bits against the plain criterion's."""
+    out = {}
+    for name, a, b in (("densify", dens, ref_d), ("prune", prune, ref_p)):
+        a, b = a.bool(), b.bool()
+        tp = int((a & b).sum().item())
+        pa, pb = int(a.sum().item()), int(b.sum().item())
+        out[name + "_precision"] = tp / pa if pa else 1.0
+        out[name + "_recall"] = tp / pb if pb else 1.0
+        out[name + "_accuracy"] = float((a == b).float().mean().item()) if a.numel() else 1.0
+    return out

@@ -143,6 +143,28 @@ def perturb(params, sigma=0.01, seed=1):
     return out
 
 
+def degraded_map(scene, remove=0.3, floaters=0.2, sigma=0.01, seed=2, length=1000.0, half_width=10.0,
+                 max_height=8.0):
+    """An initial map for the lifecycle workload: a random `remove` fraction of
+    the scene dropped, `floaters` x n random Gaussians added uniformly in the
+    corridor box (log-scales N(-3, 0.5), opacity logits N(0, 1), SH N(0, 0.1)),
+    and every entry perturbed by N(0, sigma)."""
+    rng = np.random.default_rng(seed)
+    n = len(scene["means"])
+    keep = rng.random(n) >= remove
+    nf = int(round(floaters * n))
+    K = (int(scene["sh_degree"]) + 1) ** 2
+    fl = dict(means=np.stack([rng.uniform(-half_width, half_width, nf), -rng.uniform(0.0, max_height, nf),
+                              rng.uniform(0.0, length, nf)], axis=1).astype(np.float32),
+              log_scales=rng.normal(-3.0, 0.5, (nf, 3)).astype(np.float32), quats=_quats(rng, nf),
+              opacity_logits=rng.standard_normal(nf).astype(np.float32),
+              sh=rng.normal(0.0, 0.1, (nf, K, 3)).astype(np.float32))
+    out = dict(scene)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        out[k] = np.concatenate([np.asarray(scene[k])[keep], fl[k]], axis=0)
+    return perturb(out, sigma, seed=seed + 1)
+
+
 def smooth_image(height, width, seed=3, channels=3):
     """A seeded image in [0,1]: a few random low-frequency waves plus fine noise."""
     rng = np.random.default_rng(seed)

@@ -253,3 +253,46 @@ def test_densify_prune_all_pruned_and_no_moments():
     out, _, _, n_out = gs.gs_densify_prune(model, keep, keep, torch.from_numpy(noise).to(DEV), -3.0)
     assert int(n_out.item()) == n
     assert torch.equal(out.data[:, :n], model.data[:, :n])
+
+
+def test_lifecycle_chunks_plain_and_learned():
+    """Two chunks of the corridor with each decider: row counts follow the bits, moments follow the rows, the
+    learned decider reports its agreement with the plain criterion."""
+    from paper_2606_30436_b300 import lifecycle
+    gt = scenes.corridor_scene(20000, seed=0, sh_degree=1, length=60.0)
+    init = scenes.degraded_map(gt, seed=2, length=60.0)
+    cfg = gs.Config()
+    cams = {f0: [scenes.corridor_camera(f0 + j, 160, 90, 112.5) for j in range(2)] for f0 in (10, 20)}
+    gtm = gs.GaussianModel.from_scene(gt, device=DEV)
+    targets = {}
+    for f0, cs in cams.items():
+        st = gs.MappingStep(gtm, cs, cfg, with_stats=False)
+        st.fit_capacity()
+        targets[f0] = st.buf.img.clone()
+    pred = lifecycle.Predictor(seed=1, device=DEV)
+    for mode in ("plain", "learned"):
+        model = gs.GaussianModel.from_scene(init, device=DEV)
+        lc = lifecycle.Lifecycle(mode, tau_d=1.0, tau_p=0.9, predictor=pred, collect=(mode == "plain"))
+        moments, steps = None, 0
+        for f0 in (10, 20):
+            step = gs.MappingStep(model, cams[f0], cfg, moments=moments, step_count=steps)
+            step.fit_capacity(slack=1.5)
+            lc.start(step)
+            for _ in range(3):
+                step.step(targets[f0])
+                lc.after_iteration(step)
+            step.check_status()
+            n = model.n
+            dens, prune = lc.decide(step, [0.0, -1.6, float(f0 + 1)])
+            d, p = dens.cpu().numpy().astype(bool), prune.cpu().numpy().astype(bool)
+            model, moments = lc.apply(step, dens, prune)
+            assert model.n == n - p.sum() + (d & ~p).sum()
+            assert moments[0].ld == model.ld and moments[0].n == model.n
+            assert torch.isfinite(model.data[:, :model.n]).all()
+            steps = step.step_count
+        assert len(lc.history) == 2
+        if mode == "plain":
+            assert len(lc.samples) == 2 and any(h["densify"] + h["prune"] > 0 for h in lc.history)
+            pred.train(lc.samples, epochs=20)
+        else:
+            assert all("prune_recall" in h for h in lc.history)

@@ -93,31 +93,42 @@ class Lifecycle:
         gs.gs_mlp_features(model, step.buf.stats_acc, self.ring, self.head, cam_centre, feat)
         return feat
 
+    def plain_bits(self, step: gs.MappingStep):
+        """The plain criterion's bits (Supp. E.1, E.2) from the chunk's accumulators."""
+        n = step.model.n
+        n_views = max(1, self.iterations * step.buf.n_views)
+        scores, ws = gs.prune_buffers(n, device=step.model.data.device)
+        gs.gs_prune_stats(step.buf.stats_acc, n, n_views, scores, ws, self.tau_d, self.tau_p)
+        return scores["densify"], scores["prune"]
+
     def decide(self, step: gs.MappingStep, cam_centre):
-        """Densify / prune bits ([n] uint8) of the chunk's Gaussians."""
+        """Densify / prune bits ([n] uint8) of the chunk's Gaussians, by the
+        chosen decider; nothing here synchronises the host."""
         model, dev = step.model, step.model.data.device
         n = model.n
-        n_views = max(1, self.iterations * step.buf.n_views)
-        scores, ws = gs.prune_buffers(n, device=dev)
-        gs.gs_prune_stats(step.buf.stats_acc, n, n_views, scores, ws, self.tau_d, self.tau_p)
-        plain_d, plain_p = scores["densify"], scores["prune"]
-        rec = dict(n=n)
-        if self.mode == "plain" and not self.collect:
-            dens, prune = plain_d, plain_p
+        self._last = None
+        if self.mode == "plain":
+            dens, prune = self.plain_bits(step)
+            if self.collect:
+                self.samples.append((self._features(step, cam_centre), n, dens.clone(), prune.clone()))
         else:
             feat = self._features(step, cam_centre)
-            if self.collect:
-                self.samples.append((feat, n, plain_d.clone(), plain_p.clone()))
-            if self.mode == "learned":
-                dens = torch.zeros(n, dtype=torch.uint8, device=dev)
-                prune = torch.zeros(n, dtype=torch.uint8, device=dev)
-                self.predictor.predict(feat, n, dens, prune)
-                rec.update(agreement(dens, prune, plain_d, plain_p))
-            else:
-                dens, prune = plain_d, plain_p
-        rec.update(densify=int(dens.sum().item()), prune=int(prune.sum().item()))
-        self.history.append(rec)
+            dens = torch.zeros(n, dtype=torch.uint8, device=dev)
+            prune = torch.zeros(n, dtype=torch.uint8, device=dev)
+            self.predictor.predict(feat, n, dens, prune)
+        self._last = (n, dens, prune)
         return dens, prune
+
+    def judge(self, step: gs.MappingStep):
+        """Records the chunk's bit counts and, for the learned decider, its
+        agreement with the plain criterion on the same accumulators (call after
+        decide, before apply)."""
+        n, dens, prune = self._last
+        rec = dict(n=n, densify=int(dens.sum().item()), prune=int(prune.sum().item()))
+        if self.mode == "learned":
+            rec.update(agreement(dens, prune, *self.plain_bits(step)))
+        self.history.append(rec)
+        return rec
 
     def apply(self, step: gs.MappingStep, dens, prune):
         """New parameters and moments after the actions."""
@@ -126,7 +137,8 @@ class Lifecycle:
         out, m, v, _ = gs.gs_densify_prune(model, dens, prune, noise, self.split_log_scale, self.split_factor,
                                            exp_avg=step.exp_avg, exp_avg_sq=step.exp_avg_sq,
                                            capacity=gs.padded(model.n + int(dens.sum().item())))
-        self.history[-1]["n_after"] = out.n
+        if self.history:
+            self.history[-1]["n_after"] = out.n
         return out, (m, v)
 
 

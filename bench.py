@@ -361,7 +361,7 @@ def chunk_bytes(N, K, views):
 
 
 def run_chunk(args, world, dev):
-    """Batched chunk (configs[2]): one graph launch renders, differentiates and
+    """Batched chunk: one graph launch renders, differentiates and
     updates 2M shared Gaussians over 16 keyframes of uneven resolution; the
     same keyframes as 16 single-view iterations are the plain comparison."""
     import torch
@@ -381,7 +381,7 @@ def run_chunk(args, world, dev):
             tcache[key] = render_targets(gs, tscene, [cams], cfg, dev)[0]
         return tcache[key]
 
-    best, table = autotune(model, cams, targets_for, reps=2)
+    best, table = autotune(model, cams, targets_for, reps=2, segments=(0, 1024, 4096))
     target = targets_for(best)
     st = gs.MappingStep(model, cams, best, lambda_dssim=LAMBDA, lr=gs.default_lr(extent=10.0), with_stats=True)
     needed = st.fit_capacity(slack=1.1)
@@ -447,7 +447,8 @@ def run_chunk(args, world, dev):
             "hbm": {"algorithmic_bytes": int(B), "achieved_gbs": round(B / (ms * 1e-3) / 1e9, 1),
                     "frac_of_peak": round(B / (ms * 1e-3) / 1e9 / peak, 4)},
             "tuned": {"tile": "%dx%d" % (best.tile_w, best.tile_h), "batch": best.batch,
-                      "sweep_ms": {"%dx%d/%d" % k: round(v, 3) for k, v in sorted(table.items())}},
+                      "segment": best.segment,
+                      "sweep_ms": {"%dx%d/%d/%d" % k: round(v, 3) for k, v in sorted(table.items())}},
             "pairs": needed, "visible_records": V, "tiles": tiles_total, "steps": steps}
 
 

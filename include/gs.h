@@ -73,6 +73,17 @@ typedef struct {
     int32_t batch;          /* pairs a warp scans per step in the compositing
                                kernels: 128, 256 or 512 (0 selects 512); a
                                tuning knob only, results do not depend on it */
+    int32_t segment;        /* 0, or a power of two 32..65536: the pair list of a
+                               tile longer than `segment` pairs is composited in
+                               segments of that many pairs, one warp per segment
+                               and 8x4 block: the forward composites each segment
+                               from T = 1, chains the segments (T_start = product
+                               of the earlier segments' T, C += T_start C_s) and
+                               composites again, from the chained state, the one
+                               segment where a pixel stops; the backward walks
+                               each segment from the state recorded at its end.
+                               Needs gs_frame.seg_ws.  Results equal the unsplit
+                               traversal up to FP32 rounding */
 } gs_raster_cfg;
 
 /* Gaussian parameters: ONE device buffer of K planes of ld floats
@@ -130,6 +141,11 @@ typedef struct {
     int32_t *last;    /* [sum_v H_v W_v] pairs of the tile consumed up to and including
                          the last blended one (0 = none) */
     float *depth;     /* nullable: [sum_v H_v W_v] D^ = sum_j T_j alpha_j z_j (Supp. D.2) */
+    void *seg_ws;     /* split workspace, gs_segment_workspace_size bytes (256-byte
+                         aligned, sized for binning->max_pairs); written by
+                         gs_render_fwd, read by gs_render_bwd; required when
+                         cfg->segment > 0, else ignored */
+    size_t seg_ws_bytes;
 } gs_frame;
 
 /* Per-Gaussian lifecycle accumulators, planes of ld floats, accumulated over
@@ -173,6 +189,12 @@ gs_status gs_block_mask_size(int64_t max_pairs, size_t *bytes);
 
 /* Workspace bytes of gs_loss for a view of h x w pixels (the largest view). */
 gs_status gs_loss_workspace_size(int32_t h, int32_t w, size_t *bytes);
+
+/* Bytes of gs_frame.seg_ws for max_pairs pairs split every `segment` pairs:
+ * per long tile (more than `segment` pairs) a plan entry, per segment of its
+ * eight 8x4 blocks the forward's local state (768 bytes) and the backward's
+ * checkpoint (640 bytes); about 1.4 KB x 16 max_pairs / segment. */
+gs_status gs_segment_workspace_size(int64_t max_pairs, int32_t segment, size_t *bytes);
 
 /* Workspace bytes of gs_render_bwd for n_records records. */
 gs_status gs_bwd_workspace_size(int64_t n_records, size_t *bytes);

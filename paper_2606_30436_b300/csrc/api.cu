@@ -26,6 +26,45 @@ gs_status check_cfg(const gs_raster_cfg *cfg) {
         !(cfg->t_min >= 0.0f) || !(cfg->dilation >= 0.0f) || !(cfg->tan_clamp > 0.0f))
         return GS_ERR_INVALID;
     if (cfg->batch != 0 && cfg->batch != 128 && cfg->batch != 256 && cfg->batch != 512) return GS_ERR_INVALID;
+    const int sg = cfg->segment;
+    if (sg != 0 && (sg < 32 || sg > 65536 || (sg & (sg - 1)))) return GS_ERR_INVALID;
+    return GS_OK;
+}
+
+size_t seg_ws_bytes(long long max_pairs, int segment) {
+    const long long hcap = seg_heavy_capacity(max_pairs, segment), fcap = seg_item_capacity(max_pairs, segment);
+    const long long cap = seg_capacity(max_pairs, segment);
+    return 256 + align_up(sizeof(int4) * (size_t)hcap, 256) + align_up(sizeof(float) * kFresFloats * (size_t)fcap, 256) +
+           align_up(sizeof(int4) * (size_t)fcap, 256) + align_up(sizeof(int2) * (size_t)cap, 256) +
+           sizeof(float) * kCkptFloats * (size_t)cap;
+}
+
+// The split workspace of a frame (no split: all null, capacities 0).
+gs_status seg_of(const gs_raster_cfg *cfg, const gs_binning *binning, const gs_frame *frame, SegWs &seg) {
+    seg = SegWs{nullptr, nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr, 0};
+    if (cfg->segment == 0) return GS_OK;
+    if (!frame->seg_ws || ((uintptr_t)frame->seg_ws & 255u) ||
+        frame->seg_ws_bytes < seg_ws_bytes(binning->max_pairs, cfg->segment))
+        return GS_ERR_INVALID;
+    const long long hcap = seg_heavy_capacity(binning->max_pairs, cfg->segment);
+    const long long fcap = seg_item_capacity(binning->max_pairs, cfg->segment);
+    const long long cap = seg_capacity(binning->max_pairs, cfg->segment);
+    if (fcap > 0x7fffffffll) return GS_ERR_INVALID;
+    unsigned char *b = (unsigned char *)frame->seg_ws;
+    size_t off = 256;
+    seg.count = (int *)b;
+    seg.heavy = (int4 *)(b + off);
+    off += align_up(sizeof(int4) * (size_t)hcap, 256);
+    seg.fres = (float *)(b + off);
+    off += align_up(sizeof(float) * kFresFloats * (size_t)fcap, 256);
+    seg.tasks = (int4 *)(b + off);
+    off += align_up(sizeof(int4) * (size_t)fcap, 256);
+    seg.items = (int2 *)(b + off);
+    off += align_up(sizeof(int2) * (size_t)cap, 256);
+    seg.ckpt = (float *)(b + off);
+    seg.hcap = (int)hcap;
+    seg.fcap = (int)fcap;
+    seg.cap = (int)cap;
     return GS_OK;
 }
 
@@ -65,6 +104,9 @@ gs_status build_views(const gs_camera *cams, int n_views, const gs_raster_cfg *c
     for (int k = 0; k < 3; ++k) rc.bg[k] = cfg->bg[k];
     rc.tile_w = cfg->tile_w; rc.tile_h = cfg->tile_h;
     rc.batch = cfg->batch == 0 ? 512 : cfg->batch;
+    rc.seg_shift = -1;
+    for (int k = 5; k <= 16; ++k)
+        if (cfg->segment == (1 << k)) rc.seg_shift = k;
     return GS_OK;
 }
 
@@ -143,6 +185,12 @@ GS_API gs_status gs_loss_workspace_size(int32_t h, int32_t w, size_t *bytes) {
     return GS_OK;
 }
 
+GS_API gs_status gs_segment_workspace_size(int64_t max_pairs, int32_t segment, size_t *bytes) {
+    if (!bytes || max_pairs < 0 || segment < 32 || segment > 65536 || (segment & (segment - 1))) return GS_ERR_INVALID;
+    *bytes = seg_ws_bytes(max_pairs, segment);
+    return GS_OK;
+}
+
 GS_API gs_status gs_bwd_workspace_size(int64_t n_records, size_t *bytes) {
     if (!bytes || n_records < 0) return GS_ERR_INVALID;
     *bytes = align_up(sizeof(float) * (size_t)kAccPlanes * (size_t)n_records, 256);
@@ -198,10 +246,12 @@ GS_API gs_status gs_render_fwd(const gs_projected *proj, const gs_binning *binni
     if (!proj || (st = check_proj(proj, proj->ld)) != GS_OK) return GS_ERR_INVALID;
     if ((st = check_binning(binning)) != GS_OK) return st;
     if (!frame || !frame->img || !frame->T_final || !frame->last) return GS_ERR_INVALID;
+    SegWs seg;
+    if ((st = seg_of(cfg, binning, frame, seg)) != GS_OK) return st;
     launch_render_fwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, binning->block_mask,
                       binning->tile_order, (const float2 *)proj->xy,
                       (const float4 *)proj->conic_opacity, (const float4 *)proj->rgb_depth, frame->img,
-                      frame->T_final, frame->last, frame->depth, (cudaStream_t)stream);
+                      frame->T_final, frame->last, frame->depth, seg, (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
 }
 
@@ -295,6 +345,8 @@ GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, i
         return GS_ERR_INVALID;
     if (!proj || check_proj(proj, params->ld) != GS_OK || check_binning(binning) != GS_OK) return GS_ERR_INVALID;
     if (!frame || !frame->img || !frame->T_final || !frame->last || !dL_dimg) return GS_ERR_INVALID;
+    SegWs seg;
+    if ((st = seg_of(cfg, binning, frame, seg)) != GS_OK) return st;
     const bool want_stats = stats != nullptr;
     if (want_stats && (!stats->acc || stats->ld < params->n || !target)) return GS_ERR_INVALID;
     const long long nrec = (long long)n_views * params->ld;
@@ -308,7 +360,8 @@ GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, i
     launch_render_bwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, binning->block_mask,
                       binning->tile_order, (const float2 *)proj->xy,
                       (const float4 *)proj->conic_opacity, (const float4 *)proj->rgb_depth, frame->img,
-                      frame->T_final, frame->last, dL_dimg, dL_ddepth, target, tau_err, want_stats, acc, nrec, s);
+                      frame->T_final, frame->last, dL_dimg, dL_ddepth, target, tau_err, want_stats, acc, nrec,
+                      frame->depth, seg, s);
     if (grads)
         launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius, acc, nrec,
                            grads->data, accumulate, loss_per_view, want_stats ? stats->acc : nullptr,

@@ -34,8 +34,42 @@ struct RasterCfg {
     float near_z, dilation, alpha_min, alpha_max, t_min, tan_clamp;
     float bg[3];
     int tile_w, tile_h;
-    int batch;  // pairs a warp scans per step (128, 256, 512)
+    int batch;      // pairs a warp scans per step (128, 256, 512)
+    int seg_shift;  // log2 of the backward's segment length, -1 = no split
 };
+
+// Workspace of the split compositing kernels.  count[0] segment items of the
+// forward, count[1] long tiles, count[2] backward checkpoints.  heavy: per long
+// tile (schedule index, tile, first item, segments S); fres: per forward item
+// the 32 lanes' local T, C0, C1, C2, depth and last (bit 31: stopped), [6][32];
+// items / ckpt: per backward checkpoint (unit, boundary k) and the 32 lanes' T
+// and colour in front (C0, C1, C2, depth) after the pairs before the boundary,
+// [5][32] floats.
+struct SegWs {
+    int *count;   // [0] forward items, [1] long tiles, [2] checkpoints, [3] re-run tasks
+    int4 *heavy;
+    int hcap;
+    float *fres;
+    int4 *tasks;  // forward re-runs: (item, lane mask, first checkpoint slot of the block, 0)
+    int fcap;     // items, and re-run tasks (at most one per item)
+    int2 *items;
+    float *ckpt;
+    int cap;
+};
+constexpr int kCkptFloats = 5 * 32;
+constexpr int kFresFloats = 6 * 32;
+
+// long tiles: each holds more than one segment of pairs
+__host__ __device__ __forceinline__ long long seg_heavy_capacity(long long max_pairs, int segment) {
+    return ((max_pairs > 0 ? max_pairs : 1) + segment - 1) / segment + 1;
+}
+// forward items: 8 blocks x S segments per long tile, S <= len / segment + 1
+__host__ __device__ __forceinline__ long long seg_item_capacity(long long max_pairs, int segment) {
+    return 16 * seg_heavy_capacity(max_pairs, segment);
+}
+__host__ __device__ __forceinline__ long long seg_capacity(long long max_pairs, int segment) {
+    return 8 * (((max_pairs > 0 ? max_pairs : 1) + segment - 1) / segment) + 8;
+}
 
 // The view that owns a global tile index (linear scan: <= 64 views, uniform
 // across the block, served from the constant bank).

@@ -29,14 +29,16 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
                         void *ws, int *status, cudaStream_t s);
 
 void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
-                       const uint8_t *masks, const int *order, const float2 *xy, const float4 *co, const float4 *rgbd,
-                       float *img, float *T_final, int *last, float *depth, cudaStream_t s);
+                       const uint8_t *masks, const int *order, const float2 *xy, const float4 *co,
+                       const float4 *rgbd, float *img, float *T_final, int *last, float *depth, const SegWs &seg,
+                       cudaStream_t s);
 
 void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
                        const uint8_t *masks, const int *order, const float2 *xy, const float4 *co, const float4 *rgbd,
                        const float *img, const float *T_final,
                        const int *last, const float *dL_dimg, const float *dL_ddepth, const float *target,
-                       float tau_err, bool stats, float *acc, long long nrec, cudaStream_t s);
+                       float tau_err, bool stats, float *acc, long long nrec, const float *depth, const SegWs &seg,
+                       cudaStream_t s);
 
 size_t loss_workspace_bytes(int h, int w);
 bool loss_static_fits(int h, int w);

@@ -11,6 +11,8 @@
 // next 32 already in flight.  There is no CTA-wide barrier: a block whose
 // pixels saturate early retires at once, and the long chains of a
 // vanishing-point tile touch only the pairs that reach each block.
+#include <algorithm>
+
 #include "gs_internal.cuh"
 #include "gs_kernels.h"
 
@@ -121,8 +123,181 @@ __device__ __forceinline__ void gather(Rec &r, const int *list, int idx, int tot
     load_rec(r, xy, co, rgbd, valid ? ids[r.pos] : 0, valid);
 }
 
+// Compositing state of one lane's pixel.
+struct FwdState {
+    float T, C0, C1, C2, D;
+    int last;   // pairs of the tile consumed up to and including the last blended one
+    bool done;  // stopped (or outside the view)
+};
+
+struct FwdShared {
+    float2 *p;
+    float4 *q, *c;
+    int *pos, *list;
+};
+
+// Front-to-back compositing of the pairs of [lo, hi) (positions in the tile's
+// list, rgx its start) relevant to block `bit` into each lane's state, with
+// the stop rule of Supp. D.2 (stop before the pair that takes T below t_min).
+// alpha of 8 staged pairs at a time (independent, so their latencies overlap),
+// then the short serial transmittance update over them.
 template <int WIN>
-__global__ void __launch_bounds__(32 * kWarps) k_render_fwd(ViewTable vt, RasterCfg cfg,
+__device__ __forceinline__ void fwd_range(const RasterCfg &cfg, const uint8_t *__restrict__ masks,
+                                          const int *__restrict__ ids, const float2 *__restrict__ xy,
+                                          const float4 *__restrict__ co, const float4 *__restrict__ rgbd, int rgx,
+                                          int lo, int hi, int bit, float fx, float fy, FwdState &st,
+                                          const FwdShared &sh) {
+    const int lane = threadIdx.x & 31;
+    for (int w = lo & ~15; w < hi && !__all_sync(0xffffffffu, st.done); w += WIN) {
+        const int total = scan_window<WIN>(masks, w, lo, hi, bit, sh.list);
+        Rec cur, nxt;
+        gather(cur, sh.list, lane, total, ids, xy, co, rgbd);
+        for (int c = 0; c < total; c += 32) {
+            if (c + 32 < total) gather(nxt, sh.list, c + 32 + lane, total, ids, xy, co, rgbd);
+            sh.p[lane] = cur.p;
+            sh.q[lane] = cur.q;
+            sh.c[lane] = cur.c;
+            sh.pos[lane] = cur.pos;
+            __syncwarp();
+            const int cnt = min(32, total - c);
+            for (int k0 = 0; k0 < cnt && !st.done; k0 += 8) {
+                float al[8];
+                #pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float a = -1.0f;
+                    if (k0 + j < cnt) {
+                        const float2 p = sh.p[k0 + j];
+                        const float4 q = sh.q[k0 + j];
+                        const float power = gauss_power(q.x, q.y, q.z, fx - p.x, fy - p.y);
+                        if (power <= 0.0f) {
+                            a = fminf(cfg.alpha_max, q.w * __expf(power));
+                            if (a < cfg.alpha_min) a = -1.0f;
+                        }
+                    }
+                    al[j] = a;
+                }
+                #pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float a = al[j];
+                    if (!st.done && a >= 0.0f) {
+                        const float Tn = st.T * (1.0f - a);
+                        if (Tn < cfg.t_min) {
+                            st.done = true;
+                        } else {
+                            const float4 cc = sh.c[k0 + j];
+                            const float wgt = a * st.T;
+                            st.C0 += cc.x * wgt; st.C1 += cc.y * wgt; st.C2 += cc.z * wgt; st.D += cc.w * wgt;
+                            st.T = Tn;
+                            st.last = sh.pos[k0 + j] - rgx + 1;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (__all_sync(0xffffffffu, st.done)) break;
+            cur = nxt;
+        }
+    }
+}
+
+__device__ __forceinline__ void fwd_write(const RasterCfg &cfg, const Unit &t, const FwdState &st,
+                                          float *__restrict__ img, float *__restrict__ T_final,
+                                          int *__restrict__ last, float *__restrict__ depth) {
+    if (!t.inside) return;
+    img[t.img] = st.C0 + st.T * cfg.bg[0];
+    img[t.img + t.plane] = st.C1 + st.T * cfg.bg[1];
+    img[t.img + 2 * t.plane] = st.C2 + st.T * cfg.bg[2];
+    T_final[t.pix] = st.T;
+    last[t.pix] = st.last;
+    if (depth) depth[t.pix] = st.D;
+}
+
+// Split forward, step 1 (one CTA): the tiles whose list is longer than one
+// segment ("long" tiles), in schedule order, each with the base of its
+// 8 x S segment items (S segments per 8x4 block) -- a block scan over the
+// schedule, so bases increase with the table index.
+constexpr int kPlanThreads = 1024;
+__global__ void __launch_bounds__(kPlanThreads) k_fwd_plan(const int2 *__restrict__ ranges,
+                                                          const int *__restrict__ order, int total_tiles,
+                                                          int seg_shift, SegWs seg) {
+    __shared__ int s_items[kPlanThreads / 32], s_long[kPlanThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int per = (total_tiles + kPlanThreads - 1) / kPlanThreads;
+    const int lo = min(total_tiles, t * per), hi = min(total_tiles, lo + per);
+    int items = 0, nlong = 0;
+    for (int i = lo; i < hi; ++i) {
+        const int2 rg = ranges[order[i]];
+        const int S = (rg.y - rg.x + (1 << seg_shift) - 1) >> seg_shift;
+        if (S > 1) { items += 8 * S; ++nlong; }
+    }
+    int ii = items, il = nlong;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, ii, o), b = __shfl_up_sync(0xffffffffu, il, o);
+        if (lane >= o) { ii += a; il += b; }
+    }
+    if (lane == 31) { s_items[warp] = ii; s_long[warp] = il; }
+    __syncthreads();
+    if (warp == 0) {
+        int a = s_items[lane], b = s_long[lane], ai = a, bi = b;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, ai, o), y = __shfl_up_sync(0xffffffffu, bi, o);
+            if (lane >= o) { ai += x; bi += y; }
+        }
+        s_items[lane] = ai - a;
+        s_long[lane] = bi - b;
+    }
+    __syncthreads();
+    int base = s_items[warp] + ii - items, h = s_long[warp] + il - nlong;
+    for (int i = lo; i < hi; ++i) {
+        const int tile = order[i];
+        const int2 rg = ranges[tile];
+        const int S = (rg.y - rg.x + (1 << seg_shift) - 1) >> seg_shift;
+        if (S > 1) {
+            if (h < seg.hcap) seg.heavy[h] = make_int4(i, tile, base, S);
+            base += 8 * S;
+            ++h;
+        }
+    }
+    if (t == kPlanThreads - 1) {
+        seg.count[0] = base;  // segment items
+        seg.count[1] = h;     // long tiles
+    }
+}
+
+// Item `it` of the split forward: its long tile (the last plan entry whose
+// first item is <= it), 8x4 block and segment.
+struct ItemRef {
+    int4 H;  // (schedule index, tile, first item, segments S)
+    int blk, sgi;
+};
+__device__ __forceinline__ ItemRef item_ref(const SegWs &seg, int it) {
+    int a = 0, b = min(seg.count[1], seg.hcap) - 1;
+    while (a < b) {
+        const int m = (a + b + 1) >> 1;
+        if (seg.heavy[m].z <= it) a = m; else b = m - 1;
+    }
+    ItemRef r;
+    r.H = seg.heavy[a];
+    const int rel = it - r.H.z;
+    r.blk = rel / r.H.w;
+    r.sgi = rel - r.blk * r.H.w;
+    return r;
+}
+
+__device__ __forceinline__ void fres_store(float *r, const FwdState &st, bool flag) {
+    const int lane = threadIdx.x & 31;
+    r[lane] = st.T; r[32 + lane] = st.C0; r[64 + lane] = st.C1; r[96 + lane] = st.C2; r[128 + lane] = st.D;
+    r[160 + lane] = __int_as_float(st.last | (flag ? (int)0x80000000u : 0));
+}
+
+// Split forward, step 2: CTAs [0, item_blocks) loop over the segment items,
+// compositing one segment of a long tile's block each from T = 1 (a local
+// pass with the same stop rule; flag = stopped) into its slot of fres; the
+// other CTAs composite the short tiles' blocks whole.
+template <int WIN>
+__global__ void __launch_bounds__(32 * kWarps, 1) k_render_fwd(ViewTable vt, RasterCfg cfg,
                                                               const int2 *__restrict__ ranges,
                                                               const int *__restrict__ ids,
                                                               const uint8_t *__restrict__ masks,
@@ -131,63 +306,203 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_fwd(ViewTable vt, Raster
                                                               const float4 *__restrict__ co,
                                                               const float4 *__restrict__ rgbd,
                                                               float *__restrict__ img, float *__restrict__ T_final,
-                                                              int *__restrict__ last, float *__restrict__ depth) {
+                                                              int *__restrict__ last, float *__restrict__ depth,
+                                                              SegWs seg, int item_blocks) {
+    __shared__ int s_list[kWarps][WIN];
+    __shared__ float2 s_p[kWarps][32];
+    __shared__ float4 s_q[kWarps][32];
+    __shared__ float4 s_c[kWarps][32];
+    __shared__ int s_pos[kWarps][32];
+    const int warp = threadIdx.x >> 5;
+    const FwdShared sh{s_p[warp], s_q[warp], s_c[warp], s_pos[warp], s_list[warp]};
+    if ((int)blockIdx.x < item_blocks) {
+        const int n = min(seg.count[0], seg.fcap);
+        for (int it = blockIdx.x * kWarps + warp; it < n; it += item_blocks * kWarps) {
+            const ItemRef R = item_ref(seg, it);
+            const Unit t = unit_ctx(vt, R.H.y, R.blk);
+            const int2 rg = ranges[R.H.y];
+            const int lo = rg.x + (R.sgi << cfg.seg_shift), hi = min(rg.y, lo + (1 << cfg.seg_shift));
+            FwdState st{1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, !t.inside};
+            fwd_range<WIN>(cfg, masks, ids, xy, co, rgbd, rg.x, lo, hi, R.blk, t.px + 0.5f, t.py + 0.5f, st, sh);
+            fres_store(seg.fres + (long long)it * kFresFloats, st, st.done && t.inside);
+        }
+        return;
+    }
+    const int unit = (blockIdx.x - item_blocks) * kWarps + warp;
+    if (unit >= vt.total_tiles * 8) return;
+    const int tile = order[unit >> 3], bit = unit & 7;  // longest tiles first
+    const int2 rg = ranges[tile];
+    if (cfg.seg_shift >= 0 && rg.y - rg.x > (1 << cfg.seg_shift)) return;  // long tile: segment items
+    const Unit t = unit_ctx(vt, tile, bit);
+    FwdState st{1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, !t.inside};
+    fwd_range<WIN>(cfg, masks, ids, xy, co, rgbd, rg.x, rg.x, rg.y, bit, t.px + 0.5f, t.py + 0.5f, st, sh);
+    fwd_write(cfg, t, st, img, T_final, last, depth);
+}
+
+// Split forward, step 3: one warp per block of a long tile chains the local
+// passes of its segments in order, T_start(s+1) = T_start(s) T_s and
+// C += T_start(s) C_s, recording the state after each segment (the backward's
+// checkpoints), until every pixel has either run through all segments or
+// reached the segment where its stop falls (the local pass stopped, or the
+// chained T after it would be below t_min).  Pixels of the first kind are
+// final and written; for each segment where some pixels stop, a re-run task
+// (item, lane mask, first checkpoint slot) is registered and the pixels'
+// state entering the segment replaces their columns of that item's slot.
+constexpr int kSplitCtasPerSm = 8;
+__global__ void __launch_bounds__(32 * kWarps) k_render_fwd_combine(ViewTable vt, RasterCfg cfg,
+                                                                   float *__restrict__ img,
+                                                                   float *__restrict__ T_final,
+                                                                   int *__restrict__ last,
+                                                                   float *__restrict__ depth, SegWs seg) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = 8 * min(seg.count[1], seg.hcap);
+    for (int u = blockIdx.x * kWarps + warp; u < n; u += gridDim.x * kWarps) {
+        const int h = u >> 3, blk = u & 7;
+        const int4 H = seg.heavy[h];
+        const int S = H.w, unit = 8 * H.x + blk, item0 = H.z + blk * S;
+        if ((long long)H.z + 8ll * S > seg.fcap) continue;  // cannot happen: the capacity bounds every plan
+        const Unit t = unit_ctx(vt, H.y, blk);
+        int slot0 = 0;
+        if (lane == 0) slot0 = atomicAdd(&seg.count[2], S - 1);
+        slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+        FwdState st{1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, !t.inside};
+        bool pend = false;
+        int sstar = 0x7fffffff;
+        int sgi_end = S - 1;  // last segment whose boundary state was recorded
+        constexpr int B = 8;  // segments whose local states are loaded together
+        bool stop_chain = false;
+        for (int s0 = 0; s0 < S && !stop_chain; s0 += B) {
+            float lT[B], lC0[B], lC1[B], lC2[B], lD[B];
+            int lw[B];
+            #pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const float *r = seg.fres + (long long)(item0 + min(s0 + j, S - 1)) * kFresFloats;
+                lT[j] = r[lane]; lC0[j] = r[32 + lane]; lC1[j] = r[64 + lane]; lC2[j] = r[96 + lane];
+                lD[j] = r[128 + lane]; lw[j] = __float_as_int(r[160 + lane]);
+            }
+            #pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const int sgi = s0 + j;
+                if (sgi >= S || stop_chain) break;
+                if (!st.done && !pend) {
+                    if (lw[j] < 0 || st.T * lT[j] < cfg.t_min) {
+                        pend = true;  // the stop falls inside this segment
+                        sstar = sgi;
+                    } else {
+                        st.C0 += st.T * lC0[j];
+                        st.C1 += st.T * lC1[j];
+                        st.C2 += st.T * lC2[j];
+                        st.D += st.T * lD[j];
+                        if (lw[j] > 0) st.last = lw[j];
+                        st.T *= lT[j];
+                    }
+                }
+                const int slot = slot0 + sgi;
+                if (sgi < S - 1 && slot < seg.cap) {  // state at boundary sgi + 1
+                    float *ck = seg.ckpt + (long long)slot * kCkptFloats;
+                    ck[lane] = st.T; ck[32 + lane] = st.C0; ck[64 + lane] = st.C1; ck[96 + lane] = st.C2;
+                    ck[128 + lane] = st.D;
+                    if (lane == 0) seg.items[slot] = make_int2(unit, sgi + 1);
+                }
+                if (__all_sync(0xffffffffu, st.done || pend)) {
+                    stop_chain = true;
+                    sgi_end = sgi;
+                }
+            }
+        }
+        // reserved slots past the chain hold no checkpoint (a re-run may claim them)
+        if (lane == 0)
+            for (int k = sgi_end + 1; k < S - 1; ++k)
+                if (slot0 + k < seg.cap) seg.items[slot0 + k] = make_int2(-1, 0);
+        if (!pend) fwd_write(cfg, t, st, img, T_final, last, depth);
+        // one re-run task per segment where some pixels stop
+        bool assigned = !pend;
+        while (__any_sync(0xffffffffu, !assigned)) {
+            int smin = assigned ? 0x7fffffff : sstar;
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) smin = min(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+            const bool mine = !assigned && sstar == smin;
+            const unsigned mask = __ballot_sync(0xffffffffu, mine);
+            if (mine) fres_store(seg.fres + (long long)(item0 + smin) * kFresFloats, st, false);
+            if (lane == 0) {
+                const int task = atomicAdd(&seg.count[3], 1);
+                if (task < seg.fcap) seg.tasks[task] = make_int4(item0 + smin, (int)mask, slot0, 0);
+            }
+            assigned = assigned || mine;
+        }
+    }
+}
+
+// Split forward, step 4: each re-run task composites its segment again for
+// its pixels from their chained state with the exact stop rule (a pixel that
+// does not stop there after all continues through the next segments as the
+// chain does), records their state at the following boundaries, and writes
+// them.
+template <int WIN>
+__global__ void __launch_bounds__(32 * kWarps, 1) k_render_fwd_rerun(ViewTable vt, RasterCfg cfg,
+                                                                    const int2 *__restrict__ ranges,
+                                                                    const int *__restrict__ ids,
+                                                                    const uint8_t *__restrict__ masks,
+                                                                    const float2 *__restrict__ xy,
+                                                                    const float4 *__restrict__ co,
+                                                                    const float4 *__restrict__ rgbd,
+                                                                    float *__restrict__ img,
+                                                                    float *__restrict__ T_final,
+                                                                    int *__restrict__ last,
+                                                                    float *__restrict__ depth, SegWs seg) {
     __shared__ int s_list[kWarps][WIN];
     __shared__ float2 s_p[kWarps][32];
     __shared__ float4 s_q[kWarps][32];
     __shared__ float4 s_c[kWarps][32];
     __shared__ int s_pos[kWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int unit = blockIdx.x * kWarps + warp;
-    if (unit >= vt.total_tiles * 8) return;
-    const int tile = order[unit >> 3], bit = unit & 7;  // longest tiles first
-    const Unit t = unit_ctx(vt, tile, bit);
-    const int2 rg = ranges[tile];
-    const float fx = t.px + 0.5f, fy = t.py + 0.5f;
-    int *list = s_list[warp];
-
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Dd = 0.0f;
-    int lastc = 0;
-    bool done = !t.inside;
-    for (int w = rg.x & ~15; w < rg.y && !__all_sync(0xffffffffu, done); w += WIN) {
-        const int total = scan_window<WIN>(masks, w, rg.x, rg.y, bit, list);
-        Rec cur, nxt;
-        gather(cur, list, lane, total, ids, xy, co, rgbd);
-        for (int c = 0; c < total; c += 32) {
-            if (c + 32 < total) gather(nxt, list, c + 32 + lane, total, ids, xy, co, rgbd);
-            s_p[warp][lane] = cur.p;
-            s_q[warp][lane] = cur.q;
-            s_c[warp][lane] = cur.c;
-            s_pos[warp][lane] = cur.pos;
-            __syncwarp();
-            const int cnt = min(32, total - c);
-            for (int k = 0; k < cnt && !done; ++k) {
-                const float2 p = s_p[warp][k];
-                const float4 q = s_q[warp][k];
-                const float power = gauss_power(q.x, q.y, q.z, fx - p.x, fy - p.y);
-                if (power > 0.0f) continue;
-                const float alpha = fminf(cfg.alpha_max, q.w * __expf(power));
-                if (alpha < cfg.alpha_min) continue;
-                const float Tn = T * (1.0f - alpha);
-                if (Tn < cfg.t_min) { done = true; break; }
-                const float4 cc = s_c[warp][k];
-                const float wgt = alpha * T;
-                C0 += cc.x * wgt; C1 += cc.y * wgt; C2 += cc.z * wgt; Dd += cc.w * wgt;
-                T = Tn;
-                lastc = s_pos[warp][k] - rg.x + 1;
-            }
-            __syncwarp();
-            if (__all_sync(0xffffffffu, done)) break;
-            cur = nxt;
+    const FwdShared sh{s_p[warp], s_q[warp], s_c[warp], s_pos[warp], s_list[warp]};
+    const int n = min(seg.count[3], seg.fcap);
+    for (int k = blockIdx.x * kWarps + warp; k < n; k += gridDim.x * kWarps) {
+        const int4 task = seg.tasks[k];
+        const ItemRef R = item_ref(seg, task.x);
+        const int S = R.H.w, unit = 8 * R.H.x + R.blk, item0 = task.x - R.sgi, slot0 = task.z;
+        const bool in = (task.y >> lane) & 1;
+        const Unit t = unit_ctx(vt, R.H.y, R.blk);
+        const int2 rg = ranges[R.H.y];
+        const float fx = t.px + 0.5f, fy = t.py + 0.5f;
+        FwdState st{1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, true};
+        if (in) {
+            const float *r = seg.fres + (long long)task.x * kFresFloats;
+            st = FwdState{r[lane], r[32 + lane], r[64 + lane], r[96 + lane], r[128 + lane],
+                          __float_as_int(r[160 + lane]), false};
         }
-    }
-    if (t.inside) {
-        img[t.img] = C0 + T * cfg.bg[0];
-        img[t.img + t.plane] = C1 + T * cfg.bg[1];
-        img[t.img + 2 * t.plane] = C2 + T * cfg.bg[2];
-        T_final[t.pix] = T;
-        last[t.pix] = lastc;
-        if (depth) depth[t.pix] = Dd;
+        for (int sgi = R.sgi; sgi < S && __any_sync(0xffffffffu, !st.done); ++sgi) {
+            bool exact = sgi == R.sgi;
+            if (!exact && !st.done) {
+                const float *r = seg.fres + (long long)(item0 + sgi) * kFresFloats;
+                const float Tl = r[lane];
+                const int lw = __float_as_int(r[160 + lane]);
+                if (lw < 0 || st.T * Tl < cfg.t_min) {
+                    exact = true;
+                } else {
+                    st.C0 += st.T * r[32 + lane]; st.C1 += st.T * r[64 + lane]; st.C2 += st.T * r[96 + lane];
+                    st.D += st.T * r[128 + lane];
+                    if (lw > 0) st.last = lw;
+                    st.T *= Tl;
+                }
+            }
+            if (__any_sync(0xffffffffu, exact && !st.done)) {
+                const int lo = rg.x + (sgi << cfg.seg_shift), hi = min(rg.y, lo + (1 << cfg.seg_shift));
+                FwdState x = st;
+                x.done = st.done || !exact;
+                fwd_range<WIN>(cfg, masks, ids, xy, co, rgbd, rg.x, lo, hi, R.blk, fx, fy, x, sh);
+                if (exact && !st.done) st = x;
+            }
+            const int slot = slot0 + sgi;
+            if (in && sgi < S - 1 && slot < seg.cap) {  // this pixel's state at boundary sgi + 1
+                float *ck = seg.ckpt + (long long)slot * kCkptFloats;
+                ck[lane] = st.T; ck[32 + lane] = st.C0; ck[64 + lane] = st.C1; ck[96 + lane] = st.C2;
+                ck[128 + lane] = st.D;
+            }
+            if (lane == 0 && sgi < S - 1 && slot < seg.cap) seg.items[slot] = make_int2(unit, sgi + 1);
+        }
+        if (in) fwd_write(cfg, t, st, img, T_final, last, depth);
     }
 }
 
@@ -252,7 +567,9 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
                                                               const float *__restrict__ dL_dimg,
                                                               const float *__restrict__ dL_ddepth,
                                                               const float *__restrict__ target, float tau_err,
-                                                              float *__restrict__ acc, long long nrec) {
+                                                              float *__restrict__ acc, long long nrec,
+                                                              const float *__restrict__ depth, SegWs seg,
+                                                              int item_blocks) {
     __shared__ int s_list[kWarps][WIN];
     __shared__ float2 s_p[kWarps][32];
     __shared__ float4 s_q[kWarps][32];
@@ -260,8 +577,9 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
     __shared__ int s_id[kWarps][32];
     __shared__ int s_pos[kWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int unit = blockIdx.x * kWarps + warp;
-    if (unit >= vt.total_tiles * 8) return;
+    // one work item: a unit's last segment from T_final and the background
+    // (item < 0), or the checkpointed segment bk-1 of a long tile's block
+    auto work = [&](const int unit, const int item, const int bk) {
     const int tile = order[unit >> 3], bit = unit & 7;  // longest tiles first
     const Unit t = unit_ctx(vt, tile, bit);
     const int2 rg = ranges[tile];
@@ -293,9 +611,31 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
     // transmittance in front of it; starts as the background
     float R0 = cfg.bg[0], R1 = cfg.bg[1], R2 = cfg.bg[2], RD = 0.0f;
 
-    const int lo = rg.x, hi = rg.x + wmax;
+    // pair range of this warp: the unit's last segment [S_last << shift, wmax)
+    // or, for an item, segment bk-1, which starts from the checkpoint at
+    // boundary bk: T there and the colour behind = (final - in front) / T
+    int lo = rg.x, hi = rg.x + wmax;
+    if (cfg.seg_shift >= 0) {
+        const int s_last = (wmax - 1) >> cfg.seg_shift;
+        if (item >= 0) {
+            if (bk > s_last) return;  // boundary at or past the unit's last blended pair
+            lo = rg.x + ((bk - 1) << cfg.seg_shift);
+            hi = rg.x + (bk << cfg.seg_shift);
+            const float *ck = seg.ckpt + (long long)item * kCkptFloats;
+            if (t.inside) {
+                T = ck[lane];
+                const float inv = 1.0f / T;
+                R0 = (img[t.img] - ck[32 + lane]) * inv;
+                R1 = (img[t.img + t.plane] - ck[64 + lane]) * inv;
+                R2 = (img[t.img + 2 * t.plane] - ck[96 + lane]) * inv;
+                RD = depth ? (depth[t.pix] - ck[128 + lane]) * inv : 0.0f;
+            }
+        } else {
+            lo = rg.x + (s_last << cfg.seg_shift);
+        }
+    }
     const int wbase = rg.x & ~15;
-    for (int kw = (hi - 1 - wbase) / WIN; kw >= 0; --kw) {
+    for (int kw = (hi - 1 - wbase) / WIN; kw >= (lo - wbase) / WIN; --kw) {
         const int total = scan_window<WIN>(masks, wbase + kw * WIN, lo, hi, bit, list);
         if (total == 0) continue;
         int c = ((total - 1) >> 5) << 5;
@@ -381,16 +721,63 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
             cur = nxt;
         }
     }
+    };  // work
+    // CTAs [0, item_blocks) loop over the checkpointed segments of long tiles
+    if ((int)blockIdx.x < item_blocks) {
+        const int n = min(seg.count[2], seg.cap);
+        for (int it = blockIdx.x * kWarps + warp; it < n; it += item_blocks * kWarps) {
+            const int2 e = seg.items[it];
+            if (e.x >= 0) work(e.x, it, e.y);  // x < 0: a reserved slot without a checkpoint
+        }
+        return;
+    }
+    const int unit = (blockIdx.x - item_blocks) * kWarps + warp;
+    if (unit >= vt.total_tiles * 8) return;
+    work(unit, -1, 0);
+}
+
+static int sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+// CTAs of a grid-stride loop over at most `work` warps of work
+static int stride_blocks(long long work) {
+    return (int)std::max(1ll, std::min(ceil_div(work, kWarps), (long long)kSplitCtasPerSm * sm_count()));
 }
 
 void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
                        const uint8_t *masks, const int *order, const float2 *xy, const float4 *co,
-                       const float4 *rgbd, float *img, float *T_final, int *last, float *depth, cudaStream_t s) {
+                       const float4 *rgbd, float *img, float *T_final, int *last, float *depth, const SegWs &seg,
+                       cudaStream_t s) {
     const long long units = 8ll * vt.total_tiles;
     if (units <= 0) return;
-    const unsigned grid = (unsigned)ceil_div(units, kWarps);
-#define GS_FWD(WN) k_render_fwd<WN><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, order, xy, co, rgbd, img, \
-                                                                 T_final, last, depth)
+    const bool split = cfg.seg_shift >= 0;
+    int item_blocks = 0, cgrid = 0, rgrid = 0;
+    if (split) {
+        cudaMemsetAsync(seg.count, 0, 4 * sizeof(int), s);
+        k_fwd_plan<<<1, kPlanThreads, 0, s>>>(ranges, order, vt.total_tiles, cfg.seg_shift, seg);
+        item_blocks = stride_blocks(seg.fcap);
+        cgrid = stride_blocks(8ll * seg.hcap);
+        rgrid = stride_blocks(seg.fcap);
+    }
+    const unsigned grid = (unsigned)(item_blocks + ceil_div(units, kWarps));
+#define GS_FWD(WN)                                                                                                  \
+    do {                                                                                                            \
+        k_render_fwd<WN><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, order, xy, co, rgbd, img,        \
+                                                      T_final, last, depth, seg, item_blocks);                      \
+        if (split) {                                                                                                \
+            k_render_fwd_combine<<<cgrid, 32 * kWarps, 0, s>>>(vt, cfg, img, T_final, last, depth, seg);            \
+            k_render_fwd_rerun<WN><<<rgrid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd, img,    \
+                                                                 T_final, last, depth, seg);                        \
+        }                                                                                                           \
+    } while (0)
     if (cfg.batch == 128) GS_FWD(128);
     else if (cfg.batch == 256) GS_FWD(256);
     else GS_FWD(512);
@@ -401,13 +788,16 @@ void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ra
                        const uint8_t *masks, const int *order, const float2 *xy, const float4 *co,
                        const float4 *rgbd, const float *img, const float *T_final, const int *last, const float *dL_dimg,
                        const float *dL_ddepth, const float *target, float tau_err, bool stats, float *acc,
-                       long long nrec, cudaStream_t s) {
+                       long long nrec, const float *depth, const SegWs &seg, cudaStream_t s) {
     const long long units = 8ll * vt.total_tiles;
     if (units <= 0) return;
-    const unsigned grid = (unsigned)ceil_div(units, kWarps);
+    // segment CTAs first, so the long lists' segments start early
+    const int item_blocks = cfg.seg_shift >= 0 ? stride_blocks(seg.cap) : 0;
+    const unsigned grid = (unsigned)(item_blocks + ceil_div(units, kWarps));
 #define GS_BWD(ST, WN) k_render_bwd<ST, WN><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, order, xy, co, \
                                                                          rgbd, img, T_final, last, dL_dimg, \
-                                                                         dL_ddepth, target, tau_err, acc, nrec)
+                                                                         dL_ddepth, target, tau_err, acc, nrec, \
+                                                                         depth, seg, item_blocks)
     if (stats) {
         if (cfg.batch == 128) GS_BWD(true, 128);
         else if (cfg.batch == 256) GS_BWD(true, 256);

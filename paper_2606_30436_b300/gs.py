@@ -41,7 +41,7 @@ class Camera(C.Structure):
 class RasterCfg(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("near_z", C.c_float), ("dilation", C.c_float),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float),
-                ("tan_clamp", C.c_float), ("bg", C.c_float * 3), ("batch", C.c_int32)]
+                ("tan_clamp", C.c_float), ("bg", C.c_float * 3), ("batch", C.c_int32), ("segment", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -59,7 +59,8 @@ class Binning(C.Structure):
 
 
 class Frame(C.Structure):
-    _fields_ = [("img", C.c_void_p), ("T_final", C.c_void_p), ("last", C.c_void_p), ("depth", C.c_void_p)]
+    _fields_ = [("img", C.c_void_p), ("T_final", C.c_void_p), ("last", C.c_void_p), ("depth", C.c_void_p),
+                ("seg_ws", C.c_void_p), ("seg_ws_bytes", C.c_size_t)]
 
 
 class Stats(C.Structure):
@@ -76,7 +77,8 @@ EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspac
            "gs_bwd_workspace_size", "gs_prune_workspace_size", "gs_project", "gs_sort", "gs_render_fwd", "gs_loss",
            "gs_render_bwd", "gs_project_bwd", "gs_adam", "gs_prune_stats", "gs_loss_static",
            "gs_reg_workspace_size", "gs_geo_loss", "gs_iso_loss", "gs_actions_workspace_size", "gs_densify_prune",
-           "gs_mlp_push_blend", "gs_mlp_features", "gs_mlp_forward", "gs_mlp_train_grad", "gs_mlp_adam")
+           "gs_mlp_push_blend", "gs_mlp_features", "gs_mlp_forward", "gs_mlp_train_grad", "gs_mlp_adam",
+           "gs_segment_workspace_size")
 
 _lib = None
 
@@ -99,6 +101,7 @@ def lib():
         L.gs_block_mask_size.argtypes = [i64, P(sz)]
         L.gs_loss_workspace_size.argtypes = [i32, i32, P(sz)]
         L.gs_bwd_workspace_size.argtypes = [i64, P(sz)]
+        L.gs_segment_workspace_size.argtypes = [i64, i32, P(sz)]
         L.gs_prune_workspace_size.argtypes = [i64, P(sz)]
         L.gs_project.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), vp, vp]
         L.gs_sort.argtypes = [P(Projected), P(Camera), i32, P(RasterCfg), P(Binning), vp, sz, vp, vp]
@@ -177,10 +180,11 @@ class Config:
     tan_clamp: float = 1.3
     bg: tuple = (0.0, 0.0, 0.0)
     batch: int = 512
+    segment: int = 256  # split length of long tile lists, in pairs (0 = no split)
 
     def c(self) -> RasterCfg:
         return RasterCfg(self.tile_w, self.tile_h, self.near_z, self.dilation, self.alpha_min, self.alpha_max,
-                         self.t_min, self.tan_clamp, (C.c_float * 3)(*self.bg), self.batch)
+                         self.t_min, self.tan_clamp, (C.c_float * 3)(*self.bg), self.batch, self.segment)
 
 
 def planes(sh_degree: int) -> int:
@@ -293,6 +297,8 @@ class Buffers:
         self.gauss_ids = torch.empty(max(self.max_pairs, 1), dtype=torch.int32, device=dev)
         self.block_mask = _workspace(lib().gs_block_mask_size, self.max_pairs, device=dev)
         self.sort_ws = _workspace(lib().gs_sort_workspace_size, self.nrec, self.max_pairs, device=dev)
+        self.seg_ws = (_workspace(lib().gs_segment_workspace_size, self.max_pairs, self.cfg.segment, device=dev)
+                       if self.cfg.segment else None)
 
     def projected(self) -> Projected:
         return Projected(self.xy.data_ptr(), self.conic_opacity.data_ptr(), self.rgb_depth.data_ptr(),
@@ -304,7 +310,9 @@ class Buffers:
 
     def frame(self) -> Frame:
         return Frame(self.img.data_ptr(), self.T_final.data_ptr(), self.last.data_ptr(),
-                     None if self.depth is None else self.depth.data_ptr())
+                     None if self.depth is None else self.depth.data_ptr(),
+                     None if self.seg_ws is None else self.seg_ws.data_ptr(),
+                     0 if self.seg_ws is None else self.seg_ws.numel())
 
     def stats(self):
         return None if self.stats_acc is None else Stats(self.stats_acc.data_ptr(), self.stats_acc.shape[1])

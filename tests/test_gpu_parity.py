@@ -37,6 +37,10 @@ CASES = {
     "single_tile_16x16": (lambda: (scenes.uniform_scene(400, seed=13, xy_range=0.6), [scenes.pinhole(16, 16, 20.0)]),
                           gs.Config()),
     "multiview_batch256": (lambda: _multi(1), gs.Config(tile_w=8, tile_h=32, batch=256)),
+    # the backward split into segments of 64 / 32 pairs from the forward's checkpoints, and no split
+    "cfg1_segment64": (_cfg1, gs.Config(segment=64)),
+    "multiview_32x8_segment32": (lambda: _multi(2, 1500), gs.Config(tile_w=32, tile_h=8, segment=32, batch=128)),
+    "cfg1_nosplit": (_cfg1, gs.Config(segment=0)),
 }
 
 
@@ -207,19 +211,22 @@ def test_backward_gradcheck_scene(D, seed):
         assert e < 1e-3, (k, e)
 
 
-def test_backward_config1():
+@pytest.mark.parametrize("segment", [256, 32, 0])
+def test_backward_config1(segment):
     scene, cams = _cfg1()
     target_scene = scenes.perturb(scene, 0.01, seed=1)
-    st, g_gpu, g_or, _, _, losses = _backward_case(scene, cams, gs.Config(), lam=0.0, with_target_from=target_scene)
+    st, g_gpu, g_or, _, _, losses = _backward_case(scene, cams, gs.Config(segment=segment), lam=0.0,
+                                                   with_target_from=target_scene)
     assert abs(st.buf.loss.item() - losses[0]) < 1e-4 * abs(losses[0])
     for k in GROUPS:
         e = rel_l2(g_gpu[k], g_or[k])
         assert e < 1e-3, (k, e)
 
 
-def test_backward_multiview_stats():
+@pytest.mark.parametrize("segment", [256, 32])
+def test_backward_multiview_stats(segment):
     scene, cams = _multi(1, 2000)
-    cfg = gs.Config(bg=(0.1, 0.2, 0.3))
+    cfg = gs.Config(bg=(0.1, 0.2, 0.3), segment=segment)
     target_scene = scenes.perturb(scene, 0.02, seed=5)
     st, g_gpu, g_or, stats, kamb, losses = _backward_case(scene, cams, cfg, with_target_from=target_scene)
     for k in GROUPS:
@@ -420,11 +427,12 @@ def test_split_backward_and_render_schedule():
     assert np.all(np.diff(cls) <= 0)
 
 
-def test_total_loss_depth_and_isotropy():
+@pytest.mark.parametrize("segment", [256, 32])
+def test_total_loss_depth_and_isotropy(segment):
     """L_total = L_photo + 0.01 L_geo + 10 L_iso (Sec. 3.2.3, Supp. D.4): the
     rendered depth, each term and every gradient group against the oracle."""
     scene, cams = _multi(1, 2000)
-    cfg = gs.Config(bg=(0.1, 0.2, 0.3))
+    cfg = gs.Config(bg=(0.1, 0.2, 0.3), segment=segment)
     oc = ocfg(cfg)
     tscene = scenes.perturb(scene, 0.02, seed=8)
     tf = [orc.forward(tscene, c, oc) for c in cams]

@@ -3,10 +3,13 @@ the library and for profiling a single launch of each kernel:
 
     python -m paper_2606_30436_b300.example --frame 500
     python -m paper_2606_30436_b300.example --chunk 16 --gaussians 2000000
+    python -m paper_2606_30436_b300.example --mlp 4000000
 
 Renders the frame(s), evaluates L = 0.8 L1 + 0.2 (1 - SSIM) against a random
 target, back-propagates to every parameter and applies one Adam update,
-then prints the visible-record and pair counts and the loss.
+then prints the visible-record and pair counts and the loss.  With --mlp N:
+one inference, one training gradient and one Adam step of the learned
+densify / prune predictor over N rows of random inputs.
 """
 from __future__ import annotations
 
@@ -23,7 +26,26 @@ def main():
     ap.add_argument("--gaussians", type=int, default=1_000_000)
     ap.add_argument("--chunk", type=int, default=0, help="keyframes of a batched chunk (0: one corridor view)")
     ap.add_argument("--iters", type=int, default=1)
+    ap.add_argument("--mlp", type=int, default=0, help="rows for the predictor instead of a mapping iteration")
     args = ap.parse_args()
+    if args.mlp:
+        n = args.mlp
+        ld = gs.padded(n)
+        g = torch.Generator(device="cuda").manual_seed(0)
+        feat = torch.rand(gs.MLP_INPUTS, ld, device="cuda", generator=g)
+        y = (torch.rand(2, n, device="cuda", generator=g) < 0.2).to(torch.uint8)
+        w = gs.mlp_init(0)
+        grad, m, v = torch.zeros_like(w), torch.zeros_like(w), torch.zeros_like(w)
+        loss = torch.zeros(1, device="cuda")
+        prob = torch.empty(2, ld, device="cuda")
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for it in range(args.iters):
+            gs.gs_mlp_forward(feat, n, w, prob, None, None, status)
+            gs.gs_mlp_train_grad(feat, y[0].contiguous(), y[1].contiguous(), n, w, grad, loss, status)
+            gs.gs_mlp_adam(w, grad, m, v, 1e-3, it + 1)
+        torch.cuda.synchronize()
+        print("rows %d bce %.6f status %d" % (n, float(loss), int(status)))
+        return
     if args.chunk:
         scene = scenes.uniform_scene(args.gaussians, seed=0, sh_degree=0)
         cams = scenes.chunk_cameras(args.chunk, seed=2)

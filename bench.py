@@ -70,6 +70,9 @@ def algorithmic_bytes(N, V, P, px, tiles, K):
         # accumulators and parameters of the visible, gradient planes of all
         "project_bwd": 52 * V + 4 * K * V + 4 * K * N,
         "adam": 28 * K * N,
+        # the projection backward fused with the dense Adam step (read parameters and
+        # both moments, write all three, of all; no gradient planes)
+        "project_bwd_adam": 52 * V + 24 * K * N,
     }
 
 
@@ -154,7 +157,8 @@ def committed_traffic(kernel):
     import re
     src = {"k_render_bwd": "paper_2606_30436_b300/csrc/render.cu",
            "k_render_fwd": "paper_2606_30436_b300/csrc/render.cu",
-           "k_adam": "paper_2606_30436_b300/csrc/adam.cu"}.get(kernel)
+           "k_adam": "paper_2606_30436_b300/csrc/adam.cu",
+           "k_project_bwd": "paper_2606_30436_b300/csrc/project.cu"}.get(kernel)
     if src is None:
         return None
     sha = kernel_source_sha(src)
@@ -171,8 +175,10 @@ def committed_traffic(kernel):
 # GPU arm
 
 STAGES = ["project", "sort", "render_fwd", "loss", "render_bwd", "project_bwd", "adam"]
+STAGES_FUSED = ["project", "sort", "render_fwd", "loss", "render_bwd", "project_bwd_adam"]
 STAGE_KERNEL = {"project": "k_project", "sort": None, "render_fwd": "k_render_fwd", "loss": None,
-                "render_bwd": "k_render_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam"}
+                "render_bwd": "k_render_bwd", "project_bwd": "k_project_bwd", "adam": "k_adam",
+                "project_bwd_adam": "k_project_bwd"}
 
 
 def eager_step(gs, step, target, events=None, stream=None):
@@ -190,9 +196,14 @@ def eager_step(gs, step, target, events=None, stream=None):
     rec(4)
     gs.gs_render_bwd(step.model, None, b, target, step.tau_err, with_stats=step.with_stats)
     rec(5)
+    step.step_count += 1
+    if step.fused_adam:
+        gs.gs_project_bwd_adam(step.model, b, step.exp_avg, step.exp_avg_sq, step.lr, step.step_count,
+                               with_stats=step.with_stats)
+        rec(6)
+        return
     gs.gs_project_bwd(step.model, step.grads, b, with_stats=step.with_stats)
     rec(6)
-    step.step_count += 1
     gs.gs_adam(step.model, step.grads, step.exp_avg, step.exp_avg_sq, step.lr, step.step_count)
     rec(7)
 
@@ -286,14 +297,15 @@ def run_corridor(args, world, dev):
     step.check_status()
 
     # per-stage timing (eager launches, events between the C-ABI calls)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)] for _ in range(args.steps)]
+    stages = STAGES_FUSED if step.fused_adam else STAGES
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(args.steps)]
     barrier(world)
     for i in range(args.steps):
         k = i % len(cams)
         step.set_cameras([cams[k]])
         eager_step(gs, step, targets[k], evs[i], stream)
     barrier(world)
-    stage_ms = {nm: sum(e[j].elapsed_time(e[j + 1]) for e in evs) / args.steps for j, nm in enumerate(STAGES)}
+    stage_ms = {nm: sum(e[j].elapsed_time(e[j + 1]) for e in evs) / args.steps for j, nm in enumerate(stages)}
 
     # end to end through the C ABI with host buffers: pinned host target in,
     # loss out, both copies inside the timed region (eager calls)
@@ -321,7 +333,7 @@ def run_corridor(args, world, dev):
     Vm, Pm = float(np.mean(vis)), float(np.mean(needed))
     ab = algorithmic_bytes(N_GAUSS, Vm, Pm, W * H, step.buf.total_tiles, model.K)
     peak, peak_kind = measured_peaks()
-    dom = max(STAGES, key=lambda s: stage_ms[s])
+    dom = max(stages, key=lambda s: stage_ms[s])
     achieved = ab[dom] / (stage_ms[dom] * 1e-3) / 1e9
     kern = STAGE_KERNEL[dom] or dom
     roof = {"kernel": kern, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -337,7 +349,8 @@ def run_corridor(args, world, dev):
         "config": workload_config(len(frames)),
         "e2e": {"value": round(replica_throughput(args.steps, world, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": 3 * W * H * 4, "d2h_bytes_per_step": 4, "wall_s": round(wall_e2e, 3)},
-        "gpu_launches": gs.launches_per_step(step.buf.total_tiles, views=1, lambda_dssim=LAMBDA) * args.steps,
+        "gpu_launches": gs.launches_per_step(step.buf.total_tiles, views=1, lambda_dssim=LAMBDA,
+                                             segment=step.cfg.segment, fused_adam=step.fused_adam) * args.steps,
         "roofline": roof,
         "step_hbm": {"algorithmic_bytes": int(total_bytes),
                      "frac_of_peak": round(total_bytes / (ms / args.steps * 1e-3) / 1e9 / peak, 4)},

@@ -337,6 +337,22 @@ gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, int32_t
                          const gs_stats *stats, gs_stream stream);
 
 /*
+ * gs_project_bwd followed by gs_adam without the gradient buffer: each
+ * Gaussian's gradient (the projection chain from the per-record gradients in
+ * ws, plus grads_in when set, plus the isotropic term's gradient
+ * iso_weight / n * dL_iso/dlog-scale when iso_weight > 0, Supp. D.4) is applied
+ * at once as one Adam step to params, exp_avg and exp_avg_sq, with the rates,
+ * betas, eps and step rules of gs_adam.  Saves writing and re-reading the
+ * gradient (8 bytes per parameter element).  stats as gs_project_bwd.
+ */
+gs_status gs_project_bwd_adam(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                              const gs_raster_cfg *cfg, const gs_projected *proj, const void *ws,
+                              size_t ws_bytes, const float *loss_per_view, const gs_params *grads_in,
+                              float iso_weight, const gs_params *exp_avg, const gs_params *exp_avg_sq,
+                              const float lr_groups[6], float beta1, float beta2, float eps, int64_t step,
+                              const int64_t *step_device, const gs_stats *stats, gs_stream stream);
+
+/*
  * Adam (Kingma & Ba) with bias correction over every parameter plane, dense:
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; p -= lr m^ / (sqrt(v^) + eps),
  * m^ = m/(1-b1^step), v^ = v/(1-b2^step).  lr_groups (host) holds six rates:

@@ -392,6 +392,40 @@ GS_API gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, 
     return cuda_status(cudaGetLastError());
 }
 
+GS_API gs_status gs_project_bwd_adam(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                                     const gs_raster_cfg *cfg, const gs_projected *proj, const void *ws,
+                                     size_t ws_bytes, const float *loss_per_view, const gs_params *grads_in,
+                                     float iso_weight, const gs_params *exp_avg, const gs_params *exp_avg_sq,
+                                     const float lr_groups[6], float beta1, float beta2, float eps, int64_t step,
+                                     const int64_t *step_device, const gs_stats *stats, gs_stream stream) {
+    ViewTable vt;
+    RasterCfg rc;
+    gs_status st = build_views(cams, n_views, cfg, vt, rc);
+    if (st == GS_OK) st = check_params(params);
+    if (st == GS_OK) st = check_params(exp_avg);
+    if (st == GS_OK) st = check_params(exp_avg_sq);
+    if (st == GS_OK && grads_in) st = check_params(grads_in);
+    if (st != GS_OK) return st;
+    for (const gs_params *q : {exp_avg, exp_avg_sq, grads_in})
+        if (q && (q->ld != params->ld || q->n != params->n || q->sh_degree != params->sh_degree)) return GS_ERR_INVALID;
+    if (!proj || check_proj(proj, params->ld) != GS_OK) return GS_ERR_INVALID;
+    if (!lr_groups || (step < 1 && !step_device) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f) || !(iso_weight >= 0.0f))
+        return GS_ERR_INVALID;
+    if (step_device && ((uintptr_t)step_device & 7u)) return GS_ERR_INVALID;
+    if (stats && (!stats->acc || stats->ld < params->n)) return GS_ERR_INVALID;
+    const long long nrec = (long long)n_views * params->ld;
+    size_t need = 0;
+    gs_bwd_workspace_size(nrec, &need);
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < need) return GS_ERR_INVALID;
+    launch_project_bwd_adam(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius,
+                            (const float *)ws, nrec, grads_in ? grads_in->data : nullptr, exp_avg->data,
+                            exp_avg_sq->data, lr_groups, beta1, beta2, eps, step, (const long long *)step_device,
+                            iso_weight, loss_per_view, stats ? stats->acc : nullptr, stats ? stats->ld : 0,
+                            (cudaStream_t)stream);
+    return cuda_status(cudaGetLastError());
+}
+
 GS_API gs_status gs_adam(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
                          const gs_params *exp_avg_sq, const float lr_groups[6], float beta1, float beta2, float eps,
                          int64_t step, const int64_t *step_device, gs_stream stream) {

@@ -186,4 +186,20 @@ __device__ __forceinline__ void quat_rotation(float qw, float qx, float qy, floa
     R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
 }
 
+// Gradient of gscale * sum_k |s_k - mean(s)|, s = exp(log-scale), with
+// respect to the three log-scales, added into g (the isotropic term L_iso,
+// Supp. D.4): d|s_k - m|/ds_j = sign(s_k - m) (delta_kj - 1/3).
+__device__ __forceinline__ void iso_grad(float ls0, float ls1, float ls2, float gscale, float *g) {
+    const float s0 = expf(ls0), s1 = expf(ls1), s2 = expf(ls2);
+    const float m = (s0 + s1 + s2) * (1.0f / 3.0f);
+    const float d0 = s0 - m, d1 = s1 - m, d2 = s2 - m;
+    const float e0 = d0 > 0.f ? 1.f : (d0 < 0.f ? -1.f : 0.f);
+    const float e1 = d1 > 0.f ? 1.f : (d1 < 0.f ? -1.f : 0.f);
+    const float e2 = d2 > 0.f ? 1.f : (d2 < 0.f ? -1.f : 0.f);
+    const float em = (e0 + e1 + e2) * (1.0f / 3.0f);
+    g[0] += gscale * (e0 - em) * s0;
+    g[1] += gscale * (e1 - em) * s1;
+    g[2] += gscale * (e2 - em) * s2;
+}
+
 }  // namespace gs

@@ -20,6 +20,11 @@ void launch_project(const float *P, long long n, long long ld, int D, const View
 void launch_project_bwd(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
                         const int *radius, const float *acc, long long nrec, float *G, int accumulate,
                         const float *loss_per_view, float *stats, long long stats_ld, cudaStream_t s);
+void launch_project_bwd_adam(float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
+                             const int *radius, const float *acc, long long nrec, const float *G_in, float *m,
+                             float *v, const float lr[6], float beta1, float beta2, float eps, long long step,
+                             const long long *step_dev, float iso_weight, const float *loss_per_view, float *stats,
+                             long long stats_ld, cudaStream_t s);
 
 // Binning: workspace layout and launch of the whole sort pipeline.
 size_t sort_workspace_bytes(long long nrec, long long max_pairs);

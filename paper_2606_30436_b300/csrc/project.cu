@@ -241,34 +241,137 @@ __device__ __forceinline__ Cov3 cov3(const float *R, const float *s) {
     return S;
 }
 
-template <int D>
-__global__ void __launch_bounds__(256, 2) k_project_bwd(const float *__restrict__ P, long long n, long long ld,
+// Adam applied where the projection backward finishes a Gaussian's gradient
+// (the fused mode): moments, rates and bias corrections of one step.
+struct FusedAdam {
+    float *m, *v;
+    float lr[6];
+    float b1, b2, eps, inv_bc1, inv_sqrt_bc2;
+    const long long *step_dev;  // nullable: the step is read here at run time
+    float iso_gscale;           // lambda_iso / n: the isotropic term's gradient scale (0: none)
+    const float *G_in;          // nullable: gradient added to the computed one
+};
+
+__device__ __forceinline__ int adam_group(int plane) {
+    // means, log-scales, quaternion, opacity, SH degree 0, SH degree >= 1
+    return plane < 3 ? 0 : plane < 6 ? 1 : plane < 10 ? 2 : plane == 10 ? 3 : plane < 14 ? 4 : 5;
+}
+
+// Projection backward, one thread per Gaussian (planes of ld):
+//  colour part, channel by channel: each SH plane's gradient sum_v gc_v Y(d_v)
+//  is complete in registers after the view loop, and the direction term of the
+//  mean is accumulated per (channel, view) through the SH vector-Jacobian product
+//  (linear in its weights);
+//  geometry part, view by view: opacity, conic -> 2D covariance -> Sigma
+//  (summed over views), Jacobian and position; then Sigma -> scale, rotation.
+// Each plane's gradient is emitted once: written to G (accumulated when
+// `accumulate`), or, in the fused mode, turned into one Adam step of the
+// parameter and its moments, with the isotropic term and G_in added first.
+// Folds the lifecycle statistics of the views into stats (nullable).
+constexpr int kFusedThreads = 128;  // fused mode: Gaussians per CTA (four CTAs per SM overlap the two phases)
+
+template <int D, bool ADAM>
+__global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 2) k_project_bwd(float *__restrict__ P, long long n, long long ld,
                                                      ViewTable vt, RasterCfg cfg, const int *__restrict__ radius,
                                                      const float *__restrict__ acc, long long nrec,
                                                      float *__restrict__ G, int accumulate,
                                                      const float *__restrict__ loss_per_view,
-                                                     float *__restrict__ stats, long long stats_ld) {
+                                                     float *__restrict__ stats, long long stats_ld, FusedAdam fa) {
     constexpr int K = (D + 1) * (D + 1);
+    if (ADAM && fa.step_dev) {  // bias corrections from the device step counter (graph replay)
+        __shared__ float s_bc[2];
+        if (threadIdx.x == 0) {
+            const double t = (double)*fa.step_dev;
+            s_bc[0] = (float)(1.0 / (1.0 - pow((double)fa.b1, t)));
+            s_bc[1] = (float)(1.0 / sqrt(1.0 - pow((double)fa.b2, t)));
+        }
+        __syncthreads();
+        fa.inv_bc1 = s_bc[0];
+        fa.inv_sqrt_bc2 = s_bc[1];
+    }
+    constexpr int NP = 11 + 3 * K;  // parameter planes
+    extern __shared__ float s_grad[];  // fused mode: [NP][kFusedThreads] gradients of the CTA's Gaussians
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ld) return;
-    if (g >= n) {  // padding: zero gradient (Adam then leaves the padding unchanged)
-        if (!accumulate)
-            for (int k = 0; k < 11 + 3 * K; ++k) G[k * ld + g] = 0.0f;
-        return;
+    if (!ADAM) {
+        if (g >= ld) return;
+        if (g >= n) {  // padding: zero gradient
+            if (!accumulate)
+                for (int k = 0; k < NP; ++k) G[k * ld + g] = 0.0f;
+            return;
+        }
+    }
+    // one plane's gradient: to G, or (fused) to the CTA's shared gradient block
+    auto emit = [&](int plane, float grad) {
+        if (ADAM) {
+            s_grad[plane * kFusedThreads + threadIdx.x] = grad;
+        } else {
+            const long long i = (long long)plane * ld + g;
+            G[i] = accumulate ? G[i] + grad : grad;
+        }
+    };
+    if (ADAM && g >= n) {  // padding and the CTA's tail: zero gradient
+        for (int k = 0; k < NP; ++k) emit(k, 0.0f);
+    } else {
+
+    const float mx = P[0 * ld + g], my = P[1 * ld + g], mz = P[2 * ld + g];
+    float gmean[3] = {0, 0, 0};
+
+    // ---- colour: SH gradients and the direction term of the mean ----
+    #pragma unroll 1
+    for (int ch = 0; ch < 3; ++ch) {
+        float sh[K], gsh[K];
+        #pragma unroll
+        for (int k = 0; k < K; ++k) {
+            sh[k] = P[(11 + 3 * k + ch) * ld + g];
+            gsh[k] = 0.0f;
+        }
+        for (int v = 0; v < vt.n_views; ++v) {
+            const long long rec = v * ld + g;
+            if (radius[rec] <= 0) continue;
+            const ViewDesc &c = vt.v[v];
+            float ex = mx - c.campos[0], ey = my - c.campos[1], ez = mz - c.campos[2];
+            const float idist = 1.0f / sqrtf(ex * ex + ey * ey + ez * ez);
+            ex *= idist; ey *= idist; ez *= idist;
+            float Y[K];
+            sh_basis<D>(ex, ey, ez, Y);
+            float raw = 0.5f;
+            #pragma unroll
+            for (int k = 0; k < K; ++k) raw += Y[k] * sh[k];
+            const float gcv = raw < 0.0f ? 0.0f : acc[(kAccR + ch) * nrec + rec];
+            #pragma unroll
+            for (int k = 0; k < K; ++k) gsh[k] += gcv * Y[k];
+            if (D > 0) {
+                float w[K];
+                #pragma unroll
+                for (int k = 0; k < K; ++k) w[k] = gcv * sh[k];
+                float gx, gy, gz;
+                sh_basis_vjp<D>(ex, ey, ez, w, gx, gy, gz);
+                const float dd = gx * ex + gy * ey + gz * ez;  // onto the sphere's tangent plane
+                gmean[0] += (gx - ex * dd) * idist;
+                gmean[1] += (gy - ey * dd) * idist;
+                gmean[2] += (gz - ez * dd) * idist;
+            }
+        }
+        #pragma unroll
+        for (int k = 0; k < K; ++k) emit(11 + 3 * k + ch, gsh[k]);
     }
 
-    float gmean[3] = {0, 0, 0}, glogit = 0.0f;
+    // ---- geometry: opacity, conic -> 2D covariance -> Sigma, J, position ----
+    float glogit = 0.0f;
     float dSig[6] = {0, 0, 0, 0, 0, 0};  // dL/dSigma entries 00 01 02 11 12 22 (each ordered pair)
-    bool seen = false;                   // some view saw it (SH planes already written)
+    bool seen = false;
     float st_omega = 0, st_kappa = 0, st_gamma = 0, st_maxw = 0, st_gnorm = 0, st_views = 0;
-    const float mx = P[0 * ld + g], my = P[1 * ld + g], mz = P[2 * ld + g];
-
+    float R[9], s[3], nq, qh[4];
+    rot_scale(P, ld, g, R, s, nq, qh);
+    const Cov3 S = cov3(R, s);
+    const float logit = P[10 * ld + g];
+    const float o = 1.0f / (1.0f + expf(-logit));
     for (int v = 0; v < vt.n_views; ++v) {
         const long long rec = v * ld + g;
         if (radius[rec] <= 0) continue;
+        seen = true;
         const ViewDesc &c = vt.v[v];
         const float du = acc[kAccU * nrec + rec], dv = acc[kAccV * nrec + rec];
-
         if (stats) {
             const float om = acc[kAccOmega * nrec + rec];
             st_omega += om;
@@ -278,116 +381,67 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float *__restrict_
             st_gnorm += sqrtf(du * du + dv * dv);
             st_views += om > 0.0f ? 1.0f : 0.0f;
         }
-
-        // ---- colour: SH gradients and the direction term of the mean ----
-        {
-            float ex = mx - c.campos[0], ey = my - c.campos[1], ez = mz - c.campos[2];
-            const float idist = 1.0f / sqrtf(ex * ex + ey * ey + ez * ez);
-            ex *= idist; ey *= idist; ez *= idist;
-            float Y[16];
-            sh_basis<D>(ex, ey, ez, Y);
-            const bool add = accumulate || seen;
-            float w[16];
-            #pragma unroll
-            for (int k = 0; k < K; ++k) w[k] = 0.0f;
-            // one colour channel at a time keeps 16 coefficients live, not 48
-            #pragma unroll 1
-            for (int ch = 0; ch < 3; ++ch) {
-                float sh[16];
-                #pragma unroll
-                for (int k = 0; k < K; ++k) sh[k] = P[(11 + 3 * k + ch) * ld + g];
-                float raw = 0.5f;
-                #pragma unroll
-                for (int k = 0; k < K; ++k) raw += Y[k] * sh[k];
-                const float gcv = raw < 0.0f ? 0.0f : acc[(kAccR + ch) * nrec + rec];
-                #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    float *dst = G + (11 + 3 * k + ch) * ld + g;
-                    *dst = add ? *dst + gcv * Y[k] : gcv * Y[k];
-                    w[k] += gcv * sh[k];
-                }
-            }
-            if (D > 0) {
-                float gx, gy, gz;
-                sh_basis_vjp<D>(ex, ey, ez, w, gx, gy, gz);
-                const float dd = gx * ex + gy * ey + gz * ez;  // onto the sphere's tangent plane
-                gmean[0] += (gx - ex * dd) * idist;
-                gmean[1] += (gy - ey * dd) * idist;
-                gmean[2] += (gz - ez * dd) * idist;
-            }
+        glogit += acc[kAccO * nrec + rec] * o * (1.0f - o);
+        const float da = acc[kAccA * nrec + rec], db = acc[kAccB * nrec + rec], dc = acc[kAccC * nrec + rec];
+        const float gdepth = acc[kAccZ * nrec + rec];
+        const ExactPos p = exact_position(c, mx, my, mz);
+        const float x = p.xc, y = p.yc, z = p.zc;
+        const Ewa e = ewa(c, x, y, z, S);
+        const float A = e.A + cfg.dilation, B = e.B, C = e.C + cfg.dilation;
+        const float idet = 1.0f / (A * C - B * B);
+        const float qa = C * idet, qb = -B * idet, qcc = A * idet;
+        // conic Q = Sigma'^-1: dL/dSigma' = -Q G Q, G = [[da, db/2], [db/2, dc]]
+        const float hb = 0.5f * db;
+        const float QG00 = qa * da + qb * hb, QG01 = qa * hb + qb * dc;
+        const float QG10 = qb * da + qcc * hb, QG11 = qb * hb + qcc * dc;
+        const float dA = -(QG00 * qa + QG01 * qb);
+        const float dBh = -(QG00 * qb + QG01 * qcc);  // per entry of the symmetric off-diagonal
+        const float dC = -(QG10 * qb + QG11 * qcc);
+        // Sigma' = T Sigma T^T: dSigma = T^T Sd T, dT = 2 Sd T Sigma, Sd = [[dA, dBh], [dBh, dC]]
+        const float *T = e.T;
+        float U[6];
+        #pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            U[k] = dA * T[k] + dBh * T[3 + k];
+            U[3 + k] = dBh * T[k] + dC * T[3 + k];
         }
-        seen = true;
-
-        // ---- geometry: opacity, conic -> 2D covariance -> Sigma, J, position ----
-        {
-            float R[9], s[3], nq, qh[4];
-            rot_scale(P, ld, g, R, s, nq, qh);
-            const Cov3 S = cov3(R, s);
-            const float o = 1.0f / (1.0f + expf(-P[10 * ld + g]));
-            glogit += acc[kAccO * nrec + rec] * o * (1.0f - o);
-            const float da = acc[kAccA * nrec + rec], db = acc[kAccB * nrec + rec], dc = acc[kAccC * nrec + rec];
-            const float gdepth = acc[kAccZ * nrec + rec];
-            const ExactPos p = exact_position(c, mx, my, mz);
-            const float x = p.xc, y = p.yc, z = p.zc;
-            const Ewa e = ewa(c, x, y, z, S);
-            const float A = e.A + cfg.dilation, B = e.B, C = e.C + cfg.dilation;
-            const float idet = 1.0f / (A * C - B * B);
-            const float qa = C * idet, qb = -B * idet, qcc = A * idet;
-            // conic Q = Sigma'^-1: dL/dSigma' = -Q G Q, G = [[da, db/2], [db/2, dc]]
-            const float hb = 0.5f * db;
-            const float QG00 = qa * da + qb * hb, QG01 = qa * hb + qb * dc;
-            const float QG10 = qb * da + qcc * hb, QG11 = qb * hb + qcc * dc;
-            const float dA = -(QG00 * qa + QG01 * qb);
-            const float dBh = -(QG00 * qb + QG01 * qcc);  // per entry of the symmetric off-diagonal
-            const float dC = -(QG10 * qb + QG11 * qcc);
-            // Sigma' = T Sigma T^T: dSigma = T^T Sd T, dT = 2 Sd T Sigma, Sd = [[dA, dBh], [dBh, dC]]
-            const float *T = e.T;
-            float U[6];
-            #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                U[k] = dA * T[k] + dBh * T[3 + k];
-                U[3 + k] = dBh * T[k] + dC * T[3 + k];
-            }
-            dSig[0] += T[0] * U[0] + T[3] * U[3];
-            dSig[1] += T[0] * U[1] + T[3] * U[4];
-            dSig[2] += T[0] * U[2] + T[3] * U[5];
-            dSig[3] += T[1] * U[1] + T[4] * U[4];
-            dSig[4] += T[1] * U[2] + T[4] * U[5];
-            dSig[5] += T[2] * U[2] + T[5] * U[5];
-            float dT[6];
-            #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const float u0 = U[3 * r], u1 = U[3 * r + 1], u2 = U[3 * r + 2];
-                dT[3 * r + 0] = 2.0f * (u0 * S.s00 + u1 * S.s01 + u2 * S.s02);
-                dT[3 * r + 1] = 2.0f * (u0 * S.s01 + u1 * S.s11 + u2 * S.s12);
-                dT[3 * r + 2] = 2.0f * (u0 * S.s02 + u1 * S.s12 + u2 * S.s22);
-            }
-            // T = J W: dJ = dT W^T; J00 = fx/z, J02 = -fx tx/z^2, J11 = fy/z, J12 = -fy ty/z^2
-            const float dJ00 = dT[0] * c.R[0] + dT[1] * c.R[1] + dT[2] * c.R[2];
-            const float dJ02 = dT[0] * c.R[6] + dT[1] * c.R[7] + dT[2] * c.R[8];
-            const float dJ11 = dT[3] * c.R[3] + dT[4] * c.R[4] + dT[5] * c.R[5];
-            const float dJ12 = dT[3] * c.R[6] + dT[4] * c.R[7] + dT[5] * c.R[8];
-            const float iz = 1.0f / z, iz2 = iz * iz, iz3 = iz2 * iz;
-            const float dtx_dx = (e.clx_lo || e.clx_hi) ? 0.0f : 1.0f;
-            const float dtx_dz = e.clx_lo ? -c.limx : (e.clx_hi ? c.limx : 0.0f);
-            const float dty_dy = (e.cly_lo || e.cly_hi) ? 0.0f : 1.0f;
-            const float dty_dz = e.cly_lo ? -c.limy : (e.cly_hi ? c.limy : 0.0f);
-            const float gx = dJ02 * (-c.fx * iz2) * dtx_dx + du * c.fx * iz;
-            const float gy = dJ12 * (-c.fy * iz2) * dty_dy + dv * c.fy * iz;
-            const float gz = -dJ00 * c.fx * iz2 - dJ11 * c.fy * iz2 +
-                             dJ02 * (-c.fx * dtx_dz * iz2 + 2.0f * c.fx * e.tx * iz3) +
-                             dJ12 * (-c.fy * dty_dz * iz2 + 2.0f * c.fy * e.ty * iz3) -
-                             du * c.fx * x * iz2 - dv * c.fy * y * iz2 + gdepth;
-            gmean[0] += c.R[0] * gx + c.R[3] * gy + c.R[6] * gz;
-            gmean[1] += c.R[1] * gx + c.R[4] * gy + c.R[7] * gz;
-            gmean[2] += c.R[2] * gx + c.R[5] * gy + c.R[8] * gz;
+        dSig[0] += T[0] * U[0] + T[3] * U[3];
+        dSig[1] += T[0] * U[1] + T[3] * U[4];
+        dSig[2] += T[0] * U[2] + T[3] * U[5];
+        dSig[3] += T[1] * U[1] + T[4] * U[4];
+        dSig[4] += T[1] * U[2] + T[4] * U[5];
+        dSig[5] += T[2] * U[2] + T[5] * U[5];
+        float dT[6];
+        #pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float u0 = U[3 * r], u1 = U[3 * r + 1], u2 = U[3 * r + 2];
+            dT[3 * r + 0] = 2.0f * (u0 * S.s00 + u1 * S.s01 + u2 * S.s02);
+            dT[3 * r + 1] = 2.0f * (u0 * S.s01 + u1 * S.s11 + u2 * S.s12);
+            dT[3 * r + 2] = 2.0f * (u0 * S.s02 + u1 * S.s12 + u2 * S.s22);
         }
+        // T = J W: dJ = dT W^T; J00 = fx/z, J02 = -fx tx/z^2, J11 = fy/z, J12 = -fy ty/z^2
+        const float dJ00 = dT[0] * c.R[0] + dT[1] * c.R[1] + dT[2] * c.R[2];
+        const float dJ02 = dT[0] * c.R[6] + dT[1] * c.R[7] + dT[2] * c.R[8];
+        const float dJ11 = dT[3] * c.R[3] + dT[4] * c.R[4] + dT[5] * c.R[5];
+        const float dJ12 = dT[3] * c.R[6] + dT[4] * c.R[7] + dT[5] * c.R[8];
+        const float iz = 1.0f / z, iz2 = iz * iz, iz3 = iz2 * iz;
+        const float dtx_dx = (e.clx_lo || e.clx_hi) ? 0.0f : 1.0f;
+        const float dtx_dz = e.clx_lo ? -c.limx : (e.clx_hi ? c.limx : 0.0f);
+        const float dty_dy = (e.cly_lo || e.cly_hi) ? 0.0f : 1.0f;
+        const float dty_dz = e.cly_lo ? -c.limy : (e.cly_hi ? c.limy : 0.0f);
+        const float gx = dJ02 * (-c.fx * iz2) * dtx_dx + du * c.fx * iz;
+        const float gy = dJ12 * (-c.fy * iz2) * dty_dy + dv * c.fy * iz;
+        const float gz = -dJ00 * c.fx * iz2 - dJ11 * c.fy * iz2 +
+                         dJ02 * (-c.fx * dtx_dz * iz2 + 2.0f * c.fx * e.tx * iz3) +
+                         dJ12 * (-c.fy * dty_dz * iz2 + 2.0f * c.fy * e.ty * iz3) -
+                         du * c.fx * x * iz2 - dv * c.fy * y * iz2 + gdepth;
+        gmean[0] += c.R[0] * gx + c.R[3] * gy + c.R[6] * gz;
+        gmean[1] += c.R[1] * gx + c.R[4] * gy + c.R[7] * gz;
+        gmean[2] += c.R[2] * gx + c.R[5] * gy + c.R[8] * gz;
     }
 
     float glogs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0};
     if (seen) {
-        float R[9], s[3], nq, qh[4];
-        rot_scale(P, ld, g, R, s, nq, qh);
         float M[9];
         #pragma unroll
         for (int r = 0; r < 3; ++r)
@@ -424,17 +478,11 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float *__restrict_
         gq[2] = (dqy - y_ * qd) / nq;
         gq[3] = (dqz - z_ * qd) / nq;
     }
-
-    auto put = [&](int plane, float val) {
-        float *dst = G + plane * ld + g;
-        *dst = accumulate ? *dst + val : val;
-    };
-    put(0, gmean[0]); put(1, gmean[1]); put(2, gmean[2]);
-    put(3, glogs[0]); put(4, glogs[1]); put(5, glogs[2]);
-    put(6, gq[0]); put(7, gq[1]); put(8, gq[2]); put(9, gq[3]);
-    put(10, glogit);
-    if (!seen && !accumulate)
-        for (int k = 0; k < 3 * K; ++k) G[(11 + k) * ld + g] = 0.0f;
+    if (ADAM && fa.iso_gscale != 0.0f) iso_grad(P[3 * ld + g], P[4 * ld + g], P[5 * ld + g], fa.iso_gscale, glogs);
+    emit(0, gmean[0]); emit(1, gmean[1]); emit(2, gmean[2]);
+    emit(3, glogs[0]); emit(4, glogs[1]); emit(5, glogs[2]);
+    emit(6, gq[0]); emit(7, gq[1]); emit(8, gq[2]); emit(9, gq[3]);
+    emit(10, glogit);
 
     if (stats) {
         stats[0 * stats_ld + g] += st_omega;
@@ -443,6 +491,56 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float *__restrict_
         stats[3 * stats_ld + g] = fmaxf(stats[3 * stats_ld + g], st_maxw);
         stats[4 * stats_ld + g] += st_gnorm;
         stats[5 * stats_ld + g] += st_views;
+    }
+    }  // g < n
+    if (ADAM) {
+        // the CTA's NP x kFusedThreads block of parameters and moments, streamed as
+        // float4 (ld is a multiple of 32, so a float4 never crosses the end of a plane)
+        __syncthreads();
+        constexpr int Q = kFusedThreads / 4;  // float4 per plane
+        constexpr int U = 4;                  // float4 updates whose loads are issued together
+        const long long g0 = (long long)blockIdx.x * kFusedThreads;
+        const int lim = ld - g0 < kFusedThreads ? (int)(ld - g0) : kFusedThreads;
+        const float *__restrict__ Gin = fa.G_in;
+        float *__restrict__ Mp = fa.m;
+        float *__restrict__ Vp = fa.v;
+        for (int base = threadIdx.x; base < NP * Q; base += U * kFusedThreads) {
+            float4 m4[U], v4[U], p4[U], gi[U];
+            long long ii[U];
+            bool ok[U];
+            int pl[U], qq[U];
+            #pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int idx = base + u * kFusedThreads;
+                pl[u] = idx / Q;
+                qq[u] = (idx % Q) * 4;
+                ok[u] = idx < NP * Q && qq[u] < lim;
+                ii[u] = (long long)pl[u] * ld + g0 + qq[u];
+                if (ok[u]) {
+                    m4[u] = *reinterpret_cast<const float4 *>(Mp + ii[u]);
+                    v4[u] = *reinterpret_cast<const float4 *>(Vp + ii[u]);
+                    p4[u] = *reinterpret_cast<const float4 *>(P + ii[u]);
+                    gi[u] = Gin ? *reinterpret_cast<const float4 *>(Gin + ii[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            #pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!ok[u]) continue;
+                const float4 gs4 = *reinterpret_cast<const float4 *>(&s_grad[pl[u] * kFusedThreads + qq[u]]);
+                const float gr[4] = {gs4.x + gi[u].x, gs4.y + gi[u].y, gs4.z + gi[u].z, gs4.w + gi[u].w};
+                float *m = &m4[u].x, *v = &v4[u].x, *pp = &p4[u].x;
+                const float a = fa.lr[adam_group(pl[u])];
+                #pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    m[c] = fa.b1 * m[c] + (1.0f - fa.b1) * gr[c];
+                    v[c] = fa.b2 * v[c] + (1.0f - fa.b2) * gr[c] * gr[c];
+                    pp[c] -= a * (m[c] * fa.inv_bc1) / (sqrtf(v[c]) * fa.inv_sqrt_bc2 + fa.eps);
+                }
+                *reinterpret_cast<float4 *>(Mp + ii[u]) = m4[u];
+                *reinterpret_cast<float4 *>(Vp + ii[u]) = v4[u];
+                *reinterpret_cast<float4 *>(P + ii[u]) = p4[u];
+            }
+        }
     }
 }
 
@@ -463,8 +561,9 @@ void launch_project_bwd(const float *P, long long n, long long ld, int D, const 
                         const float *loss_per_view, float *stats, long long stats_ld, cudaStream_t s) {
     if (ld <= 0) return;
     const int blocks = (int)ceil_div(ld, 256);
-#define GS_PB(DD) k_project_bwd<DD><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, radius, acc, nrec, G, accumulate, \
-                                                            loss_per_view, stats, stats_ld)
+    FusedAdam fa{};
+#define GS_PB(DD) k_project_bwd<DD, false><<<blocks, 256, 0, s>>>(const_cast<float *>(P), n, ld, vt, cfg, radius, acc, \
+                                                                   nrec, G, accumulate, loss_per_view, stats, stats_ld, fa)
     switch (D) {
         case 0: GS_PB(0); break;
         case 1: GS_PB(1); break;
@@ -472,6 +571,47 @@ void launch_project_bwd(const float *P, long long n, long long ld, int D, const 
         default: GS_PB(3); break;
     }
 #undef GS_PB
+}
+
+void launch_project_bwd_adam(float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
+                             const int *radius, const float *acc, long long nrec, const float *G_in, float *m,
+                             float *v, const float lr[6], float beta1, float beta2, float eps, long long step,
+                             const long long *step_dev, float iso_weight, const float *loss_per_view, float *stats,
+                             long long stats_ld, cudaStream_t s) {
+    if (ld <= 0) return;
+    const int blocks = (int)ceil_div(ld, kFusedThreads);
+    FusedAdam fa{};
+    fa.m = m;
+    fa.v = v;
+    for (int k = 0; k < 6; ++k) fa.lr[k] = lr[k];
+    fa.b1 = beta1;
+    fa.b2 = beta2;
+    fa.eps = eps;
+    const double st = step_dev ? 1.0 : (double)step;  // placeholder when the device counter is used
+    fa.inv_bc1 = (float)(1.0 / (1.0 - pow((double)beta1, st)));
+    fa.inv_sqrt_bc2 = (float)(1.0 / sqrt(1.0 - pow((double)beta2, st)));
+    fa.step_dev = step_dev;
+    fa.iso_gscale = n > 0 ? (float)(iso_weight / (double)n) : 0.0f;
+    fa.G_in = G_in;
+#define GS_PBA(DD)                                                                                              \
+    do {                                                                                                        \
+        const int smem = (11 + 3 * (DD + 1) * (DD + 1)) * kFusedThreads * (int)sizeof(float);                   \
+        static bool attr = false; /* once per process, before any capture uses it */                            \
+        if (!attr) {                                                                                            \
+            cudaFuncSetAttribute(k_project_bwd<DD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);    \
+            attr = true;                                                                                        \
+        }                                                                                                       \
+        k_project_bwd<DD, true><<<blocks, kFusedThreads, smem, s>>>(P, n, ld, vt, cfg, radius, acc, nrec,       \
+                                                                    nullptr, 0,                                 \
+                                                          loss_per_view, stats, stats_ld, fa);                 \
+    } while (0)
+    switch (D) {
+        case 0: GS_PBA(0); break;
+        case 1: GS_PBA(1); break;
+        case 2: GS_PBA(2); break;
+        default: GS_PBA(3); break;
+    }
+#undef GS_PBA
 }
 
 }  // namespace gs

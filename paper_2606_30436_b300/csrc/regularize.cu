@@ -57,13 +57,11 @@ __global__ void __launch_bounds__(256) k_iso(const float *__restrict__ P, long l
         const float d0 = s0 - m, d1 = s1 - m, d2 = s2 - m;
         sum += (double)(fabsf(d0) + fabsf(d1) + fabsf(d2));
         if (G) {
-            const float e0 = d0 > 0.f ? 1.f : (d0 < 0.f ? -1.f : 0.f);
-            const float e1 = d1 > 0.f ? 1.f : (d1 < 0.f ? -1.f : 0.f);
-            const float e2 = d2 > 0.f ? 1.f : (d2 < 0.f ? -1.f : 0.f);
-            const float em = (e0 + e1 + e2) * (1.0f / 3.0f);  // d|s_k - m|/ds_j = e_k (delta_kj - 1/3)
-            G[3 * ld + i] += gscale * (e0 - em) * s0;
-            G[4 * ld + i] += gscale * (e1 - em) * s1;
-            G[5 * ld + i] += gscale * (e2 - em) * s2;
+            float gl[3] = {0.0f, 0.0f, 0.0f};
+            iso_grad(P[3 * ld + i], P[4 * ld + i], P[5 * ld + i], gscale, gl);
+            G[3 * ld + i] += gl[0];
+            G[4 * ld + i] += gl[1];
+            G[5 * ld + i] += gl[2];
         }
     }
     const double t = block_sum_dbl(sum, sm);

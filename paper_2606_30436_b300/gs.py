@@ -78,7 +78,7 @@ EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspac
            "gs_render_bwd", "gs_project_bwd", "gs_adam", "gs_prune_stats", "gs_loss_static",
            "gs_reg_workspace_size", "gs_geo_loss", "gs_iso_loss", "gs_actions_workspace_size", "gs_densify_prune",
            "gs_mlp_push_blend", "gs_mlp_features", "gs_mlp_forward", "gs_mlp_train_grad", "gs_mlp_adam",
-           "gs_segment_workspace_size")
+           "gs_segment_workspace_size", "gs_project_bwd_adam")
 
 _lib = None
 
@@ -116,6 +116,9 @@ def lib():
         L.gs_project_bwd.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), vp, sz, vp, P(Params), i32,
                                      P(Stats), vp]
         L.gs_adam.argtypes = [P(Params), P(Params), P(Params), P(Params), P(f32 * 6), f32, f32, f32, i64, vp, vp]
+        L.gs_project_bwd_adam.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), vp, sz, vp,
+                                          P(Params), f32, P(Params), P(Params), P(f32 * 6), f32, f32, f32, i64, vp,
+                                          P(Stats), vp]
         L.gs_prune_stats.argtypes = [P(Stats), i64, i32, f32, f32, P(ChunkScores), vp, sz, vp]
         L.gs_actions_workspace_size.argtypes = [i64, P(sz)]
         L.gs_densify_prune.argtypes = [P(Params), P(Params), P(Params), vp, vp, vp, f32, f32, P(Params), P(Params),
@@ -415,6 +418,22 @@ def gs_project_bwd(model: GaussianModel, grads: GaussianModel, buf: Buffers, acc
            "gs_project_bwd")
 
 
+def gs_project_bwd_adam(model: GaussianModel, buf: Buffers, exp_avg: GaussianModel, exp_avg_sq: GaussianModel, lr,
+                        step, beta1=0.9, beta2=0.999, eps=1e-15, iso_weight=0.0, grads_in: GaussianModel = None,
+                        with_stats=True, stream=None, step_device=None):
+    """Projection backward from the per-record gradients that gs_render_bwd(grads=None) left in buf.bwd_ws,
+    fused with one Adam step (no gradient buffer)."""
+    lrs = (C.c_float * 6)(*[float(x) for x in lr])
+    st = buf.stats() if with_stats else None
+    arr = camera_array(buf.cams)
+    _check(lib().gs_project_bwd_adam(C.byref(model.c()), arr, buf.n_views, C.byref(buf.cfg.c()),
+                                     C.byref(buf.projected()), _ptr(buf.bwd_ws), buf.bwd_ws.numel(), _ptr(buf.loss),
+                                     C.byref(grads_in.c()) if grads_in is not None else None, float(iso_weight),
+                                     C.byref(exp_avg.c()), C.byref(exp_avg_sq.c()), C.byref(lrs), beta1, beta2, eps,
+                                     int(step), _ptr(step_device), C.byref(st) if st is not None else None,
+                                     _stream(stream)), "gs_project_bwd_adam")
+
+
 def gs_adam(model: GaussianModel, grads: GaussianModel, exp_avg: GaussianModel, exp_avg_sq: GaussianModel, lr,
             step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None, step_device=None):
     lrs = (C.c_float * 6)(*[float(x) for x in lr])
@@ -530,7 +549,7 @@ class MappingStep:
 
     def __init__(self, model: GaussianModel, cams, cfg: Config = None, max_pairs=None, lambda_dssim=0.2,
                  tau_err=0.1, lr=None, with_stats=True, with_depth=False, depth_prior=None, lambda_geo=0.01,
-                 lambda_iso=0.0, moments=None, step_count=0):
+                 lambda_iso=0.0, moments=None, step_count=0, fused_adam=False):
         self.model = model
         self.cfg = cfg or Config()
         self.lambda_dssim, self.tau_err = lambda_dssim, tau_err
@@ -539,11 +558,14 @@ class MappingStep:
         with_depth = with_depth or depth_prior is not None
         self.lr = lr or default_lr()
         self.with_stats = with_stats
-        self.grads = model.like()
+        self._grads = None  # allocated on first use: the fused path needs no gradient buffer
         # Adam moments: zero, or carried over (e.g. through gs_densify_prune)
         self.exp_avg, self.exp_avg_sq = moments if moments is not None else (model.like(), model.like())
         assert self.exp_avg.ld == model.ld and self.exp_avg_sq.ld == model.ld
         self.step_count = int(step_count)
+        # Adam inside the projection backward: no gradient buffer (236 MB less at 1M
+        # Gaussians, SH3) but, at its occupancy, slower than projection backward + Adam
+        self.fused_adam = fused_adam
         if max_pairs is None:
             max_pairs = max(1 << 16, 8 * model.n * len(cams))
         self.buf = Buffers(model, cams, self.cfg, max_pairs, with_depth=with_depth, with_stats=with_stats)
@@ -553,6 +575,16 @@ class MappingStep:
         self.iso_loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self.dL_ddepth = (torch.empty(self.buf.total_pixels, dtype=torch.float32, device=dev)
                           if depth_prior is not None else None)
+
+    @property
+    def grads(self) -> GaussianModel:
+        if self._grads is None:
+            self._grads = self.model.like()
+        return self._grads
+
+    @grads.setter
+    def grads(self, value: GaussianModel):
+        self._grads = value
 
     def set_cameras(self, cams):
         assert len(cams) == self.buf.n_views
@@ -576,6 +608,20 @@ class MappingStep:
         if self.lambda_iso > 0:
             gs_iso_loss(self.model, self.lambda_iso, self.iso_loss, self.grads, self.reg_ws, stream)
 
+    def _losses_backward_adam(self, target, stream=None, step=None, step_device=None):
+        """Losses, the compositing backward, then the projection backward fused
+        with the Adam step (the gradient is never stored)."""
+        gs_loss(self.buf, target, self.lambda_dssim, stream)
+        if self.depth_prior is not None:
+            gs_geo_loss(self.buf, self.depth_prior, self.lambda_geo, self.geo_loss, self.dL_ddepth, self.reg_ws, stream)
+        gs_render_bwd(self.model, None, self.buf, target, self.tau_err, with_stats=self.with_stats,
+                      dL_ddepth=self.dL_ddepth, stream=stream)
+        if self.lambda_iso > 0:
+            gs_iso_loss(self.model, self.lambda_iso, self.iso_loss, None, self.reg_ws, stream)
+        gs_project_bwd_adam(self.model, self.buf, self.exp_avg, self.exp_avg_sq, self.lr,
+                            1 if step is None else step, iso_weight=self.lambda_iso, with_stats=self.with_stats,
+                            stream=stream, step_device=step_device)
+
     def total_loss(self):
         """L_total = sum over views of L_photo (+ lambda_geo L_geo) + lambda_iso L_iso (device tensor)."""
         t = self.buf.loss.sum()
@@ -588,6 +634,10 @@ class MappingStep:
     def step(self, target, stream=None, optimize=True):
         """One iteration on device-resident targets (frame layout)."""
         self.forward(stream)
+        if optimize and self.fused_adam:
+            self.step_count += 1
+            self._losses_backward_adam(target, stream, step=self.step_count)
+            return self.buf.loss
         self._losses_and_backward(target, stream)
         if optimize:
             self.step_count += 1
@@ -612,9 +662,12 @@ class MappingStep:
             gs_project(self.model, b)
             gs_sort(b)
             gs_render_fwd(b)
-            self._losses_and_backward(target)
             self.step_dev.add_(1)
-            gs_adam(self.model, self.grads, self.exp_avg, self.exp_avg_sq, self.lr, 1, step_device=self.step_dev)
+            if self.fused_adam:
+                self._losses_backward_adam(target, step_device=self.step_dev)
+            else:
+                self._losses_and_backward(target)
+                gs_adam(self.model, self.grads, self.exp_avg, self.exp_avg_sq, self.lr, 1, step_device=self.step_dev)
         torch.cuda.current_stream(dev).wait_stream(side)
         return graph
 
@@ -644,14 +697,16 @@ class MappingStep:
         return needed
 
 
-def launches_per_step(total_tiles, views=1, lambda_dssim=0.2):
+def launches_per_step(total_tiles, views=1, lambda_dssim=0.2, segment=256, fused_adam=False):
     """Kernel launches of the library in one mapping iteration (memsets not
     counted): project 1; sort 3 + 3x4 depth passes + 5 + 3 per tile-bit pass
-    + 1 + 3 (render schedule); render 1; loss 3 (2 when lambda = 0) per view; backward 2; Adam 1."""
+    + 1 + 3 (render schedule); render 1 (4 with the split: plan, segments,
+    combine, re-runs); loss 3 (2 when lambda = 0) per view; backward 2
+    (compositing, projection); Adam 1 unless fused into the projection backward."""
     tile_bits = 0
     while (1 << tile_bits) < total_tiles:
         tile_bits += 1
     tile_passes = (tile_bits + 7) // 8
     sort = 3 + 3 * 4 + 5 + 3 * tile_passes + 1 + 3 + (0 if tile_passes else 1)
     loss = (3 if lambda_dssim > 0 else 2) * views
-    return 1 + sort + 1 + loss + 2 + 1
+    return 1 + sort + (4 if segment else 1) + loss + 2 + (0 if fused_adam else 1)

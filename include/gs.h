@@ -190,11 +190,17 @@ gs_status gs_block_mask_size(int64_t max_pairs, size_t *bytes);
 /* Workspace bytes of gs_loss for a view of h x w pixels (the largest view). */
 gs_status gs_loss_workspace_size(int32_t h, int32_t w, size_t *bytes);
 
-/* Bytes of gs_frame.seg_ws for max_pairs pairs split every `segment` pairs:
- * per long tile (more than `segment` pairs) a plan entry, per segment of its
- * eight 8x4 blocks the forward's local state (768 bytes) and the backward's
- * checkpoint (640 bytes); about 1.4 KB x 16 max_pairs / segment. */
+/* Bytes of gs_frame.seg_ws.  A long tile (more than `segment` pairs) needs
+ * 8 x S segment items (S = its segments), each about 1.45 KB (the forward's
+ * local state, a re-run slot and the backward's checkpoint).  The capacities
+ * follow from the bytes given: gs_segment_workspace_size covers the worst case
+ * for max_pairs (every pair in a long tile), gs_segment_workspace_size_items a
+ * measured item count.  When a launch needs more items than fit, the split is
+ * off for that launch (every block walks its whole list: same results,
+ * slower) and the item count it needed is left in the workspace's int32 at
+ * byte offset 20 (the int32 at offset 16 is 1), for the caller to resize. */
 gs_status gs_segment_workspace_size(int64_t max_pairs, int32_t segment, size_t *bytes);
+gs_status gs_segment_workspace_size_items(int64_t items, size_t *bytes);
 
 /* Workspace bytes of gs_render_bwd for n_records records. */
 gs_status gs_bwd_workspace_size(int64_t n_records, size_t *bytes);

@@ -49,8 +49,10 @@ def autotune(model: gs.GaussianModel, cams, targets_for, base: gs.Config = None,
             resize = st.buf.cfg.segment != segment
             st.cfg = cfg
             st.buf.cfg = cfg
-            if resize:  # the split workspace follows the segment length
+            if resize:  # the split workspace follows the segment length and the items measured
+                st.buf.seg_items = 0
                 st.buf.set_max_pairs(st.buf.max_pairs)
+                st.fit_capacity()
             for _ in range(2):
                 st.step(target, optimize=False)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

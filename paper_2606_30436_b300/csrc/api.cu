@@ -31,40 +31,30 @@ gs_status check_cfg(const gs_raster_cfg *cfg) {
     return GS_OK;
 }
 
-size_t seg_ws_bytes(long long max_pairs, int segment) {
-    const long long hcap = seg_heavy_capacity(max_pairs, segment), fcap = seg_item_capacity(max_pairs, segment);
-    const long long cap = seg_capacity(max_pairs, segment);
-    return 256 + align_up(sizeof(int4) * (size_t)hcap, 256) + align_up(sizeof(float) * kFresFloats * (size_t)fcap, 256) +
-           align_up(sizeof(int4) * (size_t)fcap, 256) + align_up(sizeof(int2) * (size_t)cap, 256) +
-           sizeof(float) * kCkptFloats * (size_t)cap;
-}
-
-// The split workspace of a frame (no split: all null, capacities 0).
-gs_status seg_of(const gs_raster_cfg *cfg, const gs_binning *binning, const gs_frame *frame, SegWs &seg) {
+// The split workspace of a frame (no split: all null, capacities 0); its
+// capacities follow from the bytes the caller gave.
+gs_status seg_of(const gs_raster_cfg *cfg, const gs_frame *frame, SegWs &seg) {
     seg = SegWs{nullptr, nullptr, 0, nullptr, nullptr, 0, nullptr, nullptr, 0};
     if (cfg->segment == 0) return GS_OK;
-    if (!frame->seg_ws || ((uintptr_t)frame->seg_ws & 255u) ||
-        frame->seg_ws_bytes < seg_ws_bytes(binning->max_pairs, cfg->segment))
-        return GS_ERR_INVALID;
-    const long long hcap = seg_heavy_capacity(binning->max_pairs, cfg->segment);
-    const long long fcap = seg_item_capacity(binning->max_pairs, cfg->segment);
-    const long long cap = seg_capacity(binning->max_pairs, cfg->segment);
-    if (fcap > 0x7fffffffll) return GS_ERR_INVALID;
+    if (!frame->seg_ws || ((uintptr_t)frame->seg_ws & 255u)) return GS_ERR_INVALID;
+    const long long F = seg_items_in(frame->seg_ws_bytes);
+    if (F < 16 || F > 0x7fffffffll) return GS_ERR_INVALID;
+    const long long hcap = seg_heavy_for(F);
     unsigned char *b = (unsigned char *)frame->seg_ws;
     size_t off = 256;
     seg.count = (int *)b;
     seg.heavy = (int4 *)(b + off);
     off += align_up(sizeof(int4) * (size_t)hcap, 256);
     seg.fres = (float *)(b + off);
-    off += align_up(sizeof(float) * kFresFloats * (size_t)fcap, 256);
+    off += align_up(sizeof(float) * kFresFloats * (size_t)F, 256);
     seg.tasks = (int4 *)(b + off);
-    off += align_up(sizeof(int4) * (size_t)fcap, 256);
+    off += align_up(sizeof(int4) * (size_t)F, 256);
     seg.items = (int2 *)(b + off);
-    off += align_up(sizeof(int2) * (size_t)cap, 256);
+    off += align_up(sizeof(int2) * (size_t)F, 256);
     seg.ckpt = (float *)(b + off);
     seg.hcap = (int)hcap;
-    seg.fcap = (int)fcap;
-    seg.cap = (int)cap;
+    seg.fcap = (int)F;
+    seg.cap = (int)F;
     return GS_OK;
 }
 
@@ -187,7 +177,13 @@ GS_API gs_status gs_loss_workspace_size(int32_t h, int32_t w, size_t *bytes) {
 
 GS_API gs_status gs_segment_workspace_size(int64_t max_pairs, int32_t segment, size_t *bytes) {
     if (!bytes || max_pairs < 0 || segment < 32 || segment > 65536 || (segment & (segment - 1))) return GS_ERR_INVALID;
-    *bytes = seg_ws_bytes(max_pairs, segment);
+    *bytes = seg_bytes_for(seg_items_worst(max_pairs, segment));
+    return GS_OK;
+}
+
+GS_API gs_status gs_segment_workspace_size_items(int64_t items, size_t *bytes) {
+    if (!bytes || items < 0 || items > 0x7fffffffll) return GS_ERR_INVALID;
+    *bytes = seg_bytes_for(items < 16 ? 16 : items);
     return GS_OK;
 }
 
@@ -247,7 +243,7 @@ GS_API gs_status gs_render_fwd(const gs_projected *proj, const gs_binning *binni
     if ((st = check_binning(binning)) != GS_OK) return st;
     if (!frame || !frame->img || !frame->T_final || !frame->last) return GS_ERR_INVALID;
     SegWs seg;
-    if ((st = seg_of(cfg, binning, frame, seg)) != GS_OK) return st;
+    if ((st = seg_of(cfg, frame, seg)) != GS_OK) return st;
     launch_render_fwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, binning->block_mask,
                       binning->tile_order, (const float2 *)proj->xy,
                       (const float4 *)proj->conic_opacity, (const float4 *)proj->rgb_depth, frame->img,
@@ -346,7 +342,7 @@ GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, i
     if (!proj || check_proj(proj, params->ld) != GS_OK || check_binning(binning) != GS_OK) return GS_ERR_INVALID;
     if (!frame || !frame->img || !frame->T_final || !frame->last || !dL_dimg) return GS_ERR_INVALID;
     SegWs seg;
-    if ((st = seg_of(cfg, binning, frame, seg)) != GS_OK) return st;
+    if ((st = seg_of(cfg, frame, seg)) != GS_OK) return st;
     const bool want_stats = stats != nullptr;
     if (want_stats && (!stats->acc || stats->ld < params->n || !target)) return GS_ERR_INVALID;
     const long long nrec = (long long)n_views * params->ld;

@@ -30,6 +30,10 @@ struct ViewTable {
     ViewDesc v[GS_MAX_VIEWS];
 };
 
+__host__ __device__ __forceinline__ long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+
+__host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
 struct RasterCfg {
     float near_z, dilation, alpha_min, alpha_max, t_min, tan_clamp;
     float bg[3];
@@ -46,7 +50,8 @@ struct RasterCfg {
 // and colour in front (C0, C1, C2, depth) after the pairs before the boundary,
 // [5][32] floats.
 struct SegWs {
-    int *count;   // [0] forward items, [1] long tiles, [2] checkpoints, [3] re-run tasks
+    int *count;   // [0] forward items, [1] long tiles, [2] checkpoints, [3] re-run tasks,
+                  // [4] 1 = the plan did not fit (no split this launch), [5] items the plan needed
     int4 *heavy;
     int hcap;
     float *fres;
@@ -59,16 +64,25 @@ struct SegWs {
 constexpr int kCkptFloats = 5 * 32;
 constexpr int kFresFloats = 6 * 32;
 
-// long tiles: each holds more than one segment of pairs
-__host__ __device__ __forceinline__ long long seg_heavy_capacity(long long max_pairs, int segment) {
-    return ((max_pairs > 0 ? max_pairs : 1) + segment - 1) / segment + 1;
+// Capacities of a split workspace for F forward segment items: long tiles
+// <= F / 16 (each has at least two segments of 8 blocks), re-run tasks and
+// checkpoints <= F; and the bytes that takes.
+__host__ __device__ __forceinline__ long long seg_heavy_for(long long F) { return F / 16 + 1; }
+__host__ __device__ __forceinline__ size_t seg_bytes_for(long long F) {
+    return 256 + align_up(16 * (size_t)seg_heavy_for(F), 256) + align_up(4 * 192 * (size_t)F, 256) +
+           align_up(16 * (size_t)F, 256) + align_up(8 * (size_t)F, 256) + 4 * 160 * (size_t)F;
 }
-// forward items: 8 blocks x S segments per long tile, S <= len / segment + 1
-__host__ __device__ __forceinline__ long long seg_item_capacity(long long max_pairs, int segment) {
-    return 16 * seg_heavy_capacity(max_pairs, segment);
+// The largest item capacity that fits in `bytes`.
+__host__ __device__ __forceinline__ long long seg_items_in(size_t bytes) {
+    if (bytes < seg_bytes_for(16)) return 0;
+    long long F = (long long)((bytes - 256 - 5 * 256) / (1 + 768 + 16 + 8 + 640 + 1));  // estimate, then exact
+    while (seg_bytes_for(F + 1) <= bytes) ++F;
+    while (F > 16 && seg_bytes_for(F) > bytes) --F;
+    return F;
 }
-__host__ __device__ __forceinline__ long long seg_capacity(long long max_pairs, int segment) {
-    return 8 * (((max_pairs > 0 ? max_pairs : 1) + segment - 1) / segment) + 8;
+// Worst case for max_pairs pairs: every pair in a long tile, S_t <= len / segment + 1.
+__host__ __device__ __forceinline__ long long seg_items_worst(long long max_pairs, int segment) {
+    return 16 * (((max_pairs > 0 ? max_pairs : 1) + segment - 1) / segment + 1);
 }
 
 // The view that owns a global tile index (linear scan: <= 64 views, uniform
@@ -175,9 +189,7 @@ __host__ __device__ __forceinline__ long long block_mask_bytes(long long max_pai
     return max_pairs + 16 + 512;
 }
 
-__host__ __device__ __forceinline__ long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 
-__host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Rotation matrix (row-major) of the unit quaternion (w, x, y, z).
 __device__ __forceinline__ void quat_rotation(float qw, float qx, float qy, float qz, float *R) {

@@ -261,8 +261,12 @@ __global__ void __launch_bounds__(kPlanThreads) k_fwd_plan(const int2 *__restric
         }
     }
     if (t == kPlanThreads - 1) {
-        seg.count[0] = base;  // segment items
-        seg.count[1] = h;     // long tiles
+        // items, long tiles and checkpoints (8 (S - 1) per long tile) against the capacities
+        const bool fits = base <= seg.fcap && h <= seg.hcap && base - 8 * h <= seg.cap;
+        seg.count[0] = fits ? base : 0;  // segment items
+        seg.count[1] = fits ? h : 0;     // long tiles
+        seg.count[4] = fits ? 0 : 1;     // no split: every block walks its whole list
+        seg.count[5] = base;             // items needed
     }
 }
 
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(32 * kWarps, 1) k_render_fwd(ViewTable vt, Ras
     if (unit >= vt.total_tiles * 8) return;
     const int tile = order[unit >> 3], bit = unit & 7;  // longest tiles first
     const int2 rg = ranges[tile];
-    if (cfg.seg_shift >= 0 && rg.y - rg.x > (1 << cfg.seg_shift)) return;  // long tile: segment items
+    if (cfg.seg_shift >= 0 && rg.y - rg.x > (1 << cfg.seg_shift) && !seg.count[4]) return;  // long: segment items
     const Unit t = unit_ctx(vt, tile, bit);
     FwdState st{1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, !t.inside};
     fwd_range<WIN>(cfg, masks, ids, xy, co, rgbd, rg.x, rg.x, rg.y, bit, t.px + 0.5f, t.py + 0.5f, st, sh);
@@ -615,7 +619,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
     // or, for an item, segment bk-1, which starts from the checkpoint at
     // boundary bk: T there and the colour behind = (final - in front) / T
     int lo = rg.x, hi = rg.x + wmax;
-    if (cfg.seg_shift >= 0) {
+    if (cfg.seg_shift >= 0 && !seg.count[4]) {
         const int s_last = (wmax - 1) >> cfg.seg_shift;
         if (item >= 0) {
             if (bk > s_last) return;  // boundary at or past the unit's last blended pair
@@ -761,7 +765,7 @@ void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ra
     const bool split = cfg.seg_shift >= 0;
     int item_blocks = 0, cgrid = 0, rgrid = 0;
     if (split) {
-        cudaMemsetAsync(seg.count, 0, 4 * sizeof(int), s);
+        cudaMemsetAsync(seg.count, 0, 8 * sizeof(int), s);
         k_fwd_plan<<<1, kPlanThreads, 0, s>>>(ranges, order, vt.total_tiles, cfg.seg_shift, seg);
         item_blocks = stride_blocks(seg.fcap);
         cgrid = stride_blocks(8ll * seg.hcap);

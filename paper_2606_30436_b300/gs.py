@@ -78,7 +78,7 @@ EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspac
            "gs_render_bwd", "gs_project_bwd", "gs_adam", "gs_prune_stats", "gs_loss_static",
            "gs_reg_workspace_size", "gs_geo_loss", "gs_iso_loss", "gs_actions_workspace_size", "gs_densify_prune",
            "gs_mlp_push_blend", "gs_mlp_features", "gs_mlp_forward", "gs_mlp_train_grad", "gs_mlp_adam",
-           "gs_segment_workspace_size", "gs_project_bwd_adam")
+           "gs_segment_workspace_size", "gs_project_bwd_adam", "gs_segment_workspace_size_items")
 
 _lib = None
 
@@ -102,6 +102,7 @@ def lib():
         L.gs_loss_workspace_size.argtypes = [i32, i32, P(sz)]
         L.gs_bwd_workspace_size.argtypes = [i64, P(sz)]
         L.gs_segment_workspace_size.argtypes = [i64, i32, P(sz)]
+        L.gs_segment_workspace_size_items.argtypes = [i64, P(sz)]
         L.gs_prune_workspace_size.argtypes = [i64, P(sz)]
         L.gs_project.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), vp, vp]
         L.gs_sort.argtypes = [P(Projected), P(Camera), i32, P(RasterCfg), P(Binning), vp, sz, vp, vp]
@@ -300,8 +301,26 @@ class Buffers:
         self.gauss_ids = torch.empty(max(self.max_pairs, 1), dtype=torch.int32, device=dev)
         self.block_mask = _workspace(lib().gs_block_mask_size, self.max_pairs, device=dev)
         self.sort_ws = _workspace(lib().gs_sort_workspace_size, self.nrec, self.max_pairs, device=dev)
-        self.seg_ws = (_workspace(lib().gs_segment_workspace_size, self.max_pairs, self.cfg.segment, device=dev)
-                       if self.cfg.segment else None)
+        if self.cfg.segment:
+            if getattr(self, "seg_items", 0) == 0:
+                # the worst case for max_pairs, up to 65,536 items; fit_capacity grows it to the count measured
+                n = C.c_size_t()
+                _check(lib().gs_segment_workspace_size(self.max_pairs, self.cfg.segment, C.byref(n)),
+                       "gs_segment_workspace_size")
+                self.seg_items = min(65536, int(n.value) // 1433 + 16)
+            self.set_seg_items(self.seg_items)
+        else:
+            self.seg_ws = None
+
+    def set_seg_items(self, items):
+        """Split workspace for `items` forward segment items."""
+        self.seg_items = int(items)
+        self.seg_ws = _workspace(lib().gs_segment_workspace_size_items, self.seg_items, device=self.xy.device)
+
+    def seg_needed(self):
+        """(split off for lack of room in the last forward, segment items that forward needed)."""
+        h = self.seg_ws[:24].view(torch.int32).cpu().numpy()
+        return bool(h[4]), int(h[5])
 
     def projected(self) -> Projected:
         return Projected(self.xy.data_ptr(), self.conic_opacity.data_ptr(), self.rgb_depth.data_ptr(),
@@ -685,7 +704,8 @@ class MappingStep:
         return st
 
     def fit_capacity(self, slack=1.25):
-        """Runs the forward once and sizes the pair buffer to the count seen."""
+        """Runs the forward once and sizes the pair buffer (and the split
+        workspace) to the counts seen."""
         self.forward()
         torch.cuda.synchronize()
         needed = int(self.buf.counts[2].item())
@@ -693,6 +713,12 @@ class MappingStep:
             self.buf.set_max_pairs(max(1024, int(needed * slack)))
             self.forward()
             torch.cuda.synchronize()
+        if self.buf.seg_ws is not None:
+            off, items = self.buf.seg_needed()
+            if off or items > self.buf.seg_items:
+                self.buf.set_seg_items(int(items * max(slack, 1.25)) + 64)
+                self.forward()
+                torch.cuda.synchronize()
         self.check_status()
         return needed
 

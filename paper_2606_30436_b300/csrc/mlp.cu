@@ -93,6 +93,18 @@ __device__ __forceinline__ void tmem_row64(uint32_t tmem, int col, float *v) {
 }
 
 // Operand arrays start on 128-byte boundaries (descriptors need 16).
+// Columns [c0, c0 + 8) of this thread's row (one core-matrix row, 16 bytes),
+// rounded to BF16 (round to nearest even), as one 16-byte shared store.
+__device__ __forceinline__ void store_row8(__nv_bfloat16 *base, int row, int c0, int kgroups, const float *v) {
+    uint4 u;
+    __nv_bfloat162 b;
+    b = __floats2bfloat162_rn(v[0], v[1]); u.x = *reinterpret_cast<uint32_t *>(&b);
+    b = __floats2bfloat162_rn(v[2], v[3]); u.y = *reinterpret_cast<uint32_t *>(&b);
+    b = __floats2bfloat162_rn(v[4], v[5]); u.z = *reinterpret_cast<uint32_t *>(&b);
+    b = __floats2bfloat162_rn(v[6], v[7]); u.w = *reinterpret_cast<uint32_t *>(&b);
+    *reinterpret_cast<uint4 *>(base + cm_off(row, c0, kgroups)) = u;
+}
+
 struct MlpSmem {
     alignas(128) __nv_bfloat16 w1[kH * kIn];   // B of layer 1: [n = out][k = in]
     alignas(128) __nv_bfloat16 w2[kH * kH];    // B of layer 2: [n = out][k = in]
@@ -173,10 +185,9 @@ __device__ bool mlp_tile_forward(MlpSmem &s, uint32_t &phase, float *h1, float *
     if (ok) {
         tmem_row64(tmem, 0, h1);
         #pragma unroll
-        for (int c = 0; c < kH; ++c) {
-            h1[c] = fmaxf(h1[c] + s.b1[c], 0.0f);
-            s.h1[cm_off(threadIdx.x, c, kH / 8)] = __float2bfloat16_rn(h1[c]);
-        }
+        for (int c = 0; c < kH; ++c) h1[c] = fmaxf(h1[c] + s.b1[c], 0.0f);
+        #pragma unroll
+        for (int c0 = 0; c0 < kH; c0 += 8) store_row8(s.h1, threadIdx.x, c0, kH / 8, h1 + c0);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -214,7 +225,7 @@ __device__ __forceinline__ void stage_features(MlpSmem &s, const float *__restri
     }
 }
 
-__global__ void __launch_bounds__(kM) k_mlp_forward(const float *__restrict__ feat, long long n, long long ld,
+__global__ void __launch_bounds__(kM, 4) k_mlp_forward(const float *__restrict__ feat, long long n, long long ld,
                                                      const float *__restrict__ w, float *__restrict__ prob,
                                                      uint8_t *__restrict__ densify, uint8_t *__restrict__ prune,
                                                      int *__restrict__ status) {
@@ -223,10 +234,20 @@ __global__ void __launch_bounds__(kM) k_mlp_forward(const float *__restrict__ fe
     uint32_t phase = 0;
     bool ok = true;
     const long long tiles = ceil_div(n, (long long)kM);
+    // the next tile's inputs are loaded into registers while this tile's MMAs run
+    float xn[kIn];
+    auto load = [&](long long t) {
+        const long long row = t * kM + threadIdx.x;
+        #pragma unroll
+        for (int c = 0; c < kIn; ++c) xn[c] = row < n ? feat[c * ld + row] : 0.0f;
+    };
+    if ((long long)blockIdx.x < tiles) load(blockIdx.x);
     for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
         const long long row = t * kM + threadIdx.x;
         const bool valid = row < n;
-        stage_features(s, feat, ld, row, valid, nullptr);
+        store_row8(s.x, threadIdx.x, 0, kIn / 8, xn);
+        store_row8(s.x, threadIdx.x, 8, kIn / 8, xn + 8);
+        if (t + gridDim.x < tiles) load(t + gridDim.x);
         float h1[kH], h2[kH];
         ok = mlp_tile_forward(s, phase, h1, h2);
         if (ok && valid) {

@@ -267,6 +267,16 @@ def run_corridor(args, world, dev):
     step.buf.set_max_pairs(int(max(needed) * 1.15) + 1024)
     stream = torch.cuda.current_stream()
 
+    # split workspace: frames whose plan did not fit would walk whole lists (reported)
+    split_fallback = []
+    if step.buf.seg_ws is not None:
+        for k, c in enumerate(cams):
+            step.set_cameras([c])
+            step.forward()
+            torch.cuda.synchronize()
+            if step.buf.seg_needed()[0]:
+                split_fallback.append(frames[k])
+
     # eager warm-up, then one captured iteration per frame of the pool
     for i in range(args.warmup):
         step.set_cameras([cams[i % len(cams)]])
@@ -355,6 +365,7 @@ def run_corridor(args, world, dev):
         "step_hbm": {"algorithmic_bytes": int(total_bytes),
                      "frac_of_peak": round(total_bytes / (ms / args.steps * 1e-3) / 1e9 / peak, 4)},
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "split": {"segment": step.cfg.segment, "frames_without_split": split_fallback},
         "visible_mean": int(Vm), "pairs_mean": int(Pm),
         "clocks": clk,
     }
@@ -416,6 +427,14 @@ def run_chunk(args, world, dev):
     st.check_status()
     V = int(st.buf.counts[0].item())
     tiles_total = st.buf.total_tiles
+    # per-stage times of the same chunk iteration (eager launches, events between the calls)
+    stages = STAGES_FUSED if st.fused_adam else STAGES
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(steps)]
+    for i in range(steps):
+        eager_step(gs, st, target, evs[i])
+    torch.cuda.synchronize()
+    chunk_stage_ms = {nm: round(sum(e[j].elapsed_time(e[j + 1]) for e in evs) / steps, 4)
+                      for j, nm in enumerate(stages)}
     del g, st
     torch.cuda.synchronize()
 
@@ -462,7 +481,8 @@ def run_chunk(args, world, dev):
             "tuned": {"tile": "%dx%d" % (best.tile_w, best.tile_h), "batch": best.batch,
                       "segment": best.segment,
                       "sweep_ms": {"%dx%d/%d/%d" % k: round(v, 3) for k, v in sorted(table.items())}},
-            "pairs": needed, "visible_records": V, "tiles": tiles_total, "steps": steps}
+            "stages_ms": chunk_stage_ms, "pairs": needed, "visible_records": V, "tiles": tiles_total,
+            "steps": steps}
 
 
 def run_gpu(args, rank, world):

@@ -271,7 +271,7 @@ __device__ __forceinline__ int adam_group(int plane) {
 constexpr int kFusedThreads = 128;  // fused mode: Gaussians per CTA (four CTAs per SM overlap the two phases)
 
 template <int D, bool ADAM>
-__global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 2) k_project_bwd(float *__restrict__ P, long long n, long long ld,
+__global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 3) k_project_bwd(float *__restrict__ P, long long n, long long ld,
                                                      ViewTable vt, RasterCfg cfg, const int *__restrict__ radius,
                                                      const float *__restrict__ acc, long long nrec,
                                                      float *__restrict__ G, int accumulate,

@@ -163,10 +163,10 @@ __global__ void __launch_bounds__(kSortBlocks) k_radix_scan(uint32_t *__restrict
 constexpr int kDownItems = 16;
 constexpr int kDownTile = kSortThreads * kDownItems;  // 4096
 
-// With `rec` set (the last pass of the pair sort), the scatter writes the
-// outputs the renderer reads instead of the raw pairs: the Gaussian id
-// rec[value] into vout, the block mask (key >> 24) into masks, and the tile
-// (key & 0xffffff) into kout for the range pass.
+// With `rec` set (the last pass of the pair sort; only tested for null), the
+// scatter writes the outputs the renderer reads instead of the raw pairs: the
+// record (the pair's value) into vout, the block mask (key >> 24) into masks,
+// and the tile (key & 0xffffff) into kout for the range pass.
 __global__ void __launch_bounds__(kSortThreads, 3) k_radix_downsweep(const uint32_t *__restrict__ kin,
                                                                    const uint32_t *__restrict__ vin,
                                                                    uint32_t *__restrict__ kout,
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_radix_downsweep(const uint3
                 const uint32_t d = (key >> shift) & mask;
                 const uint32_t pos = s_base[d] + (uint32_t)i - s_dstart[d];
                 kout[pos] = key & 0xffffffu;
-                vout[pos] = rec[s_val[i]];
+                vout[pos] = s_val[i];  // the record
                 masks[pos] = (uint8_t)(key >> 24);
             }
         } else {
@@ -335,10 +335,11 @@ constexpr int kBigRecord = 128;  // records overlapping more tiles are emitted b
 // running slot counts (shuffles), then the slot's tile in that record's
 // rectangle (row-major) and the mask of the tile's 8x4 blocks the Gaussian
 // can reach.  key = tile | mask << 24 (the LSD sort orders on the tile bits
-// only, the mask rides along), value = depth rank.  Larger records go to a
+// only, the mask rides along), value = the record (emission follows the depth
+// order, so the stable tile partition keeps it without a rank).  Larger records go to a
 // list for k_emit_big, so no warp is left with a near-camera Gaussian's
 // thousands of tiles.
-__device__ __forceinline__ void emit_one(uint32_t o, uint32_t rank, int i, int x0, int y0, int w, int toff, int gw,
+__device__ __forceinline__ void emit_one(uint32_t o, uint32_t record, int i, int x0, int y0, int w, int toff, int gw,
                                          const Reach &rb, const ViewTable &vt,
                                          uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
     // i / w through a float reciprocal (i < 2^24, w < 2^16), then one exact correction step
@@ -348,7 +349,7 @@ __device__ __forceinline__ void emit_one(uint32_t o, uint32_t rank, int i, int x
     const int ty = y0 + qt, tx = x0 + (i - qt * w);
     const uint32_t m = block_mask_of(rb, tx * vt.tile_w, ty * vt.tile_h, vt.tile_w);
     pkey[o] = (uint32_t)(toff + ty * gw + tx) | (m << 24);
-    pval[o] = rank;
+    pval[o] = record;
 }
 
 __global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t *__restrict__ sorted_rec,
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t *__restrict__
          r0 += nwarps * 32) {
         const long long r = r0 + lane;
         const bool valid = r < V;
-        uint32_t my_off = 0;
+        uint32_t my_off = 0, my_rec = 0;
         int x0 = 0, y0 = 0, w = 1, toff = 0, gw = 1, n_small = 0;
         Reach rb;  // the record's alpha >= alpha_min box, computed once per record
         rb.cx = rb.cy = rb.ex = rb.ey = 0.0f;
@@ -374,6 +375,7 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t *__restrict__
         rb.all = false;
         if (valid) {
             const uint32_t rec = sorted_rec[r];
+            my_rec = rec;
             my_off = off[r];
             const int nt = (int)(off[r + 1] - my_off);
             if (nt > kBigRecord) {
@@ -411,6 +413,7 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t *__restrict__
             // skip back over lanes with no small slots that share the same excl
             const int ej = __shfl_sync(0xffffffffu, excl, j);
             const uint32_t oj = __shfl_sync(0xffffffffu, my_off, j);
+            const uint32_t recj = __shfl_sync(0xffffffffu, my_rec, j);
             const int jx0 = __shfl_sync(0xffffffffu, x0, j), jy0 = __shfl_sync(0xffffffffu, y0, j);
             const int jw = __shfl_sync(0xffffffffu, w, j), jtoff = __shfl_sync(0xffffffffu, toff, j);
             const int jgw = __shfl_sync(0xffffffffu, gw, j), jn = __shfl_sync(0xffffffffu, n_small, j);
@@ -422,7 +425,7 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t *__restrict__
             jr.all = (jf & 2) != 0;
             if (c < total && c - ej < jn) {
                 const int i = c - ej;
-                emit_one(oj + (uint32_t)i, (uint32_t)(r0 + j), i, jx0, jy0, jw, jtoff, jgw, jr, vt, pkey, pval);
+                emit_one(oj + (uint32_t)i, recj, i, jx0, jy0, jw, jtoff, jgw, jr, vt, pkey, pval);
             }
         }
     }
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(256) k_emit_big(const uint32_t *__restrict__ s
         const Rect rc = tile_rect(p.x, p.y, radius[rec], vt.tile_w, vt.tile_h, c.GW, c.GH);
         const Reach rb = reach_box(p, q, alpha_min);
         for (int i = threadIdx.x; i < nt; i += blockDim.x)
-            emit_one(o0 + (uint32_t)i, r, i, rc.x0, rc.y0, rc.x1 - rc.x0, c.tile_offset, c.GW, rb, vt, pkey, pval);
+            emit_one(o0 + (uint32_t)i, rec, i, rc.x0, rc.y0, rc.x1 - rc.x0, c.tile_offset, c.GW, rb, vt, pkey, pval);
     }
 }
 
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(256) k_unpack_pairs(const uint32_t *__restrict
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         const uint32_t key = pkey[p];
         tkey[p] = key & 0xffffffu;
-        ids[p] = (int)rec[pval[p]];
+        ids[p] = (int)pval[p];
         masks[p] = (uint8_t)(key >> 24);
     }
 }

@@ -27,6 +27,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="keyframes of a batched chunk (0: one corridor view)")
     ap.add_argument("--iters", type=int, default=1)
     ap.add_argument("--mlp", type=int, default=0, help="rows for the predictor instead of a mapping iteration")
+    ap.add_argument("--segment", type=int, default=None,
+                    help="split length of long tile lists (default: 256 for a corridor view, none for a chunk)")
     args = ap.parse_args()
     if args.mlp:
         n = args.mlp
@@ -53,7 +55,8 @@ def main():
         scene = scenes.corridor_scene(args.gaussians, seed=0, sh_degree=3)
         cams = [scenes.corridor_camera(args.frame)]
     model = gs.GaussianModel.from_scene(scene)
-    st = gs.MappingStep(model, cams, gs.Config(), lambda_dssim=0.2, lr=gs.default_lr(extent=10.0))
+    segment = args.segment if args.segment is not None else (0 if args.chunk else 256)
+    st = gs.MappingStep(model, cams, gs.Config(segment=segment), lambda_dssim=0.2, lr=gs.default_lr(extent=10.0))
     st.fit_capacity()
     target = torch.rand(3 * st.buf.total_pixels, device="cuda")
     for _ in range(args.iters):

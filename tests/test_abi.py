@@ -96,3 +96,23 @@ def test_plane_packing_roundtrip():
         assert np.array_equal(back[k], s[k])
     # SH coefficient k of channel c sits in plane 11 + 3k + c
     assert arr[11 + 3 * 5 + 2, 7] == s["sh"][7, 5, 2]
+
+
+def test_segment_workspace_sizes():
+    """Split-workspace sizing: the worst case for max_pairs covers 16 items per segment of pairs, sizes grow
+    with the item count, and bad arguments are refused on the host."""
+    L = gs.lib()
+    n = C.c_size_t()
+    sizes = []
+    for items in (16, 17, 1000, 65536):
+        assert L.gs_segment_workspace_size_items(items, C.byref(n)) == 0
+        sizes.append(n.value)
+    assert sizes == sorted(sizes) and sizes[0] > 0
+    assert sizes[-1] > 65536 * 1400  # about 1.4 KB per item (local state, re-run slot, checkpoint)
+    assert L.gs_segment_workspace_size(1_000_000, 256, C.byref(n)) == 0
+    worst = n.value
+    assert L.gs_segment_workspace_size_items(16 * (1_000_000 // 256 + 2), C.byref(n)) == 0
+    assert worst <= n.value
+    assert L.gs_segment_workspace_size(1000, 100, C.byref(n)) == 1   # not a power of two
+    assert L.gs_segment_workspace_size(1000, 16, C.byref(n)) == 1    # below 32
+    assert L.gs_segment_workspace_size_items(-1, C.byref(n)) == 1

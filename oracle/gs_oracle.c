@@ -979,8 +979,10 @@ void or_mlp_forward(int64_t n, const double *x, const double *w, int32_t bf16, d
 
 /* Mean binary cross-entropy over the n rows and both outputs of the labels
  * y[n][2] in {0, 1}; writes dL/dw (accumulated into g) and returns L.
- * bf16 as in or_mlp_forward; the backward then rounds the tensor-core operand
- * of the hidden-layer gradient (dL/dh2 before the product with W2) too. */
+ * bf16 as in or_mlp_forward; the backward then rounds the tensor-core
+ * operands too: dL/dh2 / scale (before the product with W2 and in the layer-2
+ * weight and bias sums, with bf16(h1)) and dL/dh1 / scale (in the layer-1 weight
+ * and bias sums, with the rounded inputs); the output layer stays unrounded. */
 double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double *w, int32_t bf16, double *g) {
     double L = 0.0;
     const double scale = 1.0 / (double)(n * OR_MLP_OUT);
@@ -1003,9 +1005,12 @@ double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double
             for (int k = 0; k < OR_MLP_OUT; ++k) s += dz[k] * w[OR_MLP_W3 + k * OR_MLP_H + c];
             dh2[c] = h2[c] > 0.0 ? s : 0.0;
         }
+        /* layer-2 weight and bias gradients: in bf16 mode a tensor-core contraction
+         * over rows of bf16(dh2 / scale) with bf16(h1) and with an exact 1 */
         for (int o = 0; o < OR_MLP_H; ++o) {
-            g[OR_MLP_B2 + o] += dh2[o];
-            for (int c = 0; c < OR_MLP_H; ++c) g[OR_MLP_W2 + o * OR_MLP_H + c] += dh2[o] * h1[c];
+            const double d = bf16 ? bf16_round(dh2[o] / scale) * scale : dh2[o];
+            g[OR_MLP_B2 + o] += d;
+            for (int c = 0; c < OR_MLP_H; ++c) g[OR_MLP_W2 + o * OR_MLP_H + c] += d * (bf16 ? bf16_round(h1[c]) : h1[c]);
         }
         double dh1[OR_MLP_H];
         for (int c = 0; c < OR_MLP_H; ++c) {
@@ -1016,9 +1021,12 @@ double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double
             }
             dh1[c] = h1[c] > 0.0 ? s : 0.0;
         }
+        /* layer-1 weight and bias gradients: likewise bf16(dh1 / scale) with the
+         * (already rounded) inputs and with an exact 1 */
         for (int o = 0; o < OR_MLP_H; ++o) {
-            g[OR_MLP_B1 + o] += dh1[o];
-            for (int c = 0; c < OR_MLP_IN; ++c) g[OR_MLP_W1 + o * OR_MLP_IN + c] += dh1[o] * xi[c];
+            const double d = bf16 ? bf16_round(dh1[o] / scale) * scale : dh1[o];
+            g[OR_MLP_B1 + o] += d;
+            for (int c = 0; c < OR_MLP_IN; ++c) g[OR_MLP_W1 + o * OR_MLP_IN + c] += d * xi[c];
         }
     }
     return L * scale;

@@ -81,3 +81,44 @@ def test_bf16_rounding(orc):
     w[0] = 1.0 + 3 * 2 ** -9
     pb, _, _ = orc.mlp_forward(x, w, bf16=True)
     assert abs(pb[0, 0] - 1 / (1 + math.exp(-(1.0 + 2 ** -7)))) < 1e-15
+
+
+def _bf16(v):
+    """Round to the nearest bfloat16 (ties to even) through float32 bits, independently of the oracle."""
+    b = np.asarray(v, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_gradient_one_unit_closed_form(orc):
+    """One connected unit per layer and one row: the hidden layers' weight and
+    bias gradients in bfloat16 mode, written out by hand with the rounding of
+    every tensor-core operand (dh2 / scale, h1, dh1 / scale, x) placed as the
+    oracle's header states; and they differ from the unrounded values."""
+    n = orc.mlp_num_weights()
+    W1, B1, W2, B2, W3, B3 = 0, 1024, 1088, 5184, 5248, 5376
+    w = np.zeros(n)
+    w[W1:W1 + 16] = np.linspace(-0.31, 0.47, 16)
+    w[B1] = 0.113
+    w[W2] = 1.37
+    w[B2] = -0.071
+    w[W3], w[W3 + 64] = 1.93, -0.87
+    w[B3:B3 + 2] = [0.3, -0.2]
+    x = (np.linspace(0.2, 1.1, 16) + 0.01 * np.random.default_rng(3).standard_normal(16))[None, :]
+    y = np.array([[1.0, 0.0]])
+    _, g = orc.mlp_bce_grad(x, y, w, bf16=True)
+    scale = 1.0 / 2.0  # one row, two outputs
+    xb, w1b, w2b = _bf16(x[0]), _bf16(w[W1:W1 + 16]), _bf16(w[W2])
+    h1 = max(xb @ w1b + w[B1], 0.0)
+    h2 = max(w2b * _bf16(h1) + w[B2], 0.0)
+    assert h1 > 0.1 and h2 > 0.1  # both units active
+    z = np.array([w[W3] * h2 + w[B3], w[W3 + 64] * h2 + w[B3 + 1]])
+    dz = (1 / (1 + np.exp(-z)) - y[0]) * scale
+    dh2 = (dz[0] * w[W3] + dz[1] * w[W3 + 64]) * (h2 > 0)
+    d2 = _bf16(dh2 / scale) * scale
+    assert abs(g[B2] - d2) <= 1e-15 and abs(g[W2] - d2 * _bf16(h1)) <= 1e-15
+    dh1 = (h1 > 0) * _bf16(dh2 / scale) * w2b * scale
+    d1 = _bf16(dh1 / scale) * scale
+    assert abs(g[B1] - d1) <= 1e-15
+    assert np.abs(g[W1:W1 + 16] - d1 * xb).max() <= 1e-15
+    assert g[W2] != dh2 * h1 and g[B1] != dh1  # the rounding is applied

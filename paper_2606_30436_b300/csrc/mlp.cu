@@ -115,24 +115,24 @@ struct MlpSmem {
     uint32_t tmem;
 };
 
-__device__ void tmem_alloc(uint32_t *slot) {
+__device__ void tmem_alloc(uint32_t *slot, uint32_t cols) {
     if ((threadIdx.x >> 5) == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_addr(slot)),
-                     "r"(kTmemCols));
+                     "r"(cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
 }
 
-__device__ void tmem_free(uint32_t tmem) {
+__device__ void tmem_free(uint32_t tmem, uint32_t cols) {
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if ((threadIdx.x >> 5) == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem),
-                                               "r"(kTmemCols));
+                                               "r"(cols));
 }
 
 // Loads the weights into shared memory (BF16 operands, FP32 rest), allocates
 // TMEM and initialises the mbarrier.
-__device__ void mlp_setup(MlpSmem &s, const float *__restrict__ w) {
+__device__ void mlp_setup(MlpSmem &s, const float *__restrict__ w, uint32_t cols = kTmemCols) {
     for (int i = threadIdx.x; i < kH * kIn; i += blockDim.x) {
         const int o = i / kIn, c = i % kIn;
         s.w1[cm_off(o, c, kIn / 8)] = __float2bfloat16_rn(w[kW1 + i]);
@@ -144,7 +144,7 @@ __device__ void mlp_setup(MlpSmem &s, const float *__restrict__ w) {
     for (int i = threadIdx.x; i < kH; i += blockDim.x) { s.b1[i] = w[kB1 + i]; s.b2[i] = w[kB2 + i]; }
     for (int i = threadIdx.x; i < kOut * kH; i += blockDim.x) s.w3[i] = w[kW3 + i];
     if (threadIdx.x < kOut) s.b3[threadIdx.x] = w[kB3 + threadIdx.x];
-    tmem_alloc(&s.tmem);
+    tmem_alloc(&s.tmem, cols);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&s.mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -157,12 +157,12 @@ __device__ void mlp_setup(MlpSmem &s, const float *__restrict__ w) {
 
 // After a timed-out wait no further MMA is issued; the last one committed
 // (parity phase ^ 1) gets one more bounded wait before its TMEM is freed.
-__device__ void mlp_finish(MlpSmem &s, bool ok, uint32_t phase, int *status) {
+__device__ void mlp_finish(MlpSmem &s, bool ok, uint32_t phase, int *status, uint32_t cols = kTmemCols) {
     if (!ok) {
         mbar_wait(&s.mbar, phase ^ 1u);
         if (threadIdx.x == 0 && status) atomicOr(status, 1 << GS_ERR_TIMEOUT);
     }
-    tmem_free(s.tmem);
+    tmem_free(s.tmem, cols);
 }
 
 // One tile's forward through layer 2.  The thread's features are already in
@@ -268,63 +268,88 @@ __global__ void __launch_bounds__(kM, 4) k_mlp_forward(const float *__restrict__
 }
 
 // Training step: mean BCE over the n rows and both outputs, gradient of every
-// weight accumulated into grads (FP32 atomics, one set per CTA).
+// weight accumulated into grads (FP32 atomics, one set per CTA).  Per tile:
+// the forward (layers 1 and 2 on the tensor cores), the head and dL/dh2 in
+// FP32, then three tcgen05 contractions with BF16 operands and FP32
+// accumulators in TMEM:
+//   dh1 (before the ReLU mask) = dh2 W2                          [128 x 64],
+//   dW2 | db2 += dh2^T [h1 | 1]   over the tile's rows (K = 128)  [64 x 80],
+//   dW1 | db1 += dh1^T [x | 1]    over the tile's rows            [64 x 32];
+// dh2 and dh1 enter as dL/dh / scale (O(1) values), the sums are rescaled at
+// the end.  The weight sums use M = 128 of which the first 64 rows are the
+// layer's outputs (the other 64 rows of D are never read; their A rows read
+// the operand stored next in shared memory).  dW3 and db3 stay on CUDA cores.
+constexpr uint32_t kTrainCols = 256;
+constexpr int kColW2 = 128, kN2 = 80;  // dW2 | db2 accumulator: 64 weights, the bias, zero padding
+constexpr int kColW1 = 208, kN1 = 32;  // dW1 | db1 accumulator: 16 weights, the bias, zero padding
+constexpr int kKR = kM / 8;            // core matrices along K = rows
+
 struct MlpTrainSmem {
     MlpSmem f;
     alignas(128) __nv_bfloat16 w2t[kH * kH];   // B of the data gradient: [n = in][k = out] = W2^T
-    alignas(128) __nv_bfloat16 dh2b[kM * kH];  // A of the data gradient: [m][k = out]
-    float h1[kM][kH + 1];         // FP32 copies for the weight-gradient reductions
-    float hd[kM][kH + 1];         // h2, then dh1
-    float dh2[kM][kH + 1];
-    float x[kM][kIn + 1];
+    alignas(128) __nv_bfloat16 dh2b[kM * kH];  // A of the data gradient: [m = row][k = out], dh2 / scale
+    alignas(128) __nv_bfloat16 a2[kH * kM];    // A of dW2: [m = out][k = row], dh2 / scale
+    alignas(128) __nv_bfloat16 b2[kN2 * kM];   // B of dW2: [n = in | 1 | 0][k = row], h1
+    alignas(128) __nv_bfloat16 a1[kH * kM];    // A of dW1: [m = out][k = row], dh1 / scale
+    alignas(128) __nv_bfloat16 b1[kN1 * kM];   // B of dW1: [n = in | 1 | 0][k = row], x
+    float h2[kM][kH + 1];                      // FP32 h2 for the output layer's gradient
     float dz[kM][kOut];
     float red[kM / 32];
 };
 
-static_assert(offsetof(MlpTrainSmem, w2t) % 128 == 0 && offsetof(MlpTrainSmem, dh2b) % 128 == 0,
+static_assert(offsetof(MlpTrainSmem, a2) + 2 * sizeof(__nv_bfloat16) * kH * kM <= offsetof(MlpTrainSmem, b2) +
+                  sizeof(__nv_bfloat16) * kN2 * kM,
+              "the M = 128 read of a2 stays inside the tile's shared memory");
+static_assert(offsetof(MlpTrainSmem, a1) + 2 * sizeof(__nv_bfloat16) * kH * kM <= sizeof(MlpTrainSmem),
+              "the M = 128 read of a1 stays inside the tile's shared memory");
+static_assert(offsetof(MlpTrainSmem, w2t) % 128 == 0 && offsetof(MlpTrainSmem, dh2b) % 128 == 0 &&
+                  offsetof(MlpTrainSmem, a2) % 128 == 0 && offsetof(MlpTrainSmem, b2) % 128 == 0 &&
+                  offsetof(MlpTrainSmem, a1) % 128 == 0 && offsetof(MlpTrainSmem, b1) % 128 == 0,
               "tensor-core operands must be 16-byte aligned");
 static_assert(sizeof(MlpTrainSmem) + 1024 <= 227 * 1024, "training tile exceeds shared memory");
+static_assert(kColW1 + kN1 <= (int)kTrainCols && kColW2 + kN2 <= kColW1, "TMEM columns");
 
 __global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat, const uint8_t *__restrict__ y_densify,
-                                                   const uint8_t *__restrict__ y_prune, long long n, long long ld, const float *__restrict__ w,
-                                                   float *__restrict__ grad, float *__restrict__ loss,
-                                                   int *__restrict__ status) {
+                                                   const uint8_t *__restrict__ y_prune, long long n, long long ld,
+                                                   const float *__restrict__ w, float *__restrict__ grad,
+                                                   float *__restrict__ loss, int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     MlpTrainSmem &s = *reinterpret_cast<MlpTrainSmem *>(smem_raw);
-    mlp_setup(s.f, w);
-    for (int i = threadIdx.x; i < kH * kH; i += blockDim.x) {
+    mlp_setup(s.f, w, kTrainCols);
+    const int t = threadIdx.x;
+    for (int i = t; i < kH * kH; i += blockDim.x) {
         const int o = i / kH, c = i % kH;  // W2[o][c] -> B[n = c][k = o]
         s.w2t[cm_off(c, o, kH / 8)] = __float2bfloat16_rn(w[kW2 + i]);
     }
+    // the constant columns of the weight sums' B operands: 1 (the bias), then zeros
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+    for (int c = kH; c < kN2; ++c) s.b2[cm_off(c, t, kKR)] = c == kH ? one : zero;
+    for (int c = kIn; c < kN1; ++c) s.b1[cm_off(c, t, kKR)] = c == kIn ? one : zero;
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
 
-    const int t = threadIdx.x;
     const float scale = 1.0f / (float)(n * kOut);
-    // per-thread shares of the weight gradient: W3 (k, c) = (t / 64, t % 64);
-    // W2 rows o = t / 2, columns 32 (t % 2) .. + 32; W1 rows o = t / 2, columns 8 (t % 2) .. + 8
-    float gw3 = 0.f, gb3 = 0.f, gw2[32], gw1[8], gb2 = 0.f, gb1 = 0.f;
-    #pragma unroll
-    for (int j = 0; j < 32; ++j) gw2[j] = 0.f;
-    #pragma unroll
-    for (int j = 0; j < 8; ++j) gw1[j] = 0.f;
+    const uint32_t tmem = s.f.tmem;
+    float gw3 = 0.f, gb3 = 0.f;  // W3 (k, c) = (t / 64, t % 64); b3 for t < 2
     double lsum = 0.0;
     uint32_t phase = 0;
-    bool ok = true;
+    bool ok = true, first = true;
     const long long tiles = ceil_div(n, (long long)kM);
     for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
         const long long row = tile * kM + t;
         const bool valid = row < n;
         float xr[kIn];
         stage_features(s.f, feat, ld, row, valid, xr);
+        #pragma unroll
+        for (int c = 0; c < kIn; ++c) s.b1[cm_off(c, t, kKR)] = __float2bfloat16_rn(xr[c]);
         float dz[kOut] = {0.f, 0.f};
         {
             float h1[kH], h2[kH];
             ok = mlp_tile_forward(s.f, phase, h1, h2);
             #pragma unroll
             for (int c = 0; c < kH; ++c) {
-                s.h1[t][c] = h1[c];
-                s.hd[t][c] = h2[c];
+                s.b2[cm_off(c, t, kKR)] = __float2bfloat16_rn(h1[c]);
+                s.h2[t][c] = h2[c];
             }
         }
         // head, BCE and dL/dh2 (FP32, this thread's row)
@@ -333,7 +358,7 @@ __global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat
             for (int k = 0; k < kOut; ++k) {
                 float z = s.f.b3[k];
                 #pragma unroll
-                for (int c = 0; c < kH; ++c) z += s.f.w3[k * kH + c] * s.hd[t][c];
+                for (int c = 0; c < kH; ++c) z += s.f.w3[k * kH + c] * s.h2[t][c];
                 const float p = 1.0f / (1.0f + expf(-z));
                 const float y = (k == 0 ? y_densify[row] : y_prune[row]) ? 1.0f : 0.0f;
                 // BCE from the logit: log(1 + e^z) - y z, stable for either sign of z
@@ -344,13 +369,10 @@ __global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat
         #pragma unroll 8
         for (int c = 0; c < kH; ++c) {
             const float d = dz[0] * s.f.w3[c] + dz[1] * s.f.w3[kH + c];
-            const float dh2 = s.hd[t][c] > 0.0f ? d : 0.0f;
-            s.dh2[t][c] = dh2;
-            // the tensor-core operand carries dh2 / scale (O(1) values) and the product is rescaled
-            s.dh2b[cm_off(t, c, kH / 8)] = __float2bfloat16_rn(dh2 / scale);
+            const __nv_bfloat16 db = __float2bfloat16_rn(s.h2[t][c] > 0.0f ? d / scale : 0.0f);
+            s.dh2b[cm_off(t, c, kH / 8)] = db;
+            s.a2[cm_off(c, t, kKR)] = db;
         }
-        #pragma unroll
-        for (int c = 0; c < kIn; ++c) s.x[t][c] = xr[c];
         s.dz[t][0] = dz[0];
         s.dz[t][1] = dz[1];
         asm volatile("fence.proxy.async.shared::cta;");
@@ -358,24 +380,23 @@ __global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat
         ok = __syncthreads_and(ok);
         if (ok && t == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // dh1 (before the ReLU mask) = dh2 W2 -> TMEM columns [0, 64)
+            // dh1 / scale (before the ReLU mask) = (dh2 / scale) W2 -> TMEM columns [0, 64)
             #pragma unroll
             for (int kb = 0; kb < kH / 16; ++kb)
-                mma_bf16(s.f.tmem, smem_desc(smem_addr(s.dh2b) + kb * 256, 128, 1024),
+                mma_bf16(tmem, smem_desc(smem_addr(s.dh2b) + kb * 256, 128, 1024),
                          smem_desc(smem_addr(s.w2t) + kb * 256, 128, 1024), idesc_bf16(kM, kH), kb > 0);
+            // dW2 | db2 += (dh2 / scale)^T [h1 | 1] over the tile's 128 rows
+            #pragma unroll
+            for (int kb = 0; kb < kM / 16; ++kb)
+                mma_bf16(tmem + kColW2, smem_desc(smem_addr(s.a2) + kb * 256, 128, kKR * 128),
+                         smem_desc(smem_addr(s.b2) + kb * 256, 128, kKR * 128), idesc_bf16(kM, kN2),
+                         !first || kb > 0);
             mma_commit(&s.f.mbar);
         }
-        // weight gradients of the head and of layer 2 while the tensor core works
+        // the output layer's gradient on CUDA cores while the tensor core works
         if (ok) {
             const int k3 = t / kH, c3 = t % kH;
-            const int o = t >> 1, half = t & 1;
-            for (int r = 0; r < kM; ++r) {
-                gw3 += s.dz[r][k3] * s.hd[r][c3];
-                const float d2 = s.dh2[r][o];
-                gb2 += (half == 0) ? d2 : 0.0f;
-                #pragma unroll
-                for (int j = 0; j < 32; ++j) gw2[j] += d2 * s.h1[r][32 * half + j];
-            }
+            for (int r = 0; r < kM; ++r) gw3 += s.dz[r][k3] * s.h2[r][c3];
             if (t < kOut)
                 for (int r = 0; r < kM; ++r) gb3 += s.dz[r][t];
         }
@@ -384,38 +405,59 @@ __global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat
             phase ^= 1u;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        __syncthreads();  // everyone done reading hd (h2) before it becomes dh1
         if (ok) {
             float d1[kH];
-            tmem_row64(s.f.tmem, 0, d1);
+            tmem_row64(tmem, 0, d1);
+            const __nv_bfloat16 *h1b = s.f.h1;
             #pragma unroll
-            for (int c = 0; c < kH; ++c) s.hd[t][c] = s.h1[t][c] > 0.0f ? d1[c] * scale : 0.0f;
-        }
-        ok = __syncthreads_and(ok);
-        if (ok) {
-            const int o = t >> 1, half = t & 1;
-            for (int r = 0; r < kM; ++r) {
-                const float d1 = s.hd[r][o];
-                gb1 += (half == 0) ? d1 : 0.0f;
-                #pragma unroll
-                for (int j = 0; j < 8; ++j) gw1[j] += d1 * s.x[r][8 * half + j];
+            for (int c = 0; c < kH; ++c) {
+                const bool on = __bfloat162float(h1b[cm_off(t, c, kH / 8)]) > 0.0f;
+                s.a1[cm_off(c, t, kKR)] = __float2bfloat16_rn(on ? d1[c] : 0.0f);
             }
         }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        ok = __syncthreads_and(ok);
+        if (ok && t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // dW1 | db1 += (dh1 / scale)^T [x | 1] over the tile's 128 rows
+            #pragma unroll
+            for (int kb = 0; kb < kM / 16; ++kb)
+                mma_bf16(tmem + kColW1, smem_desc(smem_addr(s.a1) + kb * 256, 128, kKR * 128),
+                         smem_desc(smem_addr(s.b1) + kb * 256, 128, kKR * 128), idesc_bf16(kM, kN1),
+                         !first || kb > 0);
+            mma_commit(&s.f.mbar);
+        }
+        if (ok) {
+            ok = mbar_wait(&s.f.mbar, phase);
+            phase ^= 1u;
+        }
+        first = false;
         asm volatile("tcgen05.fence::before_thread_sync;");
         ok = __syncthreads_and(ok);
     }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok && !first) {
+        // the weight sums: rows (TMEM lanes) 0-63 hold the layer's outputs (warps 0 and 1)
+        float v[kN2];
+        const uint32_t lane_base = (uint32_t)((t >> 5) * 32) << 16;
+        #pragma unroll
+        for (int c = 0; c < kN2; c += 16) tmem_ld16(tmem + lane_base + (uint32_t)(kColW2 + c), v + c);
+        float u[kN1];
+        #pragma unroll
+        for (int c = 0; c < kN1; c += 16) tmem_ld16(tmem + lane_base + (uint32_t)(kColW1 + c), u + c);
+        if (t < kH) {
+            #pragma unroll
+            for (int c = 0; c < kH; ++c) atomicAdd(&grad[kW2 + t * kH + c], v[c] * scale);
+            atomicAdd(&grad[kB2 + t], v[kH] * scale);
+            #pragma unroll
+            for (int c = 0; c < kIn; ++c) atomicAdd(&grad[kW1 + t * kIn + c], u[c] * scale);
+            atomicAdd(&grad[kB1 + t], u[kIn] * scale);
+        }
+    }
     if (ok) {
-        const int o = t >> 1, half = t & 1;
         atomicAdd(&grad[kW3 + t], gw3);
         if (t < kOut) atomicAdd(&grad[kB3 + t], gb3);
-        #pragma unroll
-        for (int j = 0; j < 32; ++j) atomicAdd(&grad[kW2 + o * kH + 32 * half + j], gw2[j]);
-        #pragma unroll
-        for (int j = 0; j < 8; ++j) atomicAdd(&grad[kW1 + o * kIn + 8 * half + j], gw1[j]);
-        if (half == 0) {
-            atomicAdd(&grad[kB2 + o], gb2);
-            atomicAdd(&grad[kB1 + o], gb1);
-        }
         // BCE partial: warp sums, then one atomic per CTA
         float lv = (float)lsum;
         #pragma unroll
@@ -428,7 +470,7 @@ __global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat
         for (int i = 0; i < kM / 32; ++i) a += s.red[i];
         atomicAdd(loss, a * scale);
     }
-    mlp_finish(s.f, ok, phase, status);
+    mlp_finish(s.f, ok, phase, status, kTrainCols);
 }
 
 // Per-Gaussian inputs of the predictor (planes of ld), from the parameters,

@@ -9,8 +9,11 @@
 // tcgen05.mma.kind::f16 with BF16 operands in shared memory (K-major, no
 // swizzle: 8x8 core matrices of 128 bytes, leading offset = the next core
 // matrix along K, stride offset = the next 8-row group) and FP32 accumulators
-// in TMEM, read back with tcgen05.ld.  The 64 -> 2 head, the BCE gradient and
-// the weight-gradient reductions over the tile run in FP32 on CUDA cores.
+// in TMEM, read back with tcgen05.ld.  The hidden layers' weight gradients
+// are tcgen05 contractions over the tile's rows whose operands are the same
+// tiles read MN-major (the transpose bits of the instruction descriptor).
+// The 64 -> 2 head, the BCE gradient and the output layer's weight gradient
+// run in FP32 on CUDA cores.
 // Every mbarrier wait is bounded; on a timeout the kernel flags the status
 // word, stops issuing, and still frees its TMEM.
 #include <algorithm>
@@ -48,10 +51,23 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | ((uint64_t)1 << 46);
 }
 
+// The same for an MN-major no-swizzle operand (core matrix = 8 K-rows of 8
+// contiguous M/N elements): the leading offset is the stride between core
+// matrices along K, the stride offset the one between 8-element groups along
+// M/N.
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t saddr, uint32_t k_stride, uint32_t mn_stride) {
+    return smem_desc(saddr, k_stride, mn_stride);
+}
+
 // Instruction descriptor, kind::f16: FP32 accumulate (bit 4), BF16 A (bit 7)
 // and B (bit 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// Both operands MN-major (transpose A at bit 15, transpose B at bit 16).
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(uint32_t M, uint32_t N) {
+    return idesc_bf16(M, N) | (1u << 15) | (1u << 16);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, bool acc) {
@@ -105,15 +121,21 @@ __device__ __forceinline__ void store_row8(__nv_bfloat16 *base, int row, int c0,
     *reinterpret_cast<uint4 *>(base + cm_off(row, c0, kgroups)) = u;
 }
 
-struct MlpSmem {
-    alignas(128) __nv_bfloat16 w1[kH * kIn];   // B of layer 1: [n = out][k = in]
-    alignas(128) __nv_bfloat16 w2[kH * kH];    // B of layer 2: [n = out][k = in]
-    alignas(128) __nv_bfloat16 x[kM * kIn];    // A of layer 1: [m][k]
-    alignas(128) __nv_bfloat16 h1[kM * kH];    // A of layer 2: [m][k]
+// KX and KH: core matrices per 8-row group of x and h1 (2 and 8 for the
+// forward; wider in training, where the extra columns hold the constant 1 of
+// the bias gradient and zero padding).
+template <int KX, int KH>
+struct MlpSmemT {
+    static constexpr int kx = KX, kh = KH;
+    alignas(128) __nv_bfloat16 w1[kH * kIn];    // B of layer 1: [n = out][k = in]
+    alignas(128) __nv_bfloat16 w2[kH * kH];     // B of layer 2: [n = out][k = in]
+    alignas(128) __nv_bfloat16 x[kM * 8 * KX];  // A of layer 1: [m = row][k = in]
+    alignas(128) __nv_bfloat16 h1[kM * 8 * KH]; // A of layer 2: [m = row][k = in]
     float b1[kH], b2[kH], w3[kOut * kH], b3[kOut];
     uint64_t mbar;
     uint32_t tmem;
 };
+using MlpSmem = MlpSmemT<kIn / 8, kH / 8>;
 
 __device__ void tmem_alloc(uint32_t *slot, uint32_t cols) {
     if ((threadIdx.x >> 5) == 0) {
@@ -132,7 +154,8 @@ __device__ void tmem_free(uint32_t tmem, uint32_t cols) {
 
 // Loads the weights into shared memory (BF16 operands, FP32 rest), allocates
 // TMEM and initialises the mbarrier.
-__device__ void mlp_setup(MlpSmem &s, const float *__restrict__ w, uint32_t cols = kTmemCols) {
+template <class S>
+__device__ void mlp_setup(S &s, const float *__restrict__ w, uint32_t cols = kTmemCols) {
     for (int i = threadIdx.x; i < kH * kIn; i += blockDim.x) {
         const int o = i / kIn, c = i % kIn;
         s.w1[cm_off(o, c, kIn / 8)] = __float2bfloat16_rn(w[kW1 + i]);
@@ -157,7 +180,8 @@ __device__ void mlp_setup(MlpSmem &s, const float *__restrict__ w, uint32_t cols
 
 // After a timed-out wait no further MMA is issued; the last one committed
 // (parity phase ^ 1) gets one more bounded wait before its TMEM is freed.
-__device__ void mlp_finish(MlpSmem &s, bool ok, uint32_t phase, int *status, uint32_t cols = kTmemCols) {
+template <class S>
+__device__ void mlp_finish(S &s, bool ok, uint32_t phase, int *status, uint32_t cols = kTmemCols) {
     if (!ok) {
         mbar_wait(&s.mbar, phase ^ 1u);
         if (threadIdx.x == 0 && status) atomicOr(status, 1 << GS_ERR_TIMEOUT);
@@ -168,14 +192,15 @@ __device__ void mlp_finish(MlpSmem &s, bool ok, uint32_t phase, int *status, uin
 // One tile's forward through layer 2.  The thread's features are already in
 // s.x; on return h2 (64 FP32, after ReLU) and h1 (64 FP32, after ReLU) hold
 // the thread's row.  Returns false on a wait timeout.
-__device__ bool mlp_tile_forward(MlpSmem &s, uint32_t &phase, float *h1, float *h2) {
+template <class S>
+__device__ bool mlp_tile_forward(S &s, uint32_t &phase, float *h1, float *h2) {
     const uint32_t tmem = s.tmem;
     asm volatile("fence.proxy.async.shared::cta;");  // s.x written by threads, read by the tensor core
     __syncthreads();
     if (threadIdx.x == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         // layer 1: D1[128 x 64] = X[128 x 16] W1^T, one K = 16 step
-        mma_bf16(tmem, smem_desc(smem_addr(s.x), 128, 256), smem_desc(smem_addr(s.w1), 128, 256),
+        mma_bf16(tmem, smem_desc(smem_addr(s.x), 128, S::kx * 128), smem_desc(smem_addr(s.w1), 128, 256),
                  idesc_bf16(kM, kH), false);
         mma_commit(&s.mbar);
     }
@@ -187,7 +212,7 @@ __device__ bool mlp_tile_forward(MlpSmem &s, uint32_t &phase, float *h1, float *
         #pragma unroll
         for (int c = 0; c < kH; ++c) h1[c] = fmaxf(h1[c] + s.b1[c], 0.0f);
         #pragma unroll
-        for (int c0 = 0; c0 < kH; c0 += 8) store_row8(s.h1, threadIdx.x, c0, kH / 8, h1 + c0);
+        for (int c0 = 0; c0 < kH; c0 += 8) store_row8(s.h1, threadIdx.x, c0, S::kh, h1 + c0);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -197,7 +222,7 @@ __device__ bool mlp_tile_forward(MlpSmem &s, uint32_t &phase, float *h1, float *
         // layer 2: D2[128 x 64] = H1[128 x 64] W2^T, four K = 16 steps of two core matrices each
         #pragma unroll
         for (int kb = 0; kb < kH / 16; ++kb)
-            mma_bf16(tmem + 64, smem_desc(smem_addr(s.h1) + kb * 256, 128, 1024),
+            mma_bf16(tmem + 64, smem_desc(smem_addr(s.h1) + kb * 256, 128, S::kh * 128),
                      smem_desc(smem_addr(s.w2) + kb * 256, 128, 1024), idesc_bf16(kM, kH), kb > 0);
         mma_commit(&s.mbar);
     }
@@ -212,17 +237,6 @@ __device__ bool mlp_tile_forward(MlpSmem &s, uint32_t &phase, float *h1, float *
         for (int c = 0; c < kH; ++c) h2[c] = fmaxf(h2[c] + s.b2[c], 0.0f);
     }
     return ok;
-}
-
-__device__ __forceinline__ void stage_features(MlpSmem &s, const float *__restrict__ feat, long long ld, long long row,
-                                               bool valid, float *x) {
-    #pragma unroll
-    for (int c = 0; c < kIn; ++c) {
-        const float v = valid ? feat[c * ld + row] : 0.0f;
-        const __nv_bfloat16 b = __float2bfloat16_rn(v);
-        s.x[cm_off(threadIdx.x, c, kIn / 8)] = b;
-        if (x) x[c] = __bfloat162float(b);
-    }
 }
 
 __global__ void __launch_bounds__(kM, 4) k_mlp_forward(const float *__restrict__ feat, long long n, long long ld,
@@ -274,45 +288,52 @@ __global__ void __launch_bounds__(kM, 4) k_mlp_forward(const float *__restrict__
 // accumulators in TMEM:
 //   dh1 (before the ReLU mask) = dh2 W2                          [128 x 64],
 //   dW2 | db2 += dh2^T [h1 | 1]   over the tile's rows (K = 128)  [64 x 80],
-//   dW1 | db1 += dh1^T [x | 1]    over the tile's rows            [64 x 32];
-// dh2 and dh1 enter as dL/dh / scale (O(1) values), the sums are rescaled at
-// the end.  The weight sums use M = 128 of which the first 64 rows are the
-// layer's outputs (the other 64 rows of D are never read; their A rows read
-// the operand stored next in shared memory).  dW3 and db3 stay on CUDA cores.
+//   dW1 | db1 += dh1^T [x | 1]    over the tile's rows            [64 x 32].
+// dh2 and dh1 are stored once, [row][out] (A of the data gradient K-major, A
+// of the weight sums MN-major); h1 and x are the forward's own operands,
+// stored with a constant-1 column (the bias) and zero padding and read
+// MN-major as the weight sums' B.  dh2 and dh1 enter as dL/dh / scale (O(1)
+// values), the sums are rescaled at the end.  The weight sums use M = 128 of
+// which the first 64 rows are the layer's outputs (rows 64-127 of D are never
+// read; their A rows read whatever shared memory follows).  dW3 and db3 stay
+// in FP32 on CUDA cores, from transposed copies of h2 and dL/dz.
 constexpr uint32_t kTrainCols = 256;
 constexpr int kColW2 = 128, kN2 = 80;  // dW2 | db2 accumulator: 64 weights, the bias, zero padding
 constexpr int kColW1 = 208, kN1 = 32;  // dW1 | db1 accumulator: 16 weights, the bias, zero padding
-constexpr int kKR = kM / 8;            // core matrices along K = rows
+constexpr int kLdH2 = kM + 4;          // padded row of the transposed h2 (16-byte aligned, conflict-free)
+using MlpTrainF = MlpSmemT<kN1 / 8, kN2 / 8>;
 
 struct MlpTrainSmem {
-    MlpSmem f;
-    alignas(128) __nv_bfloat16 w2t[kH * kH];   // B of the data gradient: [n = in][k = out] = W2^T
-    alignas(128) __nv_bfloat16 dh2b[kM * kH];  // A of the data gradient: [m = row][k = out], dh2 / scale
-    alignas(128) __nv_bfloat16 a2[kH * kM];    // A of dW2: [m = out][k = row], dh2 / scale
-    alignas(128) __nv_bfloat16 b2[kN2 * kM];   // B of dW2: [n = in | 1 | 0][k = row], h1
-    alignas(128) __nv_bfloat16 a1[kH * kM];    // A of dW1: [m = out][k = row], dh1 / scale
-    alignas(128) __nv_bfloat16 b1[kN1 * kM];   // B of dW1: [n = in | 1 | 0][k = row], x
-    float h2[kM][kH + 1];                      // FP32 h2 for the output layer's gradient
-    float dz[kM][kOut];
+    MlpTrainF f;
+    alignas(128) __nv_bfloat16 w2t[kH * kH];  // B of the data gradient: [n = in][k = out] = W2^T
+    alignas(128) __nv_bfloat16 dh[kM * kH];   // [row][out]: dh2 / scale, then dh1 / scale
+    alignas(16) float h2t[kH][kLdH2];         // FP32 h2, [out][row]
+    alignas(16) float dzt[kOut][kM];          // dL/dz, [output][row]
     float red[kM / 32];
 };
 
-static_assert(offsetof(MlpTrainSmem, a2) + 2 * sizeof(__nv_bfloat16) * kH * kM <= offsetof(MlpTrainSmem, b2) +
-                  sizeof(__nv_bfloat16) * kN2 * kM,
-              "the M = 128 read of a2 stays inside the tile's shared memory");
-static_assert(offsetof(MlpTrainSmem, a1) + 2 * sizeof(__nv_bfloat16) * kH * kM <= sizeof(MlpTrainSmem),
-              "the M = 128 read of a1 stays inside the tile's shared memory");
-static_assert(offsetof(MlpTrainSmem, w2t) % 128 == 0 && offsetof(MlpTrainSmem, dh2b) % 128 == 0 &&
-                  offsetof(MlpTrainSmem, a2) % 128 == 0 && offsetof(MlpTrainSmem, b2) % 128 == 0 &&
-                  offsetof(MlpTrainSmem, a1) % 128 == 0 && offsetof(MlpTrainSmem, b1) % 128 == 0,
+// Byte strides of the MN-major reads: dh as [m = out][k = row] has 8-out groups
+// 128 B apart and 8-row groups kH / 8 * 128 B apart; h1 and x as [n = in][k = row]
+// likewise with kN2 / 8 and kN1 / 8 groups per row group.
+constexpr uint32_t kDhK = kH / 8 * 128, kH1K = kN2 / 8 * 128, kXK = kN1 / 8 * 128;
+// Every descriptor read stays inside the CTA's shared memory whichever of the
+// two strides the hardware takes as the K one: the largest byte reached from
+// an operand's start is (last K step) + 15 or 9 or 3 groups x the larger stride
+// + one group x the other + 127.
+static_assert(offsetof(MlpTrainSmem, dh) + 7 * 2 * kDhK + 15 * kDhK + 128 + 127 < sizeof(MlpTrainSmem), "dh read");
+static_assert(offsetof(MlpTrainSmem, f) + offsetof(MlpTrainF, h1) + 7 * 2 * kH1K + 9 * kH1K + 128 + 127 <
+                  sizeof(MlpTrainSmem), "h1 read");
+static_assert(offsetof(MlpTrainF, x) + 7 * 2 * kXK + 3 * kXK + 128 + 127 < sizeof(MlpTrainSmem), "x read");
+static_assert(offsetof(MlpTrainSmem, w2t) % 128 == 0 && offsetof(MlpTrainSmem, dh) % 128 == 0 &&
+                  offsetof(MlpTrainF, x) % 128 == 0 && offsetof(MlpTrainF, h1) % 128 == 0,
               "tensor-core operands must be 16-byte aligned");
-static_assert(sizeof(MlpTrainSmem) + 1024 <= 227 * 1024, "training tile exceeds shared memory");
+static_assert(2 * (sizeof(MlpTrainSmem) + 1024) <= 228 * 1024, "two training CTAs per SM");
 static_assert(kColW1 + kN1 <= (int)kTrainCols && kColW2 + kN2 <= kColW1, "TMEM columns");
 
-__global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat, const uint8_t *__restrict__ y_densify,
-                                                   const uint8_t *__restrict__ y_prune, long long n, long long ld,
-                                                   const float *__restrict__ w, float *__restrict__ grad,
-                                                   float *__restrict__ loss, int *__restrict__ status) {
+__global__ void __launch_bounds__(kM, 2) k_mlp_train(const float *__restrict__ feat, const uint8_t *__restrict__ y_densify,
+                                                      const uint8_t *__restrict__ y_prune, long long n, long long ld,
+                                                      const float *__restrict__ w, float *__restrict__ grad,
+                                                      float *__restrict__ loss, int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     MlpTrainSmem &s = *reinterpret_cast<MlpTrainSmem *>(smem_raw);
     mlp_setup(s.f, w, kTrainCols);
@@ -321,10 +342,14 @@ __global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat
         const int o = i / kH, c = i % kH;  // W2[o][c] -> B[n = c][k = o]
         s.w2t[cm_off(c, o, kH / 8)] = __float2bfloat16_rn(w[kW2 + i]);
     }
-    // the constant columns of the weight sums' B operands: 1 (the bias), then zeros
-    const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
-    for (int c = kH; c < kN2; ++c) s.b2[cm_off(c, t, kKR)] = c == kH ? one : zero;
-    for (int c = kIn; c < kN1; ++c) s.b1[cm_off(c, t, kKR)] = c == kIn ? one : zero;
+    {
+        // the constant columns of x and h1: 1 (the bias gradient), then zeros
+        const float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {};
+        store_row8(s.f.x, t, kIn, kN1 / 8, one);
+        store_row8(s.f.x, t, kIn + 8, kN1 / 8, zero);
+        store_row8(s.f.h1, t, kH, kN2 / 8, one);
+        store_row8(s.f.h1, t, kH + 8, kN2 / 8, zero);
+    }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
 
@@ -335,46 +360,56 @@ __global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat
     uint32_t phase = 0;
     bool ok = true, first = true;
     const long long tiles = ceil_div(n, (long long)kM);
+    // the next tile's inputs are loaded into registers while this tile's MMAs run
+    float xn[kIn];
+    auto load = [&](long long tl) {
+        const long long row = tl * kM + t;
+        #pragma unroll
+        for (int c = 0; c < kIn; ++c) xn[c] = row < n ? feat[c * ld + row] : 0.0f;
+    };
+    if ((long long)blockIdx.x < tiles) load(blockIdx.x);
     for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
         const long long row = tile * kM + t;
         const bool valid = row < n;
-        float xr[kIn];
-        stage_features(s.f, feat, ld, row, valid, xr);
-        #pragma unroll
-        for (int c = 0; c < kIn; ++c) s.b1[cm_off(c, t, kKR)] = __float2bfloat16_rn(xr[c]);
-        float dz[kOut] = {0.f, 0.f};
+        const float yd = valid && y_densify[row] ? 1.0f : 0.0f, yp = valid && y_prune[row] ? 1.0f : 0.0f;
+        store_row8(s.f.x, t, 0, kN1 / 8, xn);
+        store_row8(s.f.x, t, 8, kN1 / 8, xn + 8);
+        if (tile + gridDim.x < tiles) load(tile + gridDim.x);
+        float h2[kH];
         {
-            float h1[kH], h2[kH];
+            float h1[kH];
             ok = mlp_tile_forward(s.f, phase, h1, h2);
-            #pragma unroll
-            for (int c = 0; c < kH; ++c) {
-                s.b2[cm_off(c, t, kKR)] = __float2bfloat16_rn(h1[c]);
-                s.h2[t][c] = h2[c];
-            }
         }
-        // head, BCE and dL/dh2 (FP32, this thread's row)
+        // head, BCE and (p - y) (FP32, this thread's row)
+        float r[kOut] = {0.f, 0.f};
         if (ok && valid) {
             #pragma unroll
             for (int k = 0; k < kOut; ++k) {
                 float z = s.f.b3[k];
                 #pragma unroll
-                for (int c = 0; c < kH; ++c) z += s.f.w3[k * kH + c] * s.h2[t][c];
+                for (int c = 0; c < kH; ++c) z += s.f.w3[k * kH + c] * h2[c];
                 const float p = 1.0f / (1.0f + expf(-z));
-                const float y = (k == 0 ? y_densify[row] : y_prune[row]) ? 1.0f : 0.0f;
+                const float y = k == 0 ? yd : yp;
                 // BCE from the logit: log(1 + e^z) - y z, stable for either sign of z
                 lsum += (double)(fmaxf(z, 0.0f) - y * z + log1pf(expf(-fabsf(z))));
-                dz[k] = (p - y) * scale;
+                r[k] = p - y;
             }
         }
-        #pragma unroll 8
-        for (int c = 0; c < kH; ++c) {
-            const float d = dz[0] * s.f.w3[c] + dz[1] * s.f.w3[kH + c];
-            const __nv_bfloat16 db = __float2bfloat16_rn(s.h2[t][c] > 0.0f ? d / scale : 0.0f);
-            s.dh2b[cm_off(t, c, kH / 8)] = db;
-            s.a2[cm_off(c, t, kKR)] = db;
+        // dL/dh2 / scale = [h2 > 0] (p - y) W3, rounded to BF16, [row][out]
+        #pragma unroll
+        for (int c0 = 0; c0 < kH; c0 += 8) {
+            float d[8];
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + j;
+                d[j] = h2[c] > 0.0f ? r[0] * s.f.w3[c] + r[1] * s.f.w3[kH + c] : 0.0f;
+            }
+            store_row8(s.dh, t, c0, kH / 8, d);
         }
-        s.dz[t][0] = dz[0];
-        s.dz[t][1] = dz[1];
+        #pragma unroll
+        for (int c = 0; c < kH; ++c) s.h2t[c][t] = h2[c];
+        s.dzt[0][t] = r[0] * scale;
+        s.dzt[1][t] = r[1] * scale;
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         ok = __syncthreads_and(ok);
@@ -383,22 +418,33 @@ __global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat
             // dh1 / scale (before the ReLU mask) = (dh2 / scale) W2 -> TMEM columns [0, 64)
             #pragma unroll
             for (int kb = 0; kb < kH / 16; ++kb)
-                mma_bf16(tmem, smem_desc(smem_addr(s.dh2b) + kb * 256, 128, 1024),
+                mma_bf16(tmem, smem_desc(smem_addr(s.dh) + kb * 256, 128, kDhK),
                          smem_desc(smem_addr(s.w2t) + kb * 256, 128, 1024), idesc_bf16(kM, kH), kb > 0);
-            // dW2 | db2 += (dh2 / scale)^T [h1 | 1] over the tile's 128 rows
+            // dW2 | db2 += (dh2 / scale)^T [h1 | 1] over the tile's rows, 16 rows per step
             #pragma unroll
             for (int kb = 0; kb < kM / 16; ++kb)
-                mma_bf16(tmem + kColW2, smem_desc(smem_addr(s.a2) + kb * 256, 128, kKR * 128),
-                         smem_desc(smem_addr(s.b2) + kb * 256, 128, kKR * 128), idesc_bf16(kM, kN2),
+                mma_bf16(tmem + kColW2, smem_desc_mn(smem_addr(s.dh) + kb * 2 * kDhK, kDhK, 128),
+                         smem_desc_mn(smem_addr(s.f.h1) + kb * 2 * kH1K, kH1K, 128), idesc_bf16_mn(kM, kN2),
                          !first || kb > 0);
             mma_commit(&s.f.mbar);
         }
         // the output layer's gradient on CUDA cores while the tensor core works
         if (ok) {
-            const int k3 = t / kH, c3 = t % kH;
-            for (int r = 0; r < kM; ++r) gw3 += s.dz[r][k3] * s.h2[r][c3];
-            if (t < kOut)
-                for (int r = 0; r < kM; ++r) gb3 += s.dz[r][t];
+            const float4 *hz = reinterpret_cast<const float4 *>(s.h2t[t % kH]);
+            const float4 *dq = reinterpret_cast<const float4 *>(s.dzt[t / kH]);
+            #pragma unroll 8
+            for (int q = 0; q < kM / 4; ++q) {
+                const float4 a = dq[q], b = hz[q];
+                gw3 += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+            }
+            if (t < kOut) {
+                const float4 *dz = reinterpret_cast<const float4 *>(s.dzt[t]);
+                #pragma unroll 8
+                for (int q = 0; q < kM / 4; ++q) {
+                    const float4 a = dz[q];
+                    gb3 += (a.x + a.y) + (a.z + a.w);
+                }
+            }
         }
         if (ok) {
             ok = mbar_wait(&s.f.mbar, phase);
@@ -406,13 +452,20 @@ __global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (ok) {
+            // dh1 / scale = [h1 > 0] (dh1 before the mask), over dh2 (its MMAs are done)
             float d1[kH];
             tmem_row64(tmem, 0, d1);
-            const __nv_bfloat16 *h1b = s.f.h1;
             #pragma unroll
-            for (int c = 0; c < kH; ++c) {
-                const bool on = __bfloat162float(h1b[cm_off(t, c, kH / 8)]) > 0.0f;
-                s.a1[cm_off(c, t, kKR)] = __float2bfloat16_rn(on ? d1[c] : 0.0f);
+            for (int c0 = 0; c0 < kH; c0 += 8) {
+                const uint4 hv = *reinterpret_cast<const uint4 *>(s.f.h1 + cm_off(t, c0, kN2 / 8));
+                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+                #pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    // h1 >= 0 after the ReLU: a BF16 with any magnitude bit set is positive
+                    const bool on = ((hw[j >> 1] >> (16 * (j & 1))) & 0x7fffu) != 0u;
+                    d1[c0 + j] = on ? d1[c0 + j] : 0.0f;
+                }
+                store_row8(s.dh, t, c0, kH / 8, d1 + c0);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;");
@@ -420,11 +473,11 @@ __global__ void __launch_bounds__(kM) k_mlp_train(const float *__restrict__ feat
         ok = __syncthreads_and(ok);
         if (ok && t == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // dW1 | db1 += (dh1 / scale)^T [x | 1] over the tile's 128 rows
+            // dW1 | db1 += (dh1 / scale)^T [x | 1] over the tile's rows
             #pragma unroll
             for (int kb = 0; kb < kM / 16; ++kb)
-                mma_bf16(tmem + kColW1, smem_desc(smem_addr(s.a1) + kb * 256, 128, kKR * 128),
-                         smem_desc(smem_addr(s.b1) + kb * 256, 128, kKR * 128), idesc_bf16(kM, kN1),
+                mma_bf16(tmem + kColW1, smem_desc_mn(smem_addr(s.dh) + kb * 2 * kDhK, kDhK, 128),
+                         smem_desc_mn(smem_addr(s.f.x) + kb * 2 * kXK, kXK, 128), idesc_bf16_mn(kM, kN1),
                          !first || kb > 0);
             mma_commit(&s.f.mbar);
         }
@@ -552,7 +605,8 @@ cudaError_t launch_mlp_train(const float *feat, const uint8_t *y_densify, const 
     cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * kNW, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(float), s);
     if (e != cudaSuccess) return e;
-    const long long grid = std::min<long long>(ceil_div(n, (long long)kM), (long long)sm_count());
+    // two CTAs per SM (shared memory and TMEM: 2 x 256 columns)
+    const long long grid = std::min<long long>(ceil_div(n, (long long)kM), 2ll * sm_count());
     k_mlp_train<<<(unsigned)grid, kM, smem, s>>>(feat, y_densify, y_prune, n, ld, w, grad, loss, status);
     return cudaGetLastError();
 }

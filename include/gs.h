@@ -414,10 +414,11 @@ gs_status gs_densify_prune(const gs_params *src, const gs_params *src_m, const g
  * judge of its error).  16 inputs -> 64 -> 64 (ReLU) -> 2 logits (sigmoid):
  * output 0 = densify, 1 = prune.  Weights: one FP32 array of GS_MLP_WEIGHTS
  * floats, W1[64][16] at 0, b1[64] at 1024, W2[64][64] at 1088, b2[64] at
- * 5184, W3[2][64] at 5248, b3[2] at 5376.  Layers 1 and 2 (and the data
- * gradient through layer 2) run on the tensor cores with BF16 inputs,
- * weights and hidden activations and FP32 accumulation; biases, the output
- * layer and every gradient reduction stay FP32.
+ * 5184, W3[2][64] at 5248, b3[2] at 5376.  Layers 1 and 2, the data
+ * gradient through layer 2 and the hidden layers' weight and bias gradients
+ * run on the tensor cores with BF16 operands (inputs, weights, hidden
+ * activations, dL/dh divided by 2n) and FP32 accumulation; biases, the
+ * output layer and its gradient stay FP32.
  */
 #define GS_MLP_INPUTS 16
 #define GS_MLP_HIDDEN 64

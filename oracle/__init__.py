@@ -102,6 +102,11 @@ def lib():
         L.or_mlp_features.argtypes = [i64, vp, vp, vp, vp, vp, i32, vp, vp]
         L.or_densify_prune.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, d, d, i64, vp, vp, vp]
         L.or_densify_prune.restype = i64
+        L.or_init_saliency.argtypes = [i32, i32, vp, vp, d, d, vp, vp]
+        L.or_init_probability.argtypes = [i32, i32, vp, vp, vp, vp, d, d, d, vp]
+        L.or_init_select.argtypes = [i32, i32, vp, vp, vp, C.POINTER(_Camera), d, i32, vp, vp, i64, vp, i64,
+                                     vp, vp, vp, vp, vp, vp, d, d]
+        L.or_init_select.restype = i64
     return _lib
 
 
@@ -378,6 +383,62 @@ def densify_prune(P, densify, prune, noise, split_log_scale, split_factor=1.6, m
                                   float(split_log_scale), float(split_factor), cap, _ptr(Po), _ptr(mo), _ptr(vo))
     k = min(need, cap)
     return Po[:k], mo[:k], vo[:k], need
+
+
+# --------------------------------------------------------------------------
+# Probabilistic initialisation (Sec. 3.3.1, Supp. B; readings R19-R24)
+# --------------------------------------------------------------------------
+
+@dataclass
+class InitCfg:
+    sigma1: float = 1.0
+    sigma2: float = 1.6
+    lam: float = 0.9
+    near_z: float = 0.2
+    voxel: tuple = (0.1, 0.25, 1.0, 5.0, 25.0)
+    max_dist: tuple = (10.0, 25.0, 100.0, 500.0, float("inf"))
+
+
+def init_saliency(img, depth, sigma1=1.0, sigma2=1.6):
+    """DoG [H][W] of the channel mean of img [3][H][W] and ||grad depth|| [H][W]."""
+    img, depth = _f64(img), _f64(depth)
+    H, W = depth.shape
+    dog, grad = np.zeros((H, W)), np.zeros((H, W))
+    lib().or_init_saliency(H, W, _ptr(img), _ptr(depth), float(sigma1), float(sigma2), _ptr(dog), _ptr(grad))
+    return dog, grad
+
+
+def init_probability(img, depth, img_r=None, depth_r=None, cfg: InitCfg = InitCfg()):
+    """P (or P_kf = max(P - P^, 0) when the rendered pair is given), [H][W]."""
+    img, depth = _f64(img), _f64(depth)
+    H, W = depth.shape
+    img_r = None if img_r is None else _f64(img_r)
+    depth_r = None if depth_r is None else _f64(depth_r)
+    prob = np.zeros((H, W))
+    lib().or_init_probability(H, W, _ptr(img), _ptr(depth), _ptr(img_r), _ptr(depth_r), float(cfg.sigma1),
+                              float(cfg.sigma2), float(cfg.lam), _ptr(prob))
+    return prob
+
+
+def init_select(prob, uniform, depth, cam, cfg: InitCfg = InitCfg(), old_keys=None, cap=None, tol=1e-5,
+                tol_rel=1e-5):
+    """New anchors of a keyframe: dict with keys [k][4] (level, ix, iy, iz), pos [k][3], level, pixel,
+    n_new (all new voxels, k = min(n_new, cap)), selected and uncertain [H][W] masks."""
+    prob, uniform, depth = _f64(prob), _f64(uniform), _f64(depth)
+    H, W = prob.shape
+    old = np.zeros((0, 4), np.int64) if old_keys is None else np.ascontiguousarray(old_keys, np.int64)
+    cap = H * W if cap is None else int(cap)
+    keys, pos = np.zeros((max(cap, 1), 4), np.int64), np.zeros((max(cap, 1), 3))
+    level, pixel = np.zeros(max(cap, 1), np.int32), np.zeros(max(cap, 1), np.int32)
+    sel, unc = np.zeros((H, W), np.uint8), np.zeros((H, W), np.uint8)
+    m = len(cfg.voxel)
+    n = lib().or_init_select(H, W, _ptr(prob), _ptr(uniform), _ptr(depth), C.byref(_cam(cam)), float(cfg.near_z),
+                             m, _ptr(_f64(cfg.voxel)), _ptr(_f64(cfg.max_dist)), old.shape[0], _ptr(old), cap,
+                             _ptr(keys), _ptr(pos), _ptr(level), _ptr(pixel), _ptr(sel), _ptr(unc), float(tol),
+                             float(tol_rel))
+    k = min(n, cap)
+    return dict(keys=keys[:k], pos=pos[:k], level=level[:k], pixel=pixel[:k], n_new=n, selected=sel,
+                uncertain=unc)
 
 
 # --------------------------------------------------------------------------

@@ -39,6 +39,24 @@
  *   R12 ||.||_1 in M_v sums the three colour channels.
  *   R13 S_p is 0 for Gaussians with empty footprint in the chunk and for a
  *       chunk whose active scores are all equal.
+ * Probabilistic initialisation (Sec. 3.3.1: DoG, normalised depth gradient,
+ * P, P_kf, 3x3 NMS, voxel quantisation; Supp. B: dynamic map expansion
+ * through a voxel hash; Supp. F: lambda = 0.9, m = 5 levels) reads:
+ *   R19 DoG on Y = (R + G + B) / 3; G_s sampled on integer offsets within
+ *       ceil(3 s), normalised to sum 1; replicated borders; s1 = 1, s2 = 1.6.
+ *   R20 ||grad D|| by central differences in depth units per pixel with
+ *       replicated borders; min-max over the keyframe, a flat map gives 0.
+ *   R21 P^ is the same formula applied to the rendered I^, D^ (own
+ *       min-max); the first keyframe has P^ = 0.
+ *   R22 selection: (P_kf, -raster index) is the lexicographic maximum of
+ *       the 3x3 window, P_kf > 0, a caller's uniform draw U < P_kf (the
+ *       paper samples from P_kf and names no sampler), depth > near (0.2).
+ *   R23 level = first l with ||x_c|| < max_dist_l (10, 25, 100, 500, inf m);
+ *       voxel sizes (0.1, 0.25, 1, 5, 25), the printed third size 0.1 read
+ *       as 1 (the printed sequence is otherwise increasing).
+ *   R24 voxel idx = floor(x / eps_l), anchor p = idx eps_l (the paper's
+ *       formula); one anchor per (l, idx); new anchors numbered in raster
+ *       order of the first pixel reaching their voxel.
  * Parity pins for each function are in the tests; every function below is
  * pinned (closed forms, brute force, library routines, finite differences).
  */
@@ -1097,4 +1115,167 @@ int64_t or_densify_prune(int64_t n, int32_t K_row, const double *P, const double
         }
     }
     return o;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Probabilistic initialisation (Sec. 3.3.1, Supp. B)                        */
+/* ------------------------------------------------------------------------ */
+
+static double px_at(const double *a, int H, int W, int y, int x) {
+    return a[(int64_t)clampi(y, 0, H - 1) * W + clampi(x, 0, W - 1)];
+}
+
+/* Y * G_s at every pixel: the direct 2D sum over the window (R19). */
+static void gauss_blur_2d(const double *Y, int H, int W, double s, double *out) {
+    const int r = (int)ceil(3.0 * s);
+    double norm = 0.0;
+    for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx) norm += exp(-(double)(dx * dx + dy * dy) / (2.0 * s * s));
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            double acc = 0.0;
+            for (int dy = -r; dy <= r; ++dy)
+                for (int dx = -r; dx <= r; ++dx)
+                    acc += exp(-(double)(dx * dx + dy * dy) / (2.0 * s * s)) / norm * px_at(Y, H, W, y + dy, x + dx);
+            out[(int64_t)y * W + x] = acc;
+        }
+}
+
+void or_init_saliency(int32_t H, int32_t W, const double *img, const double *depth, double sigma1,
+                      double sigma2, double *dog, double *grad) {
+    const int64_t npx = (int64_t)H * W;
+    double *Y = (double *)malloc(sizeof(double) * npx);
+    double *b1 = (double *)malloc(sizeof(double) * npx);
+    double *b2 = (double *)malloc(sizeof(double) * npx);
+    for (int64_t i = 0; i < npx; ++i) Y[i] = (img[i] + img[npx + i] + img[2 * npx + i]) / 3.0;
+    gauss_blur_2d(Y, H, W, sigma1, b1);
+    gauss_blur_2d(Y, H, W, sigma2, b2);
+    for (int64_t i = 0; i < npx; ++i) dog[i] = fmin(fabs(b1[i] - b2[i]), 1.0);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const double gx = (px_at(depth, H, W, y, x + 1) - px_at(depth, H, W, y, x - 1)) / 2.0;
+            const double gy = (px_at(depth, H, W, y + 1, x) - px_at(depth, H, W, y - 1, x)) / 2.0;
+            grad[(int64_t)y * W + x] = sqrt(gx * gx + gy * gy);
+        }
+    free(Y);
+    free(b1);
+    free(b2);
+}
+
+/* P = min(lambda DoG + (1 - lambda) minmax(||grad D||), 1) (Sec. 3.3.1, R20). */
+static void init_p(int32_t H, int32_t W, const double *img, const double *depth, double s1, double s2,
+                   double lambda, double *P) {
+    const int64_t npx = (int64_t)H * W;
+    double *dog = (double *)malloc(sizeof(double) * npx);
+    double *g = (double *)malloc(sizeof(double) * npx);
+    or_init_saliency(H, W, img, depth, s1, s2, dog, g);
+    double lo = g[0], hi = g[0];
+    for (int64_t i = 1; i < npx; ++i) {
+        lo = fmin(lo, g[i]);
+        hi = fmax(hi, g[i]);
+    }
+    for (int64_t i = 0; i < npx; ++i) {
+        const double gn = hi > lo ? (g[i] - lo) / (hi - lo) : 0.0;
+        P[i] = fmin(lambda * dog[i] + (1.0 - lambda) * gn, 1.0);
+    }
+    free(dog);
+    free(g);
+}
+
+void or_init_probability(int32_t H, int32_t W, const double *img, const double *depth, const double *img_r,
+                         const double *depth_r, double sigma1, double sigma2, double lambda, double *prob) {
+    const int64_t npx = (int64_t)H * W;
+    init_p(H, W, img, depth, sigma1, sigma2, lambda, prob);
+    if (!img_r) return;
+    double *Pr = (double *)malloc(sizeof(double) * npx);
+    init_p(H, W, img_r, depth_r, sigma1, sigma2, lambda, Pr);
+    for (int64_t i = 0; i < npx; ++i) prob[i] = fmax(prob[i] - Pr[i], 0.0); /* P_kf */
+    free(Pr);
+}
+
+int64_t or_init_select(int32_t H, int32_t W, const double *prob, const double *uniform, const double *depth,
+                       const or_camera *cam, double near_z, int32_t levels, const double *voxel,
+                       const double *max_dist, int64_t n_old, const int64_t *old_keys, int64_t cap,
+                       int64_t *new_keys, double *pos, int32_t *level, int32_t *pixel, uint8_t *selected,
+                       uint8_t *uncertain, double tol, double tol_rel) {
+    const int64_t npx = (int64_t)H * W;
+    /* every occupied voxel, old ones first; grows as voxels are met */
+    int64_t n_keys = n_old, key_cap = n_old + 1024, n_new = 0;
+    int64_t *keys = (int64_t *)malloc(sizeof(int64_t) * 4 * (size_t)key_cap);
+    if (n_old) memcpy(keys, old_keys, sizeof(int64_t) * 4 * (size_t)n_old);
+    if (selected) memset(selected, 0, (size_t)npx);
+    if (uncertain) memset(uncertain, 0, (size_t)npx);
+    const double tabs = fabs(cam->t[0]) + fabs(cam->t[1]) + fabs(cam->t[2]);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int64_t p = (int64_t)y * W + x;
+            const double P = prob[p];
+            int unsure = 0, is_max = P > 0.0;
+            if (P > 0.0 && P <= tol) unsure = 1;
+            /* 3x3 non-maximum suppression; equal values go to the lower raster index */
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int yy = y + dy, xx = x + dx;
+                    if ((dx == 0 && dy == 0) || yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                    const int64_t q = (int64_t)yy * W + xx;
+                    const double Q = prob[q];
+                    if (Q > P || (Q == P && q < p)) is_max = 0;
+                    if (P > 0.0 && Q != P && fabs(Q - P) <= tol) unsure = 1;
+                }
+            const double d = depth[p];
+            if (is_max && (fabs(uniform[p] - P) <= tol || fabs(d - near_z) <= tol_rel * near_z)) unsure = 1;
+            int l = -1, in_range = 1;
+            int64_t idx[3] = {0, 0, 0};
+            if (is_max && uniform[p] < P && d > near_z) {
+                /* the pixel centre at its depth (R1), back to the world frame */
+                const double xc[3] = {d * ((x + 0.5 - cam->cx) / cam->fx), d * ((y + 0.5 - cam->cy) / cam->fy), d};
+                double xw[3];
+                for (int i = 0; i < 3; ++i)
+                    xw[i] = cam->R[0 + i] * (xc[0] - cam->t[0]) + cam->R[3 + i] * (xc[1] - cam->t[1]) +
+                            cam->R[6 + i] * (xc[2] - cam->t[2]);
+                const double dist = sqrt(xc[0] * xc[0] + xc[1] * xc[1] + xc[2] * xc[2]);
+                for (int k = 0; k < levels && l < 0; ++k) {
+                    if (fabs(dist - max_dist[k]) <= tol_rel * dist) unsure = 1;
+                    if (dist < max_dist[k]) l = k;
+                }
+                if (l >= 0) {
+                    const double xabs = fabs(xc[0]) + fabs(xc[1]) + fabs(xc[2]);
+                    for (int i = 0; i < 3; ++i) {
+                        const double q = xw[i] / voxel[l];
+                        /* the device's FP32 point carries an error that scales with |x_c| + |t| */
+                        if (fabs(q - floor(q + 0.5)) <= tol_rel * (1.0 + fabs(q) + (xabs + tabs) / voxel[l]))
+                            unsure = 1;
+                        idx[i] = (int64_t)floor(q);
+                        if (idx[i] >= (1 << 19) || idx[i] < -(1 << 19)) in_range = 0;
+                    }
+                }
+            }
+            if (uncertain) uncertain[p] = (uint8_t)unsure;
+            if (l < 0 || !in_range) continue;
+            if (selected) selected[p] = 1;
+            int seen = 0;
+            for (int64_t k = 0; k < n_keys && !seen; ++k)
+                seen = keys[4 * k] == l && keys[4 * k + 1] == idx[0] && keys[4 * k + 2] == idx[1] &&
+                       keys[4 * k + 3] == idx[2];
+            if (seen) continue;
+            if (n_keys == key_cap) {
+                key_cap *= 2;
+                keys = (int64_t *)realloc(keys, sizeof(int64_t) * 4 * (size_t)key_cap);
+            }
+            int64_t *kk = keys + 4 * n_keys++;
+            kk[0] = l;
+            kk[1] = idx[0];
+            kk[2] = idx[1];
+            kk[3] = idx[2];
+            if (n_new < cap) {
+                memcpy(new_keys + 4 * n_new, kk, sizeof(int64_t) * 4);
+                for (int i = 0; i < 3; ++i) pos[3 * n_new + i] = (double)idx[i] * voxel[l];
+                level[n_new] = l;
+                pixel[n_new] = (int32_t)p;
+            }
+            ++n_new;
+        }
+    free(keys);
+    return n_new;
 }

@@ -707,6 +707,107 @@ def run_lifecycle(args, dev):
 # --------------------------------------------------------------------------
 # CPU arms: the FP64 oracle on the host cores
 
+def run_init(args, dev):
+    """Anchor initialisation at a keyframe (Sec. 3.3.1, Supp. B): P_kf against
+    the render, 3x3 NMS, the draw, unprojection and voxel-hash insertion, on a
+    synthetic 1280x720 driving keyframe (ground plane, boxes, sky) whose map
+    render misses 40 % of the boxes; a pool of 16 camera positions along the
+    road, one table that accumulates the anchors; the first-keyframe variant
+    (P alone) timed beside it."""
+    import torch
+    from paper_2606_30436_b300 import scenes, spawn
+
+    Hk, Wk, pool = 720, 1280, 16
+    img, depth, U = scenes.keyframe(Hk, Wk, seed=21)
+    img_r, depth_r, _ = scenes.keyframe(Hk, Wk, seed=21, missing=0.4)
+    cams = [scenes.keyframe_camera(Hk, Wk, seed=22, centre=(3.0, -1.6, 40.0 + 7.0 * k)) for k in range(pool)]
+    g = lambda a: torch.from_numpy(a).to(dev)
+    I, D, Ir, Dr, Ut = g(img), g(depth), g(img_r), g(depth_r), g(U)
+    prob = torch.empty(Hk, Wk, dtype=torch.float32, device=dev)
+    ws = spawn.init_workspace(Wk, Hk, dev)
+    amap = spawn.AnchorMap(4_000_000, device=dev)
+    stream = torch.cuda.current_stream()
+    steps = max(10, args.steps)
+    out = {"metric": "keyframe initialisations/s (720p: P_kf, 3x3 NMS, draw, voxel insertion)",
+           "unit": "keyframes/s", "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "1280x720 driving keyframe, render missing 40% of boxes, 16 camera positions",
+                      "table_slots": int(amap.keys.numel()), "l2": "inputs 18 MB per keyframe (L2-resident)"}}
+    for mode in ("residual", "first"):
+        rend = mode == "residual"
+        amap.reset()
+
+        def one(k, ev=None):
+            spawn.gs_init_probability(I, D, Ir if rend else None, Dr if rend else None, prob=prob, ws=ws)
+            if ev is not None:
+                ev.record(stream)
+            amap.insert(prob, Ut, D, cams[k % pool])
+
+        for k in range(args.warmup):
+            one(k)
+        torch.cuda.synchronize()
+        amap.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        mids = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        e0.record(stream)
+        for k in range(steps):
+            starts[k].record(stream)
+            one(k, mids[k])
+            ends[k].record(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        amap.check_status()
+        ms = e0.elapsed_time(e1) / steps
+        t_prob = sum(starts[k].elapsed_time(mids[k]) for k in range(steps)) / steps
+        t_ins = sum(mids[k].elapsed_time(ends[k]) for k in range(steps)) / steps
+        px = Hk * Wk
+        # probability stage: images and depths read, probability written (the DoG and gradient
+        # planes between its two kernels stay in L2)
+        prob_bytes = (32 if rend else 16) * px + 4 * px
+        out[mode] = {"value": round(1e3 / ms, 1), "ms_per_keyframe": round(ms, 4),
+                     "stages_ms": {"probability": round(t_prob, 4), "insert": round(t_ins, 4)},
+                     "anchors_after_pool": amap.n, "steps": steps,
+                     "probability_gbs": round(prob_bytes / (t_prob * 1e-3) / 1e9, 1)}
+    # end to end: keyframe inputs from pinned host memory, the anchor count back
+    host = [t.cpu().pin_memory() for t in (I, D, Ir, Dr, Ut)]
+    devb = [torch.empty_like(t) for t in (I, D, Ir, Dr, Ut)]
+    cnt = torch.empty(1, dtype=torch.int64).pin_memory()
+    amap.reset()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        for h, d_ in zip(host, devb):
+            d_.copy_(h, non_blocking=True)
+        spawn.gs_init_probability(devb[0], devb[1], devb[2], devb[3], prob=prob, ws=ws)
+        amap.insert(prob, devb[4], devb[1], cams[k % pool])
+        cnt.copy_(amap.count, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e = e0.elapsed_time(e1) / steps
+    peak, kind = measured_peaks()
+    r = out["residual"]
+    out.update(value=r["value"], ms_per_step=r["ms_per_keyframe"], steps=steps, warmup=args.warmup, n_gpus=1,
+               e2e={"value": round(1e3 / e2e, 1), "unit": "keyframes/s",
+                    "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in host)),
+                    "d2h_bytes_per_step": 8},
+               gpu_launches=6 * steps,
+               roofline={"kernel": "k_init_saliency + k_init_combine", "bound": "hbm",
+                         "achieved": r["probability_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": round(r["probability_gbs"] / peak, 4), "traffic": None,
+                         "peak_kind": kind + " (copy bandwidth)"})
+    # the oracle on the host cores: one keyframe
+    import oracle as orc
+    t0 = time.perf_counter()
+    P = orc.init_probability(img, depth, img_r, depth_r)
+    orc.init_select(P, U, depth, cams[0])
+    dt = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": round(1.0 / dt, 3), "unit": "keyframes/s", "cores": cpu_cores(),
+                           "kind": "oracle", "sample": "one 1280x720 keyframe (P_kf + selection)"}
+    return out
+
+
 def oracle_iteration(scene, tscene_img, cam, oc):
     import oracle as orc
     f = orc.loss_and_grads(scene, cam, oc, tscene_img, LAMBDA)
@@ -789,6 +890,8 @@ def main():
                     help="learned vs plain densify/prune over keyframe chunks (prints its own JSON line)")
     ap.add_argument("--memory", action="store_true",
                     help="peak memory at 10M Gaussians, 1920x1080, with the crop gradient check (own JSON line)")
+    ap.add_argument("--init", action="store_true",
+                    help="anchor initialisation at a 720p keyframe (probability, NMS, voxel insertion)")
     ap.add_argument("--memory-gaussians", type=int, default=10_000_000)
     ap.add_argument("--memory-iters", type=int, default=5)
     ap.add_argument("--lifecycle-gaussians", type=int, default=1_000_000)
@@ -813,6 +916,11 @@ def main():
         if rank == 0:
             import torch
             print(json.dumps(run_memory(args, torch.device("cuda", 0))), flush=True)
+        return
+    if args.init:
+        if rank == 0:
+            import torch
+            print(json.dumps(run_init(args, torch.device("cuda", 0))), flush=True)
         return
     if args.lifecycle:
         if rank == 0:

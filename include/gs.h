@@ -466,6 +466,97 @@ gs_status gs_mlp_train_grad(const float *feat, const uint8_t *y_densify, const u
 gs_status gs_mlp_adam(float *weights, const float *grad, float *exp_avg, float *exp_avg_sq, float lr,
                       float beta1, float beta2, float eps, int64_t step, gs_stream stream);
 
+/*
+ * Probabilistic initialisation of new anchors at a keyframe (Sec. 3.3.1)
+ * and the voxel hash of the dynamic map expansion (Supp. B).
+ *
+ * P = min(lambda DoG + (1 - lambda) minmax(||grad D||), 1) with DoG =
+ * min(scale |(G_s1 - G_s2) * Y|, 1), Y = (R + G + B) / 3 (scale 255 takes
+ * [0, 1] images in 8-bit intensity units), G_s the sampled 2D
+ * Gaussian of radius ceil(3 s) normalised to sum 1, ||grad D|| by central
+ * differences, borders replicated and the min-max over the keyframe (a flat
+ * map normalises to 0).  For a keyframe after the first, P_kf = max(P - P^,
+ * 0) with P^ the same map of the rendered image and depth.  A pixel spawns
+ * an anchor candidate when P_kf is the strict maximum of its 3x3 window
+ * (equal values go to the lower raster index v W + u), P_kf > 0, the
+ * caller's uniform draw there is below P_kf, and depth > near_z; its centre at that depth,
+ * x_w = R^T (d ((u+0.5-cx)/fx, (v+0.5-cy)/fy, 1) - t), goes to the first
+ * level l with ||x_c|| < max_dist[l] (none: skipped) and to the voxel
+ * idx = floor(x_w / voxel[l]) (skipped unless -2^19 <= idx < 2^19).  A voxel
+ * (l, idx) holds one anchor at p = idx * voxel[l]; voxels already in the
+ * table stay as they are, and each new voxel becomes an anchor numbered in
+ * raster order of the first pixel that reached it.  The decisions are taken
+ * in FP32.
+ */
+#define GS_INIT_MAX_LEVELS 8
+#define GS_INIT_MAX_RADIUS 16  /* ceil(3 sigma) of either blur */
+
+/* host struct; defaults: 1.0, 1.6, 0.9, 255, 0.2, 5, voxel (0.1, 0.25, 1, 5,
+ * 25) m, max_dist (10, 25, 100, 500, +inf) m */
+typedef struct {
+    float sigma1, sigma2;                /* DoG blur widths in pixels */
+    float lambda;                        /* DoG / depth-gradient balance */
+    float intensity_scale;               /* the DoG's intensity units per image unit */
+    float near_z;                        /* pixels at depth <= near_z spawn nothing */
+    int32_t levels;                      /* LoD levels m, 1..GS_INIT_MAX_LEVELS */
+    float voxel[GS_INIT_MAX_LEVELS];     /* voxel size eps_l of level l */
+    float max_dist[GS_INIT_MAX_LEVELS];  /* increasing upper camera distances */
+} gs_init_cfg;
+
+/* Open-addressing voxel table (linear probing).  A voxel key packs (l, ix,
+ * iy, iz) as l << 60 | (ix + 2^19) << 40 | (iy + 2^19) << 20 | (iz + 2^19);
+ * a free slot holds all ones.  capacity: a power of two >= 1024, each array
+ * 16-byte aligned; keep the load below ~1/2 for short probe runs. */
+typedef struct {
+    uint64_t *keys;    /* [capacity] */
+    int32_t *ids;      /* [capacity] anchor id of the slot's voxel, -1: none */
+    int32_t *owner;    /* [capacity] work state of gs_init_insert (INT32_MAX free, -1 settled) */
+    int64_t capacity;
+} gs_voxel_table;
+
+/* Anchor records, appended by gs_init_insert. */
+typedef struct {
+    float *pos;        /* [3][ld] planes: idx * voxel[l] */
+    int32_t *level;    /* [ld] */
+    int32_t *pixel;    /* [ld] spawning pixel v W + u of its keyframe */
+    int64_t *count;    /* device int64: anchors in use; receives the new total */
+    int64_t ld;        /* capacity */
+} gs_anchor_set;
+
+/* Marks every slot free. */
+gs_status gs_voxel_table_reset(const gs_voxel_table *table, gs_stream stream);
+
+/* Workspace of gs_init_probability and gs_init_insert for a W x H keyframe. */
+gs_status gs_init_workspace_size(int32_t width, int32_t height, size_t *bytes);
+
+/*
+ * prob [H][W] = P of (img [3][H][W], depth [H][W]), or P_kf when img_r /
+ * depth_r (the rendered pair; null together) are given.
+ */
+gs_status gs_init_probability(const float *img, const float *depth, const float *img_r, const float *depth_r,
+                              int32_t width, int32_t height, const gs_init_cfg *cfg, float *prob, void *ws,
+                              size_t ws_bytes, gs_stream stream);
+
+/*
+ * Candidates of prob (the output above) with the caller's uniform draws
+ * [H][W] and depth [H][W] under camera cam; new voxels enter the table and
+ * become anchors [count, count + new) of the set (count += new).  Anchors
+ * past anchors->ld are not written, their slots get id -1 and status gets
+ * bit 1<<GS_ERR_CAPACITY (a keyframe adds at most ceil(W/2) ceil(H/2)); a
+ * full table skips the pixel with the same bit.  selected [H][W] bytes
+ * (nullable): 1 where a candidate got a voxel.  Uses the same workspace.
+ */
+gs_status gs_init_insert(const float *prob, const float *uniform, const float *depth, const gs_camera *cam,
+                         const gs_init_cfg *cfg, const gs_voxel_table *table, const gs_anchor_set *anchors,
+                         uint8_t *selected, int32_t *status, void *ws, size_t ws_bytes, gs_stream stream);
+
+/*
+ * ids [n] = the anchor id of voxel (level, ix, iy, iz) = planes 0-3 of vox
+ * [4][ld] (int32), -1 when the voxel is free or out of range.
+ */
+gs_status gs_voxel_lookup(const gs_voxel_table *table, const int32_t *vox, int64_t n, int64_t ld, int32_t *ids,
+                          gs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -102,8 +102,8 @@ def lib():
         L.or_mlp_features.argtypes = [i64, vp, vp, vp, vp, vp, i32, vp, vp]
         L.or_densify_prune.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, d, d, i64, vp, vp, vp]
         L.or_densify_prune.restype = i64
-        L.or_init_saliency.argtypes = [i32, i32, vp, vp, d, d, vp, vp]
-        L.or_init_probability.argtypes = [i32, i32, vp, vp, vp, vp, d, d, d, vp]
+        L.or_init_saliency.argtypes = [i32, i32, vp, vp, d, d, d, vp, vp]
+        L.or_init_probability.argtypes = [i32, i32, vp, vp, vp, vp, d, d, d, d, vp]
         L.or_init_select.argtypes = [i32, i32, vp, vp, vp, C.POINTER(_Camera), d, i32, vp, vp, i64, vp, i64,
                                      vp, vp, vp, vp, vp, vp, d, d]
         L.or_init_select.restype = i64
@@ -394,17 +394,19 @@ class InitCfg:
     sigma1: float = 1.0
     sigma2: float = 1.6
     lam: float = 0.9
+    scale: float = 255.0
     near_z: float = 0.2
     voxel: tuple = (0.1, 0.25, 1.0, 5.0, 25.0)
     max_dist: tuple = (10.0, 25.0, 100.0, 500.0, float("inf"))
 
 
-def init_saliency(img, depth, sigma1=1.0, sigma2=1.6):
-    """DoG [H][W] of the channel mean of img [3][H][W] and ||grad depth|| [H][W]."""
+def init_saliency(img, depth, sigma1=1.0, sigma2=1.6, scale=255.0):
+    """DoG [H][W] of the channel mean of img [3][H][W] (times scale) and ||grad depth|| [H][W]."""
     img, depth = _f64(img), _f64(depth)
     H, W = depth.shape
     dog, grad = np.zeros((H, W)), np.zeros((H, W))
-    lib().or_init_saliency(H, W, _ptr(img), _ptr(depth), float(sigma1), float(sigma2), _ptr(dog), _ptr(grad))
+    lib().or_init_saliency(H, W, _ptr(img), _ptr(depth), float(sigma1), float(sigma2), float(scale), _ptr(dog),
+                           _ptr(grad))
     return dog, grad
 
 
@@ -416,7 +418,7 @@ def init_probability(img, depth, img_r=None, depth_r=None, cfg: InitCfg = InitCf
     depth_r = None if depth_r is None else _f64(depth_r)
     prob = np.zeros((H, W))
     lib().or_init_probability(H, W, _ptr(img), _ptr(depth), _ptr(img_r), _ptr(depth_r), float(cfg.sigma1),
-                              float(cfg.sigma2), float(cfg.lam), _ptr(prob))
+                              float(cfg.sigma2), float(cfg.scale), float(cfg.lam), _ptr(prob))
     return prob
 
 

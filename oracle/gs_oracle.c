@@ -42,7 +42,9 @@
  * Probabilistic initialisation (Sec. 3.3.1: DoG, normalised depth gradient,
  * P, P_kf, 3x3 NMS, voxel quantisation; Supp. B: dynamic map expansion
  * through a voxel hash; Supp. F: lambda = 0.9, m = 5 levels) reads:
- *   R19 DoG on Y = (R + G + B) / 3; G_s sampled on integer offsets within
+ *   R19 DoG on Y = (R + G + B) / 3 taken in 8-bit intensity units (255 Y;
+ *       on [0, 1] intensities the clamp at 1 could never act: the DoG of a
+ *       unit step peaks near 0.11); G_s sampled on integer offsets within
  *       ceil(3 s), normalised to sum 1; replicated borders; s1 = 1, s2 = 1.6.
  *   R20 ||grad D|| by central differences in depth units per pixel with
  *       replicated borders; min-max over the keyframe, a flat map gives 0.
@@ -1143,7 +1145,7 @@ static void gauss_blur_2d(const double *Y, int H, int W, double s, double *out) 
 }
 
 void or_init_saliency(int32_t H, int32_t W, const double *img, const double *depth, double sigma1,
-                      double sigma2, double *dog, double *grad) {
+                      double sigma2, double scale, double *dog, double *grad) {
     const int64_t npx = (int64_t)H * W;
     double *Y = (double *)malloc(sizeof(double) * npx);
     double *b1 = (double *)malloc(sizeof(double) * npx);
@@ -1151,7 +1153,7 @@ void or_init_saliency(int32_t H, int32_t W, const double *img, const double *dep
     for (int64_t i = 0; i < npx; ++i) Y[i] = (img[i] + img[npx + i] + img[2 * npx + i]) / 3.0;
     gauss_blur_2d(Y, H, W, sigma1, b1);
     gauss_blur_2d(Y, H, W, sigma2, b2);
-    for (int64_t i = 0; i < npx; ++i) dog[i] = fmin(fabs(b1[i] - b2[i]), 1.0);
+    for (int64_t i = 0; i < npx; ++i) dog[i] = fmin(scale * fabs(b1[i] - b2[i]), 1.0);
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             const double gx = (px_at(depth, H, W, y, x + 1) - px_at(depth, H, W, y, x - 1)) / 2.0;
@@ -1165,11 +1167,11 @@ void or_init_saliency(int32_t H, int32_t W, const double *img, const double *dep
 
 /* P = min(lambda DoG + (1 - lambda) minmax(||grad D||), 1) (Sec. 3.3.1, R20). */
 static void init_p(int32_t H, int32_t W, const double *img, const double *depth, double s1, double s2,
-                   double lambda, double *P) {
+                   double scale, double lambda, double *P) {
     const int64_t npx = (int64_t)H * W;
     double *dog = (double *)malloc(sizeof(double) * npx);
     double *g = (double *)malloc(sizeof(double) * npx);
-    or_init_saliency(H, W, img, depth, s1, s2, dog, g);
+    or_init_saliency(H, W, img, depth, s1, s2, scale, dog, g);
     double lo = g[0], hi = g[0];
     for (int64_t i = 1; i < npx; ++i) {
         lo = fmin(lo, g[i]);
@@ -1184,12 +1186,13 @@ static void init_p(int32_t H, int32_t W, const double *img, const double *depth,
 }
 
 void or_init_probability(int32_t H, int32_t W, const double *img, const double *depth, const double *img_r,
-                         const double *depth_r, double sigma1, double sigma2, double lambda, double *prob) {
+                         const double *depth_r, double sigma1, double sigma2, double scale, double lambda,
+                         double *prob) {
     const int64_t npx = (int64_t)H * W;
-    init_p(H, W, img, depth, sigma1, sigma2, lambda, prob);
+    init_p(H, W, img, depth, sigma1, sigma2, scale, lambda, prob);
     if (!img_r) return;
     double *Pr = (double *)malloc(sizeof(double) * npx);
-    init_p(H, W, img_r, depth_r, sigma1, sigma2, lambda, Pr);
+    init_p(H, W, img_r, depth_r, sigma1, sigma2, scale, lambda, Pr);
     for (int64_t i = 0; i < npx; ++i) prob[i] = fmax(prob[i] - Pr[i], 0.0); /* P_kf */
     free(Pr);
 }
@@ -1211,8 +1214,7 @@ int64_t or_init_select(int32_t H, int32_t W, const double *prob, const double *u
         for (int x = 0; x < W; ++x) {
             const int64_t p = (int64_t)y * W + x;
             const double P = prob[p];
-            int unsure = 0, is_max = P > 0.0;
-            if (P > 0.0 && P <= tol) unsure = 1;
+            int unsure = 0, is_max = P > 0.0, dominated = 0, close = 0;
             /* 3x3 non-maximum suppression; equal values go to the lower raster index */
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
@@ -1221,8 +1223,11 @@ int64_t or_init_select(int32_t H, int32_t W, const double *prob, const double *u
                     const int64_t q = (int64_t)yy * W + xx;
                     const double Q = prob[q];
                     if (Q > P || (Q == P && q < p)) is_max = 0;
-                    if (P > 0.0 && Q != P && fabs(Q - P) <= tol) unsure = 1;
+                    if (Q > P + tol) dominated = 1;
+                    else if (Q != P && fabs(Q - P) <= tol) close = 1;
                 }
+            /* a pixel beaten by more than tol stays suppressed; otherwise a near tie may flip */
+            if (P > 0.0 && !dominated && (close || P <= tol)) unsure = 1;
             const double d = depth[p];
             if (is_max && (fabs(uniform[p] - P) <= tol || fabs(d - near_z) <= tol_rel * near_z)) unsure = 1;
             int l = -1, in_range = 1;

@@ -172,18 +172,20 @@ int64_t or_densify_prune(int64_t n, int32_t K_row, const double *P, const double
 /* Probabilistic initialisation of new anchors at a keyframe (Sec. 3.3.1,
  * Supp. B), readings R19-R24 of gs_oracle.c.
  *
- * or_init_saliency: dog[H][W] = min(|(G_s1 - G_s2) * Y|, 1) with Y the mean
- * of the three planes of img[3][H][W] and G_s the sampled 2D Gaussian of
+ * or_init_saliency: dog[H][W] = min(scale |(G_s1 - G_s2) * Y|, 1) with Y the
+ * mean of the three planes of img[3][H][W] (scale 255: 8-bit intensity
+ * units for [0, 1] images) and G_s the sampled 2D Gaussian of
  * radius ceil(3 s) normalised to sum 1, borders replicated; grad[H][W] =
  * ||grad D|| by central differences, borders replicated. */
 void or_init_saliency(int32_t H, int32_t W, const double *img, const double *depth, double sigma1,
-                      double sigma2, double *dog, double *grad);
+                      double sigma2, double scale, double *dog, double *grad);
 
 /* prob[H][W] = max(P - P_r, 0) with P = min(lambda dog + (1 - lambda)
  * minmax(grad), 1) of (img, depth) and P_r the same of (img_r, depth_r);
  * img_r / depth_r null together: P_r = 0. */
 void or_init_probability(int32_t H, int32_t W, const double *img, const double *depth, const double *img_r,
-                         const double *depth_r, double sigma1, double sigma2, double lambda, double *prob);
+                         const double *depth_r, double sigma1, double sigma2, double scale, double lambda,
+                         double *prob);
 
 /* Selection, unprojection and voxel insertion over the pixels in raster
  * order.  Pixel p is selected when prob[p] > 0 is the (value, -index)
@@ -197,8 +199,9 @@ void or_init_probability(int32_t H, int32_t W, const double *img, const double *
  * voxel[l], level and pixel (v W + u).  Returns the number of new voxels
  * (may exceed cap).  selected[H][W] (nullable): 1 for selected pixels whose
  * point got a voxel.  uncertain[H][W] (nullable): 1 where a decision of the
- * pixel lies within tol of flipping (prob comparisons, the draw) or within
- * tol_rel, relative, of a threshold (depth, distance band, voxel boundary). */
+ * pixel lies within tol of flipping (a neighbour within tol and none above
+ * by more; the draw) or within tol_rel, relative, of a threshold (depth,
+ * distance band, voxel boundary). */
 int64_t or_init_select(int32_t H, int32_t W, const double *prob, const double *uniform, const double *depth,
                        const or_camera *cam, double near_z, int32_t levels, const double *voxel,
                        const double *max_dist, int64_t n_old, const int64_t *old_keys, int64_t cap,

@@ -530,3 +530,118 @@ GS_API gs_status gs_mlp_adam(float *weights, const float *grad, float *exp_avg, 
     return cuda_status(launch_mlp_adam(weights, grad, exp_avg, exp_avg_sq, lr, beta1, beta2, eps, step,
                                        (cudaStream_t)stream));
 }
+
+namespace {
+
+// Normalised 1D weights of the sampled Gaussian (their outer product is the
+// normalised 2D kernel).
+gs_status init_blur(const gs_init_cfg *cfg, InitBlur &bw) {
+    bw = InitBlur{};
+    const float sig[2] = {cfg->sigma1, cfg->sigma2};
+    for (int j = 0; j < 2; ++j) {
+        if (!(sig[j] > 0.0f) || std::ceil(3.0 * (double)sig[j]) > GS_INIT_MAX_RADIUS) return GS_ERR_INVALID;
+        const int r = (int)std::ceil(3.0 * (double)sig[j]);
+        double w[GS_INIT_MAX_RADIUS + 1], sum = 0.0;
+        for (int k = 0; k <= r; ++k) {
+            w[k] = std::exp(-(double)(k * k) / (2.0 * (double)sig[j] * (double)sig[j]));
+            sum += k ? 2.0 * w[k] : w[k];
+        }
+        float *dst = j ? bw.w2 : bw.w1;
+        for (int k = 0; k <= r; ++k) dst[k] = (float)(w[k] / sum);
+        (j ? bw.r2 : bw.r1) = r;
+    }
+    bw.R = bw.r1 > bw.r2 ? bw.r1 : bw.r2;
+    if (!(cfg->intensity_scale > 0.0f) || !std::isfinite(cfg->intensity_scale)) return GS_ERR_INVALID;
+    bw.scale = cfg->intensity_scale;
+    return GS_OK;
+}
+
+gs_status init_lod(const gs_init_cfg *cfg, InitLod &lod) {
+    lod = InitLod{};
+    if (cfg->levels < 1 || cfg->levels > GS_INIT_MAX_LEVELS || !(cfg->near_z >= 0.0f)) return GS_ERR_INVALID;
+    for (int l = 0; l < cfg->levels; ++l) {
+        if (!(cfg->voxel[l] > 0.0f) || !std::isfinite(cfg->voxel[l]) || !(cfg->max_dist[l] > 0.0f) ||
+            (l && !(cfg->max_dist[l] > cfg->max_dist[l - 1])))
+            return GS_ERR_INVALID;
+        lod.voxel[l] = cfg->voxel[l];
+        lod.max_dist[l] = cfg->max_dist[l];
+    }
+    lod.levels = cfg->levels;
+    lod.near_z = cfg->near_z;
+    return GS_OK;
+}
+
+bool init_size_ok(long long W, long long H) { return W >= 1 && H >= 1 && W * H <= 0x7fffffffll; }
+
+gs_status check_table(const gs_voxel_table *t) {
+    if (!t || !t->keys || !t->ids || !t->owner || !aligned16(t->keys) || !aligned16(t->ids) || !aligned16(t->owner) ||
+        t->capacity < 1024 || t->capacity > (1ll << 30) || (t->capacity & (t->capacity - 1)))
+        return GS_ERR_INVALID;
+    return GS_OK;
+}
+
+}  // namespace
+
+GS_API gs_status gs_voxel_table_reset(const gs_voxel_table *table, gs_stream stream) {
+    gs_status st = check_table(table);
+    if (st != GS_OK) return st;
+    return cuda_status(launch_voxel_reset((unsigned long long *)table->keys, table->ids, table->owner,
+                                          table->capacity, (cudaStream_t)stream));
+}
+
+GS_API gs_status gs_init_workspace_size(int32_t width, int32_t height, size_t *bytes) {
+    if (!bytes || !init_size_ok(width, height)) return GS_ERR_INVALID;
+    *bytes = init_workspace_bytes(width, height);
+    return GS_OK;
+}
+
+GS_API gs_status gs_init_probability(const float *img, const float *depth, const float *img_r, const float *depth_r,
+                                     int32_t width, int32_t height, const gs_init_cfg *cfg, float *prob, void *ws,
+                                     size_t ws_bytes, gs_stream stream) {
+    if (!cfg || !init_size_ok(width, height) || !img || !depth || !aligned16(img) || !aligned16(depth) ||
+        (!img_r) != (!depth_r) || (img_r && (!aligned16(img_r) || !aligned16(depth_r))) || !prob ||
+        !aligned16(prob) || !ws || ((uintptr_t)ws & 255u) || ws_bytes < init_workspace_bytes(width, height) ||
+        !(cfg->lambda >= 0.0f && cfg->lambda <= 1.0f))
+        return GS_ERR_INVALID;
+    InitBlur bw;
+    gs_status st = init_blur(cfg, bw);
+    if (st != GS_OK) return st;
+    return cuda_status(launch_init_probability(img, depth, img_r, depth_r, width, height, bw, cfg->lambda, prob, ws,
+                                               (cudaStream_t)stream));
+}
+
+GS_API gs_status gs_init_insert(const float *prob, const float *uniform, const float *depth, const gs_camera *cam,
+                                const gs_init_cfg *cfg, const gs_voxel_table *table, const gs_anchor_set *anchors,
+                                uint8_t *selected, int32_t *status, void *ws, size_t ws_bytes, gs_stream stream) {
+    if (!cam || !cfg || !init_size_ok(cam->width, cam->height) || !(cam->fx > 0.0f) || !(cam->fy > 0.0f) || !prob ||
+        !uniform || !depth || !aligned16(prob) || !aligned16(uniform) || !aligned16(depth) || !anchors ||
+        !anchors->pos || !aligned16(anchors->pos) || !anchors->level || !anchors->pixel || !anchors->count ||
+        ((uintptr_t)anchors->count & 7u) || anchors->ld < 0 || !ws || ((uintptr_t)ws & 255u) ||
+        ws_bytes < init_workspace_bytes(cam->width, cam->height))
+        return GS_ERR_INVALID;
+    gs_status st = check_table(table);
+    if (st != GS_OK) return st;
+    InitLod lod;
+    if ((st = init_lod(cfg, lod)) != GS_OK) return st;
+    InitCam c;
+    for (int i = 0; i < 9; ++i) c.R[i] = cam->R[i];
+    for (int i = 0; i < 3; ++i) c.t[i] = cam->t[i];
+    c.fx = cam->fx;
+    c.fy = cam->fy;
+    c.cx = cam->cx;
+    c.cy = cam->cy;
+    return cuda_status(launch_init_insert(prob, uniform, depth, cam->width, cam->height, c, lod,
+                                          (unsigned long long *)table->keys, table->ids, table->owner,
+                                          table->capacity, anchors->pos, anchors->level, anchors->pixel,
+                                          (long long *)anchors->count, anchors->ld, selected, status, ws,
+                                          (cudaStream_t)stream));
+}
+
+GS_API gs_status gs_voxel_lookup(const gs_voxel_table *table, const int32_t *vox, int64_t n, int64_t ld, int32_t *ids,
+                                 gs_stream stream) {
+    gs_status st = check_table(table);
+    if (st != GS_OK) return st;
+    if (n < 0 || ld < n || (n > 0 && (!vox || !ids || !aligned16(vox)))) return GS_ERR_INVALID;
+    return cuda_status(launch_voxel_lookup((const unsigned long long *)table->keys, table->ids, table->capacity, vox,
+                                           n, ld, ids, (cudaStream_t)stream));
+}

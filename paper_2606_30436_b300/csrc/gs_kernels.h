@@ -84,4 +84,31 @@ cudaError_t launch_mlp_train(const float *feat, const uint8_t *y_densify, const 
 cudaError_t launch_mlp_adam(float *w, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
                             long long step, cudaStream_t s);
 
+// Probabilistic initialisation (init.cu).  Blur weights w[k] of offset +-k
+// (normalised, radius r <= GS_INIT_MAX_RADIUS; R = the larger radius).
+struct InitBlur {
+    float w1[GS_INIT_MAX_RADIUS + 1], w2[GS_INIT_MAX_RADIUS + 1];
+    float scale;  // intensity units of the DoG
+    int r1, r2, R;
+};
+struct InitCam {
+    float R[9], t[3], fx, fy, cx, cy;
+};
+struct InitLod {
+    float voxel[GS_INIT_MAX_LEVELS], max_dist[GS_INIT_MAX_LEVELS];
+    float near_z;
+    int levels;
+};
+size_t init_workspace_bytes(int W, int H);
+cudaError_t launch_init_probability(const float *img, const float *depth, const float *img_r, const float *depth_r,
+                                    int W, int H, const InitBlur &bw, float lambda, float *prob, void *ws,
+                                    cudaStream_t s);
+cudaError_t launch_init_insert(const float *prob, const float *uniform, const float *depth, int W, int H,
+                               const InitCam &cam, const InitLod &lod, unsigned long long *keys, int *ids, int *owner,
+                               long long cap, float *pos, int *level, int *pixel, long long *count, long long ld,
+                               uint8_t *selected, int *status, void *ws, cudaStream_t s);
+cudaError_t launch_voxel_lookup(const unsigned long long *keys, const int *ids, long long cap, const int *vox,
+                                long long n, long long ld, int *out, cudaStream_t s);
+cudaError_t launch_voxel_reset(unsigned long long *keys, int *ids, int *owner, long long cap, cudaStream_t s);
+
 }  // namespace gs

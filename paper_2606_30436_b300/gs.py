@@ -78,7 +78,9 @@ EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspac
            "gs_render_bwd", "gs_project_bwd", "gs_adam", "gs_prune_stats", "gs_loss_static",
            "gs_reg_workspace_size", "gs_geo_loss", "gs_iso_loss", "gs_actions_workspace_size", "gs_densify_prune",
            "gs_mlp_push_blend", "gs_mlp_features", "gs_mlp_forward", "gs_mlp_train_grad", "gs_mlp_adam",
-           "gs_segment_workspace_size", "gs_project_bwd_adam", "gs_segment_workspace_size_items")
+           "gs_segment_workspace_size", "gs_project_bwd_adam", "gs_segment_workspace_size_items",
+           "gs_voxel_table_reset", "gs_init_workspace_size", "gs_init_probability", "gs_init_insert",
+           "gs_voxel_lookup")
 
 _lib = None
 

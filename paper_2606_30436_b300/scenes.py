@@ -177,3 +177,62 @@ def smooth_image(height, width, seed=3, channels=3):
             img[c] += np.sin(fx * xx + fy * yy + ph)
         img[c] = 0.5 + 0.12 * img[c] + rng.normal(0.0, 0.05, (height, width))
     return np.clip(img, 0.0, 1.0).astype(np.float32)
+
+
+def keyframe(height, width, seed=4, missing=0.0):
+    """A synthetic driving keyframe for the anchor initialisation: image
+    [3][H][W] in [0, 1] and metric depth [H][W] (0 marks the sky above the
+    horizon).  The ground is a plane 1.6 m below a camera with fx = fy = 0.9 W
+    (depth = 1.6 fy / (v - horizon)); axis-aligned boxes (facades, vehicles) at
+    random depths have sharp colour and depth edges and some carry a fine
+    checker texture; the sky is a smooth gradient.  With missing > 0 that
+    fraction of the boxes is left out, as a render of an incomplete map would
+    show it.  Also returns uniform [H][W] draws.  float32 throughout."""
+    rng = np.random.default_rng(seed)
+    H, W = int(height), int(width)
+    f = 0.9 * W
+    horizon = 0.45 * H
+    v = np.arange(H, dtype=np.float64)[:, None] + 0.5
+    u = np.arange(W, dtype=np.float64)[None, :] + 0.5
+    ground = v > horizon + 1.0
+    depth = np.where(ground, 1.6 * f / np.maximum(v - horizon, 1e-6), 0.0) * np.ones((1, W))
+    depth = np.minimum(depth, 400.0)
+    base = rng.uniform(0.25, 0.6, 3)
+    img = np.empty((3, H, W))
+    for c in range(3):
+        sky = 0.55 + 0.35 * (1.0 - v / horizon) * (c == 2) + 0.05 * np.sin(u / W * 3.0 + c)
+        road = base[c] + 0.05 * np.sin(u / 37.0 + v / 11.0 + c)
+        img[c] = np.where(ground, road, sky)
+    n_box = 24
+    keep = rng.random(n_box) >= missing
+    for b in range(n_box):
+        d = float(np.exp(rng.uniform(np.log(4.0), np.log(150.0))))
+        wpx = rng.uniform(0.5, 6.0) * f / d
+        hpx = rng.uniform(0.8, 8.0) * f / d
+        x0 = rng.uniform(-0.1 * W, 1.05 * W)
+        foot = horizon + 1.6 * f / d  # the box stands on the ground at depth d
+        colour = rng.uniform(0.05, 0.95, 3)
+        checker = rng.random() < 0.4
+        period = rng.integers(2, 6)
+        if not keep[b]:
+            continue
+        m = (u >= x0) & (u < x0 + wpx) & (v >= foot - hpx) & (v < foot) & ((depth == 0.0) | (depth > d))
+        if not m.any():
+            continue
+        depth = np.where(m, d, depth)
+        for c in range(3):
+            tex = colour[c]
+            if checker:
+                tex = tex + 0.15 * (((np.floor(u / period) + np.floor(v / period)) % 2) - 0.5)
+            img[c] = np.where(m, tex, img[c])
+    img = np.clip(img + rng.normal(0.0, 0.01, img.shape), 0.0, 1.0)
+    uniform = rng.random((H, W))
+    return img.astype(np.float32), depth.astype(np.float32), uniform.astype(np.float32)
+
+
+def keyframe_camera(height, width, seed=5, centre=(0.0, 0.0, 0.0), yaw_deg=0.0):
+    """Pinhole of keyframe(): fx = fy = 0.9 W, principal point at the centre."""
+    rng = np.random.default_rng(seed)
+    R_wc = yaw_matrix(yaw_deg + rng.uniform(-2.0, 2.0))
+    R, t = world_to_camera(R_wc, np.asarray(centre, np.float64))
+    return pinhole(int(width), int(height), 0.9 * width, R=R, t=t)

@@ -1,22 +1,24 @@
 // init.cu -- probabilistic initialisation of new anchors at a keyframe
 // (Sec. 3.3.1) and the voxel hash of the dynamic map expansion (Supp. B).
 //
-// k_init_saliency: 32x8 pixel tiles.  The channel mean Y of the tile and a
-// halo of the larger blur radius is staged in shared memory, blurred along
-// rows by both Gaussians in one pass, then along columns; the DoG and the
-// central-difference depth gradient are written as planes and the gradient's
-// minimum and maximum are reduced per block into two atomics (non-negative
-// FP32 bit patterns order like unsigned integers; the minimum is kept as the
-// maximum of the complement so that both words start at zero).  One launch
-// covers the keyframe and, when given, the rendered pair (blockIdx.z).
-// k_init_combine: P, and P_kf = max(P - P^, 0).
+// k_init_grad_minmax: the minimum and maximum of ||grad D|| over the
+// keyframe (and the rendered depth), reduced per block into two atomics
+// (non-negative FP32 bit patterns order like unsigned integers; the minimum
+// is kept as the maximum of the complement so that both words start at 0).
+// k_init_prob: 32x32 pixel tiles.  The channel mean Y of the tile and a halo
+// of the larger blur radius is staged in shared memory, blurred along rows by
+// both Gaussians in one pass, then along columns, each thread walking four
+// rows with a sliding window (the default radii 3 and 5 are compile-time
+// constants); the DoG, the normalised depth gradient and P of the keyframe and
+// of the render are combined in registers and only P (or P_kf) is written.
 // k_init_select: 3x3 non-maximum suppression from a staged tile, the draw,
 // the unprojection, the level and voxel key, and the insertion into the
 // table (64-bit compare-and-swap, linear probing bounded by the capacity);
 // each slot of a new voxel keeps its lowest claiming pixel (atomicMin).
-// k_init_count / k_init_scan / k_init_emit: the pixels that own a new voxel
-// are numbered in raster order (block counts, one scan, warp-ballot ranks)
-// and write the anchor records; their slots are then settled.
+// k_init_count / k_init_emit: the pixels that own a new voxel are numbered in
+// raster order: 1024-pixel blocks count them, and each emitting block sums
+// the counts of the blocks before it, ranks its own pixels and writes the
+// anchor records; their slots are then settled.
 #include <algorithm>
 #include <climits>
 #include <cstdint>
@@ -47,59 +49,27 @@ __device__ __forceinline__ unsigned long long voxel_key(int l, int ix, int iy, i
 
 __device__ __forceinline__ bool idx_in_range(int v) { return v >= -kIdxBias && v < kIdxBias; }
 
-__global__ void __launch_bounds__(kThreads) k_init_saliency(const float *__restrict__ img,
-                                                            const float *__restrict__ depth,
-                                                            const float *__restrict__ img_r,
-                                                            const float *__restrict__ depth_r, int W, int H,
-                                                            InitBlur bw, float *__restrict__ dog,
-                                                            float *__restrict__ grad, unsigned *__restrict__ minmax) {
-    __shared__ float ys[kTH + 2 * kR][kTW + 2 * kR];
-    __shared__ float hb[2][kTH + 2 * kR][kTW];
+__device__ __forceinline__ float depth_grad(const float *__restrict__ D, int W, int H, int x, int y) {
+    const long long row = (long long)y * W;
+    const float gx = (D[row + min(x + 1, W - 1)] - D[row + max(x - 1, 0)]) * 0.5f;
+    const float gy = (D[(long long)min(y + 1, H - 1) * W + x] - D[(long long)max(y - 1, 0) * W + x]) * 0.5f;
+    return sqrtf(gx * gx + gy * gy);
+}
+
+// One block per row (strided): threads walk the row, so no pixel index is divided.
+__global__ void __launch_bounds__(kThreads) k_init_grad_minmax(const float *__restrict__ depth,
+                                                               const float *__restrict__ depth_r, int W, int H,
+                                                               unsigned *__restrict__ minmax) {
     __shared__ unsigned red[2][kThreads / 32];
-    const int z = blockIdx.z;
-    const float *I = z ? img_r : img;
+    const int z = blockIdx.y;
     const float *D = z ? depth_r : depth;
-    const long long npx = (long long)W * H;
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * kTH, R = bw.R;
-    const int rows = kTH + 2 * R, cols = kTW + 2 * R;
-    // channel mean of the tile and its halo, edges replicated
-    for (int i = threadIdx.x; i < rows * cols; i += kThreads) {
-        const int r = i / cols, c = i % cols;
-        const int y = min(max(y0 - R + r, 0), H - 1), x = min(max(x0 - R + c, 0), W - 1);
-        const long long p = (long long)y * W + x;
-        ys[r][c] = (I[p] + I[npx + p] + I[2 * npx + p]) / 3.0f;
-    }
-    __syncthreads();
-    // rows: both Gaussians
-    for (int i = threadIdx.x; i < rows * kTW; i += kThreads) {
-        const int r = i / kTW, c = i % kTW + R;
-        float a = bw.w1[0] * ys[r][c], b = bw.w2[0] * ys[r][c];
-        for (int k = 1; k <= bw.r1; ++k) a += bw.w1[k] * (ys[r][c - k] + ys[r][c + k]);
-        for (int k = 1; k <= bw.r2; ++k) b += bw.w2[k] * (ys[r][c - k] + ys[r][c + k]);
-        hb[0][r][c - R] = a;
-        hb[1][r][c - R] = b;
-    }
-    __syncthreads();
-    const int tx = threadIdx.x % kTW, ty = threadIdx.x / kTW;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool in = x < W && y < H;
-    unsigned gbits = 0u;
-    if (in) {
-        const int r = ty + R;
-        float a = bw.w1[0] * hb[0][r][tx], b = bw.w2[0] * hb[1][r][tx];
-        for (int k = 1; k <= bw.r1; ++k) a += bw.w1[k] * (hb[0][r - k][tx] + hb[0][r + k][tx]);
-        for (int k = 1; k <= bw.r2; ++k) b += bw.w2[k] * (hb[1][r - k][tx] + hb[1][r + k][tx]);
-        const long long p = (long long)y * W + x;
-        dog[z * npx + p] = fminf(bw.scale * fabsf(a - b), 1.0f);
-        const long long row = (long long)y * W;
-        const float gx = (D[row + min(x + 1, W - 1)] - D[row + max(x - 1, 0)]) * 0.5f;
-        const float gy = (D[(long long)min(y + 1, H - 1) * W + x] - D[(long long)max(y - 1, 0) * W + x]) * 0.5f;
-        const float g = sqrtf(gx * gx + gy * gy);
-        grad[z * npx + p] = g;
-        gbits = __float_as_uint(g);
-    }
-    // block minimum (as the maximum of the complement) and maximum of the gradient
-    unsigned lo = in ? ~gbits : 0u, hi = gbits;
+    unsigned lo = 0u, hi = 0u;
+    for (int y = blockIdx.x; y < H; y += gridDim.x)
+        for (int x = threadIdx.x; x < W; x += kThreads) {
+            const unsigned g = __float_as_uint(depth_grad(D, W, H, x, y));
+            lo = max(lo, ~g);
+            hi = max(hi, g);
+        }
     lo = __reduce_max_sync(0xffffffffu, lo);
     hi = __reduce_max_sync(0xffffffffu, hi);
     if ((threadIdx.x & 31) == 0) {
@@ -117,21 +87,115 @@ __global__ void __launch_bounds__(kThreads) k_init_saliency(const float *__restr
     }
 }
 
-__device__ __forceinline__ float init_p(const float *dog, const float *grad, const unsigned *minmax, int z,
-                                        long long npx, long long i, float lambda) {
+constexpr int kPT = 32, kPH = 16;                        // probability tile: 32 x 16 pixels
+constexpr int kRowsPerThread = kPH / (kThreads / kPT);  // 2 consecutive rows per thread
+
+// P of one map for the thread's pixels (rows kRowsPerThread ty + j, column
+// tx of the tile).  R1, R2 > 0: compile-time radii; 0: the runtime ones.
+template <int R1, int R2, int RS>
+__device__ __forceinline__ void tile_p(const float *__restrict__ I, const float *__restrict__ D, int W, int H,
+                                       int x0, int y0, const InitBlur &bw, const unsigned *__restrict__ minmax, int z,
+                                       float lambda, float (*ys)[kPT + 2 * RS], float (*hb)[kPH + 2 * RS][kPT],
+                                       float (*ds)[kPT + 2], float *pv) {
+    const int r1 = R1 ? R1 : bw.r1, r2 = R2 ? R2 : bw.r2, R = R1 ? RS : bw.R;
+    const long long npx = (long long)W * H;
+    const int nx = kPT + 2 * R, ny = kPH + 2 * R;
+    constexpr float kThird = 1.0f / 3.0f;
+    // channel mean with a halo of R and the depth with a halo of 1, edges replicated
+    for (int i = threadIdx.x; i < ny * nx; i += kThreads) {
+        const int r = i / nx, c = i % nx;
+        const int y = min(max(y0 - R + r, 0), H - 1), x = min(max(x0 - R + c, 0), W - 1);
+        const long long p = (long long)y * W + x;
+        ys[r][c] = (I[p] + I[npx + p] + I[2 * npx + p]) * kThird;
+    }
+    for (int i = threadIdx.x; i < (kPH + 2) * (kPT + 2); i += kThreads) {
+        const int r = i / (kPT + 2), c = i % (kPT + 2);
+        const int y = min(max(y0 - 1 + r, 0), H - 1), x = min(max(x0 - 1 + c, 0), W - 1);
+        ds[r][c] = D[(long long)y * W + x];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < ny * kPT; i += kThreads) {
+        const int r = i / kPT, c = i % kPT + R;
+        float a = bw.w1[0] * ys[r][c], b = bw.w2[0] * ys[r][c];
+        #pragma unroll
+        for (int k = 1; k <= (R1 ? R1 : kR); ++k)
+            if (R1 || k <= r1) a += bw.w1[k] * (ys[r][c - k] + ys[r][c + k]);
+        #pragma unroll
+        for (int k = 1; k <= (R2 ? R2 : kR); ++k)
+            if (R2 || k <= r2) b += bw.w2[k] * (ys[r][c - k] + ys[r][c + k]);
+        hb[0][r][c - R] = a;
+        hb[1][r][c - R] = b;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % kPT, ty = threadIdx.x / kPT, o0 = kRowsPerThread * ty;
+    float b1[kRowsPerThread], b2[kRowsPerThread];
+    if (R1 && R2) {
+        // sliding windows down the column: rows o0 + R - r .. o0 + 3 + R + r of hb
+        float c1[kRowsPerThread + 2 * (R1 ? R1 : 1)], c2[kRowsPerThread + 2 * (R2 ? R2 : 1)];
+        #pragma unroll
+        for (int k = 0; k < kRowsPerThread + 2 * R1; ++k) c1[k] = hb[0][o0 + R - R1 + k][tx];
+        #pragma unroll
+        for (int k = 0; k < kRowsPerThread + 2 * R2; ++k) c2[k] = hb[1][o0 + R - R2 + k][tx];
+        #pragma unroll
+        for (int j = 0; j < kRowsPerThread; ++j) {
+            float a = bw.w1[0] * c1[j + R1], b = bw.w2[0] * c2[j + R2];
+            #pragma unroll
+            for (int k = 1; k <= R1; ++k) a += bw.w1[k] * (c1[j + R1 - k] + c1[j + R1 + k]);
+            #pragma unroll
+            for (int k = 1; k <= R2; ++k) b += bw.w2[k] * (c2[j + R2 - k] + c2[j + R2 + k]);
+            b1[j] = a;
+            b2[j] = b;
+        }
+    } else {
+        #pragma unroll
+        for (int j = 0; j < kRowsPerThread; ++j) {
+            const int r = o0 + j + R;
+            float a = bw.w1[0] * hb[0][r][tx], b = bw.w2[0] * hb[1][r][tx];
+            for (int k = 1; k <= r1; ++k) a += bw.w1[k] * (hb[0][r - k][tx] + hb[0][r + k][tx]);
+            for (int k = 1; k <= r2; ++k) b += bw.w2[k] * (hb[1][r - k][tx] + hb[1][r + k][tx]);
+            b1[j] = a;
+            b2[j] = b;
+        }
+    }
     const float lo = __uint_as_float(~minmax[2 * z]), hi = __uint_as_float(minmax[2 * z + 1]);
-    const float gn = hi > lo ? (grad[z * npx + i] - lo) / (hi - lo) : 0.0f;
-    return fminf(lambda * dog[z * npx + i] + (1.0f - lambda) * gn, 1.0f);
+    const int x = x0 + tx;
+    #pragma unroll
+    for (int j = 0; j < kRowsPerThread; ++j) {
+        const int y = y0 + o0 + j;
+        float p = 0.0f;
+        if (x < W && y < H) {
+            const float dog = fminf(bw.scale * fabsf(b1[j] - b2[j]), 1.0f);
+            const int r = o0 + j + 1, c = tx + 1;
+            const float gx = (ds[r][c + 1] - ds[r][c - 1]) * 0.5f, gy = (ds[r + 1][c] - ds[r - 1][c]) * 0.5f;
+            const float gn = hi > lo ? (sqrtf(gx * gx + gy * gy) - lo) / (hi - lo) : 0.0f;
+            p = fminf(lambda * dog + (1.0f - lambda) * gn, 1.0f);
+        }
+        pv[j] = z ? fmaxf(pv[j] - p, 0.0f) : p;  // P_kf = max(P - P^, 0)
+    }
 }
 
-__global__ void k_init_combine(const float *__restrict__ dog, const float *__restrict__ grad,
-                               const unsigned *__restrict__ minmax, long long npx, int rendered, float lambda,
-                               float *__restrict__ prob) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= npx) return;
-    float p = init_p(dog, grad, minmax, 0, npx, i, lambda);
-    if (rendered) p = fmaxf(p - init_p(dog, grad, minmax, 1, npx, i, lambda), 0.0f);
-    prob[i] = p;
+template <int R1, int R2>
+__global__ void __launch_bounds__(kThreads) k_init_prob(const float *__restrict__ img, const float *__restrict__ depth,
+                                                        const float *__restrict__ img_r,
+                                                        const float *__restrict__ depth_r, int W, int H,
+                                                        const __grid_constant__ InitBlur bw,
+                                                        const unsigned *__restrict__ minmax, float lambda,
+                                                        float *__restrict__ prob) {
+    constexpr int RS = R1 && R2 ? (R1 > R2 ? R1 : R2) : kR;
+    __shared__ float ys[kPH + 2 * RS][kPT + 2 * RS];
+    __shared__ float hb[2][kPH + 2 * RS][kPT];
+    __shared__ float ds[kPH + 2][kPT + 2];
+    const int x0 = blockIdx.x * kPT, y0 = blockIdx.y * kPH;
+    float pv[kRowsPerThread];
+    tile_p<R1, R2, RS>(img, depth, W, H, x0, y0, bw, minmax, 0, lambda, ys, hb, ds, pv);
+    if (img_r) {
+        __syncthreads();  // the tile's shared arrays are reused for the render
+        tile_p<R1, R2, RS>(img_r, depth_r, W, H, x0, y0, bw, minmax, 1, lambda, ys, hb, ds, pv);
+    }
+    const int x = x0 + threadIdx.x % kPT, yb = y0 + kRowsPerThread * (threadIdx.x / kPT);
+    #pragma unroll
+    for (int j = 0; j < kRowsPerThread; ++j)
+        if (x < W && yb + j < H) prob[(long long)(yb + j) * W + x] = pv[j];
 }
 
 __global__ void __launch_bounds__(kThreads) k_init_select(const float *__restrict__ prob,
@@ -217,90 +281,103 @@ __device__ __forceinline__ bool owns_new(const int *cand, const int *owner, long
     return s >= 0 && owner[s] == (int)i;
 }
 
-__global__ void __launch_bounds__(kThreads) k_init_count(const int *__restrict__ cand, const int *__restrict__ owner,
-                                                         long long npx, int *__restrict__ bsum) {
-    const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
-    const int c = __syncthreads_count(owns_new(cand, owner, npx, i));
-    if (threadIdx.x == 0) bsum[blockIdx.x] = c;
+constexpr int kPx = 4 * kThreads;  // pixels per counting / emitting block, four consecutive per thread
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *red) {
+    #pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T t = 0;
+    #pragma unroll
+    for (int i = 0; i < kThreads / 32; ++i) t += red[i];
+    return t;
 }
 
-// Exclusive scan of the block counts in one block; count (the anchors in
-// use) is the base and receives the new total.
-__global__ void __launch_bounds__(1024) k_init_scan(const int *__restrict__ bsum, int nb, long long *__restrict__ boff,
-                                                    long long *__restrict__ count) {
-    __shared__ long long wsum[32];
-    __shared__ long long carry;
-    if (threadIdx.x == 0) carry = *count;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < nb; base += 1024) {
-        const int i = base + threadIdx.x;
-        const long long v = i < nb ? bsum[i] : 0;
-        long long s = v;
-        #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const long long u = __shfl_up_sync(0xffffffffu, s, off);
-            if (lane >= off) s += u;
-        }
-        if (lane == 31) wsum[warp] = s;
-        __syncthreads();
-        if (warp == 0) {
-            long long w = wsum[lane];
-            #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const long long u = __shfl_up_sync(0xffffffffu, w, off);
-                if (lane >= off) w += u;
-            }
-            wsum[lane] = w;
-        }
-        __syncthreads();
-        const long long incl = s + (warp ? wsum[warp - 1] : 0);
-        if (i < nb) boff[i] = carry + incl - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry += incl;
-        __syncthreads();
+__global__ void __launch_bounds__(kThreads) k_init_count(const int *__restrict__ cand, const int *__restrict__ owner,
+                                                         long long npx, int *__restrict__ bsum,
+                                                         const long long *__restrict__ count,
+                                                         long long *__restrict__ base) {
+    __shared__ int red[kThreads / 32];
+    const long long i0 = (long long)blockIdx.x * kPx + 4 * threadIdx.x;
+    int c = 0;
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) c += owns_new(cand, owner, npx, i0 + j);
+    c = block_sum(c, red);
+    if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = c;
+        if (blockIdx.x == 0) *base = *count;  // the anchors already in use
     }
-    if (threadIdx.x == 0) *count = carry;
 }
 
 __global__ void __launch_bounds__(kThreads) k_init_emit(const int *__restrict__ cand, int *__restrict__ owner,
                                                         const unsigned long long *__restrict__ keys,
                                                         int *__restrict__ ids, long long npx,
-                                                        const long long *__restrict__ boff,
-                                                        const __grid_constant__ InitLod lod,
-                                                        float *__restrict__ pos, int *__restrict__ level,
-                                                        int *__restrict__ pixel, long long ld,
+                                                        const int *__restrict__ bsum, const long long *__restrict__ base,
+                                                        const __grid_constant__ InitLod lod, float *__restrict__ pos,
+                                                        int *__restrict__ level, int *__restrict__ pixel,
+                                                        long long ld, long long *__restrict__ count,
                                                         int *__restrict__ status) {
-    __shared__ int wcount[kThreads / 32];
-    const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
-    // only a voxel's owner settles its slot, so the others' tests are unaffected
-    const bool f = owns_new(cand, owner, npx, i);
-    const unsigned ballot = __ballot_sync(0xffffffffu, f);
+    __shared__ long long red[kThreads / 32];
+    __shared__ int wsum[kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) wcount[warp] = __popc(ballot);
-    __syncthreads();
-    if (!f) return;
-    int woff = 0;
-    for (int k = 0; k < warp; ++k) woff += wcount[k];
-    const long long id = boff[blockIdx.x] + woff + __popc(ballot & ((1u << lane) - 1u));
-    const int s = cand[i];
-    const unsigned long long key = keys[s];
-    const int l = (int)(key >> 60);
-    const int ix = (int)((key >> 40) & 0xfffffu) - kIdxBias, iy = (int)((key >> 20) & 0xfffffu) - kIdxBias,
-              iz = (int)(key & 0xfffffu) - kIdxBias;
-    if (id < ld) {
-        const float e = lod.voxel[l];
-        pos[id] = (float)ix * e;
-        pos[ld + id] = (float)iy * e;
-        pos[2 * ld + id] = (float)iz * e;
-        level[id] = l;
-        pixel[id] = (int)i;
-        ids[s] = (int)id;
-    } else {
-        ids[s] = -1;
-        if (status) atomicOr(status, 1 << GS_ERR_CAPACITY);
+    // the new anchors of all earlier blocks
+    long long before = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kThreads) before += bsum[b];
+    before = block_sum(before, red);
+    // only a voxel's owner settles its slot, so the others' tests are unaffected
+    const long long i0 = (long long)blockIdx.x * kPx + 4 * threadIdx.x;
+    bool f[4];
+    int c = 0;
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        f[j] = owns_new(cand, owner, npx, i0 + j);
+        c += f[j];
     }
-    owner[s] = -1;
+    // exclusive scan of the per-thread counts over the block
+    int incl = c;
+    #pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int woff = 0, total = 0;
+    #pragma unroll
+    for (int k = 0; k < kThreads / 32; ++k) {
+        woff += k < warp ? wsum[k] : 0;
+        total += wsum[k];
+    }
+    const long long b0 = *base;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *count = b0 + before + total;
+    long long id = b0 + before + woff + incl - c;
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (!f[j]) continue;
+        const long long i = i0 + j;
+        const int s = cand[i];
+        const unsigned long long key = keys[s];
+        const int l = (int)(key >> 60);
+        const int ix = (int)((key >> 40) & 0xfffffu) - kIdxBias, iy = (int)((key >> 20) & 0xfffffu) - kIdxBias,
+                  iz = (int)(key & 0xfffffu) - kIdxBias;
+        if (id < ld) {
+            const float e = lod.voxel[l];
+            pos[id] = (float)ix * e;
+            pos[ld + id] = (float)iy * e;
+            pos[2 * ld + id] = (float)iz * e;
+            level[id] = l;
+            pixel[id] = (int)i;
+            ids[s] = (int)id;
+        } else {
+            ids[s] = -1;
+            if (status) atomicOr(status, 1 << GS_ERR_CAPACITY);
+        }
+        owner[s] = -1;
+        ++id;
+    }
 }
 
 __global__ void k_voxel_lookup(const unsigned long long *__restrict__ keys, const int *__restrict__ ids, long long cap,
@@ -335,36 +412,26 @@ __global__ void k_voxel_reset(unsigned long long *__restrict__ keys, int *__rest
 
 struct InitWs {
     unsigned *minmax;
-    float *dog, *grad;
+    long long *base;
     int *cand, *bsum;
-    long long *boff;
 };
 
 InitWs carve(void *ws, int W, int H) {
-    const size_t npx = (size_t)W * H, nb = (npx + kThreads - 1) / kThreads;
+    const size_t npx = (size_t)W * H;
     unsigned char *b = (unsigned char *)ws;
     InitWs w;
-    size_t off = 0;
-    w.minmax = (unsigned *)(b + off);
-    off += 256;
-    w.dog = (float *)(b + off);
-    off += align_up(sizeof(float) * 2 * npx, 256);
-    w.grad = (float *)(b + off);
-    off += align_up(sizeof(float) * 2 * npx, 256);
-    w.cand = (int *)(b + off);
-    off += align_up(sizeof(int) * npx, 256);
-    w.bsum = (int *)(b + off);
-    off += align_up(sizeof(int) * nb, 256);
-    w.boff = (long long *)(b + off);
+    w.minmax = (unsigned *)b;
+    w.base = (long long *)(b + 64);
+    w.cand = (int *)(b + 256);
+    w.bsum = (int *)(b + 256 + align_up(sizeof(int) * npx, 256));
     return w;
 }
 
 }  // namespace
 
 size_t init_workspace_bytes(int W, int H) {
-    const size_t npx = (size_t)W * H, nb = (npx + kThreads - 1) / kThreads;
-    return 256 + 2 * align_up(sizeof(float) * 2 * npx, 256) + align_up(sizeof(int) * npx, 256) +
-           align_up(sizeof(int) * nb, 256) + align_up(sizeof(long long) * nb, 256);
+    const size_t npx = (size_t)W * H, nb = (npx + kPx - 1) / kPx;
+    return 256 + align_up(sizeof(int) * npx, 256) + align_up(sizeof(int) * nb, 256);
 }
 
 cudaError_t launch_init_probability(const float *img, const float *depth, const float *img_r, const float *depth_r,
@@ -374,11 +441,13 @@ cudaError_t launch_init_probability(const float *img, const float *depth, const 
     const int nimg = img_r ? 2 : 1;
     cudaError_t e = cudaMemsetAsync(w.minmax, 0, 4 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)ceil_div(W, kTW), (unsigned)ceil_div(H, kTH), (unsigned)nimg);
-    k_init_saliency<<<grid, kThreads, 0, s>>>(img, depth, img_r, depth_r, W, H, bw, w.dog, w.grad, w.minmax);
-    const long long npx = (long long)W * H;
-    k_init_combine<<<(unsigned)ceil_div(npx, 256ll), 256, 0, s>>>(w.dog, w.grad, w.minmax, npx, nimg == 2, lambda,
-                                                                    prob);
+    const dim3 mgrid((unsigned)std::min(H, 592), (unsigned)nimg);
+    k_init_grad_minmax<<<mgrid, kThreads, 0, s>>>(depth, depth_r, W, H, w.minmax);
+    const dim3 grid((unsigned)ceil_div(W, kPT), (unsigned)ceil_div(H, kPH));
+    if (bw.r1 == 3 && bw.r2 == 5)
+        k_init_prob<3, 5><<<grid, kThreads, 0, s>>>(img, depth, img_r, depth_r, W, H, bw, w.minmax, lambda, prob);
+    else
+        k_init_prob<0, 0><<<grid, kThreads, 0, s>>>(img, depth, img_r, depth_r, W, H, bw, w.minmax, lambda, prob);
     return cudaGetLastError();
 }
 
@@ -388,13 +457,13 @@ cudaError_t launch_init_insert(const float *prob, const float *uniform, const fl
                                uint8_t *selected, int *status, void *ws, cudaStream_t s) {
     InitWs w = carve(ws, W, H);
     const long long npx = (long long)W * H;
-    const int nb = (int)ceil_div(npx, (long long)kThreads);
+    const int nb = (int)ceil_div(npx, (long long)kPx);
     const dim3 grid((unsigned)ceil_div(W, kTW), (unsigned)ceil_div(H, kTH));
     k_init_select<<<grid, kThreads, 0, s>>>(prob, uniform, depth, W, H, cam, lod, keys, owner, cap, w.cand, selected,
                                             status);
-    k_init_count<<<nb, kThreads, 0, s>>>(w.cand, owner, npx, w.bsum);
-    k_init_scan<<<1, 1024, 0, s>>>(w.bsum, nb, w.boff, count);
-    k_init_emit<<<nb, kThreads, 0, s>>>(w.cand, owner, keys, ids, npx, w.boff, lod, pos, level, pixel, ld, status);
+    k_init_count<<<nb, kThreads, 0, s>>>(w.cand, owner, npx, w.bsum, count, w.base);
+    k_init_emit<<<nb, kThreads, 0, s>>>(w.cand, owner, keys, ids, npx, w.bsum, w.base, lod, pos, level, pixel, ld,
+                                        count, status);
     return cudaGetLastError();
 }
 

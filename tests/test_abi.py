@@ -116,3 +116,43 @@ def test_segment_workspace_sizes():
     assert L.gs_segment_workspace_size(1000, 100, C.byref(n)) == 1   # not a power of two
     assert L.gs_segment_workspace_size(1000, 16, C.byref(n)) == 1    # below 32
     assert L.gs_segment_workspace_size_items(-1, C.byref(n)) == 1
+
+
+def test_init_arguments_rejected_on_host():
+    """The initialisation entry points refuse bad sizes, blur widths, level tables and
+    table capacities before touching the device."""
+    from paper_2606_30436_b300 import spawn
+    L = spawn._lib()
+    n = C.c_size_t()
+    assert L.gs_init_workspace_size(1280, 720, C.byref(n)) == 0 and n.value >= 4 * 1280 * 720
+    assert L.gs_init_workspace_size(0, 720, C.byref(n)) == 1
+    assert L.gs_init_workspace_size(1 << 16, 1 << 16, C.byref(n)) == 1  # pixel index beyond int32
+    ws = C.c_void_p(256)
+    big = n.value
+    ok = spawn.init_config()
+    args = (C.c_void_p(16), C.c_void_p(32), None, None, 64, 48)
+    for bad in (spawn.init_config(sigma1=6.0),   # radius ceil(18) beyond 16
+                spawn.init_config(sigma2=0.0), spawn.init_config(lam=1.5), spawn.init_config(scale=0.0)):
+        assert L.gs_init_probability(*args, C.byref(bad), C.c_void_p(48), ws, big, None) == 1
+    # rendered pair given halfway, misaligned output, small workspace
+    assert L.gs_init_probability(C.c_void_p(16), C.c_void_p(32), C.c_void_p(64), None, 64, 48, C.byref(ok),
+                                 C.c_void_p(48), ws, big, None) == 1
+    assert L.gs_init_probability(*args, C.byref(ok), C.c_void_p(52), ws, big, None) == 1
+    assert L.gs_init_probability(*args, C.byref(ok), C.c_void_p(48), ws, 16, None) == 1
+    cam = gs.make_camera(scenes.pinhole(64, 48, 60.0))
+    good_table = spawn.VoxelTable(16, 32, 48, 1024)
+    anchors = spawn.AnchorSet(16, 32, 48, 64, 100)
+    for table in (spawn.VoxelTable(16, 32, 48, 1000),     # not a power of two
+                  spawn.VoxelTable(16, 32, 48, 512),      # below 1024
+                  spawn.VoxelTable(None, 32, 48, 1024)):
+        assert L.gs_init_insert(C.c_void_p(16), C.c_void_p(32), C.c_void_p(48), C.byref(cam), C.byref(ok),
+                                C.byref(table), C.byref(anchors), None, None, ws, big, None) == 1
+    for cfg in (spawn.init_config(voxel=(0.1, 0.25), max_dist=(10.0, 5.0)),   # bands not increasing
+                spawn.init_config(voxel=(0.0,), max_dist=(10.0,))):
+        assert L.gs_init_insert(C.c_void_p(16), C.c_void_p(32), C.c_void_p(48), C.byref(cam), C.byref(cfg),
+                                C.byref(good_table), C.byref(anchors), None, None, ws, big, None) == 1
+    bad_count = spawn.AnchorSet(16, 32, 48, 60, 100)  # count not 8-byte aligned
+    assert L.gs_init_insert(C.c_void_p(16), C.c_void_p(32), C.c_void_p(48), C.byref(cam), C.byref(ok),
+                            C.byref(good_table), C.byref(bad_count), None, None, ws, big, None) == 1
+    assert L.gs_voxel_lookup(C.byref(good_table), C.c_void_p(16), 5, 4, C.c_void_p(32), None) == 1  # ld < n
+    assert L.gs_voxel_table_reset(C.byref(spawn.VoxelTable(16, 32, 48, 3000)), None) == 1

@@ -107,6 +107,9 @@ def lib():
         L.or_init_select.argtypes = [i32, i32, vp, vp, vp, C.POINTER(_Camera), d, i32, vp, vp, i64, vp, i64,
                                      vp, vp, vp, vp, vp, vp, d, d]
         L.or_init_select.restype = i64
+        L.or_anchor_num_weights.restype = i32
+        L.or_anchor_decode.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d]
+        L.or_anchor_decode_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     return _lib
 
 
@@ -441,6 +444,59 @@ def init_select(prob, uniform, depth, cam, cfg: InitCfg = InitCfg(), old_keys=No
     k = min(n, cap)
     return dict(keys=keys[:k], pos=pos[:k], level=level[:k], pixel=pixel[:k], n_new=n, selected=sel,
                 uncertain=unc)
+
+
+# --------------------------------------------------------------------------
+# Scaffold-GS anchors (Supp. D.1, D.3; readings R25-R29)
+# --------------------------------------------------------------------------
+
+ANCHOR_K = 10
+ANCHOR_F = 32
+
+
+def anchor_num_weights():
+    return lib().or_anchor_num_weights()
+
+
+def _anchor_args(A):
+    n = len(A["level"])
+    return (n, _f64(A["pos"], (n, 3)), np.ascontiguousarray(A["level"], np.int32), _f64(A["feat"], (n, ANCHOR_F)),
+            _f64(A["log_l"], (n, 3)), _f64(A["offs"], (n, ANCHOR_K, 3)))
+
+
+def anchor_decode(A, w, cam_centre, max_dist, tol=1e-6):
+    """Decoded Gaussians of anchors A (dict pos, level, feat, log_l, offs): rows [10 n][14], keep and unsure."""
+    n, pos, lv, feat, log_l, offs = _anchor_args(A)
+    w, cc, md = _f64(w), _f64(cam_centre, (3,)), _f64(max_dist)
+    rows = np.zeros((ANCHOR_K * n, 14))
+    keep, unsure = np.zeros(ANCHOR_K * n, np.uint8), np.zeros(ANCHOR_K * n, np.uint8)
+    lib().or_anchor_decode(n, _ptr(pos), _ptr(lv), _ptr(feat), _ptr(log_l), _ptr(offs), _ptr(w), _ptr(cc), _ptr(md),
+                           _ptr(rows), _ptr(keep), _ptr(unsure), float(tol))
+    return rows, keep.astype(bool), unsure.astype(bool)
+
+
+def anchor_decode_backward(A, w, cam_centre, max_dist, g_rows):
+    """Gradients (feat, log_l, offs, w) of a loss with dL/drows = g_rows."""
+    n, pos, lv, feat, log_l, offs = _anchor_args(A)
+    w, cc, md, g = _f64(w), _f64(cam_centre, (3,)), _f64(max_dist), _f64(g_rows, (ANCHOR_K * n, 14))
+    gf, gl, go, gw = np.zeros_like(feat), np.zeros_like(log_l), np.zeros_like(offs), np.zeros_like(w)
+    lib().or_anchor_decode_backward(n, _ptr(pos), _ptr(lv), _ptr(feat), _ptr(log_l), _ptr(offs), _ptr(w), _ptr(cc),
+                                    _ptr(md), _ptr(g), _ptr(gf), _ptr(gl), _ptr(go), _ptr(gw))
+    return gf, gl, go, gw
+
+
+def rows_to_params(rows):
+    """Decoded rows [m][14] as SH-degree-0 Gaussian parameters for forward / loss_and_grads."""
+    m = rows.shape[0]
+    return dict(means=rows[:, 0:3].copy(), log_scales=rows[:, 3:6].copy(), quats=rows[:, 6:10].copy(),
+                opacity_logits=rows[:, 10].copy(), sh=rows[:, 11:14].reshape(m, 1, 3).copy(), sh_degree=0)
+
+
+def grads_to_rows(g):
+    """Parameter gradients of loss_and_grads back to the row layout."""
+    m = g["opacity_logits"].shape[0]
+    return np.concatenate([g["means"], g["log_scales"], g["quats"], g["opacity_logits"].reshape(m, 1),
+                           g["sh"].reshape(m, 3)], axis=1)
 
 
 # --------------------------------------------------------------------------

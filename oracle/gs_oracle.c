@@ -19,7 +19,8 @@
  * cited 3D Gaussian splatting work, written here from the mathematics:
  *   R1 camera: x_c = R x_w + t, x right, y down, z forward; u = fx x/z + cx;
  *      pixel (i, j) samples (i + 0.5, j + 0.5).
- *   R2 cull z <= near (0.2) and empty tile rectangles.
+ *   R2 cull z <= near (0.2), empty tile rectangles and opacity below alpha_min
+ *      (FP32 logit below the FP32 logit of alpha_min: such a Gaussian never blends).
  *   R3 Sigma = R(q) S S^T R(q)^T, S = diag(exp(log_scale)); EWA
  *      Sigma' = J W Sigma W^T J^T + 0.3 I with J evaluated at x/z, y/z clamped
  *      to 1.3 tan(fov/2); the clamp has zero derivative on the clamped side.
@@ -59,6 +60,22 @@
  *   R24 voxel idx = floor(x / eps_l), anchor p = idx eps_l (the paper's
  *       formula); one anchor per (l, idx); new anchors numbered in raster
  *       order of the first pixel reaching their voxel.
+ * Scaffold-GS anchors (Supp. D.1 decoding, Supp. D.3 LoD mask) read:
+ *   R25 one decoder for the K = 10 Gaussians of an anchor: input (f, dir,
+ *       log(1 + d)) (32 + 3 + 1), hidden layer of 64 with ReLU, 14 K linear
+ *       outputs, per Gaussian (colour 3, opacity 1, rotation 4, scale 3,
+ *       offset 3).
+ *   R26 colour = sigmoid, opacity = tanh (Gaussians with opacity <= 0 are
+ *       dropped, as in Scaffold-GS), rotation = (1, 0, 0, 0) + output
+ *       (normalised by the rasteriser), scale factor = sigmoid, offset raw.
+ *   R27 mu = p + (O_k + dO_k) * l, s = l * ds_k (l = exp of the stored
+ *       log-scale), opacity masked by the LoD band of the anchor's level:
+ *       [max_dist[l-1], max_dist[l]) (0 below the first level, R23 bands).
+ *   R28 decoded Gaussians enter the rasteriser as SH-degree-0 Gaussians:
+ *       sh0 = (c - 1/2) / Y00, opacity logit = log(a / (1 - a)); dropped ones
+ *       get logit -30 and are culled (R2).
+ *   R29 anchor positions stay fixed; f, the log-scale, the offsets and the
+ *       decoder's weights are optimised.
  * Parity pins for each function are in the tests; every function below is
  * pinned (closed forms, brute force, library routines, finite differences).
  */
@@ -232,6 +249,9 @@ void or_project(const or_params *p, const or_camera *cam, const or_cfg *cfg, or_
         const double x = pc[0], y = pc[1], z = pc[2];
 
         int culled = cfg->fp32_positions ? (zc32 <= (float)cfg->near_z) : (z <= cfg->near_z);
+        /* R2: a Gaussian whose opacity is below alpha_min can never blend under R8; the
+           test is on the FP32 logit against the FP32 logit of alpha_min */
+        culled |= (float)p->opacity_logits[i] < (float)log(cfg->alpha_min / (1.0 - cfg->alpha_min));
         if (culled) continue;
 
         /* 3D covariance */
@@ -1283,4 +1303,143 @@ int64_t or_init_select(int32_t H, int32_t W, const double *prob, const double *u
         }
     free(keys);
     return n_new;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Scaffold-GS anchor decoding (Supp. D.1, D.3; readings R25-R29)            */
+/* ------------------------------------------------------------------------ */
+
+#define OR_ANC_K 10
+#define OR_ANC_F 32
+#define OR_ANC_IN 36
+#define OR_ANC_H 64
+#define OR_ANC_OUT (14 * OR_ANC_K)
+#define OR_ANC_W1 0
+#define OR_ANC_B1 (OR_ANC_W1 + OR_ANC_H * OR_ANC_IN)
+#define OR_ANC_W2 (OR_ANC_B1 + OR_ANC_H)
+#define OR_ANC_B2 (OR_ANC_W2 + OR_ANC_OUT * OR_ANC_H)
+#define OR_ANC_NW (OR_ANC_B2 + OR_ANC_OUT)
+#define OR_Y00 0.28209479177387814 /* 1 / (2 sqrt(pi)) */
+
+int32_t or_anchor_num_weights(void) { return OR_ANC_NW; }
+
+static double sigm(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+/* Decoder input, hidden pre-activations and the 14 K outputs of anchor i. */
+static void anchor_mlp(const double *pos, const double *feat, const double *w, const double cc[3], double *x,
+                       double *pre, double *z, double *dist) {
+    double v[3];
+    for (int a = 0; a < 3; ++a) v[a] = pos[a] - cc[a];
+    const double d = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int c = 0; c < OR_ANC_F; ++c) x[c] = feat[c];
+    for (int a = 0; a < 3; ++a) x[OR_ANC_F + a] = v[a] / d;
+    x[OR_ANC_F + 3] = log1p(d);
+    for (int o = 0; o < OR_ANC_H; ++o) {
+        double s = w[OR_ANC_B1 + o];
+        for (int c = 0; c < OR_ANC_IN; ++c) s += w[OR_ANC_W1 + o * OR_ANC_IN + c] * x[c];
+        pre[o] = s;
+    }
+    for (int o = 0; o < OR_ANC_OUT; ++o) {
+        double s = w[OR_ANC_B2 + o];
+        for (int c = 0; c < OR_ANC_H; ++c) s += w[OR_ANC_W2 + o * OR_ANC_H + c] * (pre[c] > 0.0 ? pre[c] : 0.0);
+        z[o] = s;
+    }
+    *dist = d;
+}
+
+static int lod_active(int32_t level, double d, const double *max_dist) {
+    const double lo = level > 0 ? max_dist[level - 1] : 0.0;
+    return d >= lo && d < max_dist[level];
+}
+
+void or_anchor_decode(int64_t n, const double *pos, const int32_t *level, const double *feat, const double *log_l,
+                      const double *offs, const double *w, const double cam_c[3], const double *max_dist,
+                      double *rows, uint8_t *keep, uint8_t *unsure, double tol) {
+    for (int64_t i = 0; i < n; ++i) {
+        double x[OR_ANC_IN], pre[OR_ANC_H], z[OR_ANC_OUT], d;
+        anchor_mlp(pos + 3 * i, feat + OR_ANC_F * i, w, cam_c, x, pre, z, &d);
+        const int M = lod_active(level[i], d, max_dist);
+        const double lo = level[i] > 0 ? max_dist[level[i] - 1] : 0.0;
+        int near_band = fabs(d - lo) <= tol * d || fabs(d - max_dist[level[i]]) <= tol * d;
+        const double *L = log_l + 3 * i;
+        for (int k = 0; k < OR_ANC_K; ++k) {
+            const double *zk = z + 14 * k;
+            double *r = rows + 14 * (k * n + i);
+            const double a = tanh(zk[3]);
+            const int kp = M && a > 0.0;
+            if (keep) keep[k * n + i] = (uint8_t)kp;
+            if (unsure) unsure[k * n + i] = (uint8_t)(near_band || fabs(zk[3]) <= tol);
+            if (!kp) {  /* dropped: a culled placeholder at the anchor */
+                for (int c = 0; c < 3; ++c) r[c] = pos[3 * i + c];
+                for (int c = 0; c < 3; ++c) r[3 + c] = L[c];
+                r[6] = 1.0; r[7] = r[8] = r[9] = 0.0;
+                r[10] = -30.0;
+                r[11] = r[12] = r[13] = 0.0;
+                continue;
+            }
+            for (int c = 0; c < 3; ++c) {
+                const double l = exp(L[c]);
+                r[c] = pos[3 * i + c] + (offs[(OR_ANC_K * i + k) * 3 + c] + zk[11 + c]) * l;  /* mean */
+                r[3 + c] = L[c] + log(sigm(zk[8 + c]));                                       /* log(l ds) */
+            }
+            r[6] = 1.0 + zk[4];
+            r[7] = zk[5];
+            r[8] = zk[6];
+            r[9] = zk[7];
+            r[10] = log(a / (1.0 - a));
+            for (int c = 0; c < 3; ++c) r[11 + c] = (sigm(zk[c]) - 0.5) / OR_Y00;
+        }
+    }
+}
+
+void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *level, const double *feat,
+                               const double *log_l, const double *offs, const double *w, const double cam_c[3],
+                               const double *max_dist, const double *g_rows, double *g_feat, double *g_log_l,
+                               double *g_offs, double *g_w) {
+    for (int64_t i = 0; i < n; ++i) {
+        double x[OR_ANC_IN], pre[OR_ANC_H], z[OR_ANC_OUT], d, dz[OR_ANC_OUT];
+        anchor_mlp(pos + 3 * i, feat + OR_ANC_F * i, w, cam_c, x, pre, z, &d);
+        const int M = lod_active(level[i], d, max_dist);
+        const double *L = log_l + 3 * i;
+        for (int o = 0; o < OR_ANC_OUT; ++o) dz[o] = 0.0;
+        for (int k = 0; k < OR_ANC_K; ++k) {
+            const double *zk = z + 14 * k;
+            const double a = tanh(zk[3]);
+            if (!(M && a > 0.0)) continue;  /* dropped Gaussians pass no gradient */
+            const double *g = g_rows + 14 * (k * n + i);
+            double *dk = dz + 14 * k;
+            for (int c = 0; c < 3; ++c) {
+                const double l = exp(L[c]);
+                const double O = offs[(OR_ANC_K * i + k) * 3 + c] + zk[11 + c];
+                dk[11 + c] = g[c] * l;                                  /* offset */
+                g_offs[(OR_ANC_K * i + k) * 3 + c] += g[c] * l;
+                g_log_l[3 * i + c] += g[c] * O * l + g[3 + c];          /* mean and log-scale */
+                dk[8 + c] = g[3 + c] * (1.0 - sigm(zk[8 + c]));         /* d log(sigmoid) */
+                const double sc = sigm(zk[c]);
+                dk[c] = g[11 + c] * sc * (1.0 - sc) / OR_Y00;           /* colour */
+            }
+            for (int c = 0; c < 4; ++c) dk[4 + c] = g[6 + c];           /* rotation */
+            dk[3] = g[10] * (1.0 + a) / a;  /* d logit(tanh z) / dz = (1 - a^2) / (a (1 - a)) */
+        }
+        double dh[OR_ANC_H];
+        for (int c = 0; c < OR_ANC_H; ++c) dh[c] = 0.0;
+        for (int o = 0; o < OR_ANC_OUT; ++o) {
+            if (dz[o] == 0.0) continue;
+            g_w[OR_ANC_B2 + o] += dz[o];
+            for (int c = 0; c < OR_ANC_H; ++c) {
+                const double h = pre[c] > 0.0 ? pre[c] : 0.0;
+                g_w[OR_ANC_W2 + o * OR_ANC_H + c] += dz[o] * h;
+                dh[c] += dz[o] * w[OR_ANC_W2 + o * OR_ANC_H + c];
+            }
+        }
+        for (int c = 0; c < OR_ANC_H; ++c) {
+            const double dp = pre[c] > 0.0 ? dh[c] : 0.0;
+            if (dp == 0.0) continue;
+            g_w[OR_ANC_B1 + c] += dp;
+            for (int m = 0; m < OR_ANC_IN; ++m) {
+                g_w[OR_ANC_W1 + c * OR_ANC_IN + m] += dp * x[m];
+                if (m < OR_ANC_F) g_feat[OR_ANC_F * i + m] += dp * w[OR_ANC_W1 + c * OR_ANC_IN + m];
+            }
+        }
+    }
 }

@@ -208,6 +208,26 @@ int64_t or_init_select(int32_t H, int32_t W, const double *prob, const double *u
                        int64_t *new_keys, double *pos, int32_t *level, int32_t *pixel, uint8_t *selected,
                        uint8_t *uncertain, double tol, double tol_rel);
 
+/* Scaffold-GS anchor decoding (Supp. D.1, D.3), readings R25-R29 of
+ * gs_oracle.c.  Anchors: pos[n][3] (fixed), level[n], feat[n][32],
+ * log_l[n][3], offs[n][10][3]; decoder weights W1[64][36], b1[64],
+ * W2[140][64], b2[140] in one array (or_anchor_num_weights()).  The
+ * Gaussian k of anchor i is row k n + i of rows[10 n][14] = [mean 3,
+ * log-scale 3, quaternion 4, opacity logit 1, sh0 3]; keep[10 n] (nullable)
+ * marks the Gaussians not dropped (LoD band and opacity > 0); unsure[10 n]
+ * (nullable) marks those whose keep decision is within tol (relative
+ * distance to a band edge, |opacity pre-activation|). */
+int32_t or_anchor_num_weights(void);
+void or_anchor_decode(int64_t n, const double *pos, const int32_t *level, const double *feat, const double *log_l,
+                      const double *offs, const double *w, const double cam_c[3], const double *max_dist,
+                      double *rows, uint8_t *keep, uint8_t *unsure, double tol);
+/* Accumulates into g_feat, g_log_l, g_offs and g_w the gradient of a loss
+ * whose gradient with respect to rows is g_rows (same layout). */
+void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *level, const double *feat,
+                               const double *log_l, const double *offs, const double *w, const double cam_c[3],
+                               const double *max_dist, const double *g_rows, double *g_feat, double *g_log_l,
+                               double *g_offs, double *g_w);
+
 #ifdef __cplusplus
 }
 #endif

@@ -557,6 +557,57 @@ gs_status gs_init_insert(const float *prob, const float *uniform, const float *d
 gs_status gs_voxel_lookup(const gs_voxel_table *table, const int32_t *vox, int64_t n, int64_t ld, int32_t *ids,
                           gs_stream stream);
 
+/*
+ * Scaffold-GS anchors (Sec. 3.2.1, Supp. D.1 decoding, Supp. D.3 LoD mask).
+ * An anchor i at a fixed position p (e.g. a voxel of gs_init_insert, with
+ * its level l) holds a feature f (32), a log-scale log l (3) and K = 10
+ * offsets O_k (3 each).  For a camera centre c, d = ||p - c||, its decoder
+ * (one hidden layer of 64 with ReLU; weights W1[64][36], b1[64],
+ * W2[140][64], b2[140] in one array) maps (f, (p - c)/d, log(1 + d)) to 14
+ * outputs per Gaussian k: colour (sigmoid), opacity a (tanh), rotation
+ * (1, 0, 0, 0) + output, scale factor ds (sigmoid), offset dO.  Gaussian k
+ * has mean p + (O_k + dO_k) * l, scale l * ds, and opacity a where d lies in
+ * the level's band [max_dist[l-1], max_dist[l]) (0 below the first) and
+ * a > 0; otherwise it is dropped.
+ */
+#define GS_ANCHOR_K 10
+#define GS_ANCHOR_FEAT 32
+#define GS_ANCHOR_PLANES 65      /* 0-31 feature, 32-34 log-scale, 35 + 3k + c offset k */
+#define GS_ANCHOR_WEIGHTS 11468
+
+typedef struct {
+    float *data;           /* [GS_ANCHOR_PLANES][ld] */
+    const float *pos;      /* [3][ld] positions (not optimised) */
+    const int32_t *level;  /* [ld] LoD level of each anchor */
+    int64_t n, ld;         /* anchors, plane stride (a multiple of 4) */
+} gs_anchor_params;
+
+/*
+ * Decodes every anchor for a camera centre (host float[3]) into out: an SH
+ * degree 0 gs_params with out->n == GS_ANCHOR_K * a->ld; Gaussian k of
+ * anchor i is column k * a->ld + i.  Dropped Gaussians (and the padding
+ * anchors i >= n) get opacity logit -30, which the projection culls, so out
+ * renders directly through gs_project ... gs_render_bwd.  max_dist: host
+ * float[levels] (the bands of gs_init_cfg), 1 <= levels <= 8.
+ */
+gs_status gs_anchor_decode(const gs_anchor_params *a, const float *weights, const float cam_centre[3],
+                           const float *max_dist, int32_t levels, const gs_params *out, gs_stream stream);
+
+/*
+ * Gradient of a loss with respect to the anchors (grad_anchor
+ * [GS_ANCHOR_PLANES][a->ld], overwritten) and the decoder's weights
+ * (grad_weights [GS_ANCHOR_WEIGHTS], overwritten) from its gradient with
+ * respect to the decoded Gaussians (grad_out, laid out as out above, e.g.
+ * the gradient buffer of gs_render_bwd / gs_project_bwd).
+ */
+gs_status gs_anchor_decode_bwd(const gs_anchor_params *a, const float *weights, const float cam_centre[3],
+                               const float *max_dist, int32_t levels, const gs_params *grad_out,
+                               float *grad_anchor, float *grad_weights, gs_stream stream);
+
+/* Adam with bias correction over n contiguous floats (p, g, m, v device). */
+gs_status gs_adam_flat(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2,
+                       float eps, int64_t step, gs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -251,7 +251,10 @@ void or_project(const or_params *p, const or_camera *cam, const or_cfg *cfg, or_
         int culled = cfg->fp32_positions ? (zc32 <= (float)cfg->near_z) : (z <= cfg->near_z);
         /* R2: a Gaussian whose opacity is below alpha_min can never blend under R8; the
            test is on the FP32 logit against the FP32 logit of alpha_min */
-        culled |= (float)p->opacity_logits[i] < (float)log(cfg->alpha_min / (1.0 - cfg->alpha_min));
+        {
+            const double am = (double)(float)cfg->alpha_min;  /* the device receives alpha_min in FP32 */
+            culled |= (float)p->opacity_logits[i] < (float)log(am / (1.0 - am));
+        }
         if (culled) continue;
 
         /* 3D covariance */

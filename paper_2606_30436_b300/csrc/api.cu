@@ -91,6 +91,7 @@ gs_status build_views(const gs_camera *cams, int n_views, const gs_raster_cfg *c
     vt.total_tiles = (int)tiles;
     rc.near_z = cfg->near_z; rc.dilation = cfg->dilation; rc.alpha_min = cfg->alpha_min;
     rc.alpha_max = cfg->alpha_max; rc.t_min = cfg->t_min; rc.tan_clamp = cfg->tan_clamp;
+    rc.logit_min = (float)std::log((double)cfg->alpha_min / (1.0 - (double)cfg->alpha_min));
     for (int k = 0; k < 3; ++k) rc.bg[k] = cfg->bg[k];
     rc.tile_w = cfg->tile_w; rc.tile_h = cfg->tile_h;
     rc.batch = cfg->batch == 0 ? 512 : cfg->batch;
@@ -644,4 +645,64 @@ GS_API gs_status gs_voxel_lookup(const gs_voxel_table *table, const int32_t *vox
     if (n < 0 || ld < n || (n > 0 && (!vox || !ids || !aligned16(vox)))) return GS_ERR_INVALID;
     return cuda_status(launch_voxel_lookup((const unsigned long long *)table->keys, table->ids, table->capacity, vox,
                                            n, ld, ids, (cudaStream_t)stream));
+}
+
+namespace {
+
+gs_status anchor_view(const gs_anchor_params *a, const float cam_centre[3], const float *max_dist, int levels,
+                      AnchorView &v) {
+    if (!a || !a->data || !a->pos || !a->level || !aligned16(a->data) || !aligned16(a->pos) || a->n < 0 ||
+        a->ld < a->n || (a->ld & 3) || !cam_centre || !max_dist || levels < 1 || levels > GS_INIT_MAX_LEVELS)
+        return GS_ERR_INVALID;
+    v = AnchorView{};
+    for (int k = 0; k < 3; ++k) v.c[k] = cam_centre[k];
+    for (int l = 0; l < levels; ++l) {
+        if (!(max_dist[l] > 0.0f) || (l && !(max_dist[l] > max_dist[l - 1]))) return GS_ERR_INVALID;
+        v.lo[l] = l ? max_dist[l - 1] : 0.0f;
+        v.hi[l] = max_dist[l];
+    }
+    v.levels = levels;
+    return GS_OK;
+}
+
+gs_status check_decoded(const gs_anchor_params *a, const gs_params *out) {
+    gs_status st = check_params(out);
+    if (st != GS_OK) return st;
+    if (out->sh_degree != 0 || out->n != (int64_t)GS_ANCHOR_K * a->ld) return GS_ERR_INVALID;
+    return GS_OK;
+}
+
+}  // namespace
+
+GS_API gs_status gs_anchor_decode(const gs_anchor_params *a, const float *weights, const float cam_centre[3],
+                                  const float *max_dist, int32_t levels, const gs_params *out, gs_stream stream) {
+    AnchorView v;
+    gs_status st = anchor_view(a, cam_centre, max_dist, levels, v);
+    if (st == GS_OK) st = check_decoded(a, out);
+    if (st != GS_OK) return st;
+    if (!weights || !aligned16(weights)) return GS_ERR_INVALID;
+    return cuda_status(launch_anchor_decode(a->data, a->pos, a->level, a->n, a->ld, weights, v, out->data, out->ld,
+                                            (cudaStream_t)stream));
+}
+
+GS_API gs_status gs_anchor_decode_bwd(const gs_anchor_params *a, const float *weights, const float cam_centre[3],
+                                      const float *max_dist, int32_t levels, const gs_params *grad_out,
+                                      float *grad_anchor, float *grad_weights, gs_stream stream) {
+    AnchorView v;
+    gs_status st = anchor_view(a, cam_centre, max_dist, levels, v);
+    if (st == GS_OK) st = check_decoded(a, grad_out);
+    if (st != GS_OK) return st;
+    if (!weights || !aligned16(weights) || !grad_anchor || !aligned16(grad_anchor) || !grad_weights ||
+        !aligned16(grad_weights))
+        return GS_ERR_INVALID;
+    return cuda_status(launch_anchor_decode_bwd(a->data, a->pos, a->level, a->n, a->ld, weights, v, grad_out->data,
+                                                grad_out->ld, grad_anchor, grad_weights, (cudaStream_t)stream));
+}
+
+GS_API gs_status gs_adam_flat(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,
+                              float beta2, float eps, int64_t step, gs_stream stream) {
+    if (n < 0 || (n > 0 && (!p || !g || !m || !v)) || step < 1 || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f) || !(lr >= 0.0f))
+        return GS_ERR_INVALID;
+    return cuda_status(launch_adam_flat(p, g, m, v, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream));
 }

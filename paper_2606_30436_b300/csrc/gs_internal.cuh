@@ -36,6 +36,7 @@ __host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return
 
 struct RasterCfg {
     float near_z, dilation, alpha_min, alpha_max, t_min, tan_clamp;
+    float logit_min;  // FP32 logit of alpha_min: a Gaussian below it never blends and is culled
     float bg[3];
     int tile_w, tile_h;
     int batch;      // pairs a warp scans per step (128, 256, 512)

@@ -111,4 +111,18 @@ cudaError_t launch_voxel_lookup(const unsigned long long *keys, const int *ids, 
                                 long long n, long long ld, int *out, cudaStream_t s);
 cudaError_t launch_voxel_reset(unsigned long long *keys, int *ids, int *owner, long long cap, cudaStream_t s);
 
+// Scaffold-GS anchors (anchors.cu): camera centre and the LoD band [lo, hi) of each level.
+struct AnchorView {
+    float c[3];
+    float lo[GS_INIT_MAX_LEVELS], hi[GS_INIT_MAX_LEVELS];
+    int levels;
+};
+cudaError_t launch_anchor_decode(const float *A, const float *pos, const int *level, long long n, long long ld,
+                                 const float *w, const AnchorView &v, float *G, long long gld, cudaStream_t s);
+cudaError_t launch_anchor_decode_bwd(const float *A, const float *pos, const int *level, long long n, long long ld,
+                                     const float *w, const AnchorView &v, const float *GG, long long gld, float *gA,
+                                     float *gw, cudaStream_t s);
+cudaError_t launch_adam_flat(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
+                             float eps, long long step, cudaStream_t s);
+
 }  // namespace gs

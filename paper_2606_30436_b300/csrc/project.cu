@@ -128,9 +128,11 @@ __global__ void __launch_bounds__(256, 3) k_project(const float *__restrict__ P,
     }
     const float mx = P[0 * ld + g], my = P[1 * ld + g], mz = P[2 * ld + g];
 
-    // cheap near-plane pass first: skip the remaining loads if no view sees it
+    // cheap near-plane pass first: skip the remaining loads if no view sees it; a
+    // Gaussian whose opacity is below alpha_min can never blend and is culled too
+    const bool bright = !(P[10 * ld + g] < cfg.logit_min);
     bool any = false;
-    for (int v = 0; v < vt.n_views; ++v) {
+    for (int v = 0; v < vt.n_views && bright; ++v) {
         const ViewDesc &c = vt.v[v];
         float zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.R[6], mx), __fmul_rn(c.R[7], my)), __fmul_rn(c.R[8], mz)), c.t[2]);
         any |= zc > cfg.near_z;

@@ -80,7 +80,7 @@ EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspac
            "gs_mlp_push_blend", "gs_mlp_features", "gs_mlp_forward", "gs_mlp_train_grad", "gs_mlp_adam",
            "gs_segment_workspace_size", "gs_project_bwd_adam", "gs_segment_workspace_size_items",
            "gs_voxel_table_reset", "gs_init_workspace_size", "gs_init_probability", "gs_init_insert",
-           "gs_voxel_lookup")
+           "gs_voxel_lookup", "gs_anchor_decode", "gs_anchor_decode_bwd", "gs_adam_flat")
 
 _lib = None
 

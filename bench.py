@@ -808,6 +808,126 @@ def run_init(args, dev):
     return out
 
 
+def run_anchors(args, dev):
+    """Scaffold-GS anchor mapping (Supp. D.1, D.3): 200k anchors x 10 decoded
+    Gaussians along the 1 km corridor, SH0 colour from the view-dependent
+    decoder, one 1280x720 view per iteration over the 16-frame pool; per
+    iteration decode -> project / sort / render -> L1 + D-SSIM -> backward ->
+    decoder backward -> Adam on anchors and decoder (eager launches).  An
+    anchor's level is the LoD band of a log-uniform spawning distance in
+    [2, 400] m, so each view activates, band by band, the anchors of the
+    matching level."""
+    import math as _m
+    import torch
+    from paper_2606_30436_b300 import anchors, gs, scenes
+
+    n = args.anchors_n
+    rng = np.random.default_rng(0)
+    base = scenes.corridor_scene(n, seed=0, sh_degree=0)
+    pos = np.asarray(base["means"], np.float64)
+    spawn_d = np.exp(rng.uniform(np.log(2.0), np.log(400.0), n))
+    bands = np.array(anchors.MAX_DIST_DEFAULT[:-1])
+    level = np.searchsorted(bands, spawn_d, side="right").astype(np.int32)
+    voxel = np.array(anchors.VOXEL_DEFAULT)
+    log_l = np.log(voxel[level])[:, None] + rng.normal(0, 0.1, (n, 3))
+    feat = rng.normal(0, 0.3, (n, 32))
+    offs = rng.normal(0, 0.5, (n, 10, 3))
+    w = anchors.init_weights(0, device="cpu").numpy()
+    w[anchors.W2:anchors.B2] += rng.normal(0, 0.05, anchors.B2 - anchors.W2).astype(np.float32)
+    model = anchors.AnchorModel.from_arrays(pos, level, feat, log_l, offs, w, device=dev)
+    frames = frame_pool(args.frames)
+    cams = [scenes.corridor_camera(f, W, H, F) for f in frames]
+    # targets: renders of the same anchors with perturbed features
+    tmodel = anchors.AnchorModel.from_arrays(pos, level, feat + rng.normal(0, 0.05, feat.shape), log_l, offs, w,
+                                             device=dev)
+    tst = anchors.AnchorStep(tmodel, cams[0], gs.Config())
+    targets = []
+    for c in cams:
+        tst.set_camera(c)
+        anchors.gs_anchor_decode(tmodel, anchors.camera_centre(c), tst.gauss)
+        tst.map.fit_capacity(slack=1.2)
+        targets.append(tst.map.buf.img.clone())
+    del tst, tmodel
+    st = anchors.AnchorStep(model, cams[0], gs.Config(), lambda_dssim=LAMBDA)
+    needed, vis = [], []
+    for c in cams:
+        st.set_camera(c)
+        anchors.gs_anchor_decode(model, anchors.camera_centre(c), st.gauss)
+        needed.append(st.map.fit_capacity(slack=1.0))
+        vis.append(int(st.map.buf.counts[0].item()))
+    st.map.buf.set_max_pairs(int(max(needed) * 1.15) + 1024)
+    stream = torch.cuda.current_stream()
+    for i in range(args.warmup):
+        st.set_camera(cams[i % len(cams)])
+        st.step(targets[i % len(cams)])
+    torch.cuda.synchronize()
+    st.map.check_status()
+    steps = max(10, min(args.steps, 100))
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        st.set_camera(cams[i % len(cams)])
+        st.step(targets[i % len(cams)])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / steps
+    st.map.check_status()
+    # per-stage times (events between the C-ABI calls)
+    names = ("decode", "render_fwd", "loss_bwd", "decode_bwd", "adam")
+    acc = {k: 0.0 for k in names}
+    for i in range(steps):
+        c = cams[i % len(cams)]
+        st.set_camera(c)
+        cc = anchors.camera_centre(c)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        ev[0].record(stream)
+        anchors.gs_anchor_decode(model, cc, st.gauss)
+        ev[1].record(stream)
+        st.map.forward()
+        ev[2].record(stream)
+        st.map._losses_and_backward(targets[i % len(cams)])
+        ev[3].record(stream)
+        anchors.gs_anchor_decode_bwd(model, cc, st.map.grads, st.g_anchor, st.g_w)
+        ev[4].record(stream)
+        st.step_count += 1
+        for lo, hi, lr in ((0, 32, 7.5e-3), (32, 35, 7e-3), (35, 65, 1e-2)):
+            anchors.gs_adam_flat(model.data[lo:hi], st.g_anchor[lo:hi], st.m_a[lo:hi], st.v_a[lo:hi], lr,
+                                 st.step_count)
+        anchors.gs_adam_flat(model.weights, st.g_w, st.m_w, st.v_w, 4e-3, st.step_count)
+        ev[5].record(stream)
+        torch.cuda.synchronize()
+        for j, k in enumerate(names):
+            acc[k] += ev[j].elapsed_time(ev[j + 1])
+    stage = {k: round(v / steps, 4) for k, v in acc.items()}
+    # the decoder kernels are FP32 FMA streams: 2 (36*64 + 140*64) flops per anchor forward,
+    # recomputed in the backward plus dW2, dW1, dL/dh, dL/df (~4x the forward)
+    fl_fwd = 2.0 * (36 * 64 + 140 * 64) * n
+    peak_fp32 = alu_peak_tflops(clk)
+    dom = "decode_bwd" if stage["decode_bwd"] >= stage["decode"] else "decode"
+    fl = fl_fwd * (4.0 if dom == "decode_bwd" else 1.0)
+    achieved = fl / (stage[dom] * 1e-3) / 1e12
+    return {"metric": "anchor mapping iters/s (200k anchors x 10 Gaussians, 720p, decode+fwd+bwd+Adam)",
+            "value": round(1e3 / ms, 2), "unit": "iters/s", "ms_per_step": round(ms, 4), "steps": steps,
+            "warmup": args.warmup, "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "corridor anchors, K=10, 5 LoD levels, 1280x720, 16-frame pool",
+                       "anchors": n, "decoded_slots": 10 * model.ld, "launch": "eager"},
+            "stages_ms": stage, "visible_mean": int(np.mean(vis)), "pairs_mean": int(np.mean(needed)),
+            "roofline": {"kernel": "k_anchor_" + dom, "bound": "alu", "achieved": round(achieved, 2),
+                         "peak": round(peak_fp32, 1), "unit": "TFLOP/s", "frac": round(achieved / peak_fp32, 4),
+                         "traffic": None, "peak_kind": "FP32 FMA: 148 SMs x 128 lanes x 2 flops x SM clock"},
+            "clocks": clk}
+
+
+def alu_peak_tflops(clk):
+    """FP32 FMA peak at the sampled SM clock (148 SMs x 128 FP32 lanes x 2 flops)."""
+    mhz = (clk or {}).get("sm_mhz") or 1920.0
+    return 148 * 128 * 2 * float(mhz) * 1e6 / 1e12
+
+
 def oracle_iteration(scene, tscene_img, cam, oc):
     import oracle as orc
     f = orc.loss_and_grads(scene, cam, oc, tscene_img, LAMBDA)
@@ -890,6 +1010,9 @@ def main():
                     help="learned vs plain densify/prune over keyframe chunks (prints its own JSON line)")
     ap.add_argument("--memory", action="store_true",
                     help="peak memory at 10M Gaussians, 1920x1080, with the crop gradient check (own JSON line)")
+    ap.add_argument("--anchors", action="store_true",
+                    help="Scaffold-GS anchor mapping iteration (decode, render, backward, decoder backward, Adam)")
+    ap.add_argument("--anchors-n", type=int, default=200_000)
     ap.add_argument("--init", action="store_true",
                     help="anchor initialisation at a 720p keyframe (probability, NMS, voxel insertion)")
     ap.add_argument("--memory-gaussians", type=int, default=10_000_000)
@@ -916,6 +1039,11 @@ def main():
         if rank == 0:
             import torch
             print(json.dumps(run_memory(args, torch.device("cuda", 0))), flush=True)
+        return
+    if args.anchors:
+        if rank == 0:
+            import torch
+            print(json.dumps(run_anchors(args, torch.device("cuda", 0))), flush=True)
         return
     if args.init:
         if rank == 0:

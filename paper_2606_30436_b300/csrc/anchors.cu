@@ -12,9 +12,11 @@
 // k_anchor_decode_bwd: 128-anchor tiles, thread per anchor.  The inputs, the
 // hidden activations and dL/dz of the tile are staged in shared memory
 // ([row][129]: a column read by a warp touches 32 banks); each thread then
-// owns 70 entries of dW2 and 18 of dW1 and sums them over the tile's anchors
-// in registers across its tiles (one FP32 atomic per weight per CTA at the
-// end), and takes its own anchor's dL/dh = W2^T dz and dL/df = W1^T dL/dpre.
+// owns 70 entries of dW2 (35 outputs of its warp x 2 hidden units of its
+// lane, so a row of the tile costs 37 loads for 70 FMAs) and 18 of dW1, sums
+// them over the tile's anchors in registers across its tiles (one FP32
+// atomic per weight per CTA at the end), and takes its own anchor's
+// dL/dh = W2^T dz and dL/df = W1^T dL/dpre.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -163,6 +165,10 @@ __global__ void __launch_bounds__(kBT) k_anchor_decode_bwd(const float *__restri
     for (int j = t; j < kANW; j += kBT) s.w[j] = w[j];
     constexpr int kE2 = kAOut * kAH / kBT, kE1 = kAH * kAIn / kBT;  // 70, 18 entries per thread
     static_assert(kE2 * kBT == kAOut * kAH && kE1 * kBT == kAH * kAIn, "weight entries per thread");
+    // dW2 entries of this thread: outputs kO2 * warp + j (j < kO2), hidden units lane and lane + 32
+    constexpr int kO2 = kAOut / (kBT / 32);  // 35
+    static_assert(kO2 * (kBT / 32) == kAOut && 2 * kO2 == kE2 && kAH == 64, "dW2 blocking");
+    const int warp = t >> 5, lane = t & 31;
     float aW2[kE2], aW1[kE1], aB2[2] = {0.0f, 0.0f}, aB1 = 0.0f;
     #pragma unroll
     for (int j = 0; j < kE2; ++j) aW2[j] = 0.0f;
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(kBT) k_anchor_decode_bwd(const float *__restri
             }
             #pragma unroll
             for (int c = 0; c < kAIn; ++c) s.xs[c][t] = x[c];
-            #pragma unroll 4
+            #pragma unroll
             for (int o = 0; o < kAH; ++o) {
                 float a = s.w[kAB1 + o];
                 #pragma unroll
@@ -248,14 +254,16 @@ __global__ void __launch_bounds__(kBT) k_anchor_decode_bwd(const float *__restri
             for (int c = 0; c < 3; ++c) gA[(kPlaneLogL + c) * ld + i] = gL[c];
         }
         __syncthreads();
-        // dW2, db2 over the tile's anchors
-        #pragma unroll
-        for (int j = 0; j < kE2; ++j) {
-            const int e = t + kBT * j, o = e / kAH, c = e % kAH;
-            float a = 0.0f;
-            #pragma unroll 8
-            for (int r = 0; r < kBT; ++r) a += s.dz[o][r] * s.hs[c][r];
-            aW2[j] += a;
+        // dW2, db2 over the tile's anchors: per row r, 35 broadcast loads of dz and two of h
+        // feed 70 accumulators
+        for (int r = 0; r < kBT; ++r) {
+            const float h0 = s.hs[lane][r], h1 = s.hs[lane + 32][r];
+            #pragma unroll
+            for (int j = 0; j < kO2; ++j) {
+                const float g = s.dz[kO2 * warp + j][r];
+                aW2[2 * j] += g * h0;
+                aW2[2 * j + 1] += g * h1;
+            }
         }
         #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -306,7 +314,11 @@ __global__ void __launch_bounds__(kBT) k_anchor_decode_bwd(const float *__restri
         __syncthreads();  // the tile's shared arrays are rewritten next
     }
     #pragma unroll
-    for (int j = 0; j < kE2; ++j) atomicAdd(&gw[kAW2 + t + kBT * j], aW2[j]);
+    for (int j = 0; j < kO2; ++j) {
+        const int o = kO2 * warp + j;
+        atomicAdd(&gw[kAW2 + o * kAH + lane], aW2[2 * j]);
+        atomicAdd(&gw[kAW2 + o * kAH + lane + 32], aW2[2 * j + 1]);
+    }
     #pragma unroll
     for (int j = 0; j < kE1; ++j) atomicAdd(&gw[kAW1 + t + kBT * j], aW1[j]);
     #pragma unroll

@@ -32,6 +32,7 @@ constexpr int kAK = GS_ANCHOR_K, kAF = GS_ANCHOR_FEAT, kAIn = kAF + 4, kAH = 64,
 constexpr int kAW1 = 0, kAB1 = kAW1 + kAH * kAIn, kAW2 = kAB1 + kAH, kAB2 = kAW2 + kAOut * kAH,
               kANW = kAB2 + kAOut;
 static_assert(kANW == GS_ANCHOR_WEIGHTS, "decoder weight count");
+static_assert(kAIn % 4 == 0 && kAH % 4 == 0 && kAW2 % 4 == 0, "weight rows on 16-byte boundaries");
 constexpr int kPlaneLogL = kAF, kPlaneOffs = kAF + 3;
 static_assert(kPlaneOffs + 3 * kAK == GS_ANCHOR_PLANES, "anchor planes");
 constexpr float kY00 = 0.28209479177387814f;
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(256) k_anchor_decode(const float *__restrict__
                                                        const int *__restrict__ level, long long n, long long ld,
                                                        const float *__restrict__ w, const __grid_constant__ AnchorView v,
                                                        float *__restrict__ G, long long gld) {
-    __shared__ float sw[kANW];
+    __shared__ __align__(16) float sw[kANW];
     for (int j = threadIdx.x; j < kANW; j += blockDim.x) sw[j] = w[j];
     __syncthreads();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -102,11 +103,16 @@ __global__ void __launch_bounds__(256) k_anchor_decode(const float *__restrict__
         }
         M = band_active(v, level[i], d);
         if (M) {
+            // weight rows read as float4 broadcasts (rows start on 16-byte boundaries)
             #pragma unroll
             for (int o = 0; o < kAH; ++o) {
+                const float4 *w4 = reinterpret_cast<const float4 *>(sw + kAW1 + o * kAIn);
                 float s = sw[kAB1 + o];
                 #pragma unroll
-                for (int c = 0; c < kAIn; ++c) s += sw[kAW1 + o * kAIn + c] * x[c];
+                for (int c = 0; c < kAIn / 4; ++c) {
+                    const float4 q = w4[c];
+                    s += q.x * x[4 * c] + q.y * x[4 * c + 1] + q.z * x[4 * c + 2] + q.w * x[4 * c + 3];
+                }
                 h[o] = fmaxf(s, 0.0f);
             }
         }
@@ -121,9 +127,13 @@ __global__ void __launch_bounds__(256) k_anchor_decode(const float *__restrict__
         #pragma unroll
         for (int j = 0; j < 14; ++j) {
             const int o = 14 * k + j;
+            const float4 *w4 = reinterpret_cast<const float4 *>(sw + kAW2 + o * kAH);
             float s = sw[kAB2 + o];
             #pragma unroll
-            for (int c = 0; c < kAH; ++c) s += sw[kAW2 + o * kAH + c] * h[c];
+            for (int c = 0; c < kAH / 4; ++c) {
+                const float4 q = w4[c];
+                s += q.x * h[4 * c] + q.y * h[4 * c + 1] + q.z * h[4 * c + 2] + q.w * h[4 * c + 3];
+            }
             z[j] = s;
         }
         const float a = tanhf(z[3]);
@@ -280,8 +290,15 @@ __global__ void __launch_bounds__(kBT) k_anchor_decode_bwd(const float *__restri
         for (int c = 0; c < kAH; ++c) dp[c] = 0.0f;
         for (int o = 0; o < kAOut; ++o) {
             const float g = s.dz[o][t];
+            const float4 *w4 = reinterpret_cast<const float4 *>(s.w + kAW2 + o * kAH);
             #pragma unroll
-            for (int c = 0; c < kAH; ++c) dp[c] += s.w[kAW2 + o * kAH + c] * g;
+            for (int c = 0; c < kAH / 4; ++c) {
+                const float4 q = w4[c];
+                dp[4 * c] += q.x * g;
+                dp[4 * c + 1] += q.y * g;
+                dp[4 * c + 2] += q.z * g;
+                dp[4 * c + 3] += q.w * g;
+            }
         }
         #pragma unroll
         for (int c = 0; c < kAH; ++c) dp[c] = s.hs[c][t] > 0.0f ? dp[c] : 0.0f;

@@ -793,7 +793,7 @@ def run_init(args, dev):
                     "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in host)),
                     "d2h_bytes_per_step": 8},
                gpu_launches=6 * steps,
-               roofline={"kernel": "k_init_saliency + k_init_combine", "bound": "hbm",
+               roofline={"kernel": "k_init_grad_minmax + k_init_prob", "bound": "hbm",
                          "achieved": r["probability_gbs"], "peak": peak, "unit": "GB/s",
                          "frac": round(r["probability_gbs"] / peak, 4), "traffic": None,
                          "peak_kind": kind + " (copy bandwidth)"})
@@ -817,7 +817,6 @@ def run_anchors(args, dev):
     anchor's level is the LoD band of a log-uniform spawning distance in
     [2, 400] m, so each view activates, band by band, the anchors of the
     matching level."""
-    import math as _m
     import torch
     from paper_2606_30436_b300 import anchors, gs, scenes
 

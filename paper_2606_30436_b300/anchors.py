@@ -151,13 +151,11 @@ class AnchorStep:
         self.gauss = model.decoded()
         gs_anchor_decode(model, camera_centre(cam), self.gauss, self.max_dist)
         self.map = gs.MappingStep(self.gauss, [cam], cfg, lambda_dssim=lambda_dssim, with_stats=False)
-        dev = model.data.device
         self.g_anchor = torch.zeros_like(model.data)
         self.g_w = torch.zeros_like(model.weights)
         self.m_a, self.v_a = torch.zeros_like(model.data), torch.zeros_like(model.data)
         self.m_w, self.v_w = torch.zeros_like(model.weights), torch.zeros_like(model.weights)
         self.step_count = 0
-        del dev
 
     def fit_capacity(self, slack=1.25):
         return self.map.fit_capacity(slack)

@@ -4,12 +4,16 @@ the library and for profiling a single launch of each kernel:
     python -m paper_2606_30436_b300.example --frame 500
     python -m paper_2606_30436_b300.example --chunk 16 --gaussians 2000000
     python -m paper_2606_30436_b300.example --mlp 4000000
+    python -m paper_2606_30436_b300.example --keyframe --iters 60
 
 Renders the frame(s), evaluates L = 0.8 L1 + 0.2 (1 - SSIM) against a random
 target, back-propagates to every parameter and applies one Adam update,
 then prints the visible-record and pair counts and the loss.  With --mlp N:
 one inference, one training gradient and one Adam step of the learned
-densify / prune predictor over N rows of random inputs.
+densify / prune predictor over N rows of random inputs.  With --keyframe: a
+synthetic 360x640 driving keyframe spawns anchors (probability map, 3x3 NMS,
+voxel hash), which are then mapped on the keyframe's own image for --iters
+anchor iterations (prints the anchor count and the loss before and after).
 """
 from __future__ import annotations
 
@@ -27,9 +31,31 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="keyframes of a batched chunk (0: one corridor view)")
     ap.add_argument("--iters", type=int, default=1)
     ap.add_argument("--mlp", type=int, default=0, help="rows for the predictor instead of a mapping iteration")
+    ap.add_argument("--keyframe", action="store_true",
+                    help="initialise anchors at a synthetic keyframe and map them on its image")
+    ap.add_argument("--keyframe-size", type=int, nargs=2, default=(360, 640), metavar=("H", "W"))
     ap.add_argument("--segment", type=int, default=None,
                     help="split length of long tile lists (default: 256 for a corridor view, none for a chunk)")
     args = ap.parse_args()
+    if args.keyframe:
+        # a new keyframe: probability map, voxel insertion, anchors, anchor mapping on its image
+        from . import anchors, spawn
+        H, W = args.keyframe_size
+        img, depth, U = scenes.keyframe(H, W, seed=51)
+        cam = scenes.keyframe_camera(H, W, seed=52, centre=(0.0, -1.6, 20.0))
+        prob = spawn.gs_init_probability(torch.from_numpy(img).cuda(), torch.from_numpy(depth).cuda())
+        amap = spawn.AnchorMap(H * W // 4 + 16)
+        amap.insert(prob, torch.from_numpy(U).cuda(), torch.from_numpy(depth).cuda(), cam)
+        torch.cuda.synchronize()
+        amap.check_status()
+        model = anchors.AnchorModel.from_anchor_map(amap)
+        st = anchors.AnchorStep(model, cam, gs.Config(), lambda_dssim=0.2)
+        st.fit_capacity(slack=3.0)
+        tgt = torch.from_numpy(img.reshape(-1)).cuda()
+        losses = [float(st.step(tgt).item()) for _ in range(args.iters)]
+        st.map.check_status()
+        print("anchors %d, loss %.5f -> %.5f over %d iterations" % (model.n, losses[0], losses[-1], len(losses)))
+        return
     if args.mlp:
         n = args.mlp
         ld = gs.padded(n)

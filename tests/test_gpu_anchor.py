@@ -3,8 +3,6 @@ oracle: the decoded Gaussians (keep decisions outside the oracle's near-tie
 set), the decoder's backward, a whole anchor mapping iteration (decode,
 render, L1 + D-SSIM, backward, decoder backward) against the oracle's chain,
 the flat Adam, and a few iterations lowering the loss."""
-import math
-
 import numpy as np
 import pytest
 import torch
@@ -166,3 +164,35 @@ def test_anchor_steps_lower_the_loss():
     torch.cuda.synchronize()
     st.map.check_status()
     assert float(last.item()) < 0.8 * first
+
+
+def test_keyframe_to_anchor_mapping():
+    """The chain of a new keyframe: probability, voxel insertion, anchors from the
+    inserted voxels (zero features, voxel-size scales), then anchor mapping on the
+    keyframe's own image lowers the loss."""
+    from paper_2606_30436_b300 import spawn
+    H, W = 120, 200
+    img, depth, U = scenes.keyframe(H, W, seed=51)
+    cam = scenes.keyframe_camera(H, W, seed=52, centre=(0.0, -1.6, 20.0))
+    prob = spawn.gs_init_probability(torch.from_numpy(img).to(DEV), torch.from_numpy(depth).to(DEV))
+    amap = spawn.AnchorMap(8192)
+    amap.insert(prob, torch.from_numpy(U).to(DEV), torch.from_numpy(depth).to(DEV), cam)
+    torch.cuda.synchronize()
+    amap.check_status()
+    m = anchors.AnchorModel.from_anchor_map(amap)
+    n = m.n
+    assert n > 50
+    assert torch.equal(m.pos[:, :n], amap.pos[:, :n]) and torch.equal(m.level[:n], amap.level[:n])
+    eps = np.log(np.asarray(anchors.VOXEL_DEFAULT))[amap.level[:n].cpu().numpy()]
+    assert np.allclose(m.data[32:35, :n].cpu().numpy(), eps[None, :], atol=1e-6)
+    assert torch.all(m.data[:32, :n] == 0) and torch.all(m.data[35:, :n] == 0)
+    st = anchors.AnchorStep(m, cam, gs.Config(), lambda_dssim=0.2)
+    st.fit_capacity(slack=3.0)
+    tgt = torch.from_numpy(img.reshape(-1)).to(DEV)
+    first = float(st.step(tgt).item())
+    for _ in range(40):
+        last = st.step(tgt)
+    torch.cuda.synchronize()
+    st.map.check_status()
+    assert np.isfinite(float(last.item())) and float(last.item()) < first
+    assert torch.isfinite(m.data).all() and torch.isfinite(m.weights).all()

@@ -7,7 +7,6 @@ Gaussian."""
 import math
 
 import numpy as np
-import pytest
 
 import oracle as orc
 from paper_2606_30436_b300 import scenes

@@ -661,7 +661,7 @@ def run_lifecycle(args, dev):
             step.check_status()
             # the chunk's views as the map renders them after its iterations (last forward pass)
             chunk_psnr.append(psnr(step.buf.img, targets[f0]))
-            lc.judge(step)
+            lc.assess(step)
             model, moments = lc.apply(step, dens, prune)
             lc.history[-1]["psnr_db"] = round(chunk_psnr[-1], 3)
             iter_ms += ev[0].elapsed_time(ev[1])

@@ -411,7 +411,7 @@ gs_status gs_densify_prune(const gs_params *src, const gs_params *src_m, const g
 /*
  * Learned densify / prune predictor (not in the paper: an MLP trained on the
  * decisions of the plain criterion above, which stays the fallback and the
- * judge of its error).  16 inputs -> 64 -> 64 (ReLU) -> 2 logits (sigmoid):
+ * reference for its error).  16 inputs -> 64 -> 64 (ReLU) -> 2 logits (sigmoid):
  * output 0 = densify, 1 = prune.  Weights: one FP32 array of GS_MLP_WEIGHTS
  * floats, W1[64][16] at 0, b1[64] at 1024, W2[64][64] at 1088, b2[64] at
  * 5184, W3[2][64] at 5248, b3[2] at 5376.  Layers 1 and 2, the data

@@ -9,7 +9,7 @@ parameters and the Adam moments:
   min-max-normalised S_p > tau_p over the active Gaussians);
 * ``learned``: the BF16 tensor-core predictor (``gs_mlp_features`` +
   ``gs_mlp_forward``) trained on the plain criterion's bits, which stays the
-  fallback and the judge of its error (``agreement``).
+  fallback and the reference for its error (``agreement``).
 
 Readings: the statistics of a chunk are summed over its iterations and views,
 so |V_c| = iterations x views; decisions are taken and applied per chunk (the
@@ -119,7 +119,7 @@ class Lifecycle:
         self._last = (n, dens, prune)
         return dens, prune
 
-    def judge(self, step: gs.MappingStep):
+    def assess(self, step: gs.MappingStep):
         """Records the chunk's bit counts and, for the learned decider, its
         agreement with the plain criterion on the same accumulators (call after
         decide, before apply)."""

@@ -285,7 +285,7 @@ def test_lifecycle_chunks_plain_and_learned():
             n = model.n
             dens, prune = lc.decide(step, [0.0, -1.6, float(f0 + 1)])
             d, p = dens.cpu().numpy().astype(bool), prune.cpu().numpy().astype(bool)
-            rec = lc.judge(step)
+            rec = lc.assess(step)
             assert rec["densify"] == d.sum() and rec["prune"] == p.sum()
             model, moments = lc.apply(step, dens, prune)
             assert model.n == n - p.sum() + (d & ~p).sum()

@@ -297,11 +297,13 @@ gs_status gs_iso_loss(const gs_params *params, float weight, float *loss, const 
  * every GPU that loads the library until the process exits), which bounds
  * each view to at most 1280*720 pixels with width and height <= 2048;
  * larger views return GS_ERR_INVALID before anything is enqueued.  The first
- * call on a device looks up the array's device address (with that device
- * current) and caches it, so make that first call before any stream capture.
- * Every call shares the array and leaves its last contents there; calls that
- * overlap on the GPU (other streams, other threads) race on it.  It never
- * calls cudaMalloc, cudaFree or an allocating library routine.
+ * call in a device's context looks up the array's device address (with that
+ * device current) and caches it under the context, so make that first call
+ * before any stream capture; a new context on the device (after a reset of
+ * the primary context) gets its own lookup on its first call.  Every call
+ * shares the device's copy of the array and leaves its last contents there;
+ * calls that overlap on the same device (other streams, other threads) race
+ * on it.  It never calls cudaMalloc, cudaFree or an allocating library routine.
  */
 gs_status gs_loss_static(const float *img, const float *target, const gs_camera *cams, int32_t n_views,
                          float lambda_dssim, float *loss_per_view, float *dL_dimg, gs_stream stream);
@@ -448,10 +450,16 @@ gs_status gs_mlp_features(const gs_params *params, const gs_stats *stats, const 
 /*
  * Inference over n rows of feat [16][ld]: prob [2][ld] (nullable) gets the
  * sigmoid outputs; densify / prune [n] bytes (nullable) get logit > 0.
- * status (nullable) gets bit 1<<GS_ERR_TIMEOUT if a tensor-core wait gave up.
+ * max_polls bounds each wait for a tile's tensor-core products (mbarrier
+ * polls; negative selects the default 2^24, 0 gives up at the first wait).
+ * A wait that gives up stops the CTA: it issues no further products, waits
+ * (at the default bound) for the one in flight, frees its tensor memory,
+ * writes nothing more and sets bit 1<<GS_ERR_TIMEOUT in status (nullable);
+ * the call itself returns GS_OK, and rows of CTAs that gave up keep their
+ * previous prob / densify / prune contents.
  */
 gs_status gs_mlp_forward(const float *feat, int64_t n, int64_t ld, const float *weights, float *prob,
-                         uint8_t *densify, uint8_t *prune, int32_t *status, gs_stream stream);
+                         uint8_t *densify, uint8_t *prune, int32_t *status, int64_t max_polls, gs_stream stream);
 
 /*
  * Mean binary cross-entropy over the n rows and both outputs against the
@@ -468,7 +476,7 @@ gs_status gs_mlp_adam(float *weights, const float *grad, float *exp_avg, float *
 
 /*
  * Probabilistic initialisation of new anchors at a keyframe (Sec. 3.3.1)
- * and the voxel hash of the dynamic map expansion (Supp. B).
+ * and the voxel hash of the dynamic map expansion (Supp. D.5).
  *
  * P = min(lambda DoG + (1 - lambda) minmax(||grad D||), 1) with DoG =
  * min(scale |(G_s1 - G_s2) * Y|, 1), Y = (R + G + B) / 3 (scale 255 takes

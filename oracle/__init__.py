@@ -97,7 +97,7 @@ def lib():
         L.or_iso_loss.restype = d
         L.or_mlp_num_weights.restype = i32
         L.or_mlp_forward.argtypes = [i64, vp, vp, i32, vp, vp, vp]
-        L.or_mlp_bce_grad.argtypes = [i64, vp, vp, vp, i32, vp]
+        L.or_mlp_bce_grad.argtypes = [i64, vp, vp, vp, i32, vp, vp, vp]
         L.or_mlp_bce_grad.restype = d
         L.or_mlp_features.argtypes = [i64, vp, vp, vp, vp, vp, i32, vp, vp]
         L.or_densify_prune.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp, d, d, i64, vp, vp, vp]
@@ -350,12 +350,18 @@ def mlp_forward(x, w, bf16=True):
     return p, h1, h2
 
 
-def mlp_bce_grad(x, y, w, bf16=True):
-    """Mean BCE over rows and outputs, and its gradient with respect to w."""
+def mlp_bce_grad(x, y, w, bf16=True, rows=False):
+    """Mean BCE over rows and outputs, and its gradient with respect to w.
+    bf16 rounds the forward's hidden-layer operands only; the backward is
+    plain FP64.  rows=True also returns the per-row pre-activation gradients
+    (dh2, dh1), each [n][64]."""
     x, y, w = _f64(x), _f64(y), _f64(w)
     g = np.zeros_like(w)
-    L = lib().or_mlp_bce_grad(x.shape[0], _ptr(x), _ptr(y), _ptr(w), int(bool(bf16)), _ptr(g))
-    return L, g
+    n = x.shape[0]
+    dh2, dh1 = (np.zeros((n, 64)), np.zeros((n, 64))) if rows else (None, None)
+    L = lib().or_mlp_bce_grad(n, _ptr(x), _ptr(y), _ptr(w), int(bool(bf16)), _ptr(g),
+                              _ptr(dh2) if rows else None, _ptr(dh1) if rows else None)
+    return (L, g, dh2, dh1) if rows else (L, g)
 
 
 def mlp_features(means, log_scales, opacity_logits, stats, ring, head, cam_centre):
@@ -389,7 +395,7 @@ def densify_prune(P, densify, prune, noise, split_log_scale, split_factor=1.6, m
 
 
 # --------------------------------------------------------------------------
-# Probabilistic initialisation (Sec. 3.3.1, Supp. B; readings R19-R24)
+# Probabilistic initialisation (Sec. 3.3.1, Supp. D.5; readings R19-R24)
 # --------------------------------------------------------------------------
 
 @dataclass

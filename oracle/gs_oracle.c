@@ -41,7 +41,7 @@
  *   R13 S_p is 0 for Gaussians with empty footprint in the chunk and for a
  *       chunk whose active scores are all equal.
  * Probabilistic initialisation (Sec. 3.3.1: DoG, normalised depth gradient,
- * P, P_kf, 3x3 NMS, voxel quantisation; Supp. B: dynamic map expansion
+ * P, P_kf, 3x3 NMS, voxel quantisation; Supp. D.5: dynamic map expansion
  * through a voxel hash; Supp. F: lambda = 0.9, m = 5 levels) reads:
  *   R19 DoG on Y = (R + G + B) / 3 taken in 8-bit intensity units (255 Y;
  *       on [0, 1] intensities the clamp at 1 could never act: the DoG of a
@@ -1022,11 +1022,16 @@ void or_mlp_forward(int64_t n, const double *x, const double *w, int32_t bf16, d
 
 /* Mean binary cross-entropy over the n rows and both outputs of the labels
  * y[n][2] in {0, 1}; writes dL/dw (accumulated into g) and returns L.
- * bf16 as in or_mlp_forward; the backward then rounds the tensor-core
- * operands too: dL/dh2 / scale (before the product with W2 and in the layer-2
- * weight and bias sums, with bf16(h1)) and dL/dh1 / scale (in the layer-1 weight
- * and bias sums, with the rounded inputs); the output layer stays unrounded. */
-double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double *w, int32_t bf16, double *g) {
+ * bf16 as in or_mlp_forward: the forward's hidden-layer operands (x, W1, W2,
+ * h1) are rounded to bfloat16, which is all the BF16 reading fixes.  The
+ * backward is the plain FP64 chain rule of that forward, the rounding taken
+ * as the identity (a rounded operand's gradient is the gradient of the value
+ * it stands for): no quantity of the backward is rounded.
+ * dh2o, dh1o (nullable, [n][64]): the per-row gradients with respect to the
+ * layer-2 and layer-1 pre-activations (after the ReLU masks), for tests that
+ * bound how far a kernel's own roundings of them may move the weight sums. */
+double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double *w, int32_t bf16, double *g,
+                       double *dh2o, double *dh1o) {
     double L = 0.0;
     const double scale = 1.0 / (double)(n * OR_MLP_OUT);
     for (int64_t i = 0; i < n; ++i) {
@@ -1048,29 +1053,28 @@ double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double
             for (int k = 0; k < OR_MLP_OUT; ++k) s += dz[k] * w[OR_MLP_W3 + k * OR_MLP_H + c];
             dh2[c] = h2[c] > 0.0 ? s : 0.0;
         }
-        /* layer-2 weight and bias gradients: in bf16 mode a tensor-core contraction
-         * over rows of bf16(dh2 / scale) with bf16(h1) and with an exact 1 */
+        /* layer 2: z2 = W2 h1' + b2 with h1' = bf16(h1) in bf16 mode */
         for (int o = 0; o < OR_MLP_H; ++o) {
-            const double d = bf16 ? bf16_round(dh2[o] / scale) * scale : dh2[o];
-            g[OR_MLP_B2 + o] += d;
-            for (int c = 0; c < OR_MLP_H; ++c) g[OR_MLP_W2 + o * OR_MLP_H + c] += d * (bf16 ? bf16_round(h1[c]) : h1[c]);
+            g[OR_MLP_B2 + o] += dh2[o];
+            for (int c = 0; c < OR_MLP_H; ++c) g[OR_MLP_W2 + o * OR_MLP_H + c] += dh2[o] * (bf16 ? bf16_round(h1[c]) : h1[c]);
         }
+        /* through layer 2 to h1, with the weights the forward multiplied by */
         double dh1[OR_MLP_H];
         for (int c = 0; c < OR_MLP_H; ++c) {
             double s = 0.0;
             for (int o = 0; o < OR_MLP_H; ++o) {
-                double wv = w[OR_MLP_W2 + o * OR_MLP_H + c];
-                s += (bf16 ? bf16_round(dh2[o] / scale) * scale : dh2[o]) * (bf16 ? bf16_round(wv) : wv);
+                const double wv = w[OR_MLP_W2 + o * OR_MLP_H + c];
+                s += dh2[o] * (bf16 ? bf16_round(wv) : wv);
             }
             dh1[c] = h1[c] > 0.0 ? s : 0.0;
         }
-        /* layer-1 weight and bias gradients: likewise bf16(dh1 / scale) with the
-         * (already rounded) inputs and with an exact 1 */
+        /* layer 1: z1 = W1 x' + b1 with x' = bf16(x) in bf16 mode */
         for (int o = 0; o < OR_MLP_H; ++o) {
-            const double d = bf16 ? bf16_round(dh1[o] / scale) * scale : dh1[o];
-            g[OR_MLP_B1 + o] += d;
-            for (int c = 0; c < OR_MLP_IN; ++c) g[OR_MLP_W1 + o * OR_MLP_IN + c] += d * xi[c];
+            g[OR_MLP_B1 + o] += dh1[o];
+            for (int c = 0; c < OR_MLP_IN; ++c) g[OR_MLP_W1 + o * OR_MLP_IN + c] += dh1[o] * xi[c];
         }
+        if (dh2o) memcpy(dh2o + i * OR_MLP_H, dh2, sizeof(dh2));
+        if (dh1o) memcpy(dh1o + i * OR_MLP_H, dh1, sizeof(dh1));
     }
     return L * scale;
 }
@@ -1143,7 +1147,7 @@ int64_t or_densify_prune(int64_t n, int32_t K_row, const double *P, const double
 }
 
 /* ------------------------------------------------------------------------ */
-/* Probabilistic initialisation (Sec. 3.3.1, Supp. B)                        */
+/* Probabilistic initialisation (Sec. 3.3.1, Supp. D.5)                        */
 /* ------------------------------------------------------------------------ */
 
 static double px_at(const double *a, int H, int W, int y, int x) {

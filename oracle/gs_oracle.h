@@ -142,7 +142,8 @@ double or_iso_loss(int64_t n, const double *log_scales, double *g_log_scales);
  * weights W1[64][16], b1[64], W2[64][64], b2[64], W3[2][64], b3[2] in one array. */
 int32_t or_mlp_num_weights(void);
 void or_mlp_forward(int64_t n, const double *x, const double *w, int32_t bf16, double *p, double *h1, double *h2);
-double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double *w, int32_t bf16, double *g);
+double or_mlp_bce_grad(int64_t n, const double *x, const double *y, const double *w, int32_t bf16, double *g,
+                       double *dh2, double *dh1);
 
 /* The predictor's 16 inputs per Gaussian (a reading: the inputs are named in
  * the workload definition, not in the paper): sigmoid(opacity logit), the
@@ -170,7 +171,7 @@ int64_t or_densify_prune(int64_t n, int32_t K_row, const double *P, const double
                          double *m_out, double *v_out);
 
 /* Probabilistic initialisation of new anchors at a keyframe (Sec. 3.3.1,
- * Supp. B), readings R19-R24 of gs_oracle.c.
+ * Supp. D.5), readings R19-R24 of gs_oracle.c.
  *
  * or_init_saliency: dog[H][W] = min(scale |(G_s1 - G_s2) * Y|, 1) with Y the
  * mean of the three planes of img[3][H][W] (scale 255: 8-bit intensity

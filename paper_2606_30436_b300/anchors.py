@@ -86,7 +86,7 @@ class AnchorModel:
 
     @classmethod
     def from_anchor_map(cls, amap, voxel=VOXEL_DEFAULT, seed=0, device="cuda"):
-        """Anchors of gs_init_insert: zero features (Supp. B), base scale = the
+        """Anchors of gs_init_insert: zero features (Supp. D.5), base scale = the
         voxel size of the anchor's level, zero offsets."""
         n = min(amap.n, amap.capacity)
         m = cls(n, device, seed=seed)

@@ -16,7 +16,7 @@ LIB = os.path.join(PKG, "libgs.so")
 HEADER = os.path.join(ROOT, "include", "gs.h")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-shared"]
+COMPILE_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden"]
 
 
 def sources():
@@ -32,11 +32,24 @@ def _stale():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles each source to an object in parallel (_build/), then links."""
     if not force and not _stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
+    objdir = os.path.join(ROOT, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    procs = []
+    for src in sources():
+        obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc, *ARCH, *COMPILE_FLAGS, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append((subprocess.Popen(cmd, cwd=CSRC), obj, src))
+    failed = [src for p, _, src in procs if p.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, "nvcc " + " ".join(os.path.basename(f) for f in failed))
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-o", tmp, *sources()]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for _, o, _ in procs]]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd, cwd=CSRC)

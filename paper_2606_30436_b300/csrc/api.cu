@@ -506,11 +506,13 @@ GS_API gs_status gs_mlp_features(const gs_params *params, const gs_stats *stats,
 }
 
 GS_API gs_status gs_mlp_forward(const float *feat, int64_t n, int64_t ld, const float *weights, float *prob,
-                                uint8_t *densify, uint8_t *prune, int32_t *status, gs_stream stream) {
+                                uint8_t *densify, uint8_t *prune, int32_t *status, int64_t max_polls,
+                                gs_stream stream) {
     if (!feat || !aligned16(feat) || n < 0 || ld < n || (ld & 3) || !weights || !aligned16(weights) ||
         (prob && !aligned16(prob)))
         return GS_ERR_INVALID;
-    return cuda_status(launch_mlp_forward(feat, n, ld, weights, prob, densify, prune, status, (cudaStream_t)stream));
+    return cuda_status(launch_mlp_forward(feat, n, ld, weights, prob, densify, prune, status, max_polls,
+                                         (cudaStream_t)stream));
 }
 
 GS_API gs_status gs_mlp_train_grad(const float *feat, const uint8_t *y_densify, const uint8_t *y_prune, int64_t n,

@@ -78,7 +78,7 @@ cudaError_t launch_mlp_push_blend(float *stats, long long sld, long long n, floa
 cudaError_t launch_mlp_features(const float *P, long long n, long long ld, const float *stats, long long sld,
                                 const float *ring, int head, const float cam[3], float *feat, cudaStream_t s);
 cudaError_t launch_mlp_forward(const float *feat, long long n, long long ld, const float *w, float *prob,
-                               uint8_t *densify, uint8_t *prune, int *status, cudaStream_t s);
+                               uint8_t *densify, uint8_t *prune, int *status, long long max_polls, cudaStream_t s);
 cudaError_t launch_mlp_train(const float *feat, const uint8_t *y_densify, const uint8_t *y_prune, long long n,
                              long long ld, const float *w, float *grad, float *loss, int *status, cudaStream_t s);
 cudaError_t launch_mlp_adam(float *w, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,

@@ -1,5 +1,5 @@
 // init.cu -- probabilistic initialisation of new anchors at a keyframe
-// (Sec. 3.3.1) and the voxel hash of the dynamic map expansion (Supp. B).
+// (Sec. 3.3.1) and the voxel hash of the dynamic map expansion (Supp. D.5).
 //
 // k_init_grad_minmax: the minimum and maximum of ||grad D|| over the
 // keyframe (and the rendered depth), reduced per block into two atomics

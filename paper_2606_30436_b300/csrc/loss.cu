@@ -14,6 +14,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cuda.h>  // driver types only: the two context queries are fetched at run time
+
 #include "gs_internal.cuh"
 #include "gs_kernels.h"
 
@@ -223,9 +225,9 @@ cudaError_t launch_loss(const float *img, const float *target, int h, int w, flo
 // holds until the process exits.  Its size covers one view of at most
 // kStaticMaxPixels pixels (1280x720, width and height <= 2048): 9 FP32 maps of
 // the SSIM gradient plus the per-CTA partial sums.  Every scratch word a call
-// reads is written earlier in the same call, so nothing needs clearing; calls
-// that overlap on the GPU (different streams, or devices sharing nothing but
-// this array's name) race on the contents.
+// reads is written earlier in the same call, so nothing needs clearing.  Each
+// device has its own copy of the array; calls that overlap on the same device
+// (other streams, other threads) race on its contents.
 
 constexpr long long kStaticMaxPixels = 1280ll * 720ll;
 constexpr int kStaticMaxSide = 2048;
@@ -238,7 +240,40 @@ static __device__ __align__(256) unsigned char g_loss_scratch[kStaticBytes];
 namespace {
 constexpr int kMaxDevices = 128;
 std::mutex g_scratch_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
+// per device: the array's address and the id of the context it was looked up in
+struct ScratchCache {
+    unsigned long long ctx_id;
+    void *ptr;
+};
+ScratchCache g_scratch[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Unique id of the current context (never reused within a process), through
+// the driver entry points the runtime hands out; false if there is no
+// current context or the driver cannot say.
+bool current_context_id(unsigned long long *id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+            get_id = reinterpret_cast<CtxGetIdFn>(b);
+        }
+        looked_up = true;
+    }
+    if (!get_current || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 }  // namespace
 
 bool loss_static_fits(int h, int w) {
@@ -249,22 +284,30 @@ bool loss_static_fits(int h, int w) {
 
 long long loss_static_max_pixels() { return kStaticMaxPixels; }
 
-// The device address of the scratch array for the current device.  The first
-// call on a device looks it up (cudaGetSymbolAddress, with that device
-// current) and caches it; later calls only read the cache.
+// The device address of the scratch array for the current device and
+// context.  The first call in a context looks it up (cudaGetSymbolAddress,
+// with that device current) and caches it under the context's id; later calls
+// in the same context only read the cache.  A new context on the device (after
+// a reset of the primary context, say) has a new id, so the address is looked
+// up again there instead of reusing one of a destroyed context.
 cudaError_t loss_static_scratch(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    unsigned long long ctx = 0;
+    bool known = current_context_id(&ctx);
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_loss_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
+    if (known && g_scratch[dev].ptr && g_scratch[dev].ctx_id == ctx) {
+        *out = g_scratch[dev].ptr;
+        return cudaSuccess;
     }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_loss_scratch);  // makes the device's primary context current if none is
+    if (e != cudaSuccess) return e;
+    if (!known) known = current_context_id(&ctx);
+    g_scratch[dev] = known ? ScratchCache{ctx, p} : ScratchCache{0, nullptr};  // no id: look up every call
+    *out = p;
     return cudaSuccess;
 }
 

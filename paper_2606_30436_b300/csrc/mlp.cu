@@ -33,7 +33,7 @@ constexpr int kW1 = 0, kB1 = kW1 + kH * kIn, kW2 = kB1 + kH, kB2 = kW2 + kH * kH
               kB3 = kW3 + kOut * kH, kNW = kB3 + kOut;
 constexpr int kRing = 8;            // blend-weight history (views)
 constexpr int kTmemCols = 128;      // D1 in columns [0, 64), D2 in [64, 128)
-constexpr long long kSpin = 1 << 24;  // bounded mbarrier wait
+constexpr long long kSpin = 1 << 24;  // default bound of an mbarrier wait (polls)
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -80,10 +80,11 @@ __device__ __forceinline__ void mma_commit(uint64_t *mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(smem_addr(mbar)));
 }
 
-// Bounded wait for the mbarrier phase `parity`; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity) {
+// Wait for the mbarrier phase `parity`, giving up after `polls` polls (0:
+// at once, without polling); false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, long long polls = kSpin) {
     uint32_t done = 0;
-    for (long long it = 0; it < kSpin && !done; ++it)
+    for (long long it = 0; it < polls && !done; ++it)
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_addr(mbar)), "r"(parity));
     return done != 0;
@@ -193,7 +194,7 @@ __device__ void mlp_finish(S &s, bool ok, uint32_t phase, int *status, uint32_t 
 // s.x; on return h2 (64 FP32, after ReLU) and h1 (64 FP32, after ReLU) hold
 // the thread's row.  Returns false on a wait timeout.
 template <class S>
-__device__ bool mlp_tile_forward(S &s, uint32_t &phase, float *h1, float *h2) {
+__device__ bool mlp_tile_forward(S &s, uint32_t &phase, float *h1, float *h2, long long polls = kSpin) {
     const uint32_t tmem = s.tmem;
     asm volatile("fence.proxy.async.shared::cta;");  // s.x written by threads, read by the tensor core
     __syncthreads();
@@ -204,7 +205,7 @@ __device__ bool mlp_tile_forward(S &s, uint32_t &phase, float *h1, float *h2) {
                  idesc_bf16(kM, kH), false);
         mma_commit(&s.mbar);
     }
-    bool ok = mbar_wait(&s.mbar, phase);
+    bool ok = mbar_wait(&s.mbar, phase, polls);
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok) {
@@ -227,7 +228,7 @@ __device__ bool mlp_tile_forward(S &s, uint32_t &phase, float *h1, float *h2) {
         mma_commit(&s.mbar);
     }
     if (ok) {
-        ok = mbar_wait(&s.mbar, phase);
+        ok = mbar_wait(&s.mbar, phase, polls);
         phase ^= 1u;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -242,7 +243,7 @@ __device__ bool mlp_tile_forward(S &s, uint32_t &phase, float *h1, float *h2) {
 __global__ void __launch_bounds__(kM, 4) k_mlp_forward(const float *__restrict__ feat, long long n, long long ld,
                                                      const float *__restrict__ w, float *__restrict__ prob,
                                                      uint8_t *__restrict__ densify, uint8_t *__restrict__ prune,
-                                                     int *__restrict__ status) {
+                                                     int *__restrict__ status, long long polls) {
     __shared__ __align__(1024) MlpSmem s;
     mlp_setup(s, w);
     uint32_t phase = 0;
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(kM, 4) k_mlp_forward(const float *__restrict__
         store_row8(s.x, threadIdx.x, 8, kIn / 8, xn + 8);
         if (t + gridDim.x < tiles) load(t + gridDim.x);
         float h1[kH], h2[kH];
-        ok = mlp_tile_forward(s, phase, h1, h2);
+        ok = mlp_tile_forward(s, phase, h1, h2, polls);
         if (ok && valid) {
             #pragma unroll
             for (int k = 0; k < kOut; ++k) {
@@ -584,11 +585,12 @@ static int sm_count() {
 }
 
 cudaError_t launch_mlp_forward(const float *feat, long long n, long long ld, const float *w, float *prob,
-                               uint8_t *densify, uint8_t *prune, int *status, cudaStream_t s) {
+                               uint8_t *densify, uint8_t *prune, int *status, long long max_polls, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     // four CTAs per SM fill the SM's 512 TMEM columns (128 each)
     const long long grid = std::min<long long>(ceil_div(n, (long long)kM), 4ll * sm_count());
-    k_mlp_forward<<<(unsigned)grid, kM, 0, s>>>(feat, n, ld, w, prob, densify, prune, status);
+    k_mlp_forward<<<(unsigned)grid, kM, 0, s>>>(feat, n, ld, w, prob, densify, prune, status,
+                                                max_polls < 0 ? kSpin : max_polls);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ GS_MAX_VIEWS = 64
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "pair capacity exceeded",
                 4: "bounded wait timed out", 5: "non-finite value"}
 GS_ERR_CAPACITY = 3
+GS_ERR_TIMEOUT = 4
 GS_ERR_NUMERIC = 5
 
 
@@ -128,7 +129,7 @@ def lib():
                                        P(Params), vp, vp, vp, sz, vp]
         L.gs_mlp_push_blend.argtypes = [P(Stats), i64, vp, i64, i32, vp]
         L.gs_mlp_features.argtypes = [P(Params), P(Stats), vp, i32, P(f32 * 3), vp, vp]
-        L.gs_mlp_forward.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
+        L.gs_mlp_forward.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, i64, vp]
         L.gs_mlp_train_grad.argtypes = [vp, vp, vp, i64, i64, vp, vp, vp, vp, vp]
         L.gs_mlp_adam.argtypes = [vp, vp, vp, vp, f32, f32, f32, f32, i64, vp]
         for name in EXPORTS:
@@ -540,9 +541,10 @@ def gs_mlp_features(model: GaussianModel, stats_acc: torch.Tensor, ring: torch.T
                                  _stream(stream)), "gs_mlp_features")
 
 
-def gs_mlp_forward(feat: torch.Tensor, n, weights, prob=None, densify=None, prune=None, status=None, stream=None):
+def gs_mlp_forward(feat: torch.Tensor, n, weights, prob=None, densify=None, prune=None, status=None, stream=None,
+                   max_polls=-1):
     _check(lib().gs_mlp_forward(_ptr(feat), int(n), feat.shape[1], _ptr(weights), _ptr(prob), _ptr(densify),
-                                _ptr(prune), _ptr(status), _stream(stream)), "gs_mlp_forward")
+                                _ptr(prune), _ptr(status), int(max_polls), _stream(stream)), "gs_mlp_forward")
 
 
 def gs_mlp_train_grad(feat: torch.Tensor, y_densify, y_prune, n, weights, grad, loss, status=None, stream=None):
@@ -665,30 +667,66 @@ class MappingStep:
             gs_adam(self.model, self.grads, self.exp_avg, self.exp_avg_sq, self.lr, self.step_count, stream=stream)
         return self.buf.loss
 
-    def capture(self, target, stream=None):
+    # stage boundaries that capture(events=...) marks, in order
+    STAGES = ("project", "sort", "render_fwd", "loss", "render_bwd", "project_bwd", "adam")
+    STAGES_FUSED = ("project", "sort", "render_fwd", "loss", "render_bwd", "project_bwd_adam")
+
+    def capture(self, target, stream=None, events=None):
         """Captures one whole iteration (status reset, project, sort, render,
         loss, backward, Adam) for the current cameras and `target` buffer into
         a CUDA graph.  Adam reads its step from a device counter that the graph
         advances, so replays are successive iterations.  The pair buffer keeps
-        the capacity it has now (size it with fit_capacity first)."""
+        the capacity it has now (size it with fit_capacity first).
+        events: optional timing events created with external=True, one more
+        than the stages (STAGES, or STAGES_FUSED with fused_adam); the graph
+        records them at the stage boundaries, so every replay times its stages."""
         dev = self.model.data.device
         if getattr(self, "step_dev", None) is None:
             self.step_dev = torch.full((1,), self.step_count, dtype=torch.int64, device=dev)
+        stages = self.STAGES_FUSED if self.fused_adam else self.STAGES
+        assert events is None or len(events) == len(stages) + 1
         side = torch.cuda.Stream(device=dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         graph = torch.cuda.CUDAGraph()
+
+        def mark(i):
+            if events is not None:
+                events[i].record(side)
+
         with torch.cuda.graph(graph, stream=side):
             b = self.buf
             b.status.zero_()
-            gs_project(self.model, b)
-            gs_sort(b)
-            gs_render_fwd(b)
             self.step_dev.add_(1)
+            mark(0)
+            gs_project(self.model, b)
+            mark(1)
+            gs_sort(b)
+            mark(2)
+            gs_render_fwd(b)
+            mark(3)
+            gs_loss(self.buf, target, self.lambda_dssim)
+            if self.depth_prior is not None:
+                gs_geo_loss(self.buf, self.depth_prior, self.lambda_geo, self.geo_loss, self.dL_ddepth, self.reg_ws)
+            mark(4)
+            # the compositing backward leaves per-record gradients in the workspace
+            gs_render_bwd(self.model, None, self.buf, target, self.tau_err, with_stats=self.with_stats,
+                          dL_ddepth=self.dL_ddepth)
+            mark(5)
             if self.fused_adam:
-                self._losses_backward_adam(target, step_device=self.step_dev)
+                if self.lambda_iso > 0:
+                    gs_iso_loss(self.model, self.lambda_iso, self.iso_loss, None, self.reg_ws)
+                gs_project_bwd_adam(self.model, self.buf, self.exp_avg, self.exp_avg_sq, self.lr, 1,
+                                    iso_weight=self.lambda_iso, with_stats=self.with_stats,
+                                    step_device=self.step_dev)
+                mark(6)
             else:
-                self._losses_and_backward(target)
-                gs_adam(self.model, self.grads, self.exp_avg, self.exp_avg_sq, self.lr, 1, step_device=self.step_dev)
+                grads = self.grads
+                gs_project_bwd(self.model, grads, self.buf, with_stats=self.with_stats)
+                if self.lambda_iso > 0:
+                    gs_iso_loss(self.model, self.lambda_iso, self.iso_loss, grads, self.reg_ws)
+                mark(6)
+                gs_adam(self.model, grads, self.exp_avg, self.exp_avg_sq, self.lr, 1, step_device=self.step_dev)
+                mark(7)
         torch.cuda.current_stream(dev).wait_stream(side)
         return graph
 

@@ -1,5 +1,5 @@
 """Probabilistic initialisation of new anchors at a keyframe (Sec. 3.3.1) and
-the voxel hash of the dynamic map expansion (Supp. B).
+the voxel hash of the dynamic map expansion (Supp. D.5).
 
 Thin binding of ``gs_init_probability``, ``gs_init_insert``,
 ``gs_voxel_lookup`` and ``gs_voxel_table_reset`` (``include/gs.h``), and the

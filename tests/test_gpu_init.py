@@ -1,4 +1,4 @@
-"""Parity of the probabilistic initialisation (Sec. 3.3.1, Supp. B) with the
+"""Parity of the probabilistic initialisation (Sec. 3.3.1, Supp. D.5) with the
 FP64 oracle: the probability map P / P_kf element by element, the selected
 pixels outside the oracle's near-tie set, and the new anchors (voxel, level,
 spawning pixel, raster order) with the rest checked for validity; a second

@@ -1,4 +1,4 @@
-"""Pins of the oracle's probabilistic initialisation (Sec. 3.3.1, Supp. B;
+"""Pins of the oracle's probabilistic initialisation (Sec. 3.3.1, Supp. D.5;
 readings R19-R24): the DoG against scipy's Gaussian filter (separable,
 replicated borders), closed forms of the depth gradient of a quadratic bowl,
 the probability map's special cases, the 3x3 selection against a pure-Python

@@ -91,10 +91,11 @@ def _bf16(v):
 
 
 def test_bf16_gradient_one_unit_closed_form(orc):
-    """One connected unit per layer and one row: the hidden layers' weight and
-    bias gradients in bfloat16 mode, written out by hand with the rounding of
-    every tensor-core operand (dh2 / scale, h1, dh1 / scale, x) placed as the
-    oracle's header states; and they differ from the unrounded values."""
+    """One connected unit per layer and one row: in bfloat16 mode the
+    forward multiplies rounded operands (x, W1, W2, h1) and the backward is
+    the exact chain rule of that forward, written out by hand here: the
+    gradient of a rounded operand's product uses the rounded factor it was
+    multiplied by, and no backward quantity is rounded."""
     n = orc.mlp_num_weights()
     W1, B1, W2, B2, W3, B3 = 0, 1024, 1088, 5184, 5248, 5376
     w = np.zeros(n)
@@ -106,19 +107,43 @@ def test_bf16_gradient_one_unit_closed_form(orc):
     w[B3:B3 + 2] = [0.3, -0.2]
     x = (np.linspace(0.2, 1.1, 16) + 0.01 * np.random.default_rng(3).standard_normal(16))[None, :]
     y = np.array([[1.0, 0.0]])
-    _, g = orc.mlp_bce_grad(x, y, w, bf16=True)
+    L, g, dh2_rows, dh1_rows = orc.mlp_bce_grad(x, y, w, bf16=True, rows=True)
     scale = 1.0 / 2.0  # one row, two outputs
     xb, w1b, w2b = _bf16(x[0]), _bf16(w[W1:W1 + 16]), _bf16(w[W2])
     h1 = max(xb @ w1b + w[B1], 0.0)
     h2 = max(w2b * _bf16(h1) + w[B2], 0.0)
     assert h1 > 0.1 and h2 > 0.1  # both units active
+    assert _bf16(h1) != h1 and w2b != w[W2]  # the forward's rounding acts
     z = np.array([w[W3] * h2 + w[B3], w[W3 + 64] * h2 + w[B3 + 1]])
-    dz = (1 / (1 + np.exp(-z)) - y[0]) * scale
-    dh2 = (dz[0] * w[W3] + dz[1] * w[W3 + 64]) * (h2 > 0)
-    d2 = _bf16(dh2 / scale) * scale
-    assert abs(g[B2] - d2) <= 1e-15 and abs(g[W2] - d2 * _bf16(h1)) <= 1e-15
-    dh1 = (h1 > 0) * _bf16(dh2 / scale) * w2b * scale
-    d1 = _bf16(dh1 / scale) * scale
-    assert abs(g[B1] - d1) <= 1e-15
-    assert np.abs(g[W1:W1 + 16] - d1 * xb).max() <= 1e-15
-    assert g[W2] != dh2 * h1 and g[B1] != dh1  # the rounding is applied
+    p = 1 / (1 + np.exp(-z))
+    assert abs(L - (-np.log(p[0]) - np.log(1 - p[1])) * scale) <= 1e-15
+    dz = (p - y[0]) * scale
+    assert np.abs(g[B3:B3 + 2] - dz).max() <= 1e-16 and abs(g[W3] - dz[0] * h2) <= 1e-16
+    dh2 = dz[0] * w[W3] + dz[1] * w[W3 + 64]
+    assert abs(g[B2] - dh2) <= 1e-16 and abs(g[W2] - dh2 * _bf16(h1)) <= 1e-16
+    dh1 = dh2 * w2b
+    assert abs(g[B1] - dh1) <= 1e-16
+    assert np.abs(g[W1:W1 + 16] - dh1 * xb).max() <= 1e-16
+    assert abs(dh2_rows[0, 0] - dh2) <= 1e-16 and abs(dh1_rows[0, 0] - dh1) <= 1e-16
+    assert np.all(dh2_rows[0, 1:] == 0) and np.all(dh1_rows[0, 1:] == 0)
+
+
+def test_bf16_output_layer_finite_differences(orc):
+    """The parameters the bfloat16 forward does not round and that feed no
+    rounded operand (b2, W3, b3) have their exact derivatives in bfloat16
+    mode: central differences of the bfloat16-mode loss agree."""
+    rng = np.random.default_rng(12)
+    w = _w(orc, 13)
+    x = rng.standard_normal((30, 16))
+    y = (rng.uniform(size=(30, 2)) < 0.5).astype(float)
+    _, g = orc.mlp_bce_grad(x, y, w, bf16=True)
+    h = 1e-6
+    idx = [5184, 5190, 5247, 5248, 5290, 5375, 5376, 5377]
+    fd = []
+    for k in idx:
+        wp, wm = w.copy(), w.copy()
+        wp[k] += h
+        wm[k] -= h
+        fd.append((orc.mlp_bce_grad(x, y, wp, bf16=True)[0] - orc.mlp_bce_grad(x, y, wm, bf16=True)[0]) / (2 * h))
+    fd = np.array(fd)
+    assert np.linalg.norm(fd - g[idx]) <= 1e-7 * np.linalg.norm(g[idx])

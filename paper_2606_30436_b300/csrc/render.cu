@@ -301,7 +301,7 @@ __device__ __forceinline__ void fres_store(float *r, const FwdState &st, bool fl
 // pass with the same stop rule; flag = stopped) into its slot of fres; the
 // other CTAs composite the short tiles' blocks whole.
 template <int WIN>
-__global__ void __launch_bounds__(32 * kWarps, 1) k_render_fwd(ViewTable vt, RasterCfg cfg,
+__global__ void __launch_bounds__(32 * kWarps, 8) k_render_fwd(ViewTable vt, RasterCfg cfg,
                                                               const int2 *__restrict__ ranges,
                                                               const int *__restrict__ ids,
                                                               const uint8_t *__restrict__ masks,

@@ -4,15 +4,19 @@
 // (global tile << 32) | depth bits with ties broken by record index ("sorted
 // Gaussians along the ray", Supp. D.2).  It is produced in two cheaper stages:
 //   1. the visible records (radius > 0), compacted in index order, are sorted
-//      once by their 32-bit depth with a stable LSD radix sort, giving each a
-//      depth rank;
-//   2. every visible record emits one (tile, rank) pair per overlapped tile,
-//      in rank order, and a stable LSD radix sort on the tile bits alone puts
-//      the pairs in tile order while keeping rank order inside a tile.
-// Stage 2 moves 8 bytes per pair over ceil(tile_bits / 8) passes instead of
-// 12 bytes over ceil((32 + tile_bits) / 8) passes for the 64-bit key.
-// Every kernel reads its element count from device memory and runs on a fixed
-// grid, so the sequence needs no host synchronisation and can be captured.
+//      once by their 32-bit depth with a stable LSD radix sort, giving the
+//      records in depth order;
+//   2. every visible record emits one (tile, record) pair per overlapped
+//      tile, in depth order, and a stable LSD radix sort on the tile bits
+//      alone puts the pairs in tile order while keeping depth order inside a
+//      tile.
+// Each LSD pass counts the digits of every CTA's contiguous segment, scans
+// the counts and scatters stably; the grid is the number of CTAs resident at
+// once.  The last pass of the pair sort writes the renderer's ids and block
+// masks and the tile ranges (from the tile boundaries it sees), so no kernel
+// reads the pair list only to find ranges.  Every kernel reads its element
+// count from device memory and runs on a grid fixed by the capacities, so the
+// sequence needs no host synchronisation and can be captured.
 #include <algorithm>
 
 #include "gs_internal.cuh"
@@ -102,6 +106,7 @@ __global__ void __launch_bounds__(kSortBlocks) k_scan_blocks(unsigned long long 
     }
 }
 
+// Writes the visible records in index order with their depth keys.
 __global__ void __launch_bounds__(kSortThreads) k_visible_compact(const int *__restrict__ radius,
                                                                    const float4 *__restrict__ rgbd, long long nrec,
                                                                    const unsigned long long *__restrict__ blk,
@@ -124,167 +129,191 @@ __global__ void __launch_bounds__(kSortThreads) k_visible_compact(const int *__r
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort pass (keys u32 with u32 values), digit of `bits` <= 8
-// bits at `shift`; element count read from *count.
+// stable LSD radix pass (u32 keys with u32 values), digit of `bits` <= 8 bits
+// at `shift`; element count read from *count.  Three kernels: per-CTA digit
+// counts of its contiguous segment, their scan (digit-major), and the
+// scatter.  The grid is the number of CTAs resident at once (four per SM), so
+// every CTA walks one segment in rounds of 4096 elements with no second wave.
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_upsweep(const uint32_t *__restrict__ keys,
-                                                                 const int *__restrict__ count, int shift, int bits,
-                                                                 uint32_t *__restrict__ hist) {
-    __shared__ uint32_t h[256];
-    const int radix = 1 << bits;
-    const uint32_t mask = radix - 1;
-    for (int i = threadIdx.x; i < radix; i += kSortThreads) h[i] = 0;
-    __syncthreads();
-    const long long cnt_all = *count;
-    const long long seg = ceil_div(ceil_div(cnt_all, (long long)gridDim.x), (long long)(kSortThreads * 16)) *
-                          (kSortThreads * 16);  // same segments as the downsweep (kDownTile)
-    const long long beg = min(cnt_all, (long long)blockIdx.x * seg), end = min(cnt_all, beg + seg);
-    for (long long i = beg + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
-    __syncthreads();
-    for (int d = threadIdx.x; d < radix; d += kSortThreads) hist[d * kSortBlocks + blockIdx.x] = h[d];
+constexpr int kRxThreads = 256;
+constexpr int kRxItems = 16;
+constexpr int kRxRound = kRxThreads * kRxItems;  // 4096 elements per CTA round
+constexpr int kRxWarps = kRxThreads / 32;
+constexpr int kRxCtasPerSm = 4;
+constexpr int kRxBlocks = 148 * kRxCtasPerSm;
+constexpr int kRxScanThreads = 608;             // >= kRxBlocks, a multiple of 32
+
+struct RxPass {
+    const uint32_t *kin, *vin;
+    uint32_t *kout, *vout;  // kout null: keys are not needed after this pass
+    const int *count;       // element count (device)
+    long long cap;          // capacity of kout / vout / masks (elements)
+    int shift, bits;
+    long long key_div;      // > 0: the key is value / key_div (a record's view), kin unused
+    int nblocks;            // CTAs of the count and scatter kernels (kRxBlocks)
+    uint32_t *hist;         // [256][kRxBlocks] per-CTA digit counts, then their scan
+    uint32_t *dtotal;       // [256] digit totals
+    uint8_t *masks;         // last pass of the pair sort: block masks (key >> 24) ...
+    int2 *ranges;           // ... and tile ranges (INT_MAX - first, end) by atomic max
+};
+
+__device__ __forceinline__ void rx_segment(long long n, long long &beg, long long &end) {
+    const long long seg = ceil_div(ceil_div(n, (long long)gridDim.x), (long long)kRxRound) * kRxRound;
+    beg = min(n, (long long)blockIdx.x * seg);
+    end = min(n, beg + seg);
 }
 
-// One block per digit: exclusive scan of the digit's per-block counts.
-__global__ void __launch_bounds__(kSortBlocks) k_radix_scan(uint32_t *__restrict__ hist, uint32_t *__restrict__ dtotal) {
+__device__ __forceinline__ uint32_t rx_key(const RxPass &a, long long i, uint32_t v) {
+    return a.key_div > 0 ? (uint32_t)v / (uint32_t)a.key_div : a.kin[i];
+}
+
+__global__ void __launch_bounds__(kRxThreads) k_rx_count(RxPass a) {
+    __shared__ uint32_t h[kRxWarps][256];
+    const int radix = 1 << a.bits;
+    const uint32_t mask = radix - 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = lane; i < 256; i += 32) h[warp][i] = 0;
+    __syncthreads();
+    long long beg, end;
+    rx_segment(*a.count, beg, end);
+    for (long long i = beg + threadIdx.x; i < end; i += kRxThreads) {
+        const uint32_t v = a.key_div > 0 ? a.vin[i] : 0u;
+        atomicAdd(&h[warp][(rx_key(a, i, v) >> a.shift) & mask], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < radix; d += kRxThreads) {
+        uint32_t c = 0;
+        #pragma unroll
+        for (int w = 0; w < kRxWarps; ++w) c += h[w][d];
+        a.hist[d * kRxBlocks + blockIdx.x] = c;
+    }
+}
+
+// One CTA per digit: exclusive scan of the digit's per-CTA counts.
+__global__ void __launch_bounds__(kRxScanThreads) k_rx_scan(RxPass a) {
     __shared__ uint32_t sm[33];
     const int d = blockIdx.x;
-    uint32_t x = hist[d * kSortBlocks + threadIdx.x], total;
-    uint32_t ex = block_exclusive_scan<uint32_t>(x, total, sm);
-    hist[d * kSortBlocks + threadIdx.x] = ex;
-    if (threadIdx.x == 0) dtotal[d] = total;
+    const bool in = (int)threadIdx.x < a.nblocks;
+    const uint32_t x = in ? a.hist[d * kRxBlocks + threadIdx.x] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan<uint32_t>(x, total, sm);
+    if (in) a.hist[d * kRxBlocks + threadIdx.x] = ex;
+    if (threadIdx.x == 0) a.dtotal[d] = total;
 }
 
-// Stable scatter of one LSD pass.  A block takes its segment in rounds of
-// kDownTile elements; each warp ranks its 512 consecutive elements (16 rounds
-// of 32 lanes) per digit with ballots (lanes whose digit bits all agree) and
-// a per-warp histogram, the warps' counts are scanned per digit, the round is
-// reordered by digit in shared memory, and written out in digit runs so that
-// the global stores are contiguous.
-constexpr int kDownItems = 16;
-constexpr int kDownTile = kSortThreads * kDownItems;  // 4096
-
-// With `rec` set (the last pass of the pair sort; only tested for null), the
-// scatter writes the outputs the renderer reads instead of the raw pairs: the
-// record (the pair's value) into vout, the block mask (key >> 24) into masks,
-// and the tile (key & 0xffffff) into kout for the range pass.
-__global__ void __launch_bounds__(kSortThreads, 3) k_radix_downsweep(const uint32_t *__restrict__ kin,
-                                                                   const uint32_t *__restrict__ vin,
-                                                                   uint32_t *__restrict__ kout,
-                                                                   uint32_t *__restrict__ vout,
-                                                                   const int *__restrict__ count, int shift, int bits,
-                                                                   const uint32_t *__restrict__ hist,
-                                                                   const uint32_t *__restrict__ dtotal,
-                                                                   const uint32_t *__restrict__ rec,
-                                                                   uint8_t *__restrict__ masks) {
-    __shared__ uint32_t s_base[256];    // global position of this block's next element of each digit
-    __shared__ uint32_t s_dstart[256];  // first local slot of each digit in the current round
-    __shared__ uint32_t s_whist[kSortThreads / 32][256];
-    __shared__ uint32_t s_key[kDownTile];
-    __shared__ uint32_t s_val[kDownTile];
+// The stable scatter.  Each warp ranks its 512 consecutive elements of a
+// round per digit (lanes holding the same digit take consecutive ranks after
+// the warp's earlier ones), the warps' counts are scanned per digit, the
+// round is reordered by digit in shared memory and written out in digit runs.
+__global__ void __launch_bounds__(kRxThreads, kRxCtasPerSm) k_rx_scatter(RxPass a) {
+    __shared__ uint32_t s_base[256];    // output position of this CTA's next element of each digit
+    __shared__ uint32_t s_dstart[257];  // first local slot of each digit in the current round
+    __shared__ uint32_t s_whist[kRxWarps][256];
+    __shared__ uint32_t s_key[kRxRound];
+    __shared__ uint32_t s_val[kRxRound];
     __shared__ uint32_t sm[33];
-    const int radix = 1 << bits;
+    const int radix = 1 << a.bits;
     const uint32_t mask = radix - 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-
+    const int dd = threadIdx.x;  // one thread per digit (radix <= 256 = blockDim)
     {
-        uint32_t t = threadIdx.x < radix ? dtotal[threadIdx.x] : 0u, tot;
-        uint32_t ex = block_exclusive_scan<uint32_t>(t, tot, sm);
-        if (threadIdx.x < radix) s_base[threadIdx.x] = ex + hist[threadIdx.x * kSortBlocks + blockIdx.x];
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(dd < radix ? a.dtotal[dd] : 0u, tot, sm);
+        if (dd < radix) s_base[dd] = ex + a.hist[dd * kRxBlocks + blockIdx.x];
     }
-    __syncthreads();
-    const long long cnt_all = *count;
-    const long long seg = ceil_div(ceil_div(cnt_all, (long long)gridDim.x), (long long)kDownTile) * kDownTile;
-    const long long beg = min(cnt_all, (long long)blockIdx.x * seg), end = min(cnt_all, beg + seg);
-    for (long long tb = beg; tb < end; tb += kDownTile) {
-        for (int i = lane; i < radix; i += 32) s_whist[warp][i] = 0;
+    long long beg, end;
+    rx_segment(*a.count, beg, end);
+    for (long long tb = beg; tb < end; tb += kRxRound) {
+        const int n_round = (int)min((long long)kRxRound, end - tb);
+        for (int i = lane; i < 256; i += 32) s_whist[warp][i] = 0;
         __syncwarp();
-        uint32_t k[kDownItems], v[kDownItems], rk[kDownItems];
+        // keys now, values only when they are placed (fewer live registers)
+        uint32_t k[kRxItems], rk[kRxItems];
         #pragma unroll
-        for (int r = 0; r < kDownItems; ++r) {
-            const long long idx = tb + warp * (32 * kDownItems) + r * 32 + lane;
-            const bool valid = idx < end;
-            k[r] = valid ? kin[idx] : 0xffffffffu;
-            v[r] = valid ? vin[idx] : 0u;
+        for (int r = 0; r < kRxItems; ++r) {
+            const int li = warp * (32 * kRxItems) + r * 32 + lane;
+            const bool valid = li < n_round;
+            k[r] = valid ? rx_key(a, tb + li, a.key_div > 0 ? a.vin[tb + li] : 0u) : 0xffffffffu;
         }
         #pragma unroll
-        for (int r = 0; r < kDownItems; ++r) {
-            const long long idx = tb + warp * (32 * kDownItems) + r * 32 + lane;
-            const bool valid = idx < end;
-            const uint32_t d = (k[r] >> shift) & mask;
-            // lanes holding the same digit: all `bits` ballots agree
+        for (int r = 0; r < kRxItems; ++r) {
+            const int li = warp * (32 * kRxItems) + r * 32 + lane;
+            const bool valid = li < n_round;
+            const uint32_t d = (k[r] >> a.shift) & mask;
+            // lanes holding the same digit: all `bits` ballots agree (cheaper than a
+            // match on digits of high entropy)
             uint32_t peers = __ballot_sync(0xffffffffu, valid);
-            for (int b = 0; b < bits; ++b) {
+            for (int b = 0; b < a.bits; ++b) {
                 const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
                 peers &= ((d >> b) & 1u) ? bal : ~bal;
             }
+            const int leader = valid ? __ffs(peers) - 1 : 0;
             uint32_t base = 0;
-            const int leader = __ffs(peers) - 1;
             if (valid && lane == leader) {
                 base = s_whist[warp][d];
                 s_whist[warp][d] = base + __popc(peers);
             }
-            base = __shfl_sync(0xffffffffu, base, valid ? leader : 0);
+            base = __shfl_sync(0xffffffffu, base, leader);
             rk[r] = valid ? base + __popc(peers & lt) : 0xffffffffu;
-            __syncwarp();
         }
         __syncthreads();
-        // per digit: exclusive scan over warps, and the round's digit totals
-        for (int dd = threadIdx.x; dd < radix; dd += kSortThreads) {
-            uint32_t sacc = 0;
+        uint32_t cnt = 0;
+        if (dd < radix) {
             #pragma unroll
-            for (int w = 0; w < kSortThreads / 32; ++w) {
+            for (int w = 0; w < kRxWarps; ++w) {
                 const uint32_t c = s_whist[w][dd];
-                s_whist[w][dd] = sacc;
-                sacc += c;
+                s_whist[w][dd] = cnt;
+                cnt += c;
             }
-            s_dstart[dd] = sacc;  // round total of digit dd (scanned below)
         }
-        __syncthreads();
         {
-            uint32_t t = threadIdx.x < radix ? s_dstart[threadIdx.x] : 0u, tot;
-            const uint32_t ex = block_exclusive_scan<uint32_t>(t, tot, sm);
-            if (threadIdx.x < radix) s_dstart[threadIdx.x] = ex;
+            uint32_t tot;
+            const uint32_t ex = block_exclusive_scan<uint32_t>(dd < radix ? cnt : 0u, tot, sm);
+            if (dd < radix) s_dstart[dd] = ex;
+            if (dd == 0) s_dstart[radix] = (uint32_t)n_round;
         }
         __syncthreads();
-        // reorder the round by digit in shared memory
         #pragma unroll
-        for (int r = 0; r < kDownItems; ++r) {
+        for (int r = 0; r < kRxItems; ++r) {
             if (rk[r] != 0xffffffffu) {
-                const uint32_t d = (k[r] >> shift) & mask;
+                const int li = warp * (32 * kRxItems) + r * 32 + lane;
+                const uint32_t d = (k[r] >> a.shift) & mask;
                 const uint32_t slot = s_dstart[d] + s_whist[warp][d] + rk[r];
                 s_key[slot] = k[r];
-                s_val[slot] = v[r];
+                s_val[slot] = a.vin[tb + li];
             }
         }
         __syncthreads();
-        const int n_round = (int)min((long long)kDownTile, end - tb);
-        if (rec) {
-            for (int i = threadIdx.x; i < n_round; i += kSortThreads) {
-                const uint32_t key = s_key[i];
-                const uint32_t d = (key >> shift) & mask;
-                const uint32_t pos = s_base[d] + (uint32_t)i - s_dstart[d];
-                kout[pos] = key & 0xffffffu;
-                vout[pos] = s_val[i];  // the record
-                masks[pos] = (uint8_t)(key >> 24);
-            }
-        } else {
-            for (int i = threadIdx.x; i < n_round; i += kSortThreads) {
-                const uint32_t key = s_key[i];
-                const uint32_t d = (key >> shift) & mask;
-                const uint32_t pos = s_base[d] + (uint32_t)i - s_dstart[d];
-                kout[pos] = key;
-                vout[pos] = s_val[i];
+        for (int i = threadIdx.x; i < n_round; i += kRxThreads) {
+            const uint32_t key = s_key[i];
+            const uint32_t d = (key >> a.shift) & mask;
+            const long long pos = (long long)s_base[d] + i - s_dstart[d];
+            if (pos >= a.cap) continue;  // cannot happen with consistent counts
+            a.vout[pos] = s_val[i];
+            if (a.kout) a.kout[pos] = key;
+            if (a.masks) {
+                a.masks[pos] = (uint8_t)(key >> 24);
+                // tile ranges: a round's elements of one digit are sorted by the lower
+                // bits already, so a tile's elements are adjacent within the digit's run
+                const uint32_t tile = key & 0xffffffu;
+                const bool first = (uint32_t)i == s_dstart[d] || (s_key[i - 1] & 0xffffffu) != tile;
+                const bool last = (uint32_t)i + 1 == s_dstart[d + 1] || (s_key[i + 1] & 0xffffffu) != tile;
+                if (first) atomicMax(&a.ranges[tile].x, 0x7fffffff - (int)pos);
+                if (last) atomicMax(&a.ranges[tile].y, (int)(pos + 1));
             }
         }
         __syncthreads();
-        // advance the block's digit bases by this round's counts
-        for (int dd = threadIdx.x; dd < radix; dd += kSortThreads) {
-            const uint32_t nxt = (dd + 1 < radix) ? s_dstart[dd + 1] : (uint32_t)n_round;
-            s_base[dd] += nxt - s_dstart[dd];
-        }
+        if (dd < radix) s_base[dd] += s_dstart[dd + 1] - s_dstart[dd];
         __syncthreads();
     }
+}
+
+static void rx_pass(RxPass a, cudaStream_t s) {
+    a.nblocks = kRxBlocks;
+    k_rx_count<<<a.nblocks, kRxThreads, 0, s>>>(a);
+    k_rx_scan<<<1 << a.bits, kRxScanThreads, 0, s>>>(a);
+    k_rx_scatter<<<a.nblocks, kRxThreads, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -455,32 +484,19 @@ __global__ void __launch_bounds__(256) k_emit_big(const uint32_t *__restrict__ s
     }
 }
 
-// Tile ranges from the sorted tile keys (the last sort pass already wrote
-// the Gaussian ids and block masks).
-__global__ void __launch_bounds__(256) k_ranges(const uint32_t *__restrict__ tkey, const int *__restrict__ counts,
-                                                 int2 *__restrict__ ranges) {
-    const long long P = counts[1];
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
-        const uint32_t t = tkey[p];
-        if (p == 0 || tkey[p - 1] != t) ranges[t].x = (int)p;
-        if (p == P - 1 || tkey[p + 1] != t) ranges[t].y = (int)(p + 1);
-    }
-}
-
 // Without a tile pass (one tile in all): ids and masks straight from the
-// emitted pairs, which are already in order.
+// emitted pairs, which are already in order, and the one tile's range (in
+// the encoding the range fix-up of k_tile_hist expects).
 __global__ void __launch_bounds__(256) k_unpack_pairs(const uint32_t *__restrict__ pkey,
-                                                       const uint32_t *__restrict__ pval,
-                                                       const uint32_t *__restrict__ rec, const int *__restrict__ counts,
-                                                       uint32_t *__restrict__ tkey, int *__restrict__ ids,
-                                                       uint8_t *__restrict__ masks) {
+                                                       const uint32_t *__restrict__ pval, const int *__restrict__ counts,
+                                                       int *__restrict__ ids, uint8_t *__restrict__ masks,
+                                                       int2 *__restrict__ ranges) {
     const long long P = counts[1];
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
-        const uint32_t key = pkey[p];
-        tkey[p] = key & 0xffffffu;
         ids[p] = (int)pval[p];
-        masks[p] = (uint8_t)(key >> 24);
+        masks[p] = (uint8_t)(pkey[p] >> 24);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && P > 0) ranges[0] = make_int2(0x7fffffff, (int)P);
 }
 
 // ---------------------------------------------------------------------------
@@ -488,13 +504,18 @@ __global__ void __launch_bounds__(256) k_unpack_pairs(const uint32_t *__restrict
 // compositing kernels start the longest tiles first and their chains overlap
 // the many short tiles instead of trailing them.
 
-__global__ void __launch_bounds__(256) k_tile_hist(const int2 *__restrict__ ranges, int total_tiles,
+// The last sort pass leaves each tile's range as (INT_MAX - first, end),
+// both accumulated by atomic max over a zeroed array (end 0: no pair);
+// this pass turns them into [first, end), empty tiles into (0, 0).
+__global__ void __launch_bounds__(256) k_tile_hist(int2 *__restrict__ ranges, int total_tiles,
                                                     unsigned int *__restrict__ bucket) {
     __shared__ unsigned int h[33];
     if (threadIdx.x < 33) h[threadIdx.x] = 0;
     __syncthreads();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x) {
-        const int2 r = ranges[t];
+        int2 r = ranges[t];
+        r = r.y > 0 ? make_int2(0x7fffffff - r.x, r.y) : make_int2(0, 0);
+        ranges[t] = r;
         const unsigned c = (unsigned)(r.y - r.x);
         atomicAdd(&h[c ? 32 - __clz(c) : 0], 1u);  // 0 for empty, 1 + floor(log2 c) otherwise
     }
@@ -546,7 +567,7 @@ static SortWs carve(void *base, long long nrec, long long max_pairs) {
     };
     w.blk = (unsigned long long *)take(sizeof(unsigned long long) * (kSortBlocks + 1));
     w.bucket = (unsigned int *)take(sizeof(unsigned int) * 64);
-    w.hist = (uint32_t *)take(sizeof(uint32_t) * 256 * kSortBlocks);
+    w.hist = (uint32_t *)take(sizeof(uint32_t) * 256 * kRxBlocks);
     w.dtotal = (uint32_t *)take(sizeof(uint32_t) * 256);
     w.dk0 = (uint32_t *)take(sizeof(uint32_t) * nrec);
     w.dv0 = (uint32_t *)take(sizeof(uint32_t) * nrec);
@@ -564,29 +585,36 @@ static SortWs carve(void *base, long long nrec, long long max_pairs) {
 
 size_t sort_workspace_bytes(long long nrec, long long max_pairs) { return carve(nullptr, nrec, max_pairs).bytes; }
 
-// Sorts (k, v) in place-by-ping-pong over bits [0, total_bits); returns which
-// buffer pair holds the result (0: k0/v0, 1: k1/v1).
-// LSD radix sort of (k, v) on bits [0, total_bits) by ping-pong; returns the
-// buffer pair holding the result (0: k0/v0, 1: k1/v1).  With `rec` set the
-// last pass writes tile keys, ids = rec[v] and masks (see k_radix_downsweep),
-// the ids into final_v when given.
-static int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *count, int total_bits,
-                      uint32_t *hist, uint32_t *dtotal, cudaStream_t s, const uint32_t *rec = nullptr,
-                      uint8_t *masks = nullptr, uint32_t *final_v = nullptr) {
+// LSD radix sort of (k, v) on bits [0, total_bits) by ping-pong, in passes of
+// equal width <= 8.  The last pass writes its values into final_v when given
+// and, with masks set, the block masks and tile ranges instead of the keys.
+// Returns the buffer pair holding the result (0: k0/v0, 1: k1/v1) when
+// final_v is null.
+static int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *count, long long cap,
+                      int total_bits, uint32_t *hist, uint32_t *dtotal, cudaStream_t s, uint32_t *final_v = nullptr,
+                      uint8_t *masks = nullptr, int2 *ranges = nullptr) {
     if (total_bits <= 0) return 0;
     const int passes = (total_bits + 7) / 8;
     const int width = (total_bits + passes - 1) / passes;
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
         const int shift = p * width;
-        const int bits = min(width, total_bits - shift);
-        uint32_t *ki = cur ? k1 : k0, *vi = cur ? v1 : v0, *ko = cur ? k0 : k1, *vo = cur ? v0 : v1;
         const bool last = p == passes - 1;
-        if (last && final_v) vo = final_v;
-        k_radix_upsweep<<<kSortBlocks, kSortThreads, 0, s>>>(ki, count, shift, bits, hist);
-        k_radix_scan<<<1 << bits, kSortBlocks, 0, s>>>(hist, dtotal);
-        k_radix_downsweep<<<kSortBlocks, kSortThreads, 0, s>>>(ki, vi, ko, vo, count, shift, bits, hist, dtotal,
-                                                                last ? rec : nullptr, last ? masks : nullptr);
+        RxPass a;
+        a.kin = cur ? k1 : k0;
+        a.vin = cur ? v1 : v0;
+        a.kout = last ? nullptr : (cur ? k0 : k1);
+        a.vout = (last && final_v) ? final_v : (cur ? v0 : v1);
+        a.count = count;
+        a.cap = cap;
+        a.shift = shift;
+        a.bits = std::min(width, total_bits - shift);
+        a.key_div = 0;
+        a.hist = hist;
+        a.dtotal = dtotal;
+        a.masks = last ? masks : nullptr;
+        a.ranges = last ? ranges : nullptr;
+        rx_pass(a, s);
         cur ^= 1;
     }
     return cur;
@@ -598,18 +626,39 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
                         void *ws, int *status, cudaStream_t s) {
     SortWs w = carve(ws, nrec, max_pairs);
     cudaError_t e = cudaMemsetAsync(counts, 0, 4 * sizeof(int), s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)vt.total_tiles, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)vt.total_tiles, s);
     if (e != cudaSuccess) return e;
 
-    // stage 1: visible records sorted by depth
+    // stage 1: visible records sorted by depth, then stably by view: records in
+    // (view, depth) order, so the emission below gathers one view's records at
+    // a time (an L2-sized working set)
     k_visible_count<<<kSortBlocks, kSortThreads, 0, s>>>(radius, nrec, w.blk);
     k_scan_blocks<<<1, kSortBlocks, 0, s>>>(w.blk, 0, counts, max_pairs, status);
     k_visible_compact<<<kSortBlocks, kSortThreads, 0, s>>>(radius, rgbd, nrec, w.blk, w.dk0, w.dv0);
-    const int dres = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, counts + 0, 32, w.hist, w.dtotal, s);
+    const int dres = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, counts + 0, nrec, 32, w.hist, w.dtotal, s);
     const uint32_t *sorted_rec = dres ? w.dv1 : w.dv0;
+    if (vt.n_views > 1) {
+        int view_bits = 0;
+        while ((1 << view_bits) < vt.n_views) ++view_bits;
+        RxPass a;
+        a.kin = nullptr;
+        a.vin = sorted_rec;
+        a.kout = nullptr;
+        a.vout = dres ? w.dv0 : w.dv1;
+        a.count = counts + 0;
+        a.cap = nrec;
+        a.shift = 0;
+        a.bits = view_bits;
+        a.key_div = ld;
+        a.hist = w.hist;
+        a.dtotal = w.dtotal;
+        a.masks = nullptr;
+        a.ranges = nullptr;
+        rx_pass(a, s);
+        sorted_rec = a.vout;
+    }
 
-    // stage 2: pairs in rank order, then a stable partition by tile
+    // stage 2: pairs in depth order, then a stable partition by tile
     k_tiles_count<<<kSortBlocks, kSortThreads, 0, s>>>(sorted_rec, touched, counts, w.blk);
     k_scan_blocks<<<1, kSortBlocks, 0, s>>>(w.blk, 1, counts, max_pairs, status);
     k_tiles_offsets<<<kSortBlocks, kSortThreads, 0, s>>>(sorted_rec, touched, counts, w.blk, w.off);
@@ -619,17 +668,12 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
                                        w.pv0);
     int tile_bits = 0;
     while ((1ll << tile_bits) < (long long)vt.total_tiles) ++tile_bits;
-    const uint32_t *tkey;
     if (tile_bits > 0) {
-        // the last pass writes tile keys and ids into the other buffer pair
-        const int pres = radix_sort(w.pk0, w.pv0, w.pk1, w.pv1, counts + 1, tile_bits, w.hist, w.dtotal, s,
-                                    sorted_rec, block_mask, (uint32_t *)gauss_ids);
-        tkey = pres ? w.pk1 : w.pk0;
+        radix_sort(w.pk0, w.pv0, w.pk1, w.pv1, counts + 1, max_pairs, tile_bits, w.hist, w.dtotal, s,
+                   (uint32_t *)gauss_ids, block_mask, tile_ranges);
     } else {
-        k_unpack_pairs<<<148 * 8, 256, 0, s>>>(w.pk0, w.pv0, sorted_rec, counts, w.pk1, gauss_ids, block_mask);
-        tkey = w.pk1;
+        k_unpack_pairs<<<148 * 8, 256, 0, s>>>(w.pk0, w.pv0, counts, gauss_ids, block_mask, tile_ranges);
     }
-    k_ranges<<<148 * 8, 256, 0, s>>>(tkey, counts, tile_ranges);
     e = cudaMemsetAsync(w.bucket, 0, sizeof(unsigned int) * 64, s);
     if (e != cudaSuccess) return e;
     const int tb = (int)std::min<long long>(ceil_div(vt.total_tiles, 256), 148 * 4);

@@ -190,7 +190,7 @@ GS_API gs_status gs_segment_workspace_size_items(int64_t items, size_t *bytes) {
 
 GS_API gs_status gs_bwd_workspace_size(int64_t n_records, size_t *bytes) {
     if (!bytes || n_records < 0) return GS_ERR_INVALID;
-    *bytes = align_up(sizeof(float) * (size_t)kAccPlanes * (size_t)n_records, 256);
+    *bytes = align_up(sizeof(float) * (size_t)kAccStride * (size_t)n_records, 256);
     return GS_OK;
 }
 
@@ -352,7 +352,7 @@ GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, i
     if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < need) return GS_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     float *acc = (float *)ws;
-    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)kAccPlanes * nrec, s);
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)kAccStride * nrec, s);
     if (e != cudaSuccess) return GS_ERR_CUDA;
     launch_render_bwd(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, binning->block_mask,
                       binning->tile_order, (const float2 *)proj->xy,

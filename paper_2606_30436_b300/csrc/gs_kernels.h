@@ -8,11 +8,16 @@
 namespace gs {
 
 // Per-record accumulator planes written by the compositing backward and read by
-// the projection backward (plane p of record r at acc[p * nrec + r]).
+// the projection backward, record-major: value p of record r at
+// acc[r * kAccStride + p], so the sums of one record sit in one 64-byte line
+// and a lane adds four of them with one vector atomic.
 enum AccPlane {
     kAccU = 0, kAccV, kAccA, kAccB, kAccC, kAccO, kAccR, kAccG, kAccBl, kAccZ,
     kAccOmega, kAccKappa, kAccMaxW, kAccPlanes
 };
+constexpr int kAccStride = 16;
+static_assert(kAccU == 0 && kAccC == 4 && kAccBl == 8 && kAccOmega == 10 && kAccKappa == 11 && kAccMaxW == 12,
+              "the vector reads and atomics group the sums four by four");
 
 void launch_project(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
                     float2 *xy, float4 *co, float4 *rgbd, int *radius, int *touched, int *status, cudaStream_t s);

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 3) k_pr
             float raw = 0.5f;
             #pragma unroll
             for (int k = 0; k < K; ++k) raw += Y[k] * sh[k];
-            const float gcv = raw < 0.0f ? 0.0f : acc[(kAccR + ch) * nrec + rec];
+            const float gcv = raw < 0.0f ? 0.0f : acc[rec * kAccStride + kAccR + ch];
             #pragma unroll
             for (int k = 0; k < K; ++k) gsh[k] += gcv * Y[k];
             if (D > 0) {
@@ -373,19 +373,22 @@ __global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 3) k_pr
         if (radius[rec] <= 0) continue;
         seen = true;
         const ViewDesc &c = vt.v[v];
-        const float du = acc[kAccU * nrec + rec], dv = acc[kAccV * nrec + rec];
+        // the record's sums: u v a b | c o r g | b z omega kappa | maxw
+        const float4 *a4 = reinterpret_cast<const float4 *>(acc + rec * kAccStride);
+        const float4 s0 = a4[0], s1 = a4[1], s2 = a4[2];
+        const float du = s0.x, dv = s0.y;
         if (stats) {
-            const float om = acc[kAccOmega * nrec + rec];
+            const float om = s2.z;
             st_omega += om;
-            st_kappa += acc[kAccKappa * nrec + rec];
+            st_kappa += s2.w;
             st_gamma += (loss_per_view ? loss_per_view[v] : 0.0f) * om;
-            st_maxw = fmaxf(st_maxw, acc[kAccMaxW * nrec + rec]);
+            st_maxw = fmaxf(st_maxw, acc[rec * kAccStride + kAccMaxW]);
             st_gnorm += sqrtf(du * du + dv * dv);
             st_views += om > 0.0f ? 1.0f : 0.0f;
         }
-        glogit += acc[kAccO * nrec + rec] * o * (1.0f - o);
-        const float da = acc[kAccA * nrec + rec], db = acc[kAccB * nrec + rec], dc = acc[kAccC * nrec + rec];
-        const float gdepth = acc[kAccZ * nrec + rec];
+        glogit += s1.y * o * (1.0f - o);
+        const float da = s0.z, db = s0.w, dc = s1.x;
+        const float gdepth = s2.y;
         const ExactPos p = exact_position(c, mx, my, mz);
         const float x = p.xc, y = p.yc, z = p.zc;
         const Ewa e = ewa(c, x, y, z, S);

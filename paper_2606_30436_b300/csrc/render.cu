@@ -698,18 +698,15 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
                     }
                     if (STATS) { v[kAccOmega] = 1.0f; v[kAccKappa] = mask; v[kAccMaxW] = w; }
                 }
-                const long long r = s_id[warp][k];
+                float *ar = acc + (long long)s_id[warp][k] * kAccStride;  // this record's sums
                 if (__popc(act) <= kDirectLanes) {
-                    // a single pixel: its lane issues the updates itself
+                    // a few pixels: each active lane adds its values itself, four per vector atomic
                     if (on) {
-                        #pragma unroll
-                        for (int cc = 0; cc < kAccGrad; ++cc)
-                            if (cc != kAccZ || has_depth) atomicAdd(&acc[cc * nrec + r], v[cc]);
-                        if (STATS) {
-                            atomicAdd(&acc[kAccOmega * nrec + r], v[kAccOmega]);
-                            if (v[kAccKappa] > 0.0f) atomicAdd(&acc[kAccKappa * nrec + r], v[kAccKappa]);
-                            atomicMax((int *)&acc[kAccMaxW * nrec + r], __float_as_int(v[kAccMaxW]));  // w >= 0
-                        }
+                        float4 *a4 = reinterpret_cast<float4 *>(ar);
+                        atomicAdd(a4, make_float4(v[kAccU], v[kAccV], v[kAccA], v[kAccB]));
+                        atomicAdd(a4 + 1, make_float4(v[kAccC], v[kAccO], v[kAccR], v[kAccG]));
+                        atomicAdd(a4 + 2, make_float4(v[kAccBl], v[kAccZ], v[kAccOmega], v[kAccKappa]));
+                        if (STATS) atomicMax((int *)&ar[kAccMaxW], __float_as_int(v[kAccMaxW]));  // w >= 0
                     }
                 } else {
                     const float mw = STATS ? warp_max(v[kAccMaxW]) : 0.0f;
@@ -717,8 +714,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
                     const int plane = (lane >> 1) & 15;
                     const bool mine = (lane & 1) == 0 && plane < (STATS ? kAccMaxW : kAccGrad) &&
                                       (plane != kAccZ || has_depth) && (plane != kAccKappa || tot > 0.0f);
-                    if (mine) atomicAdd(&acc[plane * nrec + r], tot);
-                    if (STATS && lane == 1) atomicMax((int *)&acc[kAccMaxW * nrec + r], __float_as_int(mw));
+                    if (mine) atomicAdd(&ar[plane], tot);
+                    if (STATS && lane == 1) atomicMax((int *)&ar[kAccMaxW], __float_as_int(mw));
                 }
             }
             __syncwarp();

@@ -522,7 +522,7 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 constexpr int kAccGrad = 10;   // u v a b c o r g b z
-constexpr int kDirectLanes = 8;  // up to this many active lanes: each issues its own reductions
+constexpr int kDirectLanes = 16;  // up to this many active lanes: each issues its own (vector) atomics
 
 // Sums 16 values over the warp by recursive halving: at each of the four
 // steps a lane swaps half of its partial sums with its partner and keeps the

@@ -525,11 +525,11 @@ def run_gpu(args, rank, world):
 def run_memory(args, dev):
     """Peak device memory of one mapping iteration at 10M Gaussians (the
     single-view distribution of the 10k parity case), 1920x1080, fx = fy = 1800,
-    with the backward recomputing the blending from T_final and `last`; the
-    memory a stored per-pixel list backward would add (one Gaussian id and one
-    alpha, 8 bytes, per blend event, counted by the backward's |Omega|
-    statistic); and the gradient of a quarter-resolution centre crop of the same
-    view against the FP64 oracle."""
+    for both backward designs: recomputing the blending from T_final and
+    `last`, and walking per-pixel lists (record id and alpha, 8 bytes per
+    blend event) stored by the forward; each arm's time per iteration and the
+    gradient of a quarter-resolution centre crop of the same view against the
+    FP64 oracle."""
     import torch
     import oracle as orc
     from paper_2606_30436_b300 import gs, scenes
@@ -537,39 +537,48 @@ def run_memory(args, dev):
     scene = scenes.uniform_scene(n, seed=0, sh_degree=0)
     tscene = scenes.perturb(scene, 0.01, seed=1)
     cam = scenes.pinhole(w, h, f)
-    cfg = gs.Config()
     tm = gs.GaussianModel.from_scene(tscene, device=dev)
-    ts = gs.MappingStep(tm, [cam], cfg, with_stats=False)
+    ts = gs.MappingStep(tm, [cam], gs.Config(), with_stats=False)
     ts.fit_capacity()
     target = ts.buf.img.clone()
     del ts, tm
     torch.cuda.synchronize()
-    torch.cuda.empty_cache()
-    torch.cuda.reset_peak_memory_stats(dev)
-    model = gs.GaussianModel.from_scene(scene, device=dev)
-    st = gs.MappingStep(model, [cam], cfg, lambda_dssim=LAMBDA)
-    needed = st.fit_capacity(slack=1.05)
-    st.buf.stats_acc.zero_()
-    st.step(target, optimize=False)
-    torch.cuda.synchronize()
-    events = float(st.buf.stats_acc[0, :n].double().sum().item())
-    for _ in range(2):
-        st.step(target)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.memory_iters):
-        st.step(target)
-    e1.record()
-    torch.cuda.synchronize()
-    st.check_status()
-    peak = torch.cuda.max_memory_allocated(dev)
-    ms = e0.elapsed_time(e1) / args.memory_iters
-    params_bytes = model.data.numel() * 4
-    stored_extra = 8.0 * events
-    del st, model
+
+    def arm(stored):
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats(dev)
+        model = gs.GaussianModel.from_scene(scene, device=dev)
+        # no split of long tile lists in either arm: on this dense view every tile is long and saturates
+        # early, where the split only adds segment state (the autotuner's choice for dense views too)
+        st = gs.MappingStep(model, [cam], gs.Config(segment=0), lambda_dssim=LAMBDA, stored_lists=stored)
+        needed = st.fit_capacity(slack=1.05)
+        st.buf.stats_acc.zero_()
+        st.step(target, optimize=False)
+        torch.cuda.synchronize()
+        events = float(st.buf.stats_acc[0, :n].double().sum().item())
+        for _ in range(2):
+            st.step(target)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.memory_iters):
+            st.step(target)
+        e1.record()
+        torch.cuda.synchronize()
+        st.check_status()
+        out = {"peak_gb": round(torch.cuda.max_memory_allocated(dev) / 1e9, 3),
+               "ms_per_iter": round(e0.elapsed_time(e1) / args.memory_iters, 3), "pairs": int(needed),
+               "blend_events": int(events)}
+        if stored:
+            out["list_gb"] = round(st.lists.nbytes() / 1e9, 3)
+            out["list_events"] = st.lists.events()
+        del st, model
+        return out
+
+    recompute = arm(False)
+    stored = arm(True)
     torch.cuda.empty_cache()
 
-    # quarter-resolution centre crop: GPU gradient vs the FP64 oracle
+    # quarter-resolution centre crop: both arms' gradients vs the FP64 oracle
     cw, ch = w // 4, h // 4
     crop = dict(cam, width=cw, height=ch, cx=cam["cx"] - (w - cw) / 2, cy=cam["cy"] - (h - ch) / 2)
     oc = orc.Cfg()
@@ -577,29 +586,29 @@ def run_memory(args, dev):
     tgt = orc.forward(tscene, crop, oc)["img"]
     fo = orc.loss_and_grads(scene, crop, oc, tgt, LAMBDA)
     oracle_s = time.perf_counter() - t0
-    model = gs.GaussianModel.from_scene(scene, device=dev)
-    sc = gs.MappingStep(model, [crop], cfg, lambda_dssim=LAMBDA)
-    sc.fit_capacity()
-    sc.step(torch.from_numpy(tgt.astype(np.float32).reshape(-1)).to(dev), optimize=False)
-    torch.cuda.synchronize()
-    sc.check_status()
-    g = gs.unpack_planes(sc.grads.data.cpu().numpy(), n, 0)
-    err = {}
-    for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
-        a, b = np.asarray(g[k], np.float64), np.asarray(fo["grads"][k], np.float64)
-        err[k] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    for res, is_stored in ((recompute, False), (stored, True)):
+        model = gs.GaussianModel.from_scene(scene, device=dev)
+        sc = gs.MappingStep(model, [crop], gs.Config(segment=0), lambda_dssim=LAMBDA, stored_lists=is_stored)
+        sc.fit_capacity()
+        sc.step(torch.from_numpy(tgt.astype(np.float32).reshape(-1)).to(dev), optimize=False)
+        torch.cuda.synchronize()
+        sc.check_status()
+        g = gs.unpack_planes(sc.grads.data.cpu().numpy(), n, 0)
+        err = {}
+        for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+            a, b = np.asarray(g[k], np.float64), np.asarray(fo["grads"][k], np.float64)
+            err[k] = round(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)), 7)
+        res["crop_gradient_rel_l2_vs_oracle"] = err
+        del sc, model
+        torch.cuda.empty_cache()
     return {"metric": "peak device memory of one mapping iteration, recompute-in-backward vs stored per-pixel lists",
-            "unit": "GB", "value": round(peak / 1e9, 3),
+            "unit": "GB", "value": recompute["peak_gb"],
             "config": {"workload": "%d Gaussians (x, y ~ U[-5, 5], z ~ U[2, 20], SH0), 1920x1080, fx = fy = 1800, "
                                    "fwd + L1/D-SSIM(0.2) + bwd + stats + Adam" % n},
-            "pairs": int(needed), "ms_per_iter": round(ms, 3), "parameters_gb": round(params_bytes / 1e9, 3),
-            "blend_events": int(events),
-            "stored_lists": {"built": False, "extra_gb": round(stored_extra / 1e9, 3),
-                             "peak_gb_estimate": round((peak + stored_extra) / 1e9, 3),
-                             "bytes_per_event": 8,
-                             "basis": "one Gaussian id and one alpha per (pixel, blended Gaussian), the count from "
-                                      "the backward's |Omega| statistic summed over Gaussians"},
-            "crop_gradient_rel_l2_vs_oracle": {k: round(v, 7) for k, v in err.items()},
+            "recompute": recompute,
+            "stored_lists": dict(stored, built=True, bytes_per_event=8,
+                                 design="the forward stores (record id, alpha) per blended Gaussian per pixel; "
+                                        "the backward walks each pixel's list from the back"),
             "crop": "%dx%d centre crop of the same view; oracle %.1f s on %d cores" % (cw, ch, oracle_s, cpu_cores()),
             "data": "synthetic", "n_gpus": 1}
 

@@ -315,10 +315,10 @@ gs_status gs_loss_static(const float *img, const float *target, const gs_camera 
  * the workspace; then chains through the projection to every parameter plane
  * (as gs_project_bwd).  grads (same layout as params) is overwritten, or
  * accumulated into when accumulate != 0; with grads = NULL only the
- * compositing half runs and the per-record gradients stay in ws (record r's
- * plane p at float index p * n_records + r, planes dL/du, dL/dv, dL/da,
- * dL/db, dL/dc, dL/dopacity, dL/dr, dL/dg, dL/db, dL/dz, |Omega_v|, kappa_v,
- * max T*alpha).
+ * compositing half runs and the per-record gradients stay in ws, record
+ * major: record r's value p at float index r * 16 + p, values dL/du, dL/dv,
+ * dL/da, dL/db, dL/dc, dL/dopacity, dL/dr, dL/dg, dL/db, dL/dz, |Omega_v|,
+ * kappa_v, max T*alpha (p = 0..12; 13..15 unused).
  * dL_ddepth is nullable.  stats (nullable) receives the lifecycle
  * accumulators (Supp. E.1, E.2): per pixel the error mask
  * M_v = [sum_c |I - I^| > tau_err] (tau_err = 0.1, Supp. F) with the
@@ -331,6 +331,44 @@ gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, int32_t 
                         const float *dL_ddepth, const float *target, const float *loss_per_view,
                         float tau_err, const gs_params *grads, int32_t accumulate,
                         const gs_stats *stats, void *ws, size_t ws_bytes, gs_stream stream);
+
+/*
+ * Stored per-pixel lists, the alternative to recomputing the blending in the
+ * backward (the backward of the compositing sum of Supp. D.2 either way).
+ * gs_render_fwd_lists renders exactly as gs_render_fwd without the split of
+ * long tile lists (frame->seg_ws is not used) and records, per pixel of the
+ * frame layout (views back to back), the record id and alpha of every
+ * Gaussian the pixel blends, front to back: list_offsets [total_pixels + 1]
+ * int64 (device, 8-byte aligned) gets each pixel's first slot and, at
+ * [total_pixels], the number of blend events; list_ids (int32) and
+ * list_alpha (float) [list_capacity] get the events.  When the events exceed
+ * list_capacity, status gets bit 1<<GS_ERR_CAPACITY, only the slots below the
+ * capacity are written, and the count at list_offsets[total_pixels] tells
+ * the caller what to allocate.  ws: gs_list_workspace_size bytes (256-byte
+ * aligned).  Memory: 8 bytes per blend event and 8 per pixel, against none
+ * for gs_render_bwd's recompute.
+ */
+gs_status gs_list_workspace_size(int64_t total_pixels, size_t *bytes);
+gs_status gs_render_fwd_lists(const gs_projected *proj, const gs_binning *binning, const gs_camera *cams,
+                              int32_t n_views, const gs_raster_cfg *cfg, const gs_frame *frame, int64_t *list_offsets,
+                              int32_t *list_ids, float *list_alpha, int64_t list_capacity, void *ws, size_t ws_bytes,
+                              int32_t *status, gs_stream stream);
+
+/*
+ * Backward of compositing from the stored lists, then through the projection
+ * as gs_render_bwd (same outputs, same workspace layout): one thread per
+ * pixel walks its events from the back, T_j = T_{j+1} / (1 - alpha_j) from
+ * the stored alpha, the colour behind carried; alpha below alpha_max counts
+ * as unclamped (exp(power) = alpha / opacity).  No depth term.  The lists
+ * must come from a gs_render_fwd_lists call of the same frame that did not
+ * overflow.
+ */
+gs_status gs_render_bwd_lists(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                              const gs_raster_cfg *cfg, const gs_projected *proj, const gs_frame *frame,
+                              const int64_t *list_offsets, const int32_t *list_ids, const float *list_alpha,
+                              int64_t list_capacity, const float *dL_dimg, const float *target,
+                              const float *loss_per_view, float tau_err, const gs_params *grads, int32_t accumulate,
+                              const gs_stats *stats, void *ws, size_t ws_bytes, gs_stream stream);
 
 /*
  * The projection half of gs_render_bwd: chain rule from the per-record

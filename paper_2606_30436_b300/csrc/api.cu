@@ -366,6 +366,77 @@ GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, i
     return cuda_status(cudaGetLastError());
 }
 
+GS_API gs_status gs_list_workspace_size(int64_t total_pixels, size_t *bytes) {
+    if (!bytes || total_pixels < 0) return GS_ERR_INVALID;
+    *bytes = list_scan_bytes(total_pixels);
+    return GS_OK;
+}
+
+GS_API gs_status gs_render_fwd_lists(const gs_projected *proj, const gs_binning *binning, const gs_camera *cams,
+                                     int32_t n_views, const gs_raster_cfg *cfg, const gs_frame *frame,
+                                     int64_t *list_offsets, int32_t *list_ids, float *list_alpha,
+                                     int64_t list_capacity, void *ws, size_t ws_bytes, int32_t *status,
+                                     gs_stream stream) {
+    ViewTable vt;
+    RasterCfg rc;
+    gs_status st = build_views(cams, n_views, cfg, vt, rc);
+    if (st != GS_OK) return st;
+    if (!proj || check_proj(proj, proj->ld) != GS_OK || check_binning(binning) != GS_OK) return GS_ERR_INVALID;
+    if (!frame || !frame->img || !frame->T_final || !frame->last) return GS_ERR_INVALID;
+    if (!list_offsets || ((uintptr_t)list_offsets & 7u) || list_capacity < 0) return GS_ERR_INVALID;
+    if (list_capacity > 0 && (!list_ids || !list_alpha)) return GS_ERR_INVALID;
+    long long npx = 0;
+    for (int v = 0; v < n_views; ++v) npx += (long long)cams[v].width * cams[v].height;
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < list_scan_bytes(npx)) return GS_ERR_INVALID;
+    launch_render_fwd_lists(vt, rc, (const int2 *)binning->tile_ranges, binning->gauss_ids, binning->block_mask,
+                            binning->tile_order, (const float2 *)proj->xy, (const float4 *)proj->conic_opacity,
+                            (const float4 *)proj->rgb_depth, frame->img, frame->T_final, frame->last, frame->depth, npx,
+                            (long long *)list_offsets, list_ids, list_alpha, list_capacity, ws, status,
+                            (cudaStream_t)stream);
+    return cuda_status(cudaGetLastError());
+}
+
+GS_API gs_status gs_render_bwd_lists(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                                     const gs_raster_cfg *cfg, const gs_projected *proj, const gs_frame *frame,
+                                     const int64_t *list_offsets, const int32_t *list_ids, const float *list_alpha,
+                                     int64_t list_capacity, const float *dL_dimg, const float *target,
+                                     const float *loss_per_view, float tau_err, const gs_params *grads,
+                                     int32_t accumulate, const gs_stats *stats, void *ws, size_t ws_bytes,
+                                     gs_stream stream) {
+    ViewTable vt;
+    RasterCfg rc;
+    gs_status st = build_views(cams, n_views, cfg, vt, rc);
+    if (st == GS_OK) st = check_params(params);
+    if (st == GS_OK && grads) st = check_params(grads);
+    if (st != GS_OK) return st;
+    if (grads && (grads->ld != params->ld || grads->n != params->n || grads->sh_degree != params->sh_degree))
+        return GS_ERR_INVALID;
+    if (!proj || check_proj(proj, params->ld) != GS_OK) return GS_ERR_INVALID;
+    if (!frame || !frame->img || !frame->T_final || !dL_dimg) return GS_ERR_INVALID;
+    if (!list_offsets || list_capacity < 0 || (list_capacity > 0 && (!list_ids || !list_alpha))) return GS_ERR_INVALID;
+    const bool want_stats = stats != nullptr;
+    if (want_stats && (!stats->acc || stats->ld < params->n || !target)) return GS_ERR_INVALID;
+    const long long nrec = (long long)n_views * params->ld;
+    size_t need = 0;
+    gs_bwd_workspace_size(nrec, &need);
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < need) return GS_ERR_INVALID;
+    long long npx = 0;
+    for (int v = 0; v < n_views; ++v) npx += (long long)cams[v].width * cams[v].height;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *acc = (float *)ws;
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)kAccStride * nrec, s);
+    if (e != cudaSuccess) return GS_ERR_CUDA;
+    launch_render_bwd_lists(vt, rc, npx, (const long long *)list_offsets, list_ids, list_alpha, list_capacity,
+                            (const float2 *)proj->xy, (const float4 *)proj->conic_opacity,
+                            (const float4 *)proj->rgb_depth, frame->img, frame->T_final, dL_dimg, target, tau_err,
+                            want_stats, acc, s);
+    if (grads)
+        launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius, acc, nrec,
+                           grads->data, accumulate, loss_per_view, want_stats ? stats->acc : nullptr,
+                           want_stats ? stats->ld : 0, s);
+    return cuda_status(cudaGetLastError());
+}
+
 GS_API gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views,
                                 const gs_raster_cfg *cfg, const gs_projected *proj, const void *ws, size_t ws_bytes,
                                 const float *loss_per_view, const gs_params *grads, int32_t accumulate,

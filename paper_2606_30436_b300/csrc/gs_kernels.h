@@ -43,6 +43,16 @@ void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ra
                        const float4 *rgbd, float *img, float *T_final, int *last, float *depth, const SegWs &seg,
                        cudaStream_t s);
 
+size_t list_scan_bytes(long long npx);
+void launch_render_fwd_lists(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
+                             const uint8_t *masks, const int *order, const float2 *xy, const float4 *co,
+                             const float4 *rgbd, float *img, float *T_final, int *last, float *depth, long long npx,
+                             long long *count_off, int *lid, float *lal, long long cap, void *scan_ws, int *status,
+                             cudaStream_t s);
+void launch_render_bwd_lists(const ViewTable &vt, const RasterCfg &cfg, long long npx, const long long *off,
+                             const int *lid, const float *lal, long long cap, const float2 *xy, const float4 *co,
+                             const float4 *rgbd, const float *img, const float *T_final, const float *dL_dimg,
+                             const float *target, float tau_err, bool stats, float *acc, cudaStream_t s);
 void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
                        const uint8_t *masks, const int *order, const float2 *xy, const float4 *co, const float4 *rgbd,
                        const float *img, const float *T_final,

@@ -134,6 +134,14 @@ struct FwdShared {
     float2 *p;
     float4 *q, *c;
     int *pos, *list;
+    int *id;  // record ids of the staged pairs (only for a blend hook that needs them)
+};
+
+// What the forward does besides compositing when a pixel blends a Gaussian
+// (k: the pair's slot among the 32 staged, a: its alpha): nothing, normally.
+struct NoBlendHook {
+    static constexpr bool kNeedsId = false;
+    __device__ __forceinline__ void operator()(const FwdShared &, int, float) {}
 };
 
 // Front-to-back compositing of the pairs of [lo, hi) (positions in the tile's
@@ -141,12 +149,12 @@ struct FwdShared {
 // the stop rule of Supp. D.2 (stop before the pair that takes T below t_min).
 // alpha of 8 staged pairs at a time (independent, so their latencies overlap),
 // then the short serial transmittance update over them.
-template <int WIN>
+template <int WIN, class Hook = NoBlendHook>
 __device__ __forceinline__ void fwd_range(const RasterCfg &cfg, const uint8_t *__restrict__ masks,
                                           const int *__restrict__ ids, const float2 *__restrict__ xy,
                                           const float4 *__restrict__ co, const float4 *__restrict__ rgbd, int rgx,
                                           int lo, int hi, int bit, float fx, float fy, FwdState &st,
-                                          const FwdShared &sh) {
+                                          const FwdShared &sh, Hook hook = Hook()) {
     const int lane = threadIdx.x & 31;
     for (int w = lo & ~15; w < hi && !__all_sync(0xffffffffu, st.done); w += WIN) {
         const int total = scan_window<WIN>(masks, w, lo, hi, bit, sh.list);
@@ -158,6 +166,7 @@ __device__ __forceinline__ void fwd_range(const RasterCfg &cfg, const uint8_t *_
             sh.q[lane] = cur.q;
             sh.c[lane] = cur.c;
             sh.pos[lane] = cur.pos;
+            if (Hook::kNeedsId) sh.id[lane] = cur.id;
             __syncwarp();
             const int cnt = min(32, total - c);
             for (int k0 = 0; k0 < cnt && !st.done; k0 += 8) {
@@ -189,6 +198,7 @@ __device__ __forceinline__ void fwd_range(const RasterCfg &cfg, const uint8_t *_
                             st.C0 += cc.x * wgt; st.C1 += cc.y * wgt; st.C2 += cc.z * wgt; st.D += cc.w * wgt;
                             st.T = Tn;
                             st.last = sh.pos[k0 + j] - rgx + 1;
+                            hook(sh, k0 + j, a);
                         }
                     }
                 }
@@ -318,7 +328,7 @@ __global__ void __launch_bounds__(32 * kWarps, 8) k_render_fwd(ViewTable vt, Ras
     __shared__ float4 s_c[kWarps][32];
     __shared__ int s_pos[kWarps][32];
     const int warp = threadIdx.x >> 5;
-    const FwdShared sh{s_p[warp], s_q[warp], s_c[warp], s_pos[warp], s_list[warp]};
+    const FwdShared sh{s_p[warp], s_q[warp], s_c[warp], s_pos[warp], s_list[warp], nullptr};
     if ((int)blockIdx.x < item_blocks) {
         const int n = min(seg.count[0], seg.fcap);
         for (int it = blockIdx.x * kWarps + warp; it < n; it += item_blocks * kWarps) {
@@ -460,7 +470,7 @@ __global__ void __launch_bounds__(32 * kWarps, 1) k_render_fwd_rerun(ViewTable v
     __shared__ float4 s_c[kWarps][32];
     __shared__ int s_pos[kWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const FwdShared sh{s_p[warp], s_q[warp], s_c[warp], s_pos[warp], s_list[warp]};
+    const FwdShared sh{s_p[warp], s_q[warp], s_c[warp], s_pos[warp], s_list[warp], nullptr};
     const int n = min(seg.count[3], seg.fcap);
     for (int k = blockIdx.x * kWarps + warp; k < n; k += gridDim.x * kWarps) {
         const int4 task = seg.tasks[k];
@@ -737,6 +747,221 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
     work(unit, -1, 0);
 }
 
+// ---------------------------------------------------------------------------
+// Stored per-pixel lists: the alternative to recomputing the blending in the
+// backward (the paper composites sorted Gaussians along each ray, Supp. D.2;
+// either backward differentiates that sum).  The forward records, for every
+// pixel, the record id and alpha of each Gaussian it blends, front to back: a
+// counting pass (which also renders), an exclusive scan of the counts into
+// offsets, and a storing pass.  The backward walks each pixel's list from the
+// back, one thread per pixel, and adds each event's sums to its record with
+// vector atomics.  The compositing itself is the unsplit traversal of
+// k_render_fwd, bit for bit.
+
+struct ListHook {
+    static constexpr bool kNeedsId = true;
+    long long base, cap;
+    long long *n;  // this lane's count of blend events so far
+    int *__restrict__ lid;
+    float *__restrict__ lal;
+    bool store;
+    __device__ __forceinline__ void operator()(const FwdShared &sh, int k, float a) {
+        const long long j = base + *n;
+        if (store && j < cap) {
+            lid[j] = sh.id[k];
+            lal[j] = a;
+        }
+        ++*n;
+    }
+};
+
+template <int WIN, bool STORE>
+__global__ void __launch_bounds__(32 * kWarps) k_render_fwd_lists(ViewTable vt, RasterCfg cfg,
+                                                                  const int2 *__restrict__ ranges,
+                                                                  const int *__restrict__ ids,
+                                                                  const uint8_t *__restrict__ masks,
+                                                                  const int *__restrict__ order,
+                                                                  const float2 *__restrict__ xy,
+                                                                  const float4 *__restrict__ co,
+                                                                  const float4 *__restrict__ rgbd,
+                                                                  float *__restrict__ img, float *__restrict__ T_final,
+                                                                  int *__restrict__ last, float *__restrict__ depth,
+                                                                  long long *__restrict__ count_off,
+                                                                  int *__restrict__ lid, float *__restrict__ lal,
+                                                                  long long cap) {
+    __shared__ int s_list[kWarps][WIN];
+    __shared__ float2 s_p[kWarps][32];
+    __shared__ float4 s_q[kWarps][32];
+    __shared__ float4 s_c[kWarps][32];
+    __shared__ int s_pos[kWarps][32];
+    __shared__ int s_id[kWarps][32];
+    const int warp = threadIdx.x >> 5;
+    const FwdShared sh{s_p[warp], s_q[warp], s_c[warp], s_pos[warp], s_list[warp], s_id[warp]};
+    const int unit = blockIdx.x * kWarps + warp;
+    if (unit >= vt.total_tiles * 8) return;
+    const int tile = order[unit >> 3], bit = unit & 7;
+    const int2 rg = ranges[tile];
+    const Unit t = unit_ctx(vt, tile, bit);
+    FwdState st{1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0, !t.inside};
+    long long n = 0;
+    ListHook hook{STORE && t.inside ? count_off[t.pix] : 0, cap, &n, lid, lal, STORE};
+    fwd_range<WIN, ListHook>(cfg, masks, ids, xy, co, rgbd, rg.x, rg.x, rg.y, bit, t.px + 0.5f, t.py + 0.5f, st, sh,
+                             hook);
+    if (STORE) return;
+    fwd_write(cfg, t, st, img, T_final, last, depth);
+    if (t.inside) count_off[t.pix] = n;
+}
+
+// Exclusive scan of the per-pixel counts into offsets, in place, over 4096
+// pixels per CTA (4 per thread); count_off[npx] gets the total.
+constexpr int kListScanThreads = 1024, kListScanItems = 4;
+constexpr int kListScanTile = kListScanThreads * kListScanItems;
+
+__device__ __forceinline__ long long block_scan_ll(long long x, long long &total, long long *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long inc = x;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) sm[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const long long wv = sm[lane];  // 32 warps
+        long long wi = wv;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        sm[lane] = wi - wv;
+        if (lane == 31) sm[32] = wi;
+    }
+    __syncthreads();
+    const long long r = sm[warp] + inc - x;
+    total = sm[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kListScanThreads) k_list_scan_sums(const long long *__restrict__ cnt, long long npx,
+                                                                     long long *__restrict__ bsum) {
+    __shared__ long long sm[33];
+    long long x = 0;
+    const long long b = (long long)blockIdx.x * kListScanTile + threadIdx.x * kListScanItems;
+    #pragma unroll
+    for (int i = 0; i < kListScanItems; ++i) x += b + i < npx ? cnt[b + i] : 0;
+    long long total;
+    block_scan_ll(x, total, sm);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// One CTA: exclusive scan of the CTA sums; the total and the capacity check.
+__global__ void __launch_bounds__(kListScanThreads) k_list_scan_top(long long *__restrict__ bsum, int nb,
+                                                                    long long *__restrict__ count_off, long long npx,
+                                                                    long long cap, int *__restrict__ status) {
+    __shared__ long long sm[33];
+    long long run = 0;
+    for (int b0 = 0; b0 < nb; b0 += kListScanThreads) {
+        const int b = b0 + threadIdx.x;
+        const long long x = b < nb ? bsum[b] : 0;
+        long long total;
+        const long long ex = block_scan_ll(x, total, sm);
+        if (b < nb) bsum[b] = run + ex;
+        run += total;
+    }
+    if (threadIdx.x == 0) {
+        count_off[npx] = run;
+        if (run > cap && status) atomicOr(status, 1 << GS_ERR_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(kListScanThreads) k_list_scan_apply(long long *__restrict__ count_off, long long npx,
+                                                                      const long long *__restrict__ bsum) {
+    __shared__ long long sm[33];
+    const long long b = (long long)blockIdx.x * kListScanTile + threadIdx.x * kListScanItems;
+    long long c[kListScanItems], x = 0;
+    #pragma unroll
+    for (int i = 0; i < kListScanItems; ++i) {
+        c[i] = b + i < npx ? count_off[b + i] : 0;
+        x += c[i];
+    }
+    long long total;
+    long long run = bsum[blockIdx.x] + block_scan_ll(x, total, sm);
+    #pragma unroll
+    for (int i = 0; i < kListScanItems; ++i) {
+        if (b + i < npx) count_off[b + i] = run;
+        run += c[i];
+    }
+}
+
+// One thread per pixel: the pixel's blend events from the back, T recovered
+// by division as in k_render_bwd, the colour behind carried; alpha is the
+// stored one (unclamped when below alpha_max, where G = alpha / opacity).
+template <bool STATS>
+__global__ void __launch_bounds__(256) k_render_bwd_lists(ViewTable vt, RasterCfg cfg, long long npx,
+                                                          const long long *__restrict__ off,
+                                                          const int *__restrict__ lid, const float *__restrict__ lal,
+                                                          long long cap, const float2 *__restrict__ xy,
+                                                          const float4 *__restrict__ co,
+                                                          const float4 *__restrict__ rgbd,
+                                                          const float *__restrict__ img,
+                                                          const float *__restrict__ T_final,
+                                                          const float *__restrict__ dL_dimg,
+                                                          const float *__restrict__ target, float tau_err,
+                                                          float *__restrict__ acc) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
+         q += (long long)gridDim.x * blockDim.x) {
+        int v = 0;
+        while (v + 1 < vt.n_views && vt.v[v + 1].pix_offset <= q) ++v;
+        const ViewDesc &c = vt.v[v];
+        const long long local = q - c.pix_offset;
+        const int py = (int)(local / c.W), px = (int)(local - (long long)py * c.W);
+        const long long plane = (long long)c.W * c.H, i0 = 3 * c.pix_offset + local;
+        const float fx = px + 0.5f, fy = py + 0.5f;
+        float T = T_final[q];
+        const float g0 = dL_dimg[i0], g1 = dL_dimg[i0 + plane], g2 = dL_dimg[i0 + 2 * plane];
+        float mask = 0.0f;
+        if (STATS) {
+            const float e = fabsf(target[i0] - img[i0]) + fabsf(target[i0 + plane] - img[i0 + plane]) +
+                            fabsf(target[i0 + 2 * plane] - img[i0 + 2 * plane]);
+            mask = e > tau_err ? 1.0f : 0.0f;
+        }
+        float R0 = cfg.bg[0], R1 = cfg.bg[1], R2 = cfg.bg[2];
+        const long long b = off[q], e = min(off[q + 1], cap);
+        for (long long j = e - 1; j >= b; --j) {
+            const int r = lid[j];
+            const float alpha = lal[j];
+            const float2 p = xy[r];
+            const float4 qq = co[r];
+            const float4 col = rgbd[r];
+            const float dx = fx - p.x, dy = fy - p.y;
+            T = __fdividef(T, 1.0f - alpha);
+            const float w = alpha * T;
+            const float dLda = T * (g0 * (col.x - R0) + g1 * (col.y - R1) + g2 * (col.z - R2));
+            R0 = alpha * col.x + (1.0f - alpha) * R0;
+            R1 = alpha * col.y + (1.0f - alpha) * R1;
+            R2 = alpha * col.z + (1.0f - alpha) * R2;
+            float vo = 0.0f, vu = 0.0f, vv = 0.0f, va = 0.0f, vb = 0.0f, vc = 0.0f;
+            if (alpha < cfg.alpha_max) {  // alpha not clamped
+                vo = dLda * alpha / qq.w;
+                const float dp = dLda * alpha;
+                vu = dp * (qq.x * dx + qq.y * dy);
+                vv = dp * (qq.z * dy + qq.y * dx);
+                va = -0.5f * dp * dx * dx;
+                vb = -dp * dx * dy;
+                vc = -0.5f * dp * dy * dy;
+            }
+            float4 *a4 = reinterpret_cast<float4 *>(acc + (long long)r * kAccStride);
+            atomicAdd(a4, make_float4(vu, vv, va, vb));
+            atomicAdd(a4 + 1, make_float4(vc, vo, g0 * w, g1 * w));
+            atomicAdd(a4 + 2, make_float4(g2 * w, 0.0f, STATS ? 1.0f : 0.0f, mask));
+            if (STATS) atomicMax((int *)&acc[(long long)r * kAccStride + kAccMaxW], __float_as_int(w));
+        }
+    }
+}
+
 static int sm_count() {
     static int sms = 0;
     if (sms == 0) {
@@ -809,6 +1034,52 @@ void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ra
         else GS_BWD(false, 512);
     }
 #undef GS_BWD
+}
+
+size_t list_scan_bytes(long long npx) {
+    return align_up(sizeof(long long) * (size_t)(ceil_div(npx, kListScanTile) + 1), 256);
+}
+
+void launch_render_fwd_lists(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
+                             const uint8_t *masks, const int *order, const float2 *xy, const float4 *co,
+                             const float4 *rgbd, float *img, float *T_final, int *last, float *depth, long long npx,
+                             long long *count_off, int *lid, float *lal, long long cap, void *scan_ws, int *status,
+                             cudaStream_t s) {
+    const long long units = 8ll * vt.total_tiles;
+    if (units <= 0 || npx <= 0) return;
+    const unsigned grid = (unsigned)ceil_div(units, kWarps);
+    const int nb = (int)ceil_div(npx, kListScanTile);
+    long long *bsum = (long long *)scan_ws;
+#define GS_FWDL(WN)                                                                                                 \
+    do {                                                                                                            \
+        k_render_fwd_lists<WN, false><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, order, xy, co, rgbd, \
+                                                                   img, T_final, last, depth, count_off, lid, lal,  \
+                                                                   cap);                                            \
+        k_list_scan_sums<<<nb, kListScanThreads, 0, s>>>(count_off, npx, bsum);                                     \
+        k_list_scan_top<<<1, kListScanThreads, 0, s>>>(bsum, nb, count_off, npx, cap, status);                      \
+        k_list_scan_apply<<<nb, kListScanThreads, 0, s>>>(count_off, npx, bsum);                                    \
+        k_render_fwd_lists<WN, true><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, order, xy, co, rgbd,  \
+                                                                  img, T_final, last, depth, count_off, lid, lal,   \
+                                                                  cap);                                             \
+    } while (0)
+    if (cfg.batch == 128) GS_FWDL(128);
+    else if (cfg.batch == 256) GS_FWDL(256);
+    else GS_FWDL(512);
+#undef GS_FWDL
+}
+
+void launch_render_bwd_lists(const ViewTable &vt, const RasterCfg &cfg, long long npx, const long long *off,
+                             const int *lid, const float *lal, long long cap, const float2 *xy, const float4 *co,
+                             const float4 *rgbd, const float *img, const float *T_final, const float *dL_dimg,
+                             const float *target, float tau_err, bool stats, float *acc, cudaStream_t s) {
+    if (npx <= 0) return;
+    const unsigned grid = (unsigned)std::min(ceil_div(npx, 256), (long long)sm_count() * 8);
+    if (stats)
+        k_render_bwd_lists<true><<<grid, 256, 0, s>>>(vt, cfg, npx, off, lid, lal, cap, xy, co, rgbd, img, T_final,
+                                                      dL_dimg, target, tau_err, acc);
+    else
+        k_render_bwd_lists<false><<<grid, 256, 0, s>>>(vt, cfg, npx, off, lid, lal, cap, xy, co, rgbd, img, T_final,
+                                                       dL_dimg, target, tau_err, acc);
 }
 
 }  // namespace gs

@@ -81,7 +81,8 @@ EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspac
            "gs_mlp_push_blend", "gs_mlp_features", "gs_mlp_forward", "gs_mlp_train_grad", "gs_mlp_adam",
            "gs_segment_workspace_size", "gs_project_bwd_adam", "gs_segment_workspace_size_items",
            "gs_voxel_table_reset", "gs_init_workspace_size", "gs_init_probability", "gs_init_insert",
-           "gs_voxel_lookup", "gs_anchor_decode", "gs_anchor_decode_bwd", "gs_adam_flat")
+           "gs_voxel_lookup", "gs_anchor_decode", "gs_anchor_decode_bwd", "gs_adam_flat",
+           "gs_list_workspace_size", "gs_render_fwd_lists", "gs_render_bwd_lists")
 
 _lib = None
 
@@ -132,6 +133,11 @@ def lib():
         L.gs_mlp_forward.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, i64, vp]
         L.gs_mlp_train_grad.argtypes = [vp, vp, vp, i64, i64, vp, vp, vp, vp, vp]
         L.gs_mlp_adam.argtypes = [vp, vp, vp, vp, f32, f32, f32, f32, i64, vp]
+        L.gs_list_workspace_size.argtypes = [i64, P(sz)]
+        L.gs_render_fwd_lists.argtypes = [P(Projected), P(Binning), P(Camera), i32, P(RasterCfg), P(Frame), vp, vp, vp,
+                                          i64, vp, sz, vp, vp]
+        L.gs_render_bwd_lists.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), P(Frame), vp, vp, vp,
+                                          i64, vp, vp, vp, f32, P(Params), i32, P(Stats), vp, sz, vp]
         for name in EXPORTS:
             if name not in ("gs_status_string", "gs_version"):
                 getattr(L, name).restype = C.c_int
@@ -440,6 +446,51 @@ def gs_project_bwd(model: GaussianModel, grads: GaussianModel, buf: Buffers, acc
            "gs_project_bwd")
 
 
+class StoredLists:
+    """Per-pixel blend lists (record id, alpha) of gs_render_fwd_lists, with
+    their offsets; capacity in blend events (grown by MappingStep.fit_capacity)."""
+
+    def __init__(self, total_pixels, capacity, device):
+        self.total_pixels = int(total_pixels)
+        self.offsets = torch.zeros(self.total_pixels + 1, dtype=torch.int64, device=device)
+        self.scan_ws = _workspace(lib().gs_list_workspace_size, self.total_pixels, device=device)
+        self.set_capacity(capacity)
+
+    def set_capacity(self, capacity):
+        dev = self.offsets.device
+        self.capacity = int(capacity)
+        self.ids = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=dev)
+        self.alpha = torch.empty(max(self.capacity, 1), dtype=torch.float32, device=dev)
+
+    def events(self):
+        """Blend events of the last forward (host sync)."""
+        return int(self.offsets[self.total_pixels].item())
+
+    def nbytes(self):
+        return self.offsets.numel() * 8 + self.ids.numel() * 4 + self.alpha.numel() * 4 + self.scan_ws.numel()
+
+
+def gs_render_fwd_lists(buf: Buffers, lists: StoredLists, stream=None):
+    arr = camera_array(buf.cams)
+    _check(lib().gs_render_fwd_lists(C.byref(buf.projected()), C.byref(buf.binning()), arr, buf.n_views,
+                                     C.byref(buf.cfg.c()), C.byref(buf.frame()), _ptr(lists.offsets), _ptr(lists.ids),
+                                     _ptr(lists.alpha), lists.capacity, _ptr(lists.scan_ws), lists.scan_ws.numel(),
+                                     _ptr(buf.status), _stream(stream)), "gs_render_fwd_lists")
+
+
+def gs_render_bwd_lists(model: GaussianModel, grads: GaussianModel, buf: Buffers, lists: StoredLists, target=None,
+                        tau_err=0.1, accumulate=False, with_stats=True, stream=None):
+    arr = camera_array(buf.cams)
+    st = buf.stats() if with_stats else None
+    _check(lib().gs_render_bwd_lists(C.byref(model.c()), arr, buf.n_views, C.byref(buf.cfg.c()),
+                                     C.byref(buf.projected()), C.byref(buf.frame()), _ptr(lists.offsets),
+                                     _ptr(lists.ids), _ptr(lists.alpha), lists.capacity, _ptr(buf.dL_dimg),
+                                     _ptr(target), _ptr(buf.loss), float(tau_err),
+                                     None if grads is None else C.byref(grads.c()), int(bool(accumulate)),
+                                     None if st is None else C.byref(st), _ptr(buf.bwd_ws), buf.bwd_ws.numel(),
+                                     _stream(stream)), "gs_render_bwd_lists")
+
+
 def gs_project_bwd_adam(model: GaussianModel, buf: Buffers, exp_avg: GaussianModel, exp_avg_sq: GaussianModel, lr,
                         step, beta1=0.9, beta2=0.999, eps=1e-15, iso_weight=0.0, grads_in: GaussianModel = None,
                         with_stats=True, stream=None, step_device=None):
@@ -572,7 +623,7 @@ class MappingStep:
 
     def __init__(self, model: GaussianModel, cams, cfg: Config = None, max_pairs=None, lambda_dssim=0.2,
                  tau_err=0.1, lr=None, with_stats=True, with_depth=False, depth_prior=None, lambda_geo=0.01,
-                 lambda_iso=0.0, moments=None, step_count=0, fused_adam=False):
+                 lambda_iso=0.0, moments=None, step_count=0, fused_adam=False, stored_lists=False):
         self.model = model
         self.cfg = cfg or Config()
         self.lambda_dssim, self.tau_err = lambda_dssim, tau_err
@@ -591,7 +642,12 @@ class MappingStep:
         self.fused_adam = fused_adam
         if max_pairs is None:
             max_pairs = max(1 << 16, 8 * model.n * len(cams))
+        if stored_lists:  # the stored-list backward: no split, no depth term, no fused Adam
+            assert not with_depth and not fused_adam and lambda_iso == 0.0
+            self.cfg = Config(**{**self.cfg.__dict__, "segment": 0})
         self.buf = Buffers(model, cams, self.cfg, max_pairs, with_depth=with_depth, with_stats=with_stats)
+        self.lists = (StoredLists(self.buf.total_pixels, 4 * self.buf.total_pixels, model.data.device)
+                      if stored_lists else None)
         dev = model.data.device
         self.reg_ws = reg_workspace(dev) if (depth_prior is not None or lambda_iso > 0) else None
         self.geo_loss = torch.zeros(len(cams), dtype=torch.float32, device=dev)
@@ -620,10 +676,17 @@ class MappingStep:
         b.status.zero_()
         gs_project(self.model, b, stream)
         gs_sort(b, stream)
-        gs_render_fwd(b, stream)
+        if self.lists is not None:
+            gs_render_fwd_lists(b, self.lists, stream)
+        else:
+            gs_render_fwd(b, stream)
 
     def _losses_and_backward(self, target, stream=None):
         gs_loss(self.buf, target, self.lambda_dssim, stream)
+        if self.lists is not None:
+            gs_render_bwd_lists(self.model, self.grads, self.buf, self.lists, target, self.tau_err,
+                                with_stats=self.with_stats, stream=stream)
+            return
         if self.depth_prior is not None:
             gs_geo_loss(self.buf, self.depth_prior, self.lambda_geo, self.geo_loss, self.dL_ddepth, self.reg_ws, stream)
         gs_render_bwd(self.model, self.grads, self.buf, target, self.tau_err, with_stats=self.with_stats,
@@ -740,7 +803,12 @@ class MappingStep:
         st = int(self.buf.status.item())
         if st & (1 << GS_ERR_CAPACITY):
             needed = int(self.buf.counts[2].item())
-            raise GSError("pair capacity exceeded: %d pairs needed, %d available" % (needed, self.buf.max_pairs))
+            if needed > self.buf.max_pairs:
+                raise GSError("pair capacity exceeded: %d pairs needed, %d available" % (needed, self.buf.max_pairs))
+            if self.lists is not None and self.lists.events() > self.lists.capacity:
+                raise GSError("stored-list capacity exceeded: %d blend events, %d slots"
+                              % (self.lists.events(), self.lists.capacity))
+            raise GSError("capacity exceeded")
         return st
 
     def fit_capacity(self, slack=1.25):
@@ -753,6 +821,12 @@ class MappingStep:
             self.buf.set_max_pairs(max(1024, int(needed * slack)))
             self.forward()
             torch.cuda.synchronize()
+        if self.lists is not None:
+            ev = self.lists.events()
+            if ev > self.lists.capacity:
+                self.lists.set_capacity(int(ev * max(slack, 1.1)) + 1024)
+                self.forward()
+                torch.cuda.synchronize()
         if self.buf.seg_ws is not None:
             off, items = self.buf.seg_needed()
             if off or items > self.buf.seg_items:

@@ -156,3 +156,28 @@ def test_init_arguments_rejected_on_host():
                             C.byref(good_table), C.byref(bad_count), None, None, ws, big, None) == 1
     assert L.gs_voxel_lookup(C.byref(good_table), C.c_void_p(16), 5, 4, C.c_void_p(32), None) == 1  # ld < n
     assert L.gs_voxel_table_reset(C.byref(spawn.VoxelTable(16, 32, 48, 3000)), None) == 1
+
+
+def test_stored_list_arguments_rejected_on_host():
+    L = gs.lib()
+    n = C.c_size_t()
+    assert L.gs_list_workspace_size(-1, C.byref(n)) == 1
+    assert L.gs_list_workspace_size(921600, C.byref(n)) == 0 and n.value >= 8 * (921600 // 4096 + 1)
+    cam = gs.camera_array([scenes.pinhole(64, 48, 60.0)])
+    cfg = gs.Config().c()
+    proj = gs.Projected(16, 32, 48, 64, 80, 12)
+    binning = gs.Binning(16, 64, 128, 256, 512, 1000)
+    frame = gs.Frame(16, 32, 48, None, None, 0)
+    ws = 256
+    # offsets missing or misaligned, events without their arrays: rejected before any launch
+    assert L.gs_render_fwd_lists(C.byref(proj), C.byref(binning), cam, 1, C.byref(cfg), C.byref(frame), None, 64, 80,
+                                 10, ws, 1 << 20, None, None) == 1
+    assert L.gs_render_fwd_lists(C.byref(proj), C.byref(binning), cam, 1, C.byref(cfg), C.byref(frame), 4, 64, 80,
+                                 10, ws, 1 << 20, None, None) == 1
+    assert L.gs_render_fwd_lists(C.byref(proj), C.byref(binning), cam, 1, C.byref(cfg), C.byref(frame), 64, None, None,
+                                 10, ws, 1 << 20, None, None) == 1
+    assert L.gs_render_fwd_lists(C.byref(proj), C.byref(binning), cam, 1, C.byref(cfg), C.byref(frame), 64, 64, 80,
+                                 10, ws, 4, None, None) == 1  # scan workspace too small
+    p = gs.Params(16, 10, 12, 0)
+    assert L.gs_render_bwd_lists(C.byref(p), cam, 1, C.byref(cfg), C.byref(proj), C.byref(frame), None, 64, 80, 10,
+                                 96, None, None, 0.1, None, 0, None, ws, 1 << 20, None) == 1

@@ -616,8 +616,8 @@ def run_memory(args, dev):
 # --------------------------------------------------------------------------
 # lifecycle: learned vs plain densify / prune decisions over keyframe chunks
 
-def lifecycle_cams(scenes, f0, views, w, h, f):
-    return [scenes.corridor_camera(f0 + j, w, h, f) for j in range(views)]
+def lifecycle_cams(scenes, frames, w, h, f):
+    return [scenes.corridor_camera(fr, w, h, f) for fr in frames]
 
 
 def psnr(img, ref):
@@ -627,60 +627,74 @@ def psnr(img, ref):
 
 
 def run_lifecycle(args, dev):
-    """Learned vs plain lifecycle decisions on the corridor: ground truth G*
-    (the corridor scene), an initial map with 30 % of G* removed, 20 % floaters
-    added and N(0, 0.01) on every entry; chunks of `views` consecutive frames,
-    `iters` batched mapping iterations each (statistics on), then decisions and
-    densify / prune actions.  The predictor is trained on the plain criterion's
-    bits from training chunks (frames from 100) and both arms run the same
-    evaluation chunks (frames from 500)."""
+    """Learned vs plain lifecycle decisions on a long corridor: ground truth
+    G* (the corridor generator stretched to `length` metres, frames 1 m
+    apart), an initial map with 30 % of G* removed, 20 % floaters added and
+    N(0, 0.01) on every entry; keyframe chunks of C = 100 consecutive frames
+    (Supp. F), `iters` batched mapping iterations per chunk, each over `views`
+    of the chunk's frames (a rotating stride, so the iterations cover the
+    chunk), statistics summed over the chunk, then decisions and densify /
+    prune actions.  The predictor learns from a plain-criterion run over
+    training chunks (labels of future_labels: prune when the plain criterion
+    prunes the Gaussian in this or a later chunk) and both arms then run the
+    same evaluation chunks from the same initial map."""
     import torch
     from paper_2606_30436_b300 import gs, lifecycle, scenes
-    n_gt, V, T = args.lifecycle_gaussians, args.lifecycle_views, args.lifecycle_iters
+    n_gt, V, T, C = args.lifecycle_gaussians, args.lifecycle_views, args.lifecycle_iters, 100
+    length = float(args.lifecycle_length)
     w, h, f = W // 2, H // 2, F / 2
     cfg = gs.Config()
-    gt = scenes.corridor_scene(n_gt, seed=0, sh_degree=SH_DEG)
-    init = scenes.degraded_map(gt, seed=2)
-    train_starts = [100 + 2 * V * k for k in range(args.lifecycle_train_chunks)]
-    eval_starts = [500 + 2 * V * k for k in range(args.lifecycle_chunks)]
-    gt_model = gs.GaussianModel.from_scene(gt, device=dev)
-    targets = {}
-    for f0 in train_starts + eval_starts:
-        st = gs.MappingStep(gt_model, lifecycle_cams(scenes, f0, V, w, h, f), cfg, with_stats=False)
-        st.fit_capacity()
-        targets[f0] = st.buf.img.clone()
-        del st
-    del gt_model
+    gt = scenes.corridor_scene(n_gt, seed=0, sh_degree=SH_DEG, length=length)
+    init = scenes.degraded_map(gt, seed=2, length=length)
+    train_starts = [int(length * 0.1) + C * k for k in range(args.lifecycle_train_chunks)]
+    eval_starts = [int(length * 0.6) + C * k for k in range(args.lifecycle_chunks)]
     lr = gs.default_lr(extent=10.0)
+    gt_model = gs.GaussianModel.from_scene(gt, device=dev)
 
-    def render_psnr(model, starts):
-        vals = []
-        for f0 in starts:
-            st = gs.MappingStep(model, lifecycle_cams(scenes, f0, V, w, h, f), cfg, with_stats=False)
+    def chunk_targets(f0):
+        """GT renders of the chunk's C frames, [C, 3 h w] (device)."""
+        out = torch.empty(C, 3 * w * h, dtype=torch.float32, device=dev)
+        for k in range(0, C, 20):
+            st = gs.MappingStep(gt_model, lifecycle_cams(scenes, range(f0 + k, f0 + k + 20), w, h, f), cfg,
+                                with_stats=False)
             st.fit_capacity()
-            vals.append(psnr(st.buf.img, targets[f0]))
+            out[k:k + 20] = st.buf.img.view(20, -1)
             del st
-        return float(np.mean(vals))
+        return out
+
+    targets = {f0: chunk_targets(f0) for f0 in train_starts + eval_starts}
+    del gt_model
+    torch.cuda.synchronize()
+
+    def view_frames(f0, it):
+        """The iteration's frames of the chunk: a stride over the chunk, shifted every iteration."""
+        stride = C // V
+        return [f0 + (it % stride) + stride * j for j in range(V)]
 
     def run_arm(mode, starts, predictor=None, collect=False):
         model = gs.GaussianModel.from_scene(init, device=dev)
         lc = lifecycle.Lifecycle(mode, tau_d=args.tau_d, tau_p=args.tau_p, split_log_scale=-2.5,
-                                 predictor=predictor, collect=collect, seed=3)
+                                 predictor=predictor, collect=collect, seed=3, margin=args.mlp_margin,
+                                 n_initial=model.n)
         moments, step_count = None, 0
         torch.cuda.synchronize()
+        torch.cuda.empty_cache()
         torch.cuda.reset_peak_memory_stats(dev)
-        psnr0 = render_psnr(model, starts)
         iter_ms = end_ms = 0.0
-        chunk_psnr = []
+        chunk_psnr, sizes = [], [model.n]
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        tbuf = torch.empty(V * 3 * w * h, dtype=torch.float32, device=dev)
         for f0 in starts:
-            step = gs.MappingStep(model, lifecycle_cams(scenes, f0, V, w, h, f), cfg, lr=lr, moments=moments,
-                                  step_count=step_count)
+            step = gs.MappingStep(model, lifecycle_cams(scenes, view_frames(f0, 0), w, h, f), cfg, lr=lr,
+                                  moments=moments, step_count=step_count)
             step.fit_capacity(slack=1.5)
             lc.start(step)
             ev[0].record()
-            for _ in range(T):
-                step.step(targets[f0])
+            for it in range(T):
+                fr = view_frames(f0, it)
+                step.set_cameras(lifecycle_cams(scenes, fr, w, h, f))
+                tbuf.view(V, -1).copy_(targets[f0][[x - f0 for x in fr]])
+                step.step(tbuf)
                 lc.after_iteration(step)
             ev[1].record()
             centre = -np.asarray(step.buf.cams[-1]["R"], np.float64).T @ np.asarray(step.buf.cams[-1]["t"])
@@ -688,10 +702,11 @@ def run_lifecycle(args, dev):
             ev[2].record()
             torch.cuda.synchronize()
             step.check_status()
-            # the chunk's views as the map renders them after its iterations (last forward pass)
-            chunk_psnr.append(psnr(step.buf.img, targets[f0]))
+            # the last iteration's views as the map rendered them
+            chunk_psnr.append(psnr(step.buf.img, tbuf))
             lc.assess(step)
             model, moments = lc.apply(step, dens, prune)
+            sizes.append(model.n)
             lc.history[-1]["psnr_db"] = round(chunk_psnr[-1], 3)
             iter_ms += ev[0].elapsed_time(ev[1])
             end_ms += ev[1].elapsed_time(ev[2])
@@ -702,22 +717,20 @@ def run_lifecycle(args, dev):
         out = {"iters_per_s": round(len(starts) * T * 1e3 / iter_ms, 2),
                "iters_per_s_with_decisions": round(len(starts) * T * 1e3 / (iter_ms + end_ms), 2),
                "ms_per_chunk_decisions": round(end_ms / len(starts), 3),
-               "decisions": "plain: gs_prune_stats; learned: gs_mlp_features + gs_mlp_forward (the agreement "
-                            "with the plain criterion is computed outside the timed region)",
-               "peak_memory_gb": round(peak / 1e9, 3), "gaussians_start": len(init["means"]),
-               "gaussians_end": model.n, "psnr_initial_map_db": round(psnr0, 3),
-               "psnr_db": round(float(np.mean(chunk_psnr)), 3),
-               "psnr_after_last_actions_db": round(render_psnr(model, starts), 3), "chunks": lc.history}
+               "peak_memory_gb": round(peak / 1e9, 3), "gaussians": sizes,
+               "psnr_db": round(float(np.mean(chunk_psnr)), 3), "chunks": lc.history}
         return out, lc
 
     _, lc_train = run_arm("plain", train_starts, collect=True)
+    rows = lifecycle.future_labels(lc_train.samples, device=dev)
     pred = lifecycle.Predictor(seed=4, device=dev, lr=args.mlp_lr)
     t0 = time.perf_counter()
-    bce = pred.train(lc_train.samples, epochs=args.mlp_epochs)
+    bce = pred.train(rows, epochs=args.mlp_epochs)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    train_rows = int(sum(smp[1] for smp in lc_train.samples))
-    del lc_train
+    train_rows = int(sum(r[1] for r in rows))
+    pos = [int(r[3].sum().item()) for r in rows]
+    del lc_train, rows
     plain, _ = run_arm("plain", eval_starts)
     learned, _ = run_arm("learned", eval_starts, predictor=pred)
     return {"metric": "lifecycle mapping iters/s, learned vs plain densify/prune", "unit": "iters/s",
@@ -725,11 +738,15 @@ def run_lifecycle(args, dev):
             "speedup_vs_plain": round(learned["iters_per_s_with_decisions"] / plain["iters_per_s_with_decisions"], 3),
             "psnr_delta_db": round(learned["psnr_db"] - plain["psnr_db"], 3),
             "peak_memory_ratio": round(learned["peak_memory_gb"] / plain["peak_memory_gb"], 3),
-            "config": {"workload": "corridor G* %d Gaussians SH3; initial map 30%% removed, 20%% floaters, "
-                                   "N(0,0.01); chunks of %d frames at %dx%d, %d iterations each" % (n_gt, V, w, h, T),
+            "config": {"workload": "corridor G* %d Gaussians SH3 over %.0f m; initial map 30%% removed, 20%% floaters, "
+                                   "N(0,0.01); chunks of %d frames at %dx%d, %d iterations of %d views each"
+                                   % (n_gt, length, C, w, h, T, V),
                        "train_chunks": train_starts, "eval_chunks": eval_starts, "tau_d": args.tau_d,
-                       "tau_p": args.tau_p, "mlp_epochs": args.mlp_epochs},
-            "predictor": {"train_bce": round(bce, 5), "train_seconds": round(train_s, 2), "train_rows": train_rows},
+                       "tau_p": args.tau_p, "mlp_epochs": args.mlp_epochs, "fallback_margin": args.mlp_margin},
+            "predictor": {"train_bce": round(bce, 5), "train_seconds": round(train_s, 2), "train_rows": train_rows,
+                          "prune_labels_per_chunk": pos,
+                          "labels": "densify: the chunk's plain bit; prune: pruned by the plain criterion in this "
+                                    "or a later chunk; Gaussians the chunk did not see carry no label"},
             "plain": plain, "learned": learned, "data": "synthetic", "n_gpus": 1}
 
 
@@ -1080,11 +1097,13 @@ def main():
                     help="anchor initialisation at a 720p keyframe (probability, NMS, voxel insertion)")
     ap.add_argument("--memory-gaussians", type=int, default=10_000_000)
     ap.add_argument("--memory-iters", type=int, default=5)
-    ap.add_argument("--lifecycle-gaussians", type=int, default=1_000_000)
-    ap.add_argument("--lifecycle-views", type=int, default=8)
-    ap.add_argument("--lifecycle-iters", type=int, default=30)
-    ap.add_argument("--lifecycle-chunks", type=int, default=6)
-    ap.add_argument("--lifecycle-train-chunks", type=int, default=6)
+    ap.add_argument("--lifecycle-gaussians", type=int, default=10_000_000)
+    ap.add_argument("--lifecycle-length", type=float, default=10_000.0, help="corridor length in metres")
+    ap.add_argument("--lifecycle-views", type=int, default=16)
+    ap.add_argument("--lifecycle-iters", type=int, default=20)
+    ap.add_argument("--lifecycle-chunks", type=int, default=8)
+    ap.add_argument("--lifecycle-train-chunks", type=int, default=8)
+    ap.add_argument("--mlp-margin", type=float, default=0.1)
     ap.add_argument("--tau-d", type=float, default=5.0)
     ap.add_argument("--tau-p", type=float, default=0.99)
     ap.add_argument("--mlp-epochs", type=int, default=300)

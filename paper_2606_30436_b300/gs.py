@@ -640,8 +640,8 @@ class MappingStep:
         # Adam inside the projection backward: no gradient buffer (236 MB less at 1M
         # Gaussians, SH3) but, at its occupancy, slower than projection backward + Adam
         self.fused_adam = fused_adam
-        if max_pairs is None:
-            max_pairs = max(1 << 16, 8 * model.n * len(cams))
+        if max_pairs is None:  # a first guess; fit_capacity sizes it to the count measured
+            max_pairs = min(max(1 << 16, 8 * model.n * len(cams)), 1 << 25)
         if stored_lists:  # the stored-list backward: no split, no depth term, no fused Adam
             assert not with_depth and not fused_adam and lambda_iso == 0.0
             self.cfg = Config(**{**self.cfg.__dict__, "segment": 0})

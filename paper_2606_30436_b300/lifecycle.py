@@ -8,8 +8,13 @@ parameters and the Adam moments:
 * ``plain``: the paper's criterion, ``gs_prune_stats`` (S_d > tau_d,
   min-max-normalised S_p > tau_p over the active Gaussians);
 * ``learned``: the BF16 tensor-core predictor (``gs_mlp_features`` +
-  ``gs_mlp_forward``) trained on the plain criterion's bits, which stays the
-  fallback and the reference for its error (``agreement``).
+  ``gs_mlp_forward``), trained on labels the plain criterion produces
+  (``future_labels``: a Gaussian is labelled for pruning when the plain
+  criterion prunes it in this chunk or any later one, so the predictor acts
+  before the plain criterion would); where its probability lies within
+  ``margin`` of 1/2 the plain bit of the same chunk is used instead (the
+  fallback), and the plain criterion stays the reference for its error
+  (``agreement``).  Both deciders act only on Gaussians the chunk saw.
 
 Readings: the statistics of a chunk are summed over its iterations and views,
 so |V_c| = iterations x views; decisions are taken and applied per chunk (the
@@ -19,6 +24,7 @@ one slot per iteration (each slot the maximum over that iteration's views).
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import gs
@@ -56,13 +62,17 @@ class Lifecycle:
     """Statistics, decisions and actions of one chunk at a time."""
 
     def __init__(self, mode="plain", tau_d=5.0, tau_p=0.99, split_log_scale=-2.5, split_factor=1.6,
-                 predictor: Predictor = None, collect=False, seed=0):
+                 predictor: Predictor = None, collect=False, seed=0, margin=0.1, n_initial=0):
         assert mode in ("plain", "learned")
         assert mode == "plain" or predictor is not None
         self.mode, self.tau_d, self.tau_p = mode, tau_d, tau_p
         self.split_log_scale, self.split_factor = split_log_scale, split_factor
         self.predictor, self.collect = predictor, collect
-        self.samples = []   # (feat, n, y_densify, y_prune) of each chunk, with collect=True
+        self.margin = margin  # learned: the plain bit where |p - 1/2| < margin
+        # identity of every Gaussian of the current map (host), carried through the actions
+        self.ids = np.arange(n_initial, dtype=np.int64)
+        self.next_id = n_initial
+        self.samples = []   # per chunk, with collect=True: (feat, n, densify, prune, active, ids)
         self.history = []   # per chunk: n before / after, bits set, agreement with the plain criterion
         self.gen = torch.Generator(device="cuda").manual_seed(int(seed))
         self.ring = None
@@ -101,21 +111,33 @@ class Lifecycle:
         gs.gs_prune_stats(step.buf.stats_acc, n, n_views, scores, ws, self.tau_d, self.tau_p)
         return scores["densify"], scores["prune"]
 
+    def active(self, step: gs.MappingStep):
+        """[n] bool: the Gaussians blended somewhere in this chunk (|Omega| > 0)."""
+        return step.buf.stats_acc[0, :step.model.n] > 0
+
     def decide(self, step: gs.MappingStep, cam_centre):
         """Densify / prune bits ([n] uint8) of the chunk's Gaussians, by the
         chosen decider; nothing here synchronises the host."""
         model, dev = step.model, step.model.data.device
         n = model.n
         self._last = None
+        self._fallback = None
         if self.mode == "plain":
             dens, prune = self.plain_bits(step)
             if self.collect:
-                self.samples.append((self._features(step, cam_centre), n, dens.clone(), prune.clone()))
+                self.samples.append((self._features(step, cam_centre), n, dens.clone(), prune.clone(),
+                                     self.active(step).clone(), self.ids.copy()))
         else:
             feat = self._features(step, cam_centre)
-            dens = torch.zeros(n, dtype=torch.uint8, device=dev)
-            prune = torch.zeros(n, dtype=torch.uint8, device=dev)
-            self.predictor.predict(feat, n, dens, prune)
+            prob = torch.zeros(2, model.ld, dtype=torch.float32, device=dev)
+            self.predictor.predict(feat, n, None, None, prob)
+            pd, pp = self.plain_bits(step)
+            act = self.active(step)
+            unsure_d = (prob[0, :n] - 0.5).abs() < self.margin
+            unsure_p = (prob[1, :n] - 0.5).abs() < self.margin
+            dens = (torch.where(unsure_d, pd.bool(), prob[0, :n] > 0.5) & act).to(torch.uint8)
+            prune = (torch.where(unsure_p, pp.bool(), prob[1, :n] > 0.5) & act).to(torch.uint8)
+            self._fallback = (unsure_d & act, unsure_p & act, act)
         self._last = (n, dens, prune)
         return dens, prune
 
@@ -127,6 +149,10 @@ class Lifecycle:
         rec = dict(n=n, densify=int(dens.sum().item()), prune=int(prune.sum().item()))
         if self.mode == "learned":
             rec.update(agreement(dens, prune, *self.plain_bits(step)))
+            ud, up, act = self._fallback
+            na = max(1, int(act.sum().item()))
+            rec.update(fallback_densify_rate=round(int(ud.sum().item()) / na, 4),
+                       fallback_prune_rate=round(int(up.sum().item()) / na, 4), active=na)
         self.history.append(rec)
         return rec
 
@@ -139,6 +165,8 @@ class Lifecycle:
                                            capacity=gs.padded(model.n + int(dens.sum().item())))
         if self.history:
             self.history[-1]["n_after"] = out.n
+        self.ids, self.next_id = carry_ids(self.ids, dens.cpu().numpy(), prune.cpu().numpy(), self.next_id)
+        assert len(self.ids) == out.n
         return out, (m, v)
 
 
@@ -153,3 +181,37 @@ def agreement(dens, prune, ref_d, ref_p):
         out[name + "_recall"] = tp / pb if pb else 1.0
         out[name + "_accuracy"] = float((a == b).float().mean().item()) if a.numel() else 1.0
     return out
+
+
+def carry_ids(ids, dens, prune, next_id):
+    """Identities after gs_densify_prune's rows (source order; a pruned
+    Gaussian emits none, a kept one its own row, a densified one its own row
+    followed by a new one): the first row keeps the source's id, a second row
+    takes the next fresh id.  Returns (ids, next_id)."""
+    keep = np.asarray(prune) == 0
+    rows = 1 + ((np.asarray(dens) != 0) & keep)[keep].astype(np.int64)
+    src = np.repeat(np.arange(int(keep.sum())), rows)
+    out = np.repeat(np.asarray(ids, np.int64)[keep], rows)
+    second = np.zeros(len(src), bool)
+    second[1:] = src[1:] == src[:-1]
+    out[second] = next_id + np.arange(int(second.sum()))
+    return out, next_id + int(second.sum())
+
+
+def future_labels(samples, device="cuda"):
+    """Training rows from the plain criterion's chunks (Lifecycle(collect=True)
+    samples, in chunk order): the densify label is the chunk's own plain bit,
+    the prune label is set when the plain criterion prunes the Gaussian in
+    that chunk or in any later chunk of the run; only Gaussians the chunk saw
+    can carry a label.  Returns (feat, n, y_densify, y_prune) tuples."""
+    pruned_later = set()
+    rows = []
+    for feat, n, dens, prune, act, ids in reversed(samples):
+        pr = prune.cpu().numpy().astype(bool)
+        pruned_later.update(ids[pr].tolist())
+        later = np.isin(ids, np.fromiter(pruned_later, dtype=np.int64, count=len(pruned_later)))
+        a = act.cpu().numpy()
+        yp = torch.from_numpy((later & a).astype(np.uint8)).to(device)
+        yd = (dens.to(torch.bool) & act).to(torch.uint8)
+        rows.append((feat, n, yd, yp))
+    return rows[::-1]

@@ -182,7 +182,7 @@ def committed_profile(stage):
         if not m_sha or m_sha.group(1) != sha:
             continue
         out = {"profile": "profiles/" + os.path.basename(fn)}
-        for key, name in (("traffic", "dram_bytes_per_launch_bench_mean"), ("issue_active_pct", "issue_active_pct"),
+        for key, name in (("traffic", r"dram_bytes_per_launch(?:_bench_mean)?"), ("issue_active_pct", "issue_active_pct"),
                           ("warps_active_pct", "warps_active_pct")):
             m = re.search(name + r":\s*([0-9.]+)", txt)
             if m:

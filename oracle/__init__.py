@@ -108,8 +108,8 @@ def lib():
                                      vp, vp, vp, vp, vp, vp, d, d]
         L.or_init_select.restype = i64
         L.or_anchor_num_weights.restype = i32
-        L.or_anchor_decode.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d]
-        L.or_anchor_decode_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.or_anchor_decode.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, i32]
+        L.or_anchor_decode_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     return _lib
 
 
@@ -470,24 +470,26 @@ def _anchor_args(A):
             _f64(A["log_l"], (n, 3)), _f64(A["offs"], (n, ANCHOR_K, 3)))
 
 
-def anchor_decode(A, w, cam_centre, max_dist, tol=1e-6):
-    """Decoded Gaussians of anchors A (dict pos, level, feat, log_l, offs): rows [10 n][14], keep and unsure."""
+def anchor_decode(A, w, cam_centre, max_dist, tol=1e-6, bf16=False):
+    """Decoded Gaussians of anchors A (dict pos, level, feat, log_l, offs): rows [10 n][14], keep and unsure.
+    bf16 rounds the decoder's hidden-layer operands to bfloat16 (reading R30)."""
     n, pos, lv, feat, log_l, offs = _anchor_args(A)
     w, cc, md = _f64(w), _f64(cam_centre, (3,)), _f64(max_dist)
     rows = np.zeros((ANCHOR_K * n, 14))
     keep, unsure = np.zeros(ANCHOR_K * n, np.uint8), np.zeros(ANCHOR_K * n, np.uint8)
     lib().or_anchor_decode(n, _ptr(pos), _ptr(lv), _ptr(feat), _ptr(log_l), _ptr(offs), _ptr(w), _ptr(cc), _ptr(md),
-                           _ptr(rows), _ptr(keep), _ptr(unsure), float(tol))
+                           _ptr(rows), _ptr(keep), _ptr(unsure), float(tol), int(bool(bf16)))
     return rows, keep.astype(bool), unsure.astype(bool)
 
 
-def anchor_decode_backward(A, w, cam_centre, max_dist, g_rows):
-    """Gradients (feat, log_l, offs, w) of a loss with dL/drows = g_rows."""
+def anchor_decode_backward(A, w, cam_centre, max_dist, g_rows, bf16=False):
+    """Gradients (feat, log_l, offs, w) of a loss with dL/drows = g_rows (bf16: of the bfloat16-operand
+    forward, plain FP64 chain rule)."""
     n, pos, lv, feat, log_l, offs = _anchor_args(A)
     w, cc, md, g = _f64(w), _f64(cam_centre, (3,)), _f64(max_dist), _f64(g_rows, (ANCHOR_K * n, 14))
     gf, gl, go, gw = np.zeros_like(feat), np.zeros_like(log_l), np.zeros_like(offs), np.zeros_like(w)
     lib().or_anchor_decode_backward(n, _ptr(pos), _ptr(lv), _ptr(feat), _ptr(log_l), _ptr(offs), _ptr(w), _ptr(cc),
-                                    _ptr(md), _ptr(g), _ptr(gf), _ptr(gl), _ptr(go), _ptr(gw))
+                                    _ptr(md), _ptr(g), _ptr(gf), _ptr(gl), _ptr(go), _ptr(gw), int(bool(bf16)))
     return gf, gl, go, gw
 
 

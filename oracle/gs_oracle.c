@@ -1332,23 +1332,34 @@ int32_t or_anchor_num_weights(void) { return OR_ANC_NW; }
 
 static double sigm(double z) { return 1.0 / (1.0 + exp(-z)); }
 
-/* Decoder input, hidden pre-activations and the 14 K outputs of anchor i. */
+/* Decoder input, hidden pre-activations and the 14 K outputs of anchor i.
+ * bf16 != 0 (reading R30) rounds the hidden layers' operands to bfloat16 as
+ * the tensor cores take them: the input x (returned rounded), W1, the hidden
+ * activation relu(pre) and W2; the sums and the biases stay FP64. */
 static void anchor_mlp(const double *pos, const double *feat, const double *w, const double cc[3], double *x,
-                       double *pre, double *z, double *dist) {
+                       double *pre, double *z, double *dist, int bf16) {
     double v[3];
     for (int a = 0; a < 3; ++a) v[a] = pos[a] - cc[a];
     const double d = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     for (int c = 0; c < OR_ANC_F; ++c) x[c] = feat[c];
     for (int a = 0; a < 3; ++a) x[OR_ANC_F + a] = v[a] / d;
     x[OR_ANC_F + 3] = log1p(d);
+    if (bf16)
+        for (int c = 0; c < OR_ANC_IN; ++c) x[c] = bf16_round(x[c]);
     for (int o = 0; o < OR_ANC_H; ++o) {
         double s = w[OR_ANC_B1 + o];
-        for (int c = 0; c < OR_ANC_IN; ++c) s += w[OR_ANC_W1 + o * OR_ANC_IN + c] * x[c];
+        for (int c = 0; c < OR_ANC_IN; ++c) {
+            const double wv = w[OR_ANC_W1 + o * OR_ANC_IN + c];
+            s += (bf16 ? bf16_round(wv) : wv) * x[c];
+        }
         pre[o] = s;
     }
     for (int o = 0; o < OR_ANC_OUT; ++o) {
         double s = w[OR_ANC_B2 + o];
-        for (int c = 0; c < OR_ANC_H; ++c) s += w[OR_ANC_W2 + o * OR_ANC_H + c] * (pre[c] > 0.0 ? pre[c] : 0.0);
+        for (int c = 0; c < OR_ANC_H; ++c) {
+            const double wv = w[OR_ANC_W2 + o * OR_ANC_H + c], h = pre[c] > 0.0 ? pre[c] : 0.0;
+            s += (bf16 ? bf16_round(wv) : wv) * (bf16 ? bf16_round(h) : h);
+        }
         z[o] = s;
     }
     *dist = d;
@@ -1361,10 +1372,10 @@ static int lod_active(int32_t level, double d, const double *max_dist) {
 
 void or_anchor_decode(int64_t n, const double *pos, const int32_t *level, const double *feat, const double *log_l,
                       const double *offs, const double *w, const double cam_c[3], const double *max_dist,
-                      double *rows, uint8_t *keep, uint8_t *unsure, double tol) {
+                      double *rows, uint8_t *keep, uint8_t *unsure, double tol, int32_t bf16) {
     for (int64_t i = 0; i < n; ++i) {
         double x[OR_ANC_IN], pre[OR_ANC_H], z[OR_ANC_OUT], d;
-        anchor_mlp(pos + 3 * i, feat + OR_ANC_F * i, w, cam_c, x, pre, z, &d);
+        anchor_mlp(pos + 3 * i, feat + OR_ANC_F * i, w, cam_c, x, pre, z, &d, bf16);
         const int M = lod_active(level[i], d, max_dist);
         const double lo = level[i] > 0 ? max_dist[level[i] - 1] : 0.0;
         int near_band = fabs(d - lo) <= tol * d || fabs(d - max_dist[level[i]]) <= tol * d;
@@ -1402,10 +1413,12 @@ void or_anchor_decode(int64_t n, const double *pos, const int32_t *level, const 
 void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *level, const double *feat,
                                const double *log_l, const double *offs, const double *w, const double cam_c[3],
                                const double *max_dist, const double *g_rows, double *g_feat, double *g_log_l,
-                               double *g_offs, double *g_w) {
+                               double *g_offs, double *g_w, int32_t bf16) {
+    /* bf16: the plain FP64 chain rule of the bf16 forward (a rounded operand's
+     * product differentiated with the rounded factor, nothing rounded here) */
     for (int64_t i = 0; i < n; ++i) {
         double x[OR_ANC_IN], pre[OR_ANC_H], z[OR_ANC_OUT], d, dz[OR_ANC_OUT];
-        anchor_mlp(pos + 3 * i, feat + OR_ANC_F * i, w, cam_c, x, pre, z, &d);
+        anchor_mlp(pos + 3 * i, feat + OR_ANC_F * i, w, cam_c, x, pre, z, &d, bf16);
         const int M = lod_active(level[i], d, max_dist);
         const double *L = log_l + 3 * i;
         for (int o = 0; o < OR_ANC_OUT; ++o) dz[o] = 0.0;
@@ -1434,9 +1447,9 @@ void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *leve
             if (dz[o] == 0.0) continue;
             g_w[OR_ANC_B2 + o] += dz[o];
             for (int c = 0; c < OR_ANC_H; ++c) {
-                const double h = pre[c] > 0.0 ? pre[c] : 0.0;
-                g_w[OR_ANC_W2 + o * OR_ANC_H + c] += dz[o] * h;
-                dh[c] += dz[o] * w[OR_ANC_W2 + o * OR_ANC_H + c];
+                const double h = pre[c] > 0.0 ? pre[c] : 0.0, wv = w[OR_ANC_W2 + o * OR_ANC_H + c];
+                g_w[OR_ANC_W2 + o * OR_ANC_H + c] += dz[o] * (bf16 ? bf16_round(h) : h);
+                dh[c] += dz[o] * (bf16 ? bf16_round(wv) : wv);
             }
         }
         for (int c = 0; c < OR_ANC_H; ++c) {
@@ -1444,8 +1457,9 @@ void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *leve
             if (dp == 0.0) continue;
             g_w[OR_ANC_B1 + c] += dp;
             for (int m = 0; m < OR_ANC_IN; ++m) {
-                g_w[OR_ANC_W1 + c * OR_ANC_IN + m] += dp * x[m];
-                if (m < OR_ANC_F) g_feat[OR_ANC_F * i + m] += dp * w[OR_ANC_W1 + c * OR_ANC_IN + m];
+                const double wv = w[OR_ANC_W1 + c * OR_ANC_IN + m];
+                g_w[OR_ANC_W1 + c * OR_ANC_IN + m] += dp * x[m];  /* x rounded in bf16 mode */
+                if (m < OR_ANC_F) g_feat[OR_ANC_F * i + m] += dp * (bf16 ? bf16_round(wv) : wv);
             }
         }
     }

@@ -221,13 +221,15 @@ int64_t or_init_select(int32_t H, int32_t W, const double *prob, const double *u
 int32_t or_anchor_num_weights(void);
 void or_anchor_decode(int64_t n, const double *pos, const int32_t *level, const double *feat, const double *log_l,
                       const double *offs, const double *w, const double cam_c[3], const double *max_dist,
-                      double *rows, uint8_t *keep, uint8_t *unsure, double tol);
+                      double *rows, uint8_t *keep, uint8_t *unsure, double tol, int32_t bf16);
 /* Accumulates into g_feat, g_log_l, g_offs and g_w the gradient of a loss
- * whose gradient with respect to rows is g_rows (same layout). */
+ * whose gradient with respect to rows is g_rows (same layout).  bf16 != 0
+ * rounds the decoder's hidden-layer operands (input, W1, hidden activation,
+ * W2) to bfloat16 in the forward; the backward is its plain FP64 chain rule. */
 void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *level, const double *feat,
                                const double *log_l, const double *offs, const double *w, const double cam_c[3],
                                const double *max_dist, const double *g_rows, double *g_feat, double *g_log_l,
-                               double *g_offs, double *g_w);
+                               double *g_offs, double *g_w, int32_t bf16);
 
 #ifdef __cplusplus
 }

@@ -149,3 +149,88 @@ def test_opacity_cull_never_changes_an_image():
     rest = {k: (v[keep] if isinstance(v, np.ndarray) else v) for k, v in faint.items()}
     g = orc.forward(rest, cam, cfg)
     assert np.abs(f["img"] - g["img"]).max() < 1e-12
+
+
+def _bf16(v):
+    """Round to the nearest bfloat16 (ties to even) through float32 bits, independently of the oracle."""
+    b = np.asarray(v, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_mode_two_unit_closed_form():
+    """Reading R30 by hand: two hidden units feed the opacity output of
+    Gaussian 0.  In bfloat16 mode the forward multiplies rounded operands
+    (input, W1, the hidden activation, W2) and sums exactly; the backward is
+    the exact chain rule of that forward, with the rounded factors."""
+    A = _anchors(1, 5)
+    A["pos"] = np.array([[0.3, -0.2, 4.0]])
+    w = np.zeros(NW)
+    rng = np.random.default_rng(6)
+    w[W1:W1 + IN] = rng.normal(0, 0.3, IN)            # unit 0 sees every input
+    w[W1 + IN:W1 + 2 * IN] = rng.normal(0, 0.3, IN)   # unit 1 too
+    w[B1], w[B1 + 1] = 0.7, 0.9
+    w[W2 + 3 * H], w[W2 + 3 * H + 1] = 0.61, -0.27     # z[3] (opacity of Gaussian 0) = ...
+    w[B2 + 3] = 0.4
+    w[B2 + 3 + 14:B2 + 14 * K:14] = -1.0               # the other Gaussians dropped
+    cam = np.zeros(3)
+    rows, keep, _ = orc.anchor_decode(A, w, cam, BANDS, bf16=True)
+    rows64, _, _ = orc.anchor_decode(A, w, cam, BANDS, bf16=False)
+    v = A["pos"][0]
+    d = np.linalg.norm(v)
+    x = np.concatenate([A["feat"][0], v / d, [math.log1p(d)]])
+    xb = _bf16(x)
+    pre = np.array([w[B1 + u] + _bf16(w[W1 + u * IN:W1 + (u + 1) * IN]) @ xb for u in range(2)])
+    assert np.all(pre > 0)
+    hb = _bf16(pre)
+    w2b = _bf16(w[W2 + 3 * H:W2 + 3 * H + 2])
+    z3 = w[B2 + 3] + w2b @ hb
+    a = math.tanh(z3)
+    assert keep[0] and not keep[1:].any()
+    assert abs(rows[0, 10] - math.log(a / (1 - a))) < 1e-12
+    assert abs(rows[0, 10] - rows64[0, 10]) > 1e-6  # the rounding acts
+    # backward of a loss = 2.5 x (opacity logit of Gaussian 0)
+    g_rows = np.zeros_like(rows)
+    g_rows[0, 10] = 2.5
+    gf, gl, go, gw = orc.anchor_decode_backward(A, w, cam, BANDS, g_rows, bf16=True)
+    dz3 = 2.5 * (1 + a) / a
+    assert abs(gw[B2 + 3] - dz3) < 1e-12
+    assert np.allclose(gw[W2 + 3 * H:W2 + 3 * H + 2], dz3 * hb, atol=1e-12)
+    dp = dz3 * w2b
+    assert np.allclose(gw[B1:B1 + 2], dp, atol=1e-12)
+    for u in range(2):
+        assert np.allclose(gw[W1 + u * IN:W1 + (u + 1) * IN], dp[u] * xb, atol=1e-12)
+    w1b = np.stack([_bf16(w[W1 + u * IN:W1 + (u + 1) * IN]) for u in range(2)])
+    assert np.allclose(gf[0], dp @ w1b[:, :F], atol=1e-12)
+
+
+def test_bf16_mode_is_fp64_mode_on_bfloat16_values():
+    """With inputs, weights and every hidden activation representable in
+    bfloat16 (small dyadic values; the direction and distance inputs carry
+    zero weight), the two modes decode identically and the feature and
+    decoder-weight gradients agree to rounding."""
+    A = _anchors(4, 7)
+    rng = np.random.default_rng(8)
+    A["feat"] = rng.integers(-4, 5, (4, F)) / 4.0
+    w = np.zeros(NW)
+    W1m = (rng.integers(-2, 3, (H, IN)) / 8.0)
+    W1m[:, F:] = 0.0
+    w[W1:W1 + H * IN] = W1m.ravel()
+    w[B1:B1 + H] = rng.integers(0, 3, H) / 8.0
+    w[W2:W2 + 14 * K * H] = rng.integers(-2, 3, 14 * K * H) / 64.0
+    w[B2:] = rng.integers(-2, 3, 14 * K) / 8.0
+    w[B2 + 3:B2 + 14 * K:14] = 0.5
+    cam = np.zeros(3)
+    r16, k16, _ = orc.anchor_decode(A, w, cam, BANDS, bf16=True)
+    r64, k64, _ = orc.anchor_decode(A, w, cam, BANDS, bf16=False)
+    assert np.array_equal(k16, k64) and k16.any()
+    assert np.array_equal(r16, r64)
+    g_rows = rng.normal(size=r16.shape)
+    g16 = orc.anchor_decode_backward(A, w, cam, BANDS, g_rows, bf16=True)
+    g64 = orc.anchor_decode_backward(A, w, cam, BANDS, g_rows, bf16=False)
+    assert np.allclose(g16[0], g64[0], rtol=1e-12, atol=1e-12)  # features
+    gw16, gw64 = g16[3], g64[3]
+    feat_cols = np.zeros(NW, bool)
+    feat_cols[W1:W1 + H * IN] = np.tile(np.arange(IN) < F, H)
+    feat_cols[B1:] = True
+    assert np.allclose(gw16[feat_cols], gw64[feat_cols], rtol=1e-12, atol=1e-12)

@@ -110,6 +110,7 @@ def lib():
         L.or_anchor_num_weights.restype = i32
         L.or_anchor_decode.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, i32]
         L.or_anchor_decode_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+        L.or_anchor_hidden.argtypes = [i64, vp, vp, vp, vp, i32, vp, vp]
     return _lib
 
 
@@ -491,6 +492,15 @@ def anchor_decode_backward(A, w, cam_centre, max_dist, g_rows, bf16=False):
     lib().or_anchor_decode_backward(n, _ptr(pos), _ptr(lv), _ptr(feat), _ptr(log_l), _ptr(offs), _ptr(w), _ptr(cc),
                                     _ptr(md), _ptr(g), _ptr(gf), _ptr(gl), _ptr(go), _ptr(gw), int(bool(bf16)))
     return gf, gl, go, gw
+
+
+def anchor_hidden(A, w, cam_centre, bf16=False):
+    """The decoder's unrounded input x [n][36] and hidden pre-activations [n][64] (bf16 as in anchor_decode)."""
+    n, pos, lv, feat, log_l, offs = _anchor_args(A)
+    w, cc = _f64(w), _f64(cam_centre, (3,))
+    x, pre = np.zeros((n, 36)), np.zeros((n, 64))
+    lib().or_anchor_hidden(n, _ptr(pos), _ptr(feat), _ptr(w), _ptr(cc), int(bool(bf16)), _ptr(x), _ptr(pre))
+    return x, pre
 
 
 def rows_to_params(rows):

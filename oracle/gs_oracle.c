@@ -1365,6 +1365,21 @@ static void anchor_mlp(const double *pos, const double *feat, const double *w, c
     *dist = d;
 }
 
+void or_anchor_hidden(int64_t n, const double *pos, const double *feat, const double *w, const double cam_c[3],
+                      int32_t bf16, double *x_raw, double *pre) {
+    for (int64_t i = 0; i < n; ++i) {
+        double x[OR_ANC_IN], p[OR_ANC_H], z[OR_ANC_OUT], d;
+        if (x_raw) {
+            anchor_mlp(pos + 3 * i, feat + OR_ANC_F * i, w, cam_c, x, p, z, &d, 0);
+            for (int c = 0; c < OR_ANC_IN; ++c) x_raw[OR_ANC_IN * i + c] = x[c];
+        }
+        if (pre) {
+            anchor_mlp(pos + 3 * i, feat + OR_ANC_F * i, w, cam_c, x, p, z, &d, bf16);
+            for (int c = 0; c < OR_ANC_H; ++c) pre[OR_ANC_H * i + c] = p[c];
+        }
+    }
+}
+
 static int lod_active(int32_t level, double d, const double *max_dist) {
     const double lo = level > 0 ? max_dist[level - 1] : 0.0;
     return d >= lo && d < max_dist[level];

@@ -230,6 +230,12 @@ void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *leve
                                const double *log_l, const double *offs, const double *w, const double cam_c[3],
                                const double *max_dist, const double *g_rows, double *g_feat, double *g_log_l,
                                double *g_offs, double *g_w, int32_t bf16);
+/* The decoder's input x_raw[n][36] before any rounding and its hidden
+ * pre-activations pre[n][64] (bf16 as in or_anchor_decode); either
+ * nullable.  Used to find the anchors whose bfloat16 roundings sit next to a
+ * rounding midpoint. */
+void or_anchor_hidden(int64_t n, const double *pos, const double *feat, const double *w, const double cam_c[3],
+                      int32_t bf16, double *x_raw, double *pre);
 
 #ifdef __cplusplus
 }

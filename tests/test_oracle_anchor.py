@@ -234,3 +234,25 @@ def test_bf16_mode_is_fp64_mode_on_bfloat16_values():
     feat_cols[W1:W1 + H * IN] = np.tile(np.arange(IN) < F, H)
     feat_cols[B1:] = True
     assert np.allclose(gw16[feat_cols], gw64[feat_cols], rtol=1e-12, atol=1e-12)
+
+
+def test_hidden_inputs_and_pre_activations():
+    """The decoder input is (feature, unit direction from the camera, log(1 + d))
+    and the pre-activation is W1 x + b1 (a matrix product); in bf16 mode the
+    pre-activation is that product over bfloat16-rounded x and W1, while the
+    returned input stays unrounded."""
+    A = _anchors(7, 31, dist=(2.0, 40.0))
+    w = _weights(32)
+    cc = np.array([0.3, -0.2, 0.1])
+    x, pre = orc.anchor_hidden(A, w, cc)
+    v = A["pos"] - cc
+    d = np.linalg.norm(v, axis=1)
+    assert np.array_equal(x[:, :F], A["feat"])
+    assert np.allclose(x[:, F:F + 3], v / d[:, None], atol=1e-15)
+    assert np.allclose(np.expm1(x[:, F + 3]), d, rtol=1e-13)
+    W1m, b1 = w[W1:B1].reshape(H, IN), w[B1:B1 + H]
+    assert np.allclose(pre, x @ W1m.T + b1, atol=1e-12)
+    xb, preb = orc.anchor_hidden(A, w, cc, bf16=True)
+    assert np.array_equal(xb, x)
+    assert np.allclose(preb, _bf16(x) @ _bf16(W1m).T + b1, atol=1e-12)
+    assert np.abs(preb - pre).max() > 1e-4  # the rounding is visible

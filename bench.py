@@ -948,29 +948,25 @@ def run_anchors(args, dev):
         for j, k in enumerate(names):
             acc[k] += ev[j].elapsed_time(ev[j + 1])
     stage = {k: round(v / steps, 4) for k, v in acc.items()}
-    # the decoder kernels are FP32 FMA streams: 2 (36*64 + 140*64) flops per anchor forward,
-    # recomputed in the backward plus dW2, dW1, dL/dh, dL/df (~4x the forward)
-    fl_fwd = 2.0 * (36 * 64 + 140 * 64) * n
-    peak_fp32 = alu_peak_tflops(clk)
+    # the decoder kernels are HBM streams once their two layers run on the tensor cores (13.4 MFLOP
+    # per 1k anchors, microseconds at the BF16 peak): algorithmic bytes per anchor, decode = inputs
+    # (feature 32, position 3, log-scale 3, offsets 30, level 1: 276 B) + 10 x 14 decoded floats
+    # (560 B); backward = the same inputs + 10 x 14 incoming gradients + 65 anchor gradients (260 B)
+    bytes_stage = {"decode": 836.0 * model.ld, "decode_bwd": 1096.0 * n}
     dom = "decode_bwd" if stage["decode_bwd"] >= stage["decode"] else "decode"
-    fl = fl_fwd * (4.0 if dom == "decode_bwd" else 1.0)
-    achieved = fl / (stage[dom] * 1e-3) / 1e12
+    peak, kind = measured_peaks()
+    achieved = bytes_stage[dom] / (stage[dom] * 1e-3) / 1e9
     return {"metric": "anchor mapping iters/s (200k anchors x 10 Gaussians, 720p, decode+fwd+bwd+Adam)",
             "value": round(1e3 / ms, 2), "unit": "iters/s", "ms_per_step": round(ms, 4), "steps": steps,
             "warmup": args.warmup, "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "corridor anchors, K=10, 5 LoD levels, 1280x720, 16-frame pool",
-                       "anchors": n, "decoded_slots": 10 * model.ld, "launch": "eager"},
+                       "anchors": n, "decoded_slots": 10 * model.ld, "launch": "eager",
+                       "decoder": "tcgen05, bf16 operands, f32 sums"},
             "stages_ms": stage, "visible_mean": int(np.mean(vis)), "pairs_mean": int(np.mean(needed)),
-            "roofline": {"kernel": "k_anchor_" + dom, "bound": "alu", "achieved": round(achieved, 2),
-                         "peak": round(peak_fp32, 1), "unit": "TFLOP/s", "frac": round(achieved / peak_fp32, 4),
-                         "traffic": None, "peak_kind": "FP32 FMA: 148 SMs x 128 lanes x 2 flops x SM clock"},
+            "roofline": {"kernel": "k_anchor_" + dom, "bound": "hbm", "achieved": round(achieved, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "bytes_per_launch": bytes_stage[dom], "peak_kind": kind + " copy bandwidth"},
             "clocks": clk}
-
-
-def alu_peak_tflops(clk):
-    """FP32 FMA peak at the sampled SM clock (148 SMs x 128 FP32 lanes x 2 flops)."""
-    mhz = (clk or {}).get("sm_mhz") or 1920.0
-    return 148 * 128 * 2 * float(mhz) * 1e6 / 1e12
 
 
 class OracleAdam:

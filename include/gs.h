@@ -635,20 +635,32 @@ typedef struct {
  * anchors i >= n) get opacity logit -30, which the projection culls, so out
  * renders directly through gs_project ... gs_render_bwd.  max_dist: host
  * float[levels] (the bands of gs_init_cfg), 1 <= levels <= 8.
+ * The decoder's two layers run on the tensor cores with bfloat16 operands
+ * (the input x, W1, the hidden activation, W2) and FP32 sums; the biases and
+ * everything after the hidden layer are FP32.  max_polls and status
+ * (nullable device int32) as in gs_mlp_forward: a CTA whose wait for its
+ * tensor-core products gives up sets bit 1<<GS_ERR_TIMEOUT and writes no
+ * further tiles.
  */
 gs_status gs_anchor_decode(const gs_anchor_params *a, const float *weights, const float cam_centre[3],
-                           const float *max_dist, int32_t levels, const gs_params *out, gs_stream stream);
+                           const float *max_dist, int32_t levels, const gs_params *out, int32_t *status,
+                           int64_t max_polls, gs_stream stream);
 
 /*
  * Gradient of a loss with respect to the anchors (grad_anchor
  * [GS_ANCHOR_PLANES][a->ld], overwritten) and the decoder's weights
  * (grad_weights [GS_ANCHOR_WEIGHTS], overwritten) from its gradient with
  * respect to the decoded Gaussians (grad_out, laid out as out above, e.g.
- * the gradient buffer of gs_render_bwd / gs_project_bwd).
+ * the gradient buffer of gs_render_bwd / gs_project_bwd).  The products
+ * with W2, W1 and the weight gradients' sums over anchors run on the tensor
+ * cores with dL/dz and dL/d(pre-activation) rounded to bfloat16 (FP32
+ * sums); the rest is FP32.  max_polls and status as in gs_anchor_decode; a
+ * timed-out CTA adds nothing to grad_weights.
  */
 gs_status gs_anchor_decode_bwd(const gs_anchor_params *a, const float *weights, const float cam_centre[3],
                                const float *max_dist, int32_t levels, const gs_params *grad_out,
-                               float *grad_anchor, float *grad_weights, gs_stream stream);
+                               float *grad_anchor, float *grad_weights, int32_t *status, int64_t max_polls,
+                               gs_stream stream);
 
 /* Adam with bias correction over n contiguous floats (p, g, m, v device). */
 gs_status gs_adam_flat(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2,

@@ -109,7 +109,7 @@ def lib():
         L.or_init_select.restype = i64
         L.or_anchor_num_weights.restype = i32
         L.or_anchor_decode.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, i32]
-        L.or_anchor_decode_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+        L.or_anchor_decode_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp]
         L.or_anchor_hidden.argtypes = [i64, vp, vp, vp, vp, i32, vp, vp]
     return _lib
 
@@ -483,15 +483,18 @@ def anchor_decode(A, w, cam_centre, max_dist, tol=1e-6, bf16=False):
     return rows, keep.astype(bool), unsure.astype(bool)
 
 
-def anchor_decode_backward(A, w, cam_centre, max_dist, g_rows, bf16=False):
+def anchor_decode_backward(A, w, cam_centre, max_dist, g_rows, bf16=False, rows=False):
     """Gradients (feat, log_l, offs, w) of a loss with dL/drows = g_rows (bf16: of the bfloat16-operand
-    forward, plain FP64 chain rule)."""
+    forward, plain FP64 chain rule); rows=True also returns each anchor's dL/dz [n][140] and
+    dL/dpre [n][64]."""
     n, pos, lv, feat, log_l, offs = _anchor_args(A)
     w, cc, md, g = _f64(w), _f64(cam_centre, (3,)), _f64(max_dist), _f64(g_rows, (ANCHOR_K * n, 14))
     gf, gl, go, gw = np.zeros_like(feat), np.zeros_like(log_l), np.zeros_like(offs), np.zeros_like(w)
+    dz, dp = (np.zeros((n, 14 * ANCHOR_K)), np.zeros((n, 64))) if rows else (None, None)
     lib().or_anchor_decode_backward(n, _ptr(pos), _ptr(lv), _ptr(feat), _ptr(log_l), _ptr(offs), _ptr(w), _ptr(cc),
-                                    _ptr(md), _ptr(g), _ptr(gf), _ptr(gl), _ptr(go), _ptr(gw), int(bool(bf16)))
-    return gf, gl, go, gw
+                                    _ptr(md), _ptr(g), _ptr(gf), _ptr(gl), _ptr(go), _ptr(gw), int(bool(bf16)),
+                                    _ptr(dz) if rows else None, _ptr(dp) if rows else None)
+    return (gf, gl, go, gw, dz, dp) if rows else (gf, gl, go, gw)
 
 
 def anchor_hidden(A, w, cam_centre, bf16=False):

@@ -1428,7 +1428,7 @@ void or_anchor_decode(int64_t n, const double *pos, const int32_t *level, const 
 void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *level, const double *feat,
                                const double *log_l, const double *offs, const double *w, const double cam_c[3],
                                const double *max_dist, const double *g_rows, double *g_feat, double *g_log_l,
-                               double *g_offs, double *g_w, int32_t bf16) {
+                               double *g_offs, double *g_w, int32_t bf16, double *dz_out, double *dp_out) {
     /* bf16: the plain FP64 chain rule of the bf16 forward (a rounded operand's
      * product differentiated with the rounded factor, nothing rounded here) */
     for (int64_t i = 0; i < n; ++i) {
@@ -1456,6 +1456,8 @@ void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *leve
             for (int c = 0; c < 4; ++c) dk[4 + c] = g[6 + c];           /* rotation */
             dk[3] = g[10] * (1.0 + a) / a;  /* d logit(tanh z) / dz = (1 - a^2) / (a (1 - a)) */
         }
+        if (dz_out)
+            for (int o = 0; o < OR_ANC_OUT; ++o) dz_out[OR_ANC_OUT * i + o] = dz[o];
         double dh[OR_ANC_H];
         for (int c = 0; c < OR_ANC_H; ++c) dh[c] = 0.0;
         for (int o = 0; o < OR_ANC_OUT; ++o) {
@@ -1469,6 +1471,7 @@ void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *leve
         }
         for (int c = 0; c < OR_ANC_H; ++c) {
             const double dp = pre[c] > 0.0 ? dh[c] : 0.0;
+            if (dp_out) dp_out[OR_ANC_H * i + c] = dp;
             if (dp == 0.0) continue;
             g_w[OR_ANC_B1 + c] += dp;
             for (int m = 0; m < OR_ANC_IN; ++m) {

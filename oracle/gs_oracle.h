@@ -225,11 +225,13 @@ void or_anchor_decode(int64_t n, const double *pos, const int32_t *level, const 
 /* Accumulates into g_feat, g_log_l, g_offs and g_w the gradient of a loss
  * whose gradient with respect to rows is g_rows (same layout).  bf16 != 0
  * rounds the decoder's hidden-layer operands (input, W1, hidden activation,
- * W2) to bfloat16 in the forward; the backward is its plain FP64 chain rule. */
+ * W2) to bfloat16 in the forward; the backward is its plain FP64 chain rule.
+ * dz_out[n][140] and dp_out[n][64] (nullable) receive each anchor's gradient
+ * with respect to the decoder's outputs and hidden pre-activations. */
 void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *level, const double *feat,
                                const double *log_l, const double *offs, const double *w, const double cam_c[3],
                                const double *max_dist, const double *g_rows, double *g_feat, double *g_log_l,
-                               double *g_offs, double *g_w, int32_t bf16);
+                               double *g_offs, double *g_w, int32_t bf16, double *dz_out, double *dp_out);
 /* The decoder's input x_raw[n][36] before any rounding and its hidden
  * pre-activations pre[n][64] (bf16 as in or_anchor_decode); either
  * nullable.  Used to find the anchors whose bfloat16 roundings sit next to a

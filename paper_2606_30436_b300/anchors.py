@@ -42,8 +42,9 @@ def _lib():
     L = gs.lib()
     if not _typed:
         vp, i32, i64, f32, P = C.c_void_p, C.c_int32, C.c_int64, C.c_float, C.POINTER
-        L.gs_anchor_decode.argtypes = [P(AnchorParams), vp, P(f32 * 3), vp, i32, P(gs.Params), vp]
-        L.gs_anchor_decode_bwd.argtypes = [P(AnchorParams), vp, P(f32 * 3), vp, i32, P(gs.Params), vp, vp, vp]
+        L.gs_anchor_decode.argtypes = [P(AnchorParams), vp, P(f32 * 3), vp, i32, P(gs.Params), vp, i64, vp]
+        L.gs_anchor_decode_bwd.argtypes = [P(AnchorParams), vp, P(f32 * 3), vp, i32, P(gs.Params), vp, vp, vp, i64,
+                                           vp]
         L.gs_adam_flat.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp]
         _typed = True
     return L
@@ -109,20 +110,23 @@ def _bands(max_dist):
     return md, len(max_dist)
 
 
-def gs_anchor_decode(model: AnchorModel, cam_centre, out: gs.GaussianModel, max_dist=MAX_DIST_DEFAULT, stream=None):
+def gs_anchor_decode(model: AnchorModel, cam_centre, out: gs.GaussianModel, max_dist=MAX_DIST_DEFAULT, stream=None,
+                     status=None, max_polls=-1):
     md, lv = _bands(max_dist)
     cc = (C.c_float * 3)(*[float(x) for x in cam_centre])
     gs._check(_lib().gs_anchor_decode(C.byref(model.c()), gs._ptr(model.weights), C.byref(cc), md, lv,
-                                      C.byref(out.c()), gs._stream(stream)), "gs_anchor_decode")
+                                      C.byref(out.c()), gs._ptr(status), int(max_polls), gs._stream(stream)),
+              "gs_anchor_decode")
 
 
 def gs_anchor_decode_bwd(model: AnchorModel, cam_centre, grad_out: gs.GaussianModel, grad_anchor, grad_weights,
-                         max_dist=MAX_DIST_DEFAULT, stream=None):
+                         max_dist=MAX_DIST_DEFAULT, stream=None, status=None, max_polls=-1):
     md, lv = _bands(max_dist)
     cc = (C.c_float * 3)(*[float(x) for x in cam_centre])
     gs._check(_lib().gs_anchor_decode_bwd(C.byref(model.c()), gs._ptr(model.weights), C.byref(cc), md, lv,
                                           C.byref(grad_out.c()), gs._ptr(grad_anchor), gs._ptr(grad_weights),
-                                          gs._stream(stream)), "gs_anchor_decode_bwd")
+                                          gs._ptr(status), int(max_polls), gs._stream(stream)),
+              "gs_anchor_decode_bwd")
 
 
 def gs_adam_flat(p, g, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
@@ -167,9 +171,11 @@ class AnchorStep:
     def gradients(self, target, stream=None):
         """Decode, forward, loss and every gradient (anchors, decoder) without an update."""
         cc = camera_centre(self.cam)
-        gs_anchor_decode(self.model, cc, self.gauss, self.max_dist, stream)
+        status = self.map.buf.status
+        gs_anchor_decode(self.model, cc, self.gauss, self.max_dist, stream, status=status)
         loss = self.map.step(target, stream, optimize=False)
-        gs_anchor_decode_bwd(self.model, cc, self.map.grads, self.g_anchor, self.g_w, self.max_dist, stream)
+        gs_anchor_decode_bwd(self.model, cc, self.map.grads, self.g_anchor, self.g_w, self.max_dist, stream,
+                             status=status)
         return loss
 
     def step(self, target, stream=None):

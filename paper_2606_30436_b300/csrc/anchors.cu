@@ -4,25 +4,23 @@
 // the rasteriser; the backward takes the rasteriser's parameter gradients back
 // to the anchors and the decoder's weights; a flat Adam updates both.
 //
-// k_anchor_decode: thread per anchor, the decoder's weights (11,468 floats)
-// in shared memory and read as broadcasts; hidden layer in registers; slot
-// (k, i) of the output is column k ld + i of every plane (coalesced per k).
-// Dropped Gaussians (outside the level's distance band, opacity <= 0) get a
-// placeholder whose opacity logit (-30) the projection culls.
-// k_anchor_decode_bwd: 128-anchor tiles, thread per anchor.  The inputs, the
-// hidden activations and dL/dz of the tile are staged in shared memory
-// ([row][129]: a column read by a warp touches 32 banks); each thread then
-// owns 70 entries of dW2 (35 outputs of its warp x 2 hidden units of its
-// lane, so a row of the tile costs 37 loads for 70 FMAs) and 18 of dW1, sums
-// them over the tile's anchors in registers across its tiles (one FP32
-// atomic per weight per CTA at the end), and takes its own anchor's
-// dL/dh = W2^T dz and dL/df = W1^T dL/dpre.
+// Both directions run the decoder's two layers on the 5th-generation tensor
+// cores (BF16 operands in shared memory, FP32 sums in tensor memory), one
+// 128-anchor tile per MMA; the per-Gaussian activations, the decoded
+// parameters and dL/dz are FP32 on CUDA cores, one thread per anchor row.
+// Slot (k, i) of the output is column k ld + i of every plane (coalesced per
+// k).  Dropped Gaussians (outside the level's distance band, opacity <= 0) get
+// a placeholder whose opacity logit (-30) the projection culls.  Every
+// mbarrier wait is bounded; on a timeout a kernel flags the status word,
+// stops issuing and still frees its tensor memory.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 
 #include "gs_internal.cuh"
 #include "gs_kernels.h"
+#include "tcgen05.cuh"
 
 namespace gs {
 
@@ -37,27 +35,12 @@ constexpr int kPlaneLogL = kAF, kPlaneOffs = kAF + 3;
 static_assert(kPlaneOffs + 3 * kAK == GS_ANCHOR_PLANES, "anchor planes");
 constexpr float kY00 = 0.28209479177387814f;
 constexpr float kDeadLogit = -30.0f;
-constexpr int kBT = 128, kLdS = kBT + 1;  // backward tile and its padded shared row
 
 __device__ __forceinline__ float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
 
 // log(sigmoid(z)) without overflow for either sign
 __device__ __forceinline__ float log_sigmoidf(float z) {
     return z >= 0.0f ? -log1pf(expf(-z)) : z - log1pf(expf(z));
-}
-
-// Decoder input of anchor i (feature, unit direction from the camera, log(1 + d)); returns d.
-__device__ __forceinline__ float anchor_input(const float *__restrict__ A, const float *__restrict__ pos, long long ld,
-                                              long long i, const AnchorView &v, float *x) {
-    const float dx = pos[i] - v.c[0], dy = pos[ld + i] - v.c[1], dz = pos[2 * ld + i] - v.c[2];
-    const float d = sqrtf(dx * dx + dy * dy + dz * dz);
-    #pragma unroll
-    for (int c = 0; c < kAF; ++c) x[c] = A[c * ld + i];
-    x[kAF] = dx / d;
-    x[kAF + 1] = dy / d;
-    x[kAF + 2] = dz / d;
-    x[kAF + 3] = log1pf(d);
-    return d;
 }
 
 __device__ __forceinline__ bool band_active(const AnchorView &v, int l, float d) {
@@ -81,165 +64,416 @@ __device__ __forceinline__ void write_dead(float *__restrict__ G, long long gld,
     G[13 * gld + col] = 0.0f;
 }
 
-__global__ void __launch_bounds__(256) k_anchor_decode(const float *__restrict__ A, const float *__restrict__ pos,
-                                                       const int *__restrict__ level, long long n, long long ld,
-                                                       const float *__restrict__ w, const __grid_constant__ AnchorView v,
-                                                       float *__restrict__ G, long long gld) {
-    __shared__ __align__(16) float sw[kANW];
-    for (int j = threadIdx.x; j < kANW; j += blockDim.x) sw[j] = w[j];
-    __syncthreads();
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ld) return;
-    float p[3] = {0.0f, 0.0f, 0.0f}, L[3] = {0.0f, 0.0f, 0.0f};
-    bool M = false;
-    float h[kAH];
-    if (i < n) {
-        float x[kAIn];
-        const float d = anchor_input(A, pos, ld, i, v, x);
-        #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            p[c] = pos[c * ld + i];
-            L[c] = A[(kPlaneLogL + c) * ld + i];
-        }
-        M = band_active(v, level[i], d);
-        if (M) {
-            // weight rows read as float4 broadcasts (rows start on 16-byte boundaries)
-            #pragma unroll
-            for (int o = 0; o < kAH; ++o) {
-                const float4 *w4 = reinterpret_cast<const float4 *>(sw + kAW1 + o * kAIn);
-                float s = sw[kAB1 + o];
-                #pragma unroll
-                for (int c = 0; c < kAIn / 4; ++c) {
-                    const float4 q = w4[c];
-                    s += q.x * x[4 * c] + q.y * x[4 * c + 1] + q.z * x[4 * c + 2] + q.w * x[4 * c + 3];
-                }
-                h[o] = fmaxf(s, 0.0f);
-            }
+// ---------------------------------------------------------------------------
+// Tensor-core decoder.  A tile is 128 anchors = the M of one tcgen05.mma;
+// thread t of the CTA owns anchor row t (TMEM lane t).  Operands are BF16 in
+// shared memory (K-major, no swizzle: 8x8 core matrices of 128 bytes), sums
+// FP32 in TMEM; the biases are added in FP32 when a row is read back.  The
+// 140 outputs sit in 16-column slots (Gaussian k at columns 16 k .. 16 k + 13,
+// two zero columns), so one 16-column TMEM load holds one Gaussian.
+// ---------------------------------------------------------------------------
+constexpr int kM = 128;                   // anchors per tile
+constexpr int kSlot = 16, kOutP = kSlot * kAK;  // padded outputs (160)
+constexpr int kXC = 48, kXG = kXC / 8;    // x: 36 inputs, the constant 1 (column 36), zeros
+constexpr int kHC = 80, kHG = kHC / 8;    // backward h: 64 activations, the constant 1 (column 64), zeros
+constexpr int kOG = kOutP / 8;            // core matrices along the padded outputs
+static_assert(kAIn < kXC && kOutP <= 256 && kOutP % 16 == 0, "tile shapes");
+
+struct DecWeights {
+    alignas(128) __nv_bfloat16 w1[kAH * kXC];    // B of layer 1: [n = o][k = c], c >= 36 zero
+    alignas(128) __nv_bfloat16 w2[kOutP * kAH];  // B of layer 2: [n = 16 k + j][k = c], j >= 14 zero
+    float b1[kAH], b2[kOutP];                     // FP32 biases
+};
+
+// Eight consecutive FP32 weights (16-byte aligned) or zeros.
+__device__ __forceinline__ void load8(const float *__restrict__ src, bool lo, bool hi, float *v) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 a = lo ? __ldg(reinterpret_cast<const float4 *>(src)) : z;
+    const float4 b = hi ? __ldg(reinterpret_cast<const float4 *>(src) + 1) : z;
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// The BF16 operand images of W1 and W2 and the FP32 biases, from 16-byte loads (every row of
+// W1 (36 floats) and W2 (64) starts on a 16-byte boundary; blockDim.x == kM).
+__device__ void stage_weights(DecWeights &s, const float *__restrict__ w) {
+    #pragma unroll
+    for (int r = 0; r < (kAH * kXG + kM - 1) / kM; ++r) {
+        const int u = threadIdx.x + kM * r;
+        if (u < kAH * kXG) {
+            const int o = u / kXG, c0 = 8 * (u % kXG);
+            float v[8];
+            load8(w + kAW1 + o * kAIn + c0, c0 + 4 <= kAIn, c0 + 8 <= kAIn, v);
+            store_row8(s.w1, o, c0, kXG, v);
         }
     }
-    for (int k = 0; k < kAK; ++k) {
-        const long long col = k * ld + i;
-        if (!M) {
-            write_dead(G, gld, col, p, L);
-            continue;
-        }
-        float z[14];
-        #pragma unroll
-        for (int j = 0; j < 14; ++j) {
-            const int o = 14 * k + j;
-            const float4 *w4 = reinterpret_cast<const float4 *>(sw + kAW2 + o * kAH);
-            float s = sw[kAB2 + o];
-            #pragma unroll
-            for (int c = 0; c < kAH / 4; ++c) {
-                const float4 q = w4[c];
-                s += q.x * h[4 * c] + q.y * h[4 * c + 1] + q.z * h[4 * c + 2] + q.w * h[4 * c + 3];
-            }
-            z[j] = s;
-        }
-        const float a = tanhf(z[3]);
-        if (!(a > 0.0f)) {
-            write_dead(G, gld, col, p, L);
-            continue;
-        }
-        #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float l = expf(L[c]);
-            G[c * gld + col] = p[c] + (A[(kPlaneOffs + 3 * k + c) * ld + i] + z[11 + c]) * l;  // mean
-            G[(3 + c) * gld + col] = L[c] + log_sigmoidf(z[8 + c]);                          // log(l ds)
-            G[(11 + c) * gld + col] = (sigmoidf(z[c]) - 0.5f) / kY00;                          // colour
-        }
-        G[6 * gld + col] = 1.0f + z[4];
-        G[7 * gld + col] = z[5];
-        G[8 * gld + col] = z[6];
-        G[9 * gld + col] = z[7];
-        G[10 * gld + col] = logf(a) - log1pf(-a);
+    #pragma unroll
+    for (int r = 0; r < kOutP * (kAH / 8) / kM; ++r) {
+        const int u = threadIdx.x + kM * r;
+        const int q = u / (kAH / 8), c0 = 8 * (u % (kAH / 8)), k = q / kSlot, j = q % kSlot;
+        float v[8];
+        load8(w + kAW2 + (14 * k + j) * kAH + c0, j < 14, j < 14, v);
+        store_row8(s.w2, q, c0, kAH / 8, v);
+    }
+    for (int i = threadIdx.x; i < kAH; i += blockDim.x) s.b1[i] = w[kAB1 + i];
+    for (int i = threadIdx.x; i < kOutP; i += blockDim.x) {
+        const int k = i / kSlot, j = i % kSlot;
+        s.b2[i] = j < 14 ? w[kAB2 + 14 * k + j] : 0.0f;
     }
 }
 
-struct BwdSmem {
-    float w[kANW];
-    float xs[kAIn][kLdS];
-    float hs[kAH][kLdS];   // hidden activations, then dL/d(pre-activation)
-    float dz[kAOut][kLdS];
+// TMEM allocation and the mbarrier; every thread sees both on return.
+__device__ void tc_begin(uint64_t *mbar, uint32_t *slot, uint32_t cols) {
+    tmem_alloc(slot, cols);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+}
+
+// After a timed-out wait nothing more is issued; the product committed last
+// (parity phase ^ 1) gets one more bounded wait before the TMEM is freed.
+__device__ void tc_end(uint64_t *mbar, uint32_t tmem, uint32_t cols, bool ok, uint32_t phase, int *status) {
+    if (!ok) {
+        mbar_wait(mbar, phase ^ 1u);
+        if (threadIdx.x == 0 && status) atomicOr(status, 1 << GS_ERR_TIMEOUT);
+    }
+    tmem_free(tmem, cols);
+}
+
+// Commit the MMAs issued so far by thread 0 and wait for them (warp-uniform result).
+__device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t &phase, long long polls) {
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(mbar, phase, polls));
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    return ok;
+}
+
+// Thread-written operands visible to the tensor core, TMEM reads finished, then a CTA barrier.
+__device__ __forceinline__ bool tc_sync(bool ok) {
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    return __syncthreads_and(ok);
+}
+
+// The loads of one anchor's inputs (issued a tile ahead).
+struct AnchorIn {
+    float f[kAF], p[3], L[3];
+    int lv;
 };
 
-__global__ void __launch_bounds__(kBT) k_anchor_decode_bwd(const float *__restrict__ A, const float *__restrict__ pos,
-                                                           const int *__restrict__ level, long long n, long long ld,
-                                                           const float *__restrict__ w,
-                                                           const __grid_constant__ AnchorView v,
-                                                           const float *__restrict__ GG, long long gld,
-                                                           float *__restrict__ gA, float *__restrict__ gw) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    BwdSmem &s = *reinterpret_cast<BwdSmem *>(smem_raw);
+__device__ __forceinline__ void load_anchor(AnchorIn &in, const float *__restrict__ A, const float *__restrict__ pos,
+                                            const int *__restrict__ level, long long n, long long ld, long long i) {
+    const bool valid = i < n;
+    #pragma unroll
+    for (int c = 0; c < kAF; ++c) in.f[c] = valid ? A[c * ld + i] : 0.0f;
+    #pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        in.p[c] = valid ? pos[c * ld + i] : 0.0f;
+        in.L[c] = valid ? A[(kPlaneLogL + c) * ld + i] : 0.0f;
+    }
+    in.lv = valid ? level[i] : -1;
+}
+
+// The tile row of x as the tensor core reads it: (feature, direction, log(1 + d)) of an
+// active anchor (zeros otherwise), the constant 1, zeros.  Returns whether the anchor is active.
+__device__ __forceinline__ bool stage_x(__nv_bfloat16 *xs, int row, const AnchorIn &in, const AnchorView &v) {
+    const float dx = in.p[0] - v.c[0], dy = in.p[1] - v.c[1], dz = in.p[2] - v.c[2];
+    const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+    const bool M = band_active(v, in.lv, d);
+    float x[kXC];
+    #pragma unroll
+    for (int c = 0; c < kAF; ++c) x[c] = M ? in.f[c] : 0.0f;
+    x[kAF] = M ? dx / d : 0.0f;
+    x[kAF + 1] = M ? dy / d : 0.0f;
+    x[kAF + 2] = M ? dz / d : 0.0f;
+    x[kAF + 3] = M ? log1pf(d) : 0.0f;
+    x[kAIn] = 1.0f;
+    #pragma unroll
+    for (int c = kAIn + 1; c < kXC; ++c) x[c] = 0.0f;
+    #pragma unroll
+    for (int c0 = 0; c0 < kXC; c0 += 8) store_row8(xs, row, c0, kXG, x + c0);
+    return M;
+}
+
+// Layer 1 into TMEM columns [col, col + 64): D = X W1^T, three K = 16 steps.
+__device__ __forceinline__ void issue_layer1(uint32_t tmem, const __nv_bfloat16 *xs, const DecWeights &wt) {
+    #pragma unroll
+    for (int kb = 0; kb < kXC / 16; ++kb)
+        mma_bf16(tmem, smem_desc(smem_addr(xs) + kb * 256, 128, kXG * 128),
+                 smem_desc(smem_addr(wt.w1) + kb * 256, 128, kXG * 128), idesc_bf16(kM, kAH), kb > 0);
+}
+
+// Layer 2: D = H W2^T (N = 160 padded outputs), four K = 16 steps over the 64 activations.
+__device__ __forceinline__ void issue_layer2(uint32_t tmem, const __nv_bfloat16 *hs, int hg, const DecWeights &wt) {
+    #pragma unroll
+    for (int kb = 0; kb < kAH / 16; ++kb)
+        mma_bf16(tmem, smem_desc(smem_addr(hs) + kb * 256, 128, hg * 128),
+                 smem_desc(smem_addr(wt.w2) + kb * 256, 128, (kAH / 8) * 128), idesc_bf16(kM, kOutP), kb > 0);
+}
+
+// Slot k's 14 outputs (plus two zero columns) of this thread's row, biases added.
+__device__ __forceinline__ void read_slot(uint32_t tmem, int col, const DecWeights &wt, int k, float *z) {
+    tmem_ld16(tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16) + (uint32_t)(col + kSlot * k), z);
+    #pragma unroll
+    for (int j = 0; j < 14; ++j) z[j] += wt.b2[kSlot * k + j];
+}
+
+struct DecSmem {
+    DecWeights wt;
+    alignas(128) __nv_bfloat16 x[kM * kXC];  // A of layer 1: [row][c]
+    alignas(128) __nv_bfloat16 h[kM * kAH];  // A of layer 2: [row][c]
+    uint64_t mbar;
+    uint32_t tmem;
+};
+constexpr uint32_t kDecCols = 256;  // layer 1 in [0, 64), layer 2 in [64, 224)
+constexpr int kDecZ = 64;
+static_assert(kDecZ + kOutP <= (int)kDecCols, "decode TMEM columns");
+static_assert(2 * (sizeof(DecSmem) + 1024) <= 228 * 1024, "two decode CTAs per SM");
+
+__global__ void __launch_bounds__(kM, 2) k_anchor_decode(const float *__restrict__ A, const float *__restrict__ pos,
+                                                          const int *__restrict__ level, long long n, long long ld,
+                                                          const float *__restrict__ w,
+                                                          const __grid_constant__ AnchorView v,
+                                                          float *__restrict__ G, long long gld,
+                                                          int *__restrict__ status, long long polls) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    DecSmem &s = *reinterpret_cast<DecSmem *>(smem_raw);
+    stage_weights(s.wt, w);
+    tc_begin(&s.mbar, &s.tmem, kDecCols);
     const int t = threadIdx.x;
-    for (int j = t; j < kANW; j += kBT) s.w[j] = w[j];
-    constexpr int kE2 = kAOut * kAH / kBT, kE1 = kAH * kAIn / kBT;  // 70, 18 entries per thread
-    static_assert(kE2 * kBT == kAOut * kAH && kE1 * kBT == kAH * kAIn, "weight entries per thread");
-    // dW2 entries of this thread: outputs kO2 * warp + j (j < kO2), hidden units lane and lane + 32
-    constexpr int kO2 = kAOut / (kBT / 32);  // 35
-    static_assert(kO2 * (kBT / 32) == kAOut && 2 * kO2 == kE2 && kAH == 64, "dW2 blocking");
-    const int warp = t >> 5, lane = t & 31;
-    float aW2[kE2], aW1[kE1], aB2[2] = {0.0f, 0.0f}, aB1 = 0.0f;
-    #pragma unroll
-    for (int j = 0; j < kE2; ++j) aW2[j] = 0.0f;
-    #pragma unroll
-    for (int j = 0; j < kE1; ++j) aW1[j] = 0.0f;
-    __syncthreads();
-    const long long tiles = ceil_div(n, (long long)kBT);
-    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const long long i = tile * kBT + t;
-        const bool valid = i < n;
-        bool M = false;
-        float L[3] = {0.0f, 0.0f, 0.0f};
-        {
-            float x[kAIn];
-            float d = 0.0f;
-            if (valid) {
-                d = anchor_input(A, pos, ld, i, v, x);
-                M = band_active(v, level[i], d);
-                #pragma unroll
-                for (int c = 0; c < 3; ++c) L[c] = A[(kPlaneLogL + c) * ld + i];
-            } else {
-                #pragma unroll
-                for (int c = 0; c < kAIn; ++c) x[c] = 0.0f;
-            }
+    const uint32_t tmem = s.tmem;
+    uint32_t phase = 0;
+    bool ok = true;
+    const long long tiles = ceil_div(ld, (long long)kM);
+    AnchorIn in;
+    if ((long long)blockIdx.x < tiles) load_anchor(in, A, pos, level, n, ld, (long long)blockIdx.x * kM + t);
+    for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const long long i = tile * kM + t;
+        const bool M = stage_x(s.x, t, in, v);
+        float p[3], L[3], off[3 * kAK];
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) { p[c] = in.p[c]; L[c] = in.L[c]; }
+        if (tile + gridDim.x < tiles) load_anchor(in, A, pos, level, n, ld, (tile + gridDim.x) * kM + t);
+        // the offsets arrive while the two layers run
+        #pragma unroll
+        for (int c = 0; c < 3 * kAK; ++c) off[c] = M ? A[(kPlaneOffs + c) * ld + i] : 0.0f;
+        ok = tc_sync(ok);
+        if (ok && t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            issue_layer1(tmem, s.x, s.wt);
+            mma_commit(&s.mbar);
+        }
+        if (ok) ok = tc_wait(&s.mbar, phase, polls);
+        if (ok) {
+            float hv[kAH];
+            tmem_row64(tmem, 0, hv);
             #pragma unroll
-            for (int c = 0; c < kAIn; ++c) s.xs[c][t] = x[c];
+            for (int c = 0; c < kAH; ++c) hv[c] = fmaxf(hv[c] + s.wt.b1[c], 0.0f);
             #pragma unroll
-            for (int o = 0; o < kAH; ++o) {
-                float a = s.w[kAB1 + o];
+            for (int c0 = 0; c0 < kAH; c0 += 8) store_row8(s.h, t, c0, kAH / 8, hv + c0);
+        }
+        ok = tc_sync(ok);
+        if (ok && t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            issue_layer2(tmem + kDecZ, s.h, kAH / 8, s.wt);
+            mma_commit(&s.mbar);
+        }
+        if (ok) ok = tc_wait(&s.mbar, phase, polls);
+        if (ok) {
+            #pragma unroll
+            for (int k = 0; k < kAK; ++k) {
+                float z[16];
+                read_slot(tmem, kDecZ, s.wt, k, z);
+                if (i >= ld) continue;
+                const long long col = k * ld + i;
+                const float a = tanhf(z[3]);
+                if (!M || !(a > 0.0f)) {
+                    write_dead(G, gld, col, p, L);
+                    continue;
+                }
                 #pragma unroll
-                for (int c = 0; c < kAIn; ++c) a += s.w[kAW1 + o * kAIn + c] * x[c];
-                s.hs[o][t] = M ? fmaxf(a, 0.0f) : 0.0f;
+                for (int c = 0; c < 3; ++c) {
+                    const float l = expf(L[c]);
+                    G[c * gld + col] = p[c] + (off[3 * k + c] + z[11 + c]) * l;  // mean
+                    G[(3 + c) * gld + col] = L[c] + log_sigmoidf(z[8 + c]);                          // log(l ds)
+                    G[(11 + c) * gld + col] = (sigmoidf(z[c]) - 0.5f) / kY00;                          // colour
+                }
+                G[6 * gld + col] = 1.0f + z[4];
+                G[7 * gld + col] = z[5];
+                G[8 * gld + col] = z[6];
+                G[9 * gld + col] = z[7];
+                G[10 * gld + col] = logf(a) - log1pf(-a);
             }
         }
-        // dL/dz of the kept Gaussians; the anchor's own offset and log-scale gradients
-        float gL[3] = {0.0f, 0.0f, 0.0f};
-        for (int k = 0; k < kAK; ++k) {
-            float dz[14];
+    }
+    tc_end(&s.mbar, tmem, kDecCols, ok, phase, status);
+}
+
+// Backward.  Per tile, after the forward's two layers (the activations h kept
+// in shared memory with a constant-1 column, their ReLU mask in registers):
+//   dz [row][160] from the decoded Gaussians' gradients (FP32 on CUDA cores,
+//     with the anchors' offset and log-scale gradients), stored BF16;
+//   dh = dz W2                      [128 x 64]  (K = 160),
+//   dW2 | db2 += [h | 1]^T dz        over the tile's rows, [80 x 160] kept in TMEM;
+//   dp = [pre > 0] dh, stored BF16;
+//   df = dp W1 (feature columns)    [128 x 32]  (K = 64),
+//   dW1 | db1 += dp^T [x | 1]        over the tile's rows, [64 x 48] kept in TMEM.
+// The weight sums use M = 128 with the first 65 (64) rows meaningful: the
+// remaining rows of D are never read, and their A rows read whatever shared
+// memory follows the operand.  The weight sums leave TMEM once, at the end,
+// as one FP32 atomic per weight per CTA.
+struct BwdSmem {
+    alignas(128) __nv_bfloat16 dz[kM * kOutP];  // [row][16 k + j]: dL/dz (A of dh K-major, B of dW2 MN-major)
+    alignas(128) __nv_bfloat16 h[kM * kHC];     // [row][c]: h, 1, zeros (A of layer 2, A of dW2 MN-major)
+    alignas(128) __nv_bfloat16 dp[kM * kAH];    // [row][o]: dL/dpre (A of df K-major, A of dW1 MN-major)
+    alignas(128) __nv_bfloat16 x[kM * kXC];     // [row][c]: x, 1, zeros (A of layer 1, B of dW1 MN-major)
+    alignas(128) __nv_bfloat16 w2t[kAH * kOutP];  // B of dh: [n = c][k = 16 k + j] = W2^T
+    alignas(128) __nv_bfloat16 w1t[kAF * kAH];    // B of df: [n = feature c][k = o] = W1^T
+    DecWeights wt;
+    uint64_t mbar;
+    uint32_t tmem;
+};
+// TMEM columns: pre then dh in [0, 64); z then df in [64, 224); dW2 | db2 in
+// [224, 384); dW1 | db1 in [384, 432).
+constexpr uint32_t kBwdCols = 512;
+constexpr int kColZ = 64, kColDF = 64, kColW2 = 224, kColW1 = 384;
+static_assert(kColZ + kOutP <= kColW2 && kColW2 + kOutP <= kColW1 && kColW1 + kXC <= (int)kBwdCols, "TMEM columns");
+// Byte strides of the MN-major reads (8-row groups of the K-major arrays).
+constexpr uint32_t kDzK = kOG * 128, kHK = kHG * 128, kDpK = (kAH / 8) * 128, kXK = kXG * 128;
+// Every descriptor read stays inside the CTA's shared memory whichever of the
+// two strides the hardware takes as the K one: the largest byte reached from
+// an operand's start is (last K step) + (groups - 1) x the larger stride +
+// one group x the other + 127.
+static_assert(offsetof(BwdSmem, dz) + 7 * 2 * kDzK + (kOG - 1) * kDzK + 128 + 127 < sizeof(BwdSmem), "dz read");
+static_assert(offsetof(BwdSmem, h) + 7 * 2 * kHK + 15 * kHK + 128 + 127 < sizeof(BwdSmem), "h read");
+static_assert(offsetof(BwdSmem, dp) + 7 * 2 * kDpK + 15 * kDpK + 128 + 127 < sizeof(BwdSmem), "dp read");
+static_assert(offsetof(BwdSmem, x) + 7 * 2 * kXK + (kXG - 1) * kXK + 128 + 127 < sizeof(BwdSmem), "x read");
+static_assert(sizeof(BwdSmem) + 1024 <= 227 * 1024, "backward shared memory");
+
+__global__ void __launch_bounds__(kM, 1) k_anchor_decode_bwd(const float *__restrict__ A, const float *__restrict__ pos,
+                                                              const int *__restrict__ level, long long n, long long ld,
+                                                              const float *__restrict__ w,
+                                                              const __grid_constant__ AnchorView v,
+                                                              const float *__restrict__ GG, long long gld,
+                                                              float *__restrict__ gA, float *__restrict__ gw,
+                                                              int *__restrict__ status, long long polls) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    BwdSmem &s = *reinterpret_cast<BwdSmem *>(smem_raw);
+    stage_weights(s.wt, w);
+    const int t = threadIdx.x;
+    {
+        // the transposed images from FP32 copies of W2 and W1 in the (not yet used) dz and h arrays
+        float *w2f = reinterpret_cast<float *>(s.dz), *w1f = reinterpret_cast<float *>(s.h);
+        static_assert(sizeof(float) * kAOut * kAH <= sizeof(s.dz) && sizeof(float) * kAH * kAIn <= sizeof(s.h),
+                      "weight scratch");
+        for (int u = t; u < kAOut * kAH / 4; u += kM)
+            reinterpret_cast<float4 *>(w2f)[u] = __ldg(reinterpret_cast<const float4 *>(w + kAW2) + u);
+        for (int u = t; u < kAH * kAIn / 4; u += kM)
+            reinterpret_cast<float4 *>(w1f)[u] = __ldg(reinterpret_cast<const float4 *>(w + kAW1) + u);
+        __syncthreads();
+        for (int u = t; u < kAH * kOG; u += kM) {
+            const int c = u % kAH, q0 = 8 * (u / kAH);  // a warp reads 32 consecutive columns c
+            float v[8];
             #pragma unroll
-            for (int j = 0; j < 14; ++j) dz[j] = 0.0f;
-            float gO[3] = {0.0f, 0.0f, 0.0f};
-            if (M) {
-                float z[14];
+            for (int jj = 0; jj < 8; ++jj) {
+                const int k = (q0 + jj) / kSlot, j = (q0 + jj) % kSlot;
+                v[jj] = j < 14 ? w2f[(14 * k + j) * kAH + c] : 0.0f;
+            }
+            store_row8(s.w2t, c, q0, kOG, v);
+        }
+        for (int u = t; u < kAF * (kAH / 8); u += kM) {
+            const int c = u % kAF, o0 = 8 * (u / kAF);
+            float v[8];
+            #pragma unroll
+            for (int jj = 0; jj < 8; ++jj) v[jj] = w1f[(o0 + jj) * kAIn + c];
+            store_row8(s.w1t, c, o0, kAH / 8, v);
+        }
+        __syncthreads();  // the scratch is read before h's constant columns overwrite it
+    }
+    {
+        // h's constant columns: 1 (the bias gradient), then zeros
+        const float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {};
+        store_row8(s.h, t, kAH, kHG, one);
+        store_row8(s.h, t, kAH + 8, kHG, zero);
+    }
+    tc_begin(&s.mbar, &s.tmem, kBwdCols);
+    const uint32_t tmem = s.tmem;
+    const uint32_t lane_base = (uint32_t)((t >> 5) * 32) << 16;
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+    const long long tiles = ceil_div(n, (long long)kM);
+    AnchorIn in;
+    if ((long long)blockIdx.x < tiles) load_anchor(in, A, pos, level, n, ld, (long long)blockIdx.x * kM + t);
+    for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const long long i = tile * kM + t;
+        const bool valid = i < n;
+        const bool M = stage_x(s.x, t, in, v);
+        float L[3], off[3 * kAK];
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) L[c] = in.L[c];
+        if (tile + gridDim.x < tiles) load_anchor(in, A, pos, level, n, ld, (tile + gridDim.x) * kM + t);
+        // the offsets arrive while the two layers run
+        #pragma unroll
+        for (int c = 0; c < 3 * kAK; ++c) off[c] = M ? A[(kPlaneOffs + c) * ld + i] : 0.0f;
+        ok = tc_sync(ok);
+        if (ok && t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            issue_layer1(tmem, s.x, s.wt);
+            mma_commit(&s.mbar);
+        }
+        if (ok) ok = tc_wait(&s.mbar, phase, polls);
+        uint32_t on[2] = {0u, 0u};  // ReLU mask of the row's 64 pre-activations
+        if (ok) {
+            float hv[kAH];
+            tmem_row64(tmem, 0, hv);
+            #pragma unroll
+            for (int c = 0; c < kAH; ++c) {
+                const float pre = hv[c] + s.wt.b1[c];
+                const bool act = M && pre > 0.0f;
+                on[c >> 5] |= act ? 1u << (c & 31) : 0u;
+                hv[c] = act ? pre : 0.0f;
+            }
+            #pragma unroll
+            for (int c0 = 0; c0 < kAH; c0 += 8) store_row8(s.h, t, c0, kHG, hv + c0);
+        }
+        ok = tc_sync(ok);
+        if (ok && t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            issue_layer2(tmem + kColZ, s.h, kHG, s.wt);
+            mma_commit(&s.mbar);
+        }
+        // the incoming gradients of an active anchor's Gaussians, one slot ahead of their use
+        // (the first while layer 2 runs)
+        float gbuf[2][14];
+        auto load_g = [&](int k, float *g) {
+            #pragma unroll
+            for (int j = 0; j < 14; ++j) g[j] = M ? GG[j * gld + k * ld + i] : 0.0f;
+        };
+        load_g(0, gbuf[0]);
+        if (ok) ok = tc_wait(&s.mbar, phase, polls);
+        if (ok) {
+            // dL/dz of the kept Gaussians; the anchor's own offset and log-scale gradients
+            float gL[3] = {0.0f, 0.0f, 0.0f};
+            #pragma unroll
+            for (int k = 0; k < kAK; ++k) {
+                if (k + 1 < kAK) load_g(k + 1, gbuf[(k + 1) & 1]);
+                const float *g = gbuf[k & 1];
+                float z[16], dz[16];
+                read_slot(tmem, kColZ, s.wt, k, z);
                 #pragma unroll
-                for (int j = 0; j < 14; ++j) {
-                    const int o = 14 * k + j;
-                    float a = s.w[kAB2 + o];
-                    #pragma unroll 16
-                    for (int c = 0; c < kAH; ++c) a += s.w[kAW2 + o * kAH + c] * s.hs[c][t];
-                    z[j] = a;
-                }
+                for (int j = 0; j < 16; ++j) dz[j] = 0.0f;
+                float gO[3] = {0.0f, 0.0f, 0.0f};
                 const float a = tanhf(z[3]);
-                if (a > 0.0f) {
-                    const long long col = k * ld + i;
-                    float g[14];
-                    #pragma unroll
-                    for (int j = 0; j < 14; ++j) g[j] = GG[j * gld + col];
+                if (M && a > 0.0f) {
                     #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const float l = expf(L[c]);
-                        const float O = A[(kPlaneOffs + 3 * k + c) * ld + i] + z[11 + c];
+                        const float O = off[3 * k + c] + z[11 + c];
                         dz[11 + c] = g[c] * l;
                         gO[c] = g[c] * l;
                         gL[c] += g[c] * O * l + g[3 + c];
@@ -251,97 +485,97 @@ __global__ void __launch_bounds__(kBT) k_anchor_decode_bwd(const float *__restri
                     for (int c = 0; c < 4; ++c) dz[4 + c] = g[6 + c];
                     dz[3] = g[10] * (1.0f + a) / a;  // d logit(tanh z) / dz
                 }
+                store_row8(s.dz, t, kSlot * k, kOG, dz);
+                store_row8(s.dz, t, kSlot * k + 8, kOG, dz + 8);
+                if (valid) {
+                    #pragma unroll
+                    for (int c = 0; c < 3; ++c) gA[(kPlaneOffs + 3 * k + c) * ld + i] = gO[c];
+                }
             }
-            #pragma unroll
-            for (int j = 0; j < 14; ++j) s.dz[14 * k + j][t] = dz[j];
             if (valid) {
                 #pragma unroll
-                for (int c = 0; c < 3; ++c) gA[(kPlaneOffs + 3 * k + c) * ld + i] = gO[c];
+                for (int c = 0; c < 3; ++c) gA[(kPlaneLogL + c) * ld + i] = gL[c];
             }
         }
-        if (valid) {
+        ok = tc_sync(ok);
+        if (ok && t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // dh = dz W2 -> columns [0, 64), ten K = 16 steps
             #pragma unroll
-            for (int c = 0; c < 3; ++c) gA[(kPlaneLogL + c) * ld + i] = gL[c];
-        }
-        __syncthreads();
-        // dW2, db2 over the tile's anchors: per row r, 35 broadcast loads of dz and two of h
-        // feed 70 accumulators
-        for (int r = 0; r < kBT; ++r) {
-            const float h0 = s.hs[lane][r], h1 = s.hs[lane + 32][r];
+            for (int kb = 0; kb < kOutP / 16; ++kb)
+                mma_bf16(tmem, smem_desc(smem_addr(s.dz) + kb * 256, 128, kDzK),
+                         smem_desc(smem_addr(s.w2t) + kb * 256, 128, kDzK), idesc_bf16(kM, kAH), kb > 0);
+            // dW2 | db2 += [h | 1]^T dz over the tile's rows, 16 rows per step
             #pragma unroll
-            for (int j = 0; j < kO2; ++j) {
-                const float g = s.dz[kO2 * warp + j][r];
-                aW2[2 * j] += g * h0;
-                aW2[2 * j + 1] += g * h1;
-            }
+            for (int kb = 0; kb < kM / 16; ++kb)
+                mma_bf16(tmem + kColW2, smem_desc_mn(smem_addr(s.h) + kb * 2 * kHK, kHK, 128),
+                         smem_desc_mn(smem_addr(s.dz) + kb * 2 * kDzK, kDzK, 128), idesc_bf16_mn(kM, kOutP),
+                         !first || kb > 0);
+            mma_commit(&s.mbar);
         }
-        #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int o = t + kBT * q;
-            if (o < kAOut) {
-                float a = 0.0f;
-                for (int r = 0; r < kBT; ++r) a += s.dz[o][r];
-                aB2[q] += a;
-            }
-        }
-        // the anchor's dL/dh = W2^T dz through the ReLU
-        float dp[kAH];
-        #pragma unroll
-        for (int c = 0; c < kAH; ++c) dp[c] = 0.0f;
-        for (int o = 0; o < kAOut; ++o) {
-            const float g = s.dz[o][t];
-            const float4 *w4 = reinterpret_cast<const float4 *>(s.w + kAW2 + o * kAH);
+        if (ok) ok = tc_wait(&s.mbar, phase, polls);
+        if (ok) {
+            float d1[kAH];
+            tmem_row64(tmem, 0, d1);
             #pragma unroll
-            for (int c = 0; c < kAH / 4; ++c) {
-                const float4 q = w4[c];
-                dp[4 * c] += q.x * g;
-                dp[4 * c + 1] += q.y * g;
-                dp[4 * c + 2] += q.z * g;
-                dp[4 * c + 3] += q.w * g;
-            }
+            for (int c = 0; c < kAH; ++c) d1[c] = (on[c >> 5] >> (c & 31)) & 1u ? d1[c] : 0.0f;
+            #pragma unroll
+            for (int c0 = 0; c0 < kAH; c0 += 8) store_row8(s.dp, t, c0, kAH / 8, d1 + c0);
         }
-        #pragma unroll
-        for (int c = 0; c < kAH; ++c) dp[c] = s.hs[c][t] > 0.0f ? dp[c] : 0.0f;
-        __syncthreads();  // every thread has read the activations
-        #pragma unroll
-        for (int c = 0; c < kAH; ++c) s.hs[c][t] = dp[c];
-        __syncthreads();
-        // dW1, db1 over the tile's anchors; the anchor's feature gradient
-        #pragma unroll
-        for (int j = 0; j < kE1; ++j) {
-            const int e = t + kBT * j, o = e / kAIn, c = e % kAIn;
-            float a = 0.0f;
-            #pragma unroll 8
-            for (int r = 0; r < kBT; ++r) a += s.hs[o][r] * s.xs[c][r];
-            aW1[j] += a;
+        ok = tc_sync(ok);
+        if (ok && t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // df = dp W1 over the feature inputs -> columns [64, 96), four K = 16 steps
+            #pragma unroll
+            for (int kb = 0; kb < kAH / 16; ++kb)
+                mma_bf16(tmem + kColDF, smem_desc(smem_addr(s.dp) + kb * 256, 128, kDpK),
+                         smem_desc(smem_addr(s.w1t) + kb * 256, 128, kDpK), idesc_bf16(kM, kAF), kb > 0);
+            // dW1 | db1 += dp^T [x | 1] over the tile's rows
+            #pragma unroll
+            for (int kb = 0; kb < kM / 16; ++kb)
+                mma_bf16(tmem + kColW1, smem_desc_mn(smem_addr(s.dp) + kb * 2 * kDpK, kDpK, 128),
+                         smem_desc_mn(smem_addr(s.x) + kb * 2 * kXK, kXK, 128), idesc_bf16_mn(kM, kXC),
+                         !first || kb > 0);
+            mma_commit(&s.mbar);
         }
-        if (t < kAH) {
-            float a = 0.0f;
-            for (int r = 0; r < kBT; ++r) a += s.hs[t][r];
-            aB1 += a;
-        }
-        if (valid) {
-            for (int c = 0; c < kAF; ++c) {
-                float a = 0.0f;
+        if (ok) ok = tc_wait(&s.mbar, phase, polls);
+        first = false;
+        if (ok) {
+            float df[kAF];
+            tmem_ld16(tmem + lane_base + kColDF, df);
+            tmem_ld16(tmem + lane_base + kColDF + 16, df + 16);
+            if (valid) {
                 #pragma unroll
-                for (int o = 0; o < kAH; ++o) a += s.w[kAW1 + o * kAIn + c] * dp[o];
-                gA[c * ld + i] = a;
+                for (int c = 0; c < kAF; ++c) gA[c * ld + i] = df[c];
             }
         }
-        __syncthreads();  // the tile's shared arrays are rewritten next
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        ok = __syncthreads_and(ok);
     }
-    #pragma unroll
-    for (int j = 0; j < kO2; ++j) {
-        const int o = kO2 * warp + j;
-        atomicAdd(&gw[kAW2 + o * kAH + lane], aW2[2 * j]);
-        atomicAdd(&gw[kAW2 + o * kAH + lane + 32], aW2[2 * j + 1]);
+    if (ok && !first) {
+        // the weight sums: TMEM lane c < 64 holds W2[.][c] (lane 64: b2) and W1[c][.] (column 36: b1)
+        #pragma unroll
+        for (int k = 0; k < kAK; ++k) {
+            float u[16];
+            tmem_ld16(tmem + lane_base + kColW2 + kSlot * k, u);
+            if (t < kAH) {
+                #pragma unroll
+                for (int j = 0; j < 14; ++j) atomicAdd(&gw[kAW2 + (14 * k + j) * kAH + t], u[j]);
+            } else if (t == kAH) {
+                #pragma unroll
+                for (int j = 0; j < 14; ++j) atomicAdd(&gw[kAB2 + 14 * k + j], u[j]);
+            }
+        }
+        float u[kXC];
+        #pragma unroll
+        for (int c = 0; c < kXC; c += 16) tmem_ld16(tmem + lane_base + kColW1 + c, u + c);
+        if (t < kAH) {
+            #pragma unroll
+            for (int c = 0; c < kAIn; ++c) atomicAdd(&gw[kAW1 + t * kAIn + c], u[c]);
+            atomicAdd(&gw[kAB1 + t], u[kAIn]);
+        }
     }
-    #pragma unroll
-    for (int j = 0; j < kE1; ++j) atomicAdd(&gw[kAW1 + t + kBT * j], aW1[j]);
-    #pragma unroll
-    for (int q = 0; q < 2; ++q)
-        if (t + kBT * q < kAOut) atomicAdd(&gw[kAB2 + t + kBT * q], aB2[q]);
-    if (t < kAH) atomicAdd(&gw[kAB1 + t], aB1);
+    tc_end(&s.mbar, tmem, kBwdCols, ok, phase, status);
 }
 
 __global__ void k_adam_flat(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
@@ -370,27 +604,40 @@ int sm_count_anchor() {
 }  // namespace
 
 cudaError_t launch_anchor_decode(const float *A, const float *pos, const int *level, long long n, long long ld,
-                                 const float *w, const AnchorView &v, float *G, long long gld, cudaStream_t s) {
+                                 const float *w, const AnchorView &v, float *G, long long gld, int *status,
+                                 long long max_polls, cudaStream_t s) {
     if (ld <= 0) return cudaSuccess;
-    k_anchor_decode<<<(unsigned)ceil_div(ld, 256ll), 256, 0, s>>>(A, pos, level, n, ld, w, v, G, gld);
+    const size_t smem = sizeof(DecSmem) + 1024;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_anchor_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    // two CTAs per SM (2 x 256 TMEM columns)
+    const long long grid = std::min<long long>(ceil_div(ld, (long long)kM), 2ll * sm_count_anchor());
+    k_anchor_decode<<<(unsigned)grid, kM, smem, s>>>(A, pos, level, n, ld, w, v, G, gld, status,
+                                                     max_polls < 0 ? kSpin : max_polls);
     return cudaGetLastError();
 }
 
 cudaError_t launch_anchor_decode_bwd(const float *A, const float *pos, const int *level, long long n, long long ld,
                                      const float *w, const AnchorView &v, const float *GG, long long gld, float *gA,
-                                     float *gw, cudaStream_t s) {
+                                     float *gw, int *status, long long max_polls, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(gA, 0, sizeof(float) * GS_ANCHOR_PLANES * (size_t)ld, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(gw, 0, sizeof(float) * kANW, s);
     if (e != cudaSuccess || n <= 0) return e;
-    const size_t smem = sizeof(BwdSmem);
+    const size_t smem = sizeof(BwdSmem) + 1024;
     static bool attr = false;
     if (!attr) {
         e = cudaFuncSetAttribute(k_anchor_decode_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const long long grid = std::min<long long>(ceil_div(n, (long long)kBT), (long long)sm_count_anchor());
-    k_anchor_decode_bwd<<<(unsigned)grid, kBT, smem, s>>>(A, pos, level, n, ld, w, v, GG, gld, gA, gw);
+    // one CTA per SM (512 TMEM columns)
+    const long long grid = std::min<long long>(ceil_div(n, (long long)kM), (long long)sm_count_anchor());
+    k_anchor_decode_bwd<<<(unsigned)grid, kM, smem, s>>>(A, pos, level, n, ld, w, v, GG, gld, gA, gw, status,
+                                                         max_polls < 0 ? kSpin : max_polls);
     return cudaGetLastError();
 }
 

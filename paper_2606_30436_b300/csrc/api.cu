@@ -748,19 +748,21 @@ gs_status check_decoded(const gs_anchor_params *a, const gs_params *out) {
 }  // namespace
 
 GS_API gs_status gs_anchor_decode(const gs_anchor_params *a, const float *weights, const float cam_centre[3],
-                                  const float *max_dist, int32_t levels, const gs_params *out, gs_stream stream) {
+                                  const float *max_dist, int32_t levels, const gs_params *out, int32_t *status,
+                                  int64_t max_polls, gs_stream stream) {
     AnchorView v;
     gs_status st = anchor_view(a, cam_centre, max_dist, levels, v);
     if (st == GS_OK) st = check_decoded(a, out);
     if (st != GS_OK) return st;
     if (!weights || !aligned16(weights)) return GS_ERR_INVALID;
     return cuda_status(launch_anchor_decode(a->data, a->pos, a->level, a->n, a->ld, weights, v, out->data, out->ld,
-                                            (cudaStream_t)stream));
+                                            status, max_polls, (cudaStream_t)stream));
 }
 
 GS_API gs_status gs_anchor_decode_bwd(const gs_anchor_params *a, const float *weights, const float cam_centre[3],
                                       const float *max_dist, int32_t levels, const gs_params *grad_out,
-                                      float *grad_anchor, float *grad_weights, gs_stream stream) {
+                                      float *grad_anchor, float *grad_weights, int32_t *status, int64_t max_polls,
+                                      gs_stream stream) {
     AnchorView v;
     gs_status st = anchor_view(a, cam_centre, max_dist, levels, v);
     if (st == GS_OK) st = check_decoded(a, grad_out);
@@ -769,7 +771,8 @@ GS_API gs_status gs_anchor_decode_bwd(const gs_anchor_params *a, const float *we
         !aligned16(grad_weights))
         return GS_ERR_INVALID;
     return cuda_status(launch_anchor_decode_bwd(a->data, a->pos, a->level, a->n, a->ld, weights, v, grad_out->data,
-                                                grad_out->ld, grad_anchor, grad_weights, (cudaStream_t)stream));
+                                                grad_out->ld, grad_anchor, grad_weights, status, max_polls,
+                                                (cudaStream_t)stream));
 }
 
 GS_API gs_status gs_adam_flat(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,

@@ -133,10 +133,11 @@ struct AnchorView {
     int levels;
 };
 cudaError_t launch_anchor_decode(const float *A, const float *pos, const int *level, long long n, long long ld,
-                                 const float *w, const AnchorView &v, float *G, long long gld, cudaStream_t s);
+                                 const float *w, const AnchorView &v, float *G, long long gld, int *status,
+                                 long long max_polls, cudaStream_t s);
 cudaError_t launch_anchor_decode_bwd(const float *A, const float *pos, const int *level, long long n, long long ld,
                                      const float *w, const AnchorView &v, const float *GG, long long gld, float *gA,
-                                     float *gw, cudaStream_t s);
+                                     float *gw, int *status, long long max_polls, cudaStream_t s);
 cudaError_t launch_adam_flat(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
                              float eps, long long step, cudaStream_t s);
 

@@ -62,16 +62,17 @@ class Lifecycle:
     """Statistics, decisions and actions of one chunk at a time."""
 
     def __init__(self, mode="plain", tau_d=5.0, tau_p=0.99, split_log_scale=-2.5, split_factor=1.6,
-                 predictor: Predictor = None, collect=False, seed=0, margin=0.1, n_initial=0):
+                 predictor: Predictor = None, collect=False, seed=0, margin=0.1, n_initial=None):
         assert mode in ("plain", "learned")
         assert mode == "plain" or predictor is not None
         self.mode, self.tau_d, self.tau_p = mode, tau_d, tau_p
         self.split_log_scale, self.split_factor = split_log_scale, split_factor
         self.predictor, self.collect = predictor, collect
         self.margin = margin  # learned: the plain bit where |p - 1/2| < margin
-        # identity of every Gaussian of the current map (host), carried through the actions
-        self.ids = np.arange(n_initial, dtype=np.int64)
-        self.next_id = n_initial
+        # identity of every Gaussian of the current map (host), carried through the actions; numbered
+        # 0 .. n - 1 at the first chunk unless n_initial says otherwise
+        self.ids = None if n_initial is None else np.arange(n_initial, dtype=np.int64)
+        self.next_id = 0 if n_initial is None else n_initial
         self.samples = []   # per chunk, with collect=True: (feat, n, densify, prune, active, ids)
         self.history = []   # per chunk: n before / after, bits set, agreement with the plain criterion
         self.gen = torch.Generator(device="cuda").manual_seed(int(seed))
@@ -83,6 +84,9 @@ class Lifecycle:
         """Zeroes the accumulators before the chunk's first iteration."""
         assert step.buf.stats_acc is not None, "the mapping step must accumulate statistics"
         step.buf.stats_acc.zero_()
+        if self.ids is None:
+            self.ids, self.next_id = np.arange(step.model.n, dtype=np.int64), step.model.n
+        assert len(self.ids) == step.model.n, "the map changed outside the lifecycle's actions"
         ld = step.model.ld
         if self.ring is None or self.ring.shape[1] != ld:
             self.ring = torch.zeros(gs.MLP_RING, ld, dtype=torch.float32, device=step.model.data.device)

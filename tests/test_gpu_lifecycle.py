@@ -366,6 +366,6 @@ def test_lifecycle_chunks_plain_and_learned():
         assert len(lc.history) == 2
         if mode == "plain":
             assert len(lc.samples) == 2 and any(h["densify"] + h["prune"] > 0 for h in lc.history)
-            pred.train(lc.samples, epochs=20)
+            pred.train(lifecycle.future_labels(lc.samples, DEV), epochs=20)
         else:
             assert all("prune_recall" in h for h in lc.history)

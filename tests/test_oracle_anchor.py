@@ -256,3 +256,27 @@ def test_hidden_inputs_and_pre_activations():
     assert np.array_equal(xb, x)
     assert np.allclose(preb, _bf16(x) @ _bf16(W1m).T + b1, atol=1e-12)
     assert np.abs(preb - pre).max() > 1e-4  # the rounding is visible
+
+
+def test_backward_row_terms_assemble_the_gradients():
+    """The per-anchor dL/dz and dL/dpre the backward returns assemble its
+    weight and feature gradients as matrix products: dW2 = dz^T relu(pre),
+    db2 = sum dz, dW1 = dpre^T x, db1 = sum dpre, dfeat = dpre W1 (bf16 mode:
+    with the rounded operands), and dpre vanishes where pre <= 0."""
+    A = _anchors(9, 41)
+    w = _weights(42)
+    cc = np.array([0.1, 0.0, -0.2])
+    rng = np.random.default_rng(43)
+    g = rng.normal(size=(K * 9, 14))
+    for bf16 in (False, True):
+        gf, gl, go, gw, dz, dp = orc.anchor_decode_backward(A, w, cc, BANDS, g, bf16=bf16, rows=True)
+        x, pre = orc.anchor_hidden(A, w, cc, bf16=bf16)
+        r = _bf16 if bf16 else (lambda v: v)
+        h = r(np.maximum(pre, 0.0))
+        W1m = r(w[W1:B1].reshape(H, IN))
+        assert np.abs(dz).max() > 0 and np.all(dp[pre <= 0] == 0)
+        assert np.allclose(gw[W2:B2].reshape(14 * K, H), dz.T @ h, atol=1e-11)
+        assert np.allclose(gw[B2:], dz.sum(0), atol=1e-11)
+        assert np.allclose(gw[W1:B1].reshape(H, IN), dp.T @ r(x), atol=1e-11)
+        assert np.allclose(gw[B1:B1 + H], dp.sum(0), atol=1e-11)
+        assert np.allclose(gf, dp @ W1m[:, :F], atol=1e-11)

@@ -33,15 +33,15 @@ static_assert(kANW == GS_ANCHOR_WEIGHTS, "decoder weight count");
 static_assert(kAIn % 4 == 0 && kAH % 4 == 0 && kAW2 % 4 == 0, "weight rows on 16-byte boundaries");
 constexpr int kPlaneLogL = kAF, kPlaneOffs = kAF + 3;
 static_assert(kPlaneOffs + 3 * kAK == GS_ANCHOR_PLANES, "anchor planes");
-constexpr float kY00 = 0.28209479177387814f;
+constexpr float kY00 = 0.28209479177387814f, kInvY00 = 1.0f / kY00;
 constexpr float kDeadLogit = -30.0f;
 
-__device__ __forceinline__ float sigmoidf(float z) { return 1.0f / (1.0f + expf(-z)); }
+// sigmoid and log(sigmoid) from the hardware exp2 / log2 approximations (__expf, __logf: a few
+// units in the last place, well inside the decoded parameters' FP32 tolerance); the limits hold
+// for either sign (1 / inf = 0; log(1 + e^-|z|) never overflows)
+__device__ __forceinline__ float sigmoidf(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 
-// log(sigmoid(z)) without overflow for either sign
-__device__ __forceinline__ float log_sigmoidf(float z) {
-    return z >= 0.0f ? -log1pf(expf(-z)) : z - log1pf(expf(z));
-}
+__device__ __forceinline__ float log_sigmoidf(float z) { return fminf(z, 0.0f) - __logf(1.0f + __expf(-fabsf(z))); }
 
 __device__ __forceinline__ bool band_active(const AnchorView &v, int l, float d) {
     return l >= 0 && l < v.levels && d >= v.lo[l] && d < v.hi[l];
@@ -65,19 +65,29 @@ __device__ __forceinline__ void write_dead(float *__restrict__ G, long long gld,
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core decoder.  A tile is 128 anchors = the M of one tcgen05.mma;
-// thread t of the CTA owns anchor row t (TMEM lane t).  Operands are BF16 in
-// shared memory (K-major, no swizzle: 8x8 core matrices of 128 bytes), sums
-// FP32 in TMEM; the biases are added in FP32 when a row is read back.  The
-// 140 outputs sit in 16-column slots (Gaussian k at columns 16 k .. 16 k + 13,
-// two zero columns), so one 16-column TMEM load holds one Gaussian.
+// Tensor-core decoder.  A tile is 128 anchors = the M of one tcgen05.mma.
+// Two threads own each anchor row r (threads r and r + 128, i.e. warps w and
+// w + 4, which read the same TMEM lanes 32 (w % 4) ..): each takes half of
+// the row's columns or Gaussian slots in every per-row phase.  Operands are
+// BF16 in shared memory (K-major, no swizzle: 8x8 core matrices of 128
+// bytes), sums FP32 in TMEM; the biases are added in FP32 when a row is read
+// back.  The 140 outputs sit in 16-column slots (Gaussian k at columns 16 k ..
+// 16 k + 13, two zero columns), so one 16-column TMEM load holds one
+// Gaussian.  Opacity: a = tanh(z) > 0 iff z > 0, and logit(tanh z) =
+// log(expm1(2 z) / 2).
 // ---------------------------------------------------------------------------
 constexpr int kM = 128;                   // anchors per tile
+constexpr int kThreads = 2 * kM;          // two threads per anchor row
+constexpr int kHS = kAK / 2, kHF = kAF / 2, kHH = kAH / 2;  // slots, features, hidden units per half
 constexpr int kSlot = 16, kOutP = kSlot * kAK;  // padded outputs (160)
 constexpr int kXC = 48, kXG = kXC / 8;    // x: 36 inputs, the constant 1 (column 36), zeros
 constexpr int kHC = 80, kHG = kHC / 8;    // backward h: 64 activations, the constant 1 (column 64), zeros
 constexpr int kOG = kOutP / 8;            // core matrices along the padded outputs
-static_assert(kAIn < kXC && kOutP <= 256 && kOutP % 16 == 0, "tile shapes");
+static_assert(kAIn < kXC && kOutP <= 256 && kOutP % 16 == 0 && 2 * kHS == kAK && kHF == 16 && kHH == 32,
+              "tile shapes");
+
+// TMEM lane base of the calling warp (warps w and w + 4 share lanes 32 (w % 4) ..).
+__device__ __forceinline__ uint32_t lane_base() { return (uint32_t)(((threadIdx.x >> 5) & 3) * 32) << 16; }
 
 struct DecWeights {
     alignas(128) __nv_bfloat16 w1[kAH * kXC];    // B of layer 1: [n = o][k = c], c >= 36 zero
@@ -95,11 +105,11 @@ __device__ __forceinline__ void load8(const float *__restrict__ src, bool lo, bo
 }
 
 // The BF16 operand images of W1 and W2 and the FP32 biases, from 16-byte loads (every row of
-// W1 (36 floats) and W2 (64) starts on a 16-byte boundary; blockDim.x == kM).
+// W1 (36 floats) and W2 (64) starts on a 16-byte boundary).
 __device__ void stage_weights(DecWeights &s, const float *__restrict__ w) {
     #pragma unroll
-    for (int r = 0; r < (kAH * kXG + kM - 1) / kM; ++r) {
-        const int u = threadIdx.x + kM * r;
+    for (int r = 0; r < (kAH * kXG + kThreads - 1) / kThreads; ++r) {
+        const int u = threadIdx.x + kThreads * r;
         if (u < kAH * kXG) {
             const int o = u / kXG, c0 = 8 * (u % kXG);
             float v[8];
@@ -107,16 +117,17 @@ __device__ void stage_weights(DecWeights &s, const float *__restrict__ w) {
             store_row8(s.w1, o, c0, kXG, v);
         }
     }
+    static_assert(kOutP * (kAH / 8) % kThreads == 0, "W2 chunks per thread");
     #pragma unroll
-    for (int r = 0; r < kOutP * (kAH / 8) / kM; ++r) {
-        const int u = threadIdx.x + kM * r;
+    for (int r = 0; r < kOutP * (kAH / 8) / kThreads; ++r) {
+        const int u = threadIdx.x + kThreads * r;
         const int q = u / (kAH / 8), c0 = 8 * (u % (kAH / 8)), k = q / kSlot, j = q % kSlot;
         float v[8];
         load8(w + kAW2 + (14 * k + j) * kAH + c0, j < 14, j < 14, v);
         store_row8(s.w2, q, c0, kAH / 8, v);
     }
-    for (int i = threadIdx.x; i < kAH; i += blockDim.x) s.b1[i] = w[kAB1 + i];
-    for (int i = threadIdx.x; i < kOutP; i += blockDim.x) {
+    for (int i = threadIdx.x; i < kAH; i += kThreads) s.b1[i] = w[kAB1 + i];
+    for (int i = threadIdx.x; i < kOutP; i += kThreads) {
         const int k = i / kSlot, j = i % kSlot;
         s.b2[i] = j < 14 ? w[kAB2 + 14 * k + j] : 0.0f;
     }
@@ -145,7 +156,7 @@ __device__ void tc_end(uint64_t *mbar, uint32_t tmem, uint32_t cols, bool ok, ui
     tmem_free(tmem, cols);
 }
 
-// Commit the MMAs issued so far by thread 0 and wait for them (warp-uniform result).
+// Wait for the MMAs thread 0 committed (warp-uniform result).
 __device__ __forceinline__ bool tc_wait(uint64_t *mbar, uint32_t &phase, long long polls) {
     const bool ok = __all_sync(0xffffffffu, mbar_wait(mbar, phase, polls));
     phase ^= 1u;
@@ -160,17 +171,19 @@ __device__ __forceinline__ bool tc_sync(bool ok) {
     return __syncthreads_and(ok);
 }
 
-// The loads of one anchor's inputs (issued a tile ahead).
+// This half's loads of one anchor's inputs (issued a tile ahead): its 16 features, the
+// position, the log-scales and the level.
 struct AnchorIn {
-    float f[kAF], p[3], L[3];
+    float f[kHF], p[3], L[3];
     int lv;
 };
 
 __device__ __forceinline__ void load_anchor(AnchorIn &in, const float *__restrict__ A, const float *__restrict__ pos,
-                                            const int *__restrict__ level, long long n, long long ld, long long i) {
+                                            const int *__restrict__ level, long long n, long long ld, long long i,
+                                            int half) {
     const bool valid = i < n;
     #pragma unroll
-    for (int c = 0; c < kAF; ++c) in.f[c] = valid ? A[c * ld + i] : 0.0f;
+    for (int c = 0; c < kHF; ++c) in.f[c] = valid ? A[(kHF * half + c) * ld + i] : 0.0f;
     #pragma unroll
     for (int c = 0; c < 3; ++c) {
         in.p[c] = valid ? pos[c * ld + i] : 0.0f;
@@ -179,28 +192,38 @@ __device__ __forceinline__ void load_anchor(AnchorIn &in, const float *__restric
     in.lv = valid ? level[i] : -1;
 }
 
-// The tile row of x as the tensor core reads it: (feature, direction, log(1 + d)) of an
-// active anchor (zeros otherwise), the constant 1, zeros.  Returns whether the anchor is active.
-__device__ __forceinline__ bool stage_x(__nv_bfloat16 *xs, int row, const AnchorIn &in, const AnchorView &v) {
+// This half's columns of the tile row of x as the tensor core reads it: (feature,
+// direction, log(1 + d)) of an active anchor (zeros otherwise), the constant 1, zeros.
+// Half 0 writes columns 0-15, half 1 columns 16-47.  Returns whether the anchor is active.
+__device__ __forceinline__ bool stage_x(__nv_bfloat16 *xs, int row, int half, const AnchorIn &in,
+                                        const AnchorView &v) {
     const float dx = in.p[0] - v.c[0], dy = in.p[1] - v.c[1], dz = in.p[2] - v.c[2];
     const float d = sqrtf(dx * dx + dy * dy + dz * dz);
     const bool M = band_active(v, in.lv, d);
-    float x[kXC];
+    float x[8];
     #pragma unroll
-    for (int c = 0; c < kAF; ++c) x[c] = M ? in.f[c] : 0.0f;
-    x[kAF] = M ? dx / d : 0.0f;
-    x[kAF + 1] = M ? dy / d : 0.0f;
-    x[kAF + 2] = M ? dz / d : 0.0f;
-    x[kAF + 3] = M ? log1pf(d) : 0.0f;
-    x[kAIn] = 1.0f;
-    #pragma unroll
-    for (int c = kAIn + 1; c < kXC; ++c) x[c] = 0.0f;
-    #pragma unroll
-    for (int c0 = 0; c0 < kXC; c0 += 8) store_row8(xs, row, c0, kXG, x + c0);
+    for (int c0 = 0; c0 < kHF; c0 += 8) {
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = M ? in.f[c0 + j] : 0.0f;
+        store_row8(xs, row, kHF * half + c0, kXG, x);
+    }
+    if (half) {
+        const float r = 1.0f / d;
+        x[0] = M ? dx * r : 0.0f;
+        x[1] = M ? dy * r : 0.0f;
+        x[2] = M ? dz * r : 0.0f;
+        x[3] = M ? log1pf(d) : 0.0f;
+        x[4] = 1.0f;
+        x[5] = x[6] = x[7] = 0.0f;
+        store_row8(xs, row, kAF, kXG, x);
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = 0.0f;
+        store_row8(xs, row, kAF + 8, kXG, x);
+    }
     return M;
 }
 
-// Layer 1 into TMEM columns [col, col + 64): D = X W1^T, three K = 16 steps.
+// Layer 1: D = X W1^T, three K = 16 steps.
 __device__ __forceinline__ void issue_layer1(uint32_t tmem, const __nv_bfloat16 *xs, const DecWeights &wt) {
     #pragma unroll
     for (int kb = 0; kb < kXC / 16; ++kb)
@@ -216,11 +239,20 @@ __device__ __forceinline__ void issue_layer2(uint32_t tmem, const __nv_bfloat16 
                  smem_desc(smem_addr(wt.w2) + kb * 256, 128, (kAH / 8) * 128), idesc_bf16(kM, kOutP), kb > 0);
 }
 
-// Slot k's 14 outputs (plus two zero columns) of this thread's row, biases added.
-__device__ __forceinline__ void read_slot(uint32_t tmem, int col, const DecWeights &wt, int k, float *z) {
-    tmem_ld16(tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16) + (uint32_t)(col + kSlot * k), z);
+// Slot k's 14 outputs (plus two zero columns) of this thread's row, biases added; taddr =
+// the TMEM base + this warp's lane base + the outputs' first column.
+__device__ __forceinline__ void read_slot(uint32_t taddr, const DecWeights &wt, int k, float *z) {
+    tmem_ld16(taddr + (uint32_t)(kSlot * k), z);
     #pragma unroll
     for (int j = 0; j < 14; ++j) z[j] += wt.b2[kSlot * k + j];
+}
+
+// The row's hidden pre-activations of this half (columns 32 half .. + 31), bias added.
+__device__ __forceinline__ void read_hidden(uint32_t taddr, const DecWeights &wt, int half, float *pre) {
+    tmem_ld16(taddr + (uint32_t)(kHH * half), pre);
+    tmem_ld16(taddr + (uint32_t)(kHH * half + 16), pre + 16);
+    #pragma unroll
+    for (int c = 0; c < kHH; ++c) pre[c] += wt.b1[kHH * half + c];
 }
 
 struct DecSmem {
@@ -235,33 +267,36 @@ constexpr int kDecZ = 64;
 static_assert(kDecZ + kOutP <= (int)kDecCols, "decode TMEM columns");
 static_assert(2 * (sizeof(DecSmem) + 1024) <= 228 * 1024, "two decode CTAs per SM");
 
-__global__ void __launch_bounds__(kM, 2) k_anchor_decode(const float *__restrict__ A, const float *__restrict__ pos,
-                                                          const int *__restrict__ level, long long n, long long ld,
-                                                          const float *__restrict__ w,
-                                                          const __grid_constant__ AnchorView v,
-                                                          float *__restrict__ G, long long gld,
-                                                          int *__restrict__ status, long long polls) {
+__global__ void __launch_bounds__(kThreads, 2) k_anchor_decode(const float *__restrict__ A,
+                                                                const float *__restrict__ pos,
+                                                                const int *__restrict__ level, long long n,
+                                                                long long ld, const float *__restrict__ w,
+                                                                const __grid_constant__ AnchorView v,
+                                                                float *__restrict__ G, long long gld,
+                                                                int *__restrict__ status, long long polls) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     DecSmem &s = *reinterpret_cast<DecSmem *>(smem_raw);
     stage_weights(s.wt, w);
     tc_begin(&s.mbar, &s.tmem, kDecCols);
-    const int t = threadIdx.x;
-    const uint32_t tmem = s.tmem;
+    const int t = threadIdx.x, row = t & (kM - 1), half = t >> 7;
+    const uint32_t tmem = s.tmem, lb = lane_base();
     uint32_t phase = 0;
     bool ok = true;
     const long long tiles = ceil_div(ld, (long long)kM);
     AnchorIn in;
-    if ((long long)blockIdx.x < tiles) load_anchor(in, A, pos, level, n, ld, (long long)blockIdx.x * kM + t);
+    if ((long long)blockIdx.x < tiles) load_anchor(in, A, pos, level, n, ld, (long long)blockIdx.x * kM + row, half);
     for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const long long i = tile * kM + t;
-        const bool M = stage_x(s.x, t, in, v);
-        float p[3], L[3], off[3 * kAK];
+        const long long i = tile * kM + row;
+        const bool M = stage_x(s.x, row, half, in, v);
+        float p[3], L[3], l[3], off[3 * kHS];
         #pragma unroll
         for (int c = 0; c < 3; ++c) { p[c] = in.p[c]; L[c] = in.L[c]; }
-        if (tile + gridDim.x < tiles) load_anchor(in, A, pos, level, n, ld, (tile + gridDim.x) * kM + t);
-        // the offsets arrive while the two layers run
+        if (tile + gridDim.x < tiles) load_anchor(in, A, pos, level, n, ld, (tile + gridDim.x) * kM + row, half);
+        // this half's offsets arrive while the two layers run
         #pragma unroll
-        for (int c = 0; c < 3 * kAK; ++c) off[c] = M ? A[(kPlaneOffs + c) * ld + i] : 0.0f;
+        for (int c = 0; c < 3 * kHS; ++c) off[c] = M ? A[(kPlaneOffs + 3 * kHS * half + c) * ld + i] : 0.0f;
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) l[c] = expf(L[c]);
         ok = tc_sync(ok);
         if (ok && t == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -270,12 +305,12 @@ __global__ void __launch_bounds__(kM, 2) k_anchor_decode(const float *__restrict
         }
         if (ok) ok = tc_wait(&s.mbar, phase, polls);
         if (ok) {
-            float hv[kAH];
-            tmem_row64(tmem, 0, hv);
+            float hv[kHH];
+            read_hidden(tmem + lb, s.wt, half, hv);
             #pragma unroll
-            for (int c = 0; c < kAH; ++c) hv[c] = fmaxf(hv[c] + s.wt.b1[c], 0.0f);
+            for (int c = 0; c < kHH; ++c) hv[c] = fmaxf(hv[c], 0.0f);
             #pragma unroll
-            for (int c0 = 0; c0 < kAH; c0 += 8) store_row8(s.h, t, c0, kAH / 8, hv + c0);
+            for (int c0 = 0; c0 < kHH; c0 += 8) store_row8(s.h, row, kHH * half + c0, kAH / 8, hv + c0);
         }
         ok = tc_sync(ok);
         if (ok && t == 0) {
@@ -286,28 +321,27 @@ __global__ void __launch_bounds__(kM, 2) k_anchor_decode(const float *__restrict
         if (ok) ok = tc_wait(&s.mbar, phase, polls);
         if (ok) {
             #pragma unroll
-            for (int k = 0; k < kAK; ++k) {
+            for (int kk = 0; kk < kHS; ++kk) {
+                const int k = kHS * half + kk;
                 float z[16];
-                read_slot(tmem, kDecZ, s.wt, k, z);
+                read_slot(tmem + lb + kDecZ, s.wt, k, z);
                 if (i >= ld) continue;
                 const long long col = k * ld + i;
-                const float a = tanhf(z[3]);
-                if (!M || !(a > 0.0f)) {
+                if (!M || !(z[3] > 0.0f)) {
                     write_dead(G, gld, col, p, L);
                     continue;
                 }
                 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float l = expf(L[c]);
-                    G[c * gld + col] = p[c] + (off[3 * k + c] + z[11 + c]) * l;  // mean
-                    G[(3 + c) * gld + col] = L[c] + log_sigmoidf(z[8 + c]);                          // log(l ds)
-                    G[(11 + c) * gld + col] = (sigmoidf(z[c]) - 0.5f) / kY00;                          // colour
+                    G[c * gld + col] = p[c] + (off[3 * kk + c] + z[11 + c]) * l[c];  // mean
+                    G[(3 + c) * gld + col] = L[c] + log_sigmoidf(z[8 + c]);          // log(l ds)
+                    G[(11 + c) * gld + col] = (sigmoidf(z[c]) - 0.5f) * kInvY00;       // colour
                 }
                 G[6 * gld + col] = 1.0f + z[4];
                 G[7 * gld + col] = z[5];
                 G[8 * gld + col] = z[6];
                 G[9 * gld + col] = z[7];
-                G[10 * gld + col] = logf(a) - log1pf(-a);
+                G[10 * gld + col] = logf(0.5f * expm1f(2.0f * z[3]));  // logit(tanh z)
             }
         }
     }
@@ -335,6 +369,7 @@ struct BwdSmem {
     alignas(128) __nv_bfloat16 w2t[kAH * kOutP];  // B of dh: [n = c][k = 16 k + j] = W2^T
     alignas(128) __nv_bfloat16 w1t[kAF * kAH];    // B of df: [n = feature c][k = o] = W1^T
     DecWeights wt;
+    float gLx[3][kM];  // half 1's share of the log-scale gradients
     uint64_t mbar;
     uint32_t tmem;
 };
@@ -355,71 +390,77 @@ static_assert(offsetof(BwdSmem, dp) + 7 * 2 * kDpK + 15 * kDpK + 128 + 127 < siz
 static_assert(offsetof(BwdSmem, x) + 7 * 2 * kXK + (kXG - 1) * kXK + 128 + 127 < sizeof(BwdSmem), "x read");
 static_assert(sizeof(BwdSmem) + 1024 <= 227 * 1024, "backward shared memory");
 
-__global__ void __launch_bounds__(kM, 1) k_anchor_decode_bwd(const float *__restrict__ A, const float *__restrict__ pos,
-                                                              const int *__restrict__ level, long long n, long long ld,
-                                                              const float *__restrict__ w,
-                                                              const __grid_constant__ AnchorView v,
-                                                              const float *__restrict__ GG, long long gld,
-                                                              float *__restrict__ gA, float *__restrict__ gw,
-                                                              int *__restrict__ status, long long polls) {
+__global__ void __launch_bounds__(kThreads, 1) k_anchor_decode_bwd(const float *__restrict__ A,
+                                                                    const float *__restrict__ pos,
+                                                                    const int *__restrict__ level, long long n,
+                                                                    long long ld, const float *__restrict__ w,
+                                                                    const __grid_constant__ AnchorView v,
+                                                                    const float *__restrict__ GG, long long gld,
+                                                                    float *__restrict__ gA, float *__restrict__ gw,
+                                                                    int *__restrict__ status, long long polls) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     BwdSmem &s = *reinterpret_cast<BwdSmem *>(smem_raw);
     stage_weights(s.wt, w);
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, row = t & (kM - 1), half = t >> 7;
     {
         // the transposed images from FP32 copies of W2 and W1 in the (not yet used) dz and h arrays
         float *w2f = reinterpret_cast<float *>(s.dz), *w1f = reinterpret_cast<float *>(s.h);
         static_assert(sizeof(float) * kAOut * kAH <= sizeof(s.dz) && sizeof(float) * kAH * kAIn <= sizeof(s.h),
                       "weight scratch");
-        for (int u = t; u < kAOut * kAH / 4; u += kM)
+        for (int u = t; u < kAOut * kAH / 4; u += kThreads)
             reinterpret_cast<float4 *>(w2f)[u] = __ldg(reinterpret_cast<const float4 *>(w + kAW2) + u);
-        for (int u = t; u < kAH * kAIn / 4; u += kM)
+        for (int u = t; u < kAH * kAIn / 4; u += kThreads)
             reinterpret_cast<float4 *>(w1f)[u] = __ldg(reinterpret_cast<const float4 *>(w + kAW1) + u);
         __syncthreads();
-        for (int u = t; u < kAH * kOG; u += kM) {
+        for (int u = t; u < kAH * kOG; u += kThreads) {
             const int c = u % kAH, q0 = 8 * (u / kAH);  // a warp reads 32 consecutive columns c
-            float v[8];
+            float vv[8];
             #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
                 const int k = (q0 + jj) / kSlot, j = (q0 + jj) % kSlot;
-                v[jj] = j < 14 ? w2f[(14 * k + j) * kAH + c] : 0.0f;
+                vv[jj] = j < 14 ? w2f[(14 * k + j) * kAH + c] : 0.0f;
             }
-            store_row8(s.w2t, c, q0, kOG, v);
+            store_row8(s.w2t, c, q0, kOG, vv);
         }
-        for (int u = t; u < kAF * (kAH / 8); u += kM) {
+        for (int u = t; u < kAF * (kAH / 8); u += kThreads) {
             const int c = u % kAF, o0 = 8 * (u / kAF);
-            float v[8];
+            float vv[8];
             #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) v[jj] = w1f[(o0 + jj) * kAIn + c];
-            store_row8(s.w1t, c, o0, kAH / 8, v);
+            for (int jj = 0; jj < 8; ++jj) vv[jj] = w1f[(o0 + jj) * kAIn + c];
+            store_row8(s.w1t, c, o0, kAH / 8, vv);
         }
         __syncthreads();  // the scratch is read before h's constant columns overwrite it
-    }
-    {
-        // h's constant columns: 1 (the bias gradient), then zeros
+        // h's constant columns: 1 (the bias gradient; half 0), then zeros (half 1)
         const float one[8] = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, zero[8] = {};
-        store_row8(s.h, t, kAH, kHG, one);
-        store_row8(s.h, t, kAH + 8, kHG, zero);
+        store_row8(s.h, row, kAH + 8 * half, kHG, half ? zero : one);
     }
     tc_begin(&s.mbar, &s.tmem, kBwdCols);
-    const uint32_t tmem = s.tmem;
-    const uint32_t lane_base = (uint32_t)((t >> 5) * 32) << 16;
+    const uint32_t tmem = s.tmem, lb = lane_base();
     uint32_t phase = 0;
     bool ok = true, first = true;
     const long long tiles = ceil_div(n, (long long)kM);
     AnchorIn in;
-    if ((long long)blockIdx.x < tiles) load_anchor(in, A, pos, level, n, ld, (long long)blockIdx.x * kM + t);
+    if ((long long)blockIdx.x < tiles) load_anchor(in, A, pos, level, n, ld, (long long)blockIdx.x * kM + row, half);
     for (long long tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const long long i = tile * kM + t;
+        const long long i = tile * kM + row;
         const bool valid = i < n;
-        const bool M = stage_x(s.x, t, in, v);
-        float L[3], off[3 * kAK];
+        const bool M = stage_x(s.x, row, half, in, v);
+        float l[3], off[3 * kHS];
         #pragma unroll
-        for (int c = 0; c < 3; ++c) L[c] = in.L[c];
-        if (tile + gridDim.x < tiles) load_anchor(in, A, pos, level, n, ld, (tile + gridDim.x) * kM + t);
-        // the offsets arrive while the two layers run
+        for (int c = 0; c < 3; ++c) l[c] = in.L[c];
+        if (tile + gridDim.x < tiles) load_anchor(in, A, pos, level, n, ld, (tile + gridDim.x) * kM + row, half);
+        // this half's offsets and the incoming gradients of its Gaussians arrive while the two
+        // layers run (70 loads in flight per thread)
         #pragma unroll
-        for (int c = 0; c < 3 * kAK; ++c) off[c] = M ? A[(kPlaneOffs + c) * ld + i] : 0.0f;
+        for (int c = 0; c < 3 * kHS; ++c) off[c] = M ? A[(kPlaneOffs + 3 * kHS * half + c) * ld + i] : 0.0f;
+        float gin[kHS][14];
+        #pragma unroll
+        for (int kk = 0; kk < kHS; ++kk) {
+            #pragma unroll
+            for (int j = 0; j < 14; ++j) gin[kk][j] = M ? GG[j * gld + (kHS * half + kk) * ld + i] : 0.0f;
+        }
+        #pragma unroll
+        for (int c = 0; c < 3; ++c) l[c] = expf(l[c]);
         ok = tc_sync(ok);
         if (ok && t == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -427,19 +468,18 @@ __global__ void __launch_bounds__(kM, 1) k_anchor_decode_bwd(const float *__rest
             mma_commit(&s.mbar);
         }
         if (ok) ok = tc_wait(&s.mbar, phase, polls);
-        uint32_t on[2] = {0u, 0u};  // ReLU mask of the row's 64 pre-activations
+        uint32_t on = 0u;  // ReLU mask of this half's 32 pre-activations
         if (ok) {
-            float hv[kAH];
-            tmem_row64(tmem, 0, hv);
+            float hv[kHH];
+            read_hidden(tmem + lb, s.wt, half, hv);
             #pragma unroll
-            for (int c = 0; c < kAH; ++c) {
-                const float pre = hv[c] + s.wt.b1[c];
-                const bool act = M && pre > 0.0f;
-                on[c >> 5] |= act ? 1u << (c & 31) : 0u;
-                hv[c] = act ? pre : 0.0f;
+            for (int c = 0; c < kHH; ++c) {
+                const bool act = M && hv[c] > 0.0f;
+                on |= act ? 1u << c : 0u;
+                hv[c] = act ? hv[c] : 0.0f;
             }
             #pragma unroll
-            for (int c0 = 0; c0 < kAH; c0 += 8) store_row8(s.h, t, c0, kHG, hv + c0);
+            for (int c0 = 0; c0 < kHH; c0 += 8) store_row8(s.h, row, kHH * half + c0, kHG, hv + c0);
         }
         ok = tc_sync(ok);
         if (ok && t == 0) {
@@ -447,54 +487,48 @@ __global__ void __launch_bounds__(kM, 1) k_anchor_decode_bwd(const float *__rest
             issue_layer2(tmem + kColZ, s.h, kHG, s.wt);
             mma_commit(&s.mbar);
         }
-        // the incoming gradients of an active anchor's Gaussians, one slot ahead of their use
-        // (the first while layer 2 runs)
-        float gbuf[2][14];
-        auto load_g = [&](int k, float *g) {
-            #pragma unroll
-            for (int j = 0; j < 14; ++j) g[j] = M ? GG[j * gld + k * ld + i] : 0.0f;
-        };
-        load_g(0, gbuf[0]);
         if (ok) ok = tc_wait(&s.mbar, phase, polls);
         if (ok) {
-            // dL/dz of the kept Gaussians; the anchor's own offset and log-scale gradients
+            // dL/dz of this half's kept Gaussians; their offset gradients and the log-scale ones
             float gL[3] = {0.0f, 0.0f, 0.0f};
             #pragma unroll
-            for (int k = 0; k < kAK; ++k) {
-                if (k + 1 < kAK) load_g(k + 1, gbuf[(k + 1) & 1]);
-                const float *g = gbuf[k & 1];
+            for (int kk = 0; kk < kHS; ++kk) {
+                const int k = kHS * half + kk;
+                const float *g = gin[kk];
                 float z[16], dz[16];
-                read_slot(tmem, kColZ, s.wt, k, z);
+                read_slot(tmem + lb + kColZ, s.wt, k, z);
                 #pragma unroll
                 for (int j = 0; j < 16; ++j) dz[j] = 0.0f;
                 float gO[3] = {0.0f, 0.0f, 0.0f};
-                const float a = tanhf(z[3]);
-                if (M && a > 0.0f) {
+                if (M && z[3] > 0.0f) {
                     #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        const float l = expf(L[c]);
-                        const float O = off[3 * k + c] + z[11 + c];
-                        dz[11 + c] = g[c] * l;
-                        gO[c] = g[c] * l;
-                        gL[c] += g[c] * O * l + g[3 + c];
+                        const float O = off[3 * kk + c] + z[11 + c];
+                        dz[11 + c] = g[c] * l[c];
+                        gO[c] = g[c] * l[c];
+                        gL[c] += g[c] * O * l[c] + g[3 + c];
                         dz[8 + c] = g[3 + c] * (1.0f - sigmoidf(z[8 + c]));
                         const float sc = sigmoidf(z[c]);
-                        dz[c] = g[11 + c] * sc * (1.0f - sc) / kY00;
+                        dz[c] = g[11 + c] * sc * (1.0f - sc) * kInvY00;
                     }
                     #pragma unroll
                     for (int c = 0; c < 4; ++c) dz[4 + c] = g[6 + c];
-                    dz[3] = g[10] * (1.0f + a) / a;  // d logit(tanh z) / dz
+                    // d logit(tanh z) / dz = (1 + a) / a = 2 + 2 / expm1(2 z)
+                    dz[3] = g[10] * (2.0f + 2.0f / expm1f(2.0f * z[3]));
                 }
-                store_row8(s.dz, t, kSlot * k, kOG, dz);
-                store_row8(s.dz, t, kSlot * k + 8, kOG, dz + 8);
+                store_row8(s.dz, row, kSlot * k, kOG, dz);
+                store_row8(s.dz, row, kSlot * k + 8, kOG, dz + 8);
                 if (valid) {
                     #pragma unroll
                     for (int c = 0; c < 3; ++c) gA[(kPlaneOffs + 3 * k + c) * ld + i] = gO[c];
                 }
             }
-            if (valid) {
+            if (half) {
                 #pragma unroll
-                for (int c = 0; c < 3; ++c) gA[(kPlaneLogL + c) * ld + i] = gL[c];
+                for (int c = 0; c < 3; ++c) s.gLx[c][row] = gL[c];
+            } else {
+                #pragma unroll
+                for (int c = 0; c < 3; ++c) l[c] = gL[c];  // l is not needed any more
             }
         }
         ok = tc_sync(ok);
@@ -513,14 +547,19 @@ __global__ void __launch_bounds__(kM, 1) k_anchor_decode_bwd(const float *__rest
                          !first || kb > 0);
             mma_commit(&s.mbar);
         }
+        if (ok && !half && valid) {
+            #pragma unroll
+            for (int c = 0; c < 3; ++c) gA[(kPlaneLogL + c) * ld + i] = l[c] + s.gLx[c][row];
+        }
         if (ok) ok = tc_wait(&s.mbar, phase, polls);
         if (ok) {
-            float d1[kAH];
-            tmem_row64(tmem, 0, d1);
+            float d1[kHH];
+            tmem_ld16(tmem + lb + (uint32_t)(kHH * half), d1);
+            tmem_ld16(tmem + lb + (uint32_t)(kHH * half + 16), d1 + 16);
             #pragma unroll
-            for (int c = 0; c < kAH; ++c) d1[c] = (on[c >> 5] >> (c & 31)) & 1u ? d1[c] : 0.0f;
+            for (int c = 0; c < kHH; ++c) d1[c] = (on >> c) & 1u ? d1[c] : 0.0f;
             #pragma unroll
-            for (int c0 = 0; c0 < kAH; c0 += 8) store_row8(s.dp, t, c0, kAH / 8, d1 + c0);
+            for (int c0 = 0; c0 < kHH; c0 += 8) store_row8(s.dp, row, kHH * half + c0, kAH / 8, d1 + c0);
         }
         ok = tc_sync(ok);
         if (ok && t == 0) {
@@ -541,38 +580,47 @@ __global__ void __launch_bounds__(kM, 1) k_anchor_decode_bwd(const float *__rest
         if (ok) ok = tc_wait(&s.mbar, phase, polls);
         first = false;
         if (ok) {
-            float df[kAF];
-            tmem_ld16(tmem + lane_base + kColDF, df);
-            tmem_ld16(tmem + lane_base + kColDF + 16, df + 16);
+            float df[kHF];
+            tmem_ld16(tmem + lb + (uint32_t)(kColDF + kHF * half), df);
             if (valid) {
                 #pragma unroll
-                for (int c = 0; c < kAF; ++c) gA[c * ld + i] = df[c];
+                for (int c = 0; c < kHF; ++c) gA[(kHF * half + c) * ld + i] = df[c];
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         ok = __syncthreads_and(ok);
     }
     if (ok && !first) {
-        // the weight sums: TMEM lane c < 64 holds W2[.][c] (lane 64: b2) and W1[c][.] (column 36: b1)
+        // the weight sums: TMEM lane c < 64 holds W2[.][c] (lane 64: b2) and W1[c][.] (column 36:
+        // b1); half 0 reads slots 0-4 and W1 columns 0-31, half 1 slots 5-9 and columns 32-47
         #pragma unroll
-        for (int k = 0; k < kAK; ++k) {
+        for (int kk = 0; kk < kHS; ++kk) {
+            const int k = kHS * half + kk;
             float u[16];
-            tmem_ld16(tmem + lane_base + kColW2 + kSlot * k, u);
-            if (t < kAH) {
+            tmem_ld16(tmem + lb + (uint32_t)(kColW2 + kSlot * k), u);
+            if (row < kAH) {
                 #pragma unroll
-                for (int j = 0; j < 14; ++j) atomicAdd(&gw[kAW2 + (14 * k + j) * kAH + t], u[j]);
-            } else if (t == kAH) {
+                for (int j = 0; j < 14; ++j) atomicAdd(&gw[kAW2 + (14 * k + j) * kAH + row], u[j]);
+            } else if (row == kAH) {
                 #pragma unroll
                 for (int j = 0; j < 14; ++j) atomicAdd(&gw[kAB2 + 14 * k + j], u[j]);
             }
         }
-        float u[kXC];
-        #pragma unroll
-        for (int c = 0; c < kXC; c += 16) tmem_ld16(tmem + lane_base + kColW1 + c, u + c);
-        if (t < kAH) {
-            #pragma unroll
-            for (int c = 0; c < kAIn; ++c) atomicAdd(&gw[kAW1 + t * kAIn + c], u[c]);
-            atomicAdd(&gw[kAB1 + t], u[kAIn]);
+        float u[32];
+        if (half == 0) {
+            tmem_ld16(tmem + lb + (uint32_t)kColW1, u);
+            tmem_ld16(tmem + lb + (uint32_t)(kColW1 + 16), u + 16);
+            if (row < kAH) {
+                #pragma unroll
+                for (int c = 0; c < 32; ++c) atomicAdd(&gw[kAW1 + row * kAIn + c], u[c]);
+            }
+        } else {
+            tmem_ld16(tmem + lb + (uint32_t)(kColW1 + 32), u);
+            if (row < kAH) {
+                #pragma unroll
+                for (int c = 32; c < kAIn; ++c) atomicAdd(&gw[kAW1 + row * kAIn + c], u[c - 32]);
+                atomicAdd(&gw[kAB1 + row], u[kAIn - 32]);
+            }
         }
     }
     tc_end(&s.mbar, tmem, kBwdCols, ok, phase, status);
@@ -616,7 +664,7 @@ cudaError_t launch_anchor_decode(const float *A, const float *pos, const int *le
     }
     // two CTAs per SM (2 x 256 TMEM columns)
     const long long grid = std::min<long long>(ceil_div(ld, (long long)kM), 2ll * sm_count_anchor());
-    k_anchor_decode<<<(unsigned)grid, kM, smem, s>>>(A, pos, level, n, ld, w, v, G, gld, status,
+    k_anchor_decode<<<(unsigned)grid, kThreads, smem, s>>>(A, pos, level, n, ld, w, v, G, gld, status,
                                                      max_polls < 0 ? kSpin : max_polls);
     return cudaGetLastError();
 }
@@ -636,7 +684,7 @@ cudaError_t launch_anchor_decode_bwd(const float *A, const float *pos, const int
     }
     // one CTA per SM (512 TMEM columns)
     const long long grid = std::min<long long>(ceil_div(n, (long long)kM), (long long)sm_count_anchor());
-    k_anchor_decode_bwd<<<(unsigned)grid, kM, smem, s>>>(A, pos, level, n, ld, w, v, GG, gld, gA, gw, status,
+    k_anchor_decode_bwd<<<(unsigned)grid, kThreads, smem, s>>>(A, pos, level, n, ld, w, v, GG, gld, gA, gw, status,
                                                          max_polls < 0 ? kSpin : max_polls);
     return cudaGetLastError();
 }

@@ -197,9 +197,12 @@ def committed_profile(stage):
     if src is None:
         return {}
     sha = kernel_source_sha(src)
-    kern = STAGE_KERNELS[stage][0] if stage not in ("render_fwd",) else "k_render_fwd"
+    kern = {"render_fwd": "k_render_fwd", "decode": "k_anchor_decode",
+            "decode_bwd": "k_anchor_decode_bwd"}.get(stage) or STAGE_KERNELS[stage][0]
     for fn in sorted(glob.glob(os.path.join(ROOT, "profiles", kern + "_*.md"))):
         txt = open(fn).read()
+        if not txt.startswith("# " + kern + " "):  # a summary names its kernel first
+            continue
         m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
         if not m_sha or m_sha.group(1) != sha:
             continue
@@ -221,8 +224,9 @@ STAGES_FUSED = ["project", "sort", "render_fwd", "loss", "render_bwd", "project_
 # the library's kernels in each stage (a stage is one C-ABI call)
 STAGE_KERNELS = {
     "project": ["k_project"],
-    "sort": ["k_visible_count", "k_scan_blocks", "k_visible_compact", "k_onesweep", "k_tiles_count",
-             "k_tiles_offsets", "k_emit_pairs", "k_emit_big", "k_tile_hist", "k_tile_scan", "k_tile_scatter"],
+    "sort": ["k_visible_count", "k_scan_blocks", "k_visible_compact", "k_rx_count", "k_rx_scan", "k_rx_scatter",
+             "k_tiles_count", "k_tiles_offsets", "k_emit_pairs", "k_emit_big", "k_unpack_pairs", "k_tile_hist",
+             "k_tile_scan", "k_tile_scatter"],
     "render_fwd": ["k_fwd_plan", "k_render_fwd", "k_render_fwd_combine", "k_render_fwd_rerun"],
     "loss": ["k_ssim_fwd", "k_ssim_bwd", "k_loss_final"],
     "render_bwd": ["k_render_bwd"],
@@ -237,7 +241,9 @@ STAGE_SOURCE = {"render_bwd": "paper_2606_30436_b300/csrc/render.cu",
                 "project_bwd": "paper_2606_30436_b300/csrc/project.cu",
                 "project": "paper_2606_30436_b300/csrc/project.cu",
                 "sort": "paper_2606_30436_b300/csrc/sort.cu",
-                "loss": "paper_2606_30436_b300/csrc/loss.cu"}
+                "loss": "paper_2606_30436_b300/csrc/loss.cu",
+                "decode": "paper_2606_30436_b300/csrc/anchors.cu",
+                "decode_bwd": "paper_2606_30436_b300/csrc/anchors.cu"}
 
 
 def render_targets(gs, tscene, cams_list, cfg, dev):
@@ -984,6 +990,7 @@ def run_anchors(args, dev):
     dom = "decode_bwd" if kern["decode_bwd"] >= kern["decode"] else "decode"
     peak, kind = measured_peaks()
     achieved = bytes_stage[dom] / (kern[dom] * 1e-3) / 1e9
+    prof = committed_profile(dom)
     return {"metric": "anchor mapping iters/s (200k anchors x 10 Gaussians, 720p, decode+fwd+bwd+Adam)",
             "value": round(1e3 / ms, 2), "unit": "iters/s", "ms_per_step": round(ms, 4), "steps": steps,
             "warmup": args.warmup, "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -993,7 +1000,8 @@ def run_anchors(args, dev):
             "stages_ms": stage, "decoder_call_ms": {k: round(v, 4) for k, v in kern.items()},
             "visible_mean": int(np.mean(vis)), "pairs_mean": int(np.mean(needed)),
             "roofline": {"kernel": "k_anchor_" + dom, "bound": "hbm", "achieved": round(achieved, 1),
-                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": prof.get("traffic"), "traffic_source": prof.get("profile"),
                          "bytes_per_launch": bytes_stage[dom], "peak_kind": kind + " copy bandwidth"},
             "clocks": clk}
 

@@ -145,6 +145,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def with_clocks(run, args, dev):
+    """run(args, dev) with the SM clocks and throttle reasons sampled over the whole run (setup and
+    host phases included) added to its line unless it sampled its own timed region."""
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    out = run(args, dev)
+    clk = clocks.stop()
+    if "clocks" not in out and clk is not None:
+        out["clocks"] = dict(clk, scope="whole run")
+    return out
+
+
 def graph_call_ms(fn, reps=10, iters=5):
     """Device milliseconds per call of fn (launches on the current stream): reps calls captured
     in one CUDA graph, the graph replayed iters times between two events."""
@@ -1153,7 +1165,7 @@ def main():
     if args.memory:
         if rank == 0:
             import torch
-            print(json.dumps(run_memory(args, torch.device("cuda", 0))), flush=True)
+            print(json.dumps(with_clocks(run_memory, args, torch.device("cuda", 0))), flush=True)
         return
     if args.anchors:
         if rank == 0:
@@ -1163,12 +1175,12 @@ def main():
     if args.init:
         if rank == 0:
             import torch
-            print(json.dumps(run_init(args, torch.device("cuda", 0))), flush=True)
+            print(json.dumps(with_clocks(run_init, args, torch.device("cuda", 0))), flush=True)
         return
     if args.lifecycle:
         if rank == 0:
             import torch
-            print(json.dumps(run_lifecycle(args, torch.device("cuda", 0))), flush=True)
+            print(json.dumps(with_clocks(run_lifecycle, args, torch.device("cuda", 0))), flush=True)
         return
     if world > 1:
         import torch

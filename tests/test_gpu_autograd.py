@@ -1,5 +1,5 @@
 """The autograd.Function (recompute-in-backward) against the FP64 oracle
-gradient and against central finite differences of the GPU forward."""
+gradient and against central finite differences of the FP64 oracle forward."""
 import numpy as np
 import pytest
 import torch
@@ -45,7 +45,30 @@ def test_autograd_matches_oracle_gradient():
         assert rel_l2(g[k], ref[k]) < 1e-3, k
 
 
+def _entry(scene, plane):
+    """The oracle scene's array and column of a parameter plane of the GPU layout."""
+    if plane < 3:
+        return scene["means"], (slice(None), plane)
+    if plane < 6:
+        return scene["log_scales"], (slice(None), plane - 3)
+    if plane < 10:
+        return scene["quats"], (slice(None), plane - 6)
+    if plane == 10:
+        return scene["opacity_logits"], (slice(None),)
+    return scene["sh"], (slice(None), (plane - 11) // 3, (plane - 11) % 3)
+
+
 def test_autograd_finite_differences():
+    """The autograd gradient against central differences of the FP64 oracle's
+    forward (sum over both views of W . image, projected positions kept in
+    FP64 so that the function is smooth in the means) at the three largest
+    entries of eight parameter planes.  In FP64 a step of 1e-6 (relative)
+    leaves the truncation and rounding error of the difference far below the
+    check (the oracle's own analytic gradient agrees with these differences to
+    1e-6 of the tolerance), and crosses one of the forward's discrete cuts
+    (alpha >= 1/255, T >= 1e-4, the 3-sigma radius) with negligible
+    probability, so every entry must agree within 2e-3 relative (the FP32
+    backward) plus 1e-5 of the plane's largest gradient."""
     s, cams = _scene()
     model = gs.GaussianModel.from_scene(s)
     params = model.data.clone().requires_grad_(True)
@@ -54,27 +77,34 @@ def test_autograd_finite_differences():
     Wt = torch.from_numpy(rng.standard_normal(img.numel()).astype(np.float32)).cuda()
     (img * Wt).sum().backward()
     grad = params.grad.clone()
+    oc = ocfg(gs.Config(), fp32=False)  # smooth in the means: no FP32 rounding of the projected positions
+    sizes = [3 * c["height"] * c["width"] for c in cams]
+    wv = np.split(Wt.cpu().numpy().astype(np.float64), np.cumsum(sizes)[:-1])
+    base = {k: (np.asarray(v, np.float64).copy() if isinstance(v, np.ndarray) else v) for k, v in s.items()}
 
-    def f(p):
-        with torch.no_grad():
-            return float((rasterize(p, model.n, model.sh_degree, cams).double() * Wt.double()).sum())
+    def f(scene):
+        return sum(float((orc.forward(scene, cam, oc)["img"].reshape(-1) * w).sum()) for cam, w in zip(cams, wv))
 
-    # the largest gradient entries of a few planes, perturbed by a relative
-    # step.  An FP32 forward differenced over +-h also crosses the discrete
-    # alpha >= 1/255 cut at a few boundary pixels of large Gaussians (each a
-    # jump of ~W alpha_min / 2h), so most -- not all -- entries must agree;
-    # the exact gradient check is the oracle comparison above.
-    results = []
+    bad = []
+    n_checked = 0
     for plane in (0, 1, 2, 3, 5, 10, 11, 14):
         row = grad[plane, :model.n].abs()
+        scale = float(row.max())
         for g_idx in torch.topk(row, 3).indices.tolist():
-            h = 1e-3 * max(1.0, abs(float(params[plane, g_idx].detach())))
-            pp, pm = params.detach().clone(), params.detach().clone()
-            pp[plane, g_idx] += h
-            pm[plane, g_idx] -= h
-            fd = (f(pp) - f(pm)) / (2 * h)
+            arr, col = _entry(base, plane)
+            idx = (g_idx,) + tuple(col[1:])
+            v0 = float(arr[idx])
+            h = 1e-6 * max(1.0, abs(v0))
+            sp = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in base.items()}
+            sm = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in base.items()}
+            ap, _ = _entry(sp, plane)
+            am, _ = _entry(sm, plane)
+            ap[idx] = v0 + h
+            am[idx] = v0 - h
+            fd = (f(sp) - f(sm)) / (2 * h)
             an = float(grad[plane, g_idx])
-            results.append((abs(fd - an) <= 5e-2 * abs(an) + 1e-2, plane, g_idx, fd, an))
-    assert len(results) == 24
-    agree = sum(r[0] for r in results)
-    assert agree >= 20, [r for r in results if not r[0]]
+            n_checked += 1
+            if abs(fd - an) > 2e-3 * abs(an) + 1e-5 * scale:
+                bad.append((plane, g_idx, fd, an))
+    assert n_checked == 24
+    assert not bad, bad

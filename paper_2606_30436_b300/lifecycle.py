@@ -24,6 +24,8 @@ one slot per iteration (each slot the maximum over that iteration's views).
 """
 from __future__ import annotations
 
+import ctypes as C
+
 import numpy as np
 import torch
 
@@ -78,6 +80,7 @@ class Lifecycle:
         self.gen = torch.Generator(device="cuda").manual_seed(int(seed))
         self.ring = None
         self.head = gs.MLP_RING - 1
+        self._buffers = {}
         self.iterations = 0
 
     def start(self, step: gs.MappingStep):
@@ -94,6 +97,17 @@ class Lifecycle:
             self.ring.zero_()
         self.head = gs.MLP_RING - 1
         self.iterations = 0
+        # the decisions' buffers at this chunk's size, so that deciding allocates nothing
+        dev, f32, u8 = step.model.data.device, torch.float32, torch.uint8
+        n = step.model.n
+        for k, t in (("S_d", f32), ("S_p", f32), ("prune_max", f32), ("densify", u8), ("prune", u8)):
+            self._buffer(k, n, t, dev)
+        size = C.c_size_t()
+        gs._check(gs.lib().gs_prune_workspace_size(n, C.byref(size)), "gs_prune_workspace_size")
+        self._buffer("prune_ws", max(int(size.value), 256), u8, dev)
+        if self.mode == "learned" or self.collect:
+            self._buffer("feat", gs.MLP_INPUTS * ld, f32, dev)
+            self._buffer("prob", 2 * ld, f32, dev)
 
     def after_iteration(self, step: gs.MappingStep):
         """Moves this iteration's max T*alpha into the ring."""
@@ -103,15 +117,32 @@ class Lifecycle:
 
     def _features(self, step, cam_centre):
         model = step.model
-        feat = torch.zeros(gs.MLP_INPUTS, model.ld, dtype=torch.float32, device=model.data.device)
+        feat = self._buffer("feat", gs.MLP_INPUTS * model.ld, torch.float32, model.data.device)
+        feat = feat.view(gs.MLP_INPUTS, model.ld)
         gs.gs_mlp_features(model, step.buf.stats_acc, self.ring, self.head, cam_centre, feat)
         return feat
 
+    def _buffer(self, name, numel, dtype, device):
+        """A reused device buffer of at least numel elements (first numel returned): the
+        decisions then allocate nothing once the buffers have grown with the map."""
+        buf = self._buffers.get(name)
+        if buf is None or buf.numel() < numel or buf.device != device:
+            buf = torch.empty(int(numel * 1.25) + 4096, dtype=dtype, device=device)
+            self._buffers[name] = buf
+        return buf[:numel]
+
     def plain_bits(self, step: gs.MappingStep):
         """The plain criterion's bits (Supp. E.1, E.2) from the chunk's accumulators."""
-        n = step.model.n
+        n, dev = step.model.n, step.model.data.device
         n_views = max(1, self.iterations * step.buf.n_views)
-        scores, ws = gs.prune_buffers(n, device=step.model.data.device)
+        f32, u8 = torch.float32, torch.uint8
+        scores = {k: self._buffer(k, n, t, dev) for k, t in (("S_d", f32), ("S_p", f32), ("prune_max", f32),
+                                                                ("densify", u8), ("prune", u8))}
+        scores["prune_max"].zero_()  # running over the chunks of one decision: this chunk alone
+        scores["densify"].zero_()
+        size = C.c_size_t()
+        gs._check(gs.lib().gs_prune_workspace_size(n, C.byref(size)), "gs_prune_workspace_size")
+        ws = self._buffer("prune_ws", max(int(size.value), 256), u8, dev)
         gs.gs_prune_stats(step.buf.stats_acc, n, n_views, scores, ws, self.tau_d, self.tau_p)
         return scores["densify"], scores["prune"]
 
@@ -129,11 +160,11 @@ class Lifecycle:
         if self.mode == "plain":
             dens, prune = self.plain_bits(step)
             if self.collect:
-                self.samples.append((self._features(step, cam_centre), n, dens.clone(), prune.clone(),
+                self.samples.append((self._features(step, cam_centre).clone(), n, dens.clone(), prune.clone(),
                                      self.active(step).clone(), self.ids.copy()))
         else:
             feat = self._features(step, cam_centre)
-            prob = torch.zeros(2, model.ld, dtype=torch.float32, device=dev)
+            prob = self._buffer("prob", 2 * model.ld, torch.float32, dev).view(2, model.ld)
             self.predictor.predict(feat, n, None, None, prob)
             pd, pp = self.plain_bits(step)
             act = self.active(step)

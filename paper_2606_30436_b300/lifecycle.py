@@ -123,11 +123,12 @@ class Lifecycle:
         return feat
 
     def _buffer(self, name, numel, dtype, device):
-        """A reused device buffer of at least numel elements (first numel returned): the
-        decisions then allocate nothing once the buffers have grown with the map."""
+        """A reused device buffer of at least numel elements (the first numel returned),
+        grown by start() to the chunk's size so that the decisions allocate nothing."""
         buf = self._buffers.get(name)
         if buf is None or buf.numel() < numel or buf.device != device:
-            buf = torch.empty(int(numel * 1.25) + 4096, dtype=dtype, device=device)
+            self._buffers[name] = buf = None  # the old one is released first
+            buf = torch.empty(numel, dtype=dtype, device=device)
             self._buffers[name] = buf
         return buf[:numel]
 

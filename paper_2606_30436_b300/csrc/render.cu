@@ -683,31 +683,31 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
                 }
                 const uint32_t act = __ballot_sync(0xffffffffu, on);
                 if (act == 0u) continue;
+                // off lanes take alpha = G = 0: their sums below are zero and T, R stay as they are
+                // (no divergent branch around the arithmetic)
+                const float a_ = on ? alpha : 0.0f;
+                const float gu = on && q.w * G <= cfg.alpha_max ? G : 0.0f;  // alpha not clamped
+                const float4 col = s_c[warp][k];
+                T = __fdividef(T, 1.0f - a_);  // transmittance in front of this Gaussian
+                const float w = a_ * T;
                 float v[16];
-                #pragma unroll
-                for (int cc = 0; cc < 16; ++cc) v[cc] = 0.0f;
-                if (on) {
-                    const float4 col = s_c[warp][k];
-                    T = __fdividef(T, 1.0f - alpha);  // transmittance in front of this Gaussian
-                    const float w = alpha * T;
-                    v[kAccR] = g0 * w; v[kAccG] = g1 * w; v[kAccBl] = g2 * w; v[kAccZ] = gD * w;
-                    const float dLda = T * (g0 * (col.x - R0) + g1 * (col.y - R1) + g2 * (col.z - R2) +
-                                            gD * (col.w - RD));
-                    R0 = alpha * col.x + (1.0f - alpha) * R0;
-                    R1 = alpha * col.y + (1.0f - alpha) * R1;
-                    R2 = alpha * col.z + (1.0f - alpha) * R2;
-                    RD = alpha * col.w + (1.0f - alpha) * RD;
-                    if (q.w * G <= cfg.alpha_max) {  // alpha not clamped
-                        v[kAccO] = dLda * G;
-                        const float dp = dLda * q.w * G;
-                        v[kAccU] = dp * (q.x * dx + q.y * dy);
-                        v[kAccV] = dp * (q.z * dy + q.y * dx);
-                        v[kAccA] = -0.5f * dp * dx * dx;
-                        v[kAccB] = -dp * dx * dy;
-                        v[kAccC] = -0.5f * dp * dy * dy;
-                    }
-                    if (STATS) { v[kAccOmega] = 1.0f; v[kAccKappa] = mask; v[kAccMaxW] = w; }
-                }
+                v[kAccR] = g0 * w; v[kAccG] = g1 * w; v[kAccBl] = g2 * w; v[kAccZ] = gD * w;
+                const float dLda = T * (g0 * (col.x - R0) + g1 * (col.y - R1) + g2 * (col.z - R2) + gD * (col.w - RD));
+                R0 = a_ * col.x + (1.0f - a_) * R0;
+                R1 = a_ * col.y + (1.0f - a_) * R1;
+                R2 = a_ * col.z + (1.0f - a_) * R2;
+                RD = a_ * col.w + (1.0f - a_) * RD;
+                v[kAccO] = dLda * gu;
+                const float dp = dLda * q.w * gu;
+                v[kAccU] = dp * (q.x * dx + q.y * dy);
+                v[kAccV] = dp * (q.z * dy + q.y * dx);
+                v[kAccA] = -0.5f * dp * dx * dx;
+                v[kAccB] = -dp * dx * dy;
+                v[kAccC] = -0.5f * dp * dy * dy;
+                v[kAccOmega] = STATS && on ? 1.0f : 0.0f;
+                v[kAccKappa] = STATS && on ? mask : 0.0f;
+                v[kAccMaxW] = STATS ? w : 0.0f;
+                v[13] = v[14] = v[15] = 0.0f;
                 float *ar = acc + (long long)s_id[warp][k] * kAccStride;  // this record's sums
                 if (__popc(act) <= kDirectLanes) {
                     // a few pixels: each active lane adds its values itself, four per vector atomic

@@ -173,34 +173,30 @@ __device__ __forceinline__ void fwd_range(const RasterCfg &cfg, const uint8_t *_
                 float al[8];
                 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    float a = -1.0f;
-                    if (k0 + j < cnt) {
-                        const float2 p = sh.p[k0 + j];
-                        const float4 q = sh.q[k0 + j];
-                        const float power = gauss_power(q.x, q.y, q.z, fx - p.x, fy - p.y);
-                        if (power <= 0.0f) {
-                            a = fminf(cfg.alpha_max, q.w * __expf(power));
-                            if (a < cfg.alpha_min) a = -1.0f;
-                        }
-                    }
-                    al[j] = a;
+                    // every lane evaluates every staged Gaussian (slots past cnt hold stale,
+                    // in-bounds entries and are masked)
+                    const float2 p = sh.p[k0 + j];
+                    const float4 q = sh.q[k0 + j];
+                    const float power = gauss_power(q.x, q.y, q.z, fx - p.x, fy - p.y);
+                    const float a = fminf(cfg.alpha_max, q.w * __expf(power));
+                    al[j] = k0 + j < cnt && power <= 0.0f && !(a < cfg.alpha_min) ? a : -1.0f;
                 }
                 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
+                    // no divergent branch: a lane that does not take this Gaussian adds
+                    // zero-weighted colour and keeps its state
                     const float a = al[j];
-                    if (!st.done && a >= 0.0f) {
-                        const float Tn = st.T * (1.0f - a);
-                        if (Tn < cfg.t_min) {
-                            st.done = true;
-                        } else {
-                            const float4 cc = sh.c[k0 + j];
-                            const float wgt = a * st.T;
-                            st.C0 += cc.x * wgt; st.C1 += cc.y * wgt; st.C2 += cc.z * wgt; st.D += cc.w * wgt;
-                            st.T = Tn;
-                            st.last = sh.pos[k0 + j] - rgx + 1;
-                            hook(sh, k0 + j, a);
-                        }
-                    }
+                    const bool blend = !st.done && a >= 0.0f;
+                    const float Tn = st.T * (1.0f - a);
+                    const bool stop = blend && Tn < cfg.t_min;
+                    const bool take = blend && !stop;
+                    const float4 cc = sh.c[k0 + j];
+                    const float wgt = (take ? a : 0.0f) * st.T;
+                    st.C0 += cc.x * wgt; st.C1 += cc.y * wgt; st.C2 += cc.z * wgt; st.D += cc.w * wgt;
+                    st.T = take ? Tn : st.T;
+                    st.last = take ? sh.pos[k0 + j] - rgx + 1 : st.last;
+                    st.done = st.done || stop;
+                    if (take) hook(sh, k0 + j, a);
                 }
             }
             __syncwarp();
@@ -665,22 +661,14 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
             __syncwarp();
             const int cnt = min(32, total - c);
             for (int k = cnt - 1; k >= 0; --k) {
-                bool on = s_pos[warp][k] - rg.x < lst;
-                float alpha = 0.0f, G = 0.0f, dx = 0.0f, dy = 0.0f;
+                // the test without a divergent branch: every lane evaluates the Gaussian
                 const float2 p = s_p[warp][k];
                 const float4 q = s_q[warp][k];
-                if (on) {
-                    dx = fx - p.x;
-                    dy = fy - p.y;
-                    const float power = gauss_power(q.x, q.y, q.z, dx, dy);
-                    if (power > 0.0f) {
-                        on = false;
-                    } else {
-                        G = __expf(power);
-                        alpha = fminf(cfg.alpha_max, q.w * G);
-                        if (alpha < cfg.alpha_min) on = false;
-                    }
-                }
+                const float dx = fx - p.x, dy = fy - p.y;
+                const float power = gauss_power(q.x, q.y, q.z, dx, dy);
+                const float G = __expf(power);
+                const float alpha = fminf(cfg.alpha_max, q.w * G);
+                const bool on = s_pos[warp][k] - rg.x < lst && !(power > 0.0f) && !(alpha < cfg.alpha_min);
                 const uint32_t act = __ballot_sync(0xffffffffu, on);
                 if (act == 0u) continue;
                 // off lanes take alpha = G = 0: their sums below are zero and T, R stay as they are

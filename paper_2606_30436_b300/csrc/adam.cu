@@ -29,20 +29,29 @@ __global__ void __launch_bounds__(256) k_adam(float4 *__restrict__ p, const floa
         inv_bc1 = s_bc[0];
         inv_sqrt_bc2 = s_bc[1];
     }
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total4;
-         i += (long long)gridDim.x * blockDim.x) {
-        const float a = lr.lr[lr_group(i / ld4)];
-        const float4 gg = g[i];
-        float4 mm = m[i], vv = v[i], pp = p[i];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < total4; i0 += 2 * stride) {
+        float4 gg[2], mm[2], vv[2], pp[2];
+        #pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const long long i = i0 + u * stride;
+            if (i < total4) { gg[u] = g[i]; mm[u] = m[i]; vv[u] = v[i]; pp[u] = p[i]; }
+        }
+        #pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const long long i = i0 + u * stride;
+            if (i >= total4) continue;
+            const float a = lr.lr[lr_group(i / ld4)];
 #define GS_ADAM_LANE(c)                                                         \
-    mm.c = b1 * mm.c + (1.0f - b1) * gg.c;                                      \
-    vv.c = b2 * vv.c + (1.0f - b2) * gg.c * gg.c;                               \
-    pp.c -= a * (mm.c * inv_bc1) / (sqrtf(vv.c) * inv_sqrt_bc2 + eps);
-        GS_ADAM_LANE(x) GS_ADAM_LANE(y) GS_ADAM_LANE(z) GS_ADAM_LANE(w)
+    mm[u].c = b1 * mm[u].c + (1.0f - b1) * gg[u].c;                             \
+    vv[u].c = b2 * vv[u].c + (1.0f - b2) * gg[u].c * gg[u].c;                   \
+    pp[u].c -= a * (mm[u].c * inv_bc1) / (sqrtf(vv[u].c) * inv_sqrt_bc2 + eps);
+            GS_ADAM_LANE(x) GS_ADAM_LANE(y) GS_ADAM_LANE(z) GS_ADAM_LANE(w)
 #undef GS_ADAM_LANE
-        m[i] = mm;
-        v[i] = vv;
-        p[i] = pp;
+            m[i] = mm[u];
+            v[i] = vv[u];
+            p[i] = pp[u];
+        }
     }
 }
 

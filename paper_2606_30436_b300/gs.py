@@ -193,7 +193,7 @@ class Config:
     tan_clamp: float = 1.3
     bg: tuple = (0.0, 0.0, 0.0)
     batch: int = 512
-    segment: int = 256  # split length of long tile lists, in pairs (0 = no split)
+    segment: int = 512  # split length of long tile lists, in pairs (0 = no split)
 
     def c(self) -> RasterCfg:
         return RasterCfg(self.tile_w, self.tile_h, self.near_z, self.dilation, self.alpha_min, self.alpha_max,
@@ -837,7 +837,7 @@ class MappingStep:
         return needed
 
 
-def launches_per_step(total_tiles, views=1, lambda_dssim=0.2, segment=256, fused_adam=False):
+def launches_per_step(total_tiles, views=1, lambda_dssim=0.2, segment=512, fused_adam=False):
     """Kernel launches of the library in one mapping iteration (memsets not
     counted): project 1; sort 3 (visible records) + 4 depth passes (+ 1 view
     pass with several views) + 5

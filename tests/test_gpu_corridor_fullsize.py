@@ -1,8 +1,9 @@
 """Parity at the benchmark's own size: one whole 1280x720 corridor frame of
 the 1M-Gaussian SH-degree-3 scene (frame 500), run through the default
 mapping configuration -- 16x16 tiles and the split compositing of tile lists
-longer than 256 pairs, where the vanishing-point tiles hold tens of thousands
-of pairs -- against the FP64 oracle on the same inputs:
+longer than 512 pairs (and, as a second arm, 256), where the vanishing-point
+tiles hold tens of thousands of pairs -- against the FP64 oracle on the same
+inputs:
 
 - pair ids and tile ranges bit-exact (Gaussians whose radius rounds the other
   way in FP32 next to an integer are dropped from both lists and counted);
@@ -31,18 +32,21 @@ def frame():
     scene = scenes.corridor_scene(N, seed=0, sh_degree=3)
     cam = scenes.corridor_camera(FRAME, W, H, F)
     cfg = gs.Config()
-    assert cfg.segment == 256
+    assert cfg.segment == 512
     oc = ocfg(cfg)
     target = orc.forward(scenes.perturb(scene, 0.01, seed=1), cam, oc)["img"].astype(np.float32)
-    model = gs.GaussianModel.from_scene(scene)
-    st = gs.MappingStep(model, [cam], cfg, lambda_dssim=0.2, with_stats=True)
-    st.fit_capacity()
     tgt = torch.from_numpy(target.reshape(-1)).cuda()
-    st.step(tgt, optimize=False)
-    torch.cuda.synchronize()
-    st.check_status()
+    steps = {}
+    for seg in (512, 256):
+        model = gs.GaussianModel.from_scene(scene)
+        st = gs.MappingStep(model, [cam], gs.Config(segment=seg), lambda_dssim=0.2, with_stats=True)
+        st.fit_capacity()
+        st.step(tgt, optimize=False)
+        torch.cuda.synchronize()
+        st.check_status()
+        steps[seg] = st
     ref = orc.loss_and_grads(scene, cam, oc, target, 0.2)
-    return dict(scene=scene, cam=cam, cfg=cfg, st=st, ref=ref)
+    return dict(scene=scene, cam=cam, cfg=cfg, steps=steps, st=steps[512], ref=ref)
 
 
 def _flagged(frame):
@@ -64,12 +68,12 @@ def _by_tile(ids, ranges):
 
 
 def test_fullsize_split_is_exercised(frame):
-    st = frame["st"]
     ranges = frame["ref"]["ranges"]
     longest = int((ranges[:, 1] - ranges[:, 0]).max())
     assert longest > 30_000, longest  # vanishing-point tiles: many segments each
-    off, _ = st.buf.seg_needed()
-    assert not off, "the split plan did not fit its workspace"
+    for st in frame["steps"].values():
+        off, _ = st.buf.seg_needed()
+        assert not off, "the split plan did not fit its workspace"
 
 
 def test_fullsize_pairs_bit_exact(frame):
@@ -92,8 +96,9 @@ def test_fullsize_pairs_bit_exact(frame):
         assert np.array_equal(ranges[nonempty], ref["ranges"][nonempty])
 
 
-def test_fullsize_image(frame):
-    st, ref, cfg = frame["st"], frame["ref"], frame["cfg"]
+@pytest.mark.parametrize("seg", [512, 256])
+def test_fullsize_image(frame, seg):
+    st, ref, cfg = frame["steps"][seg], frame["ref"], frame["cfg"]
     _, flagged = _flagged(frame)
     b = st.buf
     img = b.view_image(0).cpu().numpy()
@@ -113,8 +118,9 @@ def test_fullsize_image(frame):
     assert np.array_equal(last[~mask], exp_last[~mask])
 
 
-def test_fullsize_loss_and_gradients(frame):
-    st, ref = frame["st"], frame["ref"]
+@pytest.mark.parametrize("seg", [512, 256])
+def test_fullsize_loss_and_gradients(frame, seg):
+    st, ref = frame["steps"][seg], frame["ref"]
     assert abs(st.buf.loss.item() - ref["loss"]) <= 1e-4 * abs(ref["loss"])
     g = gs.unpack_planes(st.grads.data.cpu().numpy(), N, 3)
     for k in GROUPS:

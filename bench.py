@@ -383,18 +383,39 @@ def run_corridor(args, world, dev):
 
     # end to end through the C ABI with host buffers: each step copies its
     # target from pinned host memory into the buffer its graph reads, replays
-    # the graph and reads the loss back, both copies inside the timed region
+    # the graph and reads the loss back, both copies inside the timed region.
+    # The copies run on a second stream one step ahead of the replays (each
+    # frame's graph reads its own target buffer): a replay waits for its
+    # target's copy, and a copy into a buffer waits for the last replay that read it.
     host_targets = [t.cpu().pin_memory() for t in targets]
     host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in range(args.steps)]
+    used = [None] * len(graphs)
     barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    copy_stream.wait_event(e0)
+
+    def copy_in(i):
+        k = i % len(graphs)
+        with torch.cuda.stream(copy_stream):
+            if used[k] is not None:
+                copy_stream.wait_event(used[k])
+            targets[k].copy_(host_targets[k], non_blocking=True)
+            copied[i].record(copy_stream)
+
     t0 = time.perf_counter()
+    copy_in(0)
     for i in range(args.steps):
         k = i % len(graphs)
-        targets[k].copy_(host_targets[k], non_blocking=True)
+        if i + 1 < args.steps:
+            copy_in(i + 1)
+        stream.wait_event(copied[i])
         step.replay(graphs[k])
         host_loss.copy_(step.buf.loss[:1], non_blocking=True)
+        used[k] = torch.cuda.Event()
+        used[k].record(stream)
     e1.record(stream)
     barrier(world)
     e2e_ms = e0.elapsed_time(e1)

@@ -115,7 +115,7 @@ __device__ __forceinline__ Ewa ewa(const ViewDesc &c, float x, float y, float z,
 }
 
 template <int D>
-__global__ void __launch_bounds__(256, 3) k_project(const float *__restrict__ P, long long n, long long ld, ViewTable vt,
+__global__ void __launch_bounds__(256, 4) k_project(const float *__restrict__ P, long long n, long long ld, ViewTable vt,
                                                  RasterCfg cfg, float2 *__restrict__ xy, float4 *__restrict__ co,
                                                  float4 *__restrict__ rgbd, int *__restrict__ radius,
                                                  int *__restrict__ touched, int *__restrict__ status) {

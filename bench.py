@@ -52,13 +52,17 @@ def frame_pool(n):
 # --------------------------------------------------------------------------
 # algorithmic bytes (the minimum HBM traffic the method implies, FP32)
 
-def step_bytes(N, K, views):
+def step_bytes(N, K, views, color_jac=False):
     """Algorithmic bytes of each stage of one mapping iteration over `views`,
     a list of (V, P, px, tiles) per view (V visible records, P pairs, px
     pixels): the minimum the method must move, every buffer touched once.
     Parameters are read once per iteration however many views see them (the
     visible union is at most N); per-view terms are summed over the views.
-      project      12N means + 4(K-3) x visible union + per view (56V records + 4N tile counts)
+    With color_jac (SH degree >= 1) the projection also writes 48 bytes per
+    record (the colour's direction gradient and clamp flags) and the projection
+    backward reads those instead of the 4(K-11) bytes of SH coefficients.
+      project      12N means + 4(K-3) x visible union + per view (56V records + 4N tile counts,
+                   + 48V with color_jac)
       sort         per view: 8N + 16V + 12P (scan, duplicate) + 24P (one read and one
                    write of the pair list) + 8P + 8 tiles (ranges)
       render_fwd   per view: 4P ids + 36P gathered records + 20px (image, T_final, last)
@@ -66,14 +70,17 @@ def step_bytes(N, K, views):
       render_bwd   per view: 40P + 12px + 20px + 36V (2D gradients through L2)
       project_bwd  4K x visible union (parameters re-read) + 4KN (gradients written)
                    + per view 32V (lifecycle accumulators read and written)
+                   (with color_jac: 44 x visible union + per view 48V instead of 4K x union)
       adam         28KN (p, g, m, v read; p, m, v written)
     """
     Vs = sum(v[0] for v in views)
     Vu = min(float(N), float(Vs))
+    cj = bool(color_jac) and K > 14  # SH degree >= 1
     b = {"project": 12 * N + 4 * (K - 3) * Vu, "sort": 0.0, "render_fwd": 0.0, "loss": 0.0, "render_bwd": 0.0,
-         "project_bwd": 4 * K * Vu + 4 * K * N, "adam": 28 * K * N}
+         "project_bwd": 4 * (11 if cj else K) * Vu + 4 * K * N, "adam": 28 * K * N}
     for (V, P, px, tiles) in views:
-        b["project"] += 56 * V + 4 * N
+        b["project"] += 56 * V + 4 * N + (48 * V if cj else 0)
+        b["project_bwd"] += 48 * V if cj else 0
         b["sort"] += 8 * N + 16 * V + 12 * P + 24 * P + 8 * P + 8 * tiles
         b["render_fwd"] += 40 * P + 20 * px
         b["loss"] += 36 * px
@@ -424,7 +431,8 @@ def run_corridor(args, world, dev):
     ms, e2e_ms = max_over_ranks([ms, e2e_ms], world, device=dev)
 
     Vm, Pm = float(np.mean(vis)), float(np.mean(needed))
-    ab = step_bytes(N_GAUSS, model.K, [(Vm, Pm, W * H, step.buf.total_tiles)])
+    ab = step_bytes(N_GAUSS, model.K, [(Vm, Pm, W * H, step.buf.total_tiles)],
+                    color_jac=step.buf.color_jac is not None)
     peak, peak_kind = measured_peaks()
     # the roofline entry is the stage (one C-ABI call) with the longest live time
     dom = max(stages, key=lambda nm: stage_ms[nm])

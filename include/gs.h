@@ -112,6 +112,15 @@ typedef struct {
     int32_t *radius;      /* pixel radius, 0 = culled */
     int32_t *tiles_touched;
     int64_t ld;
+    /* Optional (NULL = not kept), used only when sh_degree >= 1: 12 floats per
+     * record, 16-byte aligned, per colour channel c at [12*rec + 4c]: the
+     * gradient of that channel's unclamped SH colour (Eq. 1's view-dependent
+     * colour) with respect to the mean through the view direction, then 1 if
+     * the channel was kept by the clamp at 0 and 0 if clamped.  gs_project
+     * writes it for every record with radius > 0; a backward given it reads
+     * it instead of the SH coefficients, so it must come from the gs_project
+     * call on the same parameters. */
+    float *color_jac;
 } gs_projected;
 
 /* Pair list and tile ranges of all views.  Tiles of all views form one

@@ -112,6 +112,7 @@ gs_status check_proj(const gs_projected *pr, long long ld) {
     if (!pr || !pr->xy || !pr->conic_opacity || !pr->rgb_depth || !pr->radius || !pr->tiles_touched) return GS_ERR_INVALID;
     if (pr->ld != ld) return GS_ERR_INVALID;
     if (!aligned16(pr->xy) || !aligned16(pr->conic_opacity) || !aligned16(pr->rgb_depth)) return GS_ERR_INVALID;
+    if (pr->color_jac && !aligned16(pr->color_jac)) return GS_ERR_INVALID;
     return GS_OK;
 }
 
@@ -210,7 +211,7 @@ GS_API gs_status gs_project(const gs_params *params, const gs_camera *cams, int3
     if (st != GS_OK) return st;
     launch_project(params->data, params->n, params->ld, params->sh_degree, vt, rc, (float2 *)out->xy,
                    (float4 *)out->conic_opacity, (float4 *)out->rgb_depth, out->radius, out->tiles_touched, status,
-                   (cudaStream_t)stream);
+                   (float4 *)out->color_jac, (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
 }
 
@@ -362,7 +363,7 @@ GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, i
     if (grads)
         launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius, acc, nrec,
                            grads->data, accumulate, loss_per_view, want_stats ? stats->acc : nullptr,
-                           want_stats ? stats->ld : 0, s);
+                           want_stats ? stats->ld : 0, (const float4 *)proj->color_jac, s);
     return cuda_status(cudaGetLastError());
 }
 
@@ -433,7 +434,7 @@ GS_API gs_status gs_render_bwd_lists(const gs_params *params, const gs_camera *c
     if (grads)
         launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius, acc, nrec,
                            grads->data, accumulate, loss_per_view, want_stats ? stats->acc : nullptr,
-                           want_stats ? stats->ld : 0, s);
+                           want_stats ? stats->ld : 0, (const float4 *)proj->color_jac, s);
     return cuda_status(cudaGetLastError());
 }
 
@@ -456,7 +457,8 @@ GS_API gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, 
     if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < need) return GS_ERR_INVALID;
     launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius,
                        (const float *)ws, nrec, grads->data, accumulate, loss_per_view,
-                       stats ? stats->acc : nullptr, stats ? stats->ld : 0, (cudaStream_t)stream);
+                       stats ? stats->acc : nullptr, stats ? stats->ld : 0, (const float4 *)proj->color_jac,
+                       (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
 }
 

@@ -20,11 +20,13 @@ static_assert(kAccU == 0 && kAccC == 4 && kAccBl == 8 && kAccOmega == 10 && kAcc
               "the vector reads and atomics group the sums four by four");
 
 void launch_project(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
-                    float2 *xy, float4 *co, float4 *rgbd, int *radius, int *touched, int *status, cudaStream_t s);
+                    float2 *xy, float4 *co, float4 *rgbd, int *radius, int *touched, int *status, float4 *cj,
+                    cudaStream_t s);
 
 void launch_project_bwd(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
                         const int *radius, const float *acc, long long nrec, float *G, int accumulate,
-                        const float *loss_per_view, float *stats, long long stats_ld, cudaStream_t s);
+                        const float *loss_per_view, float *stats, long long stats_ld, const float4 *cj,
+                        cudaStream_t s);
 void launch_project_bwd_adam(float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
                              const int *radius, const float *acc, long long nrec, const float *G_in, float *m,
                              float *v, const float lr[6], float beta1, float beta2, float eps, long long step,

@@ -118,7 +118,8 @@ template <int D>
 __global__ void __launch_bounds__(256, 4) k_project(const float *__restrict__ P, long long n, long long ld, ViewTable vt,
                                                  RasterCfg cfg, float2 *__restrict__ xy, float4 *__restrict__ co,
                                                  float4 *__restrict__ rgbd, int *__restrict__ radius,
-                                                 int *__restrict__ touched, int *__restrict__ status) {
+                                                 int *__restrict__ touched, int *__restrict__ status,
+                                                 float4 *__restrict__ cj) {
     constexpr int K = (D + 1) * (D + 1);
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ld) return;
@@ -187,21 +188,47 @@ __global__ void __launch_bounds__(256, 4) k_project(const float *__restrict__ P,
                 if (tt <= 0) { rad = 0; tt = 0; }
             }
             if (rad > 0) {
+                xy[rec] = make_float2(p.u, p.v);
+                co[rec] = make_float4(ca, cb, cc, opacity);
                 // view-dependent colour
                 float dx = mx - c.campos[0], dy = my - c.campos[1], dz = mz - c.campos[2];
                 const float id = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
                 dx *= id; dy *= id; dz *= id;
-                float Y[16];
-                sh_basis<D>(dx, dy, dz, Y);
                 float r = 0.5f, gch = 0.5f, b = 0.5f;
-                #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    r += Y[k] * P[(11 + 3 * k) * ld + g];
-                    gch += Y[k] * P[(12 + 3 * k) * ld + g];
-                    b += Y[k] * P[(13 + 3 * k) * ld + g];
+                if (D >= 1 && cj) {
+                    // channel by channel (16 coefficients live at a time, for 64 registers per
+                    // thread at four CTAs per SM), with the gradient of the unclamped colour with
+                    // respect to the mean through the view direction, and the clamp flag, kept
+                    // for the backward, which then reads no SH coefficient
+                    #pragma unroll 1
+                    for (int ch = 0; ch < 3; ++ch) {
+                        float Y[K], w[K];
+                        sh_basis<D>(dx, dy, dz, Y);
+                        float raw = 0.5f;
+                        #pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            w[k] = P[(11 + 3 * k + ch) * ld + g];
+                            raw += Y[k] * w[k];
+                        }
+                        float gx, gy, gz;
+                        sh_basis_vjp<D>(dx, dy, dz, w, gx, gy, gz);
+                        const float dd = gx * dx + gy * dy + gz * dz;  // onto the sphere's tangent plane
+                        cj[3 * rec + ch] = make_float4((gx - dx * dd) * id, (gy - dy * dd) * id, (gz - dz * dd) * id,
+                                                       raw < 0.0f ? 0.0f : 1.0f);
+                        r = ch == 0 ? raw : r;
+                        gch = ch == 1 ? raw : gch;
+                        b = ch == 2 ? raw : b;
+                    }
+                } else {
+                    float Y[16];
+                    sh_basis<D>(dx, dy, dz, Y);
+                    #pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        r += Y[k] * P[(11 + 3 * k) * ld + g];
+                        gch += Y[k] * P[(12 + 3 * k) * ld + g];
+                        b += Y[k] * P[(13 + 3 * k) * ld + g];
+                    }
                 }
-                xy[rec] = make_float2(p.u, p.v);
-                co[rec] = make_float4(ca, cb, cc, opacity);
                 rgbd[rec] = make_float4(fmaxf(r, 0.0f), fmaxf(gch, 0.0f), fmaxf(b, 0.0f), p.zc);
             }
         }
@@ -278,7 +305,8 @@ __global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 3) k_pr
                                                      const float *__restrict__ acc, long long nrec,
                                                      float *__restrict__ G, int accumulate,
                                                      const float *__restrict__ loss_per_view,
-                                                     float *__restrict__ stats, long long stats_ld, FusedAdam fa) {
+                                                     float *__restrict__ stats, long long stats_ld, FusedAdam fa,
+                                                     const float4 *__restrict__ cj) {
     constexpr int K = (D + 1) * (D + 1);
     if (ADAM && fa.step_dev) {  // bias corrections from the device step counter (graph replay)
         __shared__ float s_bc[2];
@@ -319,43 +347,72 @@ __global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 3) k_pr
     float gmean[3] = {0, 0, 0};
 
     // ---- colour: SH gradients and the direction term of the mean ----
-    #pragma unroll 1
-    for (int ch = 0; ch < 3; ++ch) {
-        float sh[K], gsh[K];
-        #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            sh[k] = P[(11 + 3 * k + ch) * ld + g];
-            gsh[k] = 0.0f;
-        }
-        for (int v = 0; v < vt.n_views; ++v) {
-            const long long rec = v * ld + g;
-            if (radius[rec] <= 0) continue;
-            const ViewDesc &c = vt.v[v];
-            float ex = mx - c.campos[0], ey = my - c.campos[1], ez = mz - c.campos[2];
-            const float idist = 1.0f / sqrtf(ex * ex + ey * ey + ez * ez);
-            ex *= idist; ey *= idist; ez *= idist;
-            float Y[K];
-            sh_basis<D>(ex, ey, ez, Y);
-            float raw = 0.5f;
+    if (D >= 1 && cj) {
+        // from the forward's per-record colour gradients and clamp flags: no SH coefficient read
+        #pragma unroll 1
+        for (int ch = 0; ch < 3; ++ch) {
+            float gsh[K];
             #pragma unroll
-            for (int k = 0; k < K; ++k) raw += Y[k] * sh[k];
-            const float gcv = raw < 0.0f ? 0.0f : acc[rec * kAccStride + kAccR + ch];
-            #pragma unroll
-            for (int k = 0; k < K; ++k) gsh[k] += gcv * Y[k];
-            if (D > 0) {
-                float w[K];
+            for (int k = 0; k < K; ++k) gsh[k] = 0.0f;
+            for (int v = 0; v < vt.n_views; ++v) {
+                const long long rec = v * ld + g;
+                if (radius[rec] <= 0) continue;
+                const ViewDesc &c = vt.v[v];
+                float ex = mx - c.campos[0], ey = my - c.campos[1], ez = mz - c.campos[2];
+                const float idist = 1.0f / sqrtf(ex * ex + ey * ey + ez * ez);
+                ex *= idist; ey *= idist; ez *= idist;
+                float Y[K];
+                sh_basis<D>(ex, ey, ez, Y);
+                const float4 jc = cj[3 * rec + ch];
+                const float gcv = jc.w * acc[rec * kAccStride + kAccR + ch];
                 #pragma unroll
-                for (int k = 0; k < K; ++k) w[k] = gcv * sh[k];
-                float gx, gy, gz;
-                sh_basis_vjp<D>(ex, ey, ez, w, gx, gy, gz);
-                const float dd = gx * ex + gy * ey + gz * ez;  // onto the sphere's tangent plane
-                gmean[0] += (gx - ex * dd) * idist;
-                gmean[1] += (gy - ey * dd) * idist;
-                gmean[2] += (gz - ez * dd) * idist;
+                for (int k = 0; k < K; ++k) gsh[k] += gcv * Y[k];
+                gmean[0] += gcv * jc.x;
+                gmean[1] += gcv * jc.y;
+                gmean[2] += gcv * jc.z;
             }
+            #pragma unroll
+            for (int k = 0; k < K; ++k) emit(11 + 3 * k + ch, gsh[k]);
         }
-        #pragma unroll
-        for (int k = 0; k < K; ++k) emit(11 + 3 * k + ch, gsh[k]);
+    } else {
+        #pragma unroll 1
+        for (int ch = 0; ch < 3; ++ch) {
+            float sh[K], gsh[K];
+            #pragma unroll
+            for (int k = 0; k < K; ++k) {
+                sh[k] = P[(11 + 3 * k + ch) * ld + g];
+                gsh[k] = 0.0f;
+            }
+            for (int v = 0; v < vt.n_views; ++v) {
+                const long long rec = v * ld + g;
+                if (radius[rec] <= 0) continue;
+                const ViewDesc &c = vt.v[v];
+                float ex = mx - c.campos[0], ey = my - c.campos[1], ez = mz - c.campos[2];
+                const float idist = 1.0f / sqrtf(ex * ex + ey * ey + ez * ez);
+                ex *= idist; ey *= idist; ez *= idist;
+                float Y[K];
+                sh_basis<D>(ex, ey, ez, Y);
+                float raw = 0.5f;
+                #pragma unroll
+                for (int k = 0; k < K; ++k) raw += Y[k] * sh[k];
+                const float gcv = raw < 0.0f ? 0.0f : acc[rec * kAccStride + kAccR + ch];
+                #pragma unroll
+                for (int k = 0; k < K; ++k) gsh[k] += gcv * Y[k];
+                if (D > 0) {
+                    float w[K];
+                    #pragma unroll
+                    for (int k = 0; k < K; ++k) w[k] = gcv * sh[k];
+                    float gx, gy, gz;
+                    sh_basis_vjp<D>(ex, ey, ez, w, gx, gy, gz);
+                    const float dd = gx * ex + gy * ey + gz * ez;  // onto the sphere's tangent plane
+                    gmean[0] += (gx - ex * dd) * idist;
+                    gmean[1] += (gy - ey * dd) * idist;
+                    gmean[2] += (gz - ez * dd) * idist;
+                }
+            }
+            #pragma unroll
+            for (int k = 0; k < K; ++k) emit(11 + 3 * k + ch, gsh[k]);
+        }
     }
 
     // ---- geometry: opacity, conic -> 2D covariance -> Sigma, J, position ----
@@ -550,25 +607,27 @@ __global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 3) k_pr
 }
 
 void launch_project(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
-                    float2 *xy, float4 *co, float4 *rgbd, int *radius, int *touched, int *status, cudaStream_t s) {
+                    float2 *xy, float4 *co, float4 *rgbd, int *radius, int *touched, int *status, float4 *cj,
+                    cudaStream_t s) {
     if (ld <= 0) return;
     const int blocks = (int)ceil_div(ld, 256);
     switch (D) {
-        case 0: k_project<0><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status); break;
-        case 1: k_project<1><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status); break;
-        case 2: k_project<2><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status); break;
-        default: k_project<3><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status); break;
+        case 0: k_project<0><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
+        case 1: k_project<1><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
+        case 2: k_project<2><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
+        default: k_project<3><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
     }
 }
 
 void launch_project_bwd(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
                         const int *radius, const float *acc, long long nrec, float *G, int accumulate,
-                        const float *loss_per_view, float *stats, long long stats_ld, cudaStream_t s) {
+                        const float *loss_per_view, float *stats, long long stats_ld, const float4 *cj,
+                        cudaStream_t s) {
     if (ld <= 0) return;
     const int blocks = (int)ceil_div(ld, 256);
     FusedAdam fa{};
 #define GS_PB(DD) k_project_bwd<DD, false><<<blocks, 256, 0, s>>>(const_cast<float *>(P), n, ld, vt, cfg, radius, acc, \
-                                                                   nrec, G, accumulate, loss_per_view, stats, stats_ld, fa)
+                                                                   nrec, G, accumulate, loss_per_view, stats, stats_ld, fa, cj)
     switch (D) {
         case 0: GS_PB(0); break;
         case 1: GS_PB(1); break;
@@ -608,7 +667,7 @@ void launch_project_bwd_adam(float *P, long long n, long long ld, int D, const V
         }                                                                                                       \
         k_project_bwd<DD, true><<<blocks, kFusedThreads, smem, s>>>(P, n, ld, vt, cfg, radius, acc, nrec,       \
                                                                     nullptr, 0,                                 \
-                                                          loss_per_view, stats, stats_ld, fa);                 \
+                                                          loss_per_view, stats, stats_ld, fa, nullptr);        \
     } while (0)
     switch (D) {
         case 0: GS_PBA(0); break;

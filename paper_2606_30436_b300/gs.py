@@ -17,6 +17,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 from dataclasses import dataclass
+from typing import Optional
 
 import numpy as np
 import torch
@@ -51,7 +52,8 @@ class Params(C.Structure):
 
 class Projected(C.Structure):
     _fields_ = [("xy", C.c_void_p), ("conic_opacity", C.c_void_p), ("rgb_depth", C.c_void_p),
-                ("radius", C.c_void_p), ("tiles_touched", C.c_void_p), ("ld", C.c_int64)]
+                ("radius", C.c_void_p), ("tiles_touched", C.c_void_p), ("ld", C.c_int64),
+                ("color_jac", C.c_void_p)]
 
 
 class Binning(C.Structure):
@@ -194,6 +196,9 @@ class Config:
     bg: tuple = (0.0, 0.0, 0.0)
     batch: int = 512
     segment: int = 512  # split length of long tile lists, in pairs (0 = no split)
+    # keep the colour's view-direction gradient per record (SH degree >= 1) for the backward:
+    # None = where it moves fewer bytes than the backward's re-read of the SH coefficients
+    color_jac: Optional[bool] = None
 
     def c(self) -> RasterCfg:
         return RasterCfg(self.tile_w, self.tile_h, self.near_z, self.dilation, self.alpha_min, self.alpha_max,
@@ -202,6 +207,19 @@ class Config:
 
 def planes(sh_degree: int) -> int:
     return 11 + 3 * (sh_degree + 1) ** 2
+
+
+def use_color_jac(cfg: Config, sh_degree: int, n_views: int) -> bool:
+    """Whether the projection keeps the colour's direction gradient for the backward.
+    Kept, it costs 48 bytes written and 48 read per visible record, at most
+    96 n_views per Gaussian; it saves the backward's 4 (K - 11) bytes of SH
+    coefficients per Gaussian.  Automatic (None): only where the bound says it
+    saves, i.e. SH degree 3 with up to two views and degree 2 with one."""
+    if sh_degree < 1:
+        return False
+    if cfg.color_jac is not None:
+        return bool(cfg.color_jac)
+    return 96 * n_views <= 4 * (planes(sh_degree) - 11)
 
 
 def padded(n: int) -> int:
@@ -287,6 +305,10 @@ class Buffers:
         self.rgb_depth = torch.empty(nr, 4, dtype=f32, device=dev)
         self.radius = torch.empty(nr, dtype=i32, device=dev)
         self.tiles_touched = torch.empty(nr, dtype=i32, device=dev)
+        # the projection keeps what the backward needs of the SH colour, so the backward reads
+        # 48 bytes per visible record instead of every Gaussian's 3 (D+1)^2 coefficients
+        self.color_jac = (torch.empty(nr, 12, dtype=f32, device=dev)
+                          if use_color_jac(cfg, model.sh_degree, self.n_views) else None)
         self.counts = torch.zeros(4, dtype=i32, device=dev)
         self.status = torch.zeros(1, dtype=i32, device=dev)
         self.tile_ranges = torch.zeros(self.total_tiles, 2, dtype=i32, device=dev)
@@ -333,7 +355,8 @@ class Buffers:
 
     def projected(self) -> Projected:
         return Projected(self.xy.data_ptr(), self.conic_opacity.data_ptr(), self.rgb_depth.data_ptr(),
-                         self.radius.data_ptr(), self.tiles_touched.data_ptr(), self.ld)
+                         self.radius.data_ptr(), self.tiles_touched.data_ptr(), self.ld,
+                         None if self.color_jac is None else self.color_jac.data_ptr())
 
     def binning(self) -> Binning:
         return Binning(self.gauss_ids.data_ptr(), self.tile_ranges.data_ptr(), self.counts.data_ptr(),

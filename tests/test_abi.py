@@ -85,6 +85,24 @@ def test_invalid_arguments_rejected_on_host():
                      None) == 1
     bad_batch = gs.Config(batch=64).c()
     assert L.gs_view_layout(cam, 1, C.byref(bad_batch), C.byref(nt), None, None, None) == 1
+    # a kept colour gradient that is not 16-byte aligned
+    p = gs.Params(16, 10, 12, 3)
+    proj = gs.Projected(16, 32, 48, 64, 80, 12, 8)
+    assert L.gs_project(C.byref(p), cam, 1, C.byref(gs.Config().c()), C.byref(proj), None, None) == 1
+
+
+def test_color_jac_policy():
+    """The automatic choice keeps the colour gradient exactly where its bytes, 96 per
+    visible record at most (written and read back), are below the 4 (K - 11) bytes of
+    SH coefficients per Gaussian that the backward then skips."""
+    auto = gs.Config()
+    for D in range(4):
+        for views in (1, 2, 3, 16):
+            # K - 11 = 3 (D + 1)^2: 12, 27, 48 coefficients at degrees 1, 2, 3
+            want = (D, views) in {(2, 1), (3, 1), (3, 2)}
+            assert gs.use_color_jac(auto, D, views) == want, (D, views)
+            assert gs.use_color_jac(gs.Config(color_jac=True), D, views) == (D >= 1)
+            assert not gs.use_color_jac(gs.Config(color_jac=False), D, views)
 
 
 def test_plane_packing_roundtrip():

@@ -47,3 +47,16 @@ def test_chunk_reads_parameters_once():
     assert b4["adam"] == b1["adam"]
     assert b4["project"] == 12 * N + 4 * (K - 3) * N + 4 * (56 * 600 + 4 * N)
     assert b4["project_bwd"] == 4 * K * N + 4 * K * N + 4 * 32 * 600
+
+
+def test_color_jacobian_bytes():
+    """The kept colour gradient moves 48 bytes per record out and back in place of
+    the projection backward's 4(K-11) bytes of SH coefficients per visible Gaussian."""
+    N, K, V, P, px, tiles = 1_000_000, 59, 494_279, 1_177_411, 921_600, 3600
+    b0 = bench.step_bytes(N, K, [(V, P, px, tiles)])
+    b1 = bench.step_bytes(N, K, [(V, P, px, tiles)], color_jac=True)
+    assert b1["project"] == b0["project"] + 48 * V
+    assert b1["project_bwd"] == 4 * 11 * V + 4 * K * N + 32 * V + 48 * V
+    assert b1["adam"] == b0["adam"] and b1["render_bwd"] == b0["render_bwd"]
+    # SH degree 0 keeps nothing
+    assert bench.step_bytes(N, 14, [(V, P, px, tiles)], color_jac=True) == bench.step_bytes(N, 14, [(V, P, px, tiles)])

@@ -199,12 +199,17 @@ def _backward_case(scene, cams, cfg, lam=0.2, with_target_from=None):
     return st, g_gpu, g_or, stats, kamb, losses
 
 
-@pytest.mark.parametrize("D,seed", [(0, 40), (3, 41)])
-def test_backward_gradcheck_scene(D, seed):
+# color_jac: the backward takes the SH colour's direction gradient kept by the projection
+# (True) or re-reads the SH coefficients (False); both against the oracle
+@pytest.mark.parametrize("D,seed,color_jac", [(0, 40, True), (1, 42, True), (2, 43, True), (3, 41, True),
+                                              (3, 41, False), (2, 43, False)])
+def test_backward_gradcheck_scene(D, seed, color_jac):
     scene = scenes.uniform_scene(200, seed=seed, sh_degree=D)
     cams = [scenes.pinhole(64, 48, 60.0)]
     target_scene = scenes.perturb(scene, 0.01, seed=seed + 100)
-    st, g_gpu, g_or, _, _, losses = _backward_case(scene, cams, gs.Config(), with_target_from=target_scene)
+    st, g_gpu, g_or, _, _, losses = _backward_case(scene, cams, gs.Config(color_jac=color_jac),
+                                                   with_target_from=target_scene)
+    assert (st.buf.color_jac is not None) == (color_jac and D >= 1)
     assert abs(st.buf.loss.item() - losses[0]) < 1e-4 * abs(losses[0]) + 1e-7
     for k in GROUPS:
         e = rel_l2(g_gpu[k], g_or[k])
@@ -223,10 +228,10 @@ def test_backward_config1(segment):
         assert e < 1e-3, (k, e)
 
 
-@pytest.mark.parametrize("segment", [256, 32])
-def test_backward_multiview_stats(segment):
+@pytest.mark.parametrize("segment,color_jac", [(256, None), (32, None), (256, True)])
+def test_backward_multiview_stats(segment, color_jac):
     scene, cams = _multi(1, 2000)
-    cfg = gs.Config(bg=(0.1, 0.2, 0.3), segment=segment)
+    cfg = gs.Config(bg=(0.1, 0.2, 0.3), segment=segment, color_jac=color_jac)
     target_scene = scenes.perturb(scene, 0.02, seed=5)
     st, g_gpu, g_or, stats, kamb, losses = _backward_case(scene, cams, cfg, with_target_from=target_scene)
     for k in GROUPS:

@@ -458,6 +458,34 @@ gs_status gs_densify_prune(const gs_params *src, const gs_params *src_m, const g
                            int32_t *status, void *ws, size_t ws_bytes, gs_stream stream);
 
 /*
+ * Spatial order of the Gaussians (not a step of the paper's method: a layout
+ * of its parameter planes, e.g. after the actions above).  Reorders, in place,
+ * the rows 0..n-1 of params and of every extra plane set (Adam moments,
+ * per-Gaussian statistics: same ld as params) into the Morton order of the
+ * means, so that the Gaussians one view sees are near each other in memory.
+ * The order, exactly:
+ *   lo_a, hi_a  minimum and maximum of the means' axis a over the n rows
+ *   scale       1024 / max_a (hi_a - lo_a) in FP32, 0 when that is 0 or not finite
+ *   q_a         with t = (m_a - lo_a) * scale in FP32 (rounded per operation):
+ *               1023 if t >= 1023, else (int) t if t > 0, else 0
+ *   code        bit b of q_x at bit 3b, of q_y at 3b + 1, of q_z at 3b + 2
+ *   order       rows by increasing code, equal codes in their previous order.
+ * perm (nullable, [n] int32, device): new row i is previous row perm[i].
+ * Padding rows [n, ld) are left as they are; every buffer keeps its address.
+ * ws: gs_reorder_workspace_size(n, ld, largest plane count of params and the
+ * extra sets) bytes, 256-byte aligned.  n_extra <= 16.
+ */
+typedef struct {
+    float *data;    /* [planes][ld] */
+    int64_t ld;
+    int32_t planes;
+} gs_plane_set;
+
+gs_status gs_reorder_workspace_size(int64_t n, int64_t ld, int32_t max_planes, size_t *bytes);
+gs_status gs_reorder(const gs_params *params, const gs_plane_set *extra, int32_t n_extra, int32_t *perm,
+                     void *ws, size_t ws_bytes, gs_stream stream);
+
+/*
  * Learned densify / prune predictor (not in the paper: an MLP trained on the
  * decisions of the plain criterion above, which stays the fallback and the
  * reference for its error).  16 inputs -> 64 -> 64 (ReLU) -> 2 logits (sigmoid):

@@ -111,6 +111,7 @@ def lib():
         L.or_anchor_decode.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, d, i32]
         L.or_anchor_decode_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp]
         L.or_anchor_hidden.argtypes = [i64, vp, vp, vp, vp, i32, vp, vp]
+        L.or_morton_order.argtypes = [i64, vp, vp, vp]
     return _lib
 
 
@@ -542,3 +543,14 @@ def loss_and_grads(params, cam, cfg: Cfg, target, lambda_dssim=0.2, tau_err=0.1,
     g = project_backward(f["params"], cam, cfg, f["proj"], grad2d)
     f.update(loss=L, dL_dimg=dL, ssim=ssim, grad2d=grad2d, stats=stats, kappa_amb=kamb, grads=g)
     return f
+
+
+def morton_order(means):
+    """(perm int32 [n], codes uint32 [n]) of FP32 means [n, 3]: the rows in the
+    Morton order of the library's spatial reordering, ties in row order."""
+    m = np.ascontiguousarray(np.asarray(means, np.float32).reshape(-1, 3))
+    n = m.shape[0]
+    perm = np.zeros(n, np.int32)
+    codes = np.zeros(n, np.uint32)
+    lib().or_morton_order(n, _ptr(m), _ptr(codes), _ptr(perm))
+    return perm, codes

@@ -81,6 +81,7 @@
  */
 #include "gs_oracle.h"
 
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -1481,4 +1482,57 @@ void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *leve
             }
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spatial order of the rows (a memory layout, not a step of the method)      */
+/* ------------------------------------------------------------------------ */
+
+/* The Morton (Z-) order of the means as the library defines it, written with
+ * plain loops: the bounding box, one scale 1024 / (largest extent), 1024
+ * cells per axis, the cell indices' bits interleaved with x lowest, then a
+ * sort by code with ties in row order.  FP32, because the library takes the
+ * cell decision in FP32 (each operation rounded once, as here). */
+typedef struct {
+    uint32_t code;
+    int64_t row;
+} or_code_row;
+
+static int cmp_code_row(const void *a, const void *b) {
+    const or_code_row *x = (const or_code_row *)a, *y = (const or_code_row *)b;
+    if (x->code != y->code) return x->code < y->code ? -1 : 1;
+    return x->row < y->row ? -1 : (x->row > y->row);
+}
+
+void or_morton_order(int64_t n, const float *means, uint32_t *codes, int32_t *perm) {
+    if (n <= 0) return;
+    float lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = means[a];
+    for (int64_t i = 1; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            const float m = means[3 * i + a];
+            if (m < lo[a]) lo[a] = m;
+            if (m > hi[a]) hi[a] = m;
+        }
+    float ext = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        const float e = hi[a] - lo[a];
+        if (e > ext) ext = e;
+    }
+    const float scale = (ext > 0.0f && ext <= FLT_MAX) ? 1024.0f / ext : 0.0f;
+    or_code_row *cr = (or_code_row *)malloc(sizeof(or_code_row) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t code = 0;
+        for (int a = 0; a < 3; ++a) {
+            const float t = (means[3 * i + a] - lo[a]) * scale;
+            const int q = t >= 1023.0f ? 1023 : (t > 0.0f ? (int)t : 0);
+            for (int b = 0; b < 10; ++b) code |= (uint32_t)((q >> b) & 1) << (3 * b + a);
+        }
+        cr[i].code = code;
+        cr[i].row = i;
+        if (codes) codes[i] = code;
+    }
+    qsort(cr, (size_t)n, sizeof(or_code_row), cmp_code_row);
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)cr[i].row;
+    free(cr);
 }

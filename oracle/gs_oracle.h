@@ -239,6 +239,14 @@ void or_anchor_decode_backward(int64_t n, const double *pos, const int32_t *leve
 void or_anchor_hidden(int64_t n, const double *pos, const double *feat, const double *w, const double cam_c[3],
                       int32_t bf16, double *x_raw, double *pre);
 
+/* Spatial order of the rows (a memory layout of the library, not a step of
+ * the method): means[n][3] FP32; codes[n] (nullable) receive the 30-bit Morton
+ * codes, perm[n] the rows in increasing code order, ties in row order.  Box
+ * lo/hi per axis; scale = 1024 / max extent (0 if that is 0 or not finite);
+ * q = 1023 if t >= 1023, (int) t if t > 0, else 0 with t = (m - lo) * scale;
+ * bit b of q_x, q_y, q_z at 3b, 3b + 1, 3b + 2.  All arithmetic FP32. */
+void or_morton_order(int64_t n, const float *means, uint32_t *codes, int32_t *perm);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" entry points declared in include/gs.h: argument
 // validation, the per-call view table, and the kernel launches on the caller's
 // stream.  No entry point allocates device memory or synchronises the host.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -523,6 +524,36 @@ GS_API gs_status gs_prune_stats(const gs_stats *stats, int64_t n, int32_t n_view
     launch_prune(stats->acc, stats->ld, n, n_views, tau_d, tau_p, out->S_d, out->S_p, out->prune_max, out->densify,
                  out->prune, ws, (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
+}
+
+GS_API gs_status gs_reorder_workspace_size(int64_t n, int64_t ld, int32_t max_planes, size_t *bytes) {
+    if (n < 0 || ld < n || max_planes < 1 || !bytes) return GS_ERR_INVALID;
+    *bytes = reorder_workspace_bytes(n, ld, max_planes);
+    return GS_OK;
+}
+
+GS_API gs_status gs_reorder(const gs_params *params, const gs_plane_set *extra, int32_t n_extra, int32_t *perm,
+                            void *ws, size_t ws_bytes, gs_stream stream) {
+    constexpr int kMaxExtra = 16;
+    gs_status st = check_params(params);
+    if (st != GS_OK) return st;
+    if (n_extra < 0 || n_extra > kMaxExtra || (n_extra > 0 && !extra) || ((uintptr_t)perm & 3u)) return GS_ERR_INVALID;
+    float *sets[kMaxExtra];
+    int planes[kMaxExtra];
+    int maxp = GS_PLANES(params->sh_degree);
+    for (int e = 0; e < n_extra; ++e) {
+        const gs_plane_set &x = extra[e];
+        if (!x.data || !aligned16(x.data) || x.ld != params->ld || x.planes < 1 || x.planes > 65535 ||
+            x.data == params->data)
+            return GS_ERR_INVALID;
+        sets[e] = x.data;
+        planes[e] = x.planes;
+        maxp = std::max(maxp, (int)x.planes);
+    }
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < reorder_workspace_bytes(params->n, params->ld, maxp))
+        return GS_ERR_INVALID;
+    return cuda_status(launch_reorder(params->data, params->n, params->ld, GS_PLANES(params->sh_degree), sets,
+                                      planes, n_extra, perm, ws, (cudaStream_t)stream));
 }
 
 GS_API gs_status gs_actions_workspace_size(int64_t n, size_t *bytes) {

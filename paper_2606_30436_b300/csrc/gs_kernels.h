@@ -40,6 +40,17 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
                         int2 *tile_ranges, uint8_t *block_mask, int *tile_order, int *counts, long long max_pairs,
                         void *ws, int *status, cudaStream_t s);
 
+// Stable LSD radix sort of count (device) 32-bit keys with 32-bit values on bits [0, bits):
+// k0/v0 hold the input, k1/v1 the same capacity; the sorted values land in final_v.
+size_t key_sort_scratch_bytes();
+void launch_key_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *count, long long cap,
+                     int bits, void *scratch, uint32_t *final_v, cudaStream_t s);
+
+// Spatial (Morton) order of the Gaussians (reorder.cu).
+size_t reorder_workspace_bytes(long long n, long long ld, int max_planes);
+cudaError_t launch_reorder(float *P, long long n, long long ld, int planes, float *const *extra,
+                           const int *extra_planes, int n_extra, int *perm, void *ws, cudaStream_t s);
+
 void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ranges, const int *ids,
                        const uint8_t *masks, const int *order, const float2 *xy, const float4 *co,
                        const float4 *rgbd, float *img, float *T_final, int *last, float *depth, const SegWs &seg,

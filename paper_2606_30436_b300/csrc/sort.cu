@@ -620,6 +620,17 @@ static int radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, co
     return cur;
 }
 
+size_t key_sort_scratch_bytes() {
+    return align_up(sizeof(uint32_t) * 256 * kRxBlocks, 256) + align_up(sizeof(uint32_t) * 256, 256);
+}
+
+void launch_key_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, const int *count, long long cap,
+                     int bits, void *scratch, uint32_t *final_v, cudaStream_t s) {
+    uint32_t *hist = (uint32_t *)scratch;
+    uint32_t *dtotal = (uint32_t *)((char *)scratch + align_up(sizeof(uint32_t) * 256 * kRxBlocks, 256));
+    radix_sort(k0, v0, k1, v1, count, cap, bits, hist, dtotal, s, final_v);
+}
+
 cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy, const float4 *co, const float4 *rgbd,
                         long long nrec, long long ld, const ViewTable &vt, float alpha_min, int *gauss_ids,
                         int2 *tile_ranges, uint8_t *block_mask, int *tile_order, int *counts, long long max_pairs,

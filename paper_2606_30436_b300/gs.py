@@ -56,6 +56,10 @@ class Projected(C.Structure):
                 ("color_jac", C.c_void_p)]
 
 
+class PlaneSet(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("ld", C.c_int64), ("planes", C.c_int32)]
+
+
 class Binning(C.Structure):
     _fields_ = [("gauss_ids", C.c_void_p), ("tile_ranges", C.c_void_p), ("counts", C.c_void_p),
                 ("block_mask", C.c_void_p), ("tile_order", C.c_void_p), ("max_pairs", C.c_int64)]
@@ -84,7 +88,8 @@ EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspac
            "gs_segment_workspace_size", "gs_project_bwd_adam", "gs_segment_workspace_size_items",
            "gs_voxel_table_reset", "gs_init_workspace_size", "gs_init_probability", "gs_init_insert",
            "gs_voxel_lookup", "gs_anchor_decode", "gs_anchor_decode_bwd", "gs_adam_flat",
-           "gs_list_workspace_size", "gs_render_fwd_lists", "gs_render_bwd_lists")
+           "gs_list_workspace_size", "gs_render_fwd_lists", "gs_render_bwd_lists", "gs_reorder_workspace_size",
+           "gs_reorder")
 
 _lib = None
 
@@ -128,6 +133,8 @@ def lib():
                                           P(Stats), vp]
         L.gs_prune_stats.argtypes = [P(Stats), i64, i32, f32, f32, P(ChunkScores), vp, sz, vp]
         L.gs_actions_workspace_size.argtypes = [i64, P(sz)]
+        L.gs_reorder_workspace_size.argtypes = [i64, i64, i32, P(sz)]
+        L.gs_reorder.argtypes = [P(Params), P(PlaneSet), i32, vp, vp, sz, vp]
         L.gs_densify_prune.argtypes = [P(Params), P(Params), P(Params), vp, vp, vp, f32, f32, P(Params), P(Params),
                                        P(Params), vp, vp, vp, sz, vp]
         L.gs_mlp_push_blend.argtypes = [P(Stats), i64, vp, i64, i32, vp]
@@ -588,6 +595,25 @@ def gs_densify_prune(model: GaussianModel, densify, prune, noise, split_log_scal
     return out, mo, vo, n_out
 
 
+def gs_reorder(model: GaussianModel, extra=(), perm=None, ws=None, stream=None):
+    """Puts the rows of model and of every extra [planes, ld] float32 tensor (Adam
+    moments, per-Gaussian statistics) in the Morton order of the means, in place.
+    perm: an [n] int32 device tensor receiving the previous row of each new row
+    (allocated when None).  Returns perm."""
+    dev = model.data.device
+    extra = list(extra)
+    for t in extra:
+        assert t.dtype == torch.float32 and t.dim() == 2 and t.shape[1] == model.ld and t.is_contiguous()
+    sets = (PlaneSet * max(1, len(extra)))(*[PlaneSet(t.data_ptr(), model.ld, t.shape[0]) for t in extra])
+    perm = torch.empty(max(model.n, 1), dtype=torch.int32, device=dev) if perm is None else perm
+    if ws is None:
+        maxp = max([model.K] + [t.shape[0] for t in extra])
+        ws = _workspace(lib().gs_reorder_workspace_size, model.n, model.ld, maxp, device=dev)
+    _check(lib().gs_reorder(C.byref(model.c()), sets, len(extra), _ptr(perm), _ptr(ws), ws.numel(),
+                            _stream(stream)), "gs_reorder")
+    return perm[:model.n]
+
+
 MLP_INPUTS, MLP_HIDDEN, MLP_WEIGHTS, MLP_RING = 16, 64, 5378, 8
 
 
@@ -656,6 +682,7 @@ class MappingStep:
         self.lr = lr or default_lr()
         self.with_stats = with_stats
         self._grads = None  # allocated on first use: the fused path needs no gradient buffer
+        self._reorder_ws = None
         # Adam moments: zero, or carried over (e.g. through gs_densify_prune)
         self.exp_avg, self.exp_avg_sq = moments if moments is not None else (model.like(), model.like())
         assert self.exp_avg.ld == model.ld and self.exp_avg_sq.ld == model.ld
@@ -752,6 +779,21 @@ class MappingStep:
             self.step_count += 1
             gs_adam(self.model, self.grads, self.exp_avg, self.exp_avg_sq, self.lr, self.step_count, stream=stream)
         return self.buf.loss
+
+    def reorder(self, stream=None):
+        """Puts the map's rows (parameters, Adam moments, statistics) in the Morton
+        order of the means (gs_reorder): the Gaussians one view sees then share
+        memory sectors.  Every buffer keeps its address, so captured graphs stay
+        valid.  Returns the [n] int32 device permutation (new row i is previous
+        row perm[i])."""
+        if self._reorder_ws is None:
+            maxp = max(self.model.K, 6)
+            self._reorder_ws = _workspace(lib().gs_reorder_workspace_size, self.model.n, self.model.ld, maxp,
+                                          device=self.model.data.device)
+        extra = [self.exp_avg.data, self.exp_avg_sq.data]
+        if self.buf.stats_acc is not None:
+            extra.append(self.buf.stats_acc)
+        return gs_reorder(self.model, extra, ws=self._reorder_ws, stream=stream)
 
     # stage boundaries that capture(events=...) marks, in order
     STAGES = ("project", "sort", "render_fwd", "loss", "render_bwd", "project_bwd", "adam")

@@ -64,13 +64,16 @@ class Lifecycle:
     """Statistics, decisions and actions of one chunk at a time."""
 
     def __init__(self, mode="plain", tau_d=5.0, tau_p=0.99, split_log_scale=-2.5, split_factor=1.6,
-                 predictor: Predictor = None, collect=False, seed=0, margin=0.1, n_initial=None):
+                 predictor: Predictor = None, collect=False, seed=0, margin=0.1, n_initial=None, reorder=True):
         assert mode in ("plain", "learned")
         assert mode == "plain" or predictor is not None
         self.mode, self.tau_d, self.tau_p = mode, tau_d, tau_p
         self.split_log_scale, self.split_factor = split_log_scale, split_factor
         self.predictor, self.collect = predictor, collect
         self.margin = margin  # learned: the plain bit where |p - 1/2| < margin
+        # after the actions, put the new map's rows in the Morton order of the means, so that
+        # the next chunk's views read contiguous rows (ids follow the rows)
+        self.reorder = reorder
         # identity of every Gaussian of the current map (host), carried through the actions; numbered
         # 0 .. n - 1 at the first chunk unless n_initial says otherwise
         self.ids = None if n_initial is None else np.arange(n_initial, dtype=np.int64)
@@ -203,6 +206,9 @@ class Lifecycle:
             self.history[-1]["n_after"] = out.n
         self.ids, self.next_id = carry_ids(self.ids, dens.cpu().numpy(), prune.cpu().numpy(), self.next_id)
         assert len(self.ids) == out.n
+        if self.reorder and out.n > 0:
+            perm = gs.gs_reorder(out, [m.data, v.data])
+            self.ids = self.ids[perm.cpu().numpy()]
         return out, (m, v)
 
 

@@ -91,6 +91,31 @@ def test_invalid_arguments_rejected_on_host():
     assert L.gs_project(C.byref(p), cam, 1, C.byref(gs.Config().c()), C.byref(proj), None, None) == 1
 
 
+def test_reorder_arguments_rejected_on_host():
+    L = gs.lib()
+    p = gs.Params(256, 10, 12, 0)
+    n = C.c_size_t()
+    assert L.gs_reorder_workspace_size(10, 12, 14, C.byref(n)) == 0 and n.value > 0
+    assert L.gs_reorder_workspace_size(10, 8, 14, C.byref(n)) == 1  # ld < n
+    assert L.gs_reorder_workspace_size(10, 12, 0, C.byref(n)) == 1
+    need = n.value
+    L.gs_reorder_workspace_size(10, 12, 14, C.byref(n))
+    ok = (gs.PlaneSet * 2)(gs.PlaneSet(512, 12, 14), gs.PlaneSet(768, 12, 6))
+    # misaligned workspace, too small a workspace, an extra set of another ld, misaligned, too many sets
+    assert L.gs_reorder(C.byref(p), ok, 2, None, 1024 + 16, need, None) == 1
+    assert L.gs_reorder(C.byref(p), ok, 2, None, 1024, 64, None) == 1
+    bad_ld = (gs.PlaneSet * 1)(gs.PlaneSet(512, 16, 14))
+    assert L.gs_reorder(C.byref(p), bad_ld, 1, None, 1024, need, None) == 1
+    bad_al = (gs.PlaneSet * 1)(gs.PlaneSet(520, 12, 14))
+    assert L.gs_reorder(C.byref(p), bad_al, 1, None, 1024, need, None) == 1
+    same = (gs.PlaneSet * 1)(gs.PlaneSet(256, 12, 14))  # the parameters themselves
+    assert L.gs_reorder(C.byref(p), same, 1, None, 1024, need, None) == 1
+    many = (gs.PlaneSet * 17)(*[gs.PlaneSet(512 + 256 * k, 12, 1) for k in range(17)])
+    assert L.gs_reorder(C.byref(p), many, 17, None, 1024, need, None) == 1
+    assert L.gs_reorder(C.byref(p), None, 1, None, 1024, need, None) == 1
+    assert L.gs_reorder(C.byref(p), ok, 2, 2, 1024, need, None) == 1  # misaligned perm
+
+
 def test_color_jac_policy():
     """The automatic choice keeps the colour gradient exactly where its bytes, 96 per
     visible record at most (written and read back), are below the 4 (K - 11) bytes of

@@ -18,6 +18,7 @@ STRUCTS = [
     (gs.Params, "gs_params", {}),
     (gs.Projected, "gs_projected", {}),
     (gs.Binning, "gs_binning", {}),
+    (gs.PlaneSet, "gs_plane_set", {}),
     (gs.Frame, "gs_frame", {}),
     (gs.Stats, "gs_stats", {}),
     (gs.ChunkScores, "gs_chunk_scores", {}),

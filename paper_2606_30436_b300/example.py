@@ -35,7 +35,9 @@ def main():
                     help="initialise anchors at a synthetic keyframe and map them on its image")
     ap.add_argument("--keyframe-size", type=int, nargs=2, default=(360, 640), metavar=("H", "W"))
     ap.add_argument("--segment", type=int, default=None,
-                    help="split length of long tile lists (default: 256 for a corridor view, none for a chunk)")
+                    help="split length of long tile lists (default: 512 for a corridor view, none for a chunk)")
+    ap.add_argument("--no-reorder", action="store_true",
+                    help="keep the scene's row order (default: the Morton order of the means, gs_reorder)")
     args = ap.parse_args()
     if args.keyframe:
         # a new keyframe: probability map, voxel insertion, anchors, anchor mapping on its image
@@ -81,8 +83,10 @@ def main():
         scene = scenes.corridor_scene(args.gaussians, seed=0, sh_degree=3)
         cams = [scenes.corridor_camera(args.frame)]
     model = gs.GaussianModel.from_scene(scene)
-    segment = args.segment if args.segment is not None else (0 if args.chunk else 256)
+    segment = args.segment if args.segment is not None else (0 if args.chunk else 512)
     st = gs.MappingStep(model, cams, gs.Config(segment=segment), lambda_dssim=0.2, lr=gs.default_lr(extent=10.0))
+    if not args.no_reorder:
+        st.reorder()
     st.fit_capacity()
     target = torch.rand(3 * st.buf.total_pixels, device="cuda")
     for _ in range(args.iters):

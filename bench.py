@@ -52,7 +52,7 @@ def frame_pool(n):
 # --------------------------------------------------------------------------
 # algorithmic bytes (the minimum HBM traffic the method implies, FP32)
 
-def step_bytes(N, K, views, color_jac=False):
+def step_bytes(N, K, views, color_jac=False, grad_rows=False):
     """Algorithmic bytes of each stage of one mapping iteration over `views`,
     a list of (V, P, px, tiles) per view (V visible records, P pairs, px
     pixels): the minimum the method must move, every buffer touched once.
@@ -61,6 +61,9 @@ def step_bytes(N, K, views, color_jac=False):
     With color_jac (SH degree >= 1) the projection also writes 48 bytes per
     record (the colour's direction gradient and clamp flags) and the projection
     backward reads those instead of the 4(K-11) bytes of SH coefficients.
+    With grad_rows the projection backward writes only the gradient rows of
+    the Gaussians some view sees (4K per Gaussian of the visible union, plus a
+    one-byte mark per Gaussian) and Adam reads the gradient only there.
       project      12N means + 4(K-3) x visible union + per view (56V records + 4N tile counts,
                    + 48V with color_jac)
       sort         per view: 8N + 16V + 12P (scan, duplicate) + 24P (one read and one
@@ -77,7 +80,8 @@ def step_bytes(N, K, views, color_jac=False):
     Vu = min(float(N), float(Vs))
     cj = bool(color_jac) and K > 14  # SH degree >= 1
     b = {"project": 12 * N + 4 * (K - 3) * Vu, "sort": 0.0, "render_fwd": 0.0, "loss": 0.0, "render_bwd": 0.0,
-         "project_bwd": 4 * (11 if cj else K) * Vu + 4 * K * N, "adam": 28 * K * N}
+         "project_bwd": 4 * (11 if cj else K) * Vu + (4 * K * Vu + N if grad_rows else 4 * K * N),
+         "adam": 24 * K * N + 4 * K * Vu + N if grad_rows else 28 * K * N}
     for (V, P, px, tiles) in views:
         b["project"] += 56 * V + 4 * N + (48 * V if cj else 0)
         b["project_bwd"] += 48 * V if cj else 0
@@ -205,7 +209,7 @@ def kernel_source_sha(path):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def committed_profile(stage):
+def committed_profile(stage, kernel=None):
     """Counters of a stage's main kernel from its committed profiles/ summary
     (profiles/<kernel>_*.md), only while that summary's source hash matches
     the kernel source: DRAM bytes per launch and, where captured, issue-active
@@ -216,8 +220,8 @@ def committed_profile(stage):
     if src is None:
         return {}
     sha = kernel_source_sha(src)
-    kern = {"render_fwd": "k_render_fwd", "decode": "k_anchor_decode",
-            "decode_bwd": "k_anchor_decode_bwd"}.get(stage) or STAGE_KERNELS[stage][0]
+    kern = kernel or {"render_fwd": "k_render_fwd", "decode": "k_anchor_decode",
+                      "decode_bwd": "k_anchor_decode_bwd"}.get(stage) or STAGE_KERNELS[stage][0]
     for fn in sorted(glob.glob(os.path.join(ROOT, "profiles", kern + "_*.md"))):
         txt = open(fn).read()
         if not txt.startswith("# " + kern + " "):  # a summary names its kernel first
@@ -250,7 +254,7 @@ STAGE_KERNELS = {
     "loss": ["k_ssim_fwd", "k_ssim_bwd", "k_loss_final"],
     "render_bwd": ["k_render_bwd"],
     "project_bwd": ["k_project_bwd"],
-    "adam": ["k_adam"],
+    "adam": ["k_adam", "k_adam_rows"],
     "project_bwd_adam": ["k_project_bwd"],
 }
 # the kernel whose source a stage's committed profile summary is tied to
@@ -450,13 +454,16 @@ def run_corridor(args, world, dev):
 
     Vm, Pm = float(np.mean(vis)), float(np.mean(needed))
     ab = step_bytes(N_GAUSS, model.K, [(Vm, Pm, W * H, step.buf.total_tiles)],
-                    color_jac=step.buf.color_jac is not None)
+                    color_jac=step.buf.color_jac is not None, grad_rows=step.grad_rows)
     peak, peak_kind = measured_peaks()
     # the roofline entry is the stage (one C-ABI call) with the longest live time
     dom = max(stages, key=lambda nm: stage_ms[nm])
     achieved = ab[dom] / (stage_ms[dom] * 1e-3) / 1e9
-    prof = committed_profile(dom)
-    roof = {"kernel": "+".join(STAGE_KERNELS[dom]) if len(STAGE_KERNELS[dom]) <= 4 else dom + " stage",
+    kernels = STAGE_KERNELS[dom]
+    if dom == "adam":  # one of the two Adam kernels runs
+        kernels = ["k_adam_rows" if step.grad_rows else "k_adam"]
+    prof = committed_profile(dom, kernels[0])
+    roof = {"kernel": "+".join(kernels) if len(kernels) <= 4 else dom + " stage",
             "stage": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": prof.get("traffic"),
             "peak_kind": peak_kind + " (copy bandwidth)",
@@ -582,7 +589,7 @@ def run_chunk(args, world, dev):
     torch.cuda.synchronize()
 
     peak, _ = measured_peaks()
-    B = executed_bytes(step_bytes(n, model.K, per_view), STAGES)
+    B = executed_bytes(step_bytes(n, model.K, per_view, grad_rows=True), STAGES)
     return {"workload": "%d Gaussians (uniform, SH0), %d keyframes cycling 640x360..1600x900, "
                         "fwd+L1/D-SSIM+bwd+stats+Adam" % (n, nv),
             "layout": "Morton order of the means (gs_reorder at setup)",

@@ -392,6 +392,19 @@ gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, int32_t
                          const gs_stats *stats, gs_stream stream);
 
 /*
+ * gs_project_bwd (accumulate = 0) that writes only the gradient rows of the
+ * Gaussians some view sees: rows[g] (device, [grads->ld] bytes, 4-byte
+ * aligned) becomes 1 for those and 0 for every other row (padding included),
+ * whose gradient is zero and whose grads entries are left as they were.  For
+ * gs_adam_rows, which reads such a row's gradient as zero: the pair moves
+ * 8 bytes less per parameter element of the Gaussians no view sees.
+ */
+gs_status gs_project_bwd_rows(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                              const gs_raster_cfg *cfg, const gs_projected *proj, const void *ws,
+                              size_t ws_bytes, const float *loss_per_view, const gs_params *grads,
+                              const gs_stats *stats, uint8_t *rows, gs_stream stream);
+
+/*
  * gs_project_bwd followed by gs_adam without the gradient buffer: each
  * Gaussian's gradient (the projection chain from the per-record gradients in
  * ws, plus grads_in when set, plus the isotropic term's gradient
@@ -420,6 +433,17 @@ gs_status gs_project_bwd_adam(const gs_params *params, const gs_camera *cams, in
 gs_status gs_adam(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
                   const gs_params *exp_avg_sq, const float lr_groups[6], float beta1, float beta2,
                   float eps, int64_t step, const int64_t *step_device, gs_stream stream);
+
+/*
+ * gs_adam with the gradient of Gaussian g taken as zero, and grads not read
+ * there, where rows[g] == 0 (device, [params->ld] bytes, 4-byte aligned: the
+ * marks of gs_project_bwd_rows).  The same update as gs_adam after a
+ * backward that wrote those rows as zeros.
+ */
+gs_status gs_adam_rows(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
+                       const gs_params *exp_avg_sq, const uint8_t *rows, const float lr_groups[6],
+                       float beta1, float beta2, float eps, int64_t step, const int64_t *step_device,
+                       gs_stream stream);
 
 /*
  * Chunk scores and global decisions (Supp. E.1, E.2; Sec. 3.3.2) from the

@@ -364,7 +364,7 @@ GS_API gs_status gs_render_bwd(const gs_params *params, const gs_camera *cams, i
     if (grads)
         launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius, acc, nrec,
                            grads->data, accumulate, loss_per_view, want_stats ? stats->acc : nullptr,
-                           want_stats ? stats->ld : 0, (const float4 *)proj->color_jac, s);
+                           want_stats ? stats->ld : 0, (const float4 *)proj->color_jac, nullptr, s);
     return cuda_status(cudaGetLastError());
 }
 
@@ -435,14 +435,14 @@ GS_API gs_status gs_render_bwd_lists(const gs_params *params, const gs_camera *c
     if (grads)
         launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius, acc, nrec,
                            grads->data, accumulate, loss_per_view, want_stats ? stats->acc : nullptr,
-                           want_stats ? stats->ld : 0, (const float4 *)proj->color_jac, s);
+                           want_stats ? stats->ld : 0, (const float4 *)proj->color_jac, nullptr, s);
     return cuda_status(cudaGetLastError());
 }
 
-GS_API gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views,
-                                const gs_raster_cfg *cfg, const gs_projected *proj, const void *ws, size_t ws_bytes,
-                                const float *loss_per_view, const gs_params *grads, int32_t accumulate,
-                                const gs_stats *stats, gs_stream stream) {
+static gs_status project_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                             const gs_raster_cfg *cfg, const gs_projected *proj, const void *ws, size_t ws_bytes,
+                             const float *loss_per_view, const gs_params *grads, int32_t accumulate,
+                             const gs_stats *stats, uint8_t *rows, gs_stream stream) {
     ViewTable vt;
     RasterCfg rc;
     gs_status st = build_views(cams, n_views, cfg, vt, rc);
@@ -458,9 +458,26 @@ GS_API gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, 
     if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < need) return GS_ERR_INVALID;
     launch_project_bwd(params->data, params->n, params->ld, params->sh_degree, vt, rc, proj->radius,
                        (const float *)ws, nrec, grads->data, accumulate, loss_per_view,
-                       stats ? stats->acc : nullptr, stats ? stats->ld : 0, (const float4 *)proj->color_jac,
+                       stats ? stats->acc : nullptr, stats ? stats->ld : 0, (const float4 *)proj->color_jac, rows,
                        (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
+}
+
+GS_API gs_status gs_project_bwd(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                                const gs_raster_cfg *cfg, const gs_projected *proj, const void *ws, size_t ws_bytes,
+                                const float *loss_per_view, const gs_params *grads, int32_t accumulate,
+                                const gs_stats *stats, gs_stream stream) {
+    return project_bwd(params, cams, n_views, cfg, proj, ws, ws_bytes, loss_per_view, grads, accumulate, stats,
+                       nullptr, stream);
+}
+
+GS_API gs_status gs_project_bwd_rows(const gs_params *params, const gs_camera *cams, int32_t n_views,
+                                     const gs_raster_cfg *cfg, const gs_projected *proj, const void *ws,
+                                     size_t ws_bytes, const float *loss_per_view, const gs_params *grads,
+                                     const gs_stats *stats, uint8_t *rows, gs_stream stream) {
+    if (!rows || ((uintptr_t)rows & 3u)) return GS_ERR_INVALID;
+    return project_bwd(params, cams, n_views, cfg, proj, ws, ws_bytes, loss_per_view, grads, 0, stats, rows,
+                       stream);
 }
 
 GS_API gs_status gs_project_bwd_adam(const gs_params *params, const gs_camera *cams, int32_t n_views,
@@ -497,9 +514,9 @@ GS_API gs_status gs_project_bwd_adam(const gs_params *params, const gs_camera *c
     return cuda_status(cudaGetLastError());
 }
 
-GS_API gs_status gs_adam(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
-                         const gs_params *exp_avg_sq, const float lr_groups[6], float beta1, float beta2, float eps,
-                         int64_t step, const int64_t *step_device, gs_stream stream) {
+static gs_status adam(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
+                      const gs_params *exp_avg_sq, const float lr_groups[6], float beta1, float beta2, float eps,
+                      int64_t step, const int64_t *step_device, const uint8_t *rows, gs_stream stream) {
     gs_status st = check_params(params);
     if (st == GS_OK) st = check_params(grads);
     if (st == GS_OK) st = check_params(exp_avg);
@@ -512,8 +529,23 @@ GS_API gs_status gs_adam(const gs_params *params, const gs_params *grads, const 
         return GS_ERR_INVALID;
     if (step_device && ((uintptr_t)step_device & 7u)) return GS_ERR_INVALID;
     launch_adam(params->data, grads->data, exp_avg->data, exp_avg_sq->data, params->ld, GS_PLANES(params->sh_degree),
-                lr_groups, beta1, beta2, eps, step, (const long long *)step_device, (cudaStream_t)stream);
+                lr_groups, beta1, beta2, eps, step, (const long long *)step_device, rows, (cudaStream_t)stream);
     return cuda_status(cudaGetLastError());
+}
+
+GS_API gs_status gs_adam(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
+                         const gs_params *exp_avg_sq, const float lr_groups[6], float beta1, float beta2, float eps,
+                         int64_t step, const int64_t *step_device, gs_stream stream) {
+    return adam(params, grads, exp_avg, exp_avg_sq, lr_groups, beta1, beta2, eps, step, step_device, nullptr,
+                stream);
+}
+
+GS_API gs_status gs_adam_rows(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
+                              const gs_params *exp_avg_sq, const uint8_t *rows, const float lr_groups[6],
+                              float beta1, float beta2, float eps, int64_t step, const int64_t *step_device,
+                              gs_stream stream) {
+    if (!rows || ((uintptr_t)rows & 3u)) return GS_ERR_INVALID;
+    return adam(params, grads, exp_avg, exp_avg_sq, lr_groups, beta1, beta2, eps, step, step_device, rows, stream);
 }
 
 GS_API gs_status gs_prune_stats(const gs_stats *stats, int64_t n, int32_t n_views, float tau_d, float tau_p,

@@ -26,7 +26,7 @@ void launch_project(const float *P, long long n, long long ld, int D, const View
 void launch_project_bwd(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
                         const int *radius, const float *acc, long long nrec, float *G, int accumulate,
                         const float *loss_per_view, float *stats, long long stats_ld, const float4 *cj,
-                        cudaStream_t s);
+                        uint8_t *rows, cudaStream_t s);
 void launch_project_bwd_adam(float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
                              const int *radius, const float *acc, long long nrec, const float *G_in, float *m,
                              float *v, const float lr[6], float beta1, float beta2, float eps, long long step,
@@ -80,8 +80,10 @@ cudaError_t loss_static_scratch(void **out);
 cudaError_t launch_loss(const float *img, const float *target, int h, int w, float lambda, float *loss_out,
                         float *dL_dimg, void *ws, cudaStream_t s);
 
+// rows (nullable, [ld] bytes): where rows[i] == 0 the gradient of Gaussian i is zero and g is not read
 void launch_adam(float *p, const float *g, float *m, float *v, long long ld, int planes, const float lr[6],
-                 float beta1, float beta2, float eps, long long step, const long long *step_dev, cudaStream_t s);
+                 float beta1, float beta2, float eps, long long step, const long long *step_dev,
+                 const uint8_t *rows, cudaStream_t s);
 
 size_t reg_workspace_bytes();
 cudaError_t launch_geo(const float *depth, const float *prior, long long npx, float weight, float *loss, float *dL,

@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 3) k_pr
                                                      float *__restrict__ G, int accumulate,
                                                      const float *__restrict__ loss_per_view,
                                                      float *__restrict__ stats, long long stats_ld, FusedAdam fa,
-                                                     const float4 *__restrict__ cj) {
+                                                     const float4 *__restrict__ cj, uint8_t *__restrict__ rows) {
     constexpr int K = (D + 1) * (D + 1);
     if (ADAM && fa.step_dev) {  // bias corrections from the device step counter (graph replay)
         __shared__ float s_bc[2];
@@ -324,7 +324,15 @@ __global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 3) k_pr
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (!ADAM) {
         if (g >= ld) return;
-        if (g >= n) {  // padding: zero gradient
+        if (rows) {
+            // rows mode: a Gaussian no view sees has a zero gradient, which is marked instead
+            // of written (the Adam step reads it as zero)
+            bool any = false;
+            if (g < n)
+                for (int v = 0; v < vt.n_views; ++v) any |= radius[v * ld + g] > 0;
+            rows[g] = any ? 1 : 0;
+            if (!any) return;
+        } else if (g >= n) {  // padding: zero gradient
             if (!accumulate)
                 for (int k = 0; k < NP; ++k) G[k * ld + g] = 0.0f;
             return;
@@ -622,12 +630,13 @@ void launch_project(const float *P, long long n, long long ld, int D, const View
 void launch_project_bwd(const float *P, long long n, long long ld, int D, const ViewTable &vt, const RasterCfg &cfg,
                         const int *radius, const float *acc, long long nrec, float *G, int accumulate,
                         const float *loss_per_view, float *stats, long long stats_ld, const float4 *cj,
-                        cudaStream_t s) {
+                        uint8_t *rows, cudaStream_t s) {
     if (ld <= 0) return;
     const int blocks = (int)ceil_div(ld, 256);
     FusedAdam fa{};
 #define GS_PB(DD) k_project_bwd<DD, false><<<blocks, 256, 0, s>>>(const_cast<float *>(P), n, ld, vt, cfg, radius, acc, \
-                                                                   nrec, G, accumulate, loss_per_view, stats, stats_ld, fa, cj)
+                                                                   nrec, G, accumulate, loss_per_view, stats, stats_ld, fa, \
+                                                                   cj, rows)
     switch (D) {
         case 0: GS_PB(0); break;
         case 1: GS_PB(1); break;
@@ -667,7 +676,7 @@ void launch_project_bwd_adam(float *P, long long n, long long ld, int D, const V
         }                                                                                                       \
         k_project_bwd<DD, true><<<blocks, kFusedThreads, smem, s>>>(P, n, ld, vt, cfg, radius, acc, nrec,       \
                                                                     nullptr, 0,                                 \
-                                                          loss_per_view, stats, stats_ld, fa, nullptr);        \
+                                                          loss_per_view, stats, stats_ld, fa, nullptr, nullptr); \
     } while (0)
     switch (D) {
         case 0: GS_PBA(0); break;

@@ -89,7 +89,7 @@ EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspac
            "gs_voxel_table_reset", "gs_init_workspace_size", "gs_init_probability", "gs_init_insert",
            "gs_voxel_lookup", "gs_anchor_decode", "gs_anchor_decode_bwd", "gs_adam_flat",
            "gs_list_workspace_size", "gs_render_fwd_lists", "gs_render_bwd_lists", "gs_reorder_workspace_size",
-           "gs_reorder")
+           "gs_reorder", "gs_project_bwd_rows", "gs_adam_rows")
 
 _lib = None
 
@@ -128,6 +128,10 @@ def lib():
         L.gs_project_bwd.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), vp, sz, vp, P(Params), i32,
                                      P(Stats), vp]
         L.gs_adam.argtypes = [P(Params), P(Params), P(Params), P(Params), P(f32 * 6), f32, f32, f32, i64, vp, vp]
+        L.gs_project_bwd_rows.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), vp, sz, vp,
+                                          P(Params), P(Stats), vp, vp]
+        L.gs_adam_rows.argtypes = [P(Params), P(Params), P(Params), P(Params), vp, P(f32 * 6), f32, f32, f32, i64,
+                                   vp, vp]
         L.gs_project_bwd_adam.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), vp, sz, vp,
                                           P(Params), f32, P(Params), P(Params), P(f32 * 6), f32, f32, f32, i64, vp,
                                           P(Stats), vp]
@@ -206,6 +210,9 @@ class Config:
     # keep the colour's view-direction gradient per record (SH degree >= 1) for the backward:
     # None = where it moves fewer bytes than the backward's re-read of the SH coefficients
     color_jac: Optional[bool] = None
+    # optimising steps: the projection backward writes only the gradient rows of Gaussians some
+    # view sees and marks them; Adam reads the others as zero (None = wherever it applies)
+    grad_rows: Optional[bool] = None
 
     def c(self) -> RasterCfg:
         return RasterCfg(self.tile_w, self.tile_h, self.near_z, self.dilation, self.alpha_min, self.alpha_max,
@@ -465,11 +472,20 @@ def gs_render_bwd(model: GaussianModel, grads: GaussianModel, buf: Buffers, targ
 
 
 def gs_project_bwd(model: GaussianModel, grads: GaussianModel, buf: Buffers, accumulate=False, with_stats=True,
-                   stream=None):
+                   stream=None, rows=None):
     """The projection half of the backward, from the per-record gradients
-    that gs_render_bwd(grads=None) left in the workspace."""
+    that gs_render_bwd(grads=None) left in the workspace.  rows (a [ld] uint8
+    device tensor): write only the rows of Gaussians some view sees and mark
+    them there (gs_project_bwd_rows), for gs_adam(rows=...)."""
     arr = camera_array(buf.cams)
     st = buf.stats() if with_stats else None
+    if rows is not None:
+        assert not accumulate and rows.dtype == torch.uint8 and rows.numel() >= model.ld
+        _check(lib().gs_project_bwd_rows(C.byref(model.c()), arr, buf.n_views, C.byref(buf.cfg.c()),
+                                         C.byref(buf.projected()), _ptr(buf.bwd_ws), buf.bwd_ws.numel(),
+                                         _ptr(buf.loss), C.byref(grads.c()), None if st is None else C.byref(st),
+                                         _ptr(rows), _stream(stream)), "gs_project_bwd_rows")
+        return
     _check(lib().gs_project_bwd(C.byref(model.c()), arr, buf.n_views, C.byref(buf.cfg.c()), C.byref(buf.projected()),
                                 _ptr(buf.bwd_ws), buf.bwd_ws.numel(), _ptr(buf.loss), C.byref(grads.c()),
                                 int(bool(accumulate)), None if st is None else C.byref(st), _stream(stream)),
@@ -538,8 +554,14 @@ def gs_project_bwd_adam(model: GaussianModel, buf: Buffers, exp_avg: GaussianMod
 
 
 def gs_adam(model: GaussianModel, grads: GaussianModel, exp_avg: GaussianModel, exp_avg_sq: GaussianModel, lr,
-            step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None, step_device=None):
+            step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None, step_device=None, rows=None):
+    """rows: the marks of gs_project_bwd(rows=...); unmarked rows take a zero gradient."""
     lrs = (C.c_float * 6)(*[float(x) for x in lr])
+    if rows is not None:
+        _check(lib().gs_adam_rows(C.byref(model.c()), C.byref(grads.c()), C.byref(exp_avg.c()),
+                                  C.byref(exp_avg_sq.c()), _ptr(rows), C.byref(lrs), beta1, beta2, eps, int(step),
+                                  _ptr(step_device), _stream(stream)), "gs_adam_rows")
+        return
     _check(lib().gs_adam(C.byref(model.c()), C.byref(grads.c()), C.byref(exp_avg.c()), C.byref(exp_avg_sq.c()),
                          C.byref(lrs), beta1, beta2, eps, int(step), _ptr(step_device), _stream(stream)), "gs_adam")
 
@@ -683,6 +705,7 @@ class MappingStep:
         self.with_stats = with_stats
         self._grads = None  # allocated on first use: the fused path needs no gradient buffer
         self._reorder_ws = None
+        self._rows = None
         # Adam moments: zero, or carried over (e.g. through gs_densify_prune)
         self.exp_avg, self.exp_avg_sq = moments if moments is not None else (model.like(), model.like())
         assert self.exp_avg.ld == model.ld and self.exp_avg_sq.ld == model.ld
@@ -731,6 +754,21 @@ class MappingStep:
         else:
             gs_render_fwd(b, stream)
 
+    @property
+    def grad_rows(self):
+        """Whether an optimising step writes only the gradient rows of the Gaussians some
+        view sees (gs_project_bwd_rows) and Adam reads the others as zero (gs_adam_rows);
+        not with the isotropy term, whose gradient reaches every Gaussian."""
+        if self.fused_adam or self.lists is not None or self.lambda_iso > 0:
+            return False
+        return self.cfg.grad_rows is not False
+
+    @property
+    def rows(self) -> torch.Tensor:
+        if self._rows is None or self._rows.numel() != self.model.ld:
+            self._rows = torch.zeros(self.model.ld, dtype=torch.uint8, device=self.model.data.device)
+        return self._rows
+
     def _losses_and_backward(self, target, stream=None):
         gs_loss(self.buf, target, self.lambda_dssim, stream)
         if self.lists is not None:
@@ -768,11 +806,24 @@ class MappingStep:
         return t
 
     def step(self, target, stream=None, optimize=True):
-        """One iteration on device-resident targets (frame layout)."""
+        """One iteration on device-resident targets (frame layout).  An optimising step
+        with grad_rows leaves the gradient rows of Gaussians no view sees as they were."""
         self.forward(stream)
         if optimize and self.fused_adam:
             self.step_count += 1
             self._losses_backward_adam(target, stream, step=self.step_count)
+            return self.buf.loss
+        if optimize and self.grad_rows:
+            gs_loss(self.buf, target, self.lambda_dssim, stream)
+            if self.depth_prior is not None:
+                gs_geo_loss(self.buf, self.depth_prior, self.lambda_geo, self.geo_loss, self.dL_ddepth, self.reg_ws,
+                            stream)
+            gs_render_bwd(self.model, None, self.buf, target, self.tau_err, with_stats=self.with_stats,
+                          dL_ddepth=self.dL_ddepth, stream=stream)
+            gs_project_bwd(self.model, self.grads, self.buf, with_stats=self.with_stats, stream=stream, rows=self.rows)
+            self.step_count += 1
+            gs_adam(self.model, self.grads, self.exp_avg, self.exp_avg_sq, self.lr, self.step_count, stream=stream,
+                    rows=self.rows)
             return self.buf.loss
         self._losses_and_backward(target, stream)
         if optimize:
@@ -848,12 +899,13 @@ class MappingStep:
                                     step_device=self.step_dev)
                 mark(6)
             else:
-                grads = self.grads
-                gs_project_bwd(self.model, grads, self.buf, with_stats=self.with_stats)
+                grads, rows = self.grads, (self.rows if self.grad_rows else None)
+                gs_project_bwd(self.model, grads, self.buf, with_stats=self.with_stats, rows=rows)
                 if self.lambda_iso > 0:
                     gs_iso_loss(self.model, self.lambda_iso, self.iso_loss, grads, self.reg_ws)
                 mark(6)
-                gs_adam(self.model, grads, self.exp_avg, self.exp_avg_sq, self.lr, 1, step_device=self.step_dev)
+                gs_adam(self.model, grads, self.exp_avg, self.exp_avg_sq, self.lr, 1, step_device=self.step_dev,
+                        rows=rows)
                 mark(7)
         torch.cuda.current_stream(dev).wait_stream(side)
         return graph

@@ -116,6 +116,22 @@ def test_reorder_arguments_rejected_on_host():
     assert L.gs_reorder(C.byref(p), ok, 2, 2, 1024, need, None) == 1  # misaligned perm
 
 
+def test_rows_arguments_rejected_on_host():
+    L = gs.lib()
+    cam = gs.camera_array([scenes.pinhole(64, 48, 60.0)])
+    cfg = gs.Config().c()
+    lrs = (C.c_float * 6)(*([1e-3] * 6))
+    p = [gs.Params(256 * (k + 1), 10, 12, 0) for k in range(4)]
+    proj = gs.Projected(16, 32, 48, 64, 80, 12)
+    n = C.c_size_t()
+    L.gs_bwd_workspace_size(12, C.byref(n))
+    for rows in (None, 4098):  # no marks, misaligned marks
+        assert L.gs_adam_rows(C.byref(p[0]), C.byref(p[1]), C.byref(p[2]), C.byref(p[3]), rows, C.byref(lrs), 0.9,
+                              0.999, 1e-15, 1, None, None) == 1
+        assert L.gs_project_bwd_rows(C.byref(p[0]), cam, 1, C.byref(cfg), C.byref(proj), 8192, n.value, None,
+                                     C.byref(p[1]), None, rows, None) == 1
+
+
 def test_color_jac_policy():
     """The automatic choice keeps the colour gradient exactly where its bytes, 96 per
     visible record at most (written and read back), are below the 4 (K - 11) bytes of

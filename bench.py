@@ -52,7 +52,7 @@ def frame_pool(n):
 # --------------------------------------------------------------------------
 # algorithmic bytes (the minimum HBM traffic the method implies, FP32)
 
-def step_bytes(N, K, views, color_jac=False, grad_rows=False):
+def step_bytes(N, K, views, color_jac=False, grad_rows=False, adam_split=False):
     """Algorithmic bytes of each stage of one mapping iteration over `views`,
     a list of (V, P, px, tiles) per view (V visible records, P pairs, px
     pixels): the minimum the method must move, every buffer touched once.
@@ -64,6 +64,10 @@ def step_bytes(N, K, views, color_jac=False, grad_rows=False):
     With grad_rows the projection backward writes only the gradient rows of
     the Gaussians some view sees (4K per Gaussian of the visible union, plus a
     one-byte mark per Gaussian) and Adam reads the gradient only there.
+    With adam_split (and grad_rows) the Adam stage updates the marked rows
+    only (28 bytes per element of the visible union, the marks) and a
+    background kernel beside the other stages the rest ("adam_unseen": 24
+    bytes per element of the others, the radii).
       project      12N means + 4(K-3) x visible union + per view (56V records + 4N tile counts,
                    + 48V with color_jac)
       sort         per view: 8N + 16V + 12P (scan, duplicate) + 24P (one read and one
@@ -82,6 +86,9 @@ def step_bytes(N, K, views, color_jac=False, grad_rows=False):
     b = {"project": 12 * N + 4 * (K - 3) * Vu, "sort": 0.0, "render_fwd": 0.0, "loss": 0.0, "render_bwd": 0.0,
          "project_bwd": 4 * (11 if cj else K) * Vu + (4 * K * Vu + N if grad_rows else 4 * K * N),
          "adam": 24 * K * N + 4 * K * Vu + N if grad_rows else 28 * K * N}
+    if grad_rows and adam_split:
+        b["adam"] = 28 * K * Vu + N
+        b["adam_unseen"] = 24 * K * (N - Vu) + 4 * N * len(views)
     for (V, P, px, tiles) in views:
         b["project"] += 56 * V + 4 * N + (48 * V if cj else 0)
         b["project_bwd"] += 48 * V if cj else 0
@@ -96,8 +103,9 @@ def step_bytes(N, K, views, color_jac=False, grad_rows=False):
 
 
 def executed_bytes(b, stages):
-    """Total over the stages this run executed (the fused stage replaces two)."""
-    return sum(b[s] for s in stages)
+    """Total over the stages this run executed (the fused stage replaces two), with the
+    background Adam of the unseen Gaussians when the Adam stage was split."""
+    return sum(b[s] for s in stages) + (b.get("adam_unseen", 0) if "adam" in stages else 0)
 
 
 # --------------------------------------------------------------------------
@@ -454,7 +462,8 @@ def run_corridor(args, world, dev):
 
     Vm, Pm = float(np.mean(vis)), float(np.mean(needed))
     ab = step_bytes(N_GAUSS, model.K, [(Vm, Pm, W * H, step.buf.total_tiles)],
-                    color_jac=step.buf.color_jac is not None, grad_rows=step.grad_rows)
+                    color_jac=step.buf.color_jac is not None, grad_rows=step.grad_rows,
+                    adam_split=step.adam_split)
     peak, peak_kind = measured_peaks()
     # the roofline entry is the stage (one C-ABI call) with the longest live time
     dom = max(stages, key=lambda nm: stage_ms[nm])
@@ -482,12 +491,13 @@ def run_corridor(args, world, dev):
         "e2e": {"value": round(replica_throughput(args.steps, world, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": 3 * W * H * 4, "d2h_bytes_per_step": 4, "wall_s": round(wall_e2e, 3)},
         "gpu_launches": gs.launches_per_step(step.buf.total_tiles, views=1, lambda_dssim=LAMBDA,
-                                             segment=step.cfg.segment, fused_adam=step.fused_adam) * args.steps,
+                                             segment=step.cfg.segment, fused_adam=step.fused_adam,
+                                             adam_split=step.adam_split) * args.steps,
         "roofline": roof,
         "step_hbm": {"algorithmic_bytes": int(total_bytes), "stages": stages,
                      "frac_of_peak": round(total_bytes / (ms / args.steps * 1e-3) / 1e9 / peak, 4)},
         "stages_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "stage_bytes": {k: int(ab[k]) for k in stages},
+        "stage_bytes": {k: int(ab[k]) for k in stages + (["adam_unseen"] if "adam_unseen" in ab else [])},
         "split": {"segment": step.cfg.segment, "frames_without_split": split_fallback},
         "layout": layout,
         "visible_mean": int(Vm), "pairs_mean": int(Pm),
@@ -589,7 +599,7 @@ def run_chunk(args, world, dev):
     torch.cuda.synchronize()
 
     peak, _ = measured_peaks()
-    B = executed_bytes(step_bytes(n, model.K, per_view, grad_rows=True), STAGES)
+    B = executed_bytes(step_bytes(n, model.K, per_view, grad_rows=True, adam_split=True), STAGES)
     return {"workload": "%d Gaussians (uniform, SH0), %d keyframes cycling 640x360..1600x900, "
                         "fwd+L1/D-SSIM+bwd+stats+Adam" % (n, nv),
             "layout": "Morton order of the means (gs_reorder at setup)",

@@ -446,6 +446,21 @@ gs_status gs_adam_rows(const gs_params *params, const gs_params *grads, const gs
                        gs_stream stream);
 
 /*
+ * gs_adam_rows in two parts that write disjoint elements.  part 2 updates,
+ * with a zero gradient, only the Gaussians whose radius ([n_views][ld] int32
+ * of gs_project, 16-byte aligned) is 0 in every view; it reads neither grads
+ * nor rows (either may be NULL), so it may run right after gs_project, on
+ * another stream, beside the rest of the step: it is a background kernel of
+ * one CTA per SM, with streaming cache hints.  part 1 updates only the rows
+ * marked in rows (gs_project_bwd_rows).  Part 1 after the backward and part 2
+ * after the same projection give gs_adam_rows' result exactly.
+ */
+gs_status gs_adam_part(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
+                       const gs_params *exp_avg_sq, const uint8_t *rows, const int32_t *radius,
+                       int32_t n_views, int32_t part, const float lr_groups[6], float beta1, float beta2,
+                       float eps, int64_t step, const int64_t *step_device, gs_stream stream);
+
+/*
  * Chunk scores and global decisions (Supp. E.1, E.2; Sec. 3.3.2) from the
  * accumulators of one chunk: S_d = kappa / n_views; L = log(1 + gamma);
  * S_p = (L - min L) / (max L - min L) over Gaussians with |Omega| > 0 (0 for

@@ -516,7 +516,8 @@ GS_API gs_status gs_project_bwd_adam(const gs_params *params, const gs_camera *c
 
 static gs_status adam(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
                       const gs_params *exp_avg_sq, const float lr_groups[6], float beta1, float beta2, float eps,
-                      int64_t step, const int64_t *step_device, const uint8_t *rows, gs_stream stream) {
+                      int64_t step, const int64_t *step_device, const uint8_t *rows, gs_stream stream,
+                      int part = 0, const int32_t *radius = nullptr, int n_views = 0) {
     gs_status st = check_params(params);
     if (st == GS_OK) st = check_params(grads);
     if (st == GS_OK) st = check_params(exp_avg);
@@ -529,7 +530,8 @@ static gs_status adam(const gs_params *params, const gs_params *grads, const gs_
         return GS_ERR_INVALID;
     if (step_device && ((uintptr_t)step_device & 7u)) return GS_ERR_INVALID;
     launch_adam(params->data, grads->data, exp_avg->data, exp_avg_sq->data, params->ld, GS_PLANES(params->sh_degree),
-                lr_groups, beta1, beta2, eps, step, (const long long *)step_device, rows, (cudaStream_t)stream);
+                lr_groups, beta1, beta2, eps, step, (const long long *)step_device, rows, (cudaStream_t)stream, part,
+                radius, n_views);
     return cuda_status(cudaGetLastError());
 }
 
@@ -546,6 +548,22 @@ GS_API gs_status gs_adam_rows(const gs_params *params, const gs_params *grads, c
                               gs_stream stream) {
     if (!rows || ((uintptr_t)rows & 3u)) return GS_ERR_INVALID;
     return adam(params, grads, exp_avg, exp_avg_sq, lr_groups, beta1, beta2, eps, step, step_device, rows, stream);
+}
+
+GS_API gs_status gs_adam_part(const gs_params *params, const gs_params *grads, const gs_params *exp_avg,
+                              const gs_params *exp_avg_sq, const uint8_t *rows, const int32_t *radius,
+                              int32_t n_views, int32_t part, const float lr_groups[6], float beta1, float beta2,
+                              float eps, int64_t step, const int64_t *step_device, gs_stream stream) {
+    if (part == 1) {
+        if (!rows || ((uintptr_t)rows & 3u)) return GS_ERR_INVALID;
+    } else if (part == 2) {
+        if (!radius || ((uintptr_t)radius & 15u) || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_INVALID;
+        if (!grads) grads = params;  // not read
+    } else {
+        return GS_ERR_INVALID;
+    }
+    return adam(params, grads, exp_avg, exp_avg_sq, lr_groups, beta1, beta2, eps, step, step_device, rows, stream,
+                part, radius, n_views);
 }
 
 GS_API gs_status gs_prune_stats(const gs_stats *stats, int64_t n, int32_t n_views, float tau_d, float tau_p,

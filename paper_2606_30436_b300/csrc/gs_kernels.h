@@ -80,10 +80,13 @@ cudaError_t loss_static_scratch(void **out);
 cudaError_t launch_loss(const float *img, const float *target, int h, int w, float lambda, float *loss_out,
                         float *dL_dimg, void *ws, cudaStream_t s);
 
-// rows (nullable, [ld] bytes): where rows[i] == 0 the gradient of Gaussian i is zero and g is not read
+// rows (nullable, [ld] bytes): where rows[i] == 0 the gradient of Gaussian i is zero and g is not read.
+// part (with rows): 0 every row, 1 the marked rows only; part 2: only the Gaussians whose radius
+// ([n_views][ld]) is 0 in every view, rows and g unused.
 void launch_adam(float *p, const float *g, float *m, float *v, long long ld, int planes, const float lr[6],
                  float beta1, float beta2, float eps, long long step, const long long *step_dev,
-                 const uint8_t *rows, cudaStream_t s);
+                 const uint8_t *rows, cudaStream_t s, int part = 0, const int *radius = nullptr,
+                 int n_views = 0);
 
 size_t reg_workspace_bytes();
 cudaError_t launch_geo(const float *depth, const float *prior, long long npx, float weight, float *loss, float *dL,

@@ -89,7 +89,8 @@ EXPORTS = ("gs_status_string", "gs_version", "gs_view_layout", "gs_sort_workspac
            "gs_voxel_table_reset", "gs_init_workspace_size", "gs_init_probability", "gs_init_insert",
            "gs_voxel_lookup", "gs_anchor_decode", "gs_anchor_decode_bwd", "gs_adam_flat",
            "gs_list_workspace_size", "gs_render_fwd_lists", "gs_render_bwd_lists", "gs_reorder_workspace_size",
-           "gs_reorder", "gs_project_bwd_rows", "gs_adam_rows")
+           "gs_reorder", "gs_project_bwd_rows", "gs_adam_rows",
+           "gs_adam_part")
 
 _lib = None
 
@@ -132,6 +133,8 @@ def lib():
                                           P(Params), P(Stats), vp, vp]
         L.gs_adam_rows.argtypes = [P(Params), P(Params), P(Params), P(Params), vp, P(f32 * 6), f32, f32, f32, i64,
                                    vp, vp]
+        L.gs_adam_part.argtypes = [P(Params), P(Params), P(Params), P(Params), vp, vp, i32, i32, P(f32 * 6), f32,
+                                   f32, f32, i64, vp, vp]
         L.gs_project_bwd_adam.argtypes = [P(Params), P(Camera), i32, P(RasterCfg), P(Projected), vp, sz, vp,
                                           P(Params), f32, P(Params), P(Params), P(f32 * 6), f32, f32, f32, i64, vp,
                                           P(Stats), vp]
@@ -213,6 +216,9 @@ class Config:
     # optimising steps: the projection backward writes only the gradient rows of Gaussians some
     # view sees and marks them; Adam reads the others as zero (None = wherever it applies)
     grad_rows: Optional[bool] = None
+    # captured steps with grad_rows: the Adam of the Gaussians no view sees on a second stream,
+    # beside the sort, compositing and losses (None = on)
+    adam_overlap: Optional[bool] = None
 
     def c(self) -> RasterCfg:
         return RasterCfg(self.tile_w, self.tile_h, self.near_z, self.dilation, self.alpha_min, self.alpha_max,
@@ -566,6 +572,18 @@ def gs_adam(model: GaussianModel, grads: GaussianModel, exp_avg: GaussianModel, 
                          C.byref(lrs), beta1, beta2, eps, int(step), _ptr(step_device), _stream(stream)), "gs_adam")
 
 
+def gs_adam_part(model: GaussianModel, grads, exp_avg: GaussianModel, exp_avg_sq: GaussianModel, buf: Buffers,
+                 part, lr, step, rows=None, beta1=0.9, beta2=0.999, eps=1e-15, stream=None, step_device=None):
+    """One of the two disjoint parts of gs_adam(rows=...): part 2 the Gaussians no view of
+    buf sees (from the projection's radii; runs right after gs_project), part 1 the rows
+    marked by gs_project_bwd(rows=...)."""
+    lrs = (C.c_float * 6)(*[float(x) for x in lr])
+    _check(lib().gs_adam_part(C.byref(model.c()), None if grads is None else C.byref(grads.c()),
+                              C.byref(exp_avg.c()), C.byref(exp_avg_sq.c()), _ptr(rows), _ptr(buf.radius),
+                              buf.n_views, int(part), C.byref(lrs), beta1, beta2, eps, int(step), _ptr(step_device),
+                              _stream(stream)), "gs_adam_part")
+
+
 def gs_prune_stats(stats_acc: torch.Tensor, n, n_views, scores: dict, ws: torch.Tensor, tau_d=5.0, tau_p=0.99,
                    stream=None):
     st = Stats(stats_acc.data_ptr(), stats_acc.shape[1])
@@ -706,6 +724,7 @@ class MappingStep:
         self._grads = None  # allocated on first use: the fused path needs no gradient buffer
         self._reorder_ws = None
         self._rows = None
+        self._adam_stream = None
         # Adam moments: zero, or carried over (e.g. through gs_densify_prune)
         self.exp_avg, self.exp_avg_sq = moments if moments is not None else (model.like(), model.like())
         assert self.exp_avg.ld == model.ld and self.exp_avg_sq.ld == model.ld
@@ -762,6 +781,12 @@ class MappingStep:
         if self.fused_adam or self.lists is not None or self.lambda_iso > 0:
             return False
         return self.cfg.grad_rows is not False
+
+    @property
+    def adam_split(self):
+        """Whether a captured step runs the Adam of the Gaussians no view sees (which needs only
+        the projection) on a second stream beside the rest of the step."""
+        return self.grad_rows and self.cfg.adam_overlap is not False
 
     @property
     def rows(self) -> torch.Tensor:
@@ -879,6 +904,20 @@ class MappingStep:
             mark(0)
             gs_project(self.model, b)
             mark(1)
+            split = self.adam_split
+            if split:
+                # Adam of the Gaussians no view sees needs only the projection: it runs on a
+                # second stream beside the rest of the step (little DRAM traffic)
+                if self._adam_stream is None:
+                    self._adam_stream = torch.cuda.Stream(device=dev)
+                fork = torch.cuda.Event()
+                fork.record(side)
+                self._adam_stream.wait_event(fork)
+                with torch.cuda.stream(self._adam_stream):
+                    gs_adam_part(self.model, None, self.exp_avg, self.exp_avg_sq, self.buf, 2, self.lr, 1,
+                                 step_device=self.step_dev)
+                join = torch.cuda.Event()
+                join.record(self._adam_stream)
             gs_sort(b)
             mark(2)
             gs_render_fwd(b)
@@ -904,9 +943,15 @@ class MappingStep:
                 if self.lambda_iso > 0:
                     gs_iso_loss(self.model, self.lambda_iso, self.iso_loss, grads, self.reg_ws)
                 mark(6)
-                gs_adam(self.model, grads, self.exp_avg, self.exp_avg_sq, self.lr, 1, step_device=self.step_dev,
-                        rows=rows)
-                mark(7)
+                if split:
+                    gs_adam_part(self.model, grads, self.exp_avg, self.exp_avg_sq, self.buf, 1, self.lr, 1,
+                                 rows=rows, step_device=self.step_dev)
+                    mark(7)
+                    side.wait_event(join)
+                else:
+                    gs_adam(self.model, grads, self.exp_avg, self.exp_avg_sq, self.lr, 1, step_device=self.step_dev,
+                            rows=rows)
+                    mark(7)
         torch.cuda.current_stream(dev).wait_stream(side)
         return graph
 
@@ -954,18 +999,19 @@ class MappingStep:
         return needed
 
 
-def launches_per_step(total_tiles, views=1, lambda_dssim=0.2, segment=512, fused_adam=False):
+def launches_per_step(total_tiles, views=1, lambda_dssim=0.2, segment=512, fused_adam=False, adam_split=False):
     """Kernel launches of the library in one mapping iteration (memsets not
     counted): project 1; sort 3 (visible records) + 4 depth passes (+ 1 view
     pass with several views) + 5
     (pair offsets, emission) + 1 per tile-bit pass (or 1 unpack for a single
     tile) + 3 (render schedule); render 1 (4 with the split: plan, segments,
     combine, re-runs); loss 3 (2 when lambda = 0) per view; backward 2
-    (compositing, projection); Adam 1 unless fused into the projection backward."""
+    (compositing, projection); Adam 1 unless fused into the projection backward (2 when split
+    into the seen rows and the background part)."""
     tile_bits = 0
     while (1 << tile_bits) < total_tiles:
         tile_bits += 1
     tile_passes = (tile_bits + 7) // 8
     sort = 3 + 4 + (1 if views > 1 else 0) + 5 + (tile_passes if tile_passes else 1) + 3
     loss = (3 if lambda_dssim > 0 else 2) * views
-    return 1 + sort + (4 if segment else 1) + loss + 2 + (0 if fused_adam else 1)
+    return 1 + sort + (4 if segment else 1) + loss + 2 + (0 if fused_adam else 2 if adam_split else 1)

@@ -125,6 +125,15 @@ def test_rows_arguments_rejected_on_host():
     proj = gs.Projected(16, 32, 48, 64, 80, 12)
     n = C.c_size_t()
     L.gs_bwd_workspace_size(12, C.byref(n))
+    rad_ok = 1024
+    args = lambda rows, rad, nv, part: (C.byref(p[0]), C.byref(p[1]), C.byref(p[2]), C.byref(p[3]), rows, rad, nv,
+                                        part, C.byref(lrs), 0.9, 0.999, 1e-15, 1, None, None)
+    assert L.gs_adam_part(*args(4096, rad_ok, 1, 0)) == 1      # part 0 is gs_adam_rows
+    assert L.gs_adam_part(*args(4096, rad_ok, 1, 3)) == 1
+    assert L.gs_adam_part(*args(None, rad_ok, 1, 1)) == 1      # part 1 needs the marks
+    assert L.gs_adam_part(*args(None, 1028, 1, 2)) == 1        # radii not 16-byte aligned
+    assert L.gs_adam_part(*args(None, rad_ok, 0, 2)) == 1      # no view
+    assert L.gs_adam_part(*args(None, None, 1, 2)) == 1        # no radii
     for rows in (None, 4098):  # no marks, misaligned marks
         assert L.gs_adam_rows(C.byref(p[0]), C.byref(p[1]), C.byref(p[2]), C.byref(p[3]), rows, C.byref(lrs), 0.9,
                               0.999, 1e-15, 1, None, None) == 1

@@ -71,3 +71,16 @@ def test_grad_rows_bytes():
     assert b0["project_bwd"] - b1["project_bwd"] == 4 * K * (N - V) - N
     assert b0["adam"] - b1["adam"] == 4 * K * (N - V) - N
     assert b1["project"] == b0["project"] and b1["render_bwd"] == b0["render_bwd"]
+
+
+def test_adam_split_bytes():
+    """The split Adam moves the same bytes as the marked-rows Adam, the unseen Gaussians' share
+    in the background kernel (which reads the radii instead of the marks), counted once."""
+    N, K, V, P, px, tiles = 1_000_000, 59, 494_279, 1_177_411, 921_600, 3600
+    b1 = bench.step_bytes(N, K, [(V, P, px, tiles)], color_jac=True, grad_rows=True)
+    b2 = bench.step_bytes(N, K, [(V, P, px, tiles)], color_jac=True, grad_rows=True, adam_split=True)
+    assert b2["adam"] == 28 * K * V + N
+    assert b2["adam_unseen"] == 24 * K * (N - V) + 4 * N
+    assert b2["adam"] + b2["adam_unseen"] == b1["adam"] + 4 * N
+    assert bench.executed_bytes(b2, bench.STAGES) == sum(b2[s] for s in bench.STAGES) + b2["adam_unseen"]
+    assert "adam_unseen" not in b1

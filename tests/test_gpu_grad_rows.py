@@ -82,6 +82,72 @@ def test_rows_bit_identical_on_one_backward(multi, D, device_step):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("multi", [False, True])
+def test_adam_parts_equal_adam_rows(multi):
+    """Part 2 (the Gaussians no view sees, from the radii alone) and part 1 (the marked rows)
+    write disjoint elements and together give gs_adam_rows bit for bit."""
+    scene, cams = _case(multi, 3)
+    target = _target(scene, cams)
+    st = gs.MappingStep(gs.GaussianModel.from_scene(scene), cams, gs.Config(), with_stats=False)
+    st.fit_capacity(slack=2.0)
+    st.forward()
+    gs.gs_loss(st.buf, target, 0.2)
+    gs.gs_render_bwd(st.model, None, st.buf, target, with_stats=False)
+    grads = st.model.like()
+    rows = torch.zeros(st.model.ld, dtype=torch.uint8, device="cuda")
+    gs.gs_project_bwd(st.model, grads, st.buf, with_stats=False, rows=rows)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    m0 = torch.randn(st.model.data.shape, generator=g, device="cuda") * 1e-3
+    v0 = torch.rand(st.model.data.shape, generator=g, device="cuda") * 1e-6
+    step_dev = torch.full((1,), 3, dtype=torch.int64, device="cuda")
+    out = []
+    for split in (False, True):
+        p, m, v = st.model.like(), st.model.like(), st.model.like()
+        p.data.copy_(st.model.data)
+        m.data.copy_(m0)
+        v.data.copy_(v0)
+        if split:
+            gs.gs_adam_part(p, None, m, v, st.buf, 2, st.lr, 3, step_device=step_dev)
+            p2 = p.data.clone()
+            seen = rows.bool()
+            assert torch.equal(p2[:, seen], st.model.data[:, seen])  # part 2 left the seen rows alone
+            gs.gs_adam_part(p, grads, m, v, st.buf, 1, st.lr, 3, rows=rows, step_device=step_dev)
+            assert torch.equal(p.data[:, ~seen], p2[:, ~seen])        # part 1 left the unseen rows alone
+        else:
+            gs.gs_adam(p, grads, m, v, st.lr, 3, step_device=step_dev, rows=rows)
+        out.append((p.data, m.data, v.data))
+    torch.cuda.synchronize()
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
+
+
+def test_overlapped_graph_matches_serial_graph():
+    """The captured step with the unseen Gaussians' Adam on a second stream against the same
+    step captured on one stream (the tolerances of two runs, atomics in the backward)."""
+    scene, cams = _case(False, 3)
+    target = _target(scene, cams)
+    p0 = gs.GaussianModel.from_scene(scene).data
+    runs = []
+    for overlap in (True, False):
+        st = gs.MappingStep(gs.GaussianModel.from_scene(scene), cams, gs.Config(adam_overlap=overlap),
+                            lr=gs.default_lr(extent=5.0))
+        st.fit_capacity(slack=2.0)
+        g = st.capture(target)
+        for _ in range(3):
+            st.replay(g)
+        torch.cuda.synchronize()
+        st.check_status()
+        runs.append(st)
+    a, b = runs
+    n = a.model.n
+    assert rel_l2(a.exp_avg.data[:, :n].cpu().numpy(), b.exp_avg.data[:, :n].cpu().numpy()) < 1e-4
+    da = (a.model.data - p0)[:, :n].cpu().numpy()
+    db = (b.model.data - p0)[:, :n].cpu().numpy()
+    close = np.abs(da - db) <= 1e-6 + 1e-4 * np.abs(db)
+    assert close.mean() > 0.999, close.mean()
+    assert torch.equal(a.model.data[:, n:], p0[:, n:])
+
+
 def _run(scene, cams, target, rows, iters, graph, lambda_iso=0.0):
     st = gs.MappingStep(gs.GaussianModel.from_scene(scene), cams, gs.Config(grad_rows=rows),
                         lr=gs.default_lr(extent=5.0), lambda_iso=lambda_iso)

@@ -228,8 +228,8 @@ def committed_profile(stage, kernel=None):
     if src is None:
         return {}
     sha = kernel_source_sha(src)
-    kern = kernel or {"render_fwd": "k_render_fwd", "decode": "k_anchor_decode",
-                      "decode_bwd": "k_anchor_decode_bwd"}.get(stage) or STAGE_KERNELS[stage][0]
+    kern = kernel or {"render_fwd": "k_render_fwd", "decode": "k_anchor_decode", "decode_bwd": "k_anchor_decode_bwd",
+                      "sort": "sort_stage"}.get(stage) or STAGE_KERNELS[stage][0]
     for fn in sorted(glob.glob(os.path.join(ROOT, "profiles", kern + "_*.md"))):
         txt = open(fn).read()
         if not txt.startswith("# " + kern + " "):  # a summary names its kernel first

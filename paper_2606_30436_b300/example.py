@@ -36,6 +36,8 @@ def main():
     ap.add_argument("--keyframe-size", type=int, nargs=2, default=(360, 640), metavar=("H", "W"))
     ap.add_argument("--segment", type=int, default=None,
                     help="split length of long tile lists (default: 512 for a corridor view, none for a chunk)")
+    ap.add_argument("--graph", action="store_true",
+                    help="capture the iteration in a CUDA graph and replay it (as the benchmark does)")
     ap.add_argument("--no-reorder", action="store_true",
                     help="keep the scene's row order (default: the Morton order of the means, gs_reorder)")
     args = ap.parse_args()
@@ -89,8 +91,13 @@ def main():
         st.reorder()
     st.fit_capacity()
     target = torch.rand(3 * st.buf.total_pixels, device="cuda")
-    for _ in range(args.iters):
-        st.step(target)
+    if args.graph:
+        g = st.capture(target)
+        for _ in range(args.iters):
+            st.replay(g)
+    else:
+        for _ in range(args.iters):
+            st.step(target)
     torch.cuda.synchronize()
     st.check_status()
     print("visible %d pairs %d loss %.6f" % (int(st.buf.counts[0]), int(st.buf.counts[1]), float(st.buf.loss.sum())))

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(256) k_adam(float4 *__restrict__ p, const floa
                                                float4 *__restrict__ m, float4 *__restrict__ v, long long ld4,
                                                long long total4, AdamLr lr, float b1, float b2, float inv_bc1,
                                                float inv_sqrt_bc2, float eps, const long long *__restrict__ step_dev) {
+    griddep_wait();
     if (step_dev) {  // bias corrections from the device step counter (graph replay)
         __shared__ float s_bc[2];
         if (threadIdx.x == 0) {
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(256) k_adam_rows(float4 *__restrict__ p, const
                                                     float inv_sqrt_bc2, float eps,
                                                     const long long *__restrict__ step_dev,
                                                     const uint32_t *__restrict__ rows4, int part) {
+    griddep_wait();
     if (step_dev) {
         __shared__ float s_bc[2];
         if (threadIdx.x == 0) {
@@ -157,6 +159,7 @@ __global__ void __launch_bounds__(kBgThreads, 1) k_adam_unseen(float4 *__restric
                                                                float inv_sqrt_bc2, float eps,
                                                                const long long *__restrict__ step_dev,
                                                                const int4 *__restrict__ radius4, int n_views) {
+    griddep_wait();
     if (step_dev) {
         __shared__ float s_bc[2];
         if (threadIdx.x == 0) {
@@ -233,7 +236,7 @@ void launch_adam(float *p, const float *g, float *m, float *v, long long ld, int
             cudaFuncSetAttribute(k_adam_unseen, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             attr = true;
         }
-        k_adam_unseen<<<blocks, kBgThreads, 0, s>>>((float4 *)p, (float4 *)m, (float4 *)v, ld / 4, planes, L, beta1,
+        launch_pdl(k_adam_unseen, blocks, kBgThreads, 0, s, (float4 *)p, (float4 *)m, (float4 *)v, ld / 4, planes, L, beta1,
                                                     beta2, (float)(1.0 / bc1), (float)(1.0 / sqrt(bc2)), eps,
                                                     step_dev, (const int4 *)radius, n_views);
         return;
@@ -242,7 +245,7 @@ void launch_adam(float *p, const float *g, float *m, float *v, long long ld, int
         const long long items = (planes + kAdamPlanes - 1) / kAdamPlanes * (ld / 4);
         const int blocks = (int)std::min<long long>(ceil_div(items, 256), (long long)sms * 8);
         if (blocks <= 0) return;
-        k_adam_rows<<<blocks, 256, 0, s>>>((float4 *)p, (const float4 *)g, (float4 *)m, (float4 *)v, ld / 4, planes,
+        launch_pdl(k_adam_rows, blocks, 256, 0, s, (float4 *)p, (const float4 *)g, (float4 *)m, (float4 *)v, ld / 4, planes,
                                            L, beta1, beta2, (float)(1.0 / bc1), (float)(1.0 / sqrt(bc2)), eps,
                                            step_dev, (const uint32_t *)rows, part);
         return;
@@ -250,7 +253,7 @@ void launch_adam(float *p, const float *g, float *m, float *v, long long ld, int
     const long long want = ceil_div(total4, 256);
     const int blocks = (int)std::min<long long>(want, (long long)sms * 8);
     if (blocks <= 0) return;
-    k_adam<<<blocks, 256, 0, s>>>((float4 *)p, (const float4 *)g, (float4 *)m, (float4 *)v, ld / 4, total4, L, beta1,
+    launch_pdl(k_adam, blocks, 256, 0, s, (float4 *)p, (const float4 *)g, (float4 *)m, (float4 *)v, ld / 4, total4, L, beta1,
                                   beta2, (float)(1.0 / bc1), (float)(1.0 / sqrt(bc2)), eps, step_dev);
 }
 

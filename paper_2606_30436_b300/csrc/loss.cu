@@ -45,6 +45,7 @@ __device__ __forceinline__ double block_sum_d(double v, double *sm) {
 __global__ void __launch_bounds__(256) k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int H,
                                                    int W, Win win, float *__restrict__ maps, int want_grad,
                                                    double *__restrict__ partials) {
+    griddep_wait();
     __shared__ float sx[kLI][kLI + 1], sy[kLI][kLI + 1];
     __shared__ float h[5][kLI][kLT];
     __shared__ double sm[8];
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(const float *__restrict__ x, c
 __global__ void __launch_bounds__(256) k_ssim_bwd(const float *__restrict__ x, const float *__restrict__ y, int H,
                                                    int W, Win win, const float *__restrict__ maps, float l1_scale,
                                                    float ssim_scale, float *__restrict__ dL) {
+    griddep_wait();
     __shared__ float sm[3][kLI][kLI + 1];
     __shared__ float h[3][kLI][kLT];
     const int ch = blockIdx.z;
@@ -157,6 +159,7 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(const float *__restrict__ x, c
 
 __global__ void __launch_bounds__(256) k_l1(const float *__restrict__ x, const float *__restrict__ y, long long n,
                                              float scale, float *__restrict__ dL, double *__restrict__ partials) {
+    griddep_wait();
     __shared__ double sm[8];
     double s = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -173,6 +176,7 @@ __global__ void __launch_bounds__(256) k_l1(const float *__restrict__ x, const f
 
 __global__ void __launch_bounds__(256) k_loss_final(const double *__restrict__ partials, int nb, double inv_n,
                                                      float lambda, float *__restrict__ out) {
+    griddep_wait();
     __shared__ double sm[8];
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < nb; i += 256) { a += partials[2 * i]; b += partials[2 * i + 1]; }
@@ -196,8 +200,8 @@ cudaError_t launch_loss(const float *img, const float *target, int h, int w, flo
     float *maps = (float *)ws;
     double *partials = (double *)((char *)ws + align_up(sizeof(float) * 9 * (size_t)h * w, 256));
     if (lambda <= 0.0f) {
-        k_l1<<<kL1Blocks, 256, 0, s>>>(img, target, n, (float)(1.0 / (double)n), dL_dimg, partials);
-        k_loss_final<<<1, 256, 0, s>>>(partials, kL1Blocks, 1.0 / (double)n, 0.0f, loss_out);
+        launch_pdl(k_l1, kL1Blocks, 256, 0, s, img, target, n, (float)(1.0 / (double)n), dL_dimg, partials);
+        launch_pdl(k_loss_final, 1, 256, 0, s, partials, kL1Blocks, 1.0 / (double)n, 0.0f, loss_out);
         return cudaGetLastError();
     }
     Win win;
@@ -207,11 +211,11 @@ cudaError_t launch_loss(const float *img, const float *target, int h, int w, flo
         for (int k = 0; k < 2 * kLR + 1; ++k) win.w[k] = (float)(wd[k] / sum);
     }
     dim3 grid((unsigned)ceil_div(w, kLT), (unsigned)ceil_div(h, kLT), 3);
-    k_ssim_fwd<<<grid, 256, 0, s>>>(img, target, h, w, win, maps, dL_dimg != nullptr, partials);
+    launch_pdl(k_ssim_fwd, grid, 256, 0, s, img, target, h, w, win, maps, dL_dimg != nullptr, partials);
     if (dL_dimg)
-        k_ssim_bwd<<<grid, 256, 0, s>>>(img, target, h, w, win, maps, (float)((1.0 - lambda) / (double)n),
+        launch_pdl(k_ssim_bwd, grid, 256, 0, s, img, target, h, w, win, maps, (float)((1.0 - lambda) / (double)n),
                                         (float)(lambda / (double)n), dL_dimg);
-    k_loss_final<<<1, 256, 0, s>>>(partials, loss_blocks(h, w), 1.0 / (double)n, lambda, loss_out);
+    launch_pdl(k_loss_final, 1, 256, 0, s, partials, loss_blocks(h, w), 1.0 / (double)n, lambda, loss_out);
     return cudaGetLastError();
 }
 

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256, 4) k_project(const float *__restrict__ P,
                                                  float4 *__restrict__ rgbd, int *__restrict__ radius,
                                                  int *__restrict__ touched, int *__restrict__ status,
                                                  float4 *__restrict__ cj) {
+    griddep_wait();
     constexpr int K = (D + 1) * (D + 1);
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= ld) return;
@@ -307,6 +308,7 @@ __global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 3) k_pr
                                                      const float *__restrict__ loss_per_view,
                                                      float *__restrict__ stats, long long stats_ld, FusedAdam fa,
                                                      const float4 *__restrict__ cj, uint8_t *__restrict__ rows) {
+    griddep_wait();
     constexpr int K = (D + 1) * (D + 1);
     if (ADAM && fa.step_dev) {  // bias corrections from the device step counter (graph replay)
         __shared__ float s_bc[2];
@@ -620,10 +622,10 @@ void launch_project(const float *P, long long n, long long ld, int D, const View
     if (ld <= 0) return;
     const int blocks = (int)ceil_div(ld, 256);
     switch (D) {
-        case 0: k_project<0><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
-        case 1: k_project<1><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
-        case 2: k_project<2><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
-        default: k_project<3><<<blocks, 256, 0, s>>>(P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
+        case 0: launch_pdl(k_project<0>, blocks, 256, 0, s, P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
+        case 1: launch_pdl(k_project<1>, blocks, 256, 0, s, P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
+        case 2: launch_pdl(k_project<2>, blocks, 256, 0, s, P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
+        default: launch_pdl(k_project<3>, blocks, 256, 0, s, P, n, ld, vt, cfg, xy, co, rgbd, radius, touched, status, cj); break;
     }
 }
 
@@ -634,7 +636,7 @@ void launch_project_bwd(const float *P, long long n, long long ld, int D, const 
     if (ld <= 0) return;
     const int blocks = (int)ceil_div(ld, 256);
     FusedAdam fa{};
-#define GS_PB(DD) k_project_bwd<DD, false><<<blocks, 256, 0, s>>>(const_cast<float *>(P), n, ld, vt, cfg, radius, acc, \
+#define GS_PB(DD) launch_pdl(k_project_bwd<DD, false>, blocks, 256, 0, s, const_cast<float *>(P), n, ld, vt, cfg, radius, acc, \
                                                                    nrec, G, accumulate, loss_per_view, stats, stats_ld, fa, \
                                                                    cj, rows)
     switch (D) {
@@ -674,7 +676,7 @@ void launch_project_bwd_adam(float *P, long long n, long long ld, int D, const V
             cudaFuncSetAttribute(k_project_bwd<DD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);    \
             attr = true;                                                                                        \
         }                                                                                                       \
-        k_project_bwd<DD, true><<<blocks, kFusedThreads, smem, s>>>(P, n, ld, vt, cfg, radius, acc, nrec,       \
+        launch_pdl(k_project_bwd<DD, true>, blocks, kFusedThreads, smem, s, P, n, ld, vt, cfg, radius, acc, nrec,       \
                                                                     nullptr, 0,                                 \
                                                           loss_per_view, stats, stats_ld, fa, nullptr, nullptr); \
     } while (0)

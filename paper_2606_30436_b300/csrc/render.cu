@@ -226,6 +226,7 @@ constexpr int kPlanThreads = 1024;
 __global__ void __launch_bounds__(kPlanThreads) k_fwd_plan(const int2 *__restrict__ ranges,
                                                           const int *__restrict__ order, int total_tiles,
                                                           int seg_shift, SegWs seg) {
+    griddep_wait();
     __shared__ int s_items[kPlanThreads / 32], s_long[kPlanThreads / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int per = (total_tiles + kPlanThreads - 1) / kPlanThreads;
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(32 * kWarps, 8) k_render_fwd(ViewTable vt, Ras
                                                               float *__restrict__ img, float *__restrict__ T_final,
                                                               int *__restrict__ last, float *__restrict__ depth,
                                                               SegWs seg, int item_blocks) {
+    griddep_wait();
     __shared__ int s_list[kWarps][WIN];
     __shared__ float2 s_p[kWarps][32];
     __shared__ float4 s_q[kWarps][32];
@@ -364,6 +366,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_fwd_combine(ViewTable vt
                                                                    float *__restrict__ T_final,
                                                                    int *__restrict__ last,
                                                                    float *__restrict__ depth, SegWs seg) {
+    griddep_wait();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = 8 * min(seg.count[1], seg.hcap);
     for (int u = blockIdx.x * kWarps + warp; u < n; u += gridDim.x * kWarps) {
@@ -460,6 +463,7 @@ __global__ void __launch_bounds__(32 * kWarps, 1) k_render_fwd_rerun(ViewTable v
                                                                     float *__restrict__ T_final,
                                                                     int *__restrict__ last,
                                                                     float *__restrict__ depth, SegWs seg) {
+    griddep_wait();
     __shared__ int s_list[kWarps][WIN];
     __shared__ float2 s_p[kWarps][32];
     __shared__ float4 s_q[kWarps][32];
@@ -580,6 +584,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_bwd(ViewTable vt, Raster
                                                               float *__restrict__ acc, long long nrec,
                                                               const float *__restrict__ depth, SegWs seg,
                                                               int item_blocks) {
+    griddep_wait();
     __shared__ int s_list[kWarps][WIN];
     __shared__ float2 s_p[kWarps][32];
     __shared__ float4 s_q[kWarps][32];
@@ -777,6 +782,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_render_fwd_lists(ViewTable vt, 
                                                                   long long *__restrict__ count_off,
                                                                   int *__restrict__ lid, float *__restrict__ lal,
                                                                   long long cap) {
+    griddep_wait();
     __shared__ int s_list[kWarps][WIN];
     __shared__ float2 s_p[kWarps][32];
     __shared__ float4 s_q[kWarps][32];
@@ -835,6 +841,7 @@ __device__ __forceinline__ long long block_scan_ll(long long x, long long &total
 
 __global__ void __launch_bounds__(kListScanThreads) k_list_scan_sums(const long long *__restrict__ cnt, long long npx,
                                                                      long long *__restrict__ bsum) {
+    griddep_wait();
     __shared__ long long sm[33];
     long long x = 0;
     const long long b = (long long)blockIdx.x * kListScanTile + threadIdx.x * kListScanItems;
@@ -849,6 +856,7 @@ __global__ void __launch_bounds__(kListScanThreads) k_list_scan_sums(const long 
 __global__ void __launch_bounds__(kListScanThreads) k_list_scan_top(long long *__restrict__ bsum, int nb,
                                                                     long long *__restrict__ count_off, long long npx,
                                                                     long long cap, int *__restrict__ status) {
+    griddep_wait();
     __shared__ long long sm[33];
     long long run = 0;
     for (int b0 = 0; b0 < nb; b0 += kListScanThreads) {
@@ -867,6 +875,7 @@ __global__ void __launch_bounds__(kListScanThreads) k_list_scan_top(long long *_
 
 __global__ void __launch_bounds__(kListScanThreads) k_list_scan_apply(long long *__restrict__ count_off, long long npx,
                                                                       const long long *__restrict__ bsum) {
+    griddep_wait();
     __shared__ long long sm[33];
     const long long b = (long long)blockIdx.x * kListScanTile + threadIdx.x * kListScanItems;
     long long c[kListScanItems], x = 0;
@@ -899,6 +908,7 @@ __global__ void __launch_bounds__(256) k_render_bwd_lists(ViewTable vt, RasterCf
                                                           const float *__restrict__ dL_dimg,
                                                           const float *__restrict__ target, float tau_err,
                                                           float *__restrict__ acc) {
+    griddep_wait();
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < npx;
          q += (long long)gridDim.x * blockDim.x) {
         int v = 0;
@@ -976,7 +986,7 @@ void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ra
     int item_blocks = 0, cgrid = 0, rgrid = 0;
     if (split) {
         cudaMemsetAsync(seg.count, 0, 8 * sizeof(int), s);
-        k_fwd_plan<<<1, kPlanThreads, 0, s>>>(ranges, order, vt.total_tiles, cfg.seg_shift, seg);
+        launch_pdl(k_fwd_plan, 1, kPlanThreads, 0, s, ranges, order, vt.total_tiles, cfg.seg_shift, seg);
         item_blocks = stride_blocks(seg.fcap);
         cgrid = stride_blocks(8ll * seg.hcap);
         rgrid = stride_blocks(seg.fcap);
@@ -984,11 +994,11 @@ void launch_render_fwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ra
     const unsigned grid = (unsigned)(item_blocks + ceil_div(units, kWarps));
 #define GS_FWD(WN)                                                                                                  \
     do {                                                                                                            \
-        k_render_fwd<WN><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, order, xy, co, rgbd, img,        \
+        launch_pdl(k_render_fwd<WN>, grid, 32 * kWarps, 0, s, vt, cfg, ranges, ids, masks, order, xy, co, rgbd, img,        \
                                                       T_final, last, depth, seg, item_blocks);                      \
         if (split) {                                                                                                \
-            k_render_fwd_combine<<<cgrid, 32 * kWarps, 0, s>>>(vt, cfg, img, T_final, last, depth, seg);            \
-            k_render_fwd_rerun<WN><<<rgrid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, xy, co, rgbd, img,    \
+            launch_pdl(k_render_fwd_combine, cgrid, 32 * kWarps, 0, s, vt, cfg, img, T_final, last, depth, seg);            \
+            launch_pdl(k_render_fwd_rerun<WN>, rgrid, 32 * kWarps, 0, s, vt, cfg, ranges, ids, masks, xy, co, rgbd, img,    \
                                                                  T_final, last, depth, seg);                        \
         }                                                                                                           \
     } while (0)
@@ -1008,7 +1018,7 @@ void launch_render_bwd(const ViewTable &vt, const RasterCfg &cfg, const int2 *ra
     // segment CTAs first, so the long lists' segments start early
     const int item_blocks = cfg.seg_shift >= 0 ? stride_blocks(seg.cap) : 0;
     const unsigned grid = (unsigned)(item_blocks + ceil_div(units, kWarps));
-#define GS_BWD(ST, WN) k_render_bwd<ST, WN><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, order, xy, co, \
+#define GS_BWD(ST, WN) launch_pdl(k_render_bwd<ST, WN>, grid, 32 * kWarps, 0, s, vt, cfg, ranges, ids, masks, order, xy, co, \
                                                                          rgbd, img, T_final, last, dL_dimg, \
                                                                          dL_ddepth, target, tau_err, acc, nrec, \
                                                                          depth, seg, item_blocks)
@@ -1040,13 +1050,13 @@ void launch_render_fwd_lists(const ViewTable &vt, const RasterCfg &cfg, const in
     long long *bsum = (long long *)scan_ws;
 #define GS_FWDL(WN)                                                                                                 \
     do {                                                                                                            \
-        k_render_fwd_lists<WN, false><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, order, xy, co, rgbd, \
+        launch_pdl(k_render_fwd_lists<WN, false>, grid, 32 * kWarps, 0, s, vt, cfg, ranges, ids, masks, order, xy, co, rgbd, \
                                                                    img, T_final, last, depth, count_off, lid, lal,  \
                                                                    cap);                                            \
-        k_list_scan_sums<<<nb, kListScanThreads, 0, s>>>(count_off, npx, bsum);                                     \
-        k_list_scan_top<<<1, kListScanThreads, 0, s>>>(bsum, nb, count_off, npx, cap, status);                      \
-        k_list_scan_apply<<<nb, kListScanThreads, 0, s>>>(count_off, npx, bsum);                                    \
-        k_render_fwd_lists<WN, true><<<grid, 32 * kWarps, 0, s>>>(vt, cfg, ranges, ids, masks, order, xy, co, rgbd,  \
+        launch_pdl(k_list_scan_sums, nb, kListScanThreads, 0, s, count_off, npx, bsum);                                     \
+        launch_pdl(k_list_scan_top, 1, kListScanThreads, 0, s, bsum, nb, count_off, npx, cap, status);                      \
+        launch_pdl(k_list_scan_apply, nb, kListScanThreads, 0, s, count_off, npx, bsum);                                    \
+        launch_pdl(k_render_fwd_lists<WN, true>, grid, 32 * kWarps, 0, s, vt, cfg, ranges, ids, masks, order, xy, co, rgbd,  \
                                                                   img, T_final, last, depth, count_off, lid, lal,   \
                                                                   cap);                                             \
     } while (0)
@@ -1063,10 +1073,10 @@ void launch_render_bwd_lists(const ViewTable &vt, const RasterCfg &cfg, long lon
     if (npx <= 0) return;
     const unsigned grid = (unsigned)std::min(ceil_div(npx, 256), (long long)sm_count() * 8);
     if (stats)
-        k_render_bwd_lists<true><<<grid, 256, 0, s>>>(vt, cfg, npx, off, lid, lal, cap, xy, co, rgbd, img, T_final,
+        launch_pdl(k_render_bwd_lists<true>, grid, 256, 0, s, vt, cfg, npx, off, lid, lal, cap, xy, co, rgbd, img, T_final,
                                                       dL_dimg, target, tau_err, acc);
     else
-        k_render_bwd_lists<false><<<grid, 256, 0, s>>>(vt, cfg, npx, off, lid, lal, cap, xy, co, rgbd, img, T_final,
+        launch_pdl(k_render_bwd_lists<false>, grid, 256, 0, s, vt, cfg, npx, off, lid, lal, cap, xy, co, rgbd, img, T_final,
                                                        dL_dimg, target, tau_err, acc);
 }
 

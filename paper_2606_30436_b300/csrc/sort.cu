@@ -73,6 +73,7 @@ __device__ __forceinline__ void block_segment(long long count, long long &beg, l
 
 __global__ void __launch_bounds__(kSortThreads) k_visible_count(const int *__restrict__ radius, long long nrec,
                                                                  unsigned long long *__restrict__ blk) {
+    griddep_wait();
     __shared__ unsigned long long sm[33];
     long long beg, end;
     block_segment(nrec, beg, end);
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(kSortThreads) k_visible_count(const int *__res
 __global__ void __launch_bounds__(kSortBlocks) k_scan_blocks(unsigned long long *__restrict__ blk, int mode,
                                                              int *__restrict__ counts, long long max_pairs,
                                                              int *__restrict__ status) {
+    griddep_wait();
     __shared__ unsigned long long sm[33];
     unsigned long long x = blk[threadIdx.x], total;
     unsigned long long ex = block_exclusive_scan<unsigned long long>(x, total, sm);
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(kSortThreads) k_visible_compact(const int *__r
                                                                    const float4 *__restrict__ rgbd, long long nrec,
                                                                    const unsigned long long *__restrict__ blk,
                                                                    uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
+    griddep_wait();
     __shared__ unsigned long long sm[33];
     long long beg, end;
     block_segment(nrec, beg, end);
@@ -168,6 +171,7 @@ __device__ __forceinline__ uint32_t rx_key(const RxPass &a, long long i, uint32_
 }
 
 __global__ void __launch_bounds__(kRxThreads) k_rx_count(RxPass a) {
+    griddep_wait();
     __shared__ uint32_t h[kRxWarps][256];
     const int radix = 1 << a.bits;
     const uint32_t mask = radix - 1;
@@ -191,6 +195,7 @@ __global__ void __launch_bounds__(kRxThreads) k_rx_count(RxPass a) {
 
 // One CTA per digit: exclusive scan of the digit's per-CTA counts.
 __global__ void __launch_bounds__(kRxScanThreads) k_rx_scan(RxPass a) {
+    griddep_wait();
     __shared__ uint32_t sm[33];
     const int d = blockIdx.x;
     const bool in = (int)threadIdx.x < a.nblocks;
@@ -206,6 +211,7 @@ __global__ void __launch_bounds__(kRxScanThreads) k_rx_scan(RxPass a) {
 // the warp's earlier ones), the warps' counts are scanned per digit, the
 // round is reordered by digit in shared memory and written out in digit runs.
 __global__ void __launch_bounds__(kRxThreads, kRxCtasPerSm) k_rx_scatter(RxPass a) {
+    griddep_wait();
     __shared__ uint32_t s_base[256];    // output position of this CTA's next element of each digit
     __shared__ uint32_t s_dstart[257];  // first local slot of each digit in the current round
     __shared__ uint32_t s_whist[kRxWarps][256];
@@ -311,9 +317,9 @@ __global__ void __launch_bounds__(kRxThreads, kRxCtasPerSm) k_rx_scatter(RxPass 
 
 static void rx_pass(RxPass a, cudaStream_t s) {
     a.nblocks = kRxBlocks;
-    k_rx_count<<<a.nblocks, kRxThreads, 0, s>>>(a);
-    k_rx_scan<<<1 << a.bits, kRxScanThreads, 0, s>>>(a);
-    k_rx_scatter<<<a.nblocks, kRxThreads, 0, s>>>(a);
+    launch_pdl(k_rx_count, a.nblocks, kRxThreads, 0, s, a);
+    launch_pdl(k_rx_scan, 1 << a.bits, kRxScanThreads, 0, s, a);
+    launch_pdl(k_rx_scatter, a.nblocks, kRxThreads, 0, s, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -323,6 +329,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tiles_count(const uint32_t *__
                                                                const int *__restrict__ touched,
                                                                const int *__restrict__ counts,
                                                                unsigned long long *__restrict__ blk) {
+    griddep_wait();
     __shared__ unsigned long long sm[33];
     long long beg, end;
     block_segment(counts[0], beg, end);
@@ -340,6 +347,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tiles_offsets(const uint32_t *
                                                                  const int *__restrict__ counts,
                                                                  const unsigned long long *__restrict__ blk,
                                                                  uint32_t *__restrict__ off) {
+    griddep_wait();
     __shared__ unsigned long long sm[33];
     const long long V = counts[0];
     long long beg, end;
@@ -388,6 +396,7 @@ __global__ void __launch_bounds__(256) k_emit_pairs(const uint32_t *__restrict__
                                                      long long ld, ViewTable vt, float alpha_min,
                                                      int *__restrict__ counts, uint32_t *__restrict__ big,
                                                      uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+    griddep_wait();
     if (counts[1] == 0) return;  // nothing to emit, or overflow
     const long long V = counts[0];
     const int lane = threadIdx.x & 31;
@@ -467,6 +476,7 @@ __global__ void __launch_bounds__(256) k_emit_big(const uint32_t *__restrict__ s
                                                    long long ld, ViewTable vt, float alpha_min,
                                                    const int *__restrict__ counts, const uint32_t *__restrict__ big,
                                                    uint32_t *__restrict__ pkey, uint32_t *__restrict__ pval) {
+    griddep_wait();
     if (counts[1] == 0) return;
     const int nbig = counts[3];
     for (int b = blockIdx.x; b < nbig; b += gridDim.x) {
@@ -491,6 +501,7 @@ __global__ void __launch_bounds__(256) k_unpack_pairs(const uint32_t *__restrict
                                                        const uint32_t *__restrict__ pval, const int *__restrict__ counts,
                                                        int *__restrict__ ids, uint8_t *__restrict__ masks,
                                                        int2 *__restrict__ ranges) {
+    griddep_wait();
     const long long P = counts[1];
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
         ids[p] = (int)pval[p];
@@ -509,6 +520,7 @@ __global__ void __launch_bounds__(256) k_unpack_pairs(const uint32_t *__restrict
 // this pass turns them into [first, end), empty tiles into (0, 0).
 __global__ void __launch_bounds__(256) k_tile_hist(int2 *__restrict__ ranges, int total_tiles,
                                                     unsigned int *__restrict__ bucket) {
+    griddep_wait();
     __shared__ unsigned int h[33];
     if (threadIdx.x < 33) h[threadIdx.x] = 0;
     __syncthreads();
@@ -525,6 +537,7 @@ __global__ void __launch_bounds__(256) k_tile_hist(int2 *__restrict__ ranges, in
 
 // cursors: bucket 32 (longest) first
 __global__ void k_tile_scan(unsigned int *__restrict__ bucket) {
+    griddep_wait();
     if (threadIdx.x == 0) {
         unsigned int run = 0;
         for (int b = 32; b >= 0; --b) {
@@ -537,6 +550,7 @@ __global__ void k_tile_scan(unsigned int *__restrict__ bucket) {
 
 __global__ void __launch_bounds__(256) k_tile_scatter(const int2 *__restrict__ ranges, int total_tiles,
                                                        unsigned int *__restrict__ bucket, int *__restrict__ order) {
+    griddep_wait();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x) {
         const int2 r = ranges[t];
         const unsigned c = (unsigned)(r.y - r.x);
@@ -643,9 +657,9 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
     // stage 1: visible records sorted by depth, then stably by view: records in
     // (view, depth) order, so the emission below gathers one view's records at
     // a time (an L2-sized working set)
-    k_visible_count<<<kSortBlocks, kSortThreads, 0, s>>>(radius, nrec, w.blk);
-    k_scan_blocks<<<1, kSortBlocks, 0, s>>>(w.blk, 0, counts, max_pairs, status);
-    k_visible_compact<<<kSortBlocks, kSortThreads, 0, s>>>(radius, rgbd, nrec, w.blk, w.dk0, w.dv0);
+    launch_pdl(k_visible_count, kSortBlocks, kSortThreads, 0, s, radius, nrec, w.blk);
+    launch_pdl(k_scan_blocks, 1, kSortBlocks, 0, s, w.blk, 0, counts, max_pairs, status);
+    launch_pdl(k_visible_compact, kSortBlocks, kSortThreads, 0, s, radius, rgbd, nrec, w.blk, w.dk0, w.dv0);
     const int dres = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, counts + 0, nrec, 32, w.hist, w.dtotal, s);
     const uint32_t *sorted_rec = dres ? w.dv1 : w.dv0;
     if (vt.n_views > 1) {
@@ -670,12 +684,12 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
     }
 
     // stage 2: pairs in depth order, then a stable partition by tile
-    k_tiles_count<<<kSortBlocks, kSortThreads, 0, s>>>(sorted_rec, touched, counts, w.blk);
-    k_scan_blocks<<<1, kSortBlocks, 0, s>>>(w.blk, 1, counts, max_pairs, status);
-    k_tiles_offsets<<<kSortBlocks, kSortThreads, 0, s>>>(sorted_rec, touched, counts, w.blk, w.off);
-    k_emit_pairs<<<148 * 16, 256, 0, s>>>(sorted_rec, w.off, radius, xy, co, ld, vt, alpha_min, counts, w.big, w.pk0,
+    launch_pdl(k_tiles_count, kSortBlocks, kSortThreads, 0, s, sorted_rec, touched, counts, w.blk);
+    launch_pdl(k_scan_blocks, 1, kSortBlocks, 0, s, w.blk, 1, counts, max_pairs, status);
+    launch_pdl(k_tiles_offsets, kSortBlocks, kSortThreads, 0, s, sorted_rec, touched, counts, w.blk, w.off);
+    launch_pdl(k_emit_pairs, 148 * 16, 256, 0, s, sorted_rec, w.off, radius, xy, co, ld, vt, alpha_min, counts, w.big, w.pk0,
                                           w.pv0);
-    k_emit_big<<<148 * 4, 256, 0, s>>>(sorted_rec, w.off, radius, xy, co, ld, vt, alpha_min, counts, w.big, w.pk0,
+    launch_pdl(k_emit_big, 148 * 4, 256, 0, s, sorted_rec, w.off, radius, xy, co, ld, vt, alpha_min, counts, w.big, w.pk0,
                                        w.pv0);
     int tile_bits = 0;
     while ((1ll << tile_bits) < (long long)vt.total_tiles) ++tile_bits;
@@ -683,14 +697,14 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
         radix_sort(w.pk0, w.pv0, w.pk1, w.pv1, counts + 1, max_pairs, tile_bits, w.hist, w.dtotal, s,
                    (uint32_t *)gauss_ids, block_mask, tile_ranges);
     } else {
-        k_unpack_pairs<<<148 * 8, 256, 0, s>>>(w.pk0, w.pv0, counts, gauss_ids, block_mask, tile_ranges);
+        launch_pdl(k_unpack_pairs, 148 * 8, 256, 0, s, w.pk0, w.pv0, counts, gauss_ids, block_mask, tile_ranges);
     }
     e = cudaMemsetAsync(w.bucket, 0, sizeof(unsigned int) * 64, s);
     if (e != cudaSuccess) return e;
     const int tb = (int)std::min<long long>(ceil_div(vt.total_tiles, 256), 148 * 4);
-    k_tile_hist<<<tb, 256, 0, s>>>(tile_ranges, vt.total_tiles, w.bucket);
-    k_tile_scan<<<1, 32, 0, s>>>(w.bucket);
-    k_tile_scatter<<<tb, 256, 0, s>>>(tile_ranges, vt.total_tiles, w.bucket, tile_order);
+    launch_pdl(k_tile_hist, tb, 256, 0, s, tile_ranges, vt.total_tiles, w.bucket);
+    launch_pdl(k_tile_scan, 1, 32, 0, s, w.bucket);
+    launch_pdl(k_tile_scatter, tb, 256, 0, s, tile_ranges, vt.total_tiles, w.bucket, tile_order);
     return cudaGetLastError();
 }
 

@@ -114,7 +114,9 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(const float *__restrict__ x, c
 
 __global__ void __launch_bounds__(256) k_ssim_bwd(const float *__restrict__ x, const float *__restrict__ y, int H,
                                                    int W, Win win, const float *__restrict__ maps, float l1_scale,
-                                                   float ssim_scale, float *__restrict__ dL) {
+                                                   float ssim_scale, float *__restrict__ dL,
+                                                   const double *__restrict__ partials, int nb, double inv_n,
+                                                   float lambda, float *__restrict__ loss_out) {
     griddep_wait();
     __shared__ float sm[3][kLI][kLI + 1];
     __shared__ float h[3][kLI][kLT];
@@ -154,6 +156,15 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(const float *__restrict__ x, c
         const long long o = ch * plane + (long long)gy * W + gx;
         const float xv = x[o], yv = y[o];
         dL[o] = l1_scale * sgn(xv - yv) - ssim_scale * (a + 2.0f * xv * b + yv * d);
+    }
+    // the scalar loss from the forward's per-CTA sums, by one block (a launch fewer)
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
+        __shared__ double sd[8];
+        double a = 0.0, b = 0.0;
+        for (int i = threadIdx.x; i < nb; i += 256) { a += partials[2 * i]; b += partials[2 * i + 1]; }
+        const double l1 = block_sum_d(a, sd) * inv_n;
+        const double ssim = block_sum_d(b, sd) * inv_n;
+        if (threadIdx.x == 0) *loss_out = (float)((1.0 - lambda) * l1 + lambda * (1.0 - ssim));
     }
 }
 
@@ -214,8 +225,10 @@ cudaError_t launch_loss(const float *img, const float *target, int h, int w, flo
     launch_pdl(k_ssim_fwd, grid, 256, 0, s, img, target, h, w, win, maps, dL_dimg != nullptr, partials);
     if (dL_dimg)
         launch_pdl(k_ssim_bwd, grid, 256, 0, s, img, target, h, w, win, maps, (float)((1.0 - lambda) / (double)n),
-                                        (float)(lambda / (double)n), dL_dimg);
-    launch_pdl(k_loss_final, 1, 256, 0, s, partials, loss_blocks(h, w), 1.0 / (double)n, lambda, loss_out);
+                   (float)(lambda / (double)n), dL_dimg, partials, loss_blocks(h, w), 1.0 / (double)n, lambda,
+                   loss_out);
+    else
+        launch_pdl(k_loss_final, 1, 256, 0, s, partials, loss_blocks(h, w), 1.0 / (double)n, lambda, loss_out);
     return cudaGetLastError();
 }
 

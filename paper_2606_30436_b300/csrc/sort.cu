@@ -84,40 +84,36 @@ __global__ void __launch_bounds__(kSortThreads) k_visible_count(const int *__res
     if (threadIdx.x == 0) blk[blockIdx.x] = total;
 }
 
-// Exclusive scan of the per-block sums (one block of kSortBlocks threads).
-// mode 0: total -> counts[0] (visible records).
-// mode 1: total -> pairs; counts[2] = needed, counts[1] = pairs or 0 on overflow.
-__global__ void __launch_bounds__(kSortBlocks) k_scan_blocks(unsigned long long *__restrict__ blk, int mode,
-                                                             int *__restrict__ counts, long long max_pairs,
-                                                             int *__restrict__ status) {
-    griddep_wait();
-    __shared__ unsigned long long sm[33];
-    unsigned long long x = blk[threadIdx.x], total;
-    unsigned long long ex = block_exclusive_scan<unsigned long long>(x, total, sm);
-    blk[threadIdx.x] = ex;
-    if (threadIdx.x == 0) {
-        const int t32 = (int)min(total, (unsigned long long)0x7fffffff);
-        if (mode == 0) {
-            counts[0] = t32;
-        } else {
-            counts[2] = t32;
-            const bool ok = total <= (unsigned long long)max_pairs;
-            counts[1] = ok ? t32 : 0;
-            if (!ok && status) atomicOr(status, 1 << GS_ERR_CAPACITY);
-        }
+// The per-block sums' exclusive prefix for this block and their total, summed by the block
+// itself from the kSortBlocks counts (no separate scan launch; integer sums, order-free).
+__device__ __forceinline__ void block_prefix(const unsigned long long *__restrict__ blk, unsigned long long &prefix,
+                                             unsigned long long &total, unsigned long long *sm) {
+    unsigned long long a = 0, b = 0;
+    for (int i = threadIdx.x; i < kSortBlocks; i += blockDim.x) {
+        const unsigned long long x = blk[i];
+        b += x;
+        if (i < (int)blockIdx.x) a += x;
     }
+    unsigned long long ta, tb;
+    block_exclusive_scan<unsigned long long>(a, ta, sm);
+    block_exclusive_scan<unsigned long long>(b, tb, sm);
+    prefix = ta;
+    total = tb;
 }
 
-// Writes the visible records in index order with their depth keys.
+// Writes the visible records in index order with their depth keys; block 0 stores the count.
 __global__ void __launch_bounds__(kSortThreads) k_visible_compact(const int *__restrict__ radius,
                                                                    const float4 *__restrict__ rgbd, long long nrec,
                                                                    const unsigned long long *__restrict__ blk,
-                                                                   uint32_t *__restrict__ key, uint32_t *__restrict__ val) {
+                                                                   uint32_t *__restrict__ key, uint32_t *__restrict__ val,
+                                                                   int *__restrict__ counts) {
     griddep_wait();
     __shared__ unsigned long long sm[33];
     long long beg, end;
     block_segment(nrec, beg, end);
-    unsigned long long run = blk[blockIdx.x];
+    unsigned long long run, all;
+    block_prefix(blk, run, all, sm);
+    if (blockIdx.x == 0 && threadIdx.x == 0) counts[0] = (int)min(all, (unsigned long long)0x7fffffff);
     for (long long base = beg; base < end; base += kSortThreads) {
         const long long i = base + threadIdx.x;
         const bool f = i < end && radius[i] > 0;
@@ -346,13 +342,23 @@ __global__ void __launch_bounds__(kSortThreads) k_tiles_offsets(const uint32_t *
                                                                  const int *__restrict__ touched,
                                                                  const int *__restrict__ counts,
                                                                  const unsigned long long *__restrict__ blk,
-                                                                 uint32_t *__restrict__ off) {
+                                                                 uint32_t *__restrict__ off, int *counts_out,
+                                                                 long long max_pairs, int *__restrict__ status) {
     griddep_wait();
     __shared__ unsigned long long sm[33];
     const long long V = counts[0];
     long long beg, end;
     block_segment(V, beg, end);
-    unsigned long long run = blk[blockIdx.x];
+    unsigned long long run, all;
+    block_prefix(blk, run, all, sm);
+    // the pair total: counts[2] = needed, counts[1] = pairs or 0 on overflow; read by later kernels
+    const int t32 = (int)min(all, (unsigned long long)0x7fffffff);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        counts_out[2] = t32;
+        const bool ok = all <= (unsigned long long)max_pairs;
+        counts_out[1] = ok ? t32 : 0;
+        if (!ok && status) atomicOr(status, 1 << GS_ERR_CAPACITY);
+    }
     for (long long base = beg; base < end; base += kSortThreads) {
         const long long r = base + threadIdx.x;
         const int tt = r < end ? touched[sorted_rec[r]] : 0;
@@ -361,7 +367,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tiles_offsets(const uint32_t *
         if (r < end) off[r] = (uint32_t)o;
         run += total;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) off[V] = (uint32_t)counts[2];
+    if (blockIdx.x == 0 && threadIdx.x == 0) off[V] = (uint32_t)t32;
 }
 
 constexpr int kBigRecord = 128;  // records overlapping more tiles are emitted by a whole CTA
@@ -536,25 +542,27 @@ __global__ void __launch_bounds__(256) k_tile_hist(int2 *__restrict__ ranges, in
 }
 
 // cursors: bucket 32 (longest) first
-__global__ void k_tile_scan(unsigned int *__restrict__ bucket) {
-    griddep_wait();
-    if (threadIdx.x == 0) {
-        unsigned int run = 0;
-        for (int b = 32; b >= 0; --b) {
-            const unsigned int c = bucket[b];
-            bucket[b] = run;
-            run += c;
-        }
-    }
-}
 
+// Tiles into their length class's run of the schedule, longest classes first: each block
+// forms the classes' starts from the 33 counts itself (bucket[0..32]); bucket[64 + c] are the
+// cursors within the classes.
 __global__ void __launch_bounds__(256) k_tile_scatter(const int2 *__restrict__ ranges, int total_tiles,
                                                        unsigned int *__restrict__ bucket, int *__restrict__ order) {
     griddep_wait();
+    __shared__ unsigned int start[33];
+    if (threadIdx.x == 0) {
+        unsigned int run = 0;
+        for (int b = 32; b >= 0; --b) {
+            start[b] = run;
+            run += bucket[b];
+        }
+    }
+    __syncthreads();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x) {
         const int2 r = ranges[t];
         const unsigned c = (unsigned)(r.y - r.x);
-        order[atomicAdd(&bucket[c ? 32 - __clz(c) : 0], 1u)] = t;
+        const int b = c ? 32 - __clz(c) : 0;
+        order[start[b] + atomicAdd(&bucket[64 + b], 1u)] = t;
     }
 }
 
@@ -580,7 +588,7 @@ static SortWs carve(void *base, long long nrec, long long max_pairs) {
         return p;
     };
     w.blk = (unsigned long long *)take(sizeof(unsigned long long) * (kSortBlocks + 1));
-    w.bucket = (unsigned int *)take(sizeof(unsigned int) * 64);
+    w.bucket = (unsigned int *)take(sizeof(unsigned int) * 128);  // 33 class counts, 33 cursors at 64
     w.hist = (uint32_t *)take(sizeof(uint32_t) * 256 * kRxBlocks);
     w.dtotal = (uint32_t *)take(sizeof(uint32_t) * 256);
     w.dk0 = (uint32_t *)take(sizeof(uint32_t) * nrec);
@@ -658,8 +666,7 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
     // (view, depth) order, so the emission below gathers one view's records at
     // a time (an L2-sized working set)
     launch_pdl(k_visible_count, kSortBlocks, kSortThreads, 0, s, radius, nrec, w.blk);
-    launch_pdl(k_scan_blocks, 1, kSortBlocks, 0, s, w.blk, 0, counts, max_pairs, status);
-    launch_pdl(k_visible_compact, kSortBlocks, kSortThreads, 0, s, radius, rgbd, nrec, w.blk, w.dk0, w.dv0);
+    launch_pdl(k_visible_compact, kSortBlocks, kSortThreads, 0, s, radius, rgbd, nrec, w.blk, w.dk0, w.dv0, counts);
     const int dres = radix_sort(w.dk0, w.dv0, w.dk1, w.dv1, counts + 0, nrec, 32, w.hist, w.dtotal, s);
     const uint32_t *sorted_rec = dres ? w.dv1 : w.dv0;
     if (vt.n_views > 1) {
@@ -685,8 +692,8 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
 
     // stage 2: pairs in depth order, then a stable partition by tile
     launch_pdl(k_tiles_count, kSortBlocks, kSortThreads, 0, s, sorted_rec, touched, counts, w.blk);
-    launch_pdl(k_scan_blocks, 1, kSortBlocks, 0, s, w.blk, 1, counts, max_pairs, status);
-    launch_pdl(k_tiles_offsets, kSortBlocks, kSortThreads, 0, s, sorted_rec, touched, counts, w.blk, w.off);
+    launch_pdl(k_tiles_offsets, kSortBlocks, kSortThreads, 0, s, sorted_rec, touched, counts, w.blk, w.off, counts,
+               max_pairs, status);
     launch_pdl(k_emit_pairs, 148 * 16, 256, 0, s, sorted_rec, w.off, radius, xy, co, ld, vt, alpha_min, counts, w.big, w.pk0,
                                           w.pv0);
     launch_pdl(k_emit_big, 148 * 4, 256, 0, s, sorted_rec, w.off, radius, xy, co, ld, vt, alpha_min, counts, w.big, w.pk0,
@@ -699,11 +706,10 @@ cudaError_t launch_sort(const int *radius, const int *touched, const float2 *xy,
     } else {
         launch_pdl(k_unpack_pairs, 148 * 8, 256, 0, s, w.pk0, w.pv0, counts, gauss_ids, block_mask, tile_ranges);
     }
-    e = cudaMemsetAsync(w.bucket, 0, sizeof(unsigned int) * 64, s);
+    e = cudaMemsetAsync(w.bucket, 0, sizeof(unsigned int) * 128, s);
     if (e != cudaSuccess) return e;
     const int tb = (int)std::min<long long>(ceil_div(vt.total_tiles, 256), 148 * 4);
     launch_pdl(k_tile_hist, tb, 256, 0, s, tile_ranges, vt.total_tiles, w.bucket);
-    launch_pdl(k_tile_scan, 1, 32, 0, s, w.bucket);
     launch_pdl(k_tile_scatter, tb, 256, 0, s, tile_ranges, vt.total_tiles, w.bucket, tile_order);
     return cudaGetLastError();
 }

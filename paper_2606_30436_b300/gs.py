@@ -1001,17 +1001,17 @@ class MappingStep:
 
 def launches_per_step(total_tiles, views=1, lambda_dssim=0.2, segment=512, fused_adam=False, adam_split=False):
     """Kernel launches of the library in one mapping iteration (memsets not
-    counted): project 1; sort 3 (visible records) + 4 depth passes (+ 1 view
-    pass with several views) + 5
-    (pair offsets, emission) + 1 per tile-bit pass (or 1 unpack for a single
-    tile) + 3 (render schedule); render 1 (4 with the split: plan, segments,
-    combine, re-runs); loss 3 (2 when lambda = 0) per view; backward 2
-    (compositing, projection); Adam 1 unless fused into the projection backward (2 when split
-    into the seen rows and the background part)."""
+    counted): project 1; sort 2 (visible records: count, compact) + 3 per LSD
+    pass (count, scan, scatter: 4 depth passes, 1 view pass with several views,
+    one per 8 tile bits, or 1 unpack for a single tile) + 4 (pair counts,
+    offsets, emission, long records) + 2 (render schedule); render 1 (4 with
+    the split: plan, segments, combine, re-runs); loss 2 per view; backward 2
+    (compositing, projection); Adam 1 unless fused into the projection backward
+    (2 when split into the seen rows and the background part)."""
     tile_bits = 0
     while (1 << tile_bits) < total_tiles:
         tile_bits += 1
     tile_passes = (tile_bits + 7) // 8
-    sort = 3 + 4 + (1 if views > 1 else 0) + 5 + (tile_passes if tile_passes else 1) + 3
-    loss = (3 if lambda_dssim > 0 else 2) * views
+    sort = 2 + 3 * (4 + (1 if views > 1 else 0) + tile_passes) + (0 if tile_passes else 1) + 4 + 2
+    loss = 2 * views
     return 1 + sort + (4 if segment else 1) + loss + 2 + (0 if fused_adam else 2 if adam_split else 1)

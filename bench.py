@@ -255,11 +255,11 @@ STAGES_FUSED = ["project", "sort", "render_fwd", "loss", "render_bwd", "project_
 # the library's kernels in each stage (a stage is one C-ABI call)
 STAGE_KERNELS = {
     "project": ["k_project"],
-    "sort": ["k_visible_count", "k_scan_blocks", "k_visible_compact", "k_rx_count", "k_rx_scan", "k_rx_scatter",
+    "sort": ["k_visible_count", "k_visible_compact", "k_rx_count", "k_rx_scan", "k_rx_scatter",
              "k_tiles_count", "k_tiles_offsets", "k_emit_pairs", "k_emit_big", "k_unpack_pairs", "k_tile_hist",
-             "k_tile_scan", "k_tile_scatter"],
+             "k_tile_scatter"],
     "render_fwd": ["k_fwd_plan", "k_render_fwd", "k_render_fwd_combine", "k_render_fwd_rerun"],
-    "loss": ["k_ssim_fwd", "k_ssim_bwd", "k_loss_final"],
+    "loss": ["k_ssim_fwd", "k_ssim_bwd"],
     "render_bwd": ["k_render_bwd"],
     "project_bwd": ["k_project_bwd"],
     "adam": ["k_adam", "k_adam_rows"],

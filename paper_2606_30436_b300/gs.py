@@ -875,7 +875,7 @@ class MappingStep:
     STAGES = ("project", "sort", "render_fwd", "loss", "render_bwd", "project_bwd", "adam")
     STAGES_FUSED = ("project", "sort", "render_fwd", "loss", "render_bwd", "project_bwd_adam")
 
-    def capture(self, target, stream=None, events=None):
+    def capture(self, target, stream=None, events=None, keep_graph=False):
         """Captures one whole iteration (status reset, project, sort, render,
         loss, backward, Adam) for the current cameras and `target` buffer into
         a CUDA graph.  Adam reads its step from a device counter that the graph
@@ -891,7 +891,7 @@ class MappingStep:
         assert events is None or len(events) == len(stages) + 1
         side = torch.cuda.Stream(device=dev)
         side.wait_stream(torch.cuda.current_stream(dev))
-        graph = torch.cuda.CUDAGraph()
+        graph = torch.cuda.CUDAGraph(keep_graph=keep_graph)  # keep_graph: its nodes stay readable
 
         def mark(i):
             if events is not None:

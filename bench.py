@@ -986,7 +986,7 @@ def run_anchors(args, dev):
     Gaussians along the 1 km corridor, SH0 colour from the view-dependent
     decoder, one 1280x720 view per iteration over the 16-frame pool; per
     iteration decode -> project / sort / render -> L1 + D-SSIM -> backward ->
-    decoder backward -> Adam on anchors and decoder (eager launches).  An
+    decoder backward -> Adam on anchors and decoder (one CUDA graph per frame).  An
     anchor's level is the LoD band of a log-uniform spawning distance in
     [2, 400] m, so each view activates, band by band, the anchors of the
     matching level."""
@@ -1034,6 +1034,15 @@ def run_anchors(args, dev):
         st.step(targets[i % len(cams)])
     torch.cuda.synchronize()
     st.map.check_status()
+    # one captured iteration per frame of the pool (the camera centre is a decoder argument)
+    graphs = []
+    for k, c in enumerate(cams):
+        st.set_camera(c)
+        graphs.append(st.capture(targets[k]))
+    for i in range(args.warmup):
+        st.replay(graphs[i % len(graphs)])
+    torch.cuda.synchronize()
+    st.map.check_status()
     steps = max(10, min(args.steps, 100))
     clocks = ClockSampler(dev.index)
     clocks.start()
@@ -1041,42 +1050,31 @@ def run_anchors(args, dev):
     torch.cuda.synchronize()
     e0.record(stream)
     for i in range(steps):
-        st.set_camera(cams[i % len(cams)])
-        st.step(targets[i % len(cams)])
+        st.replay(graphs[i % len(graphs)])
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / steps
     st.map.check_status()
-    # per-stage times (events between the C-ABI calls)
-    names = ("decode", "render_fwd", "loss_bwd", "decode_bwd", "adam")
+    # per-stage times: the same iterations captured with timing events at the stage boundaries
+    names = st.STAGES
+    tgraphs, tevents = [], []
+    for k, c in enumerate(cams):
+        st.set_camera(c)
+        ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(names) + 1)]
+        tgraphs.append(st.capture(targets[k], events=ev))
+        tevents.append(ev)
     acc = {k: 0.0 for k in names}
     for i in range(steps):
-        c = cams[i % len(cams)]
-        st.set_camera(c)
-        cc = anchors.camera_centre(c)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
-        ev[0].record(stream)
-        anchors.gs_anchor_decode(model, cc, st.gauss)
-        ev[1].record(stream)
-        st.map.forward()
-        ev[2].record(stream)
-        st.map._losses_and_backward(targets[i % len(cams)])
-        ev[3].record(stream)
-        anchors.gs_anchor_decode_bwd(model, cc, st.map.grads, st.g_anchor, st.g_w)
-        ev[4].record(stream)
-        st.step_count += 1
-        for lo, hi, lr in ((0, 32, 7.5e-3), (32, 35, 7e-3), (35, 65, 1e-2)):
-            anchors.gs_adam_flat(model.data[lo:hi], st.g_anchor[lo:hi], st.m_a[lo:hi], st.v_a[lo:hi], lr,
-                                 st.step_count)
-        anchors.gs_adam_flat(model.weights, st.g_w, st.m_w, st.v_w, 4e-3, st.step_count)
-        ev[5].record(stream)
+        st.replay(tgraphs[i % len(tgraphs)])
         torch.cuda.synchronize()
+        ev = tevents[i % len(tevents)]
         for j, k in enumerate(names):
             acc[k] += ev[j].elapsed_time(ev[j + 1])
+    del graphs, tgraphs
     stage = {k: round(v / steps, 4) for k, v in acc.items()}
     # device time of the decoder calls alone: ten back-to-back calls captured in a CUDA graph and
-    # replayed (the stage events above also hold the host's launch latency of each C-ABI call)
+    # replayed
     cc = anchors.camera_centre(cams[0])
     kern = {"decode": graph_call_ms(lambda: anchors.gs_anchor_decode(model, cc, st.gauss)),
             "decode_bwd": graph_call_ms(lambda: anchors.gs_anchor_decode_bwd(model, cc, st.map.grads, st.g_anchor,
@@ -1094,7 +1092,7 @@ def run_anchors(args, dev):
             "value": round(1e3 / ms, 2), "unit": "iters/s", "ms_per_step": round(ms, 4), "steps": steps,
             "warmup": args.warmup, "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "corridor anchors, K=10, 5 LoD levels, 1280x720, 16-frame pool",
-                       "anchors": n, "decoded_slots": 10 * model.ld, "launch": "eager",
+                       "anchors": n, "decoded_slots": 10 * model.ld, "launch": "graph per frame",
                        "decoder": "tcgen05, bf16 operands, f32 sums"},
             "stages_ms": stage, "decoder_call_ms": {k: round(v, 4) for k, v in kern.items()},
             "visible_mean": int(np.mean(vis)), "pairs_mean": int(np.mean(needed)),

@@ -738,9 +738,11 @@ gs_status gs_anchor_decode_bwd(const gs_anchor_params *a, const float *weights, 
                                float *grad_anchor, float *grad_weights, int32_t *status, int64_t max_polls,
                                gs_stream stream);
 
-/* Adam with bias correction over n contiguous floats (p, g, m, v device). */
+/* Adam with bias correction over n contiguous floats (p, g, m, v device).
+ * step_device (nullable device int64): as in gs_adam, the step count read
+ * when the kernel runs (`step` ignored), for captured CUDA graphs. */
 gs_status gs_adam_flat(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2,
-                       float eps, int64_t step, gs_stream stream);
+                       float eps, int64_t step, const int64_t *step_device, gs_stream stream);
 
 #ifdef __cplusplus
 }

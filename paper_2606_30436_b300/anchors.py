@@ -45,7 +45,7 @@ def _lib():
         L.gs_anchor_decode.argtypes = [P(AnchorParams), vp, P(f32 * 3), vp, i32, P(gs.Params), vp, i64, vp]
         L.gs_anchor_decode_bwd.argtypes = [P(AnchorParams), vp, P(f32 * 3), vp, i32, P(gs.Params), vp, vp, vp, i64,
                                            vp]
-        L.gs_adam_flat.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp]
+        L.gs_adam_flat.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp, vp]
         _typed = True
     return L
 
@@ -129,9 +129,10 @@ def gs_anchor_decode_bwd(model: AnchorModel, cam_centre, grad_out: gs.GaussianMo
               "gs_anchor_decode_bwd")
 
 
-def gs_adam_flat(p, g, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+def gs_adam_flat(p, g, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None, step_device=None):
     gs._check(_lib().gs_adam_flat(gs._ptr(p), gs._ptr(g), gs._ptr(m), gs._ptr(v), p.numel(), float(lr),
-                                  float(beta1), float(beta2), float(eps), int(step), gs._stream(stream)),
+                                  float(beta1), float(beta2), float(eps), int(step), gs._ptr(step_device),
+                                  gs._stream(stream)),
               "gs_adam_flat")
 
 
@@ -178,12 +179,62 @@ class AnchorStep:
                              status=status)
         return loss
 
+    def _adam(self, t, stream=None, step_device=None):
+        A, G, M, V = self.model.data, self.g_anchor, self.m_a, self.v_a
+        for name, lo, hi in (("feat", 0, FEAT), ("log_l", FEAT, FEAT + 3), ("offs", FEAT + 3, PLANES)):
+            gs_adam_flat(A[lo:hi], G[lo:hi], M[lo:hi], V[lo:hi], self.lr[name], t, stream=stream,
+                         step_device=step_device)
+        gs_adam_flat(self.model.weights, self.g_w, self.m_w, self.v_w, self.lr["weights"], t, stream=stream,
+                     step_device=step_device)
+
     def step(self, target, stream=None):
         loss = self.gradients(target, stream)
         self.step_count += 1
-        t = self.step_count
-        A, G, M, V = self.model.data, self.g_anchor, self.m_a, self.v_a
-        for name, lo, hi in (("feat", 0, FEAT), ("log_l", FEAT, FEAT + 3), ("offs", FEAT + 3, PLANES)):
-            gs_adam_flat(A[lo:hi], G[lo:hi], M[lo:hi], V[lo:hi], self.lr[name], t, stream=stream)
-        gs_adam_flat(self.model.weights, self.g_w, self.m_w, self.v_w, self.lr["weights"], t, stream=stream)
+        self._adam(self.step_count, stream)
         return loss
+
+    STAGES = ("decode", "render_fwd", "loss_bwd", "decode_bwd", "adam")
+
+    def capture(self, target, events=None):
+        """One whole iteration for the current camera (its centre is a decoder argument, so a
+        graph per camera) in a CUDA graph: decode, project / sort / render, losses and
+        backward, decoder backward, Adam with a device step counter that the graph advances.
+        events: optional timing events (external=True), one more than STAGES."""
+        dev = self.model.data.device
+        if getattr(self, "step_dev", None) is None:
+            self.step_dev = torch.full((1,), self.step_count, dtype=torch.int64, device=dev)
+        assert events is None or len(events) == len(self.STAGES) + 1
+        cc = camera_centre(self.cam)
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        graph = torch.cuda.CUDAGraph()
+
+        def mark(i):
+            if events is not None:
+                events[i].record(side)
+
+        with torch.cuda.graph(graph, stream=side):
+            b = self.map.buf
+            b.status.zero_()
+            self.step_dev.add_(1)
+            mark(0)
+            gs_anchor_decode(self.model, cc, self.gauss, self.max_dist, status=b.status)
+            mark(1)
+            gs.gs_project(self.gauss, b)
+            gs.gs_sort(b)
+            gs.gs_render_fwd(b)
+            mark(2)
+            self.map._losses_and_backward(target)
+            mark(3)
+            gs_anchor_decode_bwd(self.model, cc, self.map.grads, self.g_anchor, self.g_w, self.max_dist,
+                                 status=b.status)
+            mark(4)
+            self._adam(1, step_device=self.step_dev)
+            mark(5)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        return graph
+
+    def replay(self, graph):
+        graph.replay()
+        self.step_count += 1
+        return self.map.buf.loss

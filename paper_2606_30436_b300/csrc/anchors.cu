@@ -628,13 +628,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_anchor_decode_bwd(const float *
 
 __global__ void k_adam_flat(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
                             float *__restrict__ v, long long n, float lr, float b1, float b2, float eps, float bc1,
-                            float bc2) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.0f - b1) * gi, vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+                            float bc2, const long long *__restrict__ step_dev) {
+    if (step_dev) {  // bias corrections from the device step counter (graph replay)
+        __shared__ float s_bc[2];
+        if (threadIdx.x == 0) {
+            const double t = (double)*step_dev;
+            s_bc[0] = (float)(1.0 - pow((double)b1, t));
+            s_bc[1] = (float)(1.0 - pow((double)b2, t));
+        }
+        __syncthreads();
+        bc1 = s_bc[0];
+        bc2 = s_bc[1];
+    }
+    // float4 where the four arrays allow it (the anchor planes and the decoder weights do),
+    // with the SFU's square root and division as in the Gaussians' Adam
+    const bool vec = ((((uintptr_t)p | (uintptr_t)g | (uintptr_t)m | (uintptr_t)v) & 15u) == 0) && (n & 3) == 0;
+    const float ibc1 = 1.0f / bc1, isbc2 = rsqrtf(bc2);
+    auto upd = [&](float &pi, float gi, float &mi, float &vi) {
+        mi = b1 * mi + (1.0f - b1) * gi;
+        vi = b2 * vi + (1.0f - b2) * gi * gi;
+        float sq;
+        asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(vi));
+        pi -= __fdividef(lr * (mi * ibc1), sq * isbc2 + eps);
+    };
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (vec) {
+        float4 *p4 = reinterpret_cast<float4 *>(p), *m4 = reinterpret_cast<float4 *>(m);
+        float4 *v4 = reinterpret_cast<float4 *>(v);
+        const float4 *g4 = reinterpret_cast<const float4 *>(g);
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n / 4; i += stride) {
+            float4 pp = p4[i], mm = m4[i], vv = v4[i];
+            const float4 gg = g4[i];
+            upd(pp.x, gg.x, mm.x, vv.x); upd(pp.y, gg.y, mm.y, vv.y);
+            upd(pp.z, gg.z, mm.z, vv.z); upd(pp.w, gg.w, mm.w, vv.w);
+            p4[i] = pp; m4[i] = mm; v4[i] = vv;
+        }
+    } else {
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+            float pi = p[i], mi = m[i], vi = v[i];
+            upd(pi, g[i], mi, vi);
+            p[i] = pi; m[i] = mi; v[i] = vi;
+        }
     }
 }
 
@@ -690,12 +724,13 @@ cudaError_t launch_anchor_decode_bwd(const float *A, const float *pos, const int
 }
 
 cudaError_t launch_adam_flat(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
-                             float eps, long long step, cudaStream_t s) {
+                             float eps, long long step, const long long *step_dev, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const float bc1 = (float)(1.0 - std::pow((double)b1, (double)step));
-    const float bc2 = (float)(1.0 - std::pow((double)b2, (double)step));
+    const double st = step_dev ? 1.0 : (double)step;  // placeholder when the device counter is used
+    const float bc1 = (float)(1.0 - std::pow((double)b1, st));
+    const float bc2 = (float)(1.0 - std::pow((double)b2, st));
     const long long blocks = std::min<long long>(ceil_div(n, 256ll), 4096ll);
-    k_adam_flat<<<(unsigned)blocks, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
+    k_adam_flat<<<(unsigned)blocks, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2, step_dev);
     return cudaGetLastError();
 }
 

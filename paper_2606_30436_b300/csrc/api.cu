@@ -859,9 +859,11 @@ GS_API gs_status gs_anchor_decode_bwd(const gs_anchor_params *a, const float *we
 }
 
 GS_API gs_status gs_adam_flat(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,
-                              float beta2, float eps, int64_t step, gs_stream stream) {
-    if (n < 0 || (n > 0 && (!p || !g || !m || !v)) || step < 1 || !(beta1 >= 0.0f && beta1 < 1.0f) ||
-        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f) || !(lr >= 0.0f))
+                              float beta2, float eps, int64_t step, const int64_t *step_device, gs_stream stream) {
+    if (n < 0 || (n > 0 && (!p || !g || !m || !v)) || (step < 1 && !step_device) ||
+        !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps >= 0.0f) || !(lr >= 0.0f) ||
+        ((uintptr_t)step_device & 7u))
         return GS_ERR_INVALID;
-    return cuda_status(launch_adam_flat(p, g, m, v, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream));
+    return cuda_status(launch_adam_flat(p, g, m, v, n, lr, beta1, beta2, eps, step, (const long long *)step_device,
+                                        (cudaStream_t)stream));
 }

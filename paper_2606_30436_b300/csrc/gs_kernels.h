@@ -157,6 +157,6 @@ cudaError_t launch_anchor_decode_bwd(const float *A, const float *pos, const int
                                      const float *w, const AnchorView &v, const float *GG, long long gld, float *gA,
                                      float *gw, int *status, long long max_polls, cudaStream_t s);
 cudaError_t launch_adam_flat(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
-                             float eps, long long step, cudaStream_t s);
+                             float eps, long long step, const long long *step_dev, cudaStream_t s);
 
 }  // namespace gs

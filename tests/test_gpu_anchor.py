@@ -262,16 +262,52 @@ def test_anchor_iteration_gradients_match_oracle():
     assert rel_l2(g, gw) < tol, (rel_l2(g, gw), tol)
 
 
-def test_adam_flat_matches_oracle():
+@pytest.mark.parametrize("n", [1003, 1004])  # the scalar and the float4 path
+def test_adam_flat_matches_oracle(n):
     rng = np.random.default_rng(2)
-    p, g = rng.normal(size=1003).astype(np.float32), rng.normal(size=1003).astype(np.float32)
-    m, v = (0.1 * rng.normal(size=1003)).astype(np.float32), rng.random(1003).astype(np.float32)
+    p, g = rng.normal(size=n).astype(np.float32), rng.normal(size=n).astype(np.float32)
+    m, v = (0.1 * rng.normal(size=n)).astype(np.float32), rng.random(n).astype(np.float32)
     t = [torch.from_numpy(x.copy()).to(DEV) for x in (p, g, m, v)]
     anchors.gs_adam_flat(t[0], t[1], t[2], t[3], 1e-3, 5, eps=1e-8)
     pw, pm, pv = (x.astype(np.float64) for x in (p, m, v))
-    orc.adam(pw, g.astype(np.float64), pm, pv, np.full(1003, 1e-3), 5, eps=1e-8)
+    orc.adam(pw, g.astype(np.float64), pm, pv, np.full(n, 1e-3), 5, eps=1e-8)
     assert np.abs(t[0].cpu().double().numpy() - pw).max() < 1e-6
     assert np.abs(t[3].cpu().double().numpy() - pv).max() < 1e-6
+
+
+def test_adam_flat_device_step_matches_host_step():
+    rng = np.random.default_rng(4)
+    x = [rng.normal(size=776).astype(np.float32) for _ in range(3)] + [rng.random(776).astype(np.float32)]
+    a = [torch.from_numpy(v.copy()).to(DEV) for v in x]
+    b = [torch.from_numpy(v.copy()).to(DEV) for v in x]
+    anchors.gs_adam_flat(a[0], a[1], a[2], a[3], 1e-3, 7)
+    anchors.gs_adam_flat(b[0], b[1], b[2], b[3], 1e-3, 1, step_device=torch.full((1,), 7, dtype=torch.int64,
+                                                                                 device=DEV))
+    torch.cuda.synchronize()
+    for u, w in zip(a, b):
+        assert torch.equal(u, w)
+
+
+def test_anchor_graph_replay_matches_eager_steps():
+    A, w, cam, cc, oc, target = _step_case(23)
+    tgt = torch.from_numpy(target.reshape(-1)).to(DEV)
+    runs = []
+    for graph in (False, True):
+        st = anchors.AnchorStep(_model(A, w), cam, gs.Config(), lambda_dssim=0.2)
+        st.fit_capacity(slack=3.0)
+        losses = []
+        g = st.capture(tgt) if graph else None
+        for _ in range(4):
+            losses.append(float((st.replay(g) if graph else st.step(tgt)).item()))
+        torch.cuda.synchronize()
+        st.map.check_status()
+        runs.append((losses, st.model.data.clone(), st.model.weights.clone(), st.step_count))
+    (la, pa, wa, ca), (lb, pb, wb, cb) = runs
+    assert ca == cb == 4
+    # the compositing backward sums with atomics: two runs agree to FP32 rounding
+    assert np.allclose(la, lb, rtol=1e-4, atol=0.0), (la, lb)
+    assert rel_l2(pa.cpu().numpy(), pb.cpu().numpy()) < 1e-5
+    assert rel_l2(wa.cpu().numpy(), wb.cpu().numpy()) < 1e-5
 
 
 def test_anchor_steps_lower_the_loss():

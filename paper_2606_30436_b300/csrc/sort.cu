@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(kRxThreads, kRxCtasPerSm) k_rx_scatter(RxPass 
 }
 
 static void rx_pass(RxPass a, cudaStream_t s) {
-    a.nblocks = kRxBlocks;
+    // one wave of CTAs, but no more than a round of kRxRound elements each at the capacity
+    a.nblocks = (int)std::min<long long>(kRxBlocks, std::max(1ll, ceil_div(a.cap, (long long)kRxRound)));
     launch_pdl(k_rx_count, a.nblocks, kRxThreads, 0, s, a);
     launch_pdl(k_rx_scan, 1 << a.bits, kRxScanThreads, 0, s, a);
     launch_pdl(k_rx_scatter, a.nblocks, kRxThreads, 0, s, a);

@@ -315,7 +315,7 @@ static void rx_pass(RxPass a, cudaStream_t s) {
     // one wave of CTAs, but no more than a round of kRxRound elements each at the capacity
     a.nblocks = (int)std::min<long long>(kRxBlocks, std::max(1ll, ceil_div(a.cap, (long long)kRxRound)));
     launch_pdl(k_rx_count, a.nblocks, kRxThreads, 0, s, a);
-    launch_pdl(k_rx_scan, 1 << a.bits, kRxScanThreads, 0, s, a);
+    launch_pdl(k_rx_scan, 1 << a.bits, (a.nblocks + 31) / 32 * 32, 0, s, a);  // a thread per counting CTA
     launch_pdl(k_rx_scatter, a.nblocks, kRxThreads, 0, s, a);
 }
 

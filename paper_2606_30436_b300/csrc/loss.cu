@@ -8,8 +8,9 @@
 // s_xy) the gradient with respect to the rendered image x is
 //   dSSIM/dx(q) = (G*A)(q) + 2 x(q) (G*B)(q) + y(q) (G*Cm)(q),
 //   A = ds/dmu_x - 2 mu_x ds/ds_xx - mu_y ds/ds_xy,  B = ds/ds_xx,  Cm = ds/ds_xy,
-// so the forward writes A, B, Cm and a second pass blurs them.  Sums for the
-// scalar loss are reduced per CTA and then in a fixed order (deterministic).
+// so the forward writes A, B, Cm and a second pass blurs them.  Both passes
+// are register-blocked (below).  Sums for the scalar loss are reduced per CTA
+// and then in a fixed order (deterministic).
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -42,12 +43,40 @@ __device__ __forceinline__ double block_sum_d(double v, double *sm) {
     return r;
 }
 
+// Per-thread float partials summed in float within each warp, the warp totals
+// in double and in a fixed order: a handful of double operations per block,
+// none per pixel (FP64 issues at a small fraction of the FP32 rate here).
+__device__ __forceinline__ double block_sum_f(float v, double *sm) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sm[warp] = (double)v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sm[i];
+    __syncthreads();
+    return r;
+}
+
+// Register-blocked separable passes over a staged tile.  Horizontal: a thread
+// owns kHS consecutive outputs of one staged row and walks the kHS + 10 inputs
+// once, adding each (and its products) into every output whose window holds
+// it; the lanes of a warp take consecutive rows, so with odd row strides their
+// shared-memory words fall in distinct banks.  Vertical: a lane owns one
+// column and kVR consecutive output rows of it.  Every output still sums its
+// 11 taps in window order.
+constexpr int kHS = 8;                      // outputs per thread, horizontal pass
+constexpr int kHItems = kLI * (kLT / kHS);  // 42 rows x 4 strips = 168 busy threads
+constexpr int kVR = 4;                      // output rows per thread, vertical pass (8 warps x 4 = 32)
+constexpr int kLH = kLT + 1;                // padded row of the horizontal results
+
 __global__ void __launch_bounds__(256) k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int H,
                                                    int W, Win win, float *__restrict__ maps, int want_grad,
                                                    double *__restrict__ partials) {
     griddep_wait();
     __shared__ float sx[kLI][kLI + 1], sy[kLI][kLI + 1];
-    __shared__ float h[5][kLI][kLT];
+    __shared__ float h[5][kLI][kLH];
     __shared__ double sm[8];
     const int ch = blockIdx.z;
     const long long plane = (long long)H * W;
@@ -61,38 +90,60 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(const float *__restrict__ x, c
         sy[r][c] = in ? yc[(long long)gy * W + gx] : 0.0f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kLI * kLT; i += 256) {
-        const int r = i / kLT, c = i - r * kLT;
-        float a = 0, b = 0, aa = 0, bb = 0, ab = 0;
+    if (threadIdx.x < kHItems) {
+        const int r = threadIdx.x % kLI, c0 = (threadIdx.x / kLI) * kHS;
+        float a[kHS], b[kHS], aa[kHS], bb[kHS], ab[kHS];
         #pragma unroll
-        for (int k = 0; k < 2 * kLR + 1; ++k) {
-            const float wx = win.w[k], xv = sx[r][c + k], yv = sy[r][c + k];
-            a += wx * xv; b += wx * yv; aa += wx * xv * xv; bb += wx * yv * yv; ab += wx * xv * yv;
+        for (int o = 0; o < kHS; ++o) a[o] = b[o] = aa[o] = bb[o] = ab[o] = 0.0f;
+        #pragma unroll
+        for (int j = 0; j < kHS + 2 * kLR; ++j) {
+            const float u = sx[r][c0 + j], v = sy[r][c0 + j];
+            const float uu = u * u, vv = v * v, uv = u * v;
+            #pragma unroll
+            for (int o = 0; o < kHS; ++o) {
+                const int k = j - o;
+                if (k < 0 || k > 2 * kLR) continue;
+                const float wk = win.w[k];
+                a[o] += wk * u; b[o] += wk * v; aa[o] += wk * uu; bb[o] += wk * vv; ab[o] += wk * uv;
+            }
         }
-        h[0][r][c] = a; h[1][r][c] = b; h[2][r][c] = aa; h[3][r][c] = bb; h[4][r][c] = ab;
+        #pragma unroll
+        for (int o = 0; o < kHS; ++o) {
+            h[0][r][c0 + o] = a[o]; h[1][r][c0 + o] = b[o]; h[2][r][c0 + o] = aa[o];
+            h[3][r][c0 + o] = bb[o]; h[4][r][c0 + o] = ab[o];
+        }
     }
     __syncthreads();
-    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
-    double l1 = 0.0, ss = 0.0;
-    for (int i = threadIdx.x; i < kLT * kLT; i += 256) {
-        const int r = i / kLT, c = i - r * kLT;
-        const int gy = oy + r, gx = ox + c;
-        if (gy >= H || gx >= W) continue;
-        float mx = 0, my = 0, exx = 0, eyy = 0, exy = 0;
+    const int c = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * kVR;
+    float mom[5][kVR];
+    #pragma unroll
+    for (int m = 0; m < 5; ++m) {
         #pragma unroll
-        for (int k = 0; k < 2 * kLR + 1; ++k) {
-            const float wy = win.w[k];
-            mx += wy * h[0][r + k][c]; my += wy * h[1][r + k][c];
-            exx += wy * h[2][r + k][c]; eyy += wy * h[3][r + k][c]; exy += wy * h[4][r + k][c];
+        for (int q = 0; q < kVR; ++q) mom[m][q] = 0.0f;
+        #pragma unroll
+        for (int i = 0; i < kVR + 2 * kLR; ++i) {
+            const float v = h[m][r0 + i][c];
+            #pragma unroll
+            for (int q = 0; q < kVR; ++q) {
+                const int k = i - q;
+                if (k >= 0 && k <= 2 * kLR) mom[m][q] += win.w[k] * v;
+            }
         }
-        const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+    }
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    float l1 = 0.0f, ss = 0.0f;
+    #pragma unroll
+    for (int q = 0; q < kVR; ++q) {
+        const int r = r0 + q, gy = oy + r, gx = ox + c;
+        if (gy >= H || gx >= W) continue;
+        const float mx = mom[0][q], my = mom[1][q];
+        const float sxx = mom[2][q] - mx * mx, syy = mom[3][q] - my * my, sxy = mom[4][q] - mx * my;
         const float A1 = 2.0f * mx * my + C1, A2 = 2.0f * sxy + C2;
         const float B1 = mx * mx + my * my + C1, B2 = sxx + syy + C2;
         const float iB = 1.0f / (B1 * B2);
         const float s = A1 * A2 * iB;
         ss += s;
-        const float xv = sx[r + kLR][c + kLR], yv = sy[r + kLR][c + kLR];
-        l1 += fabsf(xv - yv);
+        l1 += fabsf(sx[r + kLR][c + kLR] - sy[r + kLR][c + kLR]);
         if (want_grad) {
             const float dmu = 2.0f * my * A2 * iB - 2.0f * mx * s / B1;
             const float dsxx = -s / B2;
@@ -103,8 +154,8 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(const float *__restrict__ x, c
             maps[(3 * ch + 2) * plane + o] = dsxy;
         }
     }
-    const double tl1 = block_sum_d(l1, sm);
-    const double tss = block_sum_d(ss, sm);
+    const double tl1 = block_sum_f(l1, sm);
+    const double tss = block_sum_f(ss, sm);
     if (threadIdx.x == 0) {
         const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         partials[2 * b] = tl1;
@@ -119,7 +170,7 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(const float *__restrict__ x, c
                                                    float lambda, float *__restrict__ loss_out) {
     griddep_wait();
     __shared__ float sm[3][kLI][kLI + 1];
-    __shared__ float h[3][kLI][kLT];
+    __shared__ float h[3][kLI][kLH];
     const int ch = blockIdx.z;
     const long long plane = (long long)H * W;
     const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
@@ -132,30 +183,55 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(const float *__restrict__ x, c
         for (int m = 0; m < 3; ++m) sm[m][r][c] = in ? maps[(3 * ch + m) * plane + o] : 0.0f;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kLI * kLT; i += 256) {
-        const int r = i / kLT, c = i - r * kLT;
-        float a = 0, b = 0, d = 0;
+    if (threadIdx.x < kHItems) {
+        const int r = threadIdx.x % kLI, c0 = (threadIdx.x / kLI) * kHS;
+        float acc[3][kHS];
         #pragma unroll
-        for (int k = 0; k < 2 * kLR + 1; ++k) {
-            const float wx = win.w[k];
-            a += wx * sm[0][r][c + k]; b += wx * sm[1][r][c + k]; d += wx * sm[2][r][c + k];
+        for (int m = 0; m < 3; ++m) {
+            #pragma unroll
+            for (int o = 0; o < kHS; ++o) acc[m][o] = 0.0f;
         }
-        h[0][r][c] = a; h[1][r][c] = b; h[2][r][c] = d;
+        #pragma unroll
+        for (int j = 0; j < kHS + 2 * kLR; ++j) {
+            const float u0 = sm[0][r][c0 + j], u1 = sm[1][r][c0 + j], u2 = sm[2][r][c0 + j];
+            #pragma unroll
+            for (int o = 0; o < kHS; ++o) {
+                const int k = j - o;
+                if (k < 0 || k > 2 * kLR) continue;
+                const float wk = win.w[k];
+                acc[0][o] += wk * u0; acc[1][o] += wk * u1; acc[2][o] += wk * u2;
+            }
+        }
+        #pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            #pragma unroll
+            for (int o = 0; o < kHS; ++o) h[m][r][c0 + o] = acc[m][o];
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kLT * kLT; i += 256) {
-        const int r = i / kLT, c = i - r * kLT;
-        const int gy = oy + r, gx = ox + c;
-        if (gy >= H || gx >= W) continue;
-        float a = 0, b = 0, d = 0;
+    const int c = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * kVR;
+    float g[3][kVR];
+    #pragma unroll
+    for (int m = 0; m < 3; ++m) {
         #pragma unroll
-        for (int k = 0; k < 2 * kLR + 1; ++k) {
-            const float wy = win.w[k];
-            a += wy * h[0][r + k][c]; b += wy * h[1][r + k][c]; d += wy * h[2][r + k][c];
+        for (int q = 0; q < kVR; ++q) g[m][q] = 0.0f;
+        #pragma unroll
+        for (int i = 0; i < kVR + 2 * kLR; ++i) {
+            const float v = h[m][r0 + i][c];
+            #pragma unroll
+            for (int q = 0; q < kVR; ++q) {
+                const int k = i - q;
+                if (k >= 0 && k <= 2 * kLR) g[m][q] += win.w[k] * v;
+            }
         }
+    }
+    #pragma unroll
+    for (int q = 0; q < kVR; ++q) {
+        const int gy = oy + r0 + q, gx = ox + c;
+        if (gy >= H || gx >= W) continue;
         const long long o = ch * plane + (long long)gy * W + gx;
         const float xv = x[o], yv = y[o];
-        dL[o] = l1_scale * sgn(xv - yv) - ssim_scale * (a + 2.0f * xv * b + yv * d);
+        dL[o] = l1_scale * sgn(xv - yv) - ssim_scale * (g[0][q] + 2.0f * xv * g[1][q] + yv * g[2][q]);
     }
     // the scalar loss from the forward's per-CTA sums, by one block (a launch fewer)
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {

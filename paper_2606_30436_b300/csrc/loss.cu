@@ -65,11 +65,13 @@ __device__ __forceinline__ double block_sum_f(float v, double *sm) {
 // it; the lanes of a warp take consecutive rows, so with odd row strides their
 // shared-memory words fall in distinct banks.  Vertical: a lane owns one
 // column and kVR consecutive output rows of it.  Every output still sums its
-// 11 taps in window order.
+// 11 taps in window order.  Staging issues all of a thread's global loads
+// before its first shared-memory store, so their latencies overlap.
 constexpr int kHS = 8;                      // outputs per thread, horizontal pass
 constexpr int kHItems = kLI * (kLT / kHS);  // 42 rows x 4 strips = 168 busy threads
 constexpr int kVR = 4;                      // output rows per thread, vertical pass (8 warps x 4 = 32)
 constexpr int kLH = kLT + 1;                // padded row of the horizontal results
+constexpr int kStR = (kLI + 7) / 8;         // staged rows per warp (8 warps; 32 + 10 columns a row)
 
 __global__ void __launch_bounds__(256) k_ssim_fwd(const float *__restrict__ x, const float *__restrict__ y, int H,
                                                    int W, Win win, float *__restrict__ maps, int want_grad,
@@ -82,12 +84,27 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(const float *__restrict__ x, c
     const long long plane = (long long)H * W;
     const float *xc = x + ch * plane, *yc = y + ch * plane;
     const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
-    for (int i = threadIdx.x; i < kLI * kLI; i += 256) {
-        const int r = i / kLI, c = i - r * kLI;
-        const int gy = oy + r - kLR, gx = ox + c - kLR;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        sx[r][c] = in ? xc[(long long)gy * W + gx] : 0.0f;
-        sy[r][c] = in ? yc[(long long)gy * W + gx] : 0.0f;
+    {
+        float vx[kStR][2], vy[kStR][2];
+        #pragma unroll
+        for (int t = 0; t < kStR; ++t) {
+            #pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int r = (threadIdx.x >> 5) + 8 * t, c = (threadIdx.x & 31) + 32 * e;
+                const int gy = oy + r - kLR, gx = ox + c - kLR;
+                const bool in = r < kLI && c < kLI && gy >= 0 && gy < H && gx >= 0 && gx < W;
+                vx[t][e] = in ? xc[(long long)gy * W + gx] : 0.0f;
+                vy[t][e] = in ? yc[(long long)gy * W + gx] : 0.0f;
+            }
+        }
+        #pragma unroll
+        for (int t = 0; t < kStR; ++t) {
+            #pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int r = (threadIdx.x >> 5) + 8 * t, c = (threadIdx.x & 31) + 32 * e;
+                if (r < kLI && c < kLI) { sx[r][c] = vx[t][e]; sy[r][c] = vy[t][e]; }
+            }
+        }
     }
     __syncthreads();
     if (threadIdx.x < kHItems) {
@@ -174,13 +191,42 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(const float *__restrict__ x, c
     const int ch = blockIdx.z;
     const long long plane = (long long)H * W;
     const int ox = blockIdx.x * kLT, oy = blockIdx.y * kLT;
-    for (int i = threadIdx.x; i < kLI * kLI; i += 256) {
-        const int r = i / kLI, c = i - r * kLI;
-        const int gy = oy + r - kLR, gx = ox + c - kLR;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const long long o = (long long)gy * W + gx;
+    const int c = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * kVR;
+    {
+        float v[3][kStR][2];
         #pragma unroll
-        for (int m = 0; m < 3; ++m) sm[m][r][c] = in ? maps[(3 * ch + m) * plane + o] : 0.0f;
+        for (int t = 0; t < kStR; ++t) {
+            #pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int r = (threadIdx.x >> 5) + 8 * t, cc = c + 32 * e;
+                const int gy = oy + r - kLR, gx = ox + cc - kLR;
+                const bool in = r < kLI && cc < kLI && gy >= 0 && gy < H && gx >= 0 && gx < W;
+                const long long o = (long long)gy * W + gx;
+                #pragma unroll
+                for (int m = 0; m < 3; ++m) v[m][t][e] = in ? maps[(3 * ch + m) * plane + o] : 0.0f;
+            }
+        }
+        #pragma unroll
+        for (int t = 0; t < kStR; ++t) {
+            #pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int r = (threadIdx.x >> 5) + 8 * t, cc = c + 32 * e;
+                if (r < kLI && cc < kLI) {
+                    #pragma unroll
+                    for (int m = 0; m < 3; ++m) sm[m][r][cc] = v[m][t][e];
+                }
+            }
+        }
+    }
+    // this thread's image values for the epilogue, fetched while the tile is staged
+    float xe[kVR], ye[kVR];
+    #pragma unroll
+    for (int q = 0; q < kVR; ++q) {
+        const int gy = oy + r0 + q, gx = ox + c;
+        const bool in = gy < H && gx < W;
+        const long long o = ch * plane + (long long)gy * W + gx;
+        xe[q] = in ? x[o] : 0.0f;
+        ye[q] = in ? y[o] : 0.0f;
     }
     __syncthreads();
     if (threadIdx.x < kHItems) {
@@ -209,7 +255,6 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(const float *__restrict__ x, c
         }
     }
     __syncthreads();
-    const int c = threadIdx.x & 31, r0 = (threadIdx.x >> 5) * kVR;
     float g[3][kVR];
     #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -230,7 +275,7 @@ __global__ void __launch_bounds__(256) k_ssim_bwd(const float *__restrict__ x, c
         const int gy = oy + r0 + q, gx = ox + c;
         if (gy >= H || gx >= W) continue;
         const long long o = ch * plane + (long long)gy * W + gx;
-        const float xv = x[o], yv = y[o];
+        const float xv = xe[q], yv = ye[q];
         dL[o] = l1_scale * sgn(xv - yv) - ssim_scale * (g[0][q] + 2.0f * xv * g[1][q] + yv * g[2][q]);
     }
     // the scalar loss from the forward's per-CTA sums, by one block (a launch fewer)

@@ -43,20 +43,24 @@ __device__ __forceinline__ double block_sum_d(double v, double *sm) {
     return r;
 }
 
-// Per-thread float partials summed in float within each warp, the warp totals
-// in double and in a fixed order: a handful of double operations per block,
-// none per pixel (FP64 issues at a small fraction of the FP32 rate here).
-__device__ __forceinline__ double block_sum_f(float v, double *sm) {
+// Sum of per-thread FP32 partials over the block, in FP32 and a fixed order
+// (a CTA sums 1024 pixels' terms; the per-CTA totals are added in FP64 by the
+// final reduction).  No FP64 operation per pixel or per block: FP64 issues at
+// a small fraction of the FP32 rate here.
+__device__ __forceinline__ double block_sum_f(float v, float *sm) {
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) sm[warp] = (double)v;
+    if (lane == 0) sm[warp] = v;
     __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sm[i];
+    float r = 0.0f;
+    if (warp == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0.0f;
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
     __syncthreads();
-    return r;
+    return (double)r;
 }
 
 // Register-blocked separable passes over a staged tile.  Horizontal: a thread
@@ -79,7 +83,7 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(const float *__restrict__ x, c
     griddep_wait();
     __shared__ float sx[kLI][kLI + 1], sy[kLI][kLI + 1];
     __shared__ float h[5][kLI][kLH];
-    __shared__ double sm[8];
+    __shared__ float sm[8];
     const int ch = blockIdx.z;
     const long long plane = (long long)H * W;
     const float *xc = x + ch * plane, *yc = y + ch * plane;
@@ -161,9 +165,9 @@ __global__ void __launch_bounds__(256) k_ssim_fwd(const float *__restrict__ x, c
         const float s = A1 * A2 * iB;
         ss += s;
         l1 += fabsf(sx[r + kLR][c + kLR] - sy[r + kLR][c + kLR]);
-        if (want_grad) {
-            const float dmu = 2.0f * my * A2 * iB - 2.0f * mx * s / B1;
-            const float dsxx = -s / B2;
+        if (want_grad) {  // 1/B1 = B2 iB and 1/B2 = B1 iB: one division per pixel
+            const float dmu = 2.0f * my * A2 * iB - 2.0f * mx * s * (B2 * iB);
+            const float dsxx = -s * (B1 * iB);
             const float dsxy = 2.0f * A1 * iB;
             const long long o = (long long)gy * W + gx;
             maps[(3 * ch + 0) * plane + o] = dmu - 2.0f * mx * dsxx - my * dsxy;

@@ -31,9 +31,7 @@ __global__ void __launch_bounds__(256) k_adam(float4 *__restrict__ p, const floa
     if (step_dev) {  // bias corrections from the device step counter (graph replay)
         __shared__ float s_bc[2];
         if (threadIdx.x == 0) {
-            const double t = (double)*step_dev;
-            s_bc[0] = (float)(1.0 / (1.0 - pow((double)b1, t)));
-            s_bc[1] = (float)(1.0 / sqrt(1.0 - pow((double)b2, t)));
+            adam_bias_inv(b1, b2, *step_dev, s_bc[0], s_bc[1]);
         }
         __syncthreads();
         inv_bc1 = s_bc[0];
@@ -95,9 +93,7 @@ __global__ void __launch_bounds__(256) k_adam_rows(float4 *__restrict__ p, const
     if (step_dev) {
         __shared__ float s_bc[2];
         if (threadIdx.x == 0) {
-            const double t = (double)*step_dev;
-            s_bc[0] = (float)(1.0 / (1.0 - pow((double)b1, t)));
-            s_bc[1] = (float)(1.0 / sqrt(1.0 - pow((double)b2, t)));
+            adam_bias_inv(b1, b2, *step_dev, s_bc[0], s_bc[1]);
         }
         __syncthreads();
         inv_bc1 = s_bc[0];
@@ -163,9 +159,7 @@ __global__ void __launch_bounds__(kBgThreads, 1) k_adam_unseen(float4 *__restric
     if (step_dev) {
         __shared__ float s_bc[2];
         if (threadIdx.x == 0) {
-            const double t = (double)*step_dev;
-            s_bc[0] = (float)(1.0 / (1.0 - pow((double)b1, t)));
-            s_bc[1] = (float)(1.0 / sqrt(1.0 - pow((double)b2, t)));
+            adam_bias_inv(b1, b2, *step_dev, s_bc[0], s_bc[1]);
         }
         __syncthreads();
         inv_bc1 = s_bc[0];

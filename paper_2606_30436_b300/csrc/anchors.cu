@@ -632,9 +632,7 @@ __global__ void k_adam_flat(float *__restrict__ p, const float *__restrict__ g, 
     if (step_dev) {  // bias corrections from the device step counter (graph replay)
         __shared__ float s_bc[2];
         if (threadIdx.x == 0) {
-            const double t = (double)*step_dev;
-            s_bc[0] = (float)(1.0 - pow((double)b1, t));
-            s_bc[1] = (float)(1.0 - pow((double)b2, t));
+            adam_bias(b1, b2, *step_dev, s_bc[0], s_bc[1]);
         }
         __syncthreads();
         bc1 = s_bc[0];

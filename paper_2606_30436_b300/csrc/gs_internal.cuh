@@ -38,6 +38,57 @@ __host__ __device__ __forceinline__ long long ceil_div(long long a, long long b)
 // launched waits before anything else, so each one completes after all earlier ones.
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Adam's bias corrections from a device step counter t (a non-negative integer) without FP64,
+// which issues at a small fraction of the FP32 rate on B300 (two FP64 powers at the start of
+// every CTA held the Gaussians' Adam back by about 0.01 ms).  A value is the unevaluated sum
+// hi + lo of two floats (double-float arithmetic): a product is rounded and its exact error
+// taken with one FMA (Dekker's exact product), a sum's error with Knuth's two-sum, and beta^t
+// by binary exponentiation over the bits of t, so 1 - beta^t carries about 44 significant bits
+// and each correction is rounded to float once.  The _rn intrinsics keep the compiler from
+// fusing the rounded operations these error terms depend on.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)));
+    return ff_two_sum(p, e);
+}
+__device__ __forceinline__ FF ff_one_minus_pow(float beta, long long t) {
+    FF r{1.0f, 0.0f}, x{beta, 0.0f};
+    for (; t > 0; t >>= 1) {
+        if (t & 1) r = ff_mul(r, x);
+        x = ff_mul(x, x);
+    }
+    const FF d = ff_two_sum(1.0f, -r.hi);
+    return ff_two_sum(d.hi, __fsub_rn(d.lo, r.lo));
+}
+__device__ __forceinline__ float ff_recip(FF a) {  // 1 / (hi + lo): one Newton step from 1 / hi
+    const float q = __fdiv_rn(1.0f, a.hi);
+    const float e = fmaf(-q, a.lo, fmaf(-q, a.hi, 1.0f));
+    return fmaf(q, e, q);
+}
+__device__ __forceinline__ FF ff_sqrt(FF a) {  // sqrt(hi + lo): one Newton step from sqrt(hi)
+    const float s = __fsqrt_rn(a.hi);
+    const float r = __fadd_rn(fmaf(-s, s, a.hi), a.lo);
+    return ff_two_sum(s, __fdiv_rn(r, __fmul_rn(2.0f, s)));
+}
+// 1 / (1 - b1^t) and 1 / sqrt(1 - b2^t)
+__device__ __forceinline__ void adam_bias_inv(float b1, float b2, long long t, float &inv_bc1, float &inv_sqrt_bc2) {
+    inv_bc1 = ff_recip(ff_one_minus_pow(b1, t));
+    inv_sqrt_bc2 = ff_recip(ff_sqrt(ff_one_minus_pow(b2, t)));
+}
+// 1 - b1^t and 1 - b2^t
+__device__ __forceinline__ void adam_bias(float b1, float b2, long long t, float &bc1, float &bc2) {
+    const FF a = ff_one_minus_pow(b1, t), b = ff_one_minus_pow(b2, t);
+    bc1 = __fadd_rn(a.hi, a.lo);
+    bc2 = __fadd_rn(b.hi, b.lo);
+}
+
 template <typename... KArgs, typename... Args>
 inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                        Args &&...args) {

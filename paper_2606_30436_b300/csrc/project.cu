@@ -313,9 +313,7 @@ __global__ void __launch_bounds__(ADAM ? kFusedThreads : 256, ADAM ? 4 : 3) k_pr
     if (ADAM && fa.step_dev) {  // bias corrections from the device step counter (graph replay)
         __shared__ float s_bc[2];
         if (threadIdx.x == 0) {
-            const double t = (double)*fa.step_dev;
-            s_bc[0] = (float)(1.0 / (1.0 - pow((double)fa.b1, t)));
-            s_bc[1] = (float)(1.0 / sqrt(1.0 - pow((double)fa.b2, t)));
+            adam_bias_inv(fa.b1, fa.b2, *fa.step_dev, s_bc[0], s_bc[1]);
         }
         __syncthreads();
         fa.inv_bc1 = s_bc[0];

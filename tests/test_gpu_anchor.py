@@ -304,10 +304,14 @@ def test_anchor_graph_replay_matches_eager_steps():
         runs.append((losses, st.model.data.clone(), st.model.weights.clone(), st.step_count))
     (la, pa, wa, ca), (lb, pb, wb, cb) = runs
     assert ca == cb == 4
-    # the compositing backward sums with atomics: two runs agree to FP32 rounding
-    assert np.allclose(la, lb, rtol=1e-4, atol=0.0), (la, lb)
-    assert rel_l2(pa.cpu().numpy(), pb.cpu().numpy()) < 1e-5
-    assert rel_l2(wa.cpu().numpy(), wb.cpu().numpy()) < 1e-5
+    # the compositing backward sums with atomics, so two runs differ in the last bits of their
+    # gradients, and Adam (eps 1e-15) turns such differences in near-zero gradients into
+    # full-size steps: over four steps the losses drift apart by up to ~1e-4.  The first loss
+    # is exact; a wrong step counter or bias correction moves the later ones by far more.
+    assert la[0] == lb[0]
+    assert np.allclose(la, lb, rtol=2e-3, atol=0.0), (la, lb)
+    assert rel_l2(pa.cpu().numpy(), pb.cpu().numpy()) < 1e-4
+    assert rel_l2(wa.cpu().numpy(), wb.cpu().numpy()) < 1e-4
 
 
 def test_anchor_steps_lower_the_loss():
